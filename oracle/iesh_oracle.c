@@ -1,0 +1,1077 @@
+/*
+ * iesh_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, FP64 CPU restatement of one independent electron surface
+ * hopping (IESH) trajectory step, written from Gardner, Corken, Janke,
+ * Habershon and Maurer, "Efficient implementation and performance analysis of
+ * the independent electron surface hopping method for dynamics at metal
+ * surfaces" (arXiv:2212.00518).  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it.  It shares no code, header,
+ * table or helper with the CUDA library; the two only see the same seeded
+ * inputs.
+ *
+ * Every quantity is computed from its plain definition:
+ *   - eigenpairs of the dense one-electron Hamiltonian (Sec. II B, Eq. for
+ *     H_el^1) by this file's own cyclic Jacobi method;
+ *   - the coupling matrix Q^T (dH/dx) Q as a dense triple product (Sec. II B,
+ *     NAC equation), d_jk = <j|d/dx k>;
+ *   - the exponential integrator (Sec. II C) by this file's own complex
+ *     Hermitian Jacobi diagonalisation, c <- P exp(-i D dt) P^H c;
+ *   - determinants by Gaussian elimination, the overlap inverse by
+ *     Gauss-Jordan elimination, and in "brute" mode one determinant per
+ *     candidate configuration (Sec. II B, amplitude equations);
+ *   - Gauss-Legendre nodes by the Golub-Welsch method (Appendix A).
+ *
+ * Readings of the paper that the code takes (the paper is silent or garbled):
+ *   R1 NAC sign: d_jk = <j|d_x k> = T_jk / (lambda_k - lambda_j), the TDSE is
+ *      i c_j' = lambda_j c_j - i v sum_k d_jk c_k and B_jk uses the same d
+ *      (Tully 1990 convention; Sec. II B prints the denominator reversed).
+ *   R2 gauge: eigenvalues ascending, eigenvector impurity component > 0.
+ *   R3 generator of the exponential integrator over a step is the average of
+ *      the generators at the two ends of the step.
+ *   R4 candidate configuration J replaces slot a of the occupied list in place
+ *      (orbital m takes the place of s_a); g_{a->m} =
+ *      max(0, -2 dt v Re(<J|psi>/<K|psi>) d_{m,s_a}).
+ *   R5 candidates are summed in the order a ascending (slots of the sorted
+ *      occupation list), then m ascending; one uniform number per step.
+ *   R6 a frustrated hop leaves momentum and occupations unchanged.
+ *   R7 after an accepted hop the force is recomputed on the new surface; the
+ *      generator stored for the next step uses the post-hop velocity.
+ *   R8 Gauss-Legendre split discretisation: M/2 nodes in each half, weights
+ *      positive, V_k = sqrt(Gamma / 2 pi) sqrt(w_k) f(x).
+ */
+#include <complex.h>
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+/* ------------------------------------------------------------------------ */
+/* Status bits (per trajectory).                                             */
+/* ------------------------------------------------------------------------ */
+#define ORC_ST_JACOBI_NONCONV 1u
+#define ORC_ST_SINGULAR 2u
+#define ORC_ST_NAN 4u
+
+/* ------------------------------------------------------------------------ */
+/* Cyclic Jacobi for a real symmetric matrix (row-major, destroyed).         */
+/* On return evals[i], V[:, i] are eigenpairs (unsorted).                    */
+/* ------------------------------------------------------------------------ */
+int orc_jacobi_sym(int n, double *A, double *evals, double *V)
+{
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) V[i * n + j] = (i == j) ? 1.0 : 0.0;
+    int converged = 0;
+    for (int sweep = 0; sweep < 100; sweep++) {
+        double off = 0.0;
+        for (int p = 0; p < n; p++)
+            for (int q = p + 1; q < n; q++) off += fabs(A[p * n + q]);
+        if (off == 0.0) { converged = 1; break; }
+        for (int p = 0; p < n; p++) {
+            for (int q = p + 1; q < n; q++) {
+                double apq = A[p * n + q];
+                double app = A[p * n + p], aqq = A[q * n + q];
+                if (sweep >= 4 && fabs(apq) * 100.0 + fabs(app) == fabs(app) &&
+                    fabs(apq) * 100.0 + fabs(aqq) == fabs(aqq)) {
+                    A[p * n + q] = A[q * n + p] = 0.0;
+                    continue;
+                }
+                if (apq == 0.0) continue;
+                double theta = (aqq - app) / (2.0 * apq);
+                double t;
+                if (fabs(theta) > 1e150) t = 0.5 / theta;
+                else t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                /* A <- A J, J = [[c, s], [-s, c]] on (p, q) */
+                for (int r = 0; r < n; r++) {
+                    double arp = A[r * n + p], arq = A[r * n + q];
+                    A[r * n + p] = c * arp - s * arq;
+                    A[r * n + q] = s * arp + c * arq;
+                }
+                /* A <- J^T A */
+                for (int r = 0; r < n; r++) {
+                    double apr = A[p * n + r], aqr = A[q * n + r];
+                    A[p * n + r] = c * apr - s * aqr;
+                    A[q * n + r] = s * apr + c * aqr;
+                }
+                A[p * n + q] = A[q * n + p] = 0.0;
+                for (int r = 0; r < n; r++) {
+                    double vrp = V[r * n + p], vrq = V[r * n + q];
+                    V[r * n + p] = c * vrp - s * vrq;
+                    V[r * n + q] = s * vrp + c * vrq;
+                }
+            }
+        }
+    }
+    for (int i = 0; i < n; i++) evals[i] = A[i * n + i];
+    return converged ? 0 : -1;
+}
+
+/* Cyclic Jacobi for a complex Hermitian matrix (row-major, destroyed).
+ * Each rotation first makes a_pq real by a phase on index q, then applies a
+ * real plane rotation.  On return evals[i], V[:, i] are eigenpairs. */
+int orc_jacobi_herm(int n, cplx *A, double *evals, cplx *V)
+{
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) V[i * n + j] = (i == j) ? 1.0 : 0.0;
+    for (int i = 0; i < n; i++) A[i * n + i] = creal(A[i * n + i]);
+    int converged = 0;
+    for (int sweep = 0; sweep < 100; sweep++) {
+        double off = 0.0;
+        for (int p = 0; p < n; p++)
+            for (int q = p + 1; q < n; q++) off += cabs(A[p * n + q]);
+        if (off == 0.0) { converged = 1; break; }
+        for (int p = 0; p < n; p++) {
+            for (int q = p + 1; q < n; q++) {
+                cplx apq = A[p * n + q];
+                double r = cabs(apq);
+                double app = creal(A[p * n + p]), aqq = creal(A[q * n + q]);
+                if (sweep >= 4 && r * 100.0 + fabs(app) == fabs(app) &&
+                    r * 100.0 + fabs(aqq) == fabs(aqq)) {
+                    A[p * n + q] = A[q * n + p] = 0.0;
+                    continue;
+                }
+                if (r == 0.0) continue;
+                /* phase: column q times e^{-i phi}, row q times e^{+i phi} */
+                cplx ph = conj(apq) / r; /* e^{-i phi} */
+                for (int k = 0; k < n; k++) {
+                    A[k * n + q] *= ph;
+                    A[q * n + k] *= conj(ph);
+                    V[k * n + q] *= ph;
+                }
+                A[q * n + q] = aqq;
+                A[p * n + q] = r;
+                A[q * n + p] = r;
+                double theta = (aqq - app) / (2.0 * r);
+                double t;
+                if (fabs(theta) > 1e150) t = 0.5 / theta;
+                else t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; k++) {
+                    cplx akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - s * akq;
+                    A[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; k++) {
+                    cplx apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - s * aqk;
+                    A[q * n + k] = s * apk + c * aqk;
+                }
+                A[p * n + q] = A[q * n + p] = 0.0;
+                A[p * n + p] = creal(A[p * n + p]);
+                A[q * n + q] = creal(A[q * n + q]);
+                for (int k = 0; k < n; k++) {
+                    cplx vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - s * vkq;
+                    V[k * n + q] = s * vkp + c * vkq;
+                }
+            }
+        }
+    }
+    for (int i = 0; i < n; i++) evals[i] = creal(A[i * n + i]);
+    return converged ? 0 : -1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gauss-Legendre nodes and weights on [-1, 1] by Golub-Welsch: the nodes    */
+/* are the eigenvalues of the symmetric Jacobi matrix of the Legendre        */
+/* recurrence (off-diagonal k / sqrt(4k^2 - 1)), the weights twice the       */
+/* squared first eigenvector components (Appendix A).                        */
+/* ------------------------------------------------------------------------ */
+int orc_gauss_legendre(int n, double *x, double *w)
+{
+    double *J = calloc((size_t)n * n, sizeof(double));
+    double *V = malloc((size_t)n * n * sizeof(double));
+    double *ev = malloc((size_t)n * sizeof(double));
+    for (int k = 1; k < n; k++) {
+        double b = k / sqrt(4.0 * k * k - 1.0);
+        J[(k - 1) * n + k] = b;
+        J[k * n + (k - 1)] = b;
+    }
+    int rc = orc_jacobi_sym(n, J, ev, V);
+    /* sort ascending */
+    int *idx = malloc((size_t)n * sizeof(int));
+    for (int i = 0; i < n; i++) idx[i] = i;
+    for (int i = 0; i < n; i++)
+        for (int j = i + 1; j < n; j++)
+            if (ev[idx[j]] < ev[idx[i]]) { int t = idx[i]; idx[i] = idx[j]; idx[j] = t; }
+    for (int i = 0; i < n; i++) {
+        x[i] = ev[idx[i]];
+        double v0 = V[0 * n + idx[i]];
+        w[i] = 2.0 * v0 * v0;
+    }
+    free(idx); free(J); free(V); free(ev);
+    return rc;
+}
+
+/* Bath discretisation (Appendix A).
+ * disc 0: Gauss-Legendre split at mu: n_lo nodes on [a, mu], M - n_lo on
+ *         [mu, b] (n_lo = M/2 when n_lo < 0 is passed).
+ * disc 1: trapezoid, eps_k = a + (k-1)(b-a)/M, w_k = (b-a)/M.
+ * eps ascending; w are the quadrature weights. */
+int orc_bath(int disc, int M, double a, double b, double mu, int n_lo, double *eps, double *w)
+{
+    if (disc == 1) {
+        for (int k = 0; k < M; k++) {
+            eps[k] = a + k * (b - a) / M;
+            w[k] = (b - a) / M;
+        }
+        return 0;
+    }
+    if (n_lo < 0) n_lo = M / 2;
+    int n_hi = M - n_lo;
+    int rc = 0;
+    if (n_lo > 0) {
+        double *x = malloc(n_lo * sizeof(double)), *wl = malloc(n_lo * sizeof(double));
+        rc |= orc_gauss_legendre(n_lo, x, wl);
+        for (int k = 0; k < n_lo; k++) {
+            eps[k] = 0.5 * (mu - a) * x[k] + 0.5 * (a + mu);
+            w[k] = 0.5 * (mu - a) * wl[k];
+        }
+        free(x); free(wl);
+    }
+    if (n_hi > 0) {
+        double *x = malloc(n_hi * sizeof(double)), *wh = malloc(n_hi * sizeof(double));
+        rc |= orc_gauss_legendre(n_hi, x, wh);
+        for (int k = 0; k < n_hi; k++) {
+            eps[n_lo + k] = 0.5 * (b - mu) * x[k] + 0.5 * (mu + b);
+            w[n_lo + k] = 0.5 * (b - mu) * wh[k];
+        }
+        free(x); free(wh);
+    }
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Models (Sec. II A, Sec. III B double well, Sec. III C desorption model).  */
+/* All quantities in atomic units.                                           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int kind;        /* 0 harmonic double well, 1 desorption (Morse / repulsive /
+                        tanh coupling), 2 Morse + image-charge level + Gaussian coupling */
+    double mass;
+    double par[16];
+    double Vbar;     /* sqrt(Gamma / (2 pi)) */
+    int M, Ne;
+    const double *eps; /* [M] bath energies, ascending */
+    const double *sqw; /* [M] sqrt of quadrature weights */
+} orc_model;
+
+/* out: U0, dU0/dx, h = U1 - U0, dh/dx, f, df/dx with V_k(x) = Vbar sqw_k f(x) */
+void orc_model_eval(const orc_model *md, double x, double *out)
+{
+    const double *P = md->par;
+    double U0, dU0, U1, dU1, f, df;
+    if (md->kind == 0) {
+        /* U0 = m w^2 x^2 / 2, U1 = m w^2 (x - g)^2 / 2 + dG; P = {w, g, dG} */
+        double mw2 = md->mass * P[0] * P[0];
+        U0 = 0.5 * mw2 * x * x;
+        dU0 = mw2 * x;
+        U1 = 0.5 * mw2 * (x - P[1]) * (x - P[1]) + P[2];
+        dU1 = mw2 * (x - P[1]);
+        f = 1.0;
+        df = 0.0;
+    } else if (md->kind == 1) {
+        /* P = {De, x0, a, c, D1, D2, ap, Vinf, q, at, xt} */
+        double De = P[0], x0 = P[1], a = P[2], c = P[3], D1 = P[4], D2 = P[5], ap = P[6],
+               Vinf = P[7], q = P[8], at = P[9], xt = P[10];
+        double e = exp(-a * (x - x0));
+        U0 = De * (e - 1.0) * (e - 1.0) + c;
+        dU0 = De * 2.0 * (e - 1.0) * (-a * e);
+        double e1 = exp(-ap * (x - x0));
+        U1 = D1 * e1 * e1 - D2 * e1 + Vinf;
+        dU1 = -2.0 * ap * D1 * e1 * e1 + ap * D2 * e1;
+        double th = tanh((x - xt) / at);
+        f = 0.5 * (1.0 - q) * (1.0 - th) + q;
+        df = -0.5 * (1.0 - q) * (1.0 - th * th) / at;
+    } else {
+        /* P = {De, x0, a, c, h_inf, z_im, a_c, z_c, sigma} */
+        double De = P[0], x0 = P[1], a = P[2], c = P[3], hinf = P[4], zim = P[5], ac = P[6],
+               zc = P[7], sg = P[8];
+        double e = exp(-a * (x - x0));
+        U0 = De * (e - 1.0) * (e - 1.0) + c;
+        dU0 = De * 2.0 * (e - 1.0) * (-a * e);
+        double r = sqrt((x - zim) * (x - zim) + ac * ac);
+        double h = hinf - 0.25 / r;
+        double dh = 0.25 * (x - zim) / (r * r * r);
+        U1 = U0 + h;
+        dU1 = dU0 + dh;
+        double u = (x - zc) / sg;
+        f = exp(-0.5 * u * u);
+        df = -u / sg * f;
+    }
+    out[0] = U0;
+    out[1] = dU0;
+    out[2] = U1 - U0;
+    out[3] = dU1 - dU0;
+    out[4] = f;
+    out[5] = df;
+}
+
+/* Dense one-electron Hamiltonian (Sec. II B) and its x-derivative, index 0 the
+ * impurity |d>, index k+1 bath state k.  N = M + 1. */
+void orc_build_H(const orc_model *md, double x, double *H, double *dH)
+{
+    int N = md->M + 1;
+    double mo[6];
+    orc_model_eval(md, x, mo);
+    memset(H, 0, sizeof(double) * N * N);
+    memset(dH, 0, sizeof(double) * N * N);
+    H[0] = mo[2];
+    dH[0] = mo[3];
+    for (int k = 0; k < md->M; k++) {
+        double Vk = md->Vbar * md->sqw[k] * mo[4];
+        double dVk = md->Vbar * md->sqw[k] * mo[5];
+        H[(k + 1) * N + (k + 1)] = md->eps[k];
+        H[0 * N + (k + 1)] = H[(k + 1) * N + 0] = Vk;
+        dH[0 * N + (k + 1)] = dH[(k + 1) * N + 0] = dVk;
+    }
+}
+
+/* Eigenpairs of H(x), ascending, column i of Q (row-major Q[r*N+i]) with the
+ * gauge Q[0][i] > 0 (largest component positive if the impurity component
+ * vanishes).  Returns 0 on success. */
+int orc_eigen(const orc_model *md, double x, double *lam, double *Q)
+{
+    int N = md->M + 1;
+    double *H = malloc(sizeof(double) * N * N), *dH = malloc(sizeof(double) * N * N);
+    double *V = malloc(sizeof(double) * N * N), *ev = malloc(sizeof(double) * N);
+    int *idx = malloc(sizeof(int) * N);
+    orc_build_H(md, x, H, dH);
+    int rc = orc_jacobi_sym(N, H, ev, V);
+    for (int i = 0; i < N; i++) idx[i] = i;
+    for (int i = 0; i < N; i++)
+        for (int j = i + 1; j < N; j++)
+            if (ev[idx[j]] < ev[idx[i]]) { int t = idx[i]; idx[i] = idx[j]; idx[j] = t; }
+    for (int i = 0; i < N; i++) {
+        int c = idx[i];
+        lam[i] = ev[c];
+        double sgn;
+        if (V[0 * N + c] != 0.0) {
+            sgn = V[0 * N + c] > 0 ? 1.0 : -1.0;
+        } else {
+            int big = 0;
+            for (int r = 1; r < N; r++)
+                if (fabs(V[r * N + c]) > fabs(V[big * N + c])) big = r;
+            sgn = V[big * N + c] >= 0 ? 1.0 : -1.0;
+        }
+        for (int r = 0; r < N; r++) Q[r * N + i] = sgn * V[r * N + c];
+    }
+    free(H); free(dH); free(V); free(ev); free(idx);
+    return rc;
+}
+
+/* T = Q^T (dH/dx) Q (dense triple product) and d_jk = <j|d_x k> =
+ * T_jk / (lam_k - lam_j) for j != k, d_jj = 0 (reading R1). */
+void orc_coupling(const orc_model *md, double x, const double *lam, const double *Q, double *T,
+                  double *d)
+{
+    int N = md->M + 1;
+    double *H = malloc(sizeof(double) * N * N), *dH = malloc(sizeof(double) * N * N);
+    double *tmp = malloc(sizeof(double) * N * N);
+    orc_build_H(md, x, H, dH);
+    /* tmp = dH Q */
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            double s = 0.0;
+            for (int k = 0; k < N; k++) s += dH[i * N + k] * Q[k * N + j];
+            tmp[i * N + j] = s;
+        }
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            double s = 0.0;
+            for (int k = 0; k < N; k++) s += Q[k * N + i] * tmp[k * N + j];
+            T[i * N + j] = s;
+        }
+    for (int j = 0; j < N; j++)
+        for (int k = 0; k < N; k++)
+            d[j * N + k] = (j == k) ? 0.0 : T[j * N + k] / (lam[k] - lam[j]);
+    free(H); free(dH); free(tmp);
+}
+
+/* Hellmann-Feynman force on the occupied surface of Eq. (classical IESH
+ * Hamiltonian): F = -dU0/dx - sum_{i in s} dlambda_i/dx, dlambda_i/dx = T_ii. */
+double orc_force(const orc_model *md, double x, const double *T, const int *occ)
+{
+    int N = md->M + 1;
+    double mo[6];
+    orc_model_eval(md, x, mo);
+    double F = -mo[1];
+    for (int a = 0; a < md->Ne; a++) F -= T[occ[a] * N + occ[a]];
+    return F;
+}
+
+/* Exponential integrator (Sec. II C): C <- P exp(-i D dt) P^H C with
+ * P D P^H = Abar, Abar = (A_0 + A_1) / 2, A_jk = lam_j delta_jk - i v d_jk.
+ * C is N x Ne row-major (row = adiabatic orbital, column = electron). */
+int orc_propagate(int N, int Ne, const double *lam0, const double *d0, double v0,
+                  const double *lam1, const double *d1, double v1, double dt, cplx *C)
+{
+    cplx *A = malloc(sizeof(cplx) * N * N), *P = malloc(sizeof(cplx) * N * N);
+    cplx *tmp = malloc(sizeof(cplx) * N * Ne);
+    double *D = malloc(sizeof(double) * N);
+    for (int j = 0; j < N; j++)
+        for (int k = 0; k < N; k++) {
+            if (j == k) A[j * N + k] = 0.5 * (lam0[j] + lam1[j]);
+            else A[j * N + k] = -I * 0.5 * (v0 * d0[j * N + k] + v1 * d1[j * N + k]);
+        }
+    int rc = orc_jacobi_herm(N, A, D, P);
+    /* tmp = exp(-i D dt) P^H C */
+    for (int i = 0; i < N; i++) {
+        cplx ph = cexp(-I * D[i] * dt);
+        for (int e = 0; e < Ne; e++) {
+            cplx s = 0.0;
+            for (int k = 0; k < N; k++) s += conj(P[k * N + i]) * C[k * Ne + e];
+            tmp[i * Ne + e] = ph * s;
+        }
+    }
+    for (int j = 0; j < N; j++)
+        for (int e = 0; e < Ne; e++) {
+            cplx s = 0.0;
+            for (int i = 0; i < N; i++) s += P[j * N + i] * tmp[i * Ne + e];
+            C[j * Ne + e] = s;
+        }
+    free(A); free(P); free(tmp); free(D);
+    return rc;
+}
+
+/* Determinant by Gaussian elimination with partial pivoting (A destroyed). */
+cplx orc_det(int n, cplx *A)
+{
+    cplx det = 1.0;
+    for (int c = 0; c < n; c++) {
+        int piv = c;
+        for (int r = c + 1; r < n; r++)
+            if (cabs(A[r * n + c]) > cabs(A[piv * n + c])) piv = r;
+        if (A[piv * n + c] == 0.0) return 0.0;
+        if (piv != c) {
+            for (int k = 0; k < n; k++) {
+                cplx t = A[c * n + k]; A[c * n + k] = A[piv * n + k]; A[piv * n + k] = t;
+            }
+            det = -det;
+        }
+        det *= A[c * n + c];
+        for (int r = c + 1; r < n; r++) {
+            cplx f = A[r * n + c] / A[c * n + c];
+            for (int k = c; k < n; k++) A[r * n + k] -= f * A[c * n + k];
+        }
+    }
+    return det;
+}
+
+/* Inverse by Gauss-Jordan elimination with partial pivoting. */
+int orc_inverse(int n, const cplx *A_in, cplx *Ainv)
+{
+    cplx *A = malloc(sizeof(cplx) * n * n);
+    memcpy(A, A_in, sizeof(cplx) * n * n);
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) Ainv[i * n + j] = (i == j) ? 1.0 : 0.0;
+    for (int c = 0; c < n; c++) {
+        int piv = c;
+        for (int r = c + 1; r < n; r++)
+            if (cabs(A[r * n + c]) > cabs(A[piv * n + c])) piv = r;
+        if (A[piv * n + c] == 0.0) { free(A); return -1; }
+        if (piv != c)
+            for (int k = 0; k < n; k++) {
+                cplx t = A[c * n + k]; A[c * n + k] = A[piv * n + k]; A[piv * n + k] = t;
+                t = Ainv[c * n + k]; Ainv[c * n + k] = Ainv[piv * n + k]; Ainv[piv * n + k] = t;
+            }
+        cplx inv = 1.0 / A[c * n + c];
+        for (int k = 0; k < n; k++) { A[c * n + k] *= inv; Ainv[c * n + k] *= inv; }
+        for (int r = 0; r < n; r++) {
+            if (r == c) continue;
+            cplx f = A[r * n + c];
+            if (f == 0.0) continue;
+            for (int k = 0; k < n; k++) {
+                A[r * n + k] -= f * A[c * n + k];
+                Ainv[r * n + k] -= f * Ainv[c * n + k];
+            }
+        }
+    }
+    free(A);
+    return 0;
+}
+
+/* Hop probabilities (Sec. II B, Eqs. for g, B, A and <k|psi> = det S).
+ * S_ij = C[occ_i][j]; for slot a and unoccupied m, the candidate J replaces
+ * row a of S by row m of C; ratio R = det S_J / det S.
+ * brute = 1: one Gaussian-elimination determinant per candidate.
+ * brute = 0: R_ma = (C[m,:] S^{-1})_a with S^{-1} from Gauss-Jordan.
+ * g[a*N + m] = max(0, -2 dt v Re(R_ma) d[m][occ_a]); occupied m get 0.
+ * Returns det S in *detS; status bit on a singular S. */
+int orc_hop_probs(int N, int Ne, const int *occ, const cplx *C, const double *d, double v,
+                  double dt, int brute, double *g, double *Rre, cplx *detS)
+{
+    cplx *S = malloc(sizeof(cplx) * Ne * Ne), *W = malloc(sizeof(cplx) * Ne * Ne);
+    char *isocc = calloc(N, 1);
+    for (int a = 0; a < Ne; a++) isocc[occ[a]] = 1;
+    for (int i = 0; i < Ne; i++)
+        for (int j = 0; j < Ne; j++) S[i * Ne + j] = C[occ[i] * Ne + j];
+    memcpy(W, S, sizeof(cplx) * Ne * Ne);
+    cplx det = orc_det(Ne, W);
+    *detS = det;
+    for (int i = 0; i < Ne * N; i++) { g[i] = 0.0; if (Rre) Rre[i] = 0.0; }
+    int rc = 0;
+    if (det == 0.0) { rc = -1; goto out; }
+    if (brute) {
+        for (int a = 0; a < Ne; a++)
+            for (int m = 0; m < N; m++) {
+                if (isocc[m]) continue;
+                memcpy(W, S, sizeof(cplx) * Ne * Ne);
+                for (int j = 0; j < Ne; j++) W[a * Ne + j] = C[m * Ne + j];
+                cplx R = orc_det(Ne, W) / det;
+                double gam = -2.0 * dt * v * creal(R) * d[m * N + occ[a]];
+                g[a * N + m] = gam > 0.0 ? gam : 0.0;
+                if (Rre) Rre[a * N + m] = creal(R);
+            }
+    } else {
+        cplx *Sinv = malloc(sizeof(cplx) * Ne * Ne);
+        if (orc_inverse(Ne, S, Sinv) != 0) { free(Sinv); rc = -1; goto out; }
+        for (int m = 0; m < N; m++) {
+            if (isocc[m]) continue;
+            for (int a = 0; a < Ne; a++) {
+                cplx R = 0.0;
+                for (int j = 0; j < Ne; j++) R += C[m * Ne + j] * Sinv[j * Ne + a];
+                double gam = -2.0 * dt * v * creal(R) * d[m * N + occ[a]];
+                g[a * N + m] = gam > 0.0 ? gam : 0.0;
+                if (Rre) Rre[a * N + m] = creal(R);
+            }
+        }
+        free(Sinv);
+    }
+out:
+    free(S); free(W); free(isocc);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC11, 2011): ten rounds of     */
+/* two 32x32->64 multiplications with the Weyl key schedule.                 */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out)
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform in [0, 1) with 53 random bits from two 32-bit words. */
+double orc_u53(uint32_t hi, uint32_t lo)
+{
+    return ((double)(hi >> 5) * 67108864.0 + (double)(lo >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+/* Counter layout shared by definition with the CUDA library (not by code):
+ * key = (seed low, seed high); counter = (trajectory, stream, n_lo, n_hi). */
+void orc_draw(uint64_t seed, uint32_t traj, uint32_t stream, uint64_t n, uint32_t *out)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {traj, stream, (uint32_t)n, (uint32_t)(n >> 32)};
+    orc_philox4x32_10(ctr, key, out);
+}
+
+#define ORC_STREAM_HOP 0u
+#define ORC_STREAM_NUC 1u
+#define ORC_STREAM_ELEC 2u
+
+/* Hop uniform for trajectory traj at step index n (0-based). */
+double orc_hop_uniform(uint64_t seed, uint32_t traj, uint64_t n)
+{
+    uint32_t o[4];
+    orc_draw(seed, traj, ORC_STREAM_HOP, n, o);
+    return orc_u53(o[0], o[1]);
+}
+
+/* Thermal nuclear sample (Sec. III B Boltzmann density; Sec. III C Wigner
+ * density with Q = beta w / (2 tanh(beta w / 2))): x = x_eq + sx n1,
+ * p = sp n2 with (n1, n2) standard normal by Box-Muller. */
+void orc_sample_nuclear(uint64_t seed, uint32_t traj, double mass, double omega, double x_eq,
+                        double kT, int wigner, double *x, double *p)
+{
+    uint32_t o[4];
+    orc_draw(seed, traj, ORC_STREAM_NUC, 0, o);
+    double u1 = orc_u53(o[0], o[1]), u2 = orc_u53(o[2], o[3]);
+    double r = sqrt(-2.0 * log(1.0 - u1));
+    double n1 = r * cos(2.0 * M_PI * u2), n2 = r * sin(2.0 * M_PI * u2);
+    double kTe = kT;
+    if (wigner && kT > 0) {
+        double bw = omega / kT;
+        kTe = kT * (bw / (2.0 * tanh(0.5 * bw)));
+    }
+    *x = x_eq + sqrt(kTe / (mass * omega * omega)) * n1;
+    *p = sqrt(mass * kTe) * n2;
+}
+
+/* Exact canonical sample of Ne occupied orbitals among energies lam[0..N-1]
+ * at temperature kT (weight exp(-sum_{i in s} lam_i / kT)): orbital k is
+ * occupied with probability w_k Z(k+1, n-1) / Z(k, n), Z the partition
+ * function of the remaining orbitals with n electrons.  kT = 0 fills the
+ * lowest Ne.  occ returned ascending. */
+int orc_sample_occupations(uint64_t seed, uint32_t traj, int N, int Ne, const double *lam, double kT,
+                           int *occ)
+{
+    if (kT <= 0.0) {
+        for (int a = 0; a < Ne; a++) occ[a] = a;
+        return 0;
+    }
+    /* logZ[k][n], k = 0..N, n = 0..Ne, in log form */
+    double *lZ = malloc(sizeof(double) * (N + 1) * (Ne + 1));
+#define LZ(k, n) lZ[(k) * (Ne + 1) + (n)]
+    double ref = lam[0];
+    for (int k = 0; k <= N; k++)
+        for (int n = 0; n <= Ne; n++) LZ(k, n) = -INFINITY;
+    LZ(N, 0) = 0.0;
+    for (int k = N - 1; k >= 0; k--) {
+        double lw = -(lam[k] - ref) / kT;
+        for (int n = 0; n <= Ne; n++) {
+            double a = LZ(k + 1, n);
+            double b = (n > 0) ? lw + LZ(k + 1, n - 1) : -INFINITY;
+            double mx = a > b ? a : b;
+            LZ(k, n) = (mx == -INFINITY) ? -INFINITY : mx + log(exp(a - mx) + exp(b - mx));
+        }
+    }
+    int n = Ne, cnt = 0;
+    for (int k = 0; k < N && n > 0; k++) {
+        uint32_t o[4];
+        orc_draw(seed, traj, ORC_STREAM_ELEC, (uint64_t)k, o);
+        double u = orc_u53(o[0], o[1]);
+        double lw = -(lam[k] - ref) / kT;
+        double pk = exp(lw + LZ(k + 1, n - 1) - LZ(k, n));
+        if (u < pk) { occ[cnt++] = k; n--; }
+    }
+#undef LZ
+    free(lZ);
+    return (cnt == Ne) ? 0 : -1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One trajectory.                                                           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double x, p, F, v_prev;
+    int *occ;      /* [Ne] ascending */
+    cplx *C;       /* [N][Ne] */
+    double *lam;   /* [N] at current x */
+    double *Q, *T, *d; /* [N][N] at current x */
+    uint32_t status;
+    int64_t hops, frustrated;
+} orc_traj;
+
+static void traj_alloc(orc_traj *t, int N, int Ne)
+{
+    memset(t, 0, sizeof(*t));
+    t->occ = malloc(sizeof(int) * Ne);
+    t->C = malloc(sizeof(cplx) * N * Ne);
+    t->lam = malloc(sizeof(double) * N);
+    t->Q = malloc(sizeof(double) * N * N);
+    t->T = malloc(sizeof(double) * N * N);
+    t->d = malloc(sizeof(double) * N * N);
+}
+
+static void traj_free(orc_traj *t)
+{
+    free(t->occ); free(t->C); free(t->lam); free(t->Q); free(t->T); free(t->d);
+}
+
+/* Eigenpairs, couplings and force at the current x and occupations. */
+static void traj_prepare(const orc_model *md, orc_traj *t)
+{
+    if (orc_eigen(md, t->x, t->lam, t->Q) != 0) t->status |= ORC_ST_JACOBI_NONCONV;
+    orc_coupling(md, t->x, t->lam, t->Q, t->T, t->d);
+    t->F = orc_force(md, t->x, t->T, t->occ);
+    t->v_prev = t->p / md->mass;
+}
+
+/* Observables: impurity population of the occupied surface
+ * sum_{i in s} Q_0i^2, and of the wavefunction sum_e |sum_i Q_0i C_ie|^2. */
+static void traj_populations(const orc_model *md, const orc_traj *t, double *psh, double *pwf)
+{
+    int N = md->M + 1, Ne = md->Ne;
+    double s = 0.0;
+    for (int a = 0; a < Ne; a++) s += t->Q[0 * N + t->occ[a]] * t->Q[0 * N + t->occ[a]];
+    *psh = s;
+    double w = 0.0;
+    for (int e = 0; e < Ne; e++) {
+        cplx amp = 0.0;
+        for (int i = 0; i < N; i++) amp += t->Q[0 * N + i] * t->C[i * Ne + e];
+        w += creal(amp) * creal(amp) + cimag(amp) * cimag(amp);
+    }
+    *pwf = w;
+}
+
+/* One step (order of the paper's integrator, Sec. II C, velocity Verlet for
+ * the nuclei with the exponential integrator for the electrons, then the
+ * hopping procedure of Sec. II B).  n = index of this step.  Optional
+ * outputs of the step's hop probabilities g[Ne*N] and uniform zeta. */
+static void traj_step(const orc_model *md, orc_traj *t, double dt, uint64_t seed, uint32_t traj,
+                      uint64_t n, int brute, double *g_out, double *zeta_out, int *hop_out)
+{
+    int N = md->M + 1, Ne = md->Ne;
+    double m = md->mass;
+    double *lam0 = malloc(sizeof(double) * N), *d0 = malloc(sizeof(double) * N * N);
+    memcpy(lam0, t->lam, sizeof(double) * N);
+    memcpy(d0, t->d, sizeof(double) * N * N);
+    double v0 = t->v_prev;
+
+    t->p += 0.5 * dt * t->F;
+    t->x += dt * t->p / m;
+    if (orc_eigen(md, t->x, t->lam, t->Q) != 0) t->status |= ORC_ST_JACOBI_NONCONV;
+    orc_coupling(md, t->x, t->lam, t->Q, t->T, t->d);
+    t->F = orc_force(md, t->x, t->T, t->occ);
+    t->p += 0.5 * dt * t->F;
+    double v1 = t->p / m;
+
+    if (orc_propagate(N, Ne, lam0, d0, v0, t->lam, t->d, v1, dt, t->C) != 0)
+        t->status |= ORC_ST_JACOBI_NONCONV;
+
+    double *g = malloc(sizeof(double) * Ne * N);
+    cplx detS;
+    if (orc_hop_probs(N, Ne, t->occ, t->C, t->d, v1, dt, brute, g, NULL, &detS) != 0)
+        t->status |= ORC_ST_SINGULAR;
+    double zeta = orc_hop_uniform(seed, traj, n);
+    if (g_out) memcpy(g_out, g, sizeof(double) * Ne * N);
+    if (zeta_out) *zeta_out = zeta;
+
+    char *isocc = calloc(N, 1);
+    for (int a = 0; a < Ne; a++) isocc[t->occ[a]] = 1;
+    double cum = 0.0;
+    int ha = -1, hm = -1;
+    for (int a = 0; a < Ne && ha < 0; a++)
+        for (int mm = 0; mm < N; mm++) {
+            if (isocc[mm]) continue;
+            cum += g[a * N + mm];
+            if (cum > zeta) { ha = a; hm = mm; break; }
+        }
+    int hopped = 0;
+    if (ha >= 0) {
+        double dE = t->lam[hm] - t->lam[t->occ[ha]];
+        double p2 = t->p * t->p - 2.0 * m * dE;
+        if (p2 >= 0.0) {
+            t->p = (t->p >= 0 ? 1.0 : -1.0) * sqrt(p2);
+            t->occ[ha] = hm;
+            for (int i = 0; i < Ne; i++)
+                for (int j = i + 1; j < Ne; j++)
+                    if (t->occ[j] < t->occ[i]) { int tt = t->occ[i]; t->occ[i] = t->occ[j]; t->occ[j] = tt; }
+            t->F = orc_force(md, t->x, t->T, t->occ);
+            t->hops++;
+            hopped = 1;
+        } else {
+            t->frustrated++;
+            hopped = -1;
+        }
+    }
+    if (hop_out) *hop_out = hopped;
+    t->v_prev = t->p / m;
+    if (!isfinite(t->x) || !isfinite(t->p)) t->status |= ORC_ST_NAN;
+    free(isocc); free(g); free(lam0); free(d0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exported entry points (ctypes).                                           */
+/* ------------------------------------------------------------------------ */
+
+/* Build the model struct from flat arrays. */
+static void make_model(orc_model *md, int kind, double mass, const double *par, double Vbar, int M,
+                       int Ne, const double *eps, const double *sqw)
+{
+    md->kind = kind;
+    md->mass = mass;
+    for (int i = 0; i < 16; i++) md->par[i] = par[i];
+    md->Vbar = Vbar;
+    md->M = M;
+    md->Ne = Ne;
+    md->eps = eps;
+    md->sqw = sqw;
+}
+
+void orc_model_eval_x(int kind, double mass, const double *par, double x, double *out)
+{
+    orc_model md;
+    memset(&md, 0, sizeof(md));
+    md.kind = kind;
+    md.mass = mass;
+    for (int i = 0; i < 16; i++) md.par[i] = par[i];
+    orc_model_eval(&md, x, out);
+}
+
+/* Eigen, T, d and the force at x for a given occupation (occ may be NULL). */
+int orc_eigen_x(int kind, double mass, const double *par, double Vbar, int M, int Ne,
+                const double *eps, const double *sqw, double x, const int *occ, double *lam,
+                double *Q, double *T, double *d, double *F)
+{
+    orc_model md;
+    make_model(&md, kind, mass, par, Vbar, M, Ne, eps, sqw);
+    int rc = orc_eigen(&md, x, lam, Q);
+    orc_coupling(&md, x, lam, Q, T, d);
+    if (occ && F) *F = orc_force(&md, x, T, occ);
+    return rc;
+}
+
+typedef struct {
+    const orc_model *md;
+    int64_t t0, t1, n_steps;
+    double dt;
+    uint64_t seed, step0;
+    int brute, record_every, n_rec;
+    double *x, *p, *F;
+    int *occ;
+    cplx *C;
+    uint32_t *status;
+    int64_t *hops, *frustrated;
+    double *pop_sh, *pop_wf; /* [n_rec][n_traj] */
+    int64_t n_traj;
+    double *lam_out;
+} orc_job;
+
+static void *run_range(void *arg)
+{
+    orc_job *J = (orc_job *)arg;
+    const orc_model *md = J->md;
+    int N = md->M + 1, Ne = md->Ne;
+    orc_traj t;
+    traj_alloc(&t, N, Ne);
+    for (int64_t i = J->t0; i < J->t1; i++) {
+        t.x = J->x[i];
+        t.p = J->p[i];
+        memcpy(t.occ, J->occ + i * Ne, sizeof(int) * Ne);
+        memcpy(t.C, J->C + i * N * Ne, sizeof(cplx) * N * Ne);
+        t.status = 0;
+        t.hops = 0;
+        t.frustrated = 0;
+        traj_prepare(md, &t);
+        for (int64_t s = 0; s < J->n_steps; s++) {
+            traj_step(md, &t, J->dt, J->seed, (uint32_t)i, J->step0 + (uint64_t)s, J->brute, NULL,
+                      NULL, NULL);
+            if (J->record_every > 0 && ((s + 1) % J->record_every) == 0) {
+                int64_t r = (s + 1) / J->record_every - 1;
+                if (r < J->n_rec) {
+                    double a, b;
+                    traj_populations(md, &t, &a, &b);
+                    J->pop_sh[r * J->n_traj + i] = a;
+                    J->pop_wf[r * J->n_traj + i] = b;
+                }
+            }
+        }
+        J->x[i] = t.x;
+        J->p[i] = t.p;
+        J->F[i] = t.F;
+        memcpy(J->occ + i * Ne, t.occ, sizeof(int) * Ne);
+        memcpy(J->C + i * N * Ne, t.C, sizeof(cplx) * N * Ne);
+        J->status[i] = t.status;
+        J->hops[i] = t.hops;
+        J->frustrated[i] = t.frustrated;
+        if (J->lam_out) memcpy(J->lam_out + i * N, t.lam, sizeof(double) * N);
+    }
+    traj_free(&t);
+    return NULL;
+}
+
+/* Advance n_traj independent trajectories by n_steps from the given state.
+ * x, p [n]; occ [n][Ne] ascending; C [n][N][Ne] complex (row = orbital);
+ * on return the arrays hold the final state, F the final force,
+ * status/hops/frustrated per trajectory, lam_out (optional) [n][N].
+ * step0 is the global index of the first step (the hop uniform counter). */
+int orc_run(int kind, double mass, const double *par, double Vbar, int M, int Ne,
+            const double *eps, const double *sqw, int64_t n_traj, double *x, double *p, double *F,
+            int *occ, cplx *C, double dt, int64_t n_steps, uint64_t seed, uint64_t step0,
+            int brute, int record_every, int n_rec, double *pop_sh, double *pop_wf,
+            uint32_t *status, int64_t *hops, int64_t *frustrated, double *lam_out, int n_threads)
+{
+    orc_model md;
+    make_model(&md, kind, mass, par, Vbar, M, Ne, eps, sqw);
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > n_traj) n_threads = (int)(n_traj > 0 ? n_traj : 1);
+    pthread_t *th = malloc(sizeof(pthread_t) * n_threads);
+    orc_job *jobs = malloc(sizeof(orc_job) * n_threads);
+    for (int k = 0; k < n_threads; k++) {
+        orc_job *J = &jobs[k];
+        J->md = &md;
+        J->t0 = n_traj * k / n_threads;
+        J->t1 = n_traj * (k + 1) / n_threads;
+        J->n_steps = n_steps;
+        J->dt = dt;
+        J->seed = seed;
+        J->step0 = step0;
+        J->brute = brute;
+        J->record_every = record_every;
+        J->n_rec = n_rec;
+        J->x = x; J->p = p; J->F = F; J->occ = occ; J->C = C;
+        J->status = status; J->hops = hops; J->frustrated = frustrated;
+        J->pop_sh = pop_sh; J->pop_wf = pop_wf;
+        J->n_traj = n_traj;
+        J->lam_out = lam_out;
+        if (n_threads > 1) pthread_create(&th[k], NULL, run_range, J);
+        else run_range(J);
+    }
+    if (n_threads > 1)
+        for (int k = 0; k < n_threads; k++) pthread_join(th[k], NULL);
+    free(th);
+    free(jobs);
+    return 0;
+}
+
+/* One step of one trajectory with every intermediate exposed (for tests):
+ * returns the hop probabilities g[Ne*N] of that step, its uniform and the
+ * hop outcome (1 accepted, -1 frustrated, 0 none). */
+int orc_step_one(int kind, double mass, const double *par, double Vbar, int M, int Ne,
+                 const double *eps, const double *sqw, double *x, double *p, double *F, int *occ,
+                 cplx *C, double dt, uint64_t seed, uint32_t traj, uint64_t n, int brute, double *g,
+                 double *zeta, int *hop, double *lam_out)
+{
+    orc_model md;
+    make_model(&md, kind, mass, par, Vbar, M, Ne, eps, sqw);
+    int N = M + 1;
+    orc_traj t;
+    traj_alloc(&t, N, Ne);
+    t.x = *x;
+    t.p = *p;
+    memcpy(t.occ, occ, sizeof(int) * Ne);
+    memcpy(t.C, C, sizeof(cplx) * N * Ne);
+    traj_prepare(&md, &t);
+    traj_step(&md, &t, dt, seed, traj, n, brute, g, zeta, hop);
+    *x = t.x;
+    *p = t.p;
+    *F = t.F;
+    memcpy(occ, t.occ, sizeof(int) * Ne);
+    memcpy(C, t.C, sizeof(cplx) * N * Ne);
+    if (lam_out) memcpy(lam_out, t.lam, sizeof(double) * N);
+    int st = (int)t.status;
+    traj_free(&t);
+    return st;
+}
+
+/* Hop probabilities of a given state without stepping. */
+int orc_hop_probs_x(int N, int Ne, const int *occ, const cplx *C, const double *d, double v,
+                    double dt, int brute, double *g, double *Rre, cplx *detS)
+{
+    return orc_hop_probs(N, Ne, occ, C, d, v, dt, brute, g, Rre, detS);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Occupied-orbital energy of a two-orbital adsorbate over six coordinates   */
+/* (differentiable-energy workload).  H has rows 0, 1 for the adsorbate      */
+/* orbitals and 2 + k for bath state k:                                      */
+/*   H_aa = eps_a + sum_al g_{a,al} x_al,                                     */
+/*   H_{a,2+k} = Vbar_a sqw_k exp(-|x_a - R_a|^2 / (2 sigma_a^2)),            */
+/*   x_a = (x_{3a}, x_{3a+1}, x_{3a+2}).                                      */
+/* theta = (eps_0, eps_1, g_{0,0..5}, g_{1,0..5}, sigma_0, sigma_1) (16).     */
+/* E_occ = sum of the Ne lowest eigenvalues; gradients by Hellmann-Feynman   */
+/* from the dense eigenvectors: dE/dy = sum_{i<Ne} Q_i^T (dH/dy) Q_i.        */
+/* ------------------------------------------------------------------------ */
+static void eocc_build(int M, const double *eps, const double *sqw, const double *Vbar,
+                       const double *R, const double *x, const double *th, double *H,
+                       double *dHdx /* [6][N*N] or NULL */, double *dHdth /* [16][N*N] or NULL */)
+{
+    int N = M + 2;
+    memset(H, 0, sizeof(double) * N * N);
+    if (dHdx) memset(dHdx, 0, sizeof(double) * 6 * N * N);
+    if (dHdth) memset(dHdth, 0, sizeof(double) * 16 * N * N);
+    for (int a = 0; a < 2; a++) {
+        double h = th[a];
+        for (int al = 0; al < 6; al++) h += th[2 + 6 * a + al] * x[al];
+        H[a * N + a] = h;
+        if (dHdx)
+            for (int al = 0; al < 6; al++) dHdx[al * N * N + a * N + a] = th[2 + 6 * a + al];
+        if (dHdth) {
+            dHdth[a * N * N + a * N + a] = 1.0;
+            for (int al = 0; al < 6; al++) dHdth[(2 + 6 * a + al) * N * N + a * N + a] = x[al];
+        }
+        double sg = th[14 + a];
+        double r2 = 0.0;
+        for (int c = 0; c < 3; c++) r2 += (x[3 * a + c] - R[3 * a + c]) * (x[3 * a + c] - R[3 * a + c]);
+        double f = exp(-0.5 * r2 / (sg * sg));
+        for (int k = 0; k < M; k++) {
+            double V = Vbar[a] * sqw[k] * f;
+            H[a * N + 2 + k] = H[(2 + k) * N + a] = V;
+            if (dHdx)
+                for (int c = 0; c < 3; c++) {
+                    double dv = V * (-(x[3 * a + c] - R[3 * a + c]) / (sg * sg));
+                    dHdx[(3 * a + c) * N * N + a * N + 2 + k] = dv;
+                    dHdx[(3 * a + c) * N * N + (2 + k) * N + a] = dv;
+                }
+            if (dHdth) {
+                double dv = V * r2 / (sg * sg * sg);
+                dHdth[(14 + a) * N * N + a * N + 2 + k] = dv;
+                dHdth[(14 + a) * N * N + (2 + k) * N + a] = dv;
+            }
+        }
+    }
+    for (int k = 0; k < M; k++) H[(2 + k) * N + 2 + k] = eps[k];
+}
+
+/* E[b], dEdx[b][6], dEdth[b][16] for B geometries x[b][6], parameters th[16]. */
+int orc_eocc(int M, int Ne, const double *eps, const double *sqw, const double *Vbar,
+             const double *R, int64_t B, const double *x, const double *th, double *E,
+             double *dEdx, double *dEdth)
+{
+    int N = M + 2;
+    double *H = malloc(sizeof(double) * N * N), *V = malloc(sizeof(double) * N * N);
+    double *ev = malloc(sizeof(double) * N);
+    double *dHx = dEdx ? malloc(sizeof(double) * 6 * N * N) : NULL;
+    double *dHt = dEdth ? malloc(sizeof(double) * 16 * N * N) : NULL;
+    int *idx = malloc(sizeof(int) * N);
+    int rc = 0;
+    for (int64_t b = 0; b < B; b++) {
+        eocc_build(M, eps, sqw, Vbar, R, x + 6 * b, th, H, dHx, dHt);
+        if (orc_jacobi_sym(N, H, ev, V) != 0) rc = -1;
+        for (int i = 0; i < N; i++) idx[i] = i;
+        for (int i = 0; i < N; i++)
+            for (int j = i + 1; j < N; j++)
+                if (ev[idx[j]] < ev[idx[i]]) { int t = idx[i]; idx[i] = idx[j]; idx[j] = t; }
+        double e = 0.0;
+        for (int i = 0; i < Ne; i++) e += ev[idx[i]];
+        E[b] = e;
+        for (int y = 0; y < 6 && dEdx; y++) {
+            double s = 0.0;
+            for (int i = 0; i < Ne; i++) {
+                int c = idx[i];
+                for (int r = 0; r < N; r++) {
+                    double vr = V[r * N + c];
+                    if (vr == 0.0) continue;
+                    for (int q = 0; q < N; q++) s += vr * dHx[y * N * N + r * N + q] * V[q * N + c];
+                }
+            }
+            dEdx[6 * b + y] = s;
+        }
+        for (int y = 0; y < 16 && dEdth; y++) {
+            double s = 0.0;
+            for (int i = 0; i < Ne; i++) {
+                int c = idx[i];
+                for (int r = 0; r < N; r++) {
+                    double vr = V[r * N + c];
+                    if (vr == 0.0) continue;
+                    for (int q = 0; q < N; q++) s += vr * dHt[y * N * N + r * N + q] * V[q * N + c];
+                }
+            }
+            dEdth[16 * b + y] = s;
+        }
+    }
+    free(H); free(V); free(ev); free(idx);
+    if (dHx) free(dHx);
+    if (dHt) free(dHt);
+    return rc;
+}
+
+/* Determinant through an output pointer (out[0] real, out[1] imaginary). */
+void orc_det_x(int n, const cplx *A_in, double *out)
+{
+    cplx *A = malloc(sizeof(cplx) * n * n);
+    memcpy(A, A_in, sizeof(cplx) * n * n);
+    cplx d = orc_det(n, A);
+    out[0] = creal(d);
+    out[1] = cimag(d);
+    free(A);
+}
