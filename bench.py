@@ -1,0 +1,306 @@
+"""Benchmark of the batched IESH step on GB300.
+
+Workload (default): harmonic double-well Newns-Anderson model, M=100 bath
+states (N=101 orbitals), Ne=50 electrons, 4096 trajectories with thermal
+initial conditions at kT in {0.005, 0.0075, 0.01}, dt=1 a.u., FP64 path.
+A step is one pass of the whole IESH step (eigenpairs, force, couplings,
+exponential integrator, determinant-ratio hop probabilities, hop and
+rescale) over the whole batch.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on the
+host cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import iesh_inputs as W  # noqa: E402
+
+METRIC = "IESH trajectory-steps/s (batched, 1 GB300) vs plain FP64 path; % of roofline"
+UNIT = "traj-steps/s"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 nominal FP64 rate (recipe's nominal table)
+
+
+def workload(M=100, n_traj=4096, dt=1.0):
+    md = W.double_well(M)
+    kT = np.array([0.005, 0.0075, 0.01])[np.arange(n_traj) % 3]
+    return md, kT, dt
+
+
+def initial_state(md, kT, n, seed):
+    x, p = W.thermal_harmonic(n, md["mass"], md["par"][0], kT, seed)
+    occ = W.lowest_occupations(n, md["Ne"])
+    C = W.unit_coefficients(occ, md["M"] + 1)
+    return x, p, occ, C
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [v.strip() for v in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[5 + i].lower() in ("active", "0x1", "1")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2212_00518_gb300 as P
+    from paper_2212_00518_gb300 import build as B
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    if rank == 0 or world > 1:
+        B.build()
+    if world > 1:
+        dist.barrier()
+
+    md, kT, dt = workload(args.M, args.n_traj, args.dt)
+    n = args.n_traj
+    x, p, occ, C = initial_state(md, kT, n, seed=1000 + rank)
+    stream = torch.cuda.current_stream()
+    ctx = P.Context(md, n, precision=P.PREC_FP64, stream=stream.cuda_stream)
+    ctx.set_state(x, p, occ, C)
+    seed = args.seed + rank  # Philox key per replica
+    for _ in range(args.warmup):
+        ctx.run(dt, 1, seed)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ctx.profile(True)
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ctx.run(dt, 1, seed)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st = ctx.get_state()
+    K = ctx.propagator_terms()
+    bad = int(np.count_nonzero(st["status"]))
+
+    # ---- end to end through the C-ABI with pinned host buffers
+    N, Ne = md["M"] + 1, md["Ne"]
+    hx = torch.from_numpy(st["x"]).pin_memory()
+    hp = torch.from_numpy(st["p"]).pin_memory()
+    hocc = torch.from_numpy(st["occ"]).pin_memory()
+    hC = torch.from_numpy(st["C"].view(np.float64)).pin_memory()
+    hst = torch.zeros(n, dtype=torch.int32).pin_memory()
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.set_state(hx, hp, hocc, hC)
+        ctx.run(dt, 1, seed)
+        ctx.get_state(hx, hp, hocc, hC, hst)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = n * (8 + 8 + 2 * Ne + 16 * Ne * N)
+    d2h = h2d + 4 * n
+
+    clocks = clk.summary()
+    if rank == 0:
+        value = world * n * args.steps / (ms / 1e3)
+        # dominant kernel: the Chebyshev propagator (FP64 DFMA pipe)
+        prop_ms, prop_n = prof["propagate"]
+        flops_launch = float(np.sum(K.astype(np.float64))) * 4.0 * N * N * Ne
+        achieved = flops_launch / (prop_ms / prop_n / 1e3) / 1e12 if prop_n else None
+        kernel_share = {k: round(v[0] / max(1e-9, sum(u[0] for u in prof.values())), 4)
+                        for k, v in prof.items() if v[1]}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"double-well Newns-Anderson IESH, M={args.M} bath states, "
+                                   f"Ne={md['Ne']}, {n} trajectories per GPU, kT 0.005-0.01, "
+                                   f"dt={dt} a.u., FP64 path",
+                       "trajectories_per_gpu": n, "n_orbitals": N, "n_electrons": Ne,
+                       "precision": "fp64", "skip_bound": False,
+                       "l2": "working set > L2 (coefficients + coupling matrices "
+                             f"{(n * Ne * N * 16 + n * N * N * 8) / 1e9:.2f} GB)",
+                       "status_nonzero": bad},
+            "roofline": {"bound": "alu", "kernel": "k_cheb (Chebyshev exponential integrator)",
+                         "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                         "frac": (achieved / FP64_NOMINAL_TFLOPS) if achieved else None,
+                         "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak in "
+                                        "MEASURED_PEAKS.json)",
+                         "traffic": None, "mean_cheb_terms": float(K.mean()),
+                         "kernel_time_share": kernel_share},
+            "e2e": {"value": world * n * e2e_steps / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(sum(v[1] for v in prof.values())),
+            "clocks": clocks,
+            "impl": "ours",
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args, md, kT, dt)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# -------------------------------------------------------- CPU oracle arm
+def _oracle_sample(md, kT, dt, n_traj, n_steps, seed, threads):
+    from oracle import oracle as O
+    B = O.bind(md)
+    x, p, occ, C = initial_state(md, kT[:n_traj], n_traj, seed=1000)
+    t0 = time.perf_counter()
+    O.run(B, x, p, occ.astype(np.int32), np.transpose(C, (0, 2, 1)), dt, n_steps, seed,
+          n_threads=threads)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(args, md, kT, dt):
+    cores = os.cpu_count() or 1
+    n_traj = 2 * cores
+    steps = args.cpu_steps
+    sec = _oracle_sample(md, kT, dt, n_traj, steps, args.seed, cores)
+    return {"value": n_traj * steps / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_traj} trajectories x {steps} steps of the same workload "
+                      f"({sec:.1f} s, one trajectory per thread)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    md, kT, dt = workload(args.M, args.n_traj, args.dt)
+    cores = os.cpu_count() or 1
+    n_traj = 2 * cores
+    per_step = []
+    for _ in range(args.warmup):
+        _oracle_sample(md, kT, dt, n_traj, 1, args.seed, cores)
+    for _ in range(args.steps):
+        per_step.append(_oracle_sample(md, kT, dt, n_traj, 1, args.seed, cores))
+    sec = sum(per_step)
+    value = n_traj * args.steps / sec
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"double-well Newns-Anderson IESH, M={args.M} bath states, "
+                               f"Ne={md['Ne']}, bounded sample of {n_traj} trajectories per "
+                               f"step, dt={dt} a.u., FP64 CPU oracle"},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n_traj} trajectories x 1 step per timed step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--M", type=int, default=100)
+    ap.add_argument("--n-traj", dest="n_traj", type=int, default=4096)
+    ap.add_argument("--dt", type=float, default=1.0)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=3)
+    ap.add_argument("--cpu-steps", dest="cpu_steps", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

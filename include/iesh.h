@@ -1,0 +1,190 @@
+/*
+ * iesh.h -- C-ABI of the GB300 batched independent electron surface hopping
+ * (IESH) library, libiesh.so (sm_103a CUDA).
+ *
+ * The library advances a batch of independent IESH trajectories of a
+ * Newns-Anderson adsorbate-metal model (Gardner, Corken, Janke, Habershon,
+ * Maurer, arXiv:2212.00518, Sec. II).  One step of one trajectory is:
+ *   1. velocity-Verlet half kick and drift of the nucleus (Sec. II C);
+ *   2. eigenpairs of the arrowhead one-electron Hamiltonian H_el^1(x)
+ *      (Sec. II B, single-electron Hamiltonian);
+ *   3. Hellmann-Feynman force on the occupied surface (Sec. II B, classical
+ *      IESH Hamiltonian) and the second half kick;
+ *   4. nonadiabatic couplings d_jk = <j|d_x k> (Sec. II B) and the
+ *      exponential integrator c <- exp(-i Abar dt) c for the N x Ne
+ *      coefficient matrix (Sec. II C), Abar the average of the generators at
+ *      the two ends of the step;
+ *   5. hop probabilities g_{a->m} for every single excitation of the occupied
+ *      Slater determinant from determinant ratios (Sec. II B, g, B, A and
+ *      <k|psi> = det S), with the optional upper-bound skip of Sec. II C;
+ *   6. stochastic hop with a Philox4x32-10 uniform and energy-conserving
+ *      momentum rescaling, frustrated hops rejected (Sec. II B).
+ *
+ * Conventions
+ *   - Units are atomic units.  N = n_bath + 1 orbitals (orbital index 0..N-1
+ *     in ascending adiabatic energy), Ne electrons.
+ *   - Array arguments are plain pointers that may point to host or device
+ *     memory (the library copies with cudaMemcpyDefault).  They are owned by
+ *     the caller, never freed by the library, and must be contiguous.
+ *   - Per-trajectory arrays are trajectory-major: x[n], occ[n][Ne] (int16,
+ *     ascending), C[n][Ne][N] complex interleaved (re, im) -- double for
+ *     IESH_PREC_FP64, float for IESH_PREC_MIXED -- so the N coefficients of
+ *     one electron are contiguous.
+ *   - Every call is ordered on the stream given to iesh_create.  Calls that
+ *     read into host memory synchronise that stream before returning.
+ *   - Errors are returned as iesh_status; iesh_last_error(ctx) gives a
+ *     message.  Numerical failures of single trajectories are reported in
+ *     their status word (IESH_TRAJ_* bits) and never abort the batch.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef IESH_H
+#define IESH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct iesh_ctx iesh_ctx;
+
+typedef enum {
+    IESH_OK = 0,
+    IESH_EINVAL = 1,   /* invalid argument (null pointer, size out of range) */
+    IESH_ECUDA = 2,    /* a CUDA runtime call failed */
+    IESH_ENOMEM = 3,   /* device allocation failed */
+    IESH_ESTATE = 4,   /* call not allowed in the current state (e.g. run before init) */
+    IESH_EUNSUPPORTED = 5 /* option combination not built */
+} iesh_status;
+
+/* Per-trajectory status bits (uint32). */
+#define IESH_TRAJ_SECULAR_NONCONV 0x1u /* an eigenvalue iteration hit its cap */
+#define IESH_TRAJ_SINGULAR 0x2u        /* overlap matrix S had a zero pivot */
+#define IESH_TRAJ_NAN 0x4u             /* non-finite nucleus or force */
+#define IESH_TRAJ_DONE 0x8u            /* trajectory finished (left the surface) */
+#define IESH_TRAJ_PROP_RANGE 0x10u     /* propagator needed more terms than built */
+
+/* Model kinds (Sec. II A; Sec. III B double well; Sec. III C desorption model). */
+enum {
+    IESH_MODEL_HARMONIC = 0,    /* par = {omega, g, dG}: U0 = m w^2 x^2/2,
+                                   U1 = m w^2 (x-g)^2/2 + dG, f(x) = 1 */
+    IESH_MODEL_DESORPTION = 1,  /* par = {De, x0, a, c, D1, D2, a', Vinf, q, a~, x~}:
+                                   Morse U0, repulsive U1, tanh coupling f(x) */
+    IESH_MODEL_MORSE_IMAGE = 2  /* par = {De, x0, a, c, h_inf, z_im, a_c, z_c, sigma}:
+                                   Morse U0, h = h_inf - 1/(4 sqrt((z-z_im)^2+a_c^2)),
+                                   f = exp(-(z-z_c)^2 / (2 sigma^2)) */
+};
+/* Coupling to bath state k: V_k(x) = sqrt(gamma / 2 pi) sqrt(w_k) f(x). */
+
+enum { IESH_DISC_GL_SPLIT = 0, IESH_DISC_TRAPEZOID = 1 }; /* Appendix A */
+enum { IESH_PREC_FP64 = 0, IESH_PREC_MIXED = 1 };
+
+typedef struct {
+    int kind;          /* IESH_MODEL_* */
+    double mass;       /* nuclear mass */
+    double par[16];    /* model constants, layout per kind (above) */
+    double gamma;      /* wide-band hybridisation Gamma (Sec. II A) */
+    double band_lo;    /* band edge a */
+    double band_hi;    /* band edge b */
+    double mu;         /* split point of the Gauss-Legendre discretisation */
+    int n_bath;        /* M, bath states (N = M + 1 orbitals), 1 <= M <= 255 */
+    int n_elec;        /* Ne electrons, 1 <= Ne <= min(N - 1, 112) */
+    int disc;          /* IESH_DISC_* */
+    int n_lo;          /* Gauss-Legendre nodes below mu (-1: M/2) */
+    int n_leads;       /* 0 or 1: one band; 2: two leads (bias, Sec. II B end) */
+    double lead_mu[2]; /* split point of each lead */
+    int lead_n[2];     /* states per lead (sum = n_bath) */
+    int lead_nlo[2];   /* nodes below the lead's split point */
+    double lead_frac[2]; /* share of gamma per lead */
+} iesh_model;
+
+typedef struct {
+    int precision;     /* IESH_PREC_FP64 or IESH_PREC_MIXED */
+    int skip_bound;    /* 1: skip the ratio solve when the hop-probability upper
+                          bound of Sec. II C is below the uniform (decisions unchanged) */
+    int record_every;  /* record impurity populations every k steps (0: off) */
+    int max_records;   /* capacity of the record buffer per trajectory */
+    double z_done;     /* a trajectory is finished when x > z_done (0: never) */
+} iesh_options;
+
+/* Create a context for up to max_traj trajectories of `model`.  Discretises
+ * the bath (Appendix A), allocates all device state, and binds the CUDA
+ * stream `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
+ * On success *out holds the context; on failure *out is NULL. */
+iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_options *opt,
+                        int64_t max_traj, void *cuda_stream);
+
+/* Free the context and its device memory.  NULL is accepted. */
+iesh_status iesh_destroy(iesh_ctx *ctx);
+
+/* Copy the discretised bath: eps[M] ascending bath energies and z0[M] =
+ * sqrt(gamma / 2 pi) sqrt(w_k) (Appendix A). */
+iesh_status iesh_bath(iesh_ctx *ctx, double *eps, double *z0);
+
+/* Initialise n_traj trajectories (Sec. III B / III C initial conditions).
+ * x0, p0 [n_traj]: given positions and momenta, or NULL to draw a thermal
+ *   sample at kT_nuc (harmonic wells: Boltzmann; Morse wells: Wigner
+ *   distribution of the harmonic approximation) from Philox stream 1.
+ * occ0 [n_traj][Ne] ascending orbital indices, or NULL to draw an exact
+ *   canonical sample at kT_el (kT_el = 0: the Ne lowest orbitals).
+ * Coefficients start as unit vectors: electron j in orbital occ[j]. */
+iesh_status iesh_init_state(iesh_ctx *ctx, int64_t n_traj, const double *x0, const double *p0,
+                            const int16_t *occ0, double kT_nuc, double kT_el, uint64_t seed);
+
+/* Replace the state of n_traj trajectories with (x, p, occ, C) (layouts
+ * above) and recompute eigenpairs and forces there.  Step counters and
+ * statistics are reset.  Used to compare with other implementations from a
+ * shared state. */
+iesh_status iesh_set_state(iesh_ctx *ctx, int64_t n_traj, const double *x, const double *p,
+                           const int16_t *occ, const void *C);
+
+/* Copy out the state.  Any pointer may be NULL to skip that array. */
+iesh_status iesh_get_state(iesh_ctx *ctx, double *x, double *p, int16_t *occ, void *C,
+                           uint32_t *status);
+
+/* Advance every live trajectory by n_steps steps of length dt (steps 1-6
+ * above).  The hop uniform of trajectory t at its step n is drawn from
+ * Philox4x32-10 with key = seed and counter = (t, 0, n_lo, n_hi).
+ * Asynchronous on the context stream. */
+iesh_status iesh_run(iesh_ctx *ctx, double dt, int64_t n_steps, uint64_t seed);
+
+/* Eigenvalues lam[n][N], impurity components q0[n][N] (> 0) of the
+ * eigenvectors and the force F[n] at the current positions. */
+iesh_status iesh_get_eigen(iesh_ctx *ctx, double *lam, double *q0, double *force);
+
+/* Hop probabilities g[n][Ne][N] (slot a of the sorted occupation list,
+ * target orbital m; zero for occupied m) of the current state at velocity
+ * p/m, as used by step 5; the state is not changed. */
+iesh_status iesh_hop_probabilities(iesh_ctx *ctx, double dt, double *g);
+
+/* Per-trajectory counters: steps taken, accepted and frustrated hops. */
+iesh_status iesh_get_counters(iesh_ctx *ctx, int64_t *nstep, int32_t *hops, int32_t *frustrated);
+
+/* Recorded impurity populations [n_records][n_traj]: the occupied-surface
+ * value sum_{i in s} q0_i^2 and the wavefunction value
+ * sum_e |sum_i q0_i C_ie|^2.  *n_records receives the number recorded. */
+iesh_status iesh_get_records(iesh_ctx *ctx, double *pop_sh, double *pop_wf, int64_t *n_records);
+
+/* Chebyshev degree K[n] used by each trajectory's propagator in its last
+ * step (the number of coupling-matrix products of that step). */
+iesh_status iesh_get_propagator_terms(iesh_ctx *ctx, int32_t *K);
+
+/* Kernel timing.  With profiling on, every kernel launch of the context is
+ * bracketed by CUDA events on the context stream.  iesh_profile_read
+ * synchronises and returns, per kernel class (IESH_K_*), the summed device
+ * time in ms and the number of launches since profiling was switched on. */
+enum { IESH_K_EIGEN = 0, IESH_K_COUPLING = 1, IESH_K_PROPAGATE = 2, IESH_K_HOP = 3,
+       IESH_K_OTHER = 4, IESH_K_COUNT = 5 };
+iesh_status iesh_profile(iesh_ctx *ctx, int enable);
+iesh_status iesh_profile_read(iesh_ctx *ctx, double *ms, int64_t *launches);
+
+/* Last error message of the context (never NULL). */
+const char *iesh_last_error(const iesh_ctx *ctx);
+
+/* Name of a status code. */
+const char *iesh_status_string(iesh_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,622 @@
+// iesh_capi.cu -- C-ABI of the batched IESH library: context, bath
+// discretisation, state transfer and the step loop (declared in iesh.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/iesh.h"
+#include "iesh_common.cuh"
+#include "iesh_kernels.h"
+
+using namespace iesh;
+
+struct iesh_ctx {
+    iesh_model model;
+    iesh_options opt;
+    int64_t max_traj = 0;
+    cudaStream_t stream = nullptr;
+    int N = 0, M = 0, Ne = 0;
+    bool mixed = false;
+    std::vector<double> eps_h, z0_h;
+    ModelDev md;
+    DevState ds;
+    std::vector<void *> allocs;
+    bool have_state = false;
+    std::string err;
+    // kernel timing
+    bool prof = false;
+    struct Rec {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[IESH_K_COUNT] = {0};
+    int64_t prof_n[IESH_K_COUNT] = {0};
+};
+
+static cudaEvent_t ev_get(iesh_ctx *c)
+{
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch `fn` (returning cudaError_t) bracketed by events when profiling.
+template <class Fn>
+static cudaError_t timed(iesh_ctx *c, int cls, Fn fn)
+{
+    if (!c->prof) return fn();
+    cudaEvent_t a = ev_get(c), b = ev_get(c);
+    cudaEventRecord(a, c->stream);
+    cudaError_t e = fn();
+    cudaEventRecord(b, c->stream);
+    c->recs.push_back({cls, a, b});
+    if (c->recs.size() > 4096) {  // fold finished records to bound memory
+        cudaEventSynchronize(b);
+        for (auto &r : c->recs) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, r.a, r.b);
+            c->prof_ms[r.cls] += ms;
+            c->prof_n[r.cls] += 1;
+            c->pool.push_back(r.a);
+            c->pool.push_back(r.b);
+        }
+        c->recs.clear();
+    }
+    return e;
+}
+
+static const double kPi = 3.14159265358979323846;
+
+static iesh_status fail(iesh_ctx *c, iesh_status s, const char *fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define CU(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(ctx, IESH_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                        __FILE__, __LINE__);                                                \
+    } while (0)
+
+// ------------------------------------------------------------ bath (host)
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on the
+// Legendre polynomial P_n (three-term recurrence), started from the
+// Tricomi approximation; w = 2 / ((1 - x^2) P_n'(x)^2).
+static void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) {
+                p1 = z;
+                p0 = 1.0;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-17) break;
+        }
+        // final derivative at the converged node
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        if (n == 1) {
+            p1 = z;
+            p0 = 1.0;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+    if (n % 2 == 1) x[n / 2] = 0.0;
+}
+
+// One lead: n states on [a, b], split Gauss-Legendre at mu with n_lo nodes
+// below it (Appendix A), or the left-endpoint trapezoid rule.
+static void lead_bath(int disc, int n, double a, double b, double mu, int n_lo,
+                      std::vector<double> &eps, std::vector<double> &w)
+{
+    eps.clear();
+    w.clear();
+    if (disc == IESH_DISC_TRAPEZOID) {
+        for (int k = 0; k < n; ++k) {
+            eps.push_back(a + k * (b - a) / n);
+            w.push_back((b - a) / n);
+        }
+        return;
+    }
+    if (n_lo < 0) n_lo = n / 2;
+    const int n_hi = n - n_lo;
+    std::vector<double> x, wl;
+    if (n_lo > 0) {
+        gauss_legendre(n_lo, x, wl);
+        for (int k = 0; k < n_lo; ++k) {
+            eps.push_back(0.5 * (mu - a) * x[k] + 0.5 * (a + mu));
+            w.push_back(0.5 * (mu - a) * wl[k]);
+        }
+    }
+    if (n_hi > 0) {
+        gauss_legendre(n_hi, x, wl);
+        for (int k = 0; k < n_hi; ++k) {
+            eps.push_back(0.5 * (b - mu) * x[k] + 0.5 * (mu + b));
+            w.push_back(0.5 * (b - mu) * wl[k]);
+        }
+    }
+}
+
+static iesh_status make_bath(iesh_ctx *ctx)
+{
+    const iesh_model &m = ctx->model;
+    const double vbar = std::sqrt(m.gamma / (2.0 * kPi));
+    std::vector<std::pair<double, double>> all;
+    std::vector<double> e, w;
+    if (m.n_leads <= 1) {
+        lead_bath(m.disc, m.n_bath, m.band_lo, m.band_hi, m.mu, m.n_lo, e, w);
+        for (size_t k = 0; k < e.size(); ++k) all.push_back({e[k], vbar * std::sqrt(w[k])});
+    } else {
+        if (m.lead_n[0] + m.lead_n[1] != m.n_bath)
+            return fail(ctx, IESH_EINVAL, "lead sizes %d + %d != n_bath %d", m.lead_n[0],
+                        m.lead_n[1], m.n_bath);
+        for (int L = 0; L < 2; ++L) {
+            lead_bath(m.disc, m.lead_n[L], m.band_lo, m.band_hi, m.lead_mu[L], m.lead_nlo[L], e, w);
+            for (size_t k = 0; k < e.size(); ++k)
+                all.push_back({e[k], vbar * std::sqrt(w[k] * m.lead_frac[L])});
+        }
+        std::stable_sort(all.begin(), all.end(),
+                         [](const std::pair<double, double> &p, const std::pair<double, double> &q) {
+                             return p.first < q.first;
+                         });
+    }
+    ctx->eps_h.clear();
+    ctx->z0_h.clear();
+    for (auto &pr : all) {
+        ctx->eps_h.push_back(pr.first);
+        ctx->z0_h.push_back(pr.second);
+    }
+    for (size_t k = 1; k < ctx->eps_h.size(); ++k)
+        if (!(ctx->eps_h[k] > ctx->eps_h[k - 1]))
+            return fail(ctx, IESH_EINVAL, "bath energies must be distinct (index %zu)", k);
+    return IESH_OK;
+}
+
+// ------------------------------------------------------------------ util
+template <class T>
+static iesh_status dalloc(iesh_ctx *ctx, T **p, size_t count)
+{
+    void *q = nullptr;
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess)
+        return fail(ctx, IESH_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    cudaMemsetAsync(q, 0, bytes, ctx->stream);
+    ctx->allocs.push_back(q);
+    *p = (T *)q;
+    return IESH_OK;
+}
+
+static bool is_host_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+static iesh_status copy_in(iesh_ctx *ctx, void *dst, const void *src, size_t bytes)
+{
+    if (!bytes) return IESH_OK;
+    CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, ctx->stream));
+    return IESH_OK;
+}
+
+static iesh_status copy_out(iesh_ctx *ctx, void *dst, const void *src, size_t bytes, bool &sync)
+{
+    if (!bytes || !dst) return IESH_OK;
+    CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, ctx->stream));
+    if (is_host_ptr(dst)) sync = true;
+    return IESH_OK;
+}
+
+// ----------------------------------------------------------------- C-ABI
+extern "C" {
+
+const char *iesh_status_string(iesh_status s)
+{
+    switch (s) {
+    case IESH_OK: return "IESH_OK";
+    case IESH_EINVAL: return "IESH_EINVAL";
+    case IESH_ECUDA: return "IESH_ECUDA";
+    case IESH_ENOMEM: return "IESH_ENOMEM";
+    case IESH_ESTATE: return "IESH_ESTATE";
+    case IESH_EUNSUPPORTED: return "IESH_EUNSUPPORTED";
+    }
+    return "IESH_?";
+}
+
+const char *iesh_last_error(const iesh_ctx *ctx)
+{
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+iesh_status iesh_destroy(iesh_ctx *ctx)
+{
+    if (!ctx) return IESH_OK;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto &r : ctx->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : ctx->pool) cudaEventDestroy(e);
+    for (void *p : ctx->allocs) cudaFree(p);
+    delete ctx;
+    return IESH_OK;
+}
+
+iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_options *opt,
+                        int64_t max_traj, void *cuda_stream)
+{
+    if (!out) return IESH_EINVAL;
+    *out = nullptr;
+    if (!model || !opt || max_traj < 1) return IESH_EINVAL;
+    iesh_ctx *ctx = new iesh_ctx();
+    ctx->model = *model;
+    ctx->opt = *opt;
+    ctx->max_traj = max_traj;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    const int M = model->n_bath, Ne = model->n_elec, N = M + 1;
+    iesh_status st = IESH_OK;
+    if (model->kind < 0 || model->kind > 2) st = fail(ctx, IESH_EINVAL, "unknown model kind %d", model->kind);
+    else if (M < 1 || N > kMaxOrbitals) st = fail(ctx, IESH_EINVAL, "n_bath %d outside 1..%d", M, kMaxOrbitals - 1);
+    else if (Ne < 1 || Ne > N - 1) st = fail(ctx, IESH_EINVAL, "n_elec %d outside 1..N-1", Ne);
+    else if (Ne > kMaxHopElectrons) st = fail(ctx, IESH_EINVAL, "n_elec %d above %d", Ne, kMaxHopElectrons);
+    else if (!(model->mass > 0.0)) st = fail(ctx, IESH_EINVAL, "mass must be positive");
+    else if (!(model->gamma >= 0.0)) st = fail(ctx, IESH_EINVAL, "gamma must be >= 0");
+    else if (opt->precision != IESH_PREC_FP64)
+        st = fail(ctx, IESH_EUNSUPPORTED, "precision %d not available in this build", opt->precision);
+    else if (opt->record_every < 0 || opt->max_records < 0) st = fail(ctx, IESH_EINVAL, "negative record sizes");
+    if (st != IESH_OK) {
+        *out = ctx;  // let the caller read the message, then destroy
+        return st;
+    }
+    ctx->N = N;
+    ctx->M = M;
+    ctx->Ne = Ne;
+    ctx->mixed = opt->precision == IESH_PREC_MIXED;
+    if ((st = make_bath(ctx)) != IESH_OK) {
+        *out = ctx;
+        return st;
+    }
+    ctx->md.kind = model->kind;
+    ctx->md.mass = model->mass;
+    for (int i = 0; i < 16; ++i) ctx->md.par[i] = model->par[i];
+
+    DevState &d = ctx->ds;
+    memset(&d, 0, sizeof d);
+    d.N = N;
+    d.M = M;
+    d.Ne = Ne;
+    d.n = 0;
+    const size_t T = (size_t)max_traj;
+    d.scratch_stride = std::max<int64_t>({(int64_t)N * N, 3LL * Ne * N + Ne,
+                                          (int64_t)(N + 1) * (Ne + 1)});
+    d.scratch_stride = (d.scratch_stride + 31) & ~31LL;
+    d.record_every = opt->record_every;
+    d.max_records = opt->record_every > 0 ? opt->max_records : 0;
+    d.z_done = opt->z_done;
+    double *eps = nullptr, *z0 = nullptr;
+#define A(ptr, cnt) if ((st = dalloc(ctx, &(ptr), (cnt))) != IESH_OK) { *out = ctx; return st; }
+    A(d.x, T) A(d.p, T) A(d.F, T) A(d.dU0, T) A(d.vprev, T)
+    A(d.occ, T * Ne)
+    double *Cd = nullptr;
+    A(Cd, T * Ne * N * 2)
+    d.C = Cd;
+    A(d.lam, T * N) A(d.q0, T * N) A(d.lam_prev, T * N) A(d.q0_prev, T * N)
+    A(d.geo, T * 4) A(d.geo_prev, T * 4)
+    A(d.status, T) A(d.nstep, T) A(d.hops, T) A(d.frus, T)
+    A(d.scratch, T * (size_t)d.scratch_stride)
+    A(d.cheb, T * kChebStride)
+    A(d.rec_sh, std::max<size_t>(1, T * d.max_records))
+    A(d.rec_wf, std::max<size_t>(1, T * d.max_records))
+    A(eps, (size_t)M) A(z0, (size_t)M)
+#undef A
+    d.eps = eps;
+    d.z0 = z0;
+    cudaError_t e1 = cudaMemcpyAsync(eps, ctx->eps_h.data(), M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    cudaError_t e2 = cudaMemcpyAsync(z0, ctx->z0_h.data(), M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    cudaError_t e3 = cudaStreamSynchronize(ctx->stream);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        *out = ctx;
+        return fail(ctx, IESH_ECUDA, "bath upload failed: %s",
+                    cudaGetErrorString(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3)));
+    }
+    *out = ctx;
+    return IESH_OK;
+}
+
+iesh_status iesh_bath(iesh_ctx *ctx, double *eps, double *z0)
+{
+    if (!ctx) return IESH_EINVAL;
+    if (eps) memcpy(eps, ctx->eps_h.data(), ctx->M * sizeof(double));
+    if (z0) memcpy(z0, ctx->z0_h.data(), ctx->M * sizeof(double));
+    return IESH_OK;
+}
+
+static iesh_status reset_counters(iesh_ctx *ctx, int64_t n)
+{
+    DevState &d = ctx->ds;
+    CU(cudaMemsetAsync(d.status, 0, n * sizeof(uint32_t), ctx->stream));
+    CU(cudaMemsetAsync(d.nstep, 0, n * sizeof(int64_t), ctx->stream));
+    CU(cudaMemsetAsync(d.hops, 0, n * sizeof(int32_t), ctx->stream));
+    CU(cudaMemsetAsync(d.frus, 0, n * sizeof(int32_t), ctx->stream));
+    if (d.max_records > 0) {
+        CU(cudaMemsetAsync(d.rec_sh, 0, (size_t)n * d.max_records * sizeof(double), ctx->stream));
+        CU(cudaMemsetAsync(d.rec_wf, 0, (size_t)n * d.max_records * sizeof(double), ctx->stream));
+    }
+    return IESH_OK;
+}
+
+iesh_status iesh_init_state(iesh_ctx *ctx, int64_t n_traj, const double *x0, const double *p0,
+                            const int16_t *occ0, double kT_nuc, double kT_el, uint64_t seed)
+{
+    if (!ctx) return IESH_EINVAL;
+    if (n_traj < 0 || n_traj > ctx->max_traj)
+        return fail(ctx, IESH_EINVAL, "n_traj %lld outside 0..%lld", (long long)n_traj, (long long)ctx->max_traj);
+    if ((x0 == nullptr) != (p0 == nullptr)) return fail(ctx, IESH_EINVAL, "give both x0 and p0 or neither");
+    if (!(kT_nuc >= 0.0) || !(kT_el >= 0.0)) return fail(ctx, IESH_EINVAL, "temperatures must be >= 0");
+    DevState &d = ctx->ds;
+    d.n = n_traj;
+    iesh_status st;
+    if ((st = reset_counters(ctx, n_traj)) != IESH_OK) return st;
+    if (x0) {
+        if ((st = copy_in(ctx, d.x, x0, n_traj * sizeof(double))) != IESH_OK) return st;
+        if ((st = copy_in(ctx, d.p, p0, n_traj * sizeof(double))) != IESH_OK) return st;
+    } else {
+        double omega, xeq;
+        int wigner;
+        const double *P = ctx->model.par;
+        if (ctx->model.kind == IESH_MODEL_HARMONIC) {
+            omega = P[0];
+            xeq = 0.0;
+            wigner = 0;
+        } else {  // Morse well: harmonic frequency sqrt(2 De a^2 / m) at x0, Wigner density
+            omega = std::sqrt(2.0 * P[0] * P[2] * P[2] / ctx->model.mass);
+            xeq = P[1];
+            wigner = 1;
+        }
+        CU(launch_init_nuclear(d, ctx->model.mass, seed, kT_nuc, wigner, omega, xeq, ctx->stream));
+    }
+    // eigenpairs at x0 (occupations needed only for the force, recomputed below)
+    CU(cudaMemsetAsync(d.occ, 0, (size_t)n_traj * ctx->Ne * sizeof(int16_t), ctx->stream));
+    CU(launch_eigen(d, ctx->md, 0.0, 0, ctx->stream));
+    if (occ0) {
+        if ((st = copy_in(ctx, d.occ, occ0, (size_t)n_traj * ctx->Ne * sizeof(int16_t))) != IESH_OK) return st;
+    } else {
+        CU(launch_sample_occ(d, seed, kT_el, ctx->stream));
+    }
+    CU(launch_force(d, ctx->stream));
+    CU(launch_unit_coeffs(d, ctx->mixed, ctx->stream));
+    ctx->have_state = true;
+    return IESH_OK;
+}
+
+iesh_status iesh_set_state(iesh_ctx *ctx, int64_t n_traj, const double *x, const double *p,
+                           const int16_t *occ, const void *C)
+{
+    if (!ctx) return IESH_EINVAL;
+    if (n_traj < 0 || n_traj > ctx->max_traj)
+        return fail(ctx, IESH_EINVAL, "n_traj %lld outside 0..%lld", (long long)n_traj, (long long)ctx->max_traj);
+    if (!x || !p || !occ || !C) return fail(ctx, IESH_EINVAL, "set_state needs x, p, occ and C");
+    DevState &d = ctx->ds;
+    d.n = n_traj;
+    iesh_status st;
+    if ((st = reset_counters(ctx, n_traj)) != IESH_OK) return st;
+    const size_t csz = (size_t)n_traj * ctx->Ne * ctx->N * (ctx->mixed ? 8 : 16);
+    if ((st = copy_in(ctx, d.x, x, n_traj * sizeof(double))) != IESH_OK) return st;
+    if ((st = copy_in(ctx, d.p, p, n_traj * sizeof(double))) != IESH_OK) return st;
+    if ((st = copy_in(ctx, d.occ, occ, (size_t)n_traj * ctx->Ne * sizeof(int16_t))) != IESH_OK) return st;
+    if ((st = copy_in(ctx, d.C, C, csz)) != IESH_OK) return st;
+    CU(launch_eigen(d, ctx->md, 0.0, 0, ctx->stream));
+    ctx->have_state = true;
+    return IESH_OK;
+}
+
+iesh_status iesh_get_state(iesh_ctx *ctx, double *x, double *p, int16_t *occ, void *C,
+                           uint32_t *status)
+{
+    if (!ctx) return IESH_EINVAL;
+    const DevState &d = ctx->ds;
+    const int64_t n = d.n;
+    bool sync = false;
+    iesh_status st;
+    if ((st = copy_out(ctx, x, d.x, n * sizeof(double), sync)) != IESH_OK) return st;
+    if ((st = copy_out(ctx, p, d.p, n * sizeof(double), sync)) != IESH_OK) return st;
+    if ((st = copy_out(ctx, occ, d.occ, (size_t)n * ctx->Ne * sizeof(int16_t), sync)) != IESH_OK) return st;
+    if ((st = copy_out(ctx, C, d.C, (size_t)n * ctx->Ne * ctx->N * (ctx->mixed ? 8 : 16), sync)) != IESH_OK) return st;
+    if ((st = copy_out(ctx, status, d.status, n * sizeof(uint32_t), sync)) != IESH_OK) return st;
+    if (sync) CU(cudaStreamSynchronize(ctx->stream));
+    return IESH_OK;
+}
+
+iesh_status iesh_get_eigen(iesh_ctx *ctx, double *lam, double *q0, double *force)
+{
+    if (!ctx) return IESH_EINVAL;
+    const DevState &d = ctx->ds;
+    bool sync = false;
+    iesh_status st;
+    if ((st = copy_out(ctx, lam, d.lam, (size_t)d.n * ctx->N * sizeof(double), sync)) != IESH_OK) return st;
+    if ((st = copy_out(ctx, q0, d.q0, (size_t)d.n * ctx->N * sizeof(double), sync)) != IESH_OK) return st;
+    if ((st = copy_out(ctx, force, d.F, (size_t)d.n * sizeof(double), sync)) != IESH_OK) return st;
+    if (sync) CU(cudaStreamSynchronize(ctx->stream));
+    return IESH_OK;
+}
+
+iesh_status iesh_get_counters(iesh_ctx *ctx, int64_t *nstep, int32_t *hops, int32_t *frustrated)
+{
+    if (!ctx) return IESH_EINVAL;
+    const DevState &d = ctx->ds;
+    bool sync = false;
+    iesh_status st;
+    if ((st = copy_out(ctx, nstep, d.nstep, d.n * sizeof(int64_t), sync)) != IESH_OK) return st;
+    if ((st = copy_out(ctx, hops, d.hops, d.n * sizeof(int32_t), sync)) != IESH_OK) return st;
+    if ((st = copy_out(ctx, frustrated, d.frus, d.n * sizeof(int32_t), sync)) != IESH_OK) return st;
+    if (sync) CU(cudaStreamSynchronize(ctx->stream));
+    return IESH_OK;
+}
+
+iesh_status iesh_get_records(iesh_ctx *ctx, double *pop_sh, double *pop_wf, int64_t *n_records)
+{
+    if (!ctx) return IESH_EINVAL;
+    const DevState &d = ctx->ds;
+    int64_t n0 = 0;
+    if (d.n > 0 && d.record_every > 0) {
+        CU(cudaMemcpyAsync(&n0, d.nstep, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    const int64_t nr = d.record_every > 0 ? std::min<int64_t>(n0 / d.record_every, d.max_records) : 0;
+    if (n_records) *n_records = nr;
+    bool sync = false;
+    iesh_status st;
+    // records are stored [max_records][n] with the batch size at write time
+    if ((st = copy_out(ctx, pop_sh, d.rec_sh, (size_t)nr * d.n * sizeof(double), sync)) != IESH_OK) return st;
+    if ((st = copy_out(ctx, pop_wf, d.rec_wf, (size_t)nr * d.n * sizeof(double), sync)) != IESH_OK) return st;
+    if (sync) CU(cudaStreamSynchronize(ctx->stream));
+    return IESH_OK;
+}
+
+iesh_status iesh_run(iesh_ctx *ctx, double dt, int64_t n_steps, uint64_t seed)
+{
+    if (!ctx) return IESH_EINVAL;
+    if (!ctx->have_state) return fail(ctx, IESH_ESTATE, "run before init_state/set_state");
+    if (!(dt > 0.0) || n_steps < 0) return fail(ctx, IESH_EINVAL, "need dt > 0 and n_steps >= 0");
+    const DevState &d = ctx->ds;
+    const double tol = 1e-15;
+    for (int64_t k = 0; k < n_steps; ++k) {
+        CU(timed(ctx, IESH_K_EIGEN, [&] { return launch_eigen(d, ctx->md, dt, 1, ctx->stream); }));
+        CU(timed(ctx, IESH_K_COUPLING,
+                 [&] { return launch_coupling_fp64(d, dt, ctx->model.mass, tol, ctx->stream); }));
+        CU(timed(ctx, IESH_K_PROPAGATE, [&] { return launch_cheb_fp64(d, dt, ctx->stream); }));
+        CU(timed(ctx, IESH_K_HOP, [&] {
+            return launch_hop(d, dt, ctx->model.mass, seed, ctx->opt.skip_bound, nullptr, ctx->stream);
+        }));
+    }
+    return IESH_OK;
+}
+
+iesh_status iesh_get_propagator_terms(iesh_ctx *ctx, int32_t *K)
+{
+    if (!ctx || !K) return IESH_EINVAL;
+    const DevState &d = ctx->ds;
+    std::vector<double> tmp((size_t)d.n);
+    if (d.n > 0) {
+        CU(cudaMemcpy2DAsync(tmp.data(), sizeof(double), d.cheb + 2, kChebStride * sizeof(double),
+                             sizeof(double), (size_t)d.n, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    std::vector<int32_t> k32((size_t)d.n);
+    for (int64_t i = 0; i < d.n; ++i) k32[i] = (int32_t)tmp[i];
+    bool sync = false;
+    iesh_status st;
+    if ((st = copy_out(ctx, K, k32.data(), k32.size() * sizeof(int32_t), sync)) != IESH_OK) return st;
+    if (sync) CU(cudaStreamSynchronize(ctx->stream));
+    return IESH_OK;
+}
+
+iesh_status iesh_profile(iesh_ctx *ctx, int enable)
+{
+    if (!ctx) return IESH_EINVAL;
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (auto &r : ctx->recs) {
+        ctx->pool.push_back(r.a);
+        ctx->pool.push_back(r.b);
+    }
+    ctx->recs.clear();
+    for (int i = 0; i < IESH_K_COUNT; ++i) {
+        ctx->prof_ms[i] = 0.0;
+        ctx->prof_n[i] = 0;
+    }
+    ctx->prof = enable != 0;
+    return IESH_OK;
+}
+
+iesh_status iesh_profile_read(iesh_ctx *ctx, double *ms, int64_t *launches)
+{
+    if (!ctx) return IESH_EINVAL;
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (auto &r : ctx->recs) {
+        float m = 0.f;
+        CU(cudaEventElapsedTime(&m, r.a, r.b));
+        ctx->prof_ms[r.cls] += m;
+        ctx->prof_n[r.cls] += 1;
+        ctx->pool.push_back(r.a);
+        ctx->pool.push_back(r.b);
+    }
+    ctx->recs.clear();
+    for (int i = 0; i < IESH_K_COUNT; ++i) {
+        if (ms) ms[i] = ctx->prof_ms[i];
+        if (launches) launches[i] = ctx->prof_n[i];
+    }
+    return IESH_OK;
+}
+
+iesh_status iesh_hop_probabilities(iesh_ctx *ctx, double dt, double *g)
+{
+    if (!ctx || !g) return IESH_EINVAL;
+    if (!ctx->have_state) return fail(ctx, IESH_ESTATE, "hop_probabilities before a state exists");
+    const DevState &d = ctx->ds;
+    const size_t bytes = (size_t)d.n * ctx->Ne * ctx->N * sizeof(double);
+    double *dst = g;
+    bool host = is_host_ptr(g);
+    double *tmp = nullptr;
+    if (host) {
+        CU(cudaMallocAsync((void **)&tmp, bytes, ctx->stream));
+        dst = tmp;
+    }
+    CU(launch_hop(d, dt, ctx->model.mass, 0, 0, dst, ctx->stream));
+    if (host) {
+        CU(cudaMemcpyAsync(g, tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaFreeAsync(tmp, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    return IESH_OK;
+}
+
+}  // extern "C"

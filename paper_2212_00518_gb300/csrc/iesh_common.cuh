@@ -1,0 +1,198 @@
+// iesh_common.cuh -- device-side state layout and helpers of the batched IESH
+// library (sm_103a).  Internal to the library; the public C-ABI is iesh.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace iesh {
+
+constexpr int kMaxOrbitals = 256;   // N = M + 1 limit of the step kernels
+constexpr int kMaxHopElectrons = 112; // Ne limit of the in-shared-memory overlap inverse
+constexpr int kChebMax = 128;       // Chebyshev terms available per step
+constexpr int kChebStride = kChebMax + 8; // per-trajectory propagator record
+constexpr int kColBlock = 8;        // electrons per propagator CTA (FP64 path)
+
+enum : uint32_t {
+    ST_SECULAR = 0x1u,
+    ST_SINGULAR = 0x2u,
+    ST_NAN = 0x4u,
+    ST_DONE = 0x8u,
+    ST_PROP = 0x10u,
+};
+
+// Model constants passed by value to every kernel.
+struct ModelDev {
+    int kind;        // 0 harmonic, 1 desorption, 2 Morse + image
+    double mass;
+    double par[16];
+};
+
+// Device pointers of a context's state (structure of arrays).
+struct DevState {
+    int N, M, Ne;
+    int64_t n;                 // trajectories in the batch
+    double *x, *p, *F, *dU0, *vprev;
+    int16_t *occ;              // [n][Ne] ascending
+    void *C;                   // [n][Ne][N] double2 or float2
+    double *lam, *q0;          // [n][N] at the current position
+    double *lam_prev, *q0_prev;// [n][N] at the previous position
+    double *geo, *geo_prev;    // [n][4]: h, dh/dx, kappa = f'/f, U0
+    uint32_t *status;          // [n]
+    int64_t *nstep;            // [n] steps taken (Philox counter)
+    int32_t *hops, *frus;      // [n]
+    double *scratch;           // [n][scratch_stride] per-trajectory workspace
+    int64_t scratch_stride;    // doubles per trajectory
+    double *cheb;              // [n][kChebStride]: c, rho, K, J_0..J_K
+    double *rec_sh, *rec_wf;   // [max_records][n]
+    int record_every, max_records;
+    double z_done;
+    const double *eps, *z0;    // bath [M]: energies and sqrt(Gamma/2pi) sqrt(w_k)
+};
+
+// ---------------------------------------------------------------- models
+// U0, dU0/dx, h = U1 - U0, dh/dx, coupling factor f and df/dx at x.
+struct ModelVals {
+    double U0, dU0, h, dh, f, df;
+};
+
+__device__ __forceinline__ ModelVals model_eval(const ModelDev &md, double x)
+{
+    ModelVals o;
+    const double *P = md.par;
+    if (md.kind == 0) {
+        const double mw2 = md.mass * P[0] * P[0];
+        o.U0 = 0.5 * mw2 * x * x;
+        o.dU0 = mw2 * x;
+        // U1 - U0 = m w^2 (g^2 - 2 g x) / 2 + dG
+        o.h = 0.5 * mw2 * (P[1] * P[1] - 2.0 * P[1] * x) + P[2];
+        o.dh = -mw2 * P[1];
+        o.f = 1.0;
+        o.df = 0.0;
+    } else if (md.kind == 1) {
+        const double De = P[0], x0 = P[1], a = P[2], c = P[3], D1 = P[4], D2 = P[5], ap = P[6],
+                     Vinf = P[7], q = P[8], at = P[9], xt = P[10];
+        const double e = exp(-a * (x - x0));
+        o.U0 = De * (e - 1.0) * (e - 1.0) + c;
+        o.dU0 = -2.0 * a * De * (e - 1.0) * e;
+        const double e1 = exp(-ap * (x - x0));
+        const double U1 = D1 * e1 * e1 - D2 * e1 + Vinf;
+        const double dU1 = ap * (D2 * e1 - 2.0 * D1 * e1 * e1);
+        o.h = U1 - o.U0;
+        o.dh = dU1 - o.dU0;
+        const double th = tanh((x - xt) / at);
+        o.f = 0.5 * (1.0 - q) * (1.0 - th) + q;
+        o.df = -0.5 * (1.0 - q) * (1.0 - th * th) / at;
+    } else {
+        const double De = P[0], x0 = P[1], a = P[2], c = P[3], hinf = P[4], zim = P[5],
+                     ac = P[6], zc = P[7], sg = P[8];
+        const double e = exp(-a * (x - x0));
+        o.U0 = De * (e - 1.0) * (e - 1.0) + c;
+        o.dU0 = -2.0 * a * De * (e - 1.0) * e;
+        const double dz = x - zim;
+        const double r = sqrt(dz * dz + ac * ac);
+        o.h = hinf - 0.25 / r;
+        o.dh = 0.25 * dz / (r * r * r);
+        const double u = (x - zc) / sg;
+        o.f = exp(-0.5 * u * u);
+        o.df = -(u / sg) * o.f;
+    }
+    return o;
+}
+
+// ------------------------------------------------------ counter-based RNG
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds, each two 32x32 -> 64-bit
+// products mixed with the key; the key advances by the Weyl constants.
+struct U4 {
+    uint32_t v[4];
+};
+
+__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    U4 o;
+    o.v[0] = c0;
+    o.v[1] = c1;
+    o.v[2] = c2;
+    o.v[3] = c3;
+    return o;
+}
+
+// 53-bit uniform in [0, 1) from two words.
+__device__ __forceinline__ double u53(uint32_t hi, uint32_t lo)
+{
+    return ((double)(hi >> 5) * 67108864.0 + (double)(lo >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+// Streams of the counter layout (trajectory, stream, n_lo, n_hi).
+constexpr uint32_t kStreamHop = 0, kStreamNuc = 1, kStreamElec = 2;
+
+__device__ __forceinline__ U4 draw(uint64_t seed, uint32_t traj, uint32_t stream, uint64_t n)
+{
+    return philox4x32_10(traj, stream, (uint32_t)n, (uint32_t)(n >> 32), (uint32_t)seed,
+                         (uint32_t)(seed >> 32));
+}
+
+// ------------------------------------------------------------ reductions
+// Block-wide sum / min / max of doubles; `red` is shared scratch of >= 32
+// doubles, `ident` the identity of op.  All threads of the block must call.
+template <class Op>
+__device__ __forceinline__ double block_reduce(double v, double *red, Op op, double ident)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        double w = lane < nw ? red[lane] : ident;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w = op(w, __shfl_xor_sync(0xffffffffu, w, o));
+        if (lane == 0) red[0] = w;
+    }
+    __syncthreads();
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+struct OpSum {
+    __device__ double operator()(double a, double b) const { return a + b; }
+};
+struct OpMin {
+    __device__ double operator()(double a, double b) const { return fmin(a, b); }
+};
+struct OpMax {
+    __device__ double operator()(double a, double b) const { return fmax(a, b); }
+};
+
+__device__ __forceinline__ double block_sum(double v, double *red)
+{
+    return block_reduce(v, red, OpSum(), 0.0);
+}
+__device__ __forceinline__ double block_min(double v, double *red)
+{
+    return block_reduce(v, red, OpMin(), __longlong_as_double(0x7ff0000000000000ll));
+}
+__device__ __forceinline__ double block_max(double v, double *red)
+{
+    return block_reduce(v, red, OpMax(), __longlong_as_double(0xfff0000000000000ll));
+}
+
+}  // namespace iesh

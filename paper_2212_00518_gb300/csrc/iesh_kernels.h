@@ -1,0 +1,24 @@
+// iesh_kernels.h -- host launch wrappers of the step kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "iesh_common.cuh"
+
+namespace iesh {
+
+cudaError_t launch_eigen(const DevState &s, const ModelDev &md, double dt, int mode,
+                         cudaStream_t st);
+cudaError_t launch_force(const DevState &s, cudaStream_t st);
+cudaError_t launch_coupling_fp64(const DevState &s, double dt, double mass, double tol,
+                                 cudaStream_t st);
+cudaError_t launch_cheb_fp64(const DevState &s, double dt, cudaStream_t st);
+size_t hop_smem_bytes(int N, int Ne);
+cudaError_t launch_hop(const DevState &s, double dt, double mass, uint64_t seed, int skip_bound,
+                       double *g_out, cudaStream_t st);
+cudaError_t launch_init_nuclear(const DevState &s, double mass, uint64_t seed, double kT,
+                                int wigner, double omega, double x_eq, cudaStream_t st);
+cudaError_t launch_sample_occ(const DevState &s, uint64_t seed, double kT, cudaStream_t st);
+cudaError_t launch_unit_coeffs(const DevState &s, bool fp32, cudaStream_t st);
+
+}  // namespace iesh

@@ -1,0 +1,902 @@
+// iesh_step.cu -- FP64 kernels of one batched IESH step (sm_103a).
+//
+// One trajectory step (Gardner et al., arXiv:2212.00518, Sec. II B-C):
+//   k_eigen     velocity-Verlet kick + drift, eigenpairs of the arrowhead
+//               one-electron Hamiltonian by its secular equation, force on
+//               the occupied surface, second kick;
+//   k_build_w   step-averaged coupling generator W = dt/2 (v0 D0 + v1 D1),
+//               D_jk = <j|d_x k>, its Gershgorin spectral interval and the
+//               Chebyshev coefficients of exp(-i Abar dt);
+//   k_cheb      Chebyshev action c <- exp(-i Abar dt) c on the N x Ne
+//               coefficient matrix (the exponential integrator of Sec. II C);
+//   k_hop       overlap matrix S, its LU factors, determinant ratios for all
+//               single excitations, hop probabilities, stochastic hop and
+//               momentum rescale (Sec. II B).
+#include "iesh_common.cuh"
+#include "iesh_kernels.h"
+
+namespace iesh {
+
+constexpr double kU = 1.1102230246251565e-16;  // unit roundoff 2^-53
+
+// ============================================================= eigenpairs
+// The one-electron Hamiltonian of Sec. II B is an arrowhead matrix:
+// diag(h, eps_1..eps_M) bordered by z_k = V_k(x).  Its eigenvalues are the
+// roots of g(lam) = lam - h - sum_k z_k^2 / (lam - eps_k), one in each gap
+// of the sorted poles, and the eigenvector of root lam has impurity
+// component q0 = 1 / sqrt(g'(lam)) (chosen > 0) and bath components
+// z_k q0 / (lam - eps_k).  Each root is found in the shifted variable
+// tau = lam - eps_o relative to its nearer pole o, so lam - eps_k =
+// (eps_o - eps_k) + tau keeps full relative accuracy.
+struct Sec {
+    double g, gp, gp_rest, sabs;
+};
+
+__device__ __forceinline__ Sec sec_eval(int M, const double *__restrict__ eps,
+                                        const double *__restrict__ z2, int o, double tau,
+                                        double eomh)
+{
+    const double eo = eps[o];
+    double s1 = 0.0, s2 = 0.0, sa = 0.0;
+#pragma unroll 4
+    for (int k = 0; k < M; ++k) {
+        const double r = 1.0 / ((eo - eps[k]) + tau);
+        const double q = z2[k] * r;
+        if (k != o) {
+            s1 += q;
+            s2 = fma(q, r, s2);
+            sa += fabs(q);
+        }
+    }
+    const double qo = z2[o] / tau;
+    Sec e;
+    e.g = (eomh + tau) - s1 - qo;
+    e.gp_rest = 1.0 + s2;
+    e.gp = e.gp_rest + qo / tau;
+    e.sabs = sa + fabs(qo) + fabs(eomh) + fabs(tau);
+    return e;
+}
+
+// Root r (0..M) of the secular equation.  Fixed-weight iteration: the
+// origin pole is kept exactly and the rest is modelled by one more pole (or
+// by a linear term for the two outermost roots) matched in value and slope;
+// each model root is safeguarded by the bracket of sign changes.
+__device__ void secular_root(int r, int M, const double *__restrict__ eps,
+                             const double *__restrict__ z2, double h, double Z2, bool warm,
+                             double guess, double &lam, double &q0, uint32_t &st)
+{
+    int o, kind;
+    double lo, hi, D = 0.0, tau;
+    Sec e;
+    bool have = false;
+    if (r > 0 && r < M) {
+        const int L = r - 1;
+        D = eps[r] - eps[L];
+        const Sec em = sec_eval(M, eps, z2, L, 0.5 * D, eps[L] - h);
+        if (em.g >= 0.0) {
+            o = L; kind = 0; lo = 0.0; hi = 0.5 * D; tau = 0.5 * D; e = em; have = true;
+        } else {
+            o = r; kind = 1; lo = -0.5 * D; hi = 0.0; tau = -0.5 * D;
+        }
+    } else if (r == 0) {
+        o = 0; kind = 2;
+        const double t = h - eps[0];
+        const double lb = 0.5 * ((h + eps[0]) - sqrt(t * t + 4.0 * Z2));
+        lo = (lb - eps[0]) * (1.0 + 1e-12) - 1e-300;
+        hi = 0.0;
+        tau = 0.5 * lo;
+    } else {
+        o = M - 1; kind = 3;
+        const double t = h - eps[M - 1];
+        const double ub = 0.5 * ((h + eps[M - 1]) + sqrt(t * t + 4.0 * Z2));
+        lo = 0.0;
+        hi = (ub - eps[M - 1]) * (1.0 + 1e-12) + 1e-300;
+        tau = 0.5 * hi;
+    }
+    if (warm) {
+        const double tg = guess - eps[o];
+        if (tg > lo && tg < hi) {
+            tau = tg;
+            have = false;
+        }
+    }
+    const double eomh = eps[o] - h;
+    const double s = z2[o];
+    bool conv = false;
+    for (int it = 0; it < 80; ++it) {
+        if (!have) e = sec_eval(M, eps, z2, o, tau, eomh);
+        have = false;
+        if (fabs(e.g) <= 8.0 * kU * e.sabs) {
+            conv = true;
+            break;
+        }
+        if (e.g < 0.0) lo = tau;
+        else hi = tau;
+        double tn;
+        if (kind == 0) {
+            const double tp = tau - D;
+            const double t = e.gp_rest * tp * tp;
+            const double c = e.g + s / tau + t / tp;
+            const double B = c * D + s + t;
+            tn = 2.0 * s * D / (B + sqrt(fmax(B * B - 4.0 * c * s * D, 0.0)));
+        } else if (kind == 1) {
+            const double tp = tau + D;
+            const double t = e.gp_rest * tp * tp;
+            const double c = -(e.g + s / tau + t / tp);
+            const double B = c * D + s + t;
+            tn = -2.0 * s * D / (B + sqrt(fmax(B * B - 4.0 * c * s * D, 0.0)));
+        } else {
+            const double ee = e.gp_rest;
+            const double c = e.g - ee * tau + s / tau;
+            const double sq = sqrt(fmax(c * c + 4.0 * ee * s, 0.0));
+            if (kind == 2) tn = (c >= 0.0) ? (-c - sq) / (2.0 * ee) : -2.0 * s / (sq - c);
+            else tn = (c <= 0.0) ? (sq - c) / (2.0 * ee) : 2.0 * s / (c + sq);
+        }
+        if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+        const bool tiny = fabs(tn - tau) <= 2.0 * kU * fabs(tn);
+        tau = tn;
+        if (tiny) {
+            e = sec_eval(M, eps, z2, o, tau, eomh);
+            conv = true;
+            break;
+        }
+    }
+    if (!conv) {
+        st |= ST_SECULAR;
+        e = sec_eval(M, eps, z2, o, tau, eomh);
+    }
+    lam = eps[o] + tau;
+    q0 = 1.0 / sqrt(e.gp);
+}
+
+// mode 0: eigenpairs and force at the stored position (cold start);
+// mode 1: full first half of a step (kick, drift, eigenpairs, force, kick).
+__global__ void __launch_bounds__(256) k_eigen(DevState s, ModelDev md, double dt, int mode)
+{
+    extern __shared__ double sh[];
+    const int64_t t = blockIdx.x;
+    if (t >= s.n || (s.status[t] & ST_DONE)) return;
+    const int N = s.N, M = s.M, Ne = s.Ne;
+    double *eps_s = sh, *z2_s = eps_s + M, *lam_s = z2_s + M, *q0_s = lam_s + N,
+           *red = q0_s + N;
+    double x = s.x[t], p = s.p[t];
+    if (mode == 1) {
+        p += 0.5 * dt * s.F[t];
+        x += dt * p / md.mass;
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double l = s.lam[t * N + i];
+        if (mode == 1) {
+            s.lam_prev[t * N + i] = l;
+            s.q0_prev[t * N + i] = s.q0[t * N + i];
+        }
+        lam_s[i] = l;
+    }
+    if (mode == 1 && threadIdx.x < 4) s.geo_prev[t * 4 + threadIdx.x] = s.geo[t * 4 + threadIdx.x];
+    const ModelVals mv = model_eval(md, x);
+    double zp = 0.0;
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        eps_s[k] = s.eps[k];
+        const double z = s.z0[k] * mv.f;
+        z2_s[k] = z * z;
+        zp += z * z;
+    }
+    const double Z2 = block_sum(zp, red);  // synchronises
+    uint32_t st = 0;
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+        double l, q;
+        if (Z2 > 0.0) {
+            secular_root(r, M, eps_s, z2_s, mv.h, Z2, mode == 1, lam_s[r], l, q, st);
+        } else {
+            // no coupling: the eigenvalues are h and the bath energies
+            int pos = 0;
+            for (int k = 0; k < M; ++k) pos += (eps_s[k] < mv.h);
+            l = (r < pos) ? eps_s[r] : (r == pos ? mv.h : eps_s[r - 1]);
+            q = (r == pos) ? 1.0 : 0.0;
+        }
+        s.lam[t * N + r] = l;
+        s.q0[t * N + r] = q;
+        lam_s[r] = l;
+        q0_s[r] = q;
+    }
+    __syncthreads();
+    const double kappa = (mv.f != 0.0) ? mv.df / mv.f : 0.0;
+    double fp = 0.0;
+    for (int a = threadIdx.x; a < Ne; a += blockDim.x) {
+        const int i = s.occ[t * Ne + a];
+        const double q = q0_s[i];
+        fp += q * q * (mv.dh + 2.0 * kappa * (lam_s[i] - mv.h));
+    }
+    const double dl = block_sum(fp, red);
+    if (st) atomicOr(&s.status[t], st);
+    if (threadIdx.x == 0) {
+        const double F = -mv.dU0 - dl;
+        if (mode == 1) p += 0.5 * dt * F;
+        s.x[t] = x;
+        s.p[t] = p;
+        s.F[t] = F;
+        s.dU0[t] = mv.dU0;
+        s.geo[t * 4 + 0] = mv.h;
+        s.geo[t * 4 + 1] = mv.dh;
+        s.geo[t * 4 + 2] = kappa;
+        s.geo[t * 4 + 3] = mv.U0;
+        if (mode == 0) s.vprev[t] = p / md.mass;
+        if (!isfinite(x) || !isfinite(p) || !isfinite(F)) atomicOr(&s.status[t], ST_NAN);
+    }
+}
+
+// Force on the occupied surface from stored eigenpairs (after occupations change).
+__global__ void k_force(DevState s)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= s.n) return;
+    const int N = s.N, Ne = s.Ne;
+    const double h = s.geo[t * 4 + 0], dh = s.geo[t * 4 + 1], kap = s.geo[t * 4 + 2];
+    double F = -s.dU0[t];
+    for (int a = 0; a < Ne; ++a) {
+        const int i = s.occ[t * Ne + a];
+        const double q = s.q0[t * N + i];
+        F -= q * q * (dh + 2.0 * kap * (s.lam[t * N + i] - h));
+    }
+    s.F[t] = F;
+}
+
+// ============================================================ couplings
+// d_jk = <j|d_x k> = T_jk / (lam_k - lam_j) with the closed form of
+// T = Q^T (dH/dx) Q for the arrowhead: T_jk = q0_j q0_k [h' + kappa
+// (lam_j + lam_k - 2h)], kappa = f'/f (all couplings share f(x)).
+__device__ __forceinline__ double nac(double lj, double qj, double lk, double qk, double h,
+                                      double dh, double kap)
+{
+    return qj * qk * (dh + kap * (lj + lk - 2.0 * h)) / (lk - lj);
+}
+
+// Bessel J_0..J_K(rho) by Miller's backward recurrence normalised with
+// J_0 + 2 sum_{k>=1} J_2k = 1.
+__device__ void bessel_j(double rho, int K, double *J)
+{
+    if (rho == 0.0) {
+        J[0] = 1.0;
+        for (int k = 1; k <= K; ++k) J[k] = 0.0;
+        return;
+    }
+    int top = (K > (int)rho ? K : (int)rho) + 24 + (int)(2.0 * sqrt((double)K + rho + 1.0));
+    top += top & 1;
+    double jp1 = 0.0, j = 1e-280, norm = 0.0;
+    const double inv = 2.0 / rho;
+    for (int k = top; k >= 1; --k) {
+        const double jm1 = k * inv * j - jp1;
+        jp1 = j;
+        j = jm1;
+        const int km = k - 1;
+        if (km <= K) J[km] = j;
+        if (km >= 2 && (km & 1) == 0) norm += 2.0 * j;
+        if (fabs(j) > 1e250) {
+            j *= 1e-250;
+            jp1 *= 1e-250;
+            norm *= 1e-250;
+            for (int q = km; q <= K && q <= top; ++q)
+                if (q >= km) J[q] *= 1e-250;
+        }
+    }
+    norm += j;  // J_0
+    const double sc = 1.0 / norm;
+    for (int k = 0; k <= K; ++k) J[k] *= sc;
+}
+
+__global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double mass, double tol)
+{
+    extern __shared__ double sh[];
+    const int64_t t = blockIdx.x;
+    if (t >= s.n || (s.status[t] & ST_DONE)) return;
+    const int N = s.N;
+    double *l0 = sh, *q00 = l0 + N, *l1 = q00 + N, *q01 = l1 + N, *red = q01 + N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        l0[i] = s.lam_prev[t * N + i];
+        q00[i] = s.q0_prev[t * N + i];
+        l1[i] = s.lam[t * N + i];
+        q01[i] = s.q0[t * N + i];
+    }
+    const double h0 = s.geo_prev[t * 4], dh0 = s.geo_prev[t * 4 + 1], k0 = s.geo_prev[t * 4 + 2];
+    const double h1 = s.geo[t * 4], dh1 = s.geo[t * 4 + 1], k1 = s.geo[t * 4 + 2];
+    const double a0 = 0.5 * dt * s.vprev[t], a1 = 0.5 * dt * (s.p[t] / mass);
+    __syncthreads();
+    double *W = s.scratch + t * s.scratch_stride;
+    double lo = __longlong_as_double(0x7ff0000000000000ll), hi = -lo;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const double lk0 = l0[k], qk0 = q00[k], lk1 = l1[k], qk1 = q01[k];
+        double Rk = 0.0;
+        for (int j = 0; j < N; ++j) {
+            double w = 0.0;
+            if (j != k)
+                w = a0 * nac(l0[j], q00[j], lk0, qk0, h0, dh0, k0) +
+                    a1 * nac(l1[j], q01[j], lk1, qk1, h1, dh1, k1);
+            W[(int64_t)j * N + k] = w;
+            Rk += fabs(w);
+        }
+        const double Lk = 0.5 * dt * (lk0 + lk1);
+        lo = fmin(lo, Lk - Rk);
+        hi = fmax(hi, Lk + Rk);
+    }
+    lo = block_min(lo, red);
+    hi = block_max(hi, red);
+    if (threadIdx.x == 0) {
+        double *cb = s.cheb + t * kChebStride;
+        const double c = 0.5 * (lo + hi), rho = 0.5 * (hi - lo);
+        // smallest K whose Chebyshev tail bound 2 sum_{k>K} (rho/2)^k / k! is below tol
+        int K = 0;
+        double term = rho * 0.5;  // (rho/2)^{K+1} / (K+1)!
+        while (K < kChebMax - 2) {
+            const double ratio = (rho * 0.5) / (K + 2);
+            const double tail = (ratio < 1.0) ? 2.0 * term / (1.0 - ratio) : 1e300;
+            if (tail <= tol) break;
+            ++K;
+            term *= (rho * 0.5) / (K + 1);
+        }
+        if (K >= kChebMax - 2) atomicOr(&s.status[t], ST_PROP);
+        cb[0] = c;
+        cb[1] = rho;
+        cb[2] = (double)K;
+        bessel_j(rho, K, cb + 3);
+    }
+}
+
+// ============================================================ propagator
+// Chebyshev expansion of the exponential integrator: with the spectrum of
+// H = Abar dt inside [c - rho, c + rho] (Gershgorin),
+//   exp(-i H) v = e^{-ic} sum_k (2 - delta_k0) (-i)^k J_k(rho) T_k(X) v,
+//   X = (H - c) / rho,  T_{k+1} = 2 X T_k - T_{k-1},
+// and H v = L v - i W v with L = diag(dt (lam0 + lam1) / 2) and W the real
+// antisymmetric step-averaged coupling generator.  One CTA owns NB
+// electrons (columns) of one trajectory; thread j owns orbital row j.
+template <int NB>
+__global__ void __launch_bounds__(256) k_cheb(DevState s, double dt)
+{
+    extern __shared__ double tk[];  // [N][2 NB]
+    const int64_t t = blockIdx.x;
+    if (t >= s.n || (s.status[t] & ST_DONE)) return;
+    const int N = s.N, Ne = s.Ne;
+    const int e0 = blockIdx.y * NB;
+    const int j = threadIdx.x;
+    const bool act = j < N;
+    const double *cb = s.cheb + t * kChebStride;
+    const double c = cb[0], rho = cb[1];
+    const int K = (int)cb[2];
+    const double *J = cb + 3;
+    const double inv_rho = rho > 0.0 ? 1.0 / rho : 0.0;
+    const double *__restrict__ W = s.scratch + t * s.scratch_stride;
+    double2 *C = reinterpret_cast<double2 *>(s.C) + (int64_t)t * Ne * N;
+    const double Lc = act ? 0.5 * dt * (s.lam_prev[t * N + j] + s.lam[t * N + j]) - c : 0.0;
+
+    double tp[2 * NB], acc[2 * NB];
+#pragma unroll
+    for (int e = 0; e < NB; ++e) {
+        double2 v = make_double2(0.0, 0.0);
+        if (act && e0 + e < Ne) v = C[(int64_t)(e0 + e) * N + j];
+        tp[2 * e] = v.x;
+        tp[2 * e + 1] = v.y;
+        acc[2 * e] = J[0] * v.x;
+        acc[2 * e + 1] = J[0] * v.y;
+        if (act) {
+            tk[j * 2 * NB + 2 * e] = v.x;
+            tk[j * 2 * NB + 2 * e + 1] = v.y;
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < K; ++k) {
+        double y[2 * NB];
+#pragma unroll
+        for (int q = 0; q < 2 * NB; ++q) y[q] = 0.0;
+        if (act) {
+            for (int i = 0; i < N; ++i) {
+                const double w = -W[(int64_t)i * N + j];  // W_ji = -W_ij
+                const double *row = tk + i * 2 * NB;
+#pragma unroll
+                for (int q = 0; q < 2 * NB; ++q) y[q] = fma(w, row[q], y[q]);
+            }
+        }
+        double own[2 * NB];
+        if (act) {
+#pragma unroll
+            for (int q = 0; q < 2 * NB; ++q) own[q] = tk[j * 2 * NB + q];
+        }
+        __syncthreads();
+        if (act) {
+            const double cj = 2.0 * J[k + 1];
+            const int ph = (k + 1) & 3;  // (-i)^(k+1)
+#pragma unroll
+            for (int e = 0; e < NB; ++e) {
+                const double xr = (Lc * own[2 * e] + y[2 * e + 1]) * inv_rho;
+                const double xi = (Lc * own[2 * e + 1] - y[2 * e]) * inv_rho;
+                double nr, ni;
+                if (k == 0) {
+                    nr = xr;
+                    ni = xi;
+                } else {
+                    nr = 2.0 * xr - tp[2 * e];
+                    ni = 2.0 * xi - tp[2 * e + 1];
+                }
+                tp[2 * e] = own[2 * e];
+                tp[2 * e + 1] = own[2 * e + 1];
+                if (ph == 0) {
+                    acc[2 * e] += cj * nr;
+                    acc[2 * e + 1] += cj * ni;
+                } else if (ph == 1) {
+                    acc[2 * e] += cj * ni;
+                    acc[2 * e + 1] -= cj * nr;
+                } else if (ph == 2) {
+                    acc[2 * e] -= cj * nr;
+                    acc[2 * e + 1] -= cj * ni;
+                } else {
+                    acc[2 * e] -= cj * ni;
+                    acc[2 * e + 1] += cj * nr;
+                }
+                tk[j * 2 * NB + 2 * e] = nr;
+                tk[j * 2 * NB + 2 * e + 1] = ni;
+            }
+        }
+        __syncthreads();
+    }
+    if (act) {
+        double sc, cc;
+        sincos(c, &sc, &cc);
+#pragma unroll
+        for (int e = 0; e < NB; ++e) {
+            if (e0 + e < Ne) {
+                const double ar = acc[2 * e], ai = acc[2 * e + 1];
+                C[(int64_t)(e0 + e) * N + j] = make_double2(cc * ar + sc * ai, cc * ai - sc * ar);
+            }
+        }
+    }
+}
+
+// ================================================================= hops
+// Sec. II B: the amplitude of the occupied configuration is det S with
+// S_aj = C_{s_a, j}; the candidate that puts orbital m in slot a has
+// amplitude det S_J = det S * (C_m S^{-1})_a.  With P S = L U, the row
+// vector C_m S^{-1} is obtained by one forward substitution with U and one
+// backward substitution with L, then the row permutation.  The hop
+// probability is g_{a->m} = max(0, -2 dt v Re(R_ma) d_{m, s_a}).
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cfms(double2 acc, double2 a, double2 b)  // acc - a b
+{
+    return make_double2(acc.x - (a.x * b.x - a.y * b.y), acc.y - (a.x * b.y + a.y * b.x));
+}
+__device__ __forceinline__ double2 crcp(double2 a)
+{
+    const double d = 1.0 / (a.x * a.x + a.y * a.y);
+    return make_double2(a.x * d, -a.y * d);
+}
+
+__global__ void __launch_bounds__(256) k_hop(DevState s, double dt, double mass, uint64_t seed,
+                                             int skip_bound, double *g_out)
+{
+    extern __shared__ double sh[];
+    const int64_t t = blockIdx.x;
+    if (t >= s.n || (s.status[t] & ST_DONE)) return;
+    const int N = s.N, Ne = s.Ne;
+    double2 *A = reinterpret_cast<double2 *>(sh);            // [Ne][Ne] LU of S
+    double *lam_s = reinterpret_cast<double *>(A + Ne * Ne);  // [N]
+    double *q0_s = lam_s + N;                                 // [N]
+    double *red = q0_s + N;                                   // [64]
+    int *occ_s = reinterpret_cast<int *>(red + 64);           // [Ne]
+    int *perm = occ_s + Ne;                                   // [Ne]
+    int *isocc = perm + Ne;                                   // [N]
+    __shared__ int s_flag, s_piv, s_hop_a, s_hop_m;
+    __shared__ double s_det_abs;
+
+    const double2 *Ct = reinterpret_cast<const double2 *>(s.C) + (int64_t)t * Ne * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        lam_s[i] = s.lam[t * N + i];
+        q0_s[i] = s.q0[t * N + i];
+        isocc[i] = 0;
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < Ne; a += blockDim.x) {
+        occ_s[a] = s.occ[t * Ne + a];
+        perm[a] = a;
+        isocc[occ_s[a]] = 1;
+    }
+    if (threadIdx.x == 0) {
+        s_flag = 0;
+        s_hop_a = -1;
+        s_hop_m = -1;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < Ne * Ne; idx += blockDim.x) {
+        const int a = idx / Ne, e = idx - a * Ne;
+        A[idx] = Ct[(int64_t)e * N + occ_s[a]];
+    }
+    __syncthreads();
+
+    // ---- LU with partial pivoting, P S = L U (unit L below the diagonal)
+    double logdet = 0.0;
+    for (int kc = 0; kc < Ne; ++kc) {
+        if (threadIdx.x < 32) {
+            double best = -1.0;
+            int bi = kc;
+            for (int r = kc + threadIdx.x; r < Ne; r += 32) {
+                const double2 v = A[r * Ne + kc];
+                const double m2 = v.x * v.x + v.y * v.y;
+                if (m2 > best) {
+                    best = m2;
+                    bi = r;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (threadIdx.x == 0) {
+                s_piv = bi;
+                if (!(best > 0.0)) s_flag = 1;
+            }
+        }
+        __syncthreads();
+        if (s_flag) break;
+        const int pv = s_piv;
+        if (pv != kc) {
+            for (int c = threadIdx.x; c < Ne; c += blockDim.x) {
+                const double2 tmp = A[kc * Ne + c];
+                A[kc * Ne + c] = A[pv * Ne + c];
+                A[pv * Ne + c] = tmp;
+            }
+            if (threadIdx.x == 0) {
+                const int tp = perm[kc];
+                perm[kc] = perm[pv];
+                perm[pv] = tp;
+            }
+        }
+        __syncthreads();
+        const double2 dinv = crcp(A[kc * Ne + kc]);
+        for (int r = kc + 1 + threadIdx.x; r < Ne; r += blockDim.x)
+            A[r * Ne + kc] = cmul(A[r * Ne + kc], dinv);
+        __syncthreads();
+        const int rem = Ne - kc - 1;
+        for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
+            const int r = kc + 1 + idx / rem, c = kc + 1 + idx % rem;
+            A[r * Ne + c] = cfms(A[r * Ne + c], A[r * Ne + kc], A[kc * Ne + c]);
+        }
+        __syncthreads();
+    }
+    const bool singular = s_flag != 0;
+    if (singular && threadIdx.x == 0) atomicOr(&s.status[t], ST_SINGULAR);
+    if (!singular && threadIdx.x == 0) {
+        for (int kc = 0; kc < Ne; ++kc) {
+            const double2 u = A[kc * Ne + kc];
+            logdet += 0.5 * log(u.x * u.x + u.y * u.y);
+        }
+        s_det_abs = exp(logdet);
+    }
+    const double v = s.p[t] / mass;
+    const double geo_h = s.geo[t * 4], geo_dh = s.geo[t * 4 + 1], geo_k = s.geo[t * 4 + 2];
+    const U4 rn = draw(seed, (uint32_t)t, kStreamHop, (uint64_t)s.nstep[t]);
+    const double zeta = u53(rn.v[0], rn.v[1]);
+    __syncthreads();
+
+    bool do_ratios = !singular;
+    if (do_ratios && skip_bound && g_out == nullptr) {
+        // upper bound of the total hop probability (Sec. II C): |<J|psi>| <= 1
+        double part = 0.0;
+        for (int idx = threadIdx.x; idx < Ne * N; idx += blockDim.x) {
+            const int a = idx / N, m = idx - a * N;
+            if (!isocc[m]) {
+                const int sa = occ_s[a];
+                part += fabs(nac(lam_s[m], q0_s[m], lam_s[sa], q0_s[sa], geo_h, geo_dh, geo_k));
+            }
+        }
+        const double sd = block_sum(part, red);
+        const double bound = 2.0 * dt * fabs(v) * sd / s_det_abs;
+        if (bound * (1.0 + 1e-9) < zeta) do_ratios = false;
+    }
+
+    double *scr = s.scratch + t * s.scratch_stride;
+    double2 *Y = reinterpret_cast<double2 *>(scr);       // [Ne][N]
+    double *G = g_out ? g_out + (int64_t)t * Ne * N : scr + 2 * (int64_t)Ne * N;  // [Ne][N]
+    if (do_ratios) {
+        for (int m = threadIdx.x; m < N; m += blockDim.x) {
+            if (isocc[m]) {
+                for (int a = 0; a < Ne; ++a) G[(int64_t)a * N + m] = 0.0;
+                continue;
+            }
+            // forward: y U = c_m
+            for (int jc = 0; jc < Ne; ++jc) {
+                double2 acc = Ct[(int64_t)jc * N + m];
+                for (int i = 0; i < jc; ++i) acc = cfms(acc, Y[(int64_t)i * N + m], A[i * Ne + jc]);
+                Y[(int64_t)jc * N + m] = cmul(acc, crcp(A[jc * Ne + jc]));
+            }
+            // backward: z L = y (unit lower L), in place
+            for (int jc = Ne - 2; jc >= 0; --jc) {
+                double2 acc = Y[(int64_t)jc * N + m];
+                for (int i = jc + 1; i < Ne; ++i) acc = cfms(acc, Y[(int64_t)i * N + m], A[i * Ne + jc]);
+                Y[(int64_t)jc * N + m] = acc;
+            }
+            // R_{m, perm[i]} = z_i ; g_{a->m}
+            for (int i = 0; i < Ne; ++i) {
+                const int a = perm[i];
+                const int sa = occ_s[a];
+                const double d = nac(lam_s[m], q0_s[m], lam_s[sa], q0_s[sa], geo_h, geo_dh, geo_k);
+                const double gam = -2.0 * dt * v * Y[(int64_t)i * N + m].x * d;
+                G[(int64_t)a * N + m] = gam > 0.0 ? gam : 0.0;
+            }
+        }
+    } else if (g_out) {
+        for (int idx = threadIdx.x; idx < Ne * N; idx += blockDim.x) G[idx] = 0.0;
+    }
+    __syncthreads();
+    if (g_out) return;
+
+    // ---- stochastic selection in the order (slot a ascending, m ascending)
+    if (do_ratios) {
+        double *slot = red;  // reuse: needs Ne <= 64 entries -> use scratch beyond G when larger
+        double *slot_sum = (Ne <= 64) ? slot : scr + 3 * (int64_t)Ne * N;
+        for (int a = threadIdx.x; a < Ne; a += blockDim.x) {
+            double sa = 0.0;
+            for (int m = 0; m < N; ++m) sa += G[(int64_t)a * N + m];
+            slot_sum[a] = sa;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double cum = 0.0;
+            int a_hit = -1;
+            for (int a = 0; a < Ne; ++a) {
+                if (cum + slot_sum[a] > zeta) {
+                    a_hit = a;
+                    break;
+                }
+                cum += slot_sum[a];
+            }
+            if (a_hit >= 0) {
+                for (int m = 0; m < N; ++m) {
+                    cum += G[(int64_t)a_hit * N + m];
+                    if (cum > zeta) {
+                        s_hop_a = a_hit;
+                        s_hop_m = m;
+                        break;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- hop, rescale, force, counters (thread 0)
+    if (threadIdx.x == 0) {
+        double p = s.p[t];
+        if (s_hop_a >= 0) {
+            const int a = s_hop_a, m = s_hop_m;
+            const double dE = lam_s[m] - lam_s[occ_s[a]];
+            const double p2 = p * p - 2.0 * mass * dE;
+            if (p2 >= 0.0) {
+                p = (p >= 0.0 ? 1.0 : -1.0) * sqrt(p2);
+                // replace s_a by m and keep the list sorted
+                int b = a;
+                occ_s[b] = m;
+                while (b > 0 && occ_s[b - 1] > occ_s[b]) {
+                    const int tmp = occ_s[b - 1];
+                    occ_s[b - 1] = occ_s[b];
+                    occ_s[b] = tmp;
+                    --b;
+                }
+                while (b < Ne - 1 && occ_s[b + 1] < occ_s[b]) {
+                    const int tmp = occ_s[b + 1];
+                    occ_s[b + 1] = occ_s[b];
+                    occ_s[b] = tmp;
+                    ++b;
+                }
+                for (int q = 0; q < Ne; ++q) s.occ[t * Ne + q] = (int16_t)occ_s[q];
+                double F = -s.dU0[t];
+                for (int q = 0; q < Ne; ++q) {
+                    const int i = occ_s[q];
+                    F -= q0_s[i] * q0_s[i] * (geo_dh + 2.0 * geo_k * (lam_s[i] - geo_h));
+                }
+                s.F[t] = F;
+                s.p[t] = p;
+                s.hops[t] += 1;
+            } else {
+                s.frus[t] += 1;
+            }
+        }
+        s.vprev[t] = p / mass;
+        const int64_t ns = s.nstep[t] + 1;
+        s.nstep[t] = ns;
+        if (s.z_done > 0.0 && s.x[t] > s.z_done) atomicOr(&s.status[t], ST_DONE);
+    }
+    // ---- observables
+    if (s.record_every > 0) {
+        __syncthreads();
+        const int64_t ns = s.nstep[t];
+        if (ns % s.record_every == 0) {
+            const int64_t r = ns / s.record_every - 1;
+            if (r < s.max_records) {
+                double psh = 0.0, pwf = 0.0;
+                for (int a = threadIdx.x; a < Ne; a += blockDim.x) {
+                    const double q = q0_s[occ_s[a]];
+                    psh += q * q;
+                    double ar = 0.0, ai = 0.0;
+                    for (int i = 0; i < N; ++i) {
+                        const double2 cv = Ct[(int64_t)a * N + i];
+                        ar = fma(q0_s[i], cv.x, ar);
+                        ai = fma(q0_s[i], cv.y, ai);
+                    }
+                    pwf += ar * ar + ai * ai;
+                }
+                psh = block_sum(psh, red);
+                pwf = block_sum(pwf, red);
+                if (threadIdx.x == 0) {
+                    s.rec_sh[r * s.n + t] = psh;
+                    s.rec_wf[r * s.n + t] = pwf;
+                }
+            }
+        }
+    }
+}
+
+// ================================================================= init
+__global__ void k_init_nuclear(DevState s, double mass, uint64_t seed, double kT, int wigner,
+                               double omega, double x_eq)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= s.n) return;
+    const U4 o = draw(seed, (uint32_t)t, kStreamNuc, 0);
+    const double u1 = u53(o.v[0], o.v[1]), u2 = u53(o.v[2], o.v[3]);
+    const double r = sqrt(-2.0 * log(1.0 - u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    double kTe = kT;
+    if (wigner && kT > 0.0) {
+        const double bw = omega / kT;
+        kTe = kT * (bw / (2.0 * tanh(0.5 * bw)));
+    }
+    s.x[t] = x_eq + sqrt(kTe / (mass * omega * omega)) * (r * cs);
+    s.p[t] = sqrt(mass * kTe) * (r * sn);
+}
+
+// Exact canonical sample of the occupied orbitals at temperature kT: the
+// table logZ(k, n) of the remaining orbitals k..N-1 holding n electrons is
+// built backwards (threads over n), then orbitals are visited upwards and
+// occupied with probability exp(-lam_k/kT) Z(k+1, n-1) / Z(k, n).
+__global__ void k_sample_occ(DevState s, uint64_t seed, double kT)
+{
+    const int64_t t = blockIdx.x;
+    if (t >= s.n) return;
+    const int N = s.N, Ne = s.Ne;
+    if (kT <= 0.0) {
+        for (int a = threadIdx.x; a < Ne; a += blockDim.x) s.occ[t * Ne + a] = (int16_t)a;
+        return;
+    }
+    double *LZ = s.scratch + t * s.scratch_stride;  // [(N+1)][(Ne+1)]
+    const int W1 = Ne + 1;
+    const double ref = s.lam[t * N];
+    const double NEG = -__longlong_as_double(0x7ff0000000000000ll);
+    for (int n = threadIdx.x; n <= Ne; n += blockDim.x) LZ[(int64_t)N * W1 + n] = (n == 0) ? 0.0 : NEG;
+    __syncthreads();
+    for (int k = N - 1; k >= 0; --k) {
+        const double lw = -(s.lam[t * N + k] - ref) / kT;
+        for (int n = threadIdx.x; n <= Ne; n += blockDim.x) {
+            const double a = LZ[(int64_t)(k + 1) * W1 + n];
+            const double b = (n > 0) ? lw + LZ[(int64_t)(k + 1) * W1 + n - 1] : NEG;
+            const double mx = fmax(a, b);
+            LZ[(int64_t)k * W1 + n] = (mx == NEG) ? NEG : mx + log(exp(a - mx) + exp(b - mx));
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int n = Ne, cnt = 0;
+        for (int k = 0; k < N && n > 0; ++k) {
+            const U4 o = draw(seed, (uint32_t)t, kStreamElec, (uint64_t)k);
+            const double u = u53(o.v[0], o.v[1]);
+            const double lw = -(s.lam[t * N + k] - ref) / kT;
+            const double pk = exp(lw + LZ[(int64_t)(k + 1) * W1 + n - 1] - LZ[(int64_t)k * W1 + n]);
+            if (u < pk) {
+                s.occ[t * Ne + cnt++] = (int16_t)k;
+                --n;
+            }
+        }
+    }
+}
+
+template <class T2>
+__global__ void k_unit_coeffs(DevState s)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = s.N, Ne = s.Ne;
+    const int64_t total = s.n * Ne * N;
+    if (idx >= total) return;
+    const int64_t t = idx / ((int64_t)Ne * N);
+    const int rem = (int)(idx - t * Ne * N);
+    const int e = rem / N, i = rem - e * N;
+    T2 v;
+    v.x = (i == s.occ[t * Ne + e]) ? 1 : 0;
+    v.y = 0;
+    reinterpret_cast<T2 *>(s.C)[idx] = v;
+}
+
+// ============================================================ launches
+static inline int round32(int v) { return (v + 31) & ~31; }
+
+cudaError_t launch_eigen(const DevState &s, const ModelDev &md, double dt, int mode,
+                         cudaStream_t st)
+{
+    if (s.n == 0) return cudaSuccess;
+    const int threads = round32(s.N < 256 ? s.N : 256);
+    const size_t smem = (size_t)(2 * s.M + 2 * s.N + 32) * sizeof(double);
+    k_eigen<<<(unsigned)s.n, threads, smem, st>>>(s, md, dt, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force(const DevState &s, cudaStream_t st)
+{
+    if (s.n == 0) return cudaSuccess;
+    k_force<<<(unsigned)((s.n + 127) / 128), 128, 0, st>>>(s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coupling_fp64(const DevState &s, double dt, double mass, double tol,
+                                 cudaStream_t st)
+{
+    if (s.n == 0) return cudaSuccess;
+    const int threads = round32(s.N < 256 ? s.N : 256);
+    k_build_w<<<(unsigned)s.n, threads, (size_t)(4 * s.N + 32) * sizeof(double), st>>>(s, dt, mass, tol);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cheb_fp64(const DevState &s, double dt, cudaStream_t st)
+{
+    if (s.n == 0) return cudaSuccess;
+    const size_t smem = (size_t)s.N * 2 * kColBlock * sizeof(double);
+    dim3 grid((unsigned)s.n, (unsigned)((s.Ne + kColBlock - 1) / kColBlock));
+    k_cheb<kColBlock><<<grid, round32(s.N), smem, st>>>(s, dt);
+    return cudaGetLastError();
+}
+
+size_t hop_smem_bytes(int N, int Ne)
+{
+    return (size_t)Ne * Ne * sizeof(double2) + (size_t)(2 * N + 64) * sizeof(double) +
+           (size_t)(2 * Ne + N) * sizeof(int);
+}
+
+cudaError_t launch_hop(const DevState &s, double dt, double mass, uint64_t seed, int skip_bound,
+                       double *g_out, cudaStream_t st)
+{
+    if (s.n == 0) return cudaSuccess;
+    const size_t smem = hop_smem_bytes(s.N, s.Ne);
+    cudaFuncSetAttribute(k_hop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_hop<<<(unsigned)s.n, 256, smem, st>>>(s, dt, mass, seed, skip_bound, g_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_nuclear(const DevState &s, double mass, uint64_t seed, double kT,
+                                int wigner, double omega, double x_eq, cudaStream_t st)
+{
+    if (s.n == 0) return cudaSuccess;
+    k_init_nuclear<<<(unsigned)((s.n + 127) / 128), 128, 0, st>>>(s, mass, seed, kT, wigner, omega, x_eq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_occ(const DevState &s, uint64_t seed, double kT, cudaStream_t st)
+{
+    if (s.n == 0) return cudaSuccess;
+    k_sample_occ<<<(unsigned)s.n, 64, 0, st>>>(s, seed, kT);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unit_coeffs(const DevState &s, bool fp32, cudaStream_t st)
+{
+    if (s.n == 0) return cudaSuccess;
+    const int64_t total = s.n * s.Ne * s.N;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    if (fp32) k_unit_coeffs<float2><<<blocks, 256, 0, st>>>(s);
+    else k_unit_coeffs<double2><<<blocks, 256, 0, st>>>(s);
+    return cudaGetLastError();
+}
+
+}  // namespace iesh

@@ -1,0 +1,278 @@
+"""ctypes binding of libiesh.so (the C-ABI declared in include/iesh.h).
+
+Argument marshalling only: every step of the IESH path runs in the CUDA
+kernels of the library.  There is no fallback; if the shared library is
+missing or fails to load, ImportError/OSError propagate.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); they are
+passed to the library by pointer, which copies with cudaMemcpyDefault.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libiesh.so")
+
+IESH_OK = 0
+STATUS_NAMES = {0: "IESH_OK", 1: "IESH_EINVAL", 2: "IESH_ECUDA", 3: "IESH_ENOMEM",
+                4: "IESH_ESTATE", 5: "IESH_EUNSUPPORTED"}
+TRAJ_SECULAR_NONCONV = 0x1
+TRAJ_SINGULAR = 0x2
+TRAJ_NAN = 0x4
+TRAJ_DONE = 0x8
+TRAJ_PROP_RANGE = 0x10
+
+PREC_FP64 = 0
+PREC_MIXED = 1
+_KIND = {"harmonic": 0, "erpenbeck": 1, "morse_image": 2}
+_DISC = {"gl": 0, "trapezoid": 1}
+
+
+class IeshError(RuntimeError):
+    pass
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("mass", ctypes.c_double),
+                ("par", ctypes.c_double * 16), ("gamma", ctypes.c_double),
+                ("band_lo", ctypes.c_double), ("band_hi", ctypes.c_double),
+                ("mu", ctypes.c_double), ("n_bath", ctypes.c_int), ("n_elec", ctypes.c_int),
+                ("disc", ctypes.c_int), ("n_lo", ctypes.c_int), ("n_leads", ctypes.c_int),
+                ("lead_mu", ctypes.c_double * 2), ("lead_n", ctypes.c_int * 2),
+                ("lead_nlo", ctypes.c_int * 2), ("lead_frac", ctypes.c_double * 2)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("skip_bound", ctypes.c_int),
+                ("record_every", ctypes.c_int), ("max_records", ctypes.c_int),
+                ("z_done", ctypes.c_double)]
+
+
+EXPORTS = ["iesh_create", "iesh_destroy", "iesh_bath", "iesh_init_state", "iesh_set_state",
+           "iesh_get_state", "iesh_run", "iesh_get_eigen", "iesh_hop_probabilities",
+           "iesh_get_counters", "iesh_get_records", "iesh_get_propagator_terms", "iesh_profile",
+           "iesh_profile_read", "iesh_last_error", "iesh_status_string"]
+KERNEL_CLASSES = ["eigen", "coupling", "propagate", "hop", "other"]
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def load(path=LIB_PATH):
+    """Load libiesh.so once (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libiesh.so not built at {path}; run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    L.iesh_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_Model),
+                              ctypes.POINTER(_Options), ctypes.c_int64, _vp]
+    L.iesh_destroy.argtypes = [_vp]
+    L.iesh_bath.argtypes = [_vp, _vp, _vp]
+    L.iesh_init_state.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_uint64]
+    L.iesh_set_state.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp]
+    L.iesh_get_state.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+    L.iesh_run.argtypes = [_vp, ctypes.c_double, ctypes.c_int64, ctypes.c_uint64]
+    L.iesh_get_eigen.argtypes = [_vp, _vp, _vp, _vp]
+    L.iesh_hop_probabilities.argtypes = [_vp, ctypes.c_double, _vp]
+    L.iesh_get_counters.argtypes = [_vp, _vp, _vp, _vp]
+    L.iesh_get_records.argtypes = [_vp, _vp, _vp, _vp]
+    L.iesh_get_propagator_terms.argtypes = [_vp, _vp]
+    L.iesh_profile.argtypes = [_vp, ctypes.c_int]
+    L.iesh_profile_read.argtypes = [_vp, _vp, _vp]
+    L.iesh_last_error.argtypes = [_vp]
+    L.iesh_last_error.restype = ctypes.c_char_p
+    L.iesh_status_string.argtypes = [ctypes.c_int]
+    L.iesh_status_string.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        getattr(L, name).restype = getattr(L, name).restype if name in (
+            "iesh_last_error", "iesh_status_string") else ctypes.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "arrays must be contiguous"
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensors must be contiguous"
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def model_struct(md):
+    """iesh_model from a plain model dictionary (see iesh_inputs)."""
+    m = _Model()
+    m.kind = _KIND[md["kind"]]
+    m.mass = float(md["mass"])
+    for i, v in enumerate(md["par"]):
+        m.par[i] = float(v)
+    m.gamma = float(md["Gamma"])
+    m.band_lo, m.band_hi = (float(v) for v in md["band"])
+    m.mu = float(md.get("mu", 0.0))
+    m.n_bath = int(md["M"])
+    m.n_elec = int(md["Ne"])
+    m.disc = _DISC[md.get("disc", "gl")]
+    m.n_lo = -1 if md.get("n_lo") is None else int(md["n_lo"])
+    leads = md.get("leads")
+    if leads:
+        m.n_leads = len(leads)
+        for i, (mu_l, n_lo, n_l, frac) in enumerate(leads):
+            m.lead_mu[i] = float(mu_l)
+            m.lead_nlo[i] = int(n_lo)
+            m.lead_n[i] = int(n_l)
+            m.lead_frac[i] = float(frac)
+    return m
+
+
+def current_stream_handle():
+    """cudaStream_t of torch's current stream on the current device (0 if no torch CUDA)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return 0
+
+
+class Context:
+    """A batch of IESH trajectories on one GPU (wraps iesh_ctx)."""
+
+    def __init__(self, model, max_traj, precision=PREC_FP64, skip_bound=False, record_every=0,
+                 max_records=0, z_done=0.0, stream=None):
+        self.L = load()
+        self.model = dict(model)
+        self.N = int(model["M"]) + 1
+        self.Ne = int(model["Ne"])
+        self.precision = precision
+        self.max_traj = int(max_traj)
+        self.n = 0
+        self._m = model_struct(model)
+        self._o = _Options(precision, int(bool(skip_bound)), int(record_every), int(max_records),
+                           float(z_done))
+        self.stream = current_stream_handle() if stream is None else stream
+        h = _vp()
+        rc = self.L.iesh_create(ctypes.byref(h), ctypes.byref(self._m), ctypes.byref(self._o),
+                                self.max_traj, _vp(self.stream) if self.stream else None)
+        self._h = h
+        if rc != IESH_OK:
+            msg = self.L.iesh_last_error(h).decode() if h.value else ""
+            self.L.iesh_destroy(h)
+            self._h = None
+            raise IeshError(f"iesh_create: {STATUS_NAMES.get(rc, rc)}: {msg}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.L.iesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != IESH_OK:
+            raise IeshError(f"{what}: {STATUS_NAMES.get(rc, rc)}: "
+                            f"{self.L.iesh_last_error(self._h).decode()}")
+
+    @property
+    def cdtype(self):
+        return np.complex128 if self.precision == PREC_FP64 else np.complex64
+
+    # -------------------------------------------------------------- state
+    def bath(self):
+        eps = np.zeros(self.N - 1)
+        z0 = np.zeros(self.N - 1)
+        self._check(self.L.iesh_bath(self._h, eps.ctypes.data, z0.ctypes.data), "iesh_bath")
+        return eps, z0
+
+    def init_state(self, n, x0=None, p0=None, occ0=None, kT_nuc=0.0, kT_el=0.0, seed=0):
+        self._check(self.L.iesh_init_state(self._h, int(n), _ptr(x0), _ptr(p0), _ptr(occ0),
+                                           float(kT_nuc), float(kT_el), int(seed)),
+                    "iesh_init_state")
+        self.n = int(n)
+
+    def set_state(self, x, p, occ, C):
+        n = int(x.shape[0])
+        self._check(self.L.iesh_set_state(self._h, n, _ptr(x), _ptr(p), _ptr(occ), _ptr(C)),
+                    "iesh_set_state")
+        self.n = n
+
+    def get_state(self, x=None, p=None, occ=None, C=None, status=None):
+        """Copy the state out; by default into new host numpy arrays."""
+        n = self.n
+        x = np.zeros(n) if x is None else x
+        p = np.zeros(n) if p is None else p
+        occ = np.zeros((n, self.Ne), np.int16) if occ is None else occ
+        C = np.zeros((n, self.Ne, self.N), self.cdtype) if C is None else C
+        status = np.zeros(n, np.uint32) if status is None else status
+        self._check(self.L.iesh_get_state(self._h, _ptr(x), _ptr(p), _ptr(occ), _ptr(C),
+                                          _ptr(status)), "iesh_get_state")
+        return dict(x=x, p=p, occ=occ, C=C, status=status)
+
+    def run(self, dt, n_steps, seed=0):
+        self._check(self.L.iesh_run(self._h, float(dt), int(n_steps), int(seed)), "iesh_run")
+
+    def eigen(self):
+        lam = np.zeros((self.n, self.N))
+        q0 = np.zeros((self.n, self.N))
+        F = np.zeros(self.n)
+        self._check(self.L.iesh_get_eigen(self._h, lam.ctypes.data, q0.ctypes.data,
+                                          F.ctypes.data), "iesh_get_eigen")
+        return lam, q0, F
+
+    def hop_probabilities(self, dt):
+        g = np.zeros((self.n, self.Ne, self.N))
+        self._check(self.L.iesh_hop_probabilities(self._h, float(dt), g.ctypes.data),
+                    "iesh_hop_probabilities")
+        return g
+
+    def counters(self):
+        ns = np.zeros(self.n, np.int64)
+        hops = np.zeros(self.n, np.int32)
+        fr = np.zeros(self.n, np.int32)
+        self._check(self.L.iesh_get_counters(self._h, ns.ctypes.data, hops.ctypes.data,
+                                             fr.ctypes.data), "iesh_get_counters")
+        return ns, hops, fr
+
+    def propagator_terms(self):
+        K = np.zeros(self.n, np.int32)
+        self._check(self.L.iesh_get_propagator_terms(self._h, K.ctypes.data),
+                    "iesh_get_propagator_terms")
+        return K
+
+    def profile(self, enable=True):
+        """Switch per-kernel CUDA-event timing on (resetting it) or off."""
+        self._check(self.L.iesh_profile(self._h, int(bool(enable))), "iesh_profile")
+
+    def profile_read(self):
+        """{kernel class: (ms summed, launches)} since profiling was switched on."""
+        ms = np.zeros(len(KERNEL_CLASSES))
+        n = np.zeros(len(KERNEL_CLASSES), np.int64)
+        self._check(self.L.iesh_profile_read(self._h, ms.ctypes.data, n.ctypes.data),
+                    "iesh_profile_read")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def records(self, max_records):
+        sh = np.zeros((max_records, self.n))
+        wf = np.zeros((max_records, self.n))
+        nr = ctypes.c_int64(0)
+        self._check(self.L.iesh_get_records(self._h, sh.ctypes.data, wf.ctypes.data,
+                                            ctypes.addressof(nr)), "iesh_get_records")
+        return sh[: nr.value], wf[: nr.value]
+
+
+def vbar(model):
+    return math.sqrt(model["Gamma"] / (2 * math.pi))
