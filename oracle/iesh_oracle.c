@@ -39,6 +39,12 @@
  *      generator stored for the next step uses the post-hop velocity.
  *   R8 Gauss-Legendre split discretisation: M/2 nodes in each half, weights
  *      positive, V_k = sqrt(Gamma / 2 pi) sqrt(w_k) f(x).
+ *
+ * Impurity populations (traj_populations): the paper defers the definition
+ * of the diabatic population P_d to another work, so two readings are
+ * recorded (occupied surface, wavefunction).  They are pinned by invariants
+ * only (unit coefficients, zero coupling); against the paper's curves their
+ * parity is unpinned.
  */
 #include <complex.h>
 #include <math.h>
@@ -1074,4 +1080,23 @@ void orc_det_x(int n, const cplx *A_in, double *out)
     out[0] = creal(d);
     out[1] = cimag(d);
     free(A);
+}
+
+/* Hop selection of Sec. II B: one uniform zeta against the running sum of
+ * g[a][m] (slot a ascending, then m ascending over unoccupied orbitals).
+ * Returns a*N + m of the chosen candidate, or -1 for no hop. */
+int orc_select(int N, int Ne, const int *occ, const double *g, double zeta)
+{
+    char *isocc = calloc(N, 1);
+    for (int a = 0; a < Ne; a++) isocc[occ[a]] = 1;
+    double cum = 0.0;
+    int out = -1;
+    for (int a = 0; a < Ne && out < 0; a++)
+        for (int m = 0; m < N; m++) {
+            if (isocc[m]) continue;
+            cum += g[a * N + m];
+            if (cum > zeta) { out = a * N + m; break; }
+        }
+    free(isocc);
+    return out;
 }

@@ -75,6 +75,7 @@ def lib():
                                    ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _ip, _vp,
                                    ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
                                    ctypes.c_uint64, ctypes.c_int, _dp, _dp, _ip, _dp]
+        L.orc_select.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _dp, ctypes.c_double]
         L.orc_eocc.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_int64,
                                _dp, _dp, _dp, _dp, _dp]
         _lib = L
@@ -238,6 +239,15 @@ def hop_probs(occ, C, d, v, dt, brute=False):
     rc = lib().orc_hop_probs_x(N, Ne, occ.ctypes.data_as(_ip), C.ctypes.data, _d(_c(d)),
                                float(v), float(dt), int(brute), _d(g), _d(R), ds.ctypes.data)
     return g, R, complex(ds[0], ds[1]), rc
+
+
+def select(occ, g, zeta):
+    """(a, m) chosen by the uniform zeta from g[Ne][N], or None."""
+    g = _c(g)
+    Ne, N = g.shape
+    occ = _c(occ, np.int32)
+    r = lib().orc_select(N, Ne, occ.ctypes.data_as(_ip), _d(g), float(zeta))
+    return None if r < 0 else divmod(r, N)
 
 
 # ---------------------------------------------------------------------- random

@@ -444,3 +444,92 @@ def test_eocc_energy_and_gradients():
             e[y] = h
             fd = (_eocc_dense(eps, sqw, wl, x, th + e) - _eocc_dense(eps, sqw, wl, x, th - e)) / (2 * h)
             assert abs(dth[b, y] - fd) < 1e-8
+
+
+# ------------------------------------------------- model definitions
+def test_double_well_definition():
+    """Sec. III B: U0 has its minimum 0 at x=0, U1 its minimum dG at x=g, both
+    with curvature m w^2; h = U1 - U0 is linear in x."""
+    md = W.double_well_paper(4)
+    w, g, dG = md["par"]
+    m = md["mass"]
+    U0, dU0, h, dh, f, df = O.model_eval(md, 0.0)
+    assert U0 == 0.0 and dU0 == 0.0
+    out_g = O.model_eval(md, g)
+    assert abs((out_g[0] + out_g[2]) - dG) < 1e-15  # U1(g) = dG
+    assert abs(out_g[1] + out_g[3]) < 1e-15         # U1'(g) = 0
+    hh = 1.0  # U1 is quadratic: the second difference is exact up to rounding
+    curv1 = ((O.model_eval(md, g + hh)[0] + O.model_eval(md, g + hh)[2]) - 2 * dG
+             + (O.model_eval(md, g - hh)[0] + O.model_eval(md, g - hh)[2])) / hh ** 2
+    assert abs(curv1 - m * w * w) < 1e-9 * m * w * w
+    hs = [O.model_eval(md, x)[2] for x in (-5.0, 0.0, 5.0)]
+    assert abs((hs[2] - hs[1]) - (hs[1] - hs[0])) < 1e-15
+    assert f == 1.0 and df == 0.0
+
+
+def test_morse_image_definition():
+    """Morse well of Table II, image-charge level h -> h_inf - 1/(4 (z - z_im))
+    far from the surface, Gaussian coupling factor with f(z_c) = 1."""
+    md = W.morse_image(10)
+    De, x0, a, c, hinf, zim, ac, zc, sg = md["par"][:9]
+    U0, dU0, h, dh, f, df = O.model_eval(md, x0)
+    assert abs(U0 - c) < 1e-15 and abs(dU0) < 1e-15
+    U0far = O.model_eval(md, 1e3)[0]
+    assert abs(U0far - (De + c)) < 1e-12
+    z = 400.0
+    assert abs(O.model_eval(md, z)[2] - (hinf - 0.25 / (z - zim))) < 1e-7
+    assert O.model_eval(md, zc)[4] == 1.0
+    assert abs(O.model_eval(md, zc + sg)[4] - np.exp(-0.5)) < 1e-15
+
+
+def test_hop_selection_frequencies():
+    """Candidate J is chosen with probability g_J (Sec. II B), no hop with
+    probability 1 - sum g, for a uniform zeta."""
+    rng = np.random.default_rng(4)
+    N, Ne = 6, 2
+    occ = np.array([1, 4])
+    g = np.zeros((Ne, N))
+    for a in range(Ne):
+        for m in range(N):
+            if m not in occ:
+                g[a, m] = rng.uniform(0.0, 0.08)
+    trials = 40000
+    counts = {}
+    for _ in range(trials):
+        r = O.select(occ, g, rng.uniform())
+        counts[r] = counts.get(r, 0) + 1
+    for a in range(Ne):
+        for m in range(N):
+            if g[a, m] > 0:
+                p = g[a, m]
+                assert abs(counts.get((a, m), 0) / trials - p) < 5 * math.sqrt(p * (1 - p) / trials)
+    p0 = 1 - g.sum()
+    assert abs(counts.get(None, 0) / trials - p0) < 5 * math.sqrt(p0 * (1 - p0) / trials)
+    assert O.select(occ, g, 0.9999) is None
+
+
+def test_population_invariants():
+    """Impurity populations: with unit coefficients the wavefunction value
+    equals the occupied-surface value; both lie in [0, 1]; with zero coupling
+    they are 1 exactly when the impurity orbital is occupied."""
+    md = W.double_well_paper(12)
+    B = O.bind(md)
+    x = np.array([8.0, 9.0])
+    p = np.array([1.0, -2.0])
+    occ = np.tile(np.arange(B.Ne, dtype=np.int32), (2, 1))
+    C = np.stack([O.unit_coefficients(B.N, o) for o in occ])
+    out = O.run(B, x, p, occ, C, 1e-9, 1, seed=0, record_every=1)
+    assert np.allclose(out["pop_sh"], out["pop_wf"], atol=1e-12)
+    assert np.all((out["pop_sh"] >= 0) & (out["pop_sh"] <= 1 + 1e-12))
+    md0 = W.double_well_paper(12)
+    md0["Gamma"] = 0.0
+    B0 = O.bind(md0)
+    lam, Q, _, _, _ = O.eigen(B0, 8.0)
+    imp = int(np.argmax(np.abs(Q[0])))
+    occ0 = np.array([[i for i in range(B0.N) if i != imp][: B0.Ne]], dtype=np.int32)
+    occ1 = np.array([sorted([imp] + list(range(B0.Ne - 1 + (imp < B0.Ne - 1)))[:B0.Ne])],
+                    dtype=np.int32)
+    for o, want in ((occ0, 0.0), (occ1, 1.0)):
+        Cu = O.unit_coefficients(B0.N, o[0])[None]
+        r = O.run(B0, np.array([8.0]), np.array([0.0]), o, Cu, 1e-9, 1, seed=0, record_every=1)
+        assert abs(r["pop_sh"][0, 0] - want) < 1e-12 and abs(r["pop_wf"][0, 0] - want) < 1e-12
