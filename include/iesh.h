@@ -40,6 +40,7 @@
 #ifndef IESH_H
 #define IESH_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -177,6 +178,40 @@ enum { IESH_K_EIGEN = 0, IESH_K_COUPLING = 1, IESH_K_PROPAGATE = 2, IESH_K_HOP =
        IESH_K_OTHER = 4, IESH_K_COUNT = 5 };
 iesh_status iesh_profile(iesh_ctx *ctx, int enable);
 iesh_status iesh_profile_read(iesh_ctx *ctx, double *ms, int64_t *launches);
+
+/* ---------------------------------------------------------------------
+ * Hop probabilities without any device allocation.
+ *
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot call cudaMalloc: host frameworks that own all device memory through
+ * their own pool allocator, and latency-critical loops that cannot afford an
+ * allocation and the device synchronisation it may cause.  It computes the
+ * same g[n][Ne][N] as iesh_hop_probabilities, but from caller-owned device
+ * arrays and without a context: model (host pointer, read during the call),
+ * x[n], p[n] positions and momenta, occ[n][Ne] (int16, ascending), C
+ * [n][Ne][N] complex double coefficients, lam[n][N] and q0[n][N] the
+ * eigenvalues and eigenvector impurity components at x (as returned by
+ * iesh_get_eigen), dt the step length; output g[n][Ne][N] (device).  All
+ * array pointers must be device memory.  Work is queued on cuda_stream
+ * (a cudaStream_t, NULL = legacy default stream) and the call returns
+ * without waiting.
+ *
+ * Working memory is a fixed array of IESH_NOALLOC_SCRATCH_BYTES inside the
+ * library, resident on every device that has used this call until the
+ * process exits; one call needs 16 n Ne N + 48 n bytes (plus alignment), and
+ * a larger request returns IESH_EINVAL before any work is queued.  The first
+ * call on a device looks up that array's device address (with the device
+ * current); make this first call before any stream capture.  All calls share
+ * the one array and each call overwrites it: calls that overlap on the GPU
+ * (different streams or host threads without ordering) race and give wrong
+ * results.  Trajectories with a singular overlap matrix get g = 0.  On error
+ * a message is written to err (err_len bytes, may be NULL). */
+#define IESH_NOALLOC_SCRATCH_BYTES (32u << 20)
+iesh_status iesh_hop_probabilities_noalloc(const iesh_model *model, int64_t n, const double *x,
+                                           const double *p, const int16_t *occ, const void *C,
+                                           const double *lam, const double *q0, double dt,
+                                           double *g, void *cuda_stream, char *err,
+                                           size_t err_len);
 
 /* Last error message of the context (never NULL). */
 const char *iesh_last_error(const iesh_ctx *ctx);

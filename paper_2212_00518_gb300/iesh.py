@@ -27,6 +27,7 @@ TRAJ_PROP_RANGE = 0x10
 
 PREC_FP64 = 0
 PREC_MIXED = 1
+IESH_NOALLOC_SCRATCH_BYTES = 32 << 20
 _KIND = {"harmonic": 0, "erpenbeck": 1, "morse_image": 2}
 _DISC = {"gl": 0, "trapezoid": 1}
 
@@ -54,7 +55,8 @@ class _Options(ctypes.Structure):
 EXPORTS = ["iesh_create", "iesh_destroy", "iesh_bath", "iesh_init_state", "iesh_set_state",
            "iesh_get_state", "iesh_run", "iesh_get_eigen", "iesh_hop_probabilities",
            "iesh_get_counters", "iesh_get_records", "iesh_get_propagator_terms", "iesh_profile",
-           "iesh_profile_read", "iesh_last_error", "iesh_status_string"]
+           "iesh_profile_read", "iesh_hop_probabilities_noalloc", "iesh_last_error",
+           "iesh_status_string"]
 KERNEL_CLASSES = ["eigen", "coupling", "propagate", "hop", "other"]
 
 _lib = None
@@ -85,6 +87,9 @@ def load(path=LIB_PATH):
     L.iesh_get_propagator_terms.argtypes = [_vp, _vp]
     L.iesh_profile.argtypes = [_vp, ctypes.c_int]
     L.iesh_profile_read.argtypes = [_vp, _vp, _vp]
+    L.iesh_hop_probabilities_noalloc.argtypes = [ctypes.POINTER(_Model), ctypes.c_int64, _vp, _vp,
+                                                 _vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp,
+                                                 ctypes.c_char_p, ctypes.c_size_t]
     L.iesh_last_error.argtypes = [_vp]
     L.iesh_last_error.restype = ctypes.c_char_p
     L.iesh_status_string.argtypes = [ctypes.c_int]
@@ -272,6 +277,22 @@ class Context:
         self._check(self.L.iesh_get_records(self._h, sh.ctypes.data, wf.ctypes.data,
                                             ctypes.addressof(nr)), "iesh_get_records")
         return sh[: nr.value], wf[: nr.value]
+
+
+def hop_probabilities_noalloc(model, x, p, occ, C, lam, q0, dt, g, stream=None):
+    """Hop probabilities g[n][Ne][N] into the caller's device array `g`, with
+    no device allocation (see iesh_hop_probabilities_noalloc in iesh.h).
+    All arrays are CUDA tensors; C is complex128 [n][Ne][N]."""
+    L = load()
+    m = model_struct(model)
+    err = ctypes.create_string_buffer(512)
+    s = current_stream_handle() if stream is None else stream
+    rc = L.iesh_hop_probabilities_noalloc(ctypes.byref(m), int(x.shape[0]), _ptr(x), _ptr(p),
+                                          _ptr(occ), _ptr(C), _ptr(lam), _ptr(q0), float(dt),
+                                          _ptr(g), _vp(s) if s else None, err, len(err))
+    if rc != IESH_OK:
+        raise IeshError(f"iesh_hop_probabilities_noalloc: {STATUS_NAMES.get(rc, rc)}: "
+                        f"{err.value.decode()}")
 
 
 def vbar(model):
