@@ -32,6 +32,10 @@ METRIC = "IESH trajectory-steps/s (batched, 1 GB300) vs plain FP64 path; % of ro
 UNIT = "traj-steps/s"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 nominal FP64 rate (recipe's nominal table)
+# DRAM bytes (read + write) per trajectory of the dominant kernel, from the ncu capture in
+# profiles/iesh_fp64_step_M100.md (1024-trajectory launch, scaled per trajectory; the
+# traffic is per-trajectory W and C streams, so it grows in proportion to the batch).
+KCHEB_FP64_TRAFFIC_PER_TRAJ = (407.724544e6 + 69.759744e6) / 1024
 
 
 def workload(M=100, n_traj=4096, dt=1.0):
@@ -216,7 +220,10 @@ def run_ours(args):
                          "frac": (achieved / FP64_NOMINAL_TFLOPS) if achieved else None,
                          "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak in "
                                         "MEASURED_PEAKS.json)",
-                         "traffic": None, "mean_cheb_terms": float(K.mean()),
+                         "traffic": KCHEB_FP64_TRAFFIC_PER_TRAJ * n if args.M == 100 else None,
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                           "1024-trajectory capture scaled to the launch",
+                         "mean_cheb_terms": float(K.mean()),
                          "kernel_time_share": kernel_share},
             "e2e": {"value": world * n * e2e_steps / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -293,7 +300,7 @@ def main():
     ap.add_argument("--dt", type=float, default=1.0)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=3)
-    ap.add_argument("--cpu-steps", dest="cpu_steps", type=int, default=100)
+    ap.add_argument("--cpu-steps", dest="cpu_steps", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

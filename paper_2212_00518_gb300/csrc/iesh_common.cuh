@@ -11,7 +11,6 @@ constexpr int kMaxOrbitals = 256;   // N = M + 1 limit of the step kernels
 constexpr int kMaxHopElectrons = 112; // Ne limit of the in-shared-memory overlap inverse
 constexpr int kChebMax = 128;       // Chebyshev terms available per step
 constexpr int kChebStride = kChebMax + 8; // per-trajectory propagator record
-constexpr int kColBlock = 8;        // electrons per propagator CTA (FP64 path)
 
 enum : uint32_t {
     ST_SECULAR = 0x1u,

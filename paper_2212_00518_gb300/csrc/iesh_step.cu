@@ -347,18 +347,22 @@ __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double m
 //   exp(-i H) v = e^{-ic} sum_k (2 - delta_k0) (-i)^k J_k(rho) T_k(X) v,
 //   X = (H - c) / rho,  T_{k+1} = 2 X T_k - T_{k-1},
 // and H v = L v - i W v with L = diag(dt (lam0 + lam1) / 2) and W the real
-// antisymmetric step-averaged coupling generator.  One CTA owns NB
-// electrons (columns) of one trajectory; thread j owns orbital row j.
-template <int NB>
-__global__ void __launch_bounds__(256) k_cheb(DevState s, double dt)
+// antisymmetric step-averaged coupling generator.  One CTA owns G x EPT
+// electrons (columns) of one trajectory; thread (g, j) owns orbital row j of
+// the EPT electrons of column group g, so every warp is (nearly) full on the
+// FP64 pipe, which is the bound of this kernel.
+template <int EPT>
+__global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G)
 {
-    extern __shared__ double tk[];  // [N][2 NB]
+    extern __shared__ double tk[];  // [N][2 G EPT]
     const int64_t t = blockIdx.x;
     if (t >= s.n || (s.status[t] & ST_DONE)) return;
     const int N = s.N, Ne = s.Ne;
-    const int e0 = blockIdx.y * NB;
-    const int j = threadIdx.x;
-    const bool act = j < N;
+    const int NB = G * EPT, W2 = 2 * NB;
+    const int g = threadIdx.x / N;
+    const int j = threadIdx.x - g * N;
+    const bool act = g < G;
+    const int e0 = blockIdx.y * NB + g * EPT;  // first electron of this thread
     const double *cb = s.cheb + t * kChebStride;
     const double c = cb[0], rho = cb[1];
     const int K = (int)cb[2];
@@ -367,10 +371,11 @@ __global__ void __launch_bounds__(256) k_cheb(DevState s, double dt)
     const double *__restrict__ W = s.scratch + t * s.scratch_stride;
     double2 *C = reinterpret_cast<double2 *>(s.C) + (int64_t)t * Ne * N;
     const double Lc = act ? 0.5 * dt * (s.lam_prev[t * N + j] + s.lam[t * N + j]) - c : 0.0;
+    double *myrow = tk + j * W2 + 2 * EPT * g;
 
-    double tp[2 * NB], acc[2 * NB];
+    double tp[2 * EPT], acc[2 * EPT];
 #pragma unroll
-    for (int e = 0; e < NB; ++e) {
+    for (int e = 0; e < EPT; ++e) {
         double2 v = make_double2(0.0, 0.0);
         if (act && e0 + e < Ne) v = C[(int64_t)(e0 + e) * N + j];
         tp[2 * e] = v.x;
@@ -378,36 +383,39 @@ __global__ void __launch_bounds__(256) k_cheb(DevState s, double dt)
         acc[2 * e] = J[0] * v.x;
         acc[2 * e + 1] = J[0] * v.y;
         if (act) {
-            tk[j * 2 * NB + 2 * e] = v.x;
-            tk[j * 2 * NB + 2 * e + 1] = v.y;
+            myrow[2 * e] = v.x;
+            myrow[2 * e + 1] = v.y;
         }
     }
     __syncthreads();
     for (int k = 0; k < K; ++k) {
-        double y[2 * NB];
+        double y[2 * EPT];
 #pragma unroll
-        for (int q = 0; q < 2 * NB; ++q) y[q] = 0.0;
+        for (int q = 0; q < 2 * EPT; ++q) y[q] = 0.0;
         if (act) {
+            const double *col = tk + 2 * EPT * g;
+#pragma unroll 4
             for (int i = 0; i < N; ++i) {
-                const double w = -W[(int64_t)i * N + j];  // W_ji = -W_ij
-                const double *row = tk + i * 2 * NB;
+                const double w = W[(int64_t)i * N + j];  // W_ij = -W_ji
+                const double *row = col + i * W2;
 #pragma unroll
-                for (int q = 0; q < 2 * NB; ++q) y[q] = fma(w, row[q], y[q]);
+                for (int q = 0; q < 2 * EPT; ++q) y[q] = fma(w, row[q], y[q]);
             }
         }
-        double own[2 * NB];
+        double own[2 * EPT];
         if (act) {
 #pragma unroll
-            for (int q = 0; q < 2 * NB; ++q) own[q] = tk[j * 2 * NB + q];
+            for (int q = 0; q < 2 * EPT; ++q) own[q] = myrow[q];
         }
         __syncthreads();
         if (act) {
             const double cj = 2.0 * J[k + 1];
             const int ph = (k + 1) & 3;  // (-i)^(k+1)
 #pragma unroll
-            for (int e = 0; e < NB; ++e) {
-                const double xr = (Lc * own[2 * e] + y[2 * e + 1]) * inv_rho;
-                const double xi = (Lc * own[2 * e + 1] - y[2 * e]) * inv_rho;
+            for (int e = 0; e < EPT; ++e) {
+                // (X t)_j = ((L_j - c) t_j - i (W t)_j) / rho and (W t)_j = -y
+                const double xr = (Lc * own[2 * e] - y[2 * e + 1]) * inv_rho;
+                const double xi = (Lc * own[2 * e + 1] + y[2 * e]) * inv_rho;
                 double nr, ni;
                 if (k == 0) {
                     nr = xr;
@@ -431,8 +439,8 @@ __global__ void __launch_bounds__(256) k_cheb(DevState s, double dt)
                     acc[2 * e] -= cj * ni;
                     acc[2 * e + 1] += cj * nr;
                 }
-                tk[j * 2 * NB + 2 * e] = nr;
-                tk[j * 2 * NB + 2 * e + 1] = ni;
+                myrow[2 * e] = nr;
+                myrow[2 * e + 1] = ni;
             }
         }
         __syncthreads();
@@ -441,7 +449,7 @@ __global__ void __launch_bounds__(256) k_cheb(DevState s, double dt)
         double sc, cc;
         sincos(c, &sc, &cc);
 #pragma unroll
-        for (int e = 0; e < NB; ++e) {
+        for (int e = 0; e < EPT; ++e) {
             if (e0 + e < Ne) {
                 const double ar = acc[2 * e], ai = acc[2 * e + 1];
                 C[(int64_t)(e0 + e) * N + j] = make_double2(cc * ar + sc * ai, cc * ai - sc * ar);
@@ -479,12 +487,14 @@ __global__ void __launch_bounds__(256) k_hop(DevState s, double dt, double mass,
     if (t >= s.n || (s.status[t] & ST_DONE)) return;
     const int N = s.N, Ne = s.Ne;
     double2 *A = reinterpret_cast<double2 *>(sh);            // [Ne][Ne] LU of S
-    double *lam_s = reinterpret_cast<double *>(A + Ne * Ne);  // [N]
+    double2 *dinv = A + Ne * Ne;                              // [Ne] 1 / U_jj
+    double *lam_s = reinterpret_cast<double *>(dinv + Ne);    // [N]
     double *q0_s = lam_s + N;                                 // [N]
     double *red = q0_s + N;                                   // [64]
     int *occ_s = reinterpret_cast<int *>(red + 64);           // [Ne]
     int *perm = occ_s + Ne;                                   // [Ne]
     int *isocc = perm + Ne;                                   // [N]
+    int *unocc = isocc + N;                                   // [N - Ne] ascending
     __shared__ int s_flag, s_piv, s_hop_a, s_hop_m;
     __shared__ double s_det_abs;
 
@@ -569,6 +579,14 @@ __global__ void __launch_bounds__(256) k_hop(DevState s, double dt, double mass,
     }
     const bool singular = s_flag != 0;
     if (singular && threadIdx.x == 0) atomicOr(&s.status[t], ST_SINGULAR);
+    const int nu = N - Ne;
+    if (threadIdx.x == 0) {
+        int u = 0;
+        for (int m = 0; m < N; ++m)
+            if (!isocc[m]) unocc[u++] = m;
+    }
+    if (!singular)
+        for (int jc = threadIdx.x; jc < Ne; jc += blockDim.x) dinv[jc] = crcp(A[jc * Ne + jc]);
     if (!singular && threadIdx.x == 0) {
         for (int kc = 0; kc < Ne; ++kc) {
             const double2 u = A[kc * Ne + kc];
@@ -602,22 +620,32 @@ __global__ void __launch_bounds__(256) k_hop(DevState s, double dt, double mass,
     double2 *Y = reinterpret_cast<double2 *>(scr);       // [Ne][N]
     double *G = g_out ? g_out + (int64_t)t * Ne * N : scr + 2 * (int64_t)Ne * N;  // [Ne][N]
     if (do_ratios) {
-        for (int m = threadIdx.x; m < N; m += blockDim.x) {
-            if (isocc[m]) {
-                for (int a = 0; a < Ne; ++a) G[(int64_t)a * N + m] = 0.0;
-                continue;
-            }
-            // forward: y U = c_m
+        // one thread per unoccupied orbital m: y U = c_m, then z L = y
+        for (int u = threadIdx.x; u < nu; u += blockDim.x) {
+            const int m = unocc[u];
             for (int jc = 0; jc < Ne; ++jc) {
-                double2 acc = Ct[(int64_t)jc * N + m];
-                for (int i = 0; i < jc; ++i) acc = cfms(acc, Y[(int64_t)i * N + m], A[i * Ne + jc]);
-                Y[(int64_t)jc * N + m] = cmul(acc, crcp(A[jc * Ne + jc]));
+                double2 a0 = Ct[(int64_t)jc * N + m], a1 = make_double2(0.0, 0.0);
+                int i = 0;
+                for (; i + 1 < jc; i += 2) {
+                    a0 = cfms(a0, Y[(int64_t)i * N + m], A[i * Ne + jc]);
+                    a1 = cfms(a1, Y[(int64_t)(i + 1) * N + m], A[(i + 1) * Ne + jc]);
+                }
+                if (i < jc) a0 = cfms(a0, Y[(int64_t)i * N + m], A[i * Ne + jc]);
+                a0.x += a1.x;
+                a0.y += a1.y;
+                Y[(int64_t)jc * N + m] = cmul(a0, dinv[jc]);
             }
-            // backward: z L = y (unit lower L), in place
             for (int jc = Ne - 2; jc >= 0; --jc) {
-                double2 acc = Y[(int64_t)jc * N + m];
-                for (int i = jc + 1; i < Ne; ++i) acc = cfms(acc, Y[(int64_t)i * N + m], A[i * Ne + jc]);
-                Y[(int64_t)jc * N + m] = acc;
+                double2 a0 = Y[(int64_t)jc * N + m], a1 = make_double2(0.0, 0.0);
+                int i = jc + 1;
+                for (; i + 1 < Ne; i += 2) {
+                    a0 = cfms(a0, Y[(int64_t)i * N + m], A[i * Ne + jc]);
+                    a1 = cfms(a1, Y[(int64_t)(i + 1) * N + m], A[(i + 1) * Ne + jc]);
+                }
+                if (i < Ne) a0 = cfms(a0, Y[(int64_t)i * N + m], A[i * Ne + jc]);
+                a0.x += a1.x;
+                a0.y += a1.y;
+                Y[(int64_t)jc * N + m] = a0;
             }
             // R_{m, perm[i]} = z_i ; g_{a->m}
             for (int i = 0; i < Ne; ++i) {
@@ -628,6 +656,9 @@ __global__ void __launch_bounds__(256) k_hop(DevState s, double dt, double mass,
                 G[(int64_t)a * N + m] = gam > 0.0 ? gam : 0.0;
             }
         }
+        if (g_out)
+            for (int idx = threadIdx.x; idx < Ne * Ne; idx += blockDim.x)
+                G[(int64_t)(idx / Ne) * N + occ_s[idx % Ne]] = 0.0;
     } else if (g_out) {
         for (int idx = threadIdx.x; idx < Ne * N; idx += blockDim.x) G[idx] = 0.0;
     }
@@ -640,7 +671,7 @@ __global__ void __launch_bounds__(256) k_hop(DevState s, double dt, double mass,
         double *slot_sum = (Ne <= 64) ? slot : scr + 3 * (int64_t)Ne * N;
         for (int a = threadIdx.x; a < Ne; a += blockDim.x) {
             double sa = 0.0;
-            for (int m = 0; m < N; ++m) sa += G[(int64_t)a * N + m];
+            for (int u = 0; u < nu; ++u) sa += G[(int64_t)a * N + unocc[u]];
             slot_sum[a] = sa;
         }
         __syncthreads();
@@ -655,11 +686,11 @@ __global__ void __launch_bounds__(256) k_hop(DevState s, double dt, double mass,
                 cum += slot_sum[a];
             }
             if (a_hit >= 0) {
-                for (int m = 0; m < N; ++m) {
-                    cum += G[(int64_t)a_hit * N + m];
+                for (int u = 0; u < nu; ++u) {
+                    cum += G[(int64_t)a_hit * N + unocc[u]];
                     if (cum > zeta) {
                         s_hop_a = a_hit;
-                        s_hop_m = m;
+                        s_hop_m = unocc[u];
                         break;
                     }
                 }
@@ -849,19 +880,50 @@ cudaError_t launch_coupling_fp64(const DevState &s, double dt, double mass, doub
     return cudaGetLastError();
 }
 
+// Column-group shape of k_cheb: EPT electrons per thread and G groups per
+// CTA, chosen to fill warps (rows x groups close to a multiple of 32) and to
+// waste no electron slots, within 1024 threads.
+void cheb_shape(int N, int Ne, int &ept, int &G)
+{
+    double best = -1.0;
+    ept = 1;
+    G = 1;
+    for (int e = 2; e >= 1; --e) {
+        for (int g = 1; g * N <= 1024; ++g) {
+            const int nb = g * e;
+            if (nb > 2 * Ne + 1) break;
+            const int thr = g * N, thr32 = (thr + 31) & ~31;
+            const int blocks = (Ne + nb - 1) / nb;
+            const double eff = (double)thr / thr32 * (double)Ne / (blocks * nb);
+            // prefer larger CTAs at equal efficiency (fewer W reloads)
+            const double score = eff + 1e-4 * nb;
+            if (score > best) {
+                best = score;
+                ept = e;
+                G = g;
+            }
+        }
+    }
+}
+
 cudaError_t launch_cheb_fp64(const DevState &s, double dt, cudaStream_t st)
 {
     if (s.n == 0) return cudaSuccess;
-    const size_t smem = (size_t)s.N * 2 * kColBlock * sizeof(double);
-    dim3 grid((unsigned)s.n, (unsigned)((s.Ne + kColBlock - 1) / kColBlock));
-    k_cheb<kColBlock><<<grid, round32(s.N), smem, st>>>(s, dt);
+    int ept, G;
+    cheb_shape(s.N, s.Ne, ept, G);
+    const int nb = G * ept;
+    const size_t smem = (size_t)s.N * 2 * nb * sizeof(double);
+    const int threads = (G * s.N + 31) & ~31;
+    dim3 grid((unsigned)s.n, (unsigned)((s.Ne + nb - 1) / nb));
+    if (ept == 2) k_cheb<2><<<grid, threads, smem, st>>>(s, dt, G);
+    else k_cheb<1><<<grid, threads, smem, st>>>(s, dt, G);
     return cudaGetLastError();
 }
 
 size_t hop_smem_bytes(int N, int Ne)
 {
-    return (size_t)Ne * Ne * sizeof(double2) + (size_t)(2 * N + 64) * sizeof(double) +
-           (size_t)(2 * Ne + N) * sizeof(int);
+    return (size_t)(Ne * Ne + Ne) * sizeof(double2) + (size_t)(2 * N + 64) * sizeof(double) +
+           (size_t)(2 * Ne + 2 * N) * sizeof(int);
 }
 
 cudaError_t launch_hop(const DevState &s, double dt, double mass, uint64_t seed, int skip_bound,
