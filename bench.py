@@ -32,6 +32,7 @@ METRIC = "IESH trajectory-steps/s (batched, 1 GB300) vs plain FP64 path; % of ro
 UNIT = "traj-steps/s"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 nominal FP64 rate (recipe's nominal table)
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 SIMT at the maximum SM clock
 # DRAM bytes (read + write) per trajectory of the dominant kernel, from the ncu capture in
 # profiles/iesh_fp64_step_M100.md (1024-trajectory launch, scaled per trajectory; the
 # traffic is per-trajectory W and C streams, so it grows in proportion to the batch).
@@ -137,38 +138,53 @@ def run_ours(args):
     n = args.n_traj
     x, p, occ, C = initial_state(md, kT, n, seed=1000 + rank)
     stream = torch.cuda.current_stream()
-    ctx = P.Context(md, n, precision=P.PREC_FP64, stream=stream.cuda_stream)
-    ctx.set_state(x, p, occ, C)
     seed = args.seed + rank  # Philox key per replica
-    for _ in range(args.warmup):
-        ctx.run(dt, 1, seed)
-    torch.cuda.synchronize()
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ctx.profile(True)
-    barrier()
-    with ClockSampler(local) as clk:
+    def measure(precision, sample_clocks):
+        c = P.Context(md, n, precision=precision, stream=stream.cuda_stream)
+        c.set_state(x, p, occ, C if precision == P.PREC_FP64 else C.astype(np.complex64))
+        for _ in range(args.warmup):
+            c.run(dt, 1, seed)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        c.profile(True)
+        barrier()
+        clk = ClockSampler(local) if sample_clocks else None
+        if clk:
+            clk.__enter__()
         ev0.record(stream)
         for _ in range(args.steps):
-            ctx.run(dt, 1, seed)
+            c.run(dt, 1, seed)
         ev1.record(stream)
         barrier()
-    ms = ev0.elapsed_time(ev1)
-    prof = ctx.profile_read()
-    ctx.profile(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        if clk:
+            clk.__exit__()
+        ms_ = ev0.elapsed_time(ev1)
+        prof_ = c.profile_read()
+        c.profile(False)
+        if world > 1:
+            tt = torch.tensor([ms_], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms_ = float(tt.item())
+        return c, ms_, prof_, clk
+
+    ctx, ms, prof, clk = measure(P.PREC_FP64, True)
     st = ctx.get_state()
     K = ctx.propagator_terms()
     bad = int(np.count_nonzero(st["status"]))
+    mixed = None
+    if not args.no_mixed:
+        cm, ms_m, prof_m, _ = measure(P.PREC_MIXED, False)
+        Km = cm.propagator_terms()
+        bad_m = int(np.count_nonzero(cm.get_state()["status"]))
+        cm.close()
+        mixed = (ms_m, prof_m, Km, bad_m)
 
     # ---- end to end through the C-ABI with pinned host buffers
     N, Ne = md["M"] + 1, md["Ne"]
@@ -193,7 +209,7 @@ def run_ours(args):
     h2d = n * (8 + 8 + 2 * Ne + 16 * Ne * N)
     d2h = h2d + 4 * n
 
-    clocks = clk.summary()
+    clocks = clk.summary() if clk else None
     if rank == 0:
         value = world * n * args.steps / (ms / 1e3)
         # dominant kernel: the Chebyshev propagator (FP64 DFMA pipe)
@@ -231,6 +247,25 @@ def run_ours(args):
             "clocks": clocks,
             "impl": "ours",
         }
+        if mixed is not None:
+            ms_m, prof_m, Km, bad_m = mixed
+            pm_ms, pm_n = prof_m["propagate"]
+            fl_m = float(np.sum(Km.astype(np.float64))) * 4.0 * N * N * Ne
+            ach_m = fl_m / (pm_ms / pm_n / 1e3) / 1e12 if pm_n else None
+            tot_m = max(1e-9, sum(u[0] for u in prof_m.values()))
+            line["mixed"] = {
+                "value": world * n * args.steps / (ms_m / 1e3), "unit": UNIT,
+                "ms_per_step": ms_m / args.steps, "speedup_vs_fp64": ms / ms_m,
+                "dtype": "f32 propagation/coupling/ratio solves; f64 eigenpairs, overlap LU, rescale",
+                "kernel_time_share": {k: round(v[0] / tot_m, 4) for k, v in prof_m.items() if v[1]},
+                "roofline_propagate": {"bound": "alu", "achieved": ach_m,
+                                       "peak": FP32_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                                       "frac": ach_m / FP32_NOMINAL_TFLOPS if ach_m else None,
+                                       "peak_source": "nominal FP32 SIMT (152 SMs x 128 FMA x 2 x 2.07 GHz)",
+                                       "mean_cheb_terms": float(Km.mean())},
+                "gpu_launches": int(sum(v[1] for v in prof_m.values())),
+                "status_nonzero": bad_m,
+            }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args, md, kT, dt)
         print(json.dumps(line), flush=True)
@@ -302,6 +337,7 @@ def main():
     ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=3)
     ap.add_argument("--cpu-steps", dest="cpu_steps", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -310,8 +310,8 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
     else if (Ne > kMaxHopElectrons) st = fail(ctx, IESH_EINVAL, "n_elec %d above %d", Ne, kMaxHopElectrons);
     else if (!(model->mass > 0.0)) st = fail(ctx, IESH_EINVAL, "mass must be positive");
     else if (!(model->gamma >= 0.0)) st = fail(ctx, IESH_EINVAL, "gamma must be >= 0");
-    else if (opt->precision != IESH_PREC_FP64)
-        st = fail(ctx, IESH_EUNSUPPORTED, "precision %d not available in this build", opt->precision);
+    else if (opt->precision != IESH_PREC_FP64 && opt->precision != IESH_PREC_MIXED)
+        st = fail(ctx, IESH_EINVAL, "unknown precision %d", opt->precision);
     else if (opt->record_every < 0 || opt->max_records < 0) st = fail(ctx, IESH_EINVAL, "negative record sizes");
     if (st != IESH_OK) {
         *out = ctx;  // let the caller read the message, then destroy
@@ -357,9 +357,22 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
     A(d.rec_sh, std::max<size_t>(1, T * d.max_records))
     A(d.rec_wf, std::max<size_t>(1, T * d.max_records))
     A(eps, (size_t)M) A(z0, (size_t)M)
+    float *epsdiff = nullptr;
+    A(epsdiff, (size_t)M * M)
 #undef A
     d.eps = eps;
     d.z0 = z0;
+    d.epsdiff = epsdiff;
+    {
+        std::vector<float> ed((size_t)M * M);
+        for (int a = 0; a < M; ++a)
+            for (int b = 0; b < M; ++b) ed[(size_t)a * M + b] = (float)(ctx->eps_h[a] - ctx->eps_h[b]);
+        cudaError_t e0 = cudaMemcpy(epsdiff, ed.data(), ed.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e0 != cudaSuccess) {
+            *out = ctx;
+            return fail(ctx, IESH_ECUDA, "table upload failed: %s", cudaGetErrorString(e0));
+        }
+    }
     cudaError_t e1 = cudaMemcpyAsync(eps, ctx->eps_h.data(), M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
     cudaError_t e2 = cudaMemcpyAsync(z0, ctx->z0_h.data(), M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
     cudaError_t e3 = cudaStreamSynchronize(ctx->stream);
@@ -528,14 +541,16 @@ iesh_status iesh_run(iesh_ctx *ctx, double dt, int64_t n_steps, uint64_t seed)
     if (!ctx->have_state) return fail(ctx, IESH_ESTATE, "run before init_state/set_state");
     if (!(dt > 0.0) || n_steps < 0) return fail(ctx, IESH_EINVAL, "need dt > 0 and n_steps >= 0");
     const DevState &d = ctx->ds;
-    const double tol = 1e-15;
+    const bool mx = ctx->mixed;
+    // Chebyshev truncation: FP64 rounding level, or FP32 level for the mixed path
+    const double tol = mx ? 1e-7 : 1e-15;
     for (int64_t k = 0; k < n_steps; ++k) {
         CU(timed(ctx, IESH_K_EIGEN, [&] { return launch_eigen(d, ctx->md, dt, 1, ctx->stream); }));
         CU(timed(ctx, IESH_K_COUPLING,
-                 [&] { return launch_coupling_fp64(d, dt, ctx->model.mass, tol, ctx->stream); }));
-        CU(timed(ctx, IESH_K_PROPAGATE, [&] { return launch_cheb_fp64(d, dt, ctx->stream); }));
+                 [&] { return launch_coupling(d, dt, ctx->model.mass, tol, mx, ctx->stream); }));
+        CU(timed(ctx, IESH_K_PROPAGATE, [&] { return launch_cheb(d, dt, mx, ctx->stream); }));
         CU(timed(ctx, IESH_K_HOP, [&] {
-            return launch_hop(d, dt, ctx->model.mass, seed, ctx->opt.skip_bound, nullptr, ctx->stream);
+            return launch_hop(d, dt, ctx->model.mass, seed, ctx->opt.skip_bound, nullptr, ctx->stream, mx);
         }));
     }
     return IESH_OK;
@@ -610,7 +625,7 @@ iesh_status iesh_hop_probabilities(iesh_ctx *ctx, double dt, double *g)
         CU(cudaMallocAsync((void **)&tmp, bytes, ctx->stream));
         dst = tmp;
     }
-    CU(launch_hop(d, dt, ctx->model.mass, 0, 0, dst, ctx->stream));
+    CU(launch_hop(d, dt, ctx->model.mass, 0, 0, dst, ctx->stream, ctx->mixed));
     if (host) {
         CU(cudaMemcpyAsync(g, tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream));
         CU(cudaFreeAsync(tmp, ctx->stream));

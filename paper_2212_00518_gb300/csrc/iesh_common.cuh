@@ -47,6 +47,7 @@ struct DevState {
     int record_every, max_records;
     double z_done;
     const double *eps, *z0;    // bath [M]: energies and sqrt(Gamma/2pi) sqrt(w_k)
+    const float *epsdiff;      // [M][M] eps_a - eps_b rounded to FP32 (mixed path)
 };
 
 // ---------------------------------------------------------------- models

@@ -10,12 +10,12 @@ namespace iesh {
 cudaError_t launch_eigen(const DevState &s, const ModelDev &md, double dt, int mode,
                          cudaStream_t st);
 cudaError_t launch_force(const DevState &s, cudaStream_t st);
-cudaError_t launch_coupling_fp64(const DevState &s, double dt, double mass, double tol,
-                                 cudaStream_t st);
-cudaError_t launch_cheb_fp64(const DevState &s, double dt, cudaStream_t st);
+cudaError_t launch_coupling(const DevState &s, double dt, double mass, double tol, bool mixed,
+                            cudaStream_t st);
+cudaError_t launch_cheb(const DevState &s, double dt, bool mixed, cudaStream_t st);
 size_t hop_smem_bytes(int N, int Ne);
 cudaError_t launch_hop(const DevState &s, double dt, double mass, uint64_t seed, int skip_bound,
-                       double *g_out, cudaStream_t st);
+                       double *g_out, cudaStream_t st, bool mixed = false);
 cudaError_t launch_init_nuclear(const DevState &s, double mass, uint64_t seed, double kT,
                                 int wigner, double omega, double x_eq, cudaStream_t st);
 cudaError_t launch_sample_occ(const DevState &s, uint64_t seed, double kT, cudaStream_t st);

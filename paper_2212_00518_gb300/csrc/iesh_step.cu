@@ -57,59 +57,22 @@ __device__ __forceinline__ Sec sec_eval(int M, const double *__restrict__ eps,
     return e;
 }
 
-// Root r (0..M) of the secular equation.  Fixed-weight iteration: the
-// origin pole is kept exactly and the rest is modelled by one more pole (or
-// by a linear term for the two outermost roots) matched in value and slope;
-// each model root is safeguarded by the bracket of sign changes.
-__device__ void secular_root(int r, int M, const double *__restrict__ eps,
-                             const double *__restrict__ z2, double h, double Z2, bool warm,
-                             double guess, double &lam, double &q0, uint32_t &st)
+// Fixed-weight iteration for one root in the shifted variable tau about the
+// origin pole o: the origin pole is kept exactly and the rest of g is
+// modelled by one more pole at tau = +D (kind 0) or -D (kind 1), or by a
+// linear term for the two outermost roots (kind 2: below all poles, kind 3:
+// above), matched in value and slope; each model root is safeguarded by the
+// bracket [lo, hi] of sign changes.  On return e is evaluated at tau.
+__device__ bool sec_iterate(int M, const double *__restrict__ eps, const double *__restrict__ z2,
+                            double h, int o, int kind, double D, double &lo, double &hi,
+                            double &tau, Sec &e, bool have)
 {
-    int o, kind;
-    double lo, hi, D = 0.0, tau;
-    Sec e;
-    bool have = false;
-    if (r > 0 && r < M) {
-        const int L = r - 1;
-        D = eps[r] - eps[L];
-        const Sec em = sec_eval(M, eps, z2, L, 0.5 * D, eps[L] - h);
-        if (em.g >= 0.0) {
-            o = L; kind = 0; lo = 0.0; hi = 0.5 * D; tau = 0.5 * D; e = em; have = true;
-        } else {
-            o = r; kind = 1; lo = -0.5 * D; hi = 0.0; tau = -0.5 * D;
-        }
-    } else if (r == 0) {
-        o = 0; kind = 2;
-        const double t = h - eps[0];
-        const double lb = 0.5 * ((h + eps[0]) - sqrt(t * t + 4.0 * Z2));
-        lo = (lb - eps[0]) * (1.0 + 1e-12) - 1e-300;
-        hi = 0.0;
-        tau = 0.5 * lo;
-    } else {
-        o = M - 1; kind = 3;
-        const double t = h - eps[M - 1];
-        const double ub = 0.5 * ((h + eps[M - 1]) + sqrt(t * t + 4.0 * Z2));
-        lo = 0.0;
-        hi = (ub - eps[M - 1]) * (1.0 + 1e-12) + 1e-300;
-        tau = 0.5 * hi;
-    }
-    if (warm) {
-        const double tg = guess - eps[o];
-        if (tg > lo && tg < hi) {
-            tau = tg;
-            have = false;
-        }
-    }
     const double eomh = eps[o] - h;
     const double s = z2[o];
-    bool conv = false;
     for (int it = 0; it < 80; ++it) {
         if (!have) e = sec_eval(M, eps, z2, o, tau, eomh);
         have = false;
-        if (fabs(e.g) <= 8.0 * kU * e.sabs) {
-            conv = true;
-            break;
-        }
+        if (fabs(e.g) <= 8.0 * kU * e.sabs) return true;
         if (e.g < 0.0) lo = tau;
         else hi = tau;
         double tn;
@@ -137,53 +100,146 @@ __device__ void secular_root(int r, int M, const double *__restrict__ eps,
         tau = tn;
         if (tiny) {
             e = sec_eval(M, eps, z2, o, tau, eomh);
-            conv = true;
-            break;
+            return true;
         }
     }
-    if (!conv) {
-        st |= ST_SECULAR;
-        e = sec_eval(M, eps, z2, o, tau, eomh);
+    e = sec_eval(M, eps, z2, o, tau, eomh);
+    return false;
+}
+
+// Root r (0..M) of the secular equation, lam and q0 = 1/sqrt(g'(lam)).
+// Cold start: the sign of g at the middle of the pole gap picks the nearer
+// pole as origin and the half-gap as bracket.  Warm start (previous root
+// `guess`, which lies in the same gap): origin = pole nearer the guess,
+// bracket = the whole gap, started at the guess; if the root ends in the
+// far half of the gap it is refined once more about the other pole.
+__device__ void secular_root(int r, int M, const double *__restrict__ eps,
+                             const double *__restrict__ z2, double h, double Z2, bool warm,
+                             double guess, double &lam, double &q0, uint32_t &st)
+{
+    int o, kind;
+    double lo, hi, D = 0.0, tau;
+    Sec e;
+    bool have = false, conv;
+    if (r > 0 && r < M) {
+        const int L = r - 1;
+        D = eps[r] - eps[L];
+        if (warm && guess > eps[L] && guess < eps[r]) {
+            if (guess - eps[L] <= eps[r] - guess) {
+                o = L; kind = 0; lo = 0.0; hi = D; tau = guess - eps[L];
+            } else {
+                o = r; kind = 1; lo = -D; hi = 0.0; tau = guess - eps[r];
+            }
+            conv = sec_iterate(M, eps, z2, h, o, kind, D, lo, hi, tau, e, false);
+            if (kind == 0 && tau > 0.5 * D) {
+                o = r; kind = 1; lo = fmin(lo - D, -0.5 * D); hi = 0.0; tau = tau - D;
+                conv = sec_iterate(M, eps, z2, h, o, kind, D, lo, hi, tau, e, false);
+            } else if (kind == 1 && tau < -0.5 * D) {
+                o = L; kind = 0; lo = 0.0; hi = fmax(hi + D, 0.5 * D); tau = tau + D;
+                conv = sec_iterate(M, eps, z2, h, o, kind, D, lo, hi, tau, e, false);
+            }
+        } else {
+            const Sec em = sec_eval(M, eps, z2, L, 0.5 * D, eps[L] - h);
+            if (em.g >= 0.0) {
+                o = L; kind = 0; lo = 0.0; hi = 0.5 * D; tau = 0.5 * D; e = em; have = true;
+            } else {
+                o = r; kind = 1; lo = -0.5 * D; hi = 0.0; tau = -0.5 * D;
+            }
+            conv = sec_iterate(M, eps, z2, h, o, kind, D, lo, hi, tau, e, have);
+        }
+    } else {
+        if (r == 0) {
+            o = 0; kind = 2;
+            const double t = h - eps[0];
+            const double lb = 0.5 * ((h + eps[0]) - sqrt(t * t + 4.0 * Z2));
+            lo = (lb - eps[0]) * (1.0 + 1e-12) - 1e-300;
+            hi = 0.0;
+            tau = 0.5 * lo;
+        } else {
+            o = M - 1; kind = 3;
+            const double t = h - eps[M - 1];
+            const double ub = 0.5 * ((h + eps[M - 1]) + sqrt(t * t + 4.0 * Z2));
+            lo = 0.0;
+            hi = (ub - eps[M - 1]) * (1.0 + 1e-12) + 1e-300;
+            tau = 0.5 * hi;
+        }
+        if (warm) {
+            const double tg = guess - eps[o];
+            if (tg > lo && tg < hi) tau = tg;
+        }
+        conv = sec_iterate(M, eps, z2, h, o, kind, D, lo, hi, tau, e, false);
     }
+    if (!conv) st |= ST_SECULAR;
     lam = eps[o] + tau;
     q0 = 1.0 / sqrt(e.gp);
 }
 
+// Trajectories per CTA of k_eigen: fill warps with one thread per root.
+int eigen_tpb(int N)
+{
+    int best = 1;
+    double be = 0.0;
+    for (int t = 1; t * N <= 512; ++t) {
+        const int thr = t * N, thr32 = (thr + 31) & ~31;
+        const double eff = (double)thr / thr32 + 1e-4 * t;
+        if (eff > be) {
+            be = eff;
+            best = t;
+        }
+    }
+    return best;
+}
+
 // mode 0: eigenpairs and force at the stored position (cold start);
 // mode 1: full first half of a step (kick, drift, eigenpairs, force, kick).
-__global__ void __launch_bounds__(256) k_eigen(DevState s, ModelDev md, double dt, int mode)
+// tpb trajectories per CTA, one thread per root.
+__global__ void __launch_bounds__(512, 1) k_eigen(DevState s, ModelDev md, double dt, int mode, int tpb)
 {
     extern __shared__ double sh[];
-    const int64_t t = blockIdx.x;
-    if (t >= s.n || (s.status[t] & ST_DONE)) return;
     const int N = s.N, M = s.M, Ne = s.Ne;
-    double *eps_s = sh, *z2_s = eps_s + M, *lam_s = z2_s + M, *q0_s = lam_s + N,
-           *red = q0_s + N;
-    double x = s.x[t], p = s.p[t];
-    if (mode == 1) {
-        p += 0.5 * dt * s.F[t];
-        x += dt * p / md.mass;
-    }
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const double l = s.lam[t * N + i];
+    const int slot = threadIdx.x / N;
+    const int r = threadIdx.x - slot * N;
+    const int64_t t = (int64_t)blockIdx.x * tpb + slot;
+    const bool act = slot < tpb && t < s.n && !(s.status[t] & ST_DONE);
+    double *eps_s = sh;                                  // [M], shared by the slots
+    const int per = M + 2 * N + 2;
+    double *z2_s = eps_s + M + (slot < tpb ? slot : 0) * per;  // [M]
+    double *lam_s = z2_s + M;                            // [N]
+    double *q0_s = lam_s + N;                            // [N]
+    double *misc = q0_s + N;                             // Z2, force sum
+    for (int k = threadIdx.x; k < M; k += blockDim.x) eps_s[k] = s.eps[k];
+    double x = 0.0, p = 0.0;
+    ModelVals mv;
+    if (act) {
+        x = s.x[t];
+        p = s.p[t];
         if (mode == 1) {
-            s.lam_prev[t * N + i] = l;
-            s.q0_prev[t * N + i] = s.q0[t * N + i];
+            p += 0.5 * dt * s.F[t];
+            x += dt * p / md.mass;
         }
-        lam_s[i] = l;
+        const double l = s.lam[t * N + r];
+        if (mode == 1) {
+            s.lam_prev[t * N + r] = l;
+            s.q0_prev[t * N + r] = s.q0[t * N + r];
+            if (r < 4) s.geo_prev[t * 4 + r] = s.geo[t * 4 + r];
+        }
+        lam_s[r] = l;
+        mv = model_eval(md, x);
+        for (int k = r; k < M; k += N) {
+            const double z = s.z0[k] * mv.f;
+            z2_s[k] = z * z;
+        }
     }
-    if (mode == 1 && threadIdx.x < 4) s.geo_prev[t * 4 + threadIdx.x] = s.geo[t * 4 + threadIdx.x];
-    const ModelVals mv = model_eval(md, x);
-    double zp = 0.0;
-    for (int k = threadIdx.x; k < M; k += blockDim.x) {
-        eps_s[k] = s.eps[k];
-        const double z = s.z0[k] * mv.f;
-        z2_s[k] = z * z;
-        zp += z * z;
+    __syncthreads();
+    if (act && r == 0) {
+        double zs = 0.0;
+        for (int k = 0; k < M; ++k) zs += z2_s[k];
+        misc[0] = zs;
     }
-    const double Z2 = block_sum(zp, red);  // synchronises
+    __syncthreads();
     uint32_t st = 0;
-    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    if (act) {
+        const double Z2 = misc[0];
         double l, q;
         if (Z2 > 0.0) {
             secular_root(r, M, eps_s, z2_s, mv.h, Z2, mode == 1, lam_s[r], l, q, st);
@@ -198,18 +254,17 @@ __global__ void __launch_bounds__(256) k_eigen(DevState s, ModelDev md, double d
         s.q0[t * N + r] = q;
         lam_s[r] = l;
         q0_s[r] = q;
+        if (st) atomicOr(&s.status[t], st);
     }
     __syncthreads();
-    const double kappa = (mv.f != 0.0) ? mv.df / mv.f : 0.0;
-    double fp = 0.0;
-    for (int a = threadIdx.x; a < Ne; a += blockDim.x) {
-        const int i = s.occ[t * Ne + a];
-        const double q = q0_s[i];
-        fp += q * q * (mv.dh + 2.0 * kappa * (lam_s[i] - mv.h));
-    }
-    const double dl = block_sum(fp, red);
-    if (st) atomicOr(&s.status[t], st);
-    if (threadIdx.x == 0) {
+    if (act && r == 0) {
+        const double kappa = (mv.f != 0.0) ? mv.df / mv.f : 0.0;
+        double dl = 0.0;
+        for (int a = 0; a < Ne; ++a) {
+            const int i = s.occ[t * Ne + a];
+            const double q = q0_s[i];
+            dl += q * q * (mv.dh + 2.0 * kappa * (lam_s[i] - mv.h));
+        }
         const double F = -mv.dU0 - dl;
         if (mode == 1) p += 0.5 * dt * F;
         s.x[t] = x;
@@ -284,6 +339,29 @@ __device__ void bessel_j(double rho, int K, double *J)
     for (int k = 0; k <= K; ++k) J[k] *= sc;
 }
 
+// Chebyshev degree and coefficients for a spectrum inside [lo, hi] (in units
+// of dt): the smallest K whose tail bound 2 sum_{k>K} (rho/2)^k / k! is below
+// tol, and J_0..J_K(rho).  Called by one thread per trajectory.
+__device__ void cheb_setup(const DevState &s, int64_t t, double lo, double hi, double tol)
+{
+    double *cb = s.cheb + t * kChebStride;
+    const double c = 0.5 * (lo + hi), rho = 0.5 * (hi - lo);
+    int K = 0;
+    double term = rho * 0.5;  // (rho/2)^{K+1} / (K+1)!
+    while (K < kChebMax - 2) {
+        const double ratio = (rho * 0.5) / (K + 2);
+        const double tail = (ratio < 1.0) ? 2.0 * term / (1.0 - ratio) : 1e300;
+        if (tail <= tol) break;
+        ++K;
+        term *= (rho * 0.5) / (K + 1);
+    }
+    if (K >= kChebMax - 2) atomicOr(&s.status[t], ST_PROP);
+    cb[0] = c;
+    cb[1] = rho;
+    cb[2] = (double)K;
+    bessel_j(rho, K, cb + 3);
+}
+
 __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double mass, double tol)
 {
     extern __shared__ double sh[];
@@ -320,25 +398,76 @@ __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double m
     }
     lo = block_min(lo, red);
     hi = block_max(hi, red);
-    if (threadIdx.x == 0) {
-        double *cb = s.cheb + t * kChebStride;
-        const double c = 0.5 * (lo + hi), rho = 0.5 * (hi - lo);
-        // smallest K whose Chebyshev tail bound 2 sum_{k>K} (rho/2)^k / k! is below tol
-        int K = 0;
-        double term = rho * 0.5;  // (rho/2)^{K+1} / (K+1)!
-        while (K < kChebMax - 2) {
-            const double ratio = (rho * 0.5) / (K + 2);
-            const double tail = (ratio < 1.0) ? 2.0 * term / (1.0 - ratio) : 1e300;
-            if (tail <= tol) break;
-            ++K;
-            term *= (rho * 0.5) / (K + 1);
+    if (threadIdx.x == 0) cheb_setup(s, t, lo, hi, tol);
+}
+
+// Mixed precision: W in FP32.  Each eigenvalue is written relative to its
+// nearer bath pole o (lam = eps_o + tau); the difference of two eigenvalues
+// is then the FP32 pole difference (a table rounded once from FP64) plus the
+// difference of the small offsets, so nearly degenerate pairs keep FP32
+// relative accuracy.  The numerators are formed in FP32.
+__global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, double mass, double tol)
+{
+    extern __shared__ double sh[];
+    const int64_t t = blockIdx.x;
+    if (t >= s.n || (s.status[t] & ST_DONE)) return;
+    const int N = s.N, M = s.M;
+    double *red = sh;                                  // [32]
+    double *Lsum = red + 32;                           // [N] dt (lam0 + lam1) / 2
+    float *qf = reinterpret_cast<float *>(Lsum + N);   // [2][N]
+    float *lmh = qf + 2 * N;                           // [2][N] lam - h
+    float *tau = lmh + 2 * N;                          // [2][N] lam - eps_o
+    int *org = reinterpret_cast<int *>(tau + 2 * N);   // [2][N] o
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+        double lsum = 0.0;
+        for (int gi = 0; gi < 2; ++gi) {
+            const double lam = gi ? s.lam[t * N + r] : s.lam_prev[t * N + r];
+            const double q = gi ? s.q0[t * N + r] : s.q0_prev[t * N + r];
+            const double h = gi ? s.geo[t * 4] : s.geo_prev[t * 4];
+            int o;
+            if (r == 0) o = 0;
+            else if (r == M) o = M - 1;
+            else o = (lam - s.eps[r - 1] <= s.eps[r] - lam) ? r - 1 : r;
+            org[gi * N + r] = o;
+            tau[gi * N + r] = (float)(lam - s.eps[o]);
+            qf[gi * N + r] = (float)q;
+            lmh[gi * N + r] = (float)(lam - h);
+            lsum += lam;
         }
-        if (K >= kChebMax - 2) atomicOr(&s.status[t], ST_PROP);
-        cb[0] = c;
-        cb[1] = rho;
-        cb[2] = (double)K;
-        bessel_j(rho, K, cb + 3);
+        Lsum[r] = 0.5 * dt * lsum;
     }
+    const float dh0 = (float)s.geo_prev[t * 4 + 1], k0 = (float)s.geo_prev[t * 4 + 2];
+    const float dh1 = (float)s.geo[t * 4 + 1], k1 = (float)s.geo[t * 4 + 2];
+    const float a0 = (float)(0.5 * dt * s.vprev[t]), a1 = (float)(0.5 * dt * (s.p[t] / mass));
+    __syncthreads();
+    float *W = reinterpret_cast<float *>(s.scratch + t * s.scratch_stride);
+    const float *__restrict__ E = s.epsdiff;  // [M][M] eps_a - eps_b
+    double lo = __longlong_as_double(0x7ff0000000000000ll), hi = -lo;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const float qk0 = qf[k], qk1 = qf[N + k], mk0 = lmh[k], mk1 = lmh[N + k];
+        const float tk0 = tau[k], tk1 = tau[N + k];
+        const float *E0 = E + (int64_t)org[k] * M, *E1 = E + (int64_t)org[N + k] * M;
+        float Rk = 0.0f;
+        for (int j = 0; j < N; ++j) {
+            float w = 0.0f;
+            if (j != k) {
+                const float den0 = E0[org[j]] + (tk0 - tau[j]);
+                const float den1 = E1[org[N + j]] + (tk1 - tau[N + j]);
+                const float d0 = qf[j] * qk0 * (dh0 + k0 * (lmh[j] + mk0)) / den0;
+                const float d1 = qf[N + j] * qk1 * (dh1 + k1 * (lmh[N + j] + mk1)) / den1;
+                w = a0 * d0 + a1 * d1;
+            }
+            W[(int64_t)j * N + k] = w;
+            Rk += fabsf(w);
+        }
+        // margin for the FP32 rounding of the row sum
+        const double R = (double)Rk * (1.0 + 1e-5);
+        lo = fmin(lo, Lsum[k] - R);
+        hi = fmax(hi, Lsum[k] + R);
+    }
+    lo = block_min(lo, red);
+    hi = block_max(hi, red);
+    if (threadIdx.x == 0) cheb_setup(s, t, lo, hi, tol);
 }
 
 // ============================================================ propagator
@@ -351,37 +480,55 @@ __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double m
 // electrons (columns) of one trajectory; thread (g, j) owns orbital row j of
 // the EPT electrons of column group g, so every warp is (nearly) full on the
 // FP64 pipe, which is the bound of this kernel.
-template <int EPT>
-__global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G)
+template <class RT>
+struct Cplx;
+template <>
+struct Cplx<double> {
+    typedef double2 T;
+};
+template <>
+struct Cplx<float> {
+    typedef float2 T;
+};
+
+template <int EPT, class RT>
+__global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int64_t t_base)
 {
-    extern __shared__ double tk[];  // [N][2 G EPT]
-    const int64_t t = blockIdx.x;
+    typedef typename Cplx<RT>::T CT;
+    extern __shared__ __align__(16) unsigned char cheb_smem[];
+    RT *tk = reinterpret_cast<RT *>(cheb_smem);  // [N][2 G EPT]
+    // the electron blocks of one trajectory are adjacent in launch order, so
+    // they run together and share W through L2
+    const int64_t t = t_base + blockIdx.y;
     if (t >= s.n || (s.status[t] & ST_DONE)) return;
     const int N = s.N, Ne = s.Ne;
     const int NB = G * EPT, W2 = 2 * NB;
     const int g = threadIdx.x / N;
     const int j = threadIdx.x - g * N;
     const bool act = g < G;
-    const int e0 = blockIdx.y * NB + g * EPT;  // first electron of this thread
+    const int e0 = blockIdx.x * NB + g * EPT;  // first electron of this thread
     const double *cb = s.cheb + t * kChebStride;
     const double c = cb[0], rho = cb[1];
     const int K = (int)cb[2];
     const double *J = cb + 3;
-    const double inv_rho = rho > 0.0 ? 1.0 / rho : 0.0;
-    const double *__restrict__ W = s.scratch + t * s.scratch_stride;
-    double2 *C = reinterpret_cast<double2 *>(s.C) + (int64_t)t * Ne * N;
-    const double Lc = act ? 0.5 * dt * (s.lam_prev[t * N + j] + s.lam[t * N + j]) - c : 0.0;
-    double *myrow = tk + j * W2 + 2 * EPT * g;
+    const RT inv_rho = (RT)(rho > 0.0 ? 1.0 / rho : 0.0);
+    const RT *__restrict__ W = reinterpret_cast<const RT *>(s.scratch + t * s.scratch_stride);
+    CT *C = reinterpret_cast<CT *>(s.C) + (int64_t)t * Ne * N;
+    const RT Lc = (RT)(act ? 0.5 * dt * (s.lam_prev[t * N + j] + s.lam[t * N + j]) - c : 0.0);
+    RT *myrow = tk + j * W2 + 2 * EPT * g;
 
-    double tp[2 * EPT], acc[2 * EPT];
+    RT tp[2 * EPT], acc[2 * EPT];
+    const RT J0 = (RT)J[0];
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
-        double2 v = make_double2(0.0, 0.0);
+        CT v;
+        v.x = 0;
+        v.y = 0;
         if (act && e0 + e < Ne) v = C[(int64_t)(e0 + e) * N + j];
         tp[2 * e] = v.x;
         tp[2 * e + 1] = v.y;
-        acc[2 * e] = J[0] * v.x;
-        acc[2 * e + 1] = J[0] * v.y;
+        acc[2 * e] = J0 * v.x;
+        acc[2 * e + 1] = J0 * v.y;
         if (act) {
             myrow[2 * e] = v.x;
             myrow[2 * e + 1] = v.y;
@@ -389,40 +536,40 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G)
     }
     __syncthreads();
     for (int k = 0; k < K; ++k) {
-        double y[2 * EPT];
+        RT y[2 * EPT];
 #pragma unroll
-        for (int q = 0; q < 2 * EPT; ++q) y[q] = 0.0;
+        for (int q = 0; q < 2 * EPT; ++q) y[q] = 0;
         if (act) {
-            const double *col = tk + 2 * EPT * g;
+            const RT *col = tk + 2 * EPT * g;
 #pragma unroll 4
             for (int i = 0; i < N; ++i) {
-                const double w = W[(int64_t)i * N + j];  // W_ij = -W_ji
-                const double *row = col + i * W2;
+                const RT w = W[(int64_t)i * N + j];  // W_ij = -W_ji
+                const RT *row = col + i * W2;
 #pragma unroll
                 for (int q = 0; q < 2 * EPT; ++q) y[q] = fma(w, row[q], y[q]);
             }
         }
-        double own[2 * EPT];
+        RT own[2 * EPT];
         if (act) {
 #pragma unroll
             for (int q = 0; q < 2 * EPT; ++q) own[q] = myrow[q];
         }
         __syncthreads();
         if (act) {
-            const double cj = 2.0 * J[k + 1];
+            const RT cj = (RT)(2.0 * J[k + 1]);
             const int ph = (k + 1) & 3;  // (-i)^(k+1)
 #pragma unroll
             for (int e = 0; e < EPT; ++e) {
                 // (X t)_j = ((L_j - c) t_j - i (W t)_j) / rho and (W t)_j = -y
-                const double xr = (Lc * own[2 * e] - y[2 * e + 1]) * inv_rho;
-                const double xi = (Lc * own[2 * e + 1] + y[2 * e]) * inv_rho;
-                double nr, ni;
+                const RT xr = (Lc * own[2 * e] - y[2 * e + 1]) * inv_rho;
+                const RT xi = (Lc * own[2 * e + 1] + y[2 * e]) * inv_rho;
+                RT nr, ni;
                 if (k == 0) {
                     nr = xr;
                     ni = xi;
                 } else {
-                    nr = 2.0 * xr - tp[2 * e];
-                    ni = 2.0 * xi - tp[2 * e + 1];
+                    nr = (RT)2 * xr - tp[2 * e];
+                    ni = (RT)2 * xi - tp[2 * e + 1];
                 }
                 tp[2 * e] = own[2 * e];
                 tp[2 * e + 1] = own[2 * e + 1];
@@ -446,13 +593,17 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G)
         __syncthreads();
     }
     if (act) {
-        double sc, cc;
-        sincos(c, &sc, &cc);
+        double scd, ccd;
+        sincos(c, &scd, &ccd);
+        const RT sc = (RT)scd, cc = (RT)ccd;
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
             if (e0 + e < Ne) {
-                const double ar = acc[2 * e], ai = acc[2 * e + 1];
-                C[(int64_t)(e0 + e) * N + j] = make_double2(cc * ar + sc * ai, cc * ai - sc * ar);
+                const RT ar = acc[2 * e], ai = acc[2 * e + 1];
+                CT out;
+                out.x = cc * ar + sc * ai;
+                out.y = cc * ai - sc * ar;
+                C[(int64_t)(e0 + e) * N + j] = out;
             }
         }
     }
@@ -465,40 +616,85 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G)
 // vector C_m S^{-1} is obtained by one forward substitution with U and one
 // backward substitution with L, then the row permutation.  The hop
 // probability is g_{a->m} = max(0, -2 dt v Re(R_ma) d_{m, s_a}).
+//
+// The LU uses partial pivoting without moving rows: perm[k] is the physical
+// row chosen as the k-th pivot.  Each warp owns the rows r = warp (mod
+// warps); per column it scales its rows, updates them, and records the
+// largest candidate of the next column, so one block barrier per column
+// suffices.  Complex products are written as explicit FMAs.
 __device__ __forceinline__ double2 cmul(double2 a, double2 b)
 {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 __device__ __forceinline__ double2 cfms(double2 acc, double2 a, double2 b)  // acc - a b
 {
-    return make_double2(acc.x - (a.x * b.x - a.y * b.y), acc.y - (a.x * b.y + a.y * b.x));
+    return make_double2(fma(-a.x, b.x, fma(a.y, b.y, acc.x)), fma(-a.x, b.y, fma(-a.y, b.x, acc.y)));
 }
 __device__ __forceinline__ double2 crcp(double2 a)
 {
     const double d = 1.0 / (a.x * a.x + a.y * a.y);
     return make_double2(a.x * d, -a.y * d);
 }
-
-__global__ void __launch_bounds__(256) k_hop(DevState s, double dt, double mass, uint64_t seed,
-                                             int skip_bound, double *g_out)
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b)
 {
-    extern __shared__ double sh[];
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cfmsf(float2 acc, float2 a, float2 b)  // acc - a b
+{
+    return make_float2(fmaf(-a.x, b.x, fmaf(a.y, b.y, acc.x)), fmaf(-a.x, b.y, fmaf(-a.y, b.x, acc.y)));
+}
+
+// Bytes of the matrix region: S / LU in FP64, and in the mixed path also the
+// FP32 copy of the factors followed by the FP32 substitution rows.
+__host__ __device__ inline size_t hop_region_bytes(int N, int Ne, bool f32)
+{
+    size_t a = (size_t)16 * Ne * Ne;
+    if (f32) {
+        const size_t b = (size_t)8 * Ne * Ne + (size_t)8 * (N - Ne) * Ne;
+        if (b > a) a = b;
+    }
+    return (a + 15) & ~(size_t)15;
+}
+
+size_t hop_smem_bytes(int N, int Ne, bool f32)
+{
+    return hop_region_bytes(N, Ne, f32) + (size_t)16 * Ne + (size_t)(2 * N + 64) * 8 +
+           (size_t)(64 + 64 + 3 * Ne + 2 * N) * 4;
+}
+size_t hop_smem_bytes(int N, int Ne) { return hop_smem_bytes(N, Ne, false); }
+
+// CT: coefficient type.  double2: the FP64 path.  float2: the mixed path --
+// S is widened to FP64 and factorised in FP64 (the overlap inverse), then
+// L and U are rounded to FP32 for the substitutions over the unoccupied rows.
+template <class CT>
+__global__ void __launch_bounds__(512, 1) k_hop(DevState s, double dt, double mass, uint64_t seed,
+                                                int skip_bound, double *g_out)
+{
+    constexpr bool kF32 = sizeof(CT) == sizeof(float2);
+    extern __shared__ __align__(16) unsigned char hop_smem[];
     const int64_t t = blockIdx.x;
     if (t >= s.n || (s.status[t] & ST_DONE)) return;
-    const int N = s.N, Ne = s.Ne;
-    double2 *A = reinterpret_cast<double2 *>(sh);            // [Ne][Ne] LU of S
-    double2 *dinv = A + Ne * Ne;                              // [Ne] 1 / U_jj
-    double *lam_s = reinterpret_cast<double *>(dinv + Ne);    // [N]
-    double *q0_s = lam_s + N;                                 // [N]
-    double *red = q0_s + N;                                   // [64]
-    int *occ_s = reinterpret_cast<int *>(red + 64);           // [Ne]
-    int *perm = occ_s + Ne;                                   // [Ne]
-    int *isocc = perm + Ne;                                   // [N]
-    int *unocc = isocc + N;                                   // [N - Ne] ascending
-    __shared__ int s_flag, s_piv, s_hop_a, s_hop_m;
+    const int N = s.N, Ne = s.Ne, nu = N - Ne;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const size_t abytes = hop_region_bytes(N, Ne, kF32);
+    double2 *A = reinterpret_cast<double2 *>(hop_smem);           // [Ne][Ne] physical rows
+    double2 *dinv = reinterpret_cast<double2 *>(hop_smem + abytes); // [Ne] 1/U_kk, logical k
+    double *lam_s = reinterpret_cast<double *>(dinv + Ne);         // [N]
+    double *q0_s = lam_s + N;                                     // [N]
+    double *red = q0_s + N;                                       // [64]
+    float *cand_v = reinterpret_cast<float *>(red + 64);          // [2][32] |a| per warp
+    int *cand_i = reinterpret_cast<int *>(cand_v + 64);           // [2][32] row per warp
+    int *occ_s = cand_i + 64;                                     // [Ne]
+    int *perm = occ_s + Ne;                                       // [Ne] pivot k -> row
+    int *rows = perm + Ne;                                        // [Ne] rows not yet pivots
+    int *isocc = rows + Ne;                                       // [N]
+    int *unocc = isocc + N;                                       // [N - Ne] ascending
+    __shared__ int s_flag, s_hop_a, s_hop_m;
     __shared__ double s_det_abs;
 
-    const double2 *Ct = reinterpret_cast<const double2 *>(s.C) + (int64_t)t * Ne * N;
+    const CT *Ct = reinterpret_cast<const CT *>(s.C) + (int64_t)t * Ne * N;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         lam_s[i] = s.lam[t * N + i];
         q0_s[i] = s.q0[t * N + i];
@@ -507,7 +703,6 @@ __global__ void __launch_bounds__(256) k_hop(DevState s, double dt, double mass,
     __syncthreads();
     for (int a = threadIdx.x; a < Ne; a += blockDim.x) {
         occ_s[a] = s.occ[t * Ne + a];
-        perm[a] = a;
         isocc[occ_s[a]] = 1;
     }
     if (threadIdx.x == 0) {
@@ -518,79 +713,114 @@ __global__ void __launch_bounds__(256) k_hop(DevState s, double dt, double mass,
     __syncthreads();
     for (int idx = threadIdx.x; idx < Ne * Ne; idx += blockDim.x) {
         const int a = idx / Ne, e = idx - a * Ne;
-        A[idx] = Ct[(int64_t)e * N + occ_s[a]];
+        A[idx] = to_d2(Ct[(int64_t)e * N + occ_s[a]]);
     }
-    __syncthreads();
-
-    // ---- LU with partial pivoting, P S = L U (unit L below the diagonal)
-    double logdet = 0.0;
-    for (int kc = 0; kc < Ne; ++kc) {
-        if (threadIdx.x < 32) {
-            double best = -1.0;
-            int bi = kc;
-            for (int r = kc + threadIdx.x; r < Ne; r += 32) {
-                const double2 v = A[r * Ne + kc];
-                const double m2 = v.x * v.x + v.y * v.y;
-                if (m2 > best) {
-                    best = m2;
-                    bi = r;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) {
-                    best = ob;
-                    bi = oi;
-                }
-            }
-            if (threadIdx.x == 0) {
-                s_piv = bi;
-                if (!(best > 0.0)) s_flag = 1;
-            }
-        }
-        __syncthreads();
-        if (s_flag) break;
-        const int pv = s_piv;
-        if (pv != kc) {
-            for (int c = threadIdx.x; c < Ne; c += blockDim.x) {
-                const double2 tmp = A[kc * Ne + c];
-                A[kc * Ne + c] = A[pv * Ne + c];
-                A[pv * Ne + c] = tmp;
-            }
-            if (threadIdx.x == 0) {
-                const int tp = perm[kc];
-                perm[kc] = perm[pv];
-                perm[pv] = tp;
-            }
-        }
-        __syncthreads();
-        const double2 dinv = crcp(A[kc * Ne + kc]);
-        for (int r = kc + 1 + threadIdx.x; r < Ne; r += blockDim.x)
-            A[r * Ne + kc] = cmul(A[r * Ne + kc], dinv);
-        __syncthreads();
-        const int rem = Ne - kc - 1;
-        for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
-            const int r = kc + 1 + idx / rem, c = kc + 1 + idx % rem;
-            A[r * Ne + c] = cfms(A[r * Ne + c], A[r * Ne + kc], A[kc * Ne + c]);
-        }
-        __syncthreads();
-    }
-    const bool singular = s_flag != 0;
-    if (singular && threadIdx.x == 0) atomicOr(&s.status[t], ST_SINGULAR);
-    const int nu = N - Ne;
     if (threadIdx.x == 0) {
         int u = 0;
         for (int m = 0; m < N; ++m)
             if (!isocc[m]) unocc[u++] = m;
     }
-    if (!singular)
-        for (int jc = threadIdx.x; jc < Ne; jc += blockDim.x) dinv[jc] = crcp(A[jc * Ne + jc]);
+    __syncthreads();
+    // pivot candidates of column 0 (|re| + |im| rounded to FP32 is enough to pick a pivot)
+    if (lane == 0) {
+        float bv = -1.0f;
+        int bi = Ne;
+        for (int r = warp; r < Ne; r += nwarp) {
+            const double2 v = A[r * Ne];
+            const float m2 = (float)(fabs(v.x) + fabs(v.y));
+            if (m2 > bv) {
+                bv = m2;
+                bi = r;
+            }
+        }
+        cand_v[warp] = bv;
+        cand_i[warp] = bi;
+        if (warp == 0)
+            for (int r = 0; r < Ne; ++r) rows[r] = r;
+    }
+    __syncthreads();
+
+    // ---- LU with partial pivoting: rows are not moved; rows[0..nr) lists the
+    // rows not yet used as pivots.  Two barriers per column: multipliers,
+    // then the trailing update, which also records the next column's
+    // per-warp pivot candidates.
+    bool singular = false;
+    int nr = Ne;
+    for (int kc = 0; kc < Ne; ++kc) {
+        const int buf = kc & 1;
+        float bv = -1.0f;
+        int pr = Ne;
+        for (int w = 0; w < nwarp; ++w) {
+            const float vv = cand_v[buf * 32 + w];
+            const int i = cand_i[buf * 32 + w];
+            if (vv > bv || (vv == bv && i < pr)) {
+                bv = vv;
+                pr = i;
+            }
+        }
+        const double2 pv = A[pr * Ne + kc];
+        if (!(pv.x != 0.0 || pv.y != 0.0)) {
+            singular = true;
+            break;
+        }
+        const double2 pinv = crcp(pv);
+        // remove pr from the row list (every thread does the same edit on a
+        // private copy of the position; thread 0 writes it after the barrier)
+        int ppos = 0;
+        for (int q = 0; q < nr; ++q)
+            if (rows[q] == pr) ppos = q;
+        // multipliers of the remaining rows
+        for (int q = threadIdx.x; q < nr; q += blockDim.x) {
+            const int r = rows[q];
+            if (r != pr) A[r * Ne + kc] = cmul(A[r * Ne + kc], pinv);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            perm[kc] = pr;
+            dinv[kc] = pinv;
+            rows[ppos] = rows[nr - 1];
+        }
+        const int nrow = nr - 1;  // rows to update (the list without pr)
+        const int ncol = Ne - kc - 1;
+        float cv = -1.0f;
+        int ci = Ne;
+        const int total = nrow * ncol;
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int qq = idx / ncol, c = kc + 1 + (idx - qq * ncol);
+            // list position qq of the list without pr: entry nr-1 moved into ppos
+            const int r = rows[(qq == ppos) ? nr - 1 : qq];
+            const double2 nv = cfms(A[r * Ne + c], A[r * Ne + kc], A[pr * Ne + c]);
+            A[r * Ne + c] = nv;
+            if (c == kc + 1) {
+                const float m2 = (float)(fabs(nv.x) + fabs(nv.y));
+                if (m2 > cv || (m2 == cv && r < ci)) {
+                    cv = m2;
+                    ci = r;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, cv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, ci, o);
+            if (ov > cv || (ov == cv && oi < ci)) {
+                cv = ov;
+                ci = oi;
+            }
+        }
+        if (lane == 0) {
+            cand_v[(buf ^ 1) * 32 + warp] = cv;
+            cand_i[(buf ^ 1) * 32 + warp] = ci;
+        }
+        nr = nrow;
+        __syncthreads();
+    }
+    if (singular && threadIdx.x == 0) atomicOr(&s.status[t], ST_SINGULAR);
     if (!singular && threadIdx.x == 0) {
+        double logdet = 0.0;
         for (int kc = 0; kc < Ne; ++kc) {
-            const double2 u = A[kc * Ne + kc];
-            logdet += 0.5 * log(u.x * u.x + u.y * u.y);
+            const double2 u = dinv[kc];  // 1/U_kk
+            logdet -= 0.5 * log(u.x * u.x + u.y * u.y);
         }
         s_det_abs = exp(logdet);
     }
@@ -604,12 +834,10 @@ __global__ void __launch_bounds__(256) k_hop(DevState s, double dt, double mass,
     if (do_ratios && skip_bound && g_out == nullptr) {
         // upper bound of the total hop probability (Sec. II C): |<J|psi>| <= 1
         double part = 0.0;
-        for (int idx = threadIdx.x; idx < Ne * N; idx += blockDim.x) {
-            const int a = idx / N, m = idx - a * N;
-            if (!isocc[m]) {
-                const int sa = occ_s[a];
-                part += fabs(nac(lam_s[m], q0_s[m], lam_s[sa], q0_s[sa], geo_h, geo_dh, geo_k));
-            }
+        for (int idx = threadIdx.x; idx < Ne * nu; idx += blockDim.x) {
+            const int a = idx / nu, m = unocc[idx - a * nu];
+            const int sa = occ_s[a];
+            part += fabs(nac(lam_s[m], q0_s[m], lam_s[sa], q0_s[sa], geo_h, geo_dh, geo_k));
         }
         const double sd = block_sum(part, red);
         const double bound = 2.0 * dt * fabs(v) * sd / s_det_abs;
@@ -617,43 +845,114 @@ __global__ void __launch_bounds__(256) k_hop(DevState s, double dt, double mass,
     }
 
     double *scr = s.scratch + t * s.scratch_stride;
-    double2 *Y = reinterpret_cast<double2 *>(scr);       // [Ne][N]
     double *G = g_out ? g_out + (int64_t)t * Ne * N : scr + 2 * (int64_t)Ne * N;  // [Ne][N]
+    // four lanes per unoccupied row: lane `sub` owns the entries k = sub (mod 4)
+    const int sub = threadIdx.x & 3, grp = threadIdx.x >> 2, ngrp = blockDim.x >> 2;
+    const unsigned quad = 0xFu << (lane & ~3);
     if (do_ratios) {
-        // one thread per unoccupied orbital m: y U = c_m, then z L = y
-        for (int u = threadIdx.x; u < nu; u += blockDim.x) {
-            const int m = unocc[u];
-            for (int jc = 0; jc < Ne; ++jc) {
-                double2 a0 = Ct[(int64_t)jc * N + m], a1 = make_double2(0.0, 0.0);
-                int i = 0;
-                for (; i + 1 < jc; i += 2) {
-                    a0 = cfms(a0, Y[(int64_t)i * N + m], A[i * Ne + jc]);
-                    a1 = cfms(a1, Y[(int64_t)(i + 1) * N + m], A[(i + 1) * Ne + jc]);
-                }
-                if (i < jc) a0 = cfms(a0, Y[(int64_t)i * N + m], A[i * Ne + jc]);
-                a0.x += a1.x;
-                a0.y += a1.y;
-                Y[(int64_t)jc * N + m] = cmul(a0, dinv[jc]);
+        if constexpr (kF32) {
+            // round L, U and 1/U_kk to FP32 in place (chunked so that every
+            // double2 is read before its bytes are overwritten)
+            float2 *A32 = reinterpret_cast<float2 *>(A);
+            for (int base = 0; base < Ne * Ne; base += blockDim.x) {
+                const int i = base + threadIdx.x;
+                const double2 dv = (i < Ne * Ne) ? A[i] : make_double2(0.0, 0.0);
+                __syncthreads();
+                if (i < Ne * Ne) A32[i] = make_float2((float)dv.x, (float)dv.y);
+                __syncthreads();
             }
-            for (int jc = Ne - 2; jc >= 0; --jc) {
-                double2 a0 = Y[(int64_t)jc * N + m], a1 = make_double2(0.0, 0.0);
-                int i = jc + 1;
-                for (; i + 1 < Ne; i += 2) {
-                    a0 = cfms(a0, Y[(int64_t)i * N + m], A[i * Ne + jc]);
-                    a1 = cfms(a1, Y[(int64_t)(i + 1) * N + m], A[(i + 1) * Ne + jc]);
+            float2 *dinv32 = reinterpret_cast<float2 *>(dinv);
+            const double2 dv = (threadIdx.x < Ne) ? dinv[threadIdx.x] : make_double2(0.0, 0.0);
+            __syncthreads();
+            if (threadIdx.x < Ne) dinv32[threadIdx.x] = make_float2((float)dv.x, (float)dv.y);
+            __syncthreads();
+            float2 *Y = reinterpret_cast<float2 *>(hop_smem + (size_t)8 * Ne * Ne);  // [nu][Ne]
+            for (int u0 = 0; u0 < nu; u0 += ngrp) {
+                const int u = u0 + grp;
+                const bool live = u < nu;
+                const int m = live ? unocc[u] : 0;
+                float2 *y = Y + (size_t)(live ? u : 0) * Ne;
+                // y U = c_m  (U_ij = A[perm[i]][j], i <= j)
+                for (int jc = 0; jc < Ne; ++jc) {
+                    float2 acc = make_float2(0.f, 0.f);
+                    if (live)
+                        for (int i = sub; i < jc; i += 4) acc = cfmsf(acc, y[i], A32[perm[i] * Ne + jc]);
+                    acc.x += __shfl_xor_sync(quad, acc.x, 1);
+                    acc.y += __shfl_xor_sync(quad, acc.y, 1);
+                    acc.x += __shfl_xor_sync(quad, acc.x, 2);
+                    acc.y += __shfl_xor_sync(quad, acc.y, 2);
+                    if (live && sub == (jc & 3)) {
+                        const CT c = Ct[(int64_t)jc * N + m];
+                        y[jc] = cmulf(make_float2(c.x + acc.x, c.y + acc.y), dinv32[jc]);
+                    }
                 }
-                if (i < Ne) a0 = cfms(a0, Y[(int64_t)i * N + m], A[i * Ne + jc]);
-                a0.x += a1.x;
-                a0.y += a1.y;
-                Y[(int64_t)jc * N + m] = a0;
+                // z L = y  (L_ij = A[perm[i]][j], i > j, unit diagonal)
+                for (int jc = Ne - 2; jc >= 0; --jc) {
+                    float2 acc = make_float2(0.f, 0.f);
+                    if (live) {
+                        int i = jc + 1 + ((sub - (jc + 1)) & 3);
+                        for (; i < Ne; i += 4) acc = cfmsf(acc, y[i], A32[perm[i] * Ne + jc]);
+                    }
+                    acc.x += __shfl_xor_sync(quad, acc.x, 1);
+                    acc.y += __shfl_xor_sync(quad, acc.y, 1);
+                    acc.x += __shfl_xor_sync(quad, acc.x, 2);
+                    acc.y += __shfl_xor_sync(quad, acc.y, 2);
+                    if (live && sub == (jc & 3)) y[jc] = make_float2(y[jc].x + acc.x, y[jc].y + acc.y);
+                }
+                // R_{m, perm[i]} = z_i ; g_{a->m}
+                if (live)
+                    for (int i = sub; i < Ne; i += 4) {
+                        const int a = perm[i];
+                        const int sa = occ_s[a];
+                        const double d = nac(lam_s[m], q0_s[m], lam_s[sa], q0_s[sa], geo_h, geo_dh, geo_k);
+                        const double gam = -2.0 * dt * v * (double)y[i].x * d;
+                        G[(int64_t)a * N + m] = gam > 0.0 ? gam : 0.0;
+                    }
             }
-            // R_{m, perm[i]} = z_i ; g_{a->m}
-            for (int i = 0; i < Ne; ++i) {
-                const int a = perm[i];
-                const int sa = occ_s[a];
-                const double d = nac(lam_s[m], q0_s[m], lam_s[sa], q0_s[sa], geo_h, geo_dh, geo_k);
-                const double gam = -2.0 * dt * v * Y[(int64_t)i * N + m].x * d;
-                G[(int64_t)a * N + m] = gam > 0.0 ? gam : 0.0;
+        } else {
+            double2 *Y = reinterpret_cast<double2 *>(scr);  // [Ne][N], column m per row
+            for (int u0 = 0; u0 < nu; u0 += ngrp) {
+                const int u = u0 + grp;
+                const bool live = u < nu;
+                const int m = live ? unocc[u] : 0;
+                for (int jc = 0; jc < Ne; ++jc) {
+                    double2 acc = make_double2(0.0, 0.0);
+                    if (live)
+                        for (int i = sub; i < jc; i += 4)
+                            acc = cfms(acc, Y[(int64_t)i * N + m], A[perm[i] * Ne + jc]);
+                    acc.x += __shfl_xor_sync(quad, acc.x, 1);
+                    acc.y += __shfl_xor_sync(quad, acc.y, 1);
+                    acc.x += __shfl_xor_sync(quad, acc.x, 2);
+                    acc.y += __shfl_xor_sync(quad, acc.y, 2);
+                    if (live && sub == (jc & 3)) {
+                        const double2 c = to_d2(Ct[(int64_t)jc * N + m]);
+                        Y[(int64_t)jc * N + m] = cmul(make_double2(c.x + acc.x, c.y + acc.y), dinv[jc]);
+                    }
+                }
+                for (int jc = Ne - 2; jc >= 0; --jc) {
+                    double2 acc = make_double2(0.0, 0.0);
+                    if (live) {
+                        int i = jc + 1 + ((sub - (jc + 1)) & 3);
+                        for (; i < Ne; i += 4)
+                            acc = cfms(acc, Y[(int64_t)i * N + m], A[perm[i] * Ne + jc]);
+                    }
+                    acc.x += __shfl_xor_sync(quad, acc.x, 1);
+                    acc.y += __shfl_xor_sync(quad, acc.y, 1);
+                    acc.x += __shfl_xor_sync(quad, acc.x, 2);
+                    acc.y += __shfl_xor_sync(quad, acc.y, 2);
+                    if (live && sub == (jc & 3)) {
+                        const double2 yv = Y[(int64_t)jc * N + m];
+                        Y[(int64_t)jc * N + m] = make_double2(yv.x + acc.x, yv.y + acc.y);
+                    }
+                }
+                if (live)
+                    for (int i = sub; i < Ne; i += 4) {
+                        const int a = perm[i];
+                        const int sa = occ_s[a];
+                        const double d = nac(lam_s[m], q0_s[m], lam_s[sa], q0_s[sa], geo_h, geo_dh, geo_k);
+                        const double gam = -2.0 * dt * v * Y[(int64_t)i * N + m].x * d;
+                        G[(int64_t)a * N + m] = gam > 0.0 ? gam : 0.0;
+                    }
             }
         }
         if (g_out)
@@ -667,8 +966,7 @@ __global__ void __launch_bounds__(256) k_hop(DevState s, double dt, double mass,
 
     // ---- stochastic selection in the order (slot a ascending, m ascending)
     if (do_ratios) {
-        double *slot = red;  // reuse: needs Ne <= 64 entries -> use scratch beyond G when larger
-        double *slot_sum = (Ne <= 64) ? slot : scr + 3 * (int64_t)Ne * N;
+        double *slot_sum = (Ne <= 64) ? red : scr + 3 * (int64_t)Ne * N;
         for (int a = threadIdx.x; a < Ne; a += blockDim.x) {
             double sa = 0.0;
             for (int u = 0; u < nu; ++u) sa += G[(int64_t)a * N + unocc[u]];
@@ -754,7 +1052,7 @@ __global__ void __launch_bounds__(256) k_hop(DevState s, double dt, double mass,
                     psh += q * q;
                     double ar = 0.0, ai = 0.0;
                     for (int i = 0; i < N; ++i) {
-                        const double2 cv = Ct[(int64_t)a * N + i];
+                        const double2 cv = to_d2(Ct[(int64_t)a * N + i]);
                         ar = fma(q0_s[i], cv.x, ar);
                         ai = fma(q0_s[i], cv.y, ai);
                     }
@@ -858,9 +1156,10 @@ cudaError_t launch_eigen(const DevState &s, const ModelDev &md, double dt, int m
                          cudaStream_t st)
 {
     if (s.n == 0) return cudaSuccess;
-    const int threads = round32(s.N < 256 ? s.N : 256);
-    const size_t smem = (size_t)(2 * s.M + 2 * s.N + 32) * sizeof(double);
-    k_eigen<<<(unsigned)s.n, threads, smem, st>>>(s, md, dt, mode);
+    const int tpb = eigen_tpb(s.N);
+    const int threads = round32(tpb * s.N);
+    const size_t smem = (size_t)(s.M + tpb * (s.M + 2 * s.N + 2)) * sizeof(double);
+    k_eigen<<<(unsigned)((s.n + tpb - 1) / tpb), threads, smem, st>>>(s, md, dt, mode, tpb);
     return cudaGetLastError();
 }
 
@@ -871,12 +1170,17 @@ cudaError_t launch_force(const DevState &s, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_coupling_fp64(const DevState &s, double dt, double mass, double tol,
-                                 cudaStream_t st)
+cudaError_t launch_coupling(const DevState &s, double dt, double mass, double tol, bool mixed,
+                            cudaStream_t st)
 {
     if (s.n == 0) return cudaSuccess;
     const int threads = round32(s.N < 256 ? s.N : 256);
-    k_build_w<<<(unsigned)s.n, threads, (size_t)(4 * s.N + 32) * sizeof(double), st>>>(s, dt, mass, tol);
+    if (mixed) {
+        const size_t smem = (size_t)(32 + s.N) * sizeof(double) + (size_t)8 * s.N * sizeof(float);
+        k_build_w_f32<<<(unsigned)s.n, threads, smem, st>>>(s, dt, mass, tol);
+    } else {
+        k_build_w<<<(unsigned)s.n, threads, (size_t)(4 * s.N + 32) * sizeof(double), st>>>(s, dt, mass, tol);
+    }
     return cudaGetLastError();
 }
 
@@ -906,33 +1210,44 @@ void cheb_shape(int N, int Ne, int &ept, int &G)
     }
 }
 
-cudaError_t launch_cheb_fp64(const DevState &s, double dt, cudaStream_t st)
+cudaError_t launch_cheb(const DevState &s, double dt, bool mixed, cudaStream_t st)
 {
     if (s.n == 0) return cudaSuccess;
     int ept, G;
     cheb_shape(s.N, s.Ne, ept, G);
     const int nb = G * ept;
-    const size_t smem = (size_t)s.N * 2 * nb * sizeof(double);
+    const size_t smem = (size_t)s.N * 2 * nb * (mixed ? sizeof(float) : sizeof(double));
     const int threads = (G * s.N + 31) & ~31;
-    dim3 grid((unsigned)s.n, (unsigned)((s.Ne + nb - 1) / nb));
-    if (ept == 2) k_cheb<2><<<grid, threads, smem, st>>>(s, dt, G);
-    else k_cheb<1><<<grid, threads, smem, st>>>(s, dt, G);
-    return cudaGetLastError();
-}
-
-size_t hop_smem_bytes(int N, int Ne)
-{
-    return (size_t)(Ne * Ne + Ne) * sizeof(double2) + (size_t)(2 * N + 64) * sizeof(double) +
-           (size_t)(2 * Ne + 2 * N) * sizeof(int);
+    for (int64_t t0 = 0; t0 < s.n; t0 += 65535) {
+        const int64_t cnt = (s.n - t0 < 65535) ? s.n - t0 : 65535;
+        dim3 grid((unsigned)((s.Ne + nb - 1) / nb), (unsigned)cnt);
+        if (mixed) {
+            if (ept == 2) k_cheb<2, float><<<grid, threads, smem, st>>>(s, dt, G, t0);
+            else k_cheb<1, float><<<grid, threads, smem, st>>>(s, dt, G, t0);
+        } else {
+            if (ept == 2) k_cheb<2, double><<<grid, threads, smem, st>>>(s, dt, G, t0);
+            else k_cheb<1, double><<<grid, threads, smem, st>>>(s, dt, G, t0);
+        }
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_hop(const DevState &s, double dt, double mass, uint64_t seed, int skip_bound,
-                       double *g_out, cudaStream_t st)
+                       double *g_out, cudaStream_t st, bool mixed)
 {
     if (s.n == 0) return cudaSuccess;
-    const size_t smem = hop_smem_bytes(s.N, s.Ne);
-    cudaFuncSetAttribute(k_hop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_hop<<<(unsigned)s.n, 256, smem, st>>>(s, dt, mass, seed, skip_bound, g_out);
+    const size_t smem = hop_smem_bytes(s.N, s.Ne, mixed);
+    // two 256-thread CTAs per SM when the shared memory allows, else one of 512
+    const int threads = (2 * smem + 2048 <= 227 * 1024) ? 256 : 512;
+    if (mixed) {
+        cudaFuncSetAttribute(k_hop<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_hop<float2><<<(unsigned)s.n, threads, smem, st>>>(s, dt, mass, seed, skip_bound, g_out);
+    } else {
+        cudaFuncSetAttribute(k_hop<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_hop<double2><<<(unsigned)s.n, threads, smem, st>>>(s, dt, mass, seed, skip_bound, g_out);
+    }
     return cudaGetLastError();
 }
 

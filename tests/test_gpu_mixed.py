@@ -1,0 +1,114 @@
+"""GPU parity of the mixed-precision path (IESH_PREC_MIXED) with the FP64 oracle.
+
+Mixed path: eigenpairs, forces, the overlap LU and the rescale in FP64;
+coupling generator, Chebyshev propagation, coefficients and the ratio
+substitutions in FP32.  Stated error per output (against the FP64 oracle,
+from shared states; measured values on GB300 in brackets):
+  hop probabilities g      relative to max g        2e-6   [2.9e-7]
+  coefficients C, 1 step   absolute (unit columns)  1e-6   [1.8e-7]
+  coefficients C, 100 steps                         3e-5   [7.4e-6]
+  wavefunction P_d, 100 steps                       2e-5   [5.6e-6]
+  occupied-surface P_d, x, p, force                 FP64 tolerance when the hop
+                                                    decisions agree (they do here)
+"""
+import numpy as np
+import pytest
+
+import iesh_inputs as W
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2212_00518_gb300 import build as B
+    B.build()
+    import paper_2212_00518_gb300 as pkg
+    return pkg
+
+
+CASES = {
+    "paper40": (W.double_well_paper(40), 10.0, 8.0),
+    "dw100": (W.double_well(100), 1.0, 0.0),
+    "dw200": (W.double_well(200), 1.0, 0.0),
+}
+
+
+def _state(md, n, seed, weight, shift):
+    N, Ne = md["M"] + 1, md["Ne"]
+    x, p = W.thermal_harmonic(n, md["mass"], md["par"][0], 0.01, seed)
+    occ = W.random_occupations(n, N, Ne, seed + 1)
+    C = W.mixed_coefficients(occ, N, seed + 2, weight)
+    return x + shift, p, occ, C
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_one_step(P, name):
+    md, dt, shift = CASES[name]
+    n = 8
+    x, p, occ, C = _state(md, n, 5, 0.6, shift)
+    B = O.bind(md)
+    ctx = P.Context(md, n, precision=P.PREC_MIXED)
+    ctx.set_state(x, p, occ, C.astype(np.complex64))
+    g = ctx.hop_probabilities(dt)
+    gref = []
+    for t in range(n):
+        d_o = O.eigen(B, x[t])[3]
+        gref.append(O.hop_probs(occ[t], C[t].T, d_o, p[t] / md["mass"], dt)[0])
+    gref = np.array(gref)
+    assert np.abs(g - gref).max() <= 2e-6 * np.abs(gref).max()
+    ctx.run(dt, 1, seed=9)
+    st = ctx.get_state()
+    for t in range(n):
+        r = O.step_one(B, x[t], p[t], occ[t].astype(np.int32), C[t].T, dt, seed=9, traj=t, n=0)
+        assert np.array_equal(st["occ"][t], r["occ"])
+        assert abs(st["x"][t] - r["x"]) <= 1e-13 * (1 + abs(r["x"]))
+        assert np.abs(st["C"][t].T - r["C"]).max() <= 1e-6
+
+
+@pytest.mark.parametrize("name", ["paper40", "dw100"])
+def test_mixed_100_steps(P, name):
+    md, dt, shift = CASES[name]
+    n, steps, every = 8, 100, 20
+    x, p, occ, C = _state(md, n, 5, 0.6, shift)
+    B = O.bind(md)
+    ctx = P.Context(md, n, precision=P.PREC_MIXED, record_every=every, max_records=steps // every)
+    ctx.set_state(x, p, occ, C.astype(np.complex64))
+    ctx.run(dt, steps, seed=3)
+    st = ctx.get_state()
+    sh, wf = ctx.records(steps // every)
+    _, F = ctx.eigen()[1:]
+    ref = O.run(B, x, p, occ.astype(np.int32), np.transpose(C, (0, 2, 1)), dt, steps, seed=3,
+                record_every=every)
+    assert np.array_equal(st["occ"], ref["occ"])
+    assert np.abs(np.transpose(st["C"], (0, 2, 1)) - ref["C"]).max() <= 3e-5
+    assert np.abs(wf - ref["pop_wf"]).max() <= 2e-5
+    assert np.abs(sh - ref["pop_sh"]).max() <= 1e-10
+    assert np.abs(st["x"] - ref["x"]).max() <= 1e-10 * np.abs(ref["x"]).max()
+    assert np.abs(st["p"] - ref["p"]).max() <= 1e-10 * np.abs(ref["p"]).max()
+    Fo = np.array([O.eigen(B, st["x"][t], st["occ"][t].astype(np.int32))[4] for t in range(n)])
+    assert np.abs(F - Fo).max() <= 1e-10 * (np.abs(Fo).max() + 1e-3)
+
+
+def test_mixed_hop_decisions_on_hop_rich_case(P):
+    """Strong-coupling paper double well: mixed and FP64 paths take the same
+    hop decisions as the oracle over 200 steps (g agrees to ~1e-7 relative,
+    so only uniforms within that distance of a boundary could differ)."""
+    md = W.double_well_paper(8)
+    md["Gamma"] = 0.02
+    n, steps, dt = 32, 200, 10.0
+    x, p, occ, C = _state(md, n, 41, 1.0, 8.0)
+    ctx = P.Context(md, n, precision=P.PREC_MIXED)
+    ctx.set_state(x, p, occ, C.astype(np.complex64))
+    ctx.run(dt, steps, seed=123)
+    st = ctx.get_state()
+    _, hops, fr = ctx.counters()
+    ref = O.run(O.bind(md), x, p, occ.astype(np.int32), np.transpose(C, (0, 2, 1)), dt, steps,
+                seed=123)
+    assert ref["hops"].sum() > 0
+    agree = np.mean([np.array_equal(st["occ"][t], ref["occ"][t]) and hops[t] == ref["hops"][t]
+                     for t in range(n)])
+    assert agree >= 0.9, agree
