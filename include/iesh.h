@@ -213,6 +213,44 @@ iesh_status iesh_hop_probabilities_noalloc(const iesh_model *model, int64_t n, c
                                            double *g, void *cuda_stream, char *err,
                                            size_t err_len);
 
+/* ---------------------------------------------------------------------
+ * Occupied-orbital energy of a two-orbital adsorbate, E_occ = sum of the Ne
+ * lowest eigenvalues of the one-electron Hamiltonian (the electronic part
+ * of the classical IESH Hamiltonian, Sec. II B, at ground-state occupation),
+ * and its Hellmann-Feynman gradients.  Orbital a = 0, 1 has level
+ * h_a = theta[a] + sum_al theta[2 + 6a + al] x[al] and couples to bath state
+ * k by vbar[a] sqrt(w_k) exp(-|x_a - R_a|^2 / (2 theta[14+a]^2)), x_a =
+ * (x[3a], x[3a+1], x[3a+2]); the bath is the split Gauss-Legendre
+ * discretisation of [band_lo, band_hi] at mu (Appendix A). */
+typedef struct iesh_eocc_ctx iesh_eocc_ctx;
+typedef struct {
+    int n_bath;        /* M (2..4096) */
+    int n_elec;        /* Ne, orbitals summed (1..min(M+1, 1024)) */
+    double band_lo, band_hi, mu;
+    double vbar[2];    /* coupling amplitudes */
+    double R[6];       /* coupling centres */
+} iesh_eocc_model;
+
+/* Create / destroy (the bath lives on the device in FP64 and FP32). */
+iesh_status iesh_eocc_create(iesh_eocc_ctx **out, const iesh_eocc_model *model, void *cuda_stream);
+iesh_status iesh_eocc_destroy(iesh_eocc_ctx *ctx);
+const char *iesh_eocc_last_error(const iesh_eocc_ctx *ctx);
+
+/* Forward for B geometries.  Device pointers; element type double for
+ * precision IESH_PREC_FP64, float for IESH_PREC_MIXED.  x[B][6],
+ * theta[16] -> E[B] and saved[B][4] = (S_0, S_1, T_0, T_1), S_a = sum_{i<Ne}
+ * Q_ai^2, T_a = sum_{i<Ne} Q_ai^2 (lam_i - h_a); status[B] (uint32,
+ * IESH_TRAJ_SECULAR_NONCONV).  Asynchronous on the context stream. */
+iesh_status iesh_eocc_forward(iesh_eocc_ctx *ctx, int64_t B, int precision, const void *x,
+                              const void *theta, void *E, void *saved, uint32_t *status);
+
+/* Backward: given gE[B] = dL/dE, writes dx[B][6] = gE dE/dx, the
+ * per-geometry parameter gradients dtheta_per[B][16] (caller workspace) and
+ * their sum dtheta[16] (fixed summation order).  Same element type rules. */
+iesh_status iesh_eocc_backward(iesh_eocc_ctx *ctx, int64_t B, int precision, const void *x,
+                               const void *theta, const void *saved, const void *gE, void *dx,
+                               void *dtheta_per, void *dtheta);
+
 /* Last error message of the context (never NULL). */
 const char *iesh_last_error(const iesh_ctx *ctx);
 

@@ -1,0 +1,184 @@
+// iesh_secular.cuh -- roots of the secular equation of an arrowhead matrix
+// (internal to the library), templated on the arithmetic type.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "iesh_common.cuh"
+
+namespace iesh {
+
+template <class R>
+struct Roundoff;
+template <>
+struct Roundoff<double> {
+    static constexpr double u = 1.1102230246251565e-16;  // 2^-53
+    static constexpr double tiny = 1e-300;
+};
+template <>
+struct Roundoff<float> {
+    static constexpr float u = 5.9604645e-08f;  // 2^-24
+    static constexpr float tiny = 1e-37f;
+};
+
+
+// ============================================================= eigenpairs
+// The one-electron Hamiltonian of Sec. II B is an arrowhead matrix:
+// diag(h, eps_1..eps_M) bordered by z_k = V_k(x).  Its eigenvalues are the
+// roots of g(lam) = lam - h - sum_k z_k^2 / (lam - eps_k), one in each gap
+// of the sorted poles, and the eigenvector of root lam has impurity
+// component q0 = 1 / sqrt(g'(lam)) (chosen > 0) and bath components
+// z_k q0 / (lam - eps_k).  Each root is found in the shifted variable
+// tau = lam - eps_o relative to its nearer pole o, so lam - eps_k =
+// (eps_o - eps_k) + tau keeps full relative accuracy.
+template <class R>
+struct Sec {
+    R g, gp, gp_rest, sabs;
+};
+
+template <class R>
+__device__ __forceinline__ Sec<R> sec_eval(int M, const R *__restrict__ eps, const R *__restrict__ z2,
+                                           int o, R tau, R eomh)
+{
+    const R eo = eps[o];
+    R s1 = 0, s2 = 0, sa = 0;
+#pragma unroll 4
+    for (int k = 0; k < M; ++k) {
+        const R r = R(1) / ((eo - eps[k]) + tau);
+        const R q = z2[k] * r;
+        if (k != o) {
+            s1 += q;
+            s2 = fma(q, r, s2);
+            sa += fabs(q);
+        }
+    }
+    const R qo = z2[o] / tau;
+    Sec<R> e;
+    e.g = (eomh + tau) - s1 - qo;
+    e.gp_rest = R(1) + s2;
+    e.gp = e.gp_rest + qo / tau;
+    e.sabs = sa + fabs(qo) + fabs(eomh) + fabs(tau);
+    return e;
+}
+
+// Fixed-weight iteration for one root in the shifted variable tau about the
+// origin pole o: the origin pole is kept exactly and the rest of g is
+// modelled by one more pole at tau = +D (kind 0) or -D (kind 1), or by a
+// linear term for the two outermost roots (kind 2: below all poles, kind 3:
+// above), matched in value and slope; each model root is safeguarded by the
+// bracket [lo, hi] of sign changes.  On return e is evaluated at tau.
+template <class R>
+__device__ bool sec_iterate(int M, const R *__restrict__ eps, const R *__restrict__ z2, R h, int o,
+                            int kind, R D, R &lo, R &hi, R &tau, Sec<R> &e, bool have)
+{
+    const R u = Roundoff<R>::u;
+    const R eomh = eps[o] - h;
+    const R s = z2[o];
+    for (int it = 0; it < 80; ++it) {
+        if (!have) e = sec_eval<R>(M, eps, z2, o, tau, eomh);
+        have = false;
+        if (fabs(e.g) <= R(8) * u * e.sabs) return true;
+        if (e.g < R(0)) lo = tau;
+        else hi = tau;
+        R tn;
+        if (kind == 0) {
+            const R tp = tau - D;
+            const R t = e.gp_rest * tp * tp;
+            const R c = e.g + s / tau + t / tp;
+            const R B = c * D + s + t;
+            tn = R(2) * s * D / (B + sqrt(fmax(B * B - R(4) * c * s * D, R(0))));
+        } else if (kind == 1) {
+            const R tp = tau + D;
+            const R t = e.gp_rest * tp * tp;
+            const R c = -(e.g + s / tau + t / tp);
+            const R B = c * D + s + t;
+            tn = -R(2) * s * D / (B + sqrt(fmax(B * B - R(4) * c * s * D, R(0))));
+        } else {
+            const R ee = e.gp_rest;
+            const R c = e.g - ee * tau + s / tau;
+            const R sq = sqrt(fmax(c * c + R(4) * ee * s, R(0)));
+            if (kind == 2) tn = (c >= R(0)) ? (-c - sq) / (R(2) * ee) : -R(2) * s / (sq - c);
+            else tn = (c <= R(0)) ? (sq - c) / (R(2) * ee) : R(2) * s / (c + sq);
+        }
+        if (!(tn > lo && tn < hi)) tn = R(0.5) * (lo + hi);
+        const bool tiny = fabs(tn - tau) <= R(2) * u * fabs(tn);
+        tau = tn;
+        if (tiny) {
+            e = sec_eval<R>(M, eps, z2, o, tau, eomh);
+            return true;
+        }
+    }
+    e = sec_eval<R>(M, eps, z2, o, tau, eomh);
+    return false;
+}
+
+// Root r (0..M) of the secular equation, lam and q0 = 1/sqrt(g'(lam)).
+// Cold start: the sign of g at the middle of the pole gap picks the nearer
+// pole as origin and the half-gap as bracket.  Warm start (previous root
+// `guess`, which lies in the same gap): origin = pole nearer the guess,
+// bracket = the whole gap, started at the guess; if the root ends in the
+// far half of the gap it is refined once more about the other pole.
+template <class R>
+__device__ void secular_root(int r, int M, const R *__restrict__ eps, const R *__restrict__ z2, R h,
+                             R Z2, bool warm, R guess, R &lam, R &q0, uint32_t &st)
+{
+    int o, kind;
+    R lo, hi, D = 0, tau;
+    Sec<R> e;
+    bool have = false, conv;
+    if (r > 0 && r < M) {
+        const int L = r - 1;
+        D = eps[r] - eps[L];
+        if (warm && guess > eps[L] && guess < eps[r]) {
+            if (guess - eps[L] <= eps[r] - guess) {
+                o = L; kind = 0; lo = 0; hi = D; tau = guess - eps[L];
+            } else {
+                o = r; kind = 1; lo = -D; hi = 0; tau = guess - eps[r];
+            }
+            conv = sec_iterate<R>(M, eps, z2, h, o, kind, D, lo, hi, tau, e, false);
+            if (kind == 0 && tau > R(0.5) * D) {
+                o = r; kind = 1; lo = fmin(lo - D, -R(0.5) * D); hi = 0; tau = tau - D;
+                conv = sec_iterate<R>(M, eps, z2, h, o, kind, D, lo, hi, tau, e, false);
+            } else if (kind == 1 && tau < -R(0.5) * D) {
+                o = L; kind = 0; lo = 0; hi = fmax(hi + D, R(0.5) * D); tau = tau + D;
+                conv = sec_iterate<R>(M, eps, z2, h, o, kind, D, lo, hi, tau, e, false);
+            }
+        } else {
+            const Sec<R> em = sec_eval<R>(M, eps, z2, L, R(0.5) * D, eps[L] - h);
+            if (em.g >= R(0)) {
+                o = L; kind = 0; lo = 0; hi = R(0.5) * D; tau = R(0.5) * D; e = em; have = true;
+            } else {
+                o = r; kind = 1; lo = -R(0.5) * D; hi = 0; tau = -R(0.5) * D;
+            }
+            conv = sec_iterate<R>(M, eps, z2, h, o, kind, D, lo, hi, tau, e, have);
+        }
+    } else {
+        if (r == 0) {
+            o = 0; kind = 2;
+            const R t = h - eps[0];
+            const R lb = R(0.5) * ((h + eps[0]) - sqrt(t * t + R(4) * Z2));
+            lo = (lb - eps[0]) * (R(1) + R(64) * Roundoff<R>::u) - Roundoff<R>::tiny;
+            hi = 0;
+            tau = R(0.5) * lo;
+        } else {
+            o = M - 1; kind = 3;
+            const R t = h - eps[M - 1];
+            const R ub = R(0.5) * ((h + eps[M - 1]) + sqrt(t * t + R(4) * Z2));
+            lo = 0;
+            hi = (ub - eps[M - 1]) * (R(1) + R(64) * Roundoff<R>::u) + Roundoff<R>::tiny;
+            tau = R(0.5) * hi;
+        }
+        if (warm) {
+            const R tg = guess - eps[o];
+            if (tg > lo && tg < hi) tau = tg;
+        }
+        conv = sec_iterate<R>(M, eps, z2, h, o, kind, D, lo, hi, tau, e, false);
+    }
+    if (!conv) st |= ST_SECULAR;
+    lam = eps[o] + tau;
+    q0 = R(1) / sqrt(e.gp);
+}
+
+
+}  // namespace iesh

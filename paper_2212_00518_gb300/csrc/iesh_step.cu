@@ -14,165 +14,11 @@
 //               momentum rescale (Sec. II B).
 #include "iesh_common.cuh"
 #include "iesh_kernels.h"
+#include "iesh_secular.cuh"
 
 namespace iesh {
 
 constexpr double kU = 1.1102230246251565e-16;  // unit roundoff 2^-53
-
-// ============================================================= eigenpairs
-// The one-electron Hamiltonian of Sec. II B is an arrowhead matrix:
-// diag(h, eps_1..eps_M) bordered by z_k = V_k(x).  Its eigenvalues are the
-// roots of g(lam) = lam - h - sum_k z_k^2 / (lam - eps_k), one in each gap
-// of the sorted poles, and the eigenvector of root lam has impurity
-// component q0 = 1 / sqrt(g'(lam)) (chosen > 0) and bath components
-// z_k q0 / (lam - eps_k).  Each root is found in the shifted variable
-// tau = lam - eps_o relative to its nearer pole o, so lam - eps_k =
-// (eps_o - eps_k) + tau keeps full relative accuracy.
-struct Sec {
-    double g, gp, gp_rest, sabs;
-};
-
-__device__ __forceinline__ Sec sec_eval(int M, const double *__restrict__ eps,
-                                        const double *__restrict__ z2, int o, double tau,
-                                        double eomh)
-{
-    const double eo = eps[o];
-    double s1 = 0.0, s2 = 0.0, sa = 0.0;
-#pragma unroll 4
-    for (int k = 0; k < M; ++k) {
-        const double r = 1.0 / ((eo - eps[k]) + tau);
-        const double q = z2[k] * r;
-        if (k != o) {
-            s1 += q;
-            s2 = fma(q, r, s2);
-            sa += fabs(q);
-        }
-    }
-    const double qo = z2[o] / tau;
-    Sec e;
-    e.g = (eomh + tau) - s1 - qo;
-    e.gp_rest = 1.0 + s2;
-    e.gp = e.gp_rest + qo / tau;
-    e.sabs = sa + fabs(qo) + fabs(eomh) + fabs(tau);
-    return e;
-}
-
-// Fixed-weight iteration for one root in the shifted variable tau about the
-// origin pole o: the origin pole is kept exactly and the rest of g is
-// modelled by one more pole at tau = +D (kind 0) or -D (kind 1), or by a
-// linear term for the two outermost roots (kind 2: below all poles, kind 3:
-// above), matched in value and slope; each model root is safeguarded by the
-// bracket [lo, hi] of sign changes.  On return e is evaluated at tau.
-__device__ bool sec_iterate(int M, const double *__restrict__ eps, const double *__restrict__ z2,
-                            double h, int o, int kind, double D, double &lo, double &hi,
-                            double &tau, Sec &e, bool have)
-{
-    const double eomh = eps[o] - h;
-    const double s = z2[o];
-    for (int it = 0; it < 80; ++it) {
-        if (!have) e = sec_eval(M, eps, z2, o, tau, eomh);
-        have = false;
-        if (fabs(e.g) <= 8.0 * kU * e.sabs) return true;
-        if (e.g < 0.0) lo = tau;
-        else hi = tau;
-        double tn;
-        if (kind == 0) {
-            const double tp = tau - D;
-            const double t = e.gp_rest * tp * tp;
-            const double c = e.g + s / tau + t / tp;
-            const double B = c * D + s + t;
-            tn = 2.0 * s * D / (B + sqrt(fmax(B * B - 4.0 * c * s * D, 0.0)));
-        } else if (kind == 1) {
-            const double tp = tau + D;
-            const double t = e.gp_rest * tp * tp;
-            const double c = -(e.g + s / tau + t / tp);
-            const double B = c * D + s + t;
-            tn = -2.0 * s * D / (B + sqrt(fmax(B * B - 4.0 * c * s * D, 0.0)));
-        } else {
-            const double ee = e.gp_rest;
-            const double c = e.g - ee * tau + s / tau;
-            const double sq = sqrt(fmax(c * c + 4.0 * ee * s, 0.0));
-            if (kind == 2) tn = (c >= 0.0) ? (-c - sq) / (2.0 * ee) : -2.0 * s / (sq - c);
-            else tn = (c <= 0.0) ? (sq - c) / (2.0 * ee) : 2.0 * s / (c + sq);
-        }
-        if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
-        const bool tiny = fabs(tn - tau) <= 2.0 * kU * fabs(tn);
-        tau = tn;
-        if (tiny) {
-            e = sec_eval(M, eps, z2, o, tau, eomh);
-            return true;
-        }
-    }
-    e = sec_eval(M, eps, z2, o, tau, eomh);
-    return false;
-}
-
-// Root r (0..M) of the secular equation, lam and q0 = 1/sqrt(g'(lam)).
-// Cold start: the sign of g at the middle of the pole gap picks the nearer
-// pole as origin and the half-gap as bracket.  Warm start (previous root
-// `guess`, which lies in the same gap): origin = pole nearer the guess,
-// bracket = the whole gap, started at the guess; if the root ends in the
-// far half of the gap it is refined once more about the other pole.
-__device__ void secular_root(int r, int M, const double *__restrict__ eps,
-                             const double *__restrict__ z2, double h, double Z2, bool warm,
-                             double guess, double &lam, double &q0, uint32_t &st)
-{
-    int o, kind;
-    double lo, hi, D = 0.0, tau;
-    Sec e;
-    bool have = false, conv;
-    if (r > 0 && r < M) {
-        const int L = r - 1;
-        D = eps[r] - eps[L];
-        if (warm && guess > eps[L] && guess < eps[r]) {
-            if (guess - eps[L] <= eps[r] - guess) {
-                o = L; kind = 0; lo = 0.0; hi = D; tau = guess - eps[L];
-            } else {
-                o = r; kind = 1; lo = -D; hi = 0.0; tau = guess - eps[r];
-            }
-            conv = sec_iterate(M, eps, z2, h, o, kind, D, lo, hi, tau, e, false);
-            if (kind == 0 && tau > 0.5 * D) {
-                o = r; kind = 1; lo = fmin(lo - D, -0.5 * D); hi = 0.0; tau = tau - D;
-                conv = sec_iterate(M, eps, z2, h, o, kind, D, lo, hi, tau, e, false);
-            } else if (kind == 1 && tau < -0.5 * D) {
-                o = L; kind = 0; lo = 0.0; hi = fmax(hi + D, 0.5 * D); tau = tau + D;
-                conv = sec_iterate(M, eps, z2, h, o, kind, D, lo, hi, tau, e, false);
-            }
-        } else {
-            const Sec em = sec_eval(M, eps, z2, L, 0.5 * D, eps[L] - h);
-            if (em.g >= 0.0) {
-                o = L; kind = 0; lo = 0.0; hi = 0.5 * D; tau = 0.5 * D; e = em; have = true;
-            } else {
-                o = r; kind = 1; lo = -0.5 * D; hi = 0.0; tau = -0.5 * D;
-            }
-            conv = sec_iterate(M, eps, z2, h, o, kind, D, lo, hi, tau, e, have);
-        }
-    } else {
-        if (r == 0) {
-            o = 0; kind = 2;
-            const double t = h - eps[0];
-            const double lb = 0.5 * ((h + eps[0]) - sqrt(t * t + 4.0 * Z2));
-            lo = (lb - eps[0]) * (1.0 + 1e-12) - 1e-300;
-            hi = 0.0;
-            tau = 0.5 * lo;
-        } else {
-            o = M - 1; kind = 3;
-            const double t = h - eps[M - 1];
-            const double ub = 0.5 * ((h + eps[M - 1]) + sqrt(t * t + 4.0 * Z2));
-            lo = 0.0;
-            hi = (ub - eps[M - 1]) * (1.0 + 1e-12) + 1e-300;
-            tau = 0.5 * hi;
-        }
-        if (warm) {
-            const double tg = guess - eps[o];
-            if (tg > lo && tg < hi) tau = tg;
-        }
-        conv = sec_iterate(M, eps, z2, h, o, kind, D, lo, hi, tau, e, false);
-    }
-    if (!conv) st |= ST_SECULAR;
-    lam = eps[o] + tau;
-    q0 = 1.0 / sqrt(e.gp);
-}
 
 // Trajectories per CTA of k_eigen: fill warps with one thread per root.
 int eigen_tpb(int N)
@@ -242,7 +88,7 @@ __global__ void __launch_bounds__(512, 1) k_eigen(DevState s, ModelDev md, doubl
         const double Z2 = misc[0];
         double l, q;
         if (Z2 > 0.0) {
-            secular_root(r, M, eps_s, z2_s, mv.h, Z2, mode == 1, lam_s[r], l, q, st);
+            secular_root<double>(r, M, eps_s, z2_s, mv.h, Z2, mode == 1, lam_s[r], l, q, st);
         } else {
             // no coupling: the eigenvalues are h and the bath energies
             int pos = 0;

@@ -46,6 +46,12 @@ class _Model(ctypes.Structure):
                 ("lead_nlo", ctypes.c_int * 2), ("lead_frac", ctypes.c_double * 2)]
 
 
+class _EoccModel(ctypes.Structure):
+    _fields_ = [("n_bath", ctypes.c_int), ("n_elec", ctypes.c_int), ("band_lo", ctypes.c_double),
+                ("band_hi", ctypes.c_double), ("mu", ctypes.c_double),
+                ("vbar", ctypes.c_double * 2), ("R", ctypes.c_double * 6)]
+
+
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("skip_bound", ctypes.c_int),
                 ("record_every", ctypes.c_int), ("max_records", ctypes.c_int),
@@ -55,8 +61,9 @@ class _Options(ctypes.Structure):
 EXPORTS = ["iesh_create", "iesh_destroy", "iesh_bath", "iesh_init_state", "iesh_set_state",
            "iesh_get_state", "iesh_run", "iesh_get_eigen", "iesh_hop_probabilities",
            "iesh_get_counters", "iesh_get_records", "iesh_get_propagator_terms", "iesh_profile",
-           "iesh_profile_read", "iesh_hop_probabilities_noalloc", "iesh_last_error",
-           "iesh_status_string"]
+           "iesh_profile_read", "iesh_hop_probabilities_noalloc", "iesh_eocc_create",
+           "iesh_eocc_destroy", "iesh_eocc_last_error", "iesh_eocc_forward",
+           "iesh_eocc_backward", "iesh_last_error", "iesh_status_string"]
 KERNEL_CLASSES = ["eigen", "coupling", "propagate", "hop", "other"]
 
 _lib = None
@@ -90,13 +97,20 @@ def load(path=LIB_PATH):
     L.iesh_hop_probabilities_noalloc.argtypes = [ctypes.POINTER(_Model), ctypes.c_int64, _vp, _vp,
                                                  _vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp,
                                                  ctypes.c_char_p, ctypes.c_size_t]
+    L.iesh_eocc_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_EoccModel), _vp]
+    L.iesh_eocc_destroy.argtypes = [_vp]
+    L.iesh_eocc_last_error.argtypes = [_vp]
+    L.iesh_eocc_last_error.restype = ctypes.c_char_p
+    L.iesh_eocc_forward.argtypes = [_vp, ctypes.c_int64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
+    L.iesh_eocc_backward.argtypes = [_vp, ctypes.c_int64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp,
+                                     _vp, _vp]
     L.iesh_last_error.argtypes = [_vp]
     L.iesh_last_error.restype = ctypes.c_char_p
     L.iesh_status_string.argtypes = [ctypes.c_int]
     L.iesh_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype if name in (
-            "iesh_last_error", "iesh_status_string") else ctypes.c_int
+            "iesh_last_error", "iesh_status_string", "iesh_eocc_last_error") else ctypes.c_int
     _lib = L
     return L
 
