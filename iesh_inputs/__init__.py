@@ -167,3 +167,29 @@ def eocc_workload(M=300, B=65536, seed=5, Ne=None, band=(-0.5, 0.5)):
     x = rng.normal(0.0, 0.3, (B, 6))
     return dict(M=int(M), Ne=int(M // 2 + 1 if Ne is None else Ne), band=tuple(band), Vbar=Vbar,
                 R=R, theta=theta, x=x)
+
+
+# ----------------------------------------------------- uneven scattering batch
+def scattering_batch(n=16384, seed=4, M_choices=(50, 100, 200), biases=(0.0, 0.05, 0.1),
+                     e_range_ev=(0.2, 1.5), z0_ang=5.0, Gamma_ev=1.0, band_ev=64.0):
+    """Scattering trajectories of the Morse + image-charge model with uneven
+    bath sizes: M drawn uniformly from M_choices (Ne = M/2), one third of the
+    trajectories at each bias, incidence energy uniform in e_range_ev,
+    starting at z0 moving towards the surface.
+
+    Returns a list of groups dict(model, idx, x, p, e_inc), one per (M, bias)."""
+    rng = np.random.default_rng(seed)
+    Ms = rng.choice(np.asarray(M_choices), size=n)
+    bias = np.asarray(biases)[np.arange(n) % len(biases)]
+    e_inc = rng.uniform(ev(e_range_ev[0]), ev(e_range_ev[1]), n)
+    groups = []
+    for M in M_choices:
+        for V in biases:
+            idx = np.nonzero((Ms == M) & (bias == V))[0]
+            if idx.size == 0:
+                continue
+            md = morse_image(int(M), Gamma_ev=Gamma_ev, band_ev=band_ev, bias=float(V))
+            x = np.full(idx.size, angstrom(z0_ang))
+            p = -np.sqrt(2.0 * md["mass"] * e_inc[idx])
+            groups.append(dict(model=md, idx=idx, x=x, p=p, e_inc=e_inc[idx]))
+    return groups

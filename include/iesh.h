@@ -106,6 +106,9 @@ typedef struct {
     int record_every;  /* record impurity populations every k steps (0: off) */
     int max_records;   /* capacity of the record buffer per trajectory */
     double z_done;     /* a trajectory is finished when x > z_done (0: never) */
+    int compact_every; /* > 0: kernels visit only live trajectories (no IESH_TRAJ_DONE or
+                          IESH_TRAJ_NAN) through a device work list, compacted in place
+                          every compact_every steps of iesh_run (0: visit all) */
 } iesh_options;
 
 /* Create a context for up to max_traj trajectories of `model`.  Discretises
@@ -165,6 +168,19 @@ iesh_status iesh_get_counters(iesh_ctx *ctx, int64_t *nstep, int32_t *hops, int3
  * value sum_{i in s} q0_i^2 and the wavefunction value
  * sum_e |sum_i q0_i C_ie|^2.  *n_records receives the number recorded. */
 iesh_status iesh_get_records(iesh_ctx *ctx, double *pop_sh, double *pop_wf, int64_t *n_records);
+
+/* Number of live trajectories in the device work list (n_traj when the work
+ * list is off).  Synchronises the context stream. */
+iesh_status iesh_get_live(iesh_ctx *ctx, int64_t *n_live);
+
+/* Kernel shapes.  cheb_ept (1 or 2) electrons per thread and cheb_G column
+ * groups per CTA of the propagator (cheb_G * N <= 1024), hop_threads (256 or
+ * 512) threads of the hop kernel; 0 restores the built-in choice.  Results
+ * do not depend on the shapes except through floating-point summation order
+ * of the propagator (none: each output has a fixed order).  Used by the
+ * autotuner of the Python package. */
+iesh_status iesh_set_kernel_shape(iesh_ctx *ctx, int cheb_ept, int cheb_G, int hop_threads);
+iesh_status iesh_get_kernel_shape(iesh_ctx *ctx, int *cheb_ept, int *cheb_G, int *hop_threads);
 
 /* Chebyshev degree K[n] used by each trajectory's propagator in its last
  * step (the number of coupling-matrix products of that step). */

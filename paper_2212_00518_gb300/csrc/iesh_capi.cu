@@ -29,6 +29,8 @@ struct iesh_ctx {
     std::vector<void *> allocs;
     bool have_state = false;
     std::string err;
+    int32_t *live = nullptr, *n_live = nullptr;  // device work list
+    int64_t steps_since_init = 0;
     // kernel timing
     bool prof = false;
     struct Rec {
@@ -313,6 +315,7 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
     else if (opt->precision != IESH_PREC_FP64 && opt->precision != IESH_PREC_MIXED)
         st = fail(ctx, IESH_EINVAL, "unknown precision %d", opt->precision);
     else if (opt->record_every < 0 || opt->max_records < 0) st = fail(ctx, IESH_EINVAL, "negative record sizes");
+    else if (opt->compact_every < 0) st = fail(ctx, IESH_EINVAL, "negative compact_every");
     if (st != IESH_OK) {
         *out = ctx;  // let the caller read the message, then destroy
         return st;
@@ -354,6 +357,8 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
     A(d.status, T) A(d.nstep, T) A(d.hops, T) A(d.frus, T)
     A(d.scratch, T * (size_t)d.scratch_stride)
     A(d.cheb, T * kChebStride)
+    A(ctx->live, T)
+    A(ctx->n_live, 1)
     A(d.rec_sh, std::max<size_t>(1, T * d.max_records))
     A(d.rec_wf, std::max<size_t>(1, T * d.max_records))
     A(eps, (size_t)M) A(z0, (size_t)M)
@@ -363,6 +368,9 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
     d.eps = eps;
     d.z0 = z0;
     d.epsdiff = epsdiff;
+    d.live = (opt->compact_every > 0) ? ctx->live : nullptr;
+    d.n_live = ctx->n_live;
+    configure_hop_smem();
     {
         std::vector<float> ed((size_t)M * M);
         for (int a = 0; a < M; ++a)
@@ -396,6 +404,8 @@ iesh_status iesh_bath(iesh_ctx *ctx, double *eps, double *z0)
 static iesh_status reset_counters(iesh_ctx *ctx, int64_t n)
 {
     DevState &d = ctx->ds;
+    ctx->steps_since_init = 0;
+    CU(launch_live_init(n, ctx->live, ctx->n_live, ctx->stream));
     CU(cudaMemsetAsync(d.status, 0, n * sizeof(uint32_t), ctx->stream));
     CU(cudaMemsetAsync(d.nstep, 0, n * sizeof(int64_t), ctx->stream));
     CU(cudaMemsetAsync(d.hops, 0, n * sizeof(int32_t), ctx->stream));
@@ -552,7 +562,50 @@ iesh_status iesh_run(iesh_ctx *ctx, double dt, int64_t n_steps, uint64_t seed)
         CU(timed(ctx, IESH_K_HOP, [&] {
             return launch_hop(d, dt, ctx->model.mass, seed, ctx->opt.skip_bound, nullptr, ctx->stream, mx);
         }));
+        ++ctx->steps_since_init;
+        if (ctx->opt.compact_every > 0 && ctx->steps_since_init % ctx->opt.compact_every == 0)
+            CU(timed(ctx, IESH_K_OTHER,
+                     [&] { return launch_compact(d, ctx->live, ctx->n_live, ctx->stream); }));
     }
+    return IESH_OK;
+}
+
+iesh_status iesh_get_live(iesh_ctx *ctx, int64_t *n_live)
+{
+    if (!ctx || !n_live) return IESH_EINVAL;
+    if (ctx->opt.compact_every <= 0) {
+        *n_live = ctx->ds.n;
+        return IESH_OK;
+    }
+    int32_t v = 0;
+    CU(cudaMemcpyAsync(&v, ctx->n_live, sizeof v, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    *n_live = v;
+    return IESH_OK;
+}
+
+iesh_status iesh_set_kernel_shape(iesh_ctx *ctx, int cheb_ept, int cheb_G, int hop_threads)
+{
+    if (!ctx) return IESH_EINVAL;
+    if (cheb_ept < 0 || cheb_ept > 2 || cheb_G < 0 || (cheb_ept > 0) != (cheb_G > 0) ||
+        cheb_G * ctx->N > 1024)
+        return fail(ctx, IESH_EINVAL, "propagator shape (%d, %d) invalid for N=%d", cheb_ept, cheb_G, ctx->N);
+    if (hop_threads != 0 && hop_threads != 256 && hop_threads != 512)
+        return fail(ctx, IESH_EINVAL, "hop_threads must be 0, 256 or 512");
+    ctx->ds.cheb_ept = cheb_ept;
+    ctx->ds.cheb_G = cheb_G;
+    ctx->ds.hop_threads = hop_threads;
+    return IESH_OK;
+}
+
+iesh_status iesh_get_kernel_shape(iesh_ctx *ctx, int *cheb_ept, int *cheb_G, int *hop_threads)
+{
+    if (!ctx) return IESH_EINVAL;
+    int e = ctx->ds.cheb_ept, g = ctx->ds.cheb_G;
+    if (e == 0) cheb_shape(ctx->N, ctx->Ne, e, g);
+    if (cheb_ept) *cheb_ept = e;
+    if (cheb_G) *cheb_G = g;
+    if (hop_threads) *hop_threads = ctx->ds.hop_threads;
     return IESH_OK;
 }
 

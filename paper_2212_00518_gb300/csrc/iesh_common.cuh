@@ -48,7 +48,22 @@ struct DevState {
     double z_done;
     const double *eps, *z0;    // bath [M]: energies and sqrt(Gamma/2pi) sqrt(w_k)
     const float *epsdiff;      // [M][M] eps_a - eps_b rounded to FP32 (mixed path)
+    // work list: when live != nullptr the step kernels visit trajectory
+    // live[w] for work item w < *n_live (compacted on the device)
+    const int32_t *live;
+    const int32_t *n_live;
+    // kernel shapes (0 = built-in choice): propagator electrons per thread
+    // and column groups per CTA, threads of the hop kernel
+    int cheb_ept, cheb_G, hop_threads;
 };
+
+// Trajectory visited by work item w, or -1 when w is past the batch or the
+// live count.
+__device__ __forceinline__ int64_t traj_of(const DevState &s, int64_t w)
+{
+    if (s.live) return (w < (int64_t)*s.n_live) ? (int64_t)s.live[w] : -1;
+    return (w < s.n) ? w : -1;
+}
 
 // ---------------------------------------------------------------- models
 // U0, dU0/dx, h = U1 - U0, dh/dx, coupling factor f and df/dx at x.

@@ -20,5 +20,9 @@ cudaError_t launch_init_nuclear(const DevState &s, double mass, uint64_t seed, d
                                 int wigner, double omega, double x_eq, cudaStream_t st);
 cudaError_t launch_sample_occ(const DevState &s, uint64_t seed, double kT, cudaStream_t st);
 cudaError_t launch_unit_coeffs(const DevState &s, bool fp32, cudaStream_t st);
+cudaError_t launch_compact(const DevState &s, int32_t *live, int32_t *n_live, cudaStream_t st);
+cudaError_t launch_live_init(int64_t n, int32_t *live, int32_t *n_live, cudaStream_t st);
+void configure_hop_smem();
+void cheb_shape(int N, int Ne, int &ept, int &G);
 
 }  // namespace iesh

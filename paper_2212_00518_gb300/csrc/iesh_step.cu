@@ -45,8 +45,8 @@ __global__ void __launch_bounds__(512, 1) k_eigen(DevState s, ModelDev md, doubl
     const int N = s.N, M = s.M, Ne = s.Ne;
     const int slot = threadIdx.x / N;
     const int r = threadIdx.x - slot * N;
-    const int64_t t = (int64_t)blockIdx.x * tpb + slot;
-    const bool act = slot < tpb && t < s.n && !(s.status[t] & ST_DONE);
+    const int64_t t = slot < tpb ? traj_of(s, (int64_t)blockIdx.x * tpb + slot) : -1;
+    const bool act = t >= 0 && !(s.status[t] & ST_DONE);
     double *eps_s = sh;                                  // [M], shared by the slots
     const int per = M + 2 * N + 2;
     double *z2_s = eps_s + M + (slot < tpb ? slot : 0) * per;  // [M]
@@ -211,8 +211,8 @@ __device__ void cheb_setup(const DevState &s, int64_t t, double lo, double hi, d
 __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double mass, double tol)
 {
     extern __shared__ double sh[];
-    const int64_t t = blockIdx.x;
-    if (t >= s.n || (s.status[t] & ST_DONE)) return;
+    const int64_t t = traj_of(s, blockIdx.x);
+    if (t < 0 || (s.status[t] & ST_DONE)) return;
     const int N = s.N;
     double *l0 = sh, *q00 = l0 + N, *l1 = q00 + N, *q01 = l1 + N, *red = q01 + N;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -255,8 +255,8 @@ __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double m
 __global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, double mass, double tol)
 {
     extern __shared__ double sh[];
-    const int64_t t = blockIdx.x;
-    if (t >= s.n || (s.status[t] & ST_DONE)) return;
+    const int64_t t = traj_of(s, blockIdx.x);
+    if (t < 0 || (s.status[t] & ST_DONE)) return;
     const int N = s.N, M = s.M;
     double *red = sh;                                  // [32]
     double *Lsum = red + 32;                           // [N] dt (lam0 + lam1) / 2
@@ -345,8 +345,8 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
     RT *tk = reinterpret_cast<RT *>(cheb_smem);  // [N][2 G EPT]
     // the electron blocks of one trajectory are adjacent in launch order, so
     // they run together and share W through L2
-    const int64_t t = t_base + blockIdx.y;
-    if (t >= s.n || (s.status[t] & ST_DONE)) return;
+    const int64_t t = traj_of(s, t_base + blockIdx.y);
+    if (t < 0 || (s.status[t] & ST_DONE)) return;
     const int N = s.N, Ne = s.Ne;
     const int NB = G * EPT, W2 = 2 * NB;
     const int g = threadIdx.x / N;
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
         tp[2 * e] = v.x;
         tp[2 * e + 1] = v.y;
         acc[2 * e] = J0 * v.x;
-        acc[2 * e + 1] = J0 * v.y;
+        acc[2 * e + 1] = J0 * v.y;  // single products: no contraction possible
         if (act) {
             myrow[2 * e] = v.x;
             myrow[2 * e + 1] = v.y;
@@ -406,31 +406,32 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
             const int ph = (k + 1) & 3;  // (-i)^(k+1)
 #pragma unroll
             for (int e = 0; e < EPT; ++e) {
-                // (X t)_j = ((L_j - c) t_j - i (W t)_j) / rho and (W t)_j = -y
-                const RT xr = (Lc * own[2 * e] - y[2 * e + 1]) * inv_rho;
-                const RT xi = (Lc * own[2 * e + 1] + y[2 * e]) * inv_rho;
+                // (X t)_j = ((L_j - c) t_j - i (W t)_j) / rho and (W t)_j = -y.
+                // Explicit FMAs fix the rounding independently of the CTA shape.
+                const RT xr = fma(Lc, own[2 * e], -y[2 * e + 1]) * inv_rho;
+                const RT xi = fma(Lc, own[2 * e + 1], y[2 * e]) * inv_rho;
                 RT nr, ni;
                 if (k == 0) {
                     nr = xr;
                     ni = xi;
                 } else {
-                    nr = (RT)2 * xr - tp[2 * e];
-                    ni = (RT)2 * xi - tp[2 * e + 1];
+                    nr = fma((RT)2, xr, -tp[2 * e]);
+                    ni = fma((RT)2, xi, -tp[2 * e + 1]);
                 }
                 tp[2 * e] = own[2 * e];
                 tp[2 * e + 1] = own[2 * e + 1];
                 if (ph == 0) {
-                    acc[2 * e] += cj * nr;
-                    acc[2 * e + 1] += cj * ni;
+                    acc[2 * e] = fma(cj, nr, acc[2 * e]);
+                    acc[2 * e + 1] = fma(cj, ni, acc[2 * e + 1]);
                 } else if (ph == 1) {
-                    acc[2 * e] += cj * ni;
-                    acc[2 * e + 1] -= cj * nr;
+                    acc[2 * e] = fma(cj, ni, acc[2 * e]);
+                    acc[2 * e + 1] = fma(-cj, nr, acc[2 * e + 1]);
                 } else if (ph == 2) {
-                    acc[2 * e] -= cj * nr;
-                    acc[2 * e + 1] -= cj * ni;
+                    acc[2 * e] = fma(-cj, nr, acc[2 * e]);
+                    acc[2 * e + 1] = fma(-cj, ni, acc[2 * e + 1]);
                 } else {
-                    acc[2 * e] -= cj * ni;
-                    acc[2 * e + 1] += cj * nr;
+                    acc[2 * e] = fma(-cj, ni, acc[2 * e]);
+                    acc[2 * e + 1] = fma(cj, nr, acc[2 * e + 1]);
                 }
                 myrow[2 * e] = nr;
                 myrow[2 * e + 1] = ni;
@@ -447,8 +448,8 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
             if (e0 + e < Ne) {
                 const RT ar = acc[2 * e], ai = acc[2 * e + 1];
                 CT out;
-                out.x = cc * ar + sc * ai;
-                out.y = cc * ai - sc * ar;
+                out.x = fma(cc, ar, sc * ai);
+                out.y = fma(cc, ai, -(sc * ar));
                 C[(int64_t)(e0 + e) * N + j] = out;
             }
         }
@@ -520,8 +521,8 @@ __global__ void __launch_bounds__(512, 1) k_hop(DevState s, double dt, double ma
 {
     constexpr bool kF32 = sizeof(CT) == sizeof(float2);
     extern __shared__ __align__(16) unsigned char hop_smem[];
-    const int64_t t = blockIdx.x;
-    if (t >= s.n || (s.status[t] & ST_DONE)) return;
+    const int64_t t = traj_of(s, blockIdx.x);
+    if (t < 0 || (s.status[t] & ST_DONE)) return;
     const int N = s.N, Ne = s.Ne, nu = N - Ne;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const size_t abytes = hop_region_bytes(N, Ne, kF32);
@@ -915,6 +916,65 @@ __global__ void __launch_bounds__(512, 1) k_hop(DevState s, double dt, double ma
     }
 }
 
+// ========================================================== work list
+// Stable in-place compaction of the live list: keep the trajectories that
+// are neither finished nor non-finite.  One CTA of 1024 threads; the order
+// of the kept entries is preserved, so results do not depend on when the
+// list is compacted.
+__global__ void __launch_bounds__(1024) k_compact(const uint32_t *__restrict__ status,
+                                                  int32_t *__restrict__ live,
+                                                  int32_t *__restrict__ n_live)
+{
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t s_base;
+    const int n = *n_live;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) s_base = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        int32_t v = -1;
+        int keep = 0;
+        if (i < n) {
+            v = live[i];
+            keep = !(status[v] & (ST_DONE | ST_NAN));
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) wsum[warp] = __popc(m);
+        __syncthreads();
+        int off = s_base, tot = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < warp) off += wsum[w];
+            tot += wsum[w];
+        }
+        off += __popc(m & ((1u << lane) - 1u));
+        __syncthreads();
+        if (keep) live[off] = v;  // off <= i: earlier entries were read already
+        if (threadIdx.x == 0) s_base += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_live = s_base;
+}
+
+__global__ void k_live_init(int64_t n, int32_t *__restrict__ live, int32_t *__restrict__ n_live)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) live[i] = (int32_t)i;
+    if (i == 0) *n_live = (int32_t)n;
+}
+
+cudaError_t launch_compact(const DevState &s, int32_t *live, int32_t *n_live, cudaStream_t st)
+{
+    k_compact<<<1, 1024, 0, st>>>(s.status, live, n_live);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_live_init(int64_t n, int32_t *live, int32_t *n_live, cudaStream_t st)
+{
+    k_live_init<<<(unsigned)((n + 255) / 256 + 1), 256, 0, st>>>(n, live, n_live);
+    return cudaGetLastError();
+}
+
 // ================================================================= init
 __global__ void k_init_nuclear(DevState s, double mass, uint64_t seed, double kT, int wigner,
                                double omega, double x_eq)
@@ -1061,6 +1121,10 @@ cudaError_t launch_cheb(const DevState &s, double dt, bool mixed, cudaStream_t s
     if (s.n == 0) return cudaSuccess;
     int ept, G;
     cheb_shape(s.N, s.Ne, ept, G);
+    if (s.cheb_ept > 0 && s.cheb_G > 0) {
+        ept = s.cheb_ept;
+        G = s.cheb_G;
+    }
     const int nb = G * ept;
     const size_t smem = (size_t)s.N * 2 * nb * (mixed ? sizeof(float) : sizeof(double));
     const int threads = (G * s.N + 31) & ~31;
@@ -1080,18 +1144,47 @@ cudaError_t launch_cheb(const DevState &s, double dt, bool mixed, cudaStream_t s
     return cudaSuccess;
 }
 
+// Allow the hop kernels the device's full opt-in shared memory (minus their
+// static shared memory), so that later launches, including launches under
+// stream capture, need no attribute change.
+template <class F>
+static void allow_max_smem(F *fn)
+{
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess && optin > (int)fa.sharedSizeBytes)
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+    cudaGetLastError();
+}
+
+void configure_hop_smem()
+{
+    allow_max_smem(k_hop<float2>);
+    allow_max_smem(k_hop<double2>);
+}
+
 cudaError_t launch_hop(const DevState &s, double dt, double mass, uint64_t seed, int skip_bound,
                        double *g_out, cudaStream_t st, bool mixed)
 {
     if (s.n == 0) return cudaSuccess;
     const size_t smem = hop_smem_bytes(s.N, s.Ne, mixed);
     // two 256-thread CTAs per SM when the shared memory allows, else one of 512
-    const int threads = (2 * smem + 2048 <= 227 * 1024) ? 256 : 512;
+    int threads = (2 * smem + 2048 <= 227 * 1024) ? 256 : 512;
+    if (s.hop_threads > 0) threads = s.hop_threads;
+    // the shared-memory limit is a function attribute, not a stream operation;
+    // set it outside stream capture (contexts set it when they are created)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
     if (mixed) {
-        cudaFuncSetAttribute(k_hop<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cs == cudaStreamCaptureStatusNone)
+            cudaFuncSetAttribute(k_hop<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_hop<float2><<<(unsigned)s.n, threads, smem, st>>>(s, dt, mass, seed, skip_bound, g_out);
     } else {
-        cudaFuncSetAttribute(k_hop<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cs == cudaStreamCaptureStatusNone)
+            cudaFuncSetAttribute(k_hop<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_hop<double2><<<(unsigned)s.n, threads, smem, st>>>(s, dt, mass, seed, skip_bound, g_out);
     }
     return cudaGetLastError();

@@ -55,13 +55,14 @@ class _EoccModel(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("skip_bound", ctypes.c_int),
                 ("record_every", ctypes.c_int), ("max_records", ctypes.c_int),
-                ("z_done", ctypes.c_double)]
+                ("z_done", ctypes.c_double), ("compact_every", ctypes.c_int)]
 
 
 EXPORTS = ["iesh_create", "iesh_destroy", "iesh_bath", "iesh_init_state", "iesh_set_state",
            "iesh_get_state", "iesh_run", "iesh_get_eigen", "iesh_hop_probabilities",
            "iesh_get_counters", "iesh_get_records", "iesh_get_propagator_terms", "iesh_profile",
-           "iesh_profile_read", "iesh_hop_probabilities_noalloc", "iesh_eocc_create",
+           "iesh_profile_read", "iesh_get_live", "iesh_set_kernel_shape",
+           "iesh_get_kernel_shape", "iesh_hop_probabilities_noalloc", "iesh_eocc_create",
            "iesh_eocc_destroy", "iesh_eocc_last_error", "iesh_eocc_forward",
            "iesh_eocc_backward", "iesh_last_error", "iesh_status_string"]
 KERNEL_CLASSES = ["eigen", "coupling", "propagate", "hop", "other"]
@@ -93,6 +94,9 @@ def load(path=LIB_PATH):
     L.iesh_get_records.argtypes = [_vp, _vp, _vp, _vp]
     L.iesh_get_propagator_terms.argtypes = [_vp, _vp]
     L.iesh_profile.argtypes = [_vp, ctypes.c_int]
+    L.iesh_get_live.argtypes = [_vp, _vp]
+    L.iesh_set_kernel_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.iesh_get_kernel_shape.argtypes = [_vp, _vp, _vp, _vp]
     L.iesh_profile_read.argtypes = [_vp, _vp, _vp]
     L.iesh_hop_probabilities_noalloc.argtypes = [ctypes.POINTER(_Model), ctypes.c_int64, _vp, _vp,
                                                  _vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp,
@@ -168,7 +172,7 @@ class Context:
     """A batch of IESH trajectories on one GPU (wraps iesh_ctx)."""
 
     def __init__(self, model, max_traj, precision=PREC_FP64, skip_bound=False, record_every=0,
-                 max_records=0, z_done=0.0, stream=None):
+                 max_records=0, z_done=0.0, compact_every=0, stream=None):
         self.L = load()
         self.model = dict(model)
         self.N = int(model["M"]) + 1
@@ -178,7 +182,7 @@ class Context:
         self.n = 0
         self._m = model_struct(model)
         self._o = _Options(precision, int(bool(skip_bound)), int(record_every), int(max_records),
-                           float(z_done))
+                           float(z_done), int(compact_every))
         self.stream = current_stream_handle() if stream is None else stream
         h = _vp()
         rc = self.L.iesh_create(ctypes.byref(h), ctypes.byref(self._m), ctypes.byref(self._o),
@@ -265,6 +269,21 @@ class Context:
         self._check(self.L.iesh_get_counters(self._h, ns.ctypes.data, hops.ctypes.data,
                                              fr.ctypes.data), "iesh_get_counters")
         return ns, hops, fr
+
+    def live_count(self):
+        n = ctypes.c_int64(0)
+        self._check(self.L.iesh_get_live(self._h, ctypes.addressof(n)), "iesh_get_live")
+        return n.value
+
+    def set_kernel_shape(self, cheb_ept=0, cheb_G=0, hop_threads=0):
+        self._check(self.L.iesh_set_kernel_shape(self._h, int(cheb_ept), int(cheb_G),
+                                                 int(hop_threads)), "iesh_set_kernel_shape")
+
+    def kernel_shape(self):
+        e, g, h = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        self._check(self.L.iesh_get_kernel_shape(self._h, ctypes.addressof(e), ctypes.addressof(g),
+                                                 ctypes.addressof(h)), "iesh_get_kernel_shape")
+        return e.value, g.value, h.value
 
     def propagator_terms(self):
         K = np.zeros(self.n, np.int32)

@@ -1,0 +1,70 @@
+"""Autotuner of the kernel shapes of a context.
+
+Times candidate shapes of the Chebyshev propagator (electrons per thread x
+column groups per CTA) and of the hop kernel (threads per CTA) on a scratch
+context with the same model, precision and batch size, from the caller's
+state, and sets the fastest on the context.  Results do not depend on the
+shape (every output keeps its summation order), so tuning only changes
+speed.  Choices are cached per (N, Ne, precision, batch size) in-process.
+"""
+import numpy as np
+
+from . import iesh as _I
+
+_CACHE = {}
+
+
+def cheb_candidates(N, Ne, limit=6):
+    """Propagator shapes ranked by lane and electron-slot efficiency."""
+    out = []
+    for ept in (2, 1):
+        for G in range(1, 1024 // N + 1):
+            nb = G * ept
+            if nb > 2 * Ne + 1:
+                break
+            thr = G * N
+            thr32 = (thr + 31) // 32 * 32
+            blocks = -(-Ne // nb)
+            eff = thr / thr32 * Ne / (blocks * nb)
+            out.append((eff, nb, ept, G))
+    out.sort(key=lambda r: (-r[0], -r[1]))
+    return [(ept, G) for _, _, ept, G in out[:limit]]
+
+
+def autotune(ctx, x, p, occ, C, dt, steps=3, seed=0):
+    """Pick the fastest shapes for `ctx` from the state (x, p, occ, C).
+
+    Returns dict(cheb=(ept, G), hop_threads=..., times={...})."""
+    import torch
+
+    key = (ctx.N, ctx.Ne, ctx.precision, int(x.shape[0]))
+    if key in _CACHE:
+        best = _CACHE[key]
+        ctx.set_kernel_shape(best["cheb"][0], best["cheb"][1], best["hop_threads"])
+        return best
+    scratch = _I.Context(ctx.model, int(x.shape[0]), precision=ctx.precision, stream=ctx.stream)
+    times_cheb, times_hop = {}, {}
+
+    def trial(ept, G, hop):
+        scratch.set_state(x, p, occ, C)
+        scratch.set_kernel_shape(ept, G, hop)
+        scratch.run(dt, 1, seed)
+        scratch.profile(True)
+        scratch.run(dt, steps, seed)
+        prof = scratch.profile_read()
+        scratch.profile(False)
+        return prof["propagate"][0], prof["hop"][0]
+
+    for ept, G in cheb_candidates(ctx.N, ctx.Ne):
+        times_cheb[(ept, G)] = trial(ept, G, 0)[0]
+    for hop in (256, 512):
+        ept, G = min(times_cheb, key=times_cheb.get)
+        times_hop[hop] = trial(ept, G, hop)[1]
+    torch.cuda.synchronize()
+    scratch.close()
+    best = dict(cheb=min(times_cheb, key=times_cheb.get), hop_threads=min(times_hop, key=times_hop.get),
+                times=dict(cheb={f"{k}": v for k, v in times_cheb.items()},
+                           hop={f"{k}": v for k, v in times_hop.items()}))
+    _CACHE[key] = best
+    ctx.set_kernel_shape(best["cheb"][0], best["cheb"][1], best["hop_threads"])
+    return best

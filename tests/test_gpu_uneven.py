@@ -1,0 +1,112 @@
+"""Uneven batches on the GPU: trajectories that end early (leaving the
+surface) are dropped from a device work list compacted in place; several
+bath sizes run as separate contexts captured together in one CUDA graph;
+kernel shapes come from the autotuner.  None of these may change a result:
+the Philox counter is keyed by trajectory and step, state never moves, and
+every output keeps its summation order, so the checks here are bit-exact.
+The scattering model itself is checked against the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import iesh_inputs as W
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2212_00518_gb300 import build as B
+    B.build()
+    import paper_2212_00518_gb300 as pkg
+    return pkg
+
+
+def _mixed_direction_batch(M, n, seed, bias=0.0):
+    md = W.morse_image(M, bias=bias)
+    rng = np.random.default_rng(seed)
+    e = rng.uniform(W.ev(0.2), W.ev(1.5), n)
+    sgn = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)  # half move away from the surface
+    x = np.full(n, W.angstrom(5.0))
+    p = sgn * np.sqrt(2 * md["mass"] * e)
+    occ = W.lowest_occupations(n, md["Ne"])
+    C = W.unit_coefficients(occ, M + 1)
+    return md, x, p, occ, C
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_compaction_does_not_change_results(P, precision):
+    md, x, p, occ, C = _mixed_direction_batch(20, 48, 3)
+    z_done = W.angstrom(5.2)
+    dt = 0.1 * W.FS_AU
+    out = []
+    for ce in (0, 8):
+        ctx = P.Context(md, 48, precision=precision, z_done=z_done, compact_every=ce)
+        ctx.set_state(x, p, occ, C if precision == 0 else C.astype(np.complex64))
+        ctx.run(dt, 96, seed=11)
+        out.append((ctx.get_state(), ctx.counters(), ctx.live_count()))
+    (s0, c0, l0), (s1, c1, l1) = out
+    done = (s1["status"] & P.iesh.TRAJ_DONE) != 0
+    assert 0 < done.sum() < 48, "batch must be uneven"
+    assert l1 == int((~done).sum()) and l0 == 48
+    for k in ("x", "p", "occ", "C", "status"):
+        assert np.array_equal(s0[k], s1[k]), k
+    for a, b in zip(c0, c1):
+        assert np.array_equal(a, b)
+    # finished trajectories stopped advancing
+    assert np.all(c1[0][done] < 96) and np.all(c1[0][~done] == 96)
+
+
+def test_graph_replay_matches_eager(P):
+    from paper_2212_00518_gb300.ensemble import UnevenBatch
+    groups = W.scattering_batch(96, seed=4, M_choices=(20, 30), biases=(0.0, 0.05))
+    res = []
+    for use_graph in (False, True):
+        ub = UnevenBatch(groups, dt=0.1 * W.FS_AU, z_done=W.angstrom(5.6), precision=1,
+                         compact_every=16, seed=2)
+        ub.run(64, use_graph=use_graph)
+        res.append(ub.results())
+        ub.close()
+    for k in res[0]:
+        assert np.array_equal(res[0][k], res[1][k]), k
+
+
+def test_autotuned_shapes_keep_results(P):
+    from paper_2212_00518_gb300 import tuning
+    md = W.double_well(60)
+    n = 64
+    x, p = W.thermal_harmonic(n, md["mass"], md["par"][0], 0.01, 5)
+    occ = W.random_occupations(n, 61, 30, 6)
+    C = W.mixed_coefficients(occ, 61, 7, 0.5)
+    base = P.Context(md, n)
+    base.set_state(x, p, occ, C)
+    base.run(1.0, 5, seed=1)
+    ref = base.get_state()
+    tuned = P.Context(md, n)
+    best = tuning.autotune(tuned, x, p, occ, C, 1.0, steps=2)
+    assert tuned.kernel_shape()[:2] == tuple(best["cheb"])
+    tuned.set_state(x, p, occ, C)
+    tuned.run(1.0, 5, seed=1)
+    st = tuned.get_state()
+    for k in ("x", "p", "occ", "C"):
+        assert np.array_equal(st[k], ref[k]), k
+
+
+def test_scattering_model_matches_oracle(P):
+    """Two-lead (bias) Morse + image-charge model, trajectories flying in from
+    5 angstrom, 150 steps of 0.1 fs in FP64 against the oracle."""
+    md, x, p, occ, C = _mixed_direction_batch(20, 6, 9, bias=0.1)
+    p = -np.abs(p)
+    C = W.mixed_coefficients(occ, 21, 3, 0.4)
+    dt = 0.1 * W.FS_AU
+    ctx = P.Context(md, 6)
+    ctx.set_state(x, p, occ, C)
+    ctx.run(dt, 150, seed=8)
+    st = ctx.get_state()
+    ref = O.run(O.bind(md), x, p, occ.astype(np.int32), np.transpose(C, (0, 2, 1)), dt, 150, seed=8)
+    assert np.array_equal(st["occ"], ref["occ"])
+    assert np.abs(st["x"] - ref["x"]).max() <= 1e-9 * np.abs(ref["x"]).max()
+    assert np.abs(np.transpose(st["C"], (0, 2, 1)) - ref["C"]).max() <= 1e-8
