@@ -115,6 +115,24 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+# ------------------------------------------------------------- replicas
+def replica_seed(seed, rank):
+    """Philox key of a replica: independent streams per rank."""
+    return seed + rank
+
+
+def aggregate(ms_local, e2e_local, n_per_rank, steps, world, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: the slowest rank's time
+    bounds the job (max over ranks), the units are summed over ranks."""
+    ms, e2e = ms_local, e2e_local
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([ms_local, e2e_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e = float(t[0]), float(t[1])
+    return dict(ms=ms, e2e_s=e2e, value=world * n_per_rank * steps / (ms / 1e3))
+
+
 # ------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -138,7 +156,7 @@ def run_ours(args):
     n = args.n_traj
     x, p, occ, C = initial_state(md, kT, n, seed=1000 + rank)
     stream = torch.cuda.current_stream()
-    seed = args.seed + rank  # Philox key per replica
+    seed = replica_seed(args.seed, rank)
 
     def barrier():
         if world > 1:
@@ -168,10 +186,7 @@ def run_ours(args):
         ms_ = ev0.elapsed_time(ev1)
         prof_ = c.profile_read()
         c.profile(False)
-        if world > 1:
-            tt = torch.tensor([ms_], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms_ = float(tt.item())
+        ms_ = aggregate(ms_, 0.0, n, args.steps, world, dist if world > 1 else None, "cuda")["ms"]
         return c, ms_, prof_, clk
 
     ctx, ms, prof, clk = measure(P.PREC_FP64, True)
@@ -201,11 +216,8 @@ def run_ours(args):
         ctx.run(dt, 1, seed)
         ctx.get_state(hx, hp, hocc, hC, hst)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = aggregate(0.0, time.perf_counter() - t0, n, e2e_steps, world,
+                      dist if world > 1 else None, "cuda")["e2e_s"]
     h2d = n * (8 + 8 + 2 * Ne + 16 * Ne * N)
     d2h = h2d + 4 * n
 
@@ -324,6 +336,103 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ other workloads
+def _timed_steps(torch, stream, fn, warmup, steps):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_workload(args):
+    """Secondary measurements (one JSON line each): the M=200 mixed batch,
+    the paper-shaped timing grid, the uneven scattering batch, E_occ."""
+    import torch
+
+    import paper_2212_00518_gb300 as P
+    from paper_2212_00518_gb300 import build as B
+    B.build()
+    stream = torch.cuda.current_stream()
+    line = {"unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+            "impl": "ours"}
+    if args.workload == "paper":
+        # Sec. III B double well with the paper's constants, dt = 10 a.u.
+        res = []
+        for M in (40, 80, 200):
+            md = W.double_well_paper(M)
+            for n in (1, 4096):
+                x, p = W.thermal_harmonic(n, md["mass"], md["par"][0], 5 * 9.5e-4, seed=1)
+                occ = W.lowest_occupations(n, md["Ne"])
+                C = W.unit_coefficients(occ, M + 1)
+                for prec in (P.PREC_FP64, P.PREC_MIXED):
+                    for skip in (False, True):
+                        c = P.Context(md, n, precision=prec, skip_bound=skip, stream=stream.cuda_stream)
+                        c.set_state(x, p, occ, C if prec == P.PREC_FP64 else C.astype(np.complex64))
+                        ms = _timed_steps(torch, stream, lambda: c.run(10.0, 1, 0), args.warmup, args.steps)
+                        _, hops, _ = c.counters()
+                        res.append({"M": M, "trajectories": n, "precision": "fp64" if prec == 0 else "mixed",
+                                    "skip_bound": skip, "traj_steps_per_s": n * args.steps / (ms / 1e3),
+                                    "ms_per_step": ms / args.steps, "hops": int(hops.sum())})
+                        c.close()
+        pick = [r for r in res if r["M"] == 80 and r["trajectories"] == 4096
+                and r["precision"] == "fp64" and not r["skip_bound"]][0]
+        line.update(metric=METRIC + " [paper double well, Sec. III B constants, dt=10]",
+                    value=pick["traj_steps_per_s"], dtype="f64",
+                    config={"workload": "paper-shaped timing grid: M in {40, 80, 200}, 1 and 4096 "
+                                        "trajectories, FP64 and mixed, with and without the "
+                                        "hop-probability bound skip", "value_is": "M=80, 4096, fp64, no skip"},
+                    results=res)
+    elif args.workload == "scatter":
+        from paper_2212_00518_gb300.ensemble import UnevenBatch
+        groups = W.scattering_batch(16384, seed=4)
+        ub = UnevenBatch(groups, dt=0.1 * W.FS_AU, z_done=W.angstrom(10.0), precision=P.PREC_MIXED,
+                         compact_every=64, seed=0, autotune=args.autotune)
+        ub.run(64 * max(1, args.warmup // 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        live_steps = ub.run(ub.steps_done + 64 * args.steps)
+        sec = time.perf_counter() - t0
+        line.update(metric=METRIC + " [uneven scattering batch]", value=live_steps / sec,
+                    dtype="mixed (f32 propagation, f64 eigen/LU/rescale)",
+                    config={"workload": "16384 Morse + image-charge scattering trajectories, M in "
+                                        "{50, 100, 200} (Ne = M/2), bias 0 / 0.05 / 0.1 a.u. (two "
+                                        "leads), E_inc 0.2-1.5 eV from 5 angstrom, dt 0.1 fs, "
+                                        "end at z > 10 angstrom, work list compacted every 64 "
+                                        "steps, one CUDA graph per 64-step chunk",
+                            "contexts": len(groups), "live_after": ub.live(),
+                            "steps_timed": 64 * args.steps})
+        ub.close()
+    elif args.workload == "eocc":
+        from paper_2212_00518_gb300 import eocc as E
+        wl = W.eocc_workload(M=300, B=65536, seed=5)
+        model = E.EOccModel(wl, stream=stream.cuda_stream)
+        out = {}
+        for dtype in (torch.float32, torch.float64):
+            x = torch.tensor(wl["x"], device="cuda", dtype=dtype)
+            th = torch.tensor(wl["theta"], device="cuda", dtype=dtype)
+            gE = torch.ones(65536, device="cuda", dtype=dtype)
+
+            def step():
+                _, saved, _ = model.forward(x, th)
+                model.backward(x, th, saved, gE)
+            ms = _timed_steps(torch, stream, step, args.warmup, args.steps)
+            out[str(dtype).split(".")[-1]] = 65536 * args.steps / (ms / 1e3)
+        line.update(metric="E_occ forward + backward geometries/s", unit="geometries/s",
+                    value=out["float32"], dtype="f32",
+                    config={"workload": "two adsorbate orbitals, M=300 bath states, Ne=151, six "
+                                        "coordinates, 16 parameters, 65536 geometries"},
+                    results={"float32": out["float32"], "float64": out["float64"]})
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -338,9 +447,15 @@ def main():
     ap.add_argument("--cpu-steps", dest="cpu_steps", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--workload", choices=["dw", "paper", "scatter", "eocc"], default="dw",
+                    help="dw: the double-well batch (default, --M/--n-traj); the others print "
+                         "secondary measurements")
+    ap.add_argument("--autotune", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "dw":
+        run_workload(args)
     else:
         run_ours(args)
 

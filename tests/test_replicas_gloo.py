@@ -1,0 +1,53 @@
+"""Host logic of the multi-GPU benchmark (replicas only: independent
+trajectory batches per rank, no data-path collective) with two gloo ranks
+on the CPU: per-rank Philox keys differ, the job time is the maximum over
+ranks and the throughput sums the ranks' trajectories."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ms_local = [120.0, 150.0][rank]
+    e2e_local = [1.5, 1.2][rank]
+    agg = bench.aggregate(ms_local, e2e_local, 4096, 10, world, dist, "cpu")
+    seeds = [None] * world
+    dist.all_gather_object(seeds, bench.replica_seed(7, rank))
+    out[rank] = (agg["ms"], agg["e2e_s"], agg["value"], tuple(seeds))
+    dist.destroy_process_group()
+
+
+def test_two_rank_aggregation():
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    for r in range(2):
+        ms, e2e, value, seeds = out[r]
+        assert ms == 150.0 and e2e == 1.5
+        assert value == pytest.approx(2 * 4096 * 10 / 0.150)
+        assert seeds[0] != seeds[1]
