@@ -130,7 +130,8 @@ def aggregate(ms_local, e2e_local, n_per_rank, steps, world, dist=None, device="
         t = torch.tensor([ms_local, e2e_local], dtype=torch.float64, device=device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms, e2e = float(t[0]), float(t[1])
-    return dict(ms=ms, e2e_s=e2e, value=world * n_per_rank * steps / (ms / 1e3))
+    value = world * n_per_rank * steps / (ms / 1e3) if ms > 0 else None
+    return dict(ms=ms, e2e_s=e2e, value=value)
 
 
 # ------------------------------------------------------------- our arm

@@ -173,9 +173,13 @@ iesh_status iesh_get_records(iesh_ctx *ctx, double *pop_sh, double *pop_wf, int6
  * list is off).  Synchronises the context stream. */
 iesh_status iesh_get_live(iesh_ctx *ctx, int64_t *n_live);
 
-/* Kernel shapes.  cheb_ept (1 or 2) electrons per thread and cheb_G column
- * groups per CTA of the propagator (cheb_G * N <= 1024), hop_threads (256 or
- * 512) threads of the hop kernel; 0 restores the built-in choice.  Results
+/* Kernel shapes.  FP64 contexts: cheb_ept (1 or 2) electrons per thread and
+ * cheb_G column groups per CTA of the propagator (cheb_G * N <= 1024).
+ * Mixed contexts: cheb_ept must be 4 (each thread holds 4 orbitals x 4
+ * electrons) and cheb_G * ceil(N/4) <= 256, with 8 * Np * (8 cheb_G + 1)
+ * bytes of shared memory (Np = N rounded up to a multiple of 4) at most
+ * 110 KiB.  hop_threads (256 or 512) threads of the
+ * hop kernel; 0 restores the built-in choice; IESH_EINVAL otherwise.  Results
  * do not depend on the shapes except through floating-point summation order
  * of the propagator (none: each output has a fixed order).  Used by the
  * autotuner of the Python package. */

@@ -587,9 +587,17 @@ iesh_status iesh_get_live(iesh_ctx *ctx, int64_t *n_live)
 iesh_status iesh_set_kernel_shape(iesh_ctx *ctx, int cheb_ept, int cheb_G, int hop_threads)
 {
     if (!ctx) return IESH_EINVAL;
-    if (cheb_ept < 0 || cheb_ept > 2 || cheb_G < 0 || (cheb_ept > 0) != (cheb_G > 0) ||
-        cheb_G * ctx->N > 1024)
+    if (ctx->opt.precision == IESH_PREC_MIXED) {
+        const int nq = (ctx->N + 3) / 4;
+        if (!((cheb_ept == 0 && cheb_G == 0) ||
+              (cheb_ept == 4 && cheb_G > 0 && cheb_G * nq <= 256 &&
+               cheb32_smem_bytes(ctx->N, cheb_G) <= kCheb32MaxSmem)))
+            return fail(ctx, IESH_EINVAL, "mixed propagator shape (%d, %d) invalid for N=%d (need ept 4, G*ceil(N/4) <= 256)",
+                        cheb_ept, cheb_G, ctx->N);
+    } else if (cheb_ept < 0 || cheb_ept > 2 || cheb_G < 0 || (cheb_ept > 0) != (cheb_G > 0) ||
+               cheb_G * ctx->N > 1024) {
         return fail(ctx, IESH_EINVAL, "propagator shape (%d, %d) invalid for N=%d", cheb_ept, cheb_G, ctx->N);
+    }
     if (hop_threads != 0 && hop_threads != 256 && hop_threads != 512)
         return fail(ctx, IESH_EINVAL, "hop_threads must be 0, 256 or 512");
     ctx->ds.cheb_ept = cheb_ept;
@@ -602,7 +610,14 @@ iesh_status iesh_get_kernel_shape(iesh_ctx *ctx, int *cheb_ept, int *cheb_G, int
 {
     if (!ctx) return IESH_EINVAL;
     int e = ctx->ds.cheb_ept, g = ctx->ds.cheb_G;
-    if (e == 0) cheb_shape(ctx->N, ctx->Ne, e, g);
+    if (e == 0) {
+        if (ctx->opt.precision == IESH_PREC_MIXED) {
+            e = 4;
+            cheb32_shape(ctx->N, ctx->Ne, g);
+        } else {
+            cheb_shape(ctx->N, ctx->Ne, e, g);
+        }
+    }
     if (cheb_ept) *cheb_ept = e;
     if (cheb_G) *cheb_G = g;
     if (hop_threads) *hop_threads = ctx->ds.hop_threads;

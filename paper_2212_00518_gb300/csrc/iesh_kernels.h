@@ -24,5 +24,9 @@ cudaError_t launch_compact(const DevState &s, int32_t *live, int32_t *n_live, cu
 cudaError_t launch_live_init(int64_t n, int32_t *live, int32_t *n_live, cudaStream_t st);
 void configure_hop_smem();
 void cheb_shape(int N, int Ne, int &ept, int &G);
+// FP32 (mixed-precision) propagator: 4 electrons per thread, G column groups
+constexpr size_t kCheb32MaxSmem = 110 * 1024;
+size_t cheb32_smem_bytes(int N, int G);
+void cheb32_shape(int N, int Ne, int &G);
 
 }  // namespace iesh

@@ -1,4 +1,5 @@
-// iesh_step.cu -- FP64 kernels of one batched IESH step (sm_103a).
+// iesh_step.cu -- kernels of one batched IESH step (sm_103a), FP64 and the
+// mixed-precision variants (k_build_w_f32, k_cheb_f32t, k_hop<float2>).
 //
 // One trajectory step (Gardner et al., arXiv:2212.00518, Sec. II B-C):
 //   k_eigen     velocity-Verlet kick + drift, eigenpairs of the arrowhead
@@ -286,7 +287,8 @@ __global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, doub
     const float dh1 = (float)s.geo[t * 4 + 1], k1 = (float)s.geo[t * 4 + 2];
     const float a0 = (float)(0.5 * dt * s.vprev[t]), a1 = (float)(0.5 * dt * (s.p[t] / mass));
     __syncthreads();
-    float *W = reinterpret_cast<float *>(s.scratch + t * s.scratch_stride);
+    float *W = reinterpret_cast<float *>(s.scratch + t * s.scratch_stride);  // [N][Np]
+    const int Np = (N + 3) & ~3;
     const float *__restrict__ E = s.epsdiff;  // [M][M] eps_a - eps_b
     double lo = __longlong_as_double(0x7ff0000000000000ll), hi = -lo;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
@@ -303,11 +305,13 @@ __global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, doub
                 const float d1 = qf[N + j] * qk1 * (dh1 + k1 * (lmh[N + j] + mk1)) / den1;
                 w = a0 * d0 + a1 * d1;
             }
-            W[(int64_t)j * N + k] = w;
+            W[(int64_t)j * Np + k] = w;
             Rk += fabsf(w);
         }
         // margin for the FP32 rounding of the row sum
         const double R = (double)Rk * (1.0 + 1e-5);
+        if (k < Np - N)
+            for (int j = 0; j < N; ++j) W[(int64_t)j * Np + N + k] = 0.0f;  // row padding
         lo = fmin(lo, Lsum[k] - R);
         hi = fmax(hi, Lsum[k] + R);
     }
@@ -456,6 +460,193 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
     }
 }
 
+// FP32 propagator, register-tiled: thread (row quad rq, column group cg)
+// owns rows 4rq..4rq+3 and CE electrons (2 CE reals) of the CTA's block of
+// G*CE electrons.  Per orbital i it loads W[i][4rq..4rq+3] as one float4
+// (W_ji = -W_ij; W rows padded to a multiple of 4) and 2CE reals of t_k[i]
+// as float4 broadcasts from shared memory, for 8 CE FFMAs.  t_k and
+// t_(k-1) live in two shared buffers: t_(k+1) overwrites t_(k-1) in place
+// (each thread rewrites only its own entries), so one barrier per order
+// suffices and neither is held in registers.  Row j of a buffer starts at
+// j W2 + 4 floor(j/4): the 4-float gap after every row quad puts the row
+// quads of consecutive threads 4 banks apart, so the per-thread row
+// accesses of the recurrence are conflict-free float4 accesses.
+__device__ __forceinline__ int cheb32_row(int j, int W2) { return j * W2 + ((j >> 2) << 2); }
+
+template <int CE>
+__global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int G, int64_t t_base)
+{
+    constexpr int RQ = 4, NR = 2 * CE, NV = NR / 4;  // NV float4 per row
+    extern __shared__ __align__(16) unsigned char cheb32_smem[];
+    const int64_t t = traj_of(s, t_base + blockIdx.y);
+    if (t < 0 || (s.status[t] & ST_DONE)) return;
+    const int N = s.N, Ne = s.Ne, Np = (N + 3) & ~3;
+    const int nq = (N + RQ - 1) / RQ;
+    const int W2 = NR * G;
+    float *buf0 = reinterpret_cast<float *>(cheb32_smem);
+    float *buf1 = buf0 + cheb32_row(Np, W2);
+    const int cg = threadIdx.x / nq, rq = threadIdx.x - cg * nq;
+    const bool act = cg < G;
+    const int j0 = rq * RQ;
+    const int e0 = blockIdx.x * (CE * G) + cg * CE;
+    const int mine = cheb32_row(j0, W2) + NR * cg;  // my first row, my columns
+    const double *cb = s.cheb + t * kChebStride;
+    const double c = cb[0], rho = cb[1];
+    const int K = (int)cb[2];
+    const double *J = cb + 3;
+    const float inv_rho = (float)(rho > 0.0 ? 1.0 / rho : 0.0);
+    const float *__restrict__ W = reinterpret_cast<const float *>(s.scratch + t * s.scratch_stride);
+    float2 *C = reinterpret_cast<float2 *>(s.C) + (int64_t)t * Ne * N;
+    float Lc[RQ], acc[RQ][NR];
+    const float J0 = (float)J[0];
+#pragma unroll
+    for (int r = 0; r < RQ; ++r) {
+        const int j = j0 + r;
+        const bool ok = act && j < N;
+        Lc[r] = ok ? (float)(0.5 * dt * (s.lam_prev[t * N + j] + s.lam[t * N + j]) - c) : 0.f;
+        float v[NR];
+#pragma unroll
+        for (int e = 0; e < CE; ++e) {
+            float2 ce = make_float2(0.f, 0.f);
+            if (ok && e0 + e < Ne) ce = C[(int64_t)(e0 + e) * N + j];
+            v[2 * e] = ce.x;
+            v[2 * e + 1] = ce.y;
+            acc[r][2 * e] = J0 * ce.x;
+            acc[r][2 * e + 1] = J0 * ce.y;  // single products: no contraction possible
+        }
+        if (ok) {
+            float4 *d4 = reinterpret_cast<float4 *>(buf0 + mine + r * W2);
+#pragma unroll
+            for (int h = 0; h < NV; ++h) d4[h] = make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < K; ++k) {
+        const float *cur = (k & 1) ? buf1 : buf0;  // t_k
+        float *nxt = (k & 1) ? buf0 : buf1;        // t_(k-1), becomes t_(k+1)
+        float y[RQ][NR];
+#pragma unroll
+        for (int r = 0; r < RQ; ++r)
+#pragma unroll
+            for (int q = 0; q < NR; ++q) y[r][q] = 0.f;
+        if (act) {
+            const float *col = cur + NR * cg;
+            const float *wcol = W + j0;
+#pragma unroll 2
+            for (int i = 0; i < N; ++i) {
+                const float4 w = *reinterpret_cast<const float4 *>(wcol + (int64_t)i * Np);
+                const float4 *tr = reinterpret_cast<const float4 *>(col + cheb32_row(i, W2));
+                float tv[NR];
+#pragma unroll
+                for (int h = 0; h < NV; ++h) {
+                    const float4 a4 = tr[h];
+                    tv[4 * h] = a4.x;
+                    tv[4 * h + 1] = a4.y;
+                    tv[4 * h + 2] = a4.z;
+                    tv[4 * h + 3] = a4.w;
+                }
+                const float wr[RQ] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int r = 0; r < RQ; ++r)
+#pragma unroll
+                    for (int q = 0; q < NR; ++q) y[r][q] = fmaf(wr[r], tv[q], y[r][q]);
+            }
+            const float cj = (float)(2.0 * J[k + 1]);
+            const int ph = (k + 1) & 3;  // (-i)^(k+1)
+#pragma unroll
+            for (int r = 0; r < RQ; ++r) {
+                if (j0 + r < N) {
+                    const float4 *o4 = reinterpret_cast<const float4 *>(cur + mine + r * W2);
+                    float4 *d4 = reinterpret_cast<float4 *>(nxt + mine + r * W2);
+                    float own[NR], prv[NR], nw[NR];
+#pragma unroll
+                    for (int h = 0; h < NV; ++h) {
+                        const float4 a4 = o4[h];
+                        own[4 * h] = a4.x;
+                        own[4 * h + 1] = a4.y;
+                        own[4 * h + 2] = a4.z;
+                        own[4 * h + 3] = a4.w;
+                        float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (k > 0) b4 = d4[h];
+                        prv[4 * h] = b4.x;
+                        prv[4 * h + 1] = b4.y;
+                        prv[4 * h + 2] = b4.z;
+                        prv[4 * h + 3] = b4.w;
+                    }
+#pragma unroll
+                    for (int e = 0; e < CE; ++e) {
+                        // (X t)_j = ((L_j - c) t_j - i (W t)_j) / rho and (W t)_j = -y
+                        const float xr = fmaf(Lc[r], own[2 * e], -y[r][2 * e + 1]) * inv_rho;
+                        const float xi = fmaf(Lc[r], own[2 * e + 1], y[r][2 * e]) * inv_rho;
+                        float nr = xr, ni = xi;
+                        if (k > 0) {
+                            nr = fmaf(2.f, xr, -prv[2 * e]);
+                            ni = fmaf(2.f, xi, -prv[2 * e + 1]);
+                        }
+                        float *a = acc[r] + 2 * e;
+                        if (ph == 0) {
+                            a[0] = fmaf(cj, nr, a[0]);
+                            a[1] = fmaf(cj, ni, a[1]);
+                        } else if (ph == 1) {
+                            a[0] = fmaf(cj, ni, a[0]);
+                            a[1] = fmaf(-cj, nr, a[1]);
+                        } else if (ph == 2) {
+                            a[0] = fmaf(-cj, nr, a[0]);
+                            a[1] = fmaf(-cj, ni, a[1]);
+                        } else {
+                            a[0] = fmaf(-cj, ni, a[0]);
+                            a[1] = fmaf(cj, nr, a[1]);
+                        }
+                        nw[2 * e] = nr;
+                        nw[2 * e + 1] = ni;
+                    }
+#pragma unroll
+                    for (int h = 0; h < NV; ++h) d4[h] = make_float4(nw[4 * h], nw[4 * h + 1], nw[4 * h + 2], nw[4 * h + 3]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (act) {
+        double scd, ccd;
+        sincos(c, &scd, &ccd);
+        const float sc = (float)scd, cc = (float)ccd;
+#pragma unroll
+        for (int r = 0; r < RQ; ++r) {
+            const int j = j0 + r;
+#pragma unroll
+            for (int e = 0; e < CE; ++e)
+                if (j < N && e0 + e < Ne) {
+                    const float ar = acc[r][2 * e], ai = acc[r][2 * e + 1];
+                    C[(int64_t)(e0 + e) * N + j] = make_float2(fmaf(cc, ar, sc * ai), fmaf(cc, ai, -(sc * ar)));
+                }
+        }
+    }
+}
+
+// Column groups of k_cheb_f32t: fill the CTA (row quads x groups <= 256)
+// and waste few electron slots; two CTAs must fit in an SM's shared memory.
+size_t cheb32_smem_bytes(int N, int G)
+{
+    const int Np = (N + 3) & ~3;
+    return (size_t)2 * (Np * 8 * G + Np) * sizeof(float);  // two buffers of padded rows
+}
+void cheb32_shape(int N, int Ne, int &G)
+{
+    const int nq = (N + 3) / 4;
+    double best = -1.0;
+    G = 1;
+    for (int g = 1; g * nq <= 256 && (g == 1 || cheb32_smem_bytes(N, g) <= kCheb32MaxSmem); ++g) {
+        const int nb = 4 * g, thr = g * nq, thr32 = (thr + 31) & ~31;
+        const int blocks = (Ne + nb - 1) / nb;
+        const double eff = (double)thr / thr32 * (double)Ne / (blocks * nb) + 1e-4 * g;
+        if (eff > best) {
+            best = eff;
+            G = g;
+        }
+    }
+}
+
 // ================================================================= hops
 // Sec. II B: the amplitude of the occupied configuration is det S with
 // S_aj = C_{s_a, j}; the candidate that puts orbital m in slot a has
@@ -539,7 +730,6 @@ __global__ void __launch_bounds__(512, 1) k_hop(DevState s, double dt, double ma
     int *isocc = rows + Ne;                                       // [N]
     int *unocc = isocc + N;                                       // [N - Ne] ascending
     __shared__ int s_flag, s_hop_a, s_hop_m;
-    __shared__ double s_det_abs;
 
     const CT *Ct = reinterpret_cast<const CT *>(s.C) + (int64_t)t * Ne * N;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -610,21 +800,24 @@ __global__ void __launch_bounds__(512, 1) k_hop(DevState s, double dt, double ma
             singular = true;
             break;
         }
-        const double2 pinv = crcp(pv);
         // remove pr from the row list (every thread does the same edit on a
         // private copy of the position; thread 0 writes it after the barrier)
         int ppos = 0;
         for (int q = 0; q < nr; ++q)
             if (rows[q] == pr) ppos = q;
-        // multipliers of the remaining rows
-        for (int q = threadIdx.x; q < nr; q += blockDim.x) {
-            const int r = rows[q];
-            if (r != pr) A[r * Ne + kc] = cmul(A[r * Ne + kc], pinv);
+        // multipliers of the remaining rows: only the warps that form them
+        // take the FP64 reciprocal (the FP64 pipe charges every issuing warp)
+        if (threadIdx.x < nr) {
+            const double2 pinv = crcp(pv);
+            for (int q = threadIdx.x; q < nr; q += blockDim.x) {
+                const int r = rows[q];
+                if (r != pr) A[r * Ne + kc] = cmul(A[r * Ne + kc], pinv);
+            }
+            if (threadIdx.x == 0) dinv[kc] = pinv;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             perm[kc] = pr;
-            dinv[kc] = pinv;
             rows[ppos] = rows[nr - 1];
         }
         const int nrow = nr - 1;  // rows to update (the list without pr)
@@ -632,17 +825,28 @@ __global__ void __launch_bounds__(512, 1) k_hop(DevState s, double dt, double ma
         float cv = -1.0f;
         int ci = Ne;
         const int total = nrow * ncol;
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int qq = idx / ncol, c = kc + 1 + (idx - qq * ncol);
-            // list position qq of the list without pr: entry nr-1 moved into ppos
-            const int r = rows[(qq == ppos) ? nr - 1 : qq];
-            const double2 nv = cfms(A[r * Ne + c], A[r * Ne + kc], A[pr * Ne + c]);
-            A[r * Ne + c] = nv;
-            if (c == kc + 1) {
-                const float m2 = (float)(fabs(nv.x) + fabs(nv.y));
-                if (m2 > cv || (m2 == cv && r < ci)) {
-                    cv = m2;
-                    ci = r;
+        if (total > 0) {
+            // flattened (row, column) walk without a division per element
+            const int sq = blockDim.x / ncol, sc = blockDim.x - sq * ncol;
+            int qq = threadIdx.x / ncol, cc = threadIdx.x - qq * ncol;
+            for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+                const int c = kc + 1 + cc;
+                // list position qq of the list without pr: entry nr-1 moved into ppos
+                const int r = rows[(qq == ppos) ? nr - 1 : qq];
+                const double2 nv = cfms(A[r * Ne + c], A[r * Ne + kc], A[pr * Ne + c]);
+                A[r * Ne + c] = nv;
+                if (cc == 0) {
+                    const float m2 = (float)(fabs(nv.x) + fabs(nv.y));
+                    if (m2 > cv || (m2 == cv && r < ci)) {
+                        cv = m2;
+                        ci = r;
+                    }
+                }
+                cc += sc;
+                qq += sq;
+                if (cc >= ncol) {
+                    cc -= ncol;
+                    ++qq;
                 }
             }
         }
@@ -663,14 +867,6 @@ __global__ void __launch_bounds__(512, 1) k_hop(DevState s, double dt, double ma
         __syncthreads();
     }
     if (singular && threadIdx.x == 0) atomicOr(&s.status[t], ST_SINGULAR);
-    if (!singular && threadIdx.x == 0) {
-        double logdet = 0.0;
-        for (int kc = 0; kc < Ne; ++kc) {
-            const double2 u = dinv[kc];  // 1/U_kk
-            logdet -= 0.5 * log(u.x * u.x + u.y * u.y);
-        }
-        s_det_abs = exp(logdet);
-    }
     const double v = s.p[t] / mass;
     const double geo_h = s.geo[t * 4], geo_dh = s.geo[t * 4 + 1], geo_k = s.geo[t * 4 + 2];
     const U4 rn = draw(seed, (uint32_t)t, kStreamHop, (uint64_t)s.nstep[t]);
@@ -679,6 +875,13 @@ __global__ void __launch_bounds__(512, 1) k_hop(DevState s, double dt, double ma
 
     bool do_ratios = !singular;
     if (do_ratios && skip_bound && g_out == nullptr) {
+        // |det S| = prod |U_kk| from the stored reciprocals, as a sum of logs
+        double lg = 0.0;
+        for (int kc = threadIdx.x; kc < Ne; kc += blockDim.x) {
+            const double2 u = dinv[kc];  // 1/U_kk
+            lg -= 0.5 * log(u.x * u.x + u.y * u.y);
+        }
+        const double det_abs = exp(block_sum(lg, red));
         // upper bound of the total hop probability (Sec. II C): |<J|psi>| <= 1
         double part = 0.0;
         for (int idx = threadIdx.x; idx < Ne * nu; idx += blockDim.x) {
@@ -687,7 +890,7 @@ __global__ void __launch_bounds__(512, 1) k_hop(DevState s, double dt, double ma
             part += fabs(nac(lam_s[m], q0_s[m], lam_s[sa], q0_s[sa], geo_h, geo_dh, geo_k));
         }
         const double sd = block_sum(part, red);
-        const double bound = 2.0 * dt * fabs(v) * sd / s_det_abs;
+        const double bound = 2.0 * dt * fabs(v) * sd / det_abs;
         if (bound * (1.0 + 1e-9) < zeta) do_ratios = false;
     }
 
@@ -1119,6 +1322,22 @@ void cheb_shape(int N, int Ne, int &ept, int &G)
 cudaError_t launch_cheb(const DevState &s, double dt, bool mixed, cudaStream_t st)
 {
     if (s.n == 0) return cudaSuccess;
+    if (mixed) {
+        int G;
+        cheb32_shape(s.N, s.Ne, G);
+        if (s.cheb_G > 0 && s.cheb_ept == 4) G = s.cheb_G;
+        const int nb = 4 * G, nq = (s.N + 3) / 4;
+        const size_t smem = cheb32_smem_bytes(s.N, G);
+        const int threads = (G * nq + 31) & ~31;
+        for (int64_t t0 = 0; t0 < s.n; t0 += 65535) {
+            const int64_t cnt = (s.n - t0 < 65535) ? s.n - t0 : 65535;
+            dim3 grid((unsigned)((s.Ne + nb - 1) / nb), (unsigned)cnt);
+            k_cheb_f32t<4><<<grid, threads, smem, st>>>(s, dt, G, t0);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     int ept, G;
     cheb_shape(s.N, s.Ne, ept, G);
     if (s.cheb_ept > 0 && s.cheb_G > 0) {
@@ -1126,25 +1345,20 @@ cudaError_t launch_cheb(const DevState &s, double dt, bool mixed, cudaStream_t s
         G = s.cheb_G;
     }
     const int nb = G * ept;
-    const size_t smem = (size_t)s.N * 2 * nb * (mixed ? sizeof(float) : sizeof(double));
+    const size_t smem = (size_t)s.N * 2 * nb * sizeof(double);
     const int threads = (G * s.N + 31) & ~31;
     for (int64_t t0 = 0; t0 < s.n; t0 += 65535) {
         const int64_t cnt = (s.n - t0 < 65535) ? s.n - t0 : 65535;
         dim3 grid((unsigned)((s.Ne + nb - 1) / nb), (unsigned)cnt);
-        if (mixed) {
-            if (ept == 2) k_cheb<2, float><<<grid, threads, smem, st>>>(s, dt, G, t0);
-            else k_cheb<1, float><<<grid, threads, smem, st>>>(s, dt, G, t0);
-        } else {
-            if (ept == 2) k_cheb<2, double><<<grid, threads, smem, st>>>(s, dt, G, t0);
-            else k_cheb<1, double><<<grid, threads, smem, st>>>(s, dt, G, t0);
-        }
+        if (ept == 2) k_cheb<2, double><<<grid, threads, smem, st>>>(s, dt, G, t0);
+        else k_cheb<1, double><<<grid, threads, smem, st>>>(s, dt, G, t0);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-// Allow the hop kernels the device's full opt-in shared memory (minus their
+// Allow the hop kernels and the tiled FP32 propagator the device's full opt-in shared memory (minus their
 // static shared memory), so that later launches, including launches under
 // stream capture, need no attribute change.
 template <class F>
@@ -1164,6 +1378,7 @@ void configure_hop_smem()
 {
     allow_max_smem(k_hop<float2>);
     allow_max_smem(k_hop<double2>);
+    allow_max_smem(k_cheb_f32t<4>);
 }
 
 cudaError_t launch_hop(const DevState &s, double dt, double mass, uint64_t seed, int skip_bound,

@@ -14,9 +14,28 @@ from . import iesh as _I
 _CACHE = {}
 
 
-def cheb_candidates(N, Ne, limit=6):
-    """Propagator shapes ranked by lane and electron-slot efficiency."""
+def cheb_candidates(N, Ne, limit=6, precision=0):
+    """Propagator shapes ranked by lane and electron-slot efficiency.
+
+    FP64: (ept, G) with ept 1 or 2 electrons per thread and G * N <= 1024
+    threads.  Mixed precision: (4, G), 4 orbitals x 4 electrons per thread
+    and G * ceil(N / 4) <= 256 threads, two buffers of Np x (8G + 1) floats
+    (Np = N rounded up to a multiple of 4) in at most 110 KiB."""
     out = []
+    if precision == _I.PREC_MIXED:
+        nq = -(-N // 4)
+        Np = 4 * nq
+        for G in range(1, 256 // nq + 1):
+            if G > 1 and 2 * (Np * 8 * G + Np) * 4 > 110 * 1024:
+                break
+            nb = 4 * G
+            if nb > 4 * Ne + 3:
+                break
+            thr32 = (G * nq + 31) // 32 * 32
+            eff = G * nq / thr32 * Ne / (-(-Ne // nb) * nb)
+            out.append((eff, nb, 4, G))
+        out.sort(key=lambda r: (-r[0], -r[1]))
+        return [(ept, G) for _, _, ept, G in out[:limit]]
     for ept in (2, 1):
         for G in range(1, 1024 // N + 1):
             nb = G * ept
@@ -55,7 +74,7 @@ def autotune(ctx, x, p, occ, C, dt, steps=3, seed=0):
         scratch.profile(False)
         return prof["propagate"][0], prof["hop"][0]
 
-    for ept, G in cheb_candidates(ctx.N, ctx.Ne):
+    for ept, G in cheb_candidates(ctx.N, ctx.Ne, precision=ctx.precision):
         times_cheb[(ept, G)] = trial(ept, G, 0)[0]
     for hop in (256, 512):
         ept, G = min(times_cheb, key=times_cheb.get)

@@ -74,18 +74,21 @@ def test_graph_replay_matches_eager(P):
         assert np.array_equal(res[0][k], res[1][k]), k
 
 
-def test_autotuned_shapes_keep_results(P):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotuned_shapes_keep_results(P, precision):
     from paper_2212_00518_gb300 import tuning
     md = W.double_well(60)
     n = 64
     x, p = W.thermal_harmonic(n, md["mass"], md["par"][0], 0.01, 5)
     occ = W.random_occupations(n, 61, 30, 6)
     C = W.mixed_coefficients(occ, 61, 7, 0.5)
-    base = P.Context(md, n)
+    if precision:
+        C = C.astype(np.complex64)
+    base = P.Context(md, n, precision=precision)
     base.set_state(x, p, occ, C)
     base.run(1.0, 5, seed=1)
     ref = base.get_state()
-    tuned = P.Context(md, n)
+    tuned = P.Context(md, n, precision=precision)
     best = tuning.autotune(tuned, x, p, occ, C, 1.0, steps=2)
     assert tuned.kernel_shape()[:2] == tuple(best["cheb"])
     tuned.set_state(x, p, occ, C)
@@ -93,6 +96,14 @@ def test_autotuned_shapes_keep_results(P):
     st = tuned.get_state()
     for k in ("x", "p", "occ", "C"):
         assert np.array_equal(st[k], ref[k]), k
+    # every candidate shape gives the same bits
+    for ept, G in tuning.cheb_candidates(61, 30, precision=precision):
+        other = P.Context(md, n, precision=precision)
+        other.set_kernel_shape(ept, G, 0)
+        other.set_state(x, p, occ, C)
+        other.run(1.0, 5, seed=1)
+        assert np.array_equal(other.get_state()["C"], ref["C"]), (ept, G)
+        other.close()
 
 
 def test_scattering_model_matches_oracle(P):

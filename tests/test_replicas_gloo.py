@@ -51,3 +51,14 @@ def test_two_rank_aggregation():
         assert ms == 150.0 and e2e == 1.5
         assert value == pytest.approx(2 * 4096 * 10 / 0.150)
         assert seeds[0] != seeds[1]
+
+
+def test_single_rank_aggregation_of_host_time_only():
+    """The end-to-end leg passes no device time: no throughput, no error."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    agg = bench.aggregate(0.0, 2.5, 4096, 10, 1)
+    assert agg["e2e_s"] == 2.5 and agg["value"] is None
+    agg = bench.aggregate(200.0, 0.0, 4096, 10, 1)
+    assert agg["value"] == pytest.approx(4096 * 10 / 0.2)
