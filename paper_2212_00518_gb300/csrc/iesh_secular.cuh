@@ -29,7 +29,9 @@ struct Roundoff<float> {
 // estimate's relative error |e| far below 2^-18 the truncated e^3 term is
 // below 2^-54, so the result is within about an ulp of 1/d.  Three FMAs
 // replace a full division in the secular sums, which are the FP64-bound
-// part of the eigen solve.  Inputs are pole distances, never subnormal.
+// part of the eigen solve, and in the couplings d_jk.  Inputs are pole
+// distances and eigenvalue gaps, never subnormal (the estimate flushes
+// subnormal inputs to zero).
 template <class R>
 __device__ __forceinline__ R pole_recip(R d)
 {
@@ -55,10 +57,13 @@ __device__ __forceinline__ double pole_recip<double>(double d)
 // (eps_o - eps_k) + tau keeps full relative accuracy.
 template <class R>
 struct Sec {
-    R g, gp, gp_rest, sabs;
+    R g, gp, gp_rest, qo, sabs;
 };
 
-template <class R>
+// With ABS the sum of |z_k^2 / (lam - eps_k)| over k != o (the scale of the
+// rounding error of g, for the stopping test) is accumulated into e.sabs;
+// without it e.sabs is left at zero for the caller to fill in.
+template <class R, bool ABS>
 __device__ __forceinline__ Sec<R> sec_eval(int M, const R *__restrict__ eps, const R *__restrict__ z2,
                                            int o, R tau, R eomh)
 {
@@ -71,7 +76,7 @@ __device__ __forceinline__ Sec<R> sec_eval(int M, const R *__restrict__ eps, con
         if (k != o) {
             s1 += q;
             s2 = fma(q, r, s2);
-            sa += fabs(q);
+            if (ABS) sa += fabs(q);
         }
     }
     const R qo = z2[o] / tau;
@@ -79,7 +84,8 @@ __device__ __forceinline__ Sec<R> sec_eval(int M, const R *__restrict__ eps, con
     e.g = (eomh + tau) - s1 - qo;
     e.gp_rest = R(1) + s2;
     e.gp = e.gp_rest + qo / tau;
-    e.sabs = sa + fabs(qo) + fabs(eomh) + fabs(tau);
+    e.qo = qo;
+    e.sabs = sa;
     return e;
 }
 
@@ -96,9 +102,20 @@ __device__ bool sec_iterate(int M, const R *__restrict__ eps, const R *__restric
     const R u = Roundoff<R>::u;
     const R eomh = eps[o] - h;
     const R s = z2[o];
+    // the non-origin part of the error scale varies slowly with tau (those
+    // poles are at least half a gap away): take it from the first evaluation
+    R sa_rest;
+    if (have) {
+        sa_rest = e.sabs;
+    } else {
+        e = sec_eval<R, true>(M, eps, z2, o, tau, eomh);
+        sa_rest = e.sabs;
+        have = true;
+    }
     for (int it = 0; it < 80; ++it) {
-        if (!have) e = sec_eval<R>(M, eps, z2, o, tau, eomh);
+        if (!have) e = sec_eval<R, false>(M, eps, z2, o, tau, eomh);
         have = false;
+        e.sabs = sa_rest + fabs(e.qo) + fabs(eomh) + fabs(tau);
         if (fabs(e.g) <= R(8) * u * e.sabs) return true;
         if (e.g < R(0)) lo = tau;
         else hi = tau;
@@ -126,11 +143,11 @@ __device__ bool sec_iterate(int M, const R *__restrict__ eps, const R *__restric
         const bool tiny = fabs(tn - tau) <= R(2) * u * fabs(tn);
         tau = tn;
         if (tiny) {
-            e = sec_eval<R>(M, eps, z2, o, tau, eomh);
+            e = sec_eval<R, false>(M, eps, z2, o, tau, eomh);
             return true;
         }
     }
-    e = sec_eval<R>(M, eps, z2, o, tau, eomh);
+    e = sec_eval<R, false>(M, eps, z2, o, tau, eomh);
     return false;
 }
 
@@ -166,7 +183,7 @@ __device__ void secular_root(int r, int M, const R *__restrict__ eps, const R *_
                 conv = sec_iterate<R>(M, eps, z2, h, o, kind, D, lo, hi, tau, e, false);
             }
         } else {
-            const Sec<R> em = sec_eval<R>(M, eps, z2, L, R(0.5) * D, eps[L] - h);
+            const Sec<R> em = sec_eval<R, true>(M, eps, z2, L, R(0.5) * D, eps[L] - h);
             if (em.g >= R(0)) {
                 o = L; kind = 0; lo = 0; hi = R(0.5) * D; tau = R(0.5) * D; e = em; have = true;
             } else {

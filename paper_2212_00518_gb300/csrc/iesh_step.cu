@@ -1,5 +1,5 @@
 // iesh_step.cu -- kernels of one batched IESH step (sm_103a), FP64 and the
-// mixed-precision variants (k_build_w_f32, k_cheb_f32t, k_hop<float2>).
+// mixed-precision variants (k_build_w_f32, k_cheb_f32t, k_hop<float2, ...>).
 //
 // One trajectory step (Gardner et al., arXiv:2212.00518, Sec. II B-C):
 //   k_eigen     velocity-Verlet kick + drift, eigenpairs of the arrowhead
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(512, 1) k_eigen(DevState s, ModelDev md, doubl
     double *q0_s = lam_s + N;                            // [N]
     double *misc = q0_s + N;                             // Z2, force sum
     for (int k = threadIdx.x; k < M; k += blockDim.x) eps_s[k] = s.eps[k];
-    double x = 0.0, p = 0.0;
+    double x = 0.0, p = 0.0, guess = 0.0;
     ModelVals mv;
     if (act) {
         x = s.x[t];
@@ -65,7 +65,11 @@ __global__ void __launch_bounds__(512, 1) k_eigen(DevState s, ModelDev md, doubl
             x += dt * p / md.mass;
         }
         const double l = s.lam[t * N + r];
+        guess = l;
         if (mode == 1) {
+            // warm start from the linear extrapolation of the last two roots
+            // (lam_prev = lam after a cold start, so the first step uses lam)
+            guess = 2.0 * l - s.lam_prev[t * N + r];
             s.lam_prev[t * N + r] = l;
             s.q0_prev[t * N + r] = s.q0[t * N + r];
             if (r < 4) s.geo_prev[t * 4 + r] = s.geo[t * 4 + r];
@@ -89,7 +93,10 @@ __global__ void __launch_bounds__(512, 1) k_eigen(DevState s, ModelDev md, doubl
         const double Z2 = misc[0];
         double l, q;
         if (Z2 > 0.0) {
-            secular_root<double>(r, M, eps_s, z2_s, mv.h, Z2, mode == 1, lam_s[r], l, q, st);
+            // an extrapolation outside the root's pole gap falls back to lam
+            const double glo = r > 0 ? eps_s[r - 1] : -INFINITY, ghi = r < M ? eps_s[r] : INFINITY;
+            if (!(guess > glo && guess < ghi)) guess = lam_s[r];
+            secular_root<double>(r, M, eps_s, z2_s, mv.h, Z2, mode == 1, guess, l, q, st);
         } else {
             // no coupling: the eigenvalues are h and the bath energies
             int pos = 0;
@@ -99,6 +106,7 @@ __global__ void __launch_bounds__(512, 1) k_eigen(DevState s, ModelDev md, doubl
         }
         s.lam[t * N + r] = l;
         s.q0[t * N + r] = q;
+        if (mode == 0) s.lam_prev[t * N + r] = l;
         lam_s[r] = l;
         q0_s[r] = q;
         if (st) atomicOr(&s.status[t], st);
@@ -150,7 +158,7 @@ __global__ void k_force(DevState s)
 __device__ __forceinline__ double nac(double lj, double qj, double lk, double qk, double h,
                                       double dh, double kap)
 {
-    return qj * qk * (dh + kap * (lj + lk - 2.0 * h)) / (lk - lj);
+    return qj * qk * (dh + kap * (lj + lk - 2.0 * h)) * pole_recip<double>(lk - lj);
 }
 
 // Bessel J_0..J_K(rho) by Miller's backward recurrence normalised with
@@ -670,8 +678,18 @@ __device__ __forceinline__ double2 cfms(double2 acc, double2 a, double2 b)  // a
 }
 __device__ __forceinline__ double2 crcp(double2 a)
 {
-    const double d = 1.0 / (a.x * a.x + a.y * a.y);
+    const double m = fma(a.x, a.x, a.y * a.y);
+    const double d = m >= 2.2250738585072014e-308 ? pole_recip<double>(m) : 1.0 / m;
     return make_double2(a.x * d, -a.y * d);
+}
+// Pivot key of a complex entry: max(|re|, |im|) to 20 mantissa bits, from
+// the high words of the doubles (integer ops: the FP64 pipe is the
+// bottleneck of the factorisation).  Monotonic in the magnitude; 0 only for
+// zero (or below 2^-1042) entries; -1 marks "no candidate".
+__device__ __forceinline__ int pivot_key(double2 v)
+{
+    const int a = __double2hiint(v.x) & 0x7fffffff, b = __double2hiint(v.y) & 0x7fffffff;
+    return a > b ? a : b;
 }
 __device__ __forceinline__ double2 to_d2(double2 v) { return v; }
 __device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
@@ -706,9 +724,11 @@ size_t hop_smem_bytes(int N, int Ne) { return hop_smem_bytes(N, Ne, false); }
 // CT: coefficient type.  double2: the FP64 path.  float2: the mixed path --
 // S is widened to FP64 and factorised in FP64 (the overlap inverse), then
 // L and U are rounded to FP32 for the substitutions over the unoccupied rows.
-template <class CT>
-__global__ void __launch_bounds__(512, 1) k_hop(DevState s, double dt, double mass, uint64_t seed,
-                                                int skip_bound, double *g_out)
+// MAXT/MINB: launch bounds of the instantiation (512 x 1 for large S, 256 x
+// 3 when three CTAs fit in shared memory).
+template <class CT, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, double mass, uint64_t seed,
+                                                    int skip_bound, double *g_out)
 {
     constexpr bool kF32 = sizeof(CT) == sizeof(float2);
     extern __shared__ __align__(16) unsigned char hop_smem[];
@@ -722,7 +742,7 @@ __global__ void __launch_bounds__(512, 1) k_hop(DevState s, double dt, double ma
     double *lam_s = reinterpret_cast<double *>(dinv + Ne);         // [N]
     double *q0_s = lam_s + N;                                     // [N]
     double *red = q0_s + N;                                       // [64]
-    float *cand_v = reinterpret_cast<float *>(red + 64);          // [2][32] |a| per warp
+    int *cand_v = reinterpret_cast<int *>(red + 64);              // [2][32] pivot key per warp
     int *cand_i = reinterpret_cast<int *>(cand_v + 64);           // [2][32] row per warp
     int *occ_s = cand_i + 64;                                     // [Ne]
     int *perm = occ_s + Ne;                                       // [Ne] pivot k -> row
@@ -758,13 +778,12 @@ __global__ void __launch_bounds__(512, 1) k_hop(DevState s, double dt, double ma
             if (!isocc[m]) unocc[u++] = m;
     }
     __syncthreads();
-    // pivot candidates of column 0 (|re| + |im| rounded to FP32 is enough to pick a pivot)
+    // pivot candidates of column 0
     if (lane == 0) {
-        float bv = -1.0f;
+        int bv = -1;
         int bi = Ne;
         for (int r = warp; r < Ne; r += nwarp) {
-            const double2 v = A[r * Ne];
-            const float m2 = (float)(fabs(v.x) + fabs(v.y));
+            const int m2 = pivot_key(A[r * Ne]);
             if (m2 > bv) {
                 bv = m2;
                 bi = r;
@@ -785,21 +804,21 @@ __global__ void __launch_bounds__(512, 1) k_hop(DevState s, double dt, double ma
     int nr = Ne;
     for (int kc = 0; kc < Ne; ++kc) {
         const int buf = kc & 1;
-        float bv = -1.0f;
+        int bv = -1;
         int pr = Ne;
         for (int w = 0; w < nwarp; ++w) {
-            const float vv = cand_v[buf * 32 + w];
+            const int vv = cand_v[buf * 32 + w];
             const int i = cand_i[buf * 32 + w];
             if (vv > bv || (vv == bv && i < pr)) {
                 bv = vv;
                 pr = i;
             }
         }
-        const double2 pv = A[pr * Ne + kc];
-        if (!(pv.x != 0.0 || pv.y != 0.0)) {
+        if (bv <= 0) {  // zero pivot column
             singular = true;
             break;
         }
+        const double2 pv = A[pr * Ne + kc];
         // remove pr from the row list (every thread does the same edit on a
         // private copy of the position; thread 0 writes it after the barrier)
         int ppos = 0;
@@ -822,7 +841,7 @@ __global__ void __launch_bounds__(512, 1) k_hop(DevState s, double dt, double ma
         }
         const int nrow = nr - 1;  // rows to update (the list without pr)
         const int ncol = Ne - kc - 1;
-        float cv = -1.0f;
+        int cv = -1;
         int ci = Ne;
         const int total = nrow * ncol;
         if (total > 0) {
@@ -836,7 +855,7 @@ __global__ void __launch_bounds__(512, 1) k_hop(DevState s, double dt, double ma
                 const double2 nv = cfms(A[r * Ne + c], A[r * Ne + kc], A[pr * Ne + c]);
                 A[r * Ne + c] = nv;
                 if (cc == 0) {
-                    const float m2 = (float)(fabs(nv.x) + fabs(nv.y));
+                    const int m2 = pivot_key(nv);
                     if (m2 > cv || (m2 == cv && r < ci)) {
                         cv = m2;
                         ci = r;
@@ -852,7 +871,7 @@ __global__ void __launch_bounds__(512, 1) k_hop(DevState s, double dt, double ma
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, cv, o);
+            const int ov = __shfl_xor_sync(0xffffffffu, cv, o);
             const int oi = __shfl_xor_sync(0xffffffffu, ci, o);
             if (ov > cv || (ov == cv && oi < ci)) {
                 cv = ov;
@@ -1376,8 +1395,10 @@ static void allow_max_smem(F *fn)
 
 void configure_hop_smem()
 {
-    allow_max_smem(k_hop<float2>);
-    allow_max_smem(k_hop<double2>);
+    allow_max_smem(k_hop<float2, 512, 1>);
+    allow_max_smem(k_hop<double2, 512, 1>);
+    allow_max_smem(k_hop<float2, 256, 3>);
+    allow_max_smem(k_hop<double2, 256, 3>);
     allow_max_smem(k_cheb_f32t<4>);
 }
 
@@ -1386,21 +1407,25 @@ cudaError_t launch_hop(const DevState &s, double dt, double mass, uint64_t seed,
 {
     if (s.n == 0) return cudaSuccess;
     const size_t smem = hop_smem_bytes(s.N, s.Ne, mixed);
-    // two 256-thread CTAs per SM when the shared memory allows, else one of 512
+    // 256-thread CTAs (three per SM) when two or more fit in shared memory,
+    // else one CTA of 512
     int threads = (2 * smem + 2048 <= 227 * 1024) ? 256 : 512;
     if (s.hop_threads > 0) threads = s.hop_threads;
     // the shared-memory limit is a function attribute, not a stream operation;
     // set it outside stream capture (contexts set it when they are created)
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cs);
+    auto go = [&](auto kern) {
+        if (cs == cudaStreamCaptureStatusNone)
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<(unsigned)s.n, threads, smem, st>>>(s, dt, mass, seed, skip_bound, g_out);
+    };
     if (mixed) {
-        if (cs == cudaStreamCaptureStatusNone)
-            cudaFuncSetAttribute(k_hop<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_hop<float2><<<(unsigned)s.n, threads, smem, st>>>(s, dt, mass, seed, skip_bound, g_out);
+        if (threads == 256) go(k_hop<float2, 256, 3>);
+        else go(k_hop<float2, 512, 1>);
     } else {
-        if (cs == cudaStreamCaptureStatusNone)
-            cudaFuncSetAttribute(k_hop<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_hop<double2><<<(unsigned)s.n, threads, smem, st>>>(s, dt, mass, seed, skip_bound, g_out);
+        if (threads == 256) go(k_hop<double2, 256, 3>);
+        else go(k_hop<double2, 512, 1>);
     }
     return cudaGetLastError();
 }
