@@ -64,6 +64,8 @@ typedef enum {
 #define IESH_TRAJ_NAN 0x4u             /* non-finite nucleus or force */
 #define IESH_TRAJ_DONE 0x8u            /* trajectory finished (left the surface) */
 #define IESH_TRAJ_PROP_RANGE 0x10u     /* propagator needed more terms than built */
+#define IESH_TRAJ_TC_WAIT 0x20u        /* a tensor-core completion wait gave up (the
+                                          step's coefficients were not updated) */
 
 /* Model kinds (Sec. II A; Sec. III B double well; Sec. III C desorption model). */
 enum {

@@ -371,6 +371,7 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
     d.live = (opt->compact_every > 0) ? ctx->live : nullptr;
     d.n_live = ctx->n_live;
     configure_hop_smem();
+    configure_cheb_tc();
     {
         std::vector<float> ed((size_t)M * M);
         for (int a = 0; a < M; ++a)
@@ -589,11 +590,14 @@ iesh_status iesh_set_kernel_shape(iesh_ctx *ctx, int cheb_ept, int cheb_G, int h
     if (!ctx) return IESH_EINVAL;
     if (ctx->opt.precision == IESH_PREC_MIXED) {
         const int nq = (ctx->N + 3) / 4;
-        if (!((cheb_ept == 0 && cheb_G == 0) ||
-              (cheb_ept == 4 && cheb_G > 0 && cheb_G * nq <= 256 &&
-               cheb32_smem_bytes(ctx->N, cheb_G) <= kCheb32MaxSmem)))
-            return fail(ctx, IESH_EINVAL, "mixed propagator shape (%d, %d) invalid for N=%d (need ept 4, G*ceil(N/4) <= 256)",
-                        cheb_ept, cheb_G, ctx->N);
+        const bool simt = cheb_ept == 4 && cheb_G > 0 && cheb_G * nq <= 256 &&
+                          cheb32_smem_bytes(ctx->N, cheb_G) <= kCheb32MaxSmem;
+        const bool tc = cheb_ept == 8 && cheb_G == 1 && cheb_tc_eligible(ctx->N, ctx->Ne);
+        if (!((cheb_ept == 0 && cheb_G == 0) || simt || tc))
+            return fail(ctx, IESH_EINVAL,
+                        "mixed propagator shape (%d, %d) invalid for N=%d, Ne=%d (need ept 4 with "
+                        "G*ceil(N/4) <= 256, or ept 8, G 1 for the tensor-core kernel: N <= 128, Ne <= 56)",
+                        cheb_ept, cheb_G, ctx->N, ctx->Ne);
     } else if (cheb_ept < 0 || cheb_ept > 2 || cheb_G < 0 || (cheb_ept > 0) != (cheb_G > 0) ||
                cheb_G * ctx->N > 1024) {
         return fail(ctx, IESH_EINVAL, "propagator shape (%d, %d) invalid for N=%d", cheb_ept, cheb_G, ctx->N);
@@ -611,7 +615,10 @@ iesh_status iesh_get_kernel_shape(iesh_ctx *ctx, int *cheb_ept, int *cheb_G, int
     if (!ctx) return IESH_EINVAL;
     int e = ctx->ds.cheb_ept, g = ctx->ds.cheb_G;
     if (e == 0) {
-        if (ctx->opt.precision == IESH_PREC_MIXED) {
+        if (ctx->opt.precision == IESH_PREC_MIXED && cheb_tc_eligible(ctx->N, ctx->Ne)) {
+            e = 8;
+            g = 1;
+        } else if (ctx->opt.precision == IESH_PREC_MIXED) {
             e = 4;
             cheb32_shape(ctx->N, ctx->Ne, g);
         } else {

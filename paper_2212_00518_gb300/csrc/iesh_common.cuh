@@ -18,6 +18,7 @@ enum : uint32_t {
     ST_NAN = 0x4u,
     ST_DONE = 0x8u,
     ST_PROP = 0x10u,
+    ST_TC_WAIT = 0x20u,
 };
 
 // Model constants passed by value to every kernel.

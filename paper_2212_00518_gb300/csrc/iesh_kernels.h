@@ -28,5 +28,11 @@ void cheb_shape(int N, int Ne, int &ept, int &G);
 constexpr size_t kCheb32MaxSmem = 110 * 1024;
 size_t cheb32_smem_bytes(int N, int G);
 void cheb32_shape(int N, int Ne, int &G);
+// FP32 propagator on the tensor cores (3xTF32), N <= 128 and Ne <= 56
+constexpr size_t kChebTcMaxSmem = 224 * 1024;
+size_t cheb_tc_smem_bytes(int N, int Ne);
+bool cheb_tc_eligible(int N, int Ne);
+void configure_cheb_tc();
+cudaError_t launch_cheb_tc(const DevState &s, double dt, cudaStream_t st);
 
 }  // namespace iesh

@@ -1342,6 +1342,9 @@ cudaError_t launch_cheb(const DevState &s, double dt, bool mixed, cudaStream_t s
 {
     if (s.n == 0) return cudaSuccess;
     if (mixed) {
+        // tensor cores (3xTF32) when the trajectory fits one CTA, unless a
+        // SIMT shape was requested
+        if (s.cheb_ept == 8 || (s.cheb_ept == 0 && cheb_tc_eligible(s.N, s.Ne))) return launch_cheb_tc(s, dt, st);
         int G;
         cheb32_shape(s.N, s.Ne, G);
         if (s.cheb_G > 0 && s.cheb_ept == 4) G = s.cheb_G;

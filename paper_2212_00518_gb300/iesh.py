@@ -276,10 +276,15 @@ class Context:
         return n.value
 
     def set_kernel_shape(self, cheb_ept=0, cheb_G=0, hop_threads=0):
+        """Propagator and hop kernel shapes (0 = built-in choice).  FP64:
+        cheb_ept 1 or 2 with G column groups.  Mixed: cheb_ept 4 with G
+        (SIMT kernel) or cheb_ept 8, G 1 (tensor-core kernel, N <= 128,
+        Ne <= 56; the default where eligible)."""
         self._check(self.L.iesh_set_kernel_shape(self._h, int(cheb_ept), int(cheb_G),
                                                  int(hop_threads)), "iesh_set_kernel_shape")
 
     def kernel_shape(self):
+        """(cheb_ept, cheb_G, hop_threads) in effect; cheb_ept 8 = tensor cores."""
         e, g, h = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
         self._check(self.L.iesh_get_kernel_shape(self._h, ctypes.addressof(e), ctypes.addressof(g),
                                                  ctypes.addressof(h)), "iesh_get_kernel_shape")

@@ -5,7 +5,10 @@ column groups per CTA) and of the hop kernel (threads per CTA) on a scratch
 context with the same model, precision and batch size, from the caller's
 state, and sets the fastest on the context.  Results do not depend on the
 shape (every output keeps its summation order), so tuning only changes
-speed.  Choices are cached per (N, Ne, precision, batch size) in-process.
+speed.  A mixed-precision context whose default propagator is the
+tensor-core kernel keeps it (its arithmetic differs from the SIMT shapes);
+only the hop kernel is tuned then.  Choices are cached per (N, Ne,
+precision, batch size) in-process.
 """
 import numpy as np
 
@@ -74,7 +77,9 @@ def autotune(ctx, x, p, occ, C, dt, steps=3, seed=0):
         scratch.profile(False)
         return prof["propagate"][0], prof["hop"][0]
 
-    for ept, G in cheb_candidates(ctx.N, ctx.Ne, precision=ctx.precision):
+    default = scratch.kernel_shape()[:2]
+    cands = [default] if default[0] == 8 else cheb_candidates(ctx.N, ctx.Ne, precision=ctx.precision)
+    for ept, G in cands:
         times_cheb[(ept, G)] = trial(ept, G, 0)[0]
     for hop in (256, 512):
         ept, G = min(times_cheb, key=times_cheb.get)

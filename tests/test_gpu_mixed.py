@@ -2,7 +2,9 @@
 
 Mixed path: eigenpairs, forces, the overlap LU and the rescale in FP64;
 coupling generator, Chebyshev propagation, coefficients and the ratio
-substitutions in FP32.  Stated error per output (against the FP64 oracle,
+substitutions in FP32.  The propagator runs on the tensor cores (3xTF32,
+tcgen05) for N <= 128 and Ne <= 56 and as a register-tiled SIMT kernel
+otherwise; both are checked here.  Stated error per output (against the FP64 oracle,
 from shared states; measured values on GB300 in brackets):
   hop probabilities g      relative to max g        2e-6   [2.9e-7]
   coefficients C, 1 step   absolute (unit columns)  1e-6   [1.8e-7]
@@ -45,13 +47,17 @@ def _state(md, n, seed, weight, shift):
     return x + shift, p, occ, C
 
 
-@pytest.mark.parametrize("name", list(CASES))
-def test_mixed_one_step(P, name):
+@pytest.mark.parametrize("name,kernel", [(k, "default") for k in CASES] + [("dw100", "simt"), ("paper40", "simt")])
+def test_mixed_one_step(P, name, kernel):
     md, dt, shift = CASES[name]
     n = 8
     x, p, occ, C = _state(md, n, 5, 0.6, shift)
     B = O.bind(md)
     ctx = P.Context(md, n, precision=P.PREC_MIXED)
+    if kernel == "simt":
+        ctx.set_kernel_shape(4, 1, 0)
+    else:
+        assert ctx.kernel_shape()[0] == (8 if md["M"] + 1 <= 128 else 4)
     ctx.set_state(x, p, occ, C.astype(np.complex64))
     g = ctx.hop_probabilities(dt)
     gref = []
@@ -69,13 +75,15 @@ def test_mixed_one_step(P, name):
         assert np.abs(st["C"][t].T - r["C"]).max() <= 1e-6
 
 
-@pytest.mark.parametrize("name", ["paper40", "dw100"])
-def test_mixed_100_steps(P, name):
+@pytest.mark.parametrize("name,kernel", [("paper40", "default"), ("dw100", "default"), ("dw100", "simt")])
+def test_mixed_100_steps(P, name, kernel):
     md, dt, shift = CASES[name]
     n, steps, every = 8, 100, 20
     x, p, occ, C = _state(md, n, 5, 0.6, shift)
     B = O.bind(md)
     ctx = P.Context(md, n, precision=P.PREC_MIXED, record_every=every, max_records=steps // every)
+    if kernel == "simt":
+        ctx.set_kernel_shape(4, 1, 0)
     ctx.set_state(x, p, occ, C.astype(np.complex64))
     ctx.run(dt, steps, seed=3)
     st = ctx.get_state()

@@ -96,14 +96,23 @@ def test_autotuned_shapes_keep_results(P, precision):
     st = tuned.get_state()
     for k in ("x", "p", "occ", "C"):
         assert np.array_equal(st[k], ref[k]), k
-    # every candidate shape gives the same bits
+    # every SIMT candidate shape gives the same bits (for the mixed path the
+    # default is the tensor-core kernel, whose arithmetic differs)
+    first = None
     for ept, G in tuning.cheb_candidates(61, 30, precision=precision):
         other = P.Context(md, n, precision=precision)
         other.set_kernel_shape(ept, G, 0)
         other.set_state(x, p, occ, C)
         other.run(1.0, 5, seed=1)
-        assert np.array_equal(other.get_state()["C"], ref["C"]), (ept, G)
+        Co = other.get_state()["C"]
         other.close()
+        if precision == 0:
+            assert np.array_equal(Co, ref["C"]), (ept, G)
+        elif first is None:
+            first = Co
+            assert np.abs(Co - ref["C"]).max() <= 2e-6
+        else:
+            assert np.array_equal(Co, first), (ept, G)
 
 
 def test_scattering_model_matches_oracle(P):
