@@ -33,10 +33,19 @@ UNIT = "traj-steps/s"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 nominal FP64 rate (recipe's nominal table)
 FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 SIMT at the maximum SM clock
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 tensor rate
 # DRAM bytes (read + write) per trajectory of the dominant kernel, from the ncu capture in
 # profiles/iesh_fp64_step_M100.md (1024-trajectory launch, scaled per trajectory; the
 # traffic is per-trajectory W and C streams, so it grows in proportion to the batch).
-KCHEB_FP64_TRAFFIC_PER_TRAJ = (407.724544e6 + 69.759744e6) / 1024
+KCHEB_FP64_TRAFFIC_PER_TRAJ = (169.147904e6 + 48.495360e6) / 1024
+
+
+def measured_peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def workload(M=100, n_traj=4096, dt=1.0):
@@ -199,8 +208,9 @@ def run_ours(args):
         cm, ms_m, prof_m, _ = measure(P.PREC_MIXED, False)
         Km = cm.propagator_terms()
         bad_m = int(np.count_nonzero(cm.get_state()["status"]))
+        tc_m = cm.kernel_shape()[0] == 8  # tensor-core propagator in use
         cm.close()
-        mixed = (ms_m, prof_m, Km, bad_m)
+        mixed = (ms_m, prof_m, Km, bad_m, tc_m)
 
     # ---- end to end through the C-ABI with pinned host buffers
     N, Ne = md["M"] + 1, md["Ne"]
@@ -261,21 +271,40 @@ def run_ours(args):
             "impl": "ours",
         }
         if mixed is not None:
-            ms_m, prof_m, Km, bad_m = mixed
+            ms_m, prof_m, Km, bad_m, tc_m = mixed
             pm_ms, pm_n = prof_m["propagate"]
             fl_m = float(np.sum(Km.astype(np.float64))) * 4.0 * N * N * Ne
             ach_m = fl_m / (pm_ms / pm_n / 1e3) / 1e12 if pm_n else None
             tot_m = max(1e-9, sum(u[0] for u in prof_m.values()))
+            if tc_m:
+                bf16 = measured_peaks().get("bf16_tflops")
+                peak_m = bf16 * TF32_PER_BF16 if bf16 else 1900.0 * TF32_PER_BF16
+                # executed tensor work: 3 TF32 products (3xTF32) on the padded tile
+                Kp, NB = (N + 7) // 8 * 8, (2 * Ne + 15) // 16 * 16
+                exe = ach_m * 3 * (128 * Kp * NB) / (N * N * 2 * Ne) if ach_m else None
+                roof_m = {"bound": "tensor", "kernel": "k_cheb_tc (tcgen05 kind::tf32, 3xTF32)",
+                          "achieved": ach_m, "peak": peak_m, "unit": "TFLOP/s",
+                          "frac": ach_m / peak_m if ach_m else None,
+                          "peak_source": ("of measured: MEASURED_PEAKS.json bf16_tflops x nominal "
+                                          "TF32/BF16 ratio 1.1/2.25" if bf16 else
+                                          "of fallback: 1.9 PFLOP/s bf16 x 1.1/2.25"),
+                          "executed_tflops": exe,
+                          "note": "achieved counts the FP32 contraction 4 N^2 Ne per order; the "
+                                  "kernel executes 3 TF32 products per FP32 product on a "
+                                  f"128 x {Kp} x {NB} tile",
+                          "mean_cheb_terms": float(Km.mean())}
+            else:
+                roof_m = {"bound": "alu", "kernel": "k_cheb_f32t (register-tiled FP32 SIMT)",
+                          "achieved": ach_m, "peak": FP32_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                          "frac": ach_m / FP32_NOMINAL_TFLOPS if ach_m else None,
+                          "peak_source": "nominal FP32 SIMT (152 SMs x 128 FMA x 2 x 2.07 GHz)",
+                          "mean_cheb_terms": float(Km.mean())}
             line["mixed"] = {
                 "value": world * n * args.steps / (ms_m / 1e3), "unit": UNIT,
                 "ms_per_step": ms_m / args.steps, "speedup_vs_fp64": ms / ms_m,
                 "dtype": "f32 propagation/coupling/ratio solves; f64 eigenpairs, overlap LU, rescale",
                 "kernel_time_share": {k: round(v[0] / tot_m, 4) for k, v in prof_m.items() if v[1]},
-                "roofline_propagate": {"bound": "alu", "achieved": ach_m,
-                                       "peak": FP32_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                                       "frac": ach_m / FP32_NOMINAL_TFLOPS if ach_m else None,
-                                       "peak_source": "nominal FP32 SIMT (152 SMs x 128 FMA x 2 x 2.07 GHz)",
-                                       "mean_cheb_terms": float(Km.mean())},
+                "roofline_propagate": roof_m,
                 "gpu_launches": int(sum(v[1] for v in prof_m.values())),
                 "status_nonzero": bad_m,
             }
