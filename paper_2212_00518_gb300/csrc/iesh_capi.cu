@@ -364,10 +364,13 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
     A(eps, (size_t)M) A(z0, (size_t)M)
     float *epsdiff = nullptr;
     A(epsdiff, (size_t)M * M)
+    double *poled = nullptr;
+    A(poled, (size_t)M * M)
 #undef A
     d.eps = eps;
     d.z0 = z0;
     d.epsdiff = epsdiff;
+    d.poled = poled;
     d.live = (opt->compact_every > 0) ? ctx->live : nullptr;
     d.n_live = ctx->n_live;
     configure_hop_smem();
@@ -376,7 +379,16 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
         std::vector<float> ed((size_t)M * M);
         for (int a = 0; a < M; ++a)
             for (int b = 0; b < M; ++b) ed[(size_t)a * M + b] = (float)(ctx->eps_h[a] - ctx->eps_h[b]);
-        cudaError_t e0 = cudaMemcpy(epsdiff, ed.data(), ed.size() * sizeof(float), cudaMemcpyHostToDevice);
+        std::vector<double> pd((size_t)M * M);
+        for (int k = 0; k < M; ++k)
+            for (int o = 0; o < M; ++o) pd[(size_t)k * M + o] = ctx->eps_h[o] - ctx->eps_h[k];
+        // on the context stream, after the zero fills of dalloc (a stream created
+        // non-blocking is not ordered with the legacy default stream)
+        cudaError_t e0 = cudaMemcpyAsync(epsdiff, ed.data(), ed.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                         ctx->stream);
+        if (e0 == cudaSuccess)
+            e0 = cudaMemcpyAsync(poled, pd.data(), pd.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+        if (e0 == cudaSuccess) e0 = cudaStreamSynchronize(ctx->stream);
         if (e0 != cudaSuccess) {
             *out = ctx;
             return fail(ctx, IESH_ECUDA, "table upload failed: %s", cudaGetErrorString(e0));

@@ -49,6 +49,7 @@ struct DevState {
     double z_done;
     const double *eps, *z0;    // bath [M]: energies and sqrt(Gamma/2pi) sqrt(w_k)
     const float *epsdiff;      // [M][M] eps_a - eps_b rounded to FP32 (mixed path)
+    const double *poled;       // [M][M] poled[k M + o] = eps_o - eps_k (secular sums)
     // work list: when live != nullptr the step kernels visit trajectory
     // live[w] for work item w < *n_live (compacted on the device)
     const int32_t *live;

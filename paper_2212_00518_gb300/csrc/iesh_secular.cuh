@@ -62,16 +62,19 @@ struct Sec {
 
 // With ABS the sum of |z_k^2 / (lam - eps_k)| over k != o (the scale of the
 // rounding error of g, for the stopping test) is accumulated into e.sabs;
-// without it e.sabs is left at zero for the caller to fill in.
-template <class R, bool ABS>
+// without it e.sabs is left at zero for the caller to fill in.  With TAB the
+// pole differences eps_o - eps_k come from the table diff[k M + o] (the same
+// rounded FP64 differences, one load instead of one FP64 subtraction).
+template <class R, bool ABS, bool TAB>
 __device__ __forceinline__ Sec<R> sec_eval(int M, const R *__restrict__ eps, const R *__restrict__ z2,
-                                           int o, R tau, R eomh)
+                                           const R *__restrict__ diff, int o, R tau, R eomh)
 {
     const R eo = eps[o];
     R s1 = 0, s2 = 0, sa = 0;
 #pragma unroll 4
     for (int k = 0; k < M; ++k) {
-        const R r = pole_recip<R>((eo - eps[k]) + tau);
+        const R dko = TAB ? diff[(size_t)k * M + o] : (eo - eps[k]);
+        const R r = pole_recip<R>(dko + tau);
         const R q = z2[k] * r;
         if (k != o) {
             s1 += q;
@@ -95,9 +98,10 @@ __device__ __forceinline__ Sec<R> sec_eval(int M, const R *__restrict__ eps, con
 // linear term for the two outermost roots (kind 2: below all poles, kind 3:
 // above), matched in value and slope; each model root is safeguarded by the
 // bracket [lo, hi] of sign changes.  On return e is evaluated at tau.
-template <class R>
-__device__ bool sec_iterate(int M, const R *__restrict__ eps, const R *__restrict__ z2, R h, int o,
-                            int kind, R D, R &lo, R &hi, R &tau, Sec<R> &e, bool have)
+template <class R, bool TAB>
+__device__ bool sec_iterate(int M, const R *__restrict__ eps, const R *__restrict__ z2,
+                            const R *__restrict__ diff, R h, int o, int kind, R D, R &lo, R &hi, R &tau,
+                            Sec<R> &e, bool have)
 {
     const R u = Roundoff<R>::u;
     const R eomh = eps[o] - h;
@@ -108,12 +112,12 @@ __device__ bool sec_iterate(int M, const R *__restrict__ eps, const R *__restric
     if (have) {
         sa_rest = e.sabs;
     } else {
-        e = sec_eval<R, true>(M, eps, z2, o, tau, eomh);
+        e = sec_eval<R, true, TAB>(M, eps, z2, diff, o, tau, eomh);
         sa_rest = e.sabs;
         have = true;
     }
     for (int it = 0; it < 80; ++it) {
-        if (!have) e = sec_eval<R, false>(M, eps, z2, o, tau, eomh);
+        if (!have) e = sec_eval<R, false, TAB>(M, eps, z2, diff, o, tau, eomh);
         have = false;
         e.sabs = sa_rest + fabs(e.qo) + fabs(eomh) + fabs(tau);
         if (fabs(e.g) <= R(8) * u * e.sabs) return true;
@@ -143,11 +147,11 @@ __device__ bool sec_iterate(int M, const R *__restrict__ eps, const R *__restric
         const bool tiny = fabs(tn - tau) <= R(2) * u * fabs(tn);
         tau = tn;
         if (tiny) {
-            e = sec_eval<R, false>(M, eps, z2, o, tau, eomh);
+            e = sec_eval<R, false, TAB>(M, eps, z2, diff, o, tau, eomh);
             return true;
         }
     }
-    e = sec_eval<R, false>(M, eps, z2, o, tau, eomh);
+    e = sec_eval<R, false, TAB>(M, eps, z2, diff, o, tau, eomh);
     return false;
 }
 
@@ -157,8 +161,10 @@ __device__ bool sec_iterate(int M, const R *__restrict__ eps, const R *__restric
 // `guess`, which lies in the same gap): origin = pole nearer the guess,
 // bracket = the whole gap, started at the guess; if the root ends in the
 // far half of the gap it is refined once more about the other pole.
-template <class R>
-__device__ void secular_root(int r, int M, const R *__restrict__ eps, const R *__restrict__ z2, R h,
+// TAB: diff holds the pole differences (see sec_eval); otherwise it is unused.
+template <class R, bool TAB = false>
+__device__ void secular_root(int r, int M, const R *__restrict__ eps, const R *__restrict__ z2,
+                             const R *__restrict__ diff, R h,
                              R Z2, bool warm, R guess, R &lam, R &q0, uint32_t &st)
 {
     int o, kind;
@@ -174,22 +180,22 @@ __device__ void secular_root(int r, int M, const R *__restrict__ eps, const R *_
             } else {
                 o = r; kind = 1; lo = -D; hi = 0; tau = guess - eps[r];
             }
-            conv = sec_iterate<R>(M, eps, z2, h, o, kind, D, lo, hi, tau, e, false);
+            conv = sec_iterate<R, TAB>(M, eps, z2, diff, h, o, kind, D, lo, hi, tau, e, false);
             if (kind == 0 && tau > R(0.5) * D) {
                 o = r; kind = 1; lo = fmin(lo - D, -R(0.5) * D); hi = 0; tau = tau - D;
-                conv = sec_iterate<R>(M, eps, z2, h, o, kind, D, lo, hi, tau, e, false);
+                conv = sec_iterate<R, TAB>(M, eps, z2, diff, h, o, kind, D, lo, hi, tau, e, false);
             } else if (kind == 1 && tau < -R(0.5) * D) {
                 o = L; kind = 0; lo = 0; hi = fmax(hi + D, R(0.5) * D); tau = tau + D;
-                conv = sec_iterate<R>(M, eps, z2, h, o, kind, D, lo, hi, tau, e, false);
+                conv = sec_iterate<R, TAB>(M, eps, z2, diff, h, o, kind, D, lo, hi, tau, e, false);
             }
         } else {
-            const Sec<R> em = sec_eval<R, true>(M, eps, z2, L, R(0.5) * D, eps[L] - h);
+            const Sec<R> em = sec_eval<R, true, TAB>(M, eps, z2, diff, L, R(0.5) * D, eps[L] - h);
             if (em.g >= R(0)) {
                 o = L; kind = 0; lo = 0; hi = R(0.5) * D; tau = R(0.5) * D; e = em; have = true;
             } else {
                 o = r; kind = 1; lo = -R(0.5) * D; hi = 0; tau = -R(0.5) * D;
             }
-            conv = sec_iterate<R>(M, eps, z2, h, o, kind, D, lo, hi, tau, e, have);
+            conv = sec_iterate<R, TAB>(M, eps, z2, diff, h, o, kind, D, lo, hi, tau, e, have);
         }
     } else {
         if (r == 0) {
@@ -211,7 +217,7 @@ __device__ void secular_root(int r, int M, const R *__restrict__ eps, const R *_
             const R tg = guess - eps[o];
             if (tg > lo && tg < hi) tau = tg;
         }
-        conv = sec_iterate<R>(M, eps, z2, h, o, kind, D, lo, hi, tau, e, false);
+        conv = sec_iterate<R, TAB>(M, eps, z2, diff, h, o, kind, D, lo, hi, tau, e, false);
     }
     if (!conv) st |= ST_SECULAR;
     lam = eps[o] + tau;

@@ -37,6 +37,24 @@ int eigen_tpb(int N)
     return best;
 }
 
+__host__ __device__ inline int eigen_pow2(int n)
+{
+    int p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+// red[0] <- sum of red[0..P) (P a power of two >= the slot width), halving
+// the active range each round; every thread of the CTA must call it.
+__device__ __forceinline__ void slot_tree_sum(double *red, int r, bool inslot, int P)
+{
+    __syncthreads();
+    for (int w = P >> 1; w > 0; w >>= 1) {
+        if (inslot && r < w) red[r] += red[r + w];
+        __syncthreads();
+    }
+}
+
 // mode 0: eigenpairs and force at the stored position (cold start);
 // mode 1: full first half of a step (kick, drift, eigenpairs, force, kick).
 // tpb trajectories per CTA, one thread per root.
@@ -48,12 +66,14 @@ __global__ void __launch_bounds__(512, 1) k_eigen(DevState s, ModelDev md, doubl
     const int r = threadIdx.x - slot * N;
     const int64_t t = slot < tpb ? traj_of(s, (int64_t)blockIdx.x * tpb + slot) : -1;
     const bool act = t >= 0 && !(s.status[t] & ST_DONE);
+    const int P = eigen_pow2(N);                         // reduction width
     double *eps_s = sh;                                  // [M], shared by the slots
-    const int per = M + 2 * N + 2;
+    const int per = M + 2 * N + P;
     double *z2_s = eps_s + M + (slot < tpb ? slot : 0) * per;  // [M]
     double *lam_s = z2_s + M;                            // [N]
     double *q0_s = lam_s + N;                            // [N]
-    double *misc = q0_s + N;                             // Z2, force sum
+    double *red_s = q0_s + N;                            // [P] slot reductions
+    const bool inslot = slot < tpb;
     for (int k = threadIdx.x; k < M; k += blockDim.x) eps_s[k] = s.eps[k];
     double x = 0.0, p = 0.0, guess = 0.0;
     ModelVals mv;
@@ -82,21 +102,21 @@ __global__ void __launch_bounds__(512, 1) k_eigen(DevState s, ModelDev md, doubl
         }
     }
     __syncthreads();
-    if (act && r == 0) {
-        double zs = 0.0;
-        for (int k = 0; k < M; ++k) zs += z2_s[k];
-        misc[0] = zs;
+    // Z2 = sum_k z_k^2 by a fixed-order tree over the slot's threads
+    if (inslot) {
+        red_s[r] = (act && r < M) ? z2_s[r] : 0.0;
+        if (r < P - N) red_s[N + r] = 0.0;
     }
-    __syncthreads();
+    slot_tree_sum(red_s, r, inslot, P);
     uint32_t st = 0;
     if (act) {
-        const double Z2 = misc[0];
+        const double Z2 = red_s[0];
         double l, q;
         if (Z2 > 0.0) {
             // an extrapolation outside the root's pole gap falls back to lam
             const double glo = r > 0 ? eps_s[r - 1] : -INFINITY, ghi = r < M ? eps_s[r] : INFINITY;
             if (!(guess > glo && guess < ghi)) guess = lam_s[r];
-            secular_root<double>(r, M, eps_s, z2_s, mv.h, Z2, mode == 1, guess, l, q, st);
+            secular_root<double, true>(r, M, eps_s, z2_s, s.poled, mv.h, Z2, mode == 1, guess, l, q, st);
         } else {
             // no coupling: the eigenvalues are h and the bath energies
             int pos = 0;
@@ -112,14 +132,22 @@ __global__ void __launch_bounds__(512, 1) k_eigen(DevState s, ModelDev md, doubl
         if (st) atomicOr(&s.status[t], st);
     }
     __syncthreads();
-    if (act && r == 0) {
-        const double kappa = (mv.f != 0.0) ? mv.df / mv.f : 0.0;
-        double dl = 0.0;
-        for (int a = 0; a < Ne; ++a) {
-            const int i = s.occ[t * Ne + a];
+    // occupied-surface term of the force, sum over the occupied orbitals in
+    // list order by a fixed-order tree (slot thread a takes electron a)
+    const double kappa = (act && mv.f != 0.0) ? mv.df / mv.f : 0.0;
+    if (inslot) {
+        double c = 0.0;
+        if (act && r < Ne) {
+            const int i = s.occ[t * Ne + r];
             const double q = q0_s[i];
-            dl += q * q * (mv.dh + 2.0 * kappa * (lam_s[i] - mv.h));
+            c = q * q * (mv.dh + 2.0 * kappa * (lam_s[i] - mv.h));
         }
+        red_s[r] = c;
+        if (r < P - N) red_s[N + r] = 0.0;
+    }
+    slot_tree_sum(red_s, r, inslot, P);
+    if (act && r == 0) {
+        const double dl = red_s[0];
         const double F = -mv.dU0 - dl;
         if (mode == 1) p += 0.5 * dt * F;
         s.x[t] = x;
@@ -1286,7 +1314,7 @@ cudaError_t launch_eigen(const DevState &s, const ModelDev &md, double dt, int m
     if (s.n == 0) return cudaSuccess;
     const int tpb = eigen_tpb(s.N);
     const int threads = round32(tpb * s.N);
-    const size_t smem = (size_t)(s.M + tpb * (s.M + 2 * s.N + 2)) * sizeof(double);
+    const size_t smem = (size_t)(s.M + tpb * (s.M + 2 * s.N + eigen_pow2(s.N))) * sizeof(double);
     k_eigen<<<(unsigned)((s.n + tpb - 1) / tpb), threads, smem, st>>>(s, md, dt, mode, tpb);
     return cudaGetLastError();
 }
@@ -1401,6 +1429,7 @@ void configure_hop_smem()
     allow_max_smem(k_hop<float2, 512, 1>);
     allow_max_smem(k_hop<double2, 512, 1>);
     allow_max_smem(k_hop<float2, 256, 3>);
+    allow_max_smem(k_hop<float2, 256, 4>);
     allow_max_smem(k_hop<double2, 256, 3>);
     allow_max_smem(k_cheb_f32t<4>);
 }
@@ -1424,7 +1453,7 @@ cudaError_t launch_hop(const DevState &s, double dt, double mass, uint64_t seed,
         kern<<<(unsigned)s.n, threads, smem, st>>>(s, dt, mass, seed, skip_bound, g_out);
     };
     if (mixed) {
-        if (threads == 256) go(k_hop<float2, 256, 3>);
+        if (threads == 256) go(k_hop<float2, 256, 4>);
         else go(k_hop<float2, 512, 1>);
     } else {
         if (threads == 256) go(k_hop<double2, 256, 3>);

@@ -75,6 +75,36 @@ def test_graph_replay_matches_eager(P):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+def test_contexts_on_a_nonblocking_stream(P, precision):
+    """Several contexts created and run on one non-blocking stream (as the
+    ensemble driver does) give the same bits as a context on the default
+    stream: the library orders its own uploads after its zero fills."""
+    import torch
+    md, x, p, occ, C = _mixed_direction_batch(20, 16, 5, bias=0.05)
+    if precision:
+        C = C.astype(np.complex64)
+    dt = 0.1 * W.FS_AU
+    ref = P.Context(md, 16, precision=precision)
+    ref.set_state(x, p, occ, C)
+    ref.run(dt, 20, seed=3)
+    want = ref.get_state()
+    assert np.all(np.isfinite(want["x"])) and np.all(want["status"] == 0)
+    s = torch.cuda.Stream()
+    ctxs = [P.Context(md, 16, precision=precision, stream=s.cuda_stream) for _ in range(4)]
+    with torch.cuda.stream(s):
+        for c in ctxs:
+            c.set_state(x, p, occ, C)
+            c.run(dt, 20, seed=3)
+    torch.cuda.synchronize()
+    for c in ctxs:
+        got = c.get_state()
+        for k in ("x", "p", "occ", "C", "status"):
+            assert np.array_equal(got[k], want[k]), k
+        c.close()
+    ref.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 def test_autotuned_shapes_keep_results(P, precision):
     from paper_2212_00518_gb300 import tuning
     md = W.double_well(60)
