@@ -20,7 +20,12 @@
  *   - determinants by Gaussian elimination, the overlap inverse by
  *     Gauss-Jordan elimination, and in "brute" mode one determinant per
  *     candidate configuration (Sec. II B, amplitude equations);
- *   - Gauss-Legendre nodes by the Golub-Welsch method (Appendix A).
+ *   - Gauss-Legendre nodes by the Golub-Welsch method (Appendix A);
+ *   - the diabatic-basis propagator variant (propagator kind 1): the step's
+ *     diabatic evolution split symmetrically, exp(-i H(x_1) dt/2)
+ *     exp(-i H(x_0) dt/2), written in the adiabatic frame as
+ *     c <- exp(-i L_1 dt/2) Q_1^T Q_0 exp(-i L_0 dt/2) c with the dense
+ *     eigenvector matrices Q_0, Q_1 of the two ends of the step (reading R9).
  *
  * Readings of the paper that the code takes (the paper is silent or garbled):
  *   R1 NAC sign: d_jk = <j|d_x k> = T_jk / (lambda_k - lambda_j), the TDSE is
@@ -39,6 +44,11 @@
  *      generator stored for the next step uses the post-hop velocity.
  *   R8 Gauss-Legendre split discretisation: M/2 nodes in each half, weights
  *      positive, V_k = sqrt(Gamma / 2 pi) sqrt(w_k) f(x).
+ *   R9 diabatic-basis propagation (an alternative to the exponential of the
+ *      averaged adiabatic generator): the electronic Hamiltonian in the
+ *      fixed diabatic basis is H(x); over a step the propagator is the
+ *      symmetric product of the half-step exponentials at the two ends,
+ *      which is second order in dt like R3 and exact for frozen nuclei.
  *
  * Impurity populations (traj_populations): the paper defers the definition
  * of the diabatic population P_d to another work, so two readings are
@@ -444,6 +454,36 @@ int orc_propagate(int N, int Ne, const double *lam0, const double *d0, double v0
     return rc;
 }
 
+/* Diabatic-basis propagator variant (reading R9) in the adiabatic frame:
+ * C <- exp(-i L1 dt/2) O exp(-i L0 dt/2) C with O = Q1^T Q0, the overlaps of
+ * the adiabatic orbitals at the end of the step with those at its start
+ * (Q[k*N + i] = component k of orbital i).  C is [N][Ne]. */
+void orc_propagate_overlap(int N, int Ne, const double *lam0, const double *Q0, const double *lam1,
+                           const double *Q1, double dt, cplx *C)
+{
+    double *O = malloc(sizeof(double) * N * N);
+    cplx *tmp = malloc(sizeof(cplx) * N * Ne);
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            double s = 0.0;
+            for (int k = 0; k < N; k++) s += Q1[k * N + i] * Q0[k * N + j];
+            O[i * N + j] = s;
+        }
+    for (int j = 0; j < N; j++) {
+        cplx ph = cexp(-I * lam0[j] * 0.5 * dt);
+        for (int e = 0; e < Ne; e++) tmp[j * Ne + e] = ph * C[j * Ne + e];
+    }
+    for (int i = 0; i < N; i++) {
+        cplx ph = cexp(-I * lam1[i] * 0.5 * dt);
+        for (int e = 0; e < Ne; e++) {
+            cplx s = 0.0;
+            for (int j = 0; j < N; j++) s += O[i * N + j] * tmp[j * Ne + e];
+            C[i * Ne + e] = ph * s;
+        }
+    }
+    free(O); free(tmp);
+}
+
 /* Determinant by Gaussian elimination with partial pivoting (A destroyed). */
 cplx orc_det(int n, cplx *A)
 {
@@ -723,13 +763,15 @@ static void traj_populations(const orc_model *md, const orc_traj *t, double *psh
  * hopping procedure of Sec. II B).  n = index of this step.  Optional
  * outputs of the step's hop probabilities g[Ne*N] and uniform zeta. */
 static void traj_step(const orc_model *md, orc_traj *t, double dt, uint64_t seed, uint32_t traj,
-                      uint64_t n, int brute, double *g_out, double *zeta_out, int *hop_out)
+                      uint64_t n, int brute, int prop, double *g_out, double *zeta_out, int *hop_out)
 {
     int N = md->M + 1, Ne = md->Ne;
     double m = md->mass;
     double *lam0 = malloc(sizeof(double) * N), *d0 = malloc(sizeof(double) * N * N);
+    double *Q0 = malloc(sizeof(double) * N * N);
     memcpy(lam0, t->lam, sizeof(double) * N);
     memcpy(d0, t->d, sizeof(double) * N * N);
+    memcpy(Q0, t->Q, sizeof(double) * N * N);
     double v0 = t->v_prev;
 
     t->p += 0.5 * dt * t->F;
@@ -740,7 +782,9 @@ static void traj_step(const orc_model *md, orc_traj *t, double dt, uint64_t seed
     t->p += 0.5 * dt * t->F;
     double v1 = t->p / m;
 
-    if (orc_propagate(N, Ne, lam0, d0, v0, t->lam, t->d, v1, dt, t->C) != 0)
+    if (prop == 1)
+        orc_propagate_overlap(N, Ne, lam0, Q0, t->lam, t->Q, dt, t->C);
+    else if (orc_propagate(N, Ne, lam0, d0, v0, t->lam, t->d, v1, dt, t->C) != 0)
         t->status |= ORC_ST_JACOBI_NONCONV;
 
     double *g = malloc(sizeof(double) * Ne * N);
@@ -782,7 +826,7 @@ static void traj_step(const orc_model *md, orc_traj *t, double dt, uint64_t seed
     if (hop_out) *hop_out = hopped;
     t->v_prev = t->p / m;
     if (!isfinite(t->x) || !isfinite(t->p)) t->status |= ORC_ST_NAN;
-    free(isocc); free(g); free(lam0); free(d0);
+    free(isocc); free(g); free(lam0); free(d0); free(Q0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -831,7 +875,7 @@ typedef struct {
     int64_t t0, t1, n_steps;
     double dt;
     uint64_t seed, step0;
-    int brute, record_every, n_rec;
+    int brute, prop, record_every, n_rec;
     double *x, *p, *F;
     int *occ;
     cplx *C;
@@ -859,8 +903,8 @@ static void *run_range(void *arg)
         t.frustrated = 0;
         traj_prepare(md, &t);
         for (int64_t s = 0; s < J->n_steps; s++) {
-            traj_step(md, &t, J->dt, J->seed, (uint32_t)i, J->step0 + (uint64_t)s, J->brute, NULL,
-                      NULL, NULL);
+            traj_step(md, &t, J->dt, J->seed, (uint32_t)i, J->step0 + (uint64_t)s, J->brute, J->prop,
+                      NULL, NULL, NULL);
             if (J->record_every > 0 && ((s + 1) % J->record_every) == 0) {
                 int64_t r = (s + 1) / J->record_every - 1;
                 if (r < J->n_rec) {
@@ -894,7 +938,8 @@ int orc_run(int kind, double mass, const double *par, double Vbar, int M, int Ne
             const double *eps, const double *sqw, int64_t n_traj, double *x, double *p, double *F,
             int *occ, cplx *C, double dt, int64_t n_steps, uint64_t seed, uint64_t step0,
             int brute, int record_every, int n_rec, double *pop_sh, double *pop_wf,
-            uint32_t *status, int64_t *hops, int64_t *frustrated, double *lam_out, int n_threads)
+            uint32_t *status, int64_t *hops, int64_t *frustrated, double *lam_out, int n_threads,
+            int prop)
 {
     orc_model md;
     make_model(&md, kind, mass, par, Vbar, M, Ne, eps, sqw);
@@ -912,6 +957,7 @@ int orc_run(int kind, double mass, const double *par, double Vbar, int M, int Ne
         J->seed = seed;
         J->step0 = step0;
         J->brute = brute;
+        J->prop = prop;
         J->record_every = record_every;
         J->n_rec = n_rec;
         J->x = x; J->p = p; J->F = F; J->occ = occ; J->C = C;
@@ -935,7 +981,7 @@ int orc_run(int kind, double mass, const double *par, double Vbar, int M, int Ne
 int orc_step_one(int kind, double mass, const double *par, double Vbar, int M, int Ne,
                  const double *eps, const double *sqw, double *x, double *p, double *F, int *occ,
                  cplx *C, double dt, uint64_t seed, uint32_t traj, uint64_t n, int brute, double *g,
-                 double *zeta, int *hop, double *lam_out)
+                 double *zeta, int *hop, double *lam_out, int prop)
 {
     orc_model md;
     make_model(&md, kind, mass, par, Vbar, M, Ne, eps, sqw);
@@ -947,7 +993,7 @@ int orc_step_one(int kind, double mass, const double *par, double Vbar, int M, i
     memcpy(t.occ, occ, sizeof(int) * Ne);
     memcpy(t.C, C, sizeof(cplx) * N * Ne);
     traj_prepare(&md, &t);
-    traj_step(&md, &t, dt, seed, traj, n, brute, g, zeta, hop);
+    traj_step(&md, &t, dt, seed, traj, n, brute, prop, g, zeta, hop);
     *x = t.x;
     *p = t.p;
     *F = t.F;

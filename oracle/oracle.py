@@ -70,11 +70,13 @@ def lib():
                               ctypes.c_int, _dp, _dp, ctypes.c_int64, _dp, _dp, _dp, _ip, _vp,
                               ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
                               ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _u32p, _i64p,
-                              _i64p, _dp, ctypes.c_int]
+                              _i64p, _dp, ctypes.c_int, ctypes.c_int]
         L.orc_step_one.argtypes = [ctypes.c_int, ctypes.c_double, _dp, ctypes.c_double,
                                    ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _ip, _vp,
                                    ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
-                                   ctypes.c_uint64, ctypes.c_int, _dp, _dp, _ip, _dp]
+                                   ctypes.c_uint64, ctypes.c_int, _dp, _dp, _ip, _dp, ctypes.c_int]
+        L.orc_propagate_overlap.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp,
+                                            ctypes.c_double, _vp]
         L.orc_select.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _dp, ctypes.c_double]
         L.orc_eocc.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_int64,
                                _dp, _dp, _dp, _dp, _dp]
@@ -289,8 +291,10 @@ def unit_coefficients(N, occ):
     return C
 
 
-def step_one(model_or_bound, x, p, occ, C, dt, seed, traj, n, brute=False):
-    """One step of one trajectory from (x, p, occ, C[N][Ne]).
+def step_one(model_or_bound, x, p, occ, C, dt, seed, traj, n, brute=False, prop=0):
+    """One step of one trajectory from (x, p, occ, C[N][Ne]).  prop 0: the
+    exponential of the averaged adiabatic generator; prop 1: the
+    diabatic-basis (overlap) propagator.
 
     Returns dict with the new state and the step's g[Ne][N], zeta, hop flag."""
     B = model_or_bound if isinstance(model_or_bound, _Bound) else _Bound(model_or_bound)
@@ -306,14 +310,16 @@ def step_one(model_or_bound, x, p, occ, C, dt, seed, traj, n, brute=False):
     st = lib().orc_step_one(B.kind, B.mass, _d(B.par), B.Vbar, B.M, B.Ne, _d(B.eps), _d(B.sqw),
                             _d(xa), _d(pa), _d(Fa), occ.ctypes.data_as(_ip), C.ctypes.data,
                             float(dt), int(seed), int(traj), int(n), int(brute), _d(g),
-                            _d(zeta), hop.ctypes.data_as(_ip), _d(lam))
+                            _d(zeta), hop.ctypes.data_as(_ip), _d(lam), int(prop))
     return dict(x=float(xa[0]), p=float(pa[0]), F=float(Fa[0]), occ=occ, C=C, g=g,
                 zeta=float(zeta[0]), hop=int(hop[0]), lam=lam, status=st)
 
 
 def run(model_or_bound, x, p, occ, C, dt, n_steps, seed, step0=0, brute=False,
-        record_every=0, n_threads=None):
-    """Advance a batch: x, p [n]; occ [n][Ne]; C [n][N][Ne].  Returns a dict."""
+        record_every=0, n_threads=None, prop=0):
+    """Advance a batch: x, p [n]; occ [n][Ne]; C [n][N][Ne].  prop selects the
+    electronic propagator (0 averaged-generator exponential, 1 overlap).
+    Returns a dict."""
     B = model_or_bound if isinstance(model_or_bound, _Bound) else _Bound(model_or_bound)
     x = _c(x).copy()
     p = _c(p).copy()
@@ -335,9 +341,18 @@ def run(model_or_bound, x, p, occ, C, dt, n_steps, seed, step0=0, brute=False,
                   _d(p), _d(F), occ.ctypes.data_as(_ip), C.ctypes.data, float(dt), int(n_steps),
                   int(seed), int(step0), int(brute), int(record_every), n_rec, _d(psh), _d(pwf),
                   status.ctypes.data_as(_u32p), hops.ctypes.data_as(_i64p),
-                  frus.ctypes.data_as(_i64p), _d(lam), int(n_threads))
+                  frus.ctypes.data_as(_i64p), _d(lam), int(n_threads), int(prop))
     return dict(x=x, p=p, F=F, occ=occ, C=C, status=status, hops=hops, frustrated=frus,
                 lam=lam, pop_sh=psh[:n_rec], pop_wf=pwf[:n_rec])
+
+
+def propagate_overlap(lam0, Q0, lam1, Q1, dt, C):
+    """C[N][Ne] <- exp(-i L1 dt/2) Q1^T Q0 exp(-i L0 dt/2) C (reading R9)."""
+    N = len(lam0)
+    C = _c(C, np.complex128).copy()
+    lib().orc_propagate_overlap(N, C.shape[1], _d(_c(lam0)), _d(_c(Q0)), _d(_c(lam1)), _d(_c(Q1)),
+                                float(dt), C.ctypes.data)
+    return C
 
 
 # ------------------------------------------------------------- occupied energy
