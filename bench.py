@@ -173,8 +173,8 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def measure(precision, sample_clocks):
-        c = P.Context(md, n, precision=precision, stream=stream.cuda_stream)
+    def measure(precision, sample_clocks, propagator=0):
+        c = P.Context(md, n, precision=precision, stream=stream.cuda_stream, propagator=propagator)
         c.set_state(x, p, occ, C if precision == P.PREC_FP64 else C.astype(np.complex64))
         for _ in range(args.warmup):
             c.run(dt, 1, seed)
@@ -211,6 +211,12 @@ def run_ours(args):
         tc_m = cm.kernel_shape()[0] == 8  # tensor-core propagator in use
         cm.close()
         mixed = (ms_m, prof_m, Km, bad_m, tc_m)
+    overlap = None
+    if not args.no_overlap:
+        co, ms_o, prof_o, _ = measure(P.PREC_FP64, False, propagator=P.iesh.PROP_OVERLAP)
+        bad_o = int(np.count_nonzero(co.get_state()["status"]))
+        co.close()
+        overlap = (ms_o, prof_o, bad_o)
 
     # ---- end to end through the C-ABI with pinned host buffers
     N, Ne = md["M"] + 1, md["Ne"]
@@ -307,6 +313,24 @@ def run_ours(args):
                 "roofline_propagate": roof_m,
                 "gpu_launches": int(sum(v[1] for v in prof_m.values())),
                 "status_nonzero": bad_m,
+            }
+        if overlap is not None:
+            ms_o, prof_o, bad_o = overlap
+            tot_o = max(1e-9, sum(u[0] for u in prof_o.values()))
+            po_ms, po_n = prof_o["propagate"]
+            # one real N x N by N x 2Ne contraction per step (4 N^2 Ne flops)
+            ach_o = 4.0 * N * N * Ne * n / (po_ms / po_n / 1e3) / 1e12 if po_n else None
+            line["overlap"] = {
+                "value": world * n * args.steps / (ms_o / 1e3), "unit": UNIT,
+                "ms_per_step": ms_o / args.steps, "speedup_vs_fp64": ms / ms_o,
+                "dtype": "f64",
+                "propagator": "diabatic-basis variant: exp(-i L1 dt/2) Q1^T Q0 exp(-i L0 dt/2), "
+                              "O from the arrowhead's closed form (second order, like the "
+                              "averaged generator)",
+                "kernel_time_share": {k: round(v[0] / tot_o, 4) for k, v in prof_o.items() if v[1]},
+                "propagate_tflops": ach_o,
+                "gpu_launches": int(sum(v[1] for v in prof_o.values())),
+                "status_nonzero": bad_o,
             }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args, md, kT, dt)
@@ -477,6 +501,8 @@ def main():
     ap.add_argument("--cpu-steps", dest="cpu_steps", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-overlap", action="store_true",
+                    help="skip the diabatic-basis propagator variant")
     ap.add_argument("--workload", choices=["dw", "paper", "scatter", "eocc"], default="dw",
                     help="dw: the double-well batch (default, --M/--n-traj); the others print "
                          "secondary measurements")

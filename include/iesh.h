@@ -64,6 +64,9 @@ typedef enum {
 #define IESH_TRAJ_NAN 0x4u             /* non-finite nucleus or force */
 #define IESH_TRAJ_DONE 0x8u            /* trajectory finished (left the surface) */
 #define IESH_TRAJ_PROP_RANGE 0x10u     /* propagator needed more terms than built */
+#define IESH_PROP_AVERAGED 0
+#define IESH_PROP_OVERLAP 1
+
 #define IESH_TRAJ_TC_WAIT 0x20u        /* a tensor-core completion wait gave up (the
                                           step's coefficients were not updated) */
 
@@ -111,6 +114,11 @@ typedef struct {
     int compact_every; /* > 0: kernels visit only live trajectories (no IESH_TRAJ_DONE or
                           IESH_TRAJ_NAN) through a device work list, compacted in place
                           every compact_every steps of iesh_run (0: visit all) */
+    int propagator;    /* IESH_PROP_AVERAGED (0): exponential of the step-averaged
+                          adiabatic generator (Sec. II C); IESH_PROP_OVERLAP (1): the
+                          diabatic-basis variant, exp(-i L1 dt/2) Q1^T Q0
+                          exp(-i L0 dt/2) in the adiabatic frame (FP64 only; needs a
+                          nonzero coupling factor f(x), else IESH_TRAJ_PROP_RANGE) */
 } iesh_options;
 
 /* Create a context for up to max_traj trajectories of `model`.  Discretises

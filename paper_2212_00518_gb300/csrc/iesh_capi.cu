@@ -316,6 +316,10 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
         st = fail(ctx, IESH_EINVAL, "unknown precision %d", opt->precision);
     else if (opt->record_every < 0 || opt->max_records < 0) st = fail(ctx, IESH_EINVAL, "negative record sizes");
     else if (opt->compact_every < 0) st = fail(ctx, IESH_EINVAL, "negative compact_every");
+    else if (opt->propagator != IESH_PROP_AVERAGED && opt->propagator != IESH_PROP_OVERLAP)
+        st = fail(ctx, IESH_EINVAL, "unknown propagator %d", opt->propagator);
+    else if (opt->propagator == IESH_PROP_OVERLAP && opt->precision != IESH_PREC_FP64)
+        st = fail(ctx, IESH_EUNSUPPORTED, "the overlap propagator is FP64 only");
     if (st != IESH_OK) {
         *out = ctx;  // let the caller read the message, then destroy
         return st;
@@ -354,6 +358,8 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
     d.C = Cd;
     A(d.lam, T * N) A(d.q0, T * N) A(d.lam_prev, T * N) A(d.q0_prev, T * N)
     A(d.geo, T * 4) A(d.geo_prev, T * 4)
+    A(d.rt, T * N) A(d.rt_prev, T * N) A(d.ro, T * N) A(d.ro_prev, T * N)
+    A(d.fx, T) A(d.fx_prev, T)
     A(d.status, T) A(d.nstep, T) A(d.hops, T) A(d.frus, T)
     A(d.scratch, T * (size_t)d.scratch_stride)
     A(d.cheb, T * kChebStride)
@@ -371,6 +377,7 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
     d.z0 = z0;
     d.epsdiff = epsdiff;
     d.poled = poled;
+    d.propagator = opt->propagator;
     d.live = (opt->compact_every > 0) ? ctx->live : nullptr;
     d.n_live = ctx->n_live;
     configure_hop_smem();
@@ -569,9 +576,13 @@ iesh_status iesh_run(iesh_ctx *ctx, double dt, int64_t n_steps, uint64_t seed)
     const double tol = mx ? 1e-7 : 1e-15;
     for (int64_t k = 0; k < n_steps; ++k) {
         CU(timed(ctx, IESH_K_EIGEN, [&] { return launch_eigen(d, ctx->md, dt, 1, ctx->stream); }));
-        CU(timed(ctx, IESH_K_COUPLING,
-                 [&] { return launch_coupling(d, dt, ctx->model.mass, tol, mx, ctx->stream); }));
-        CU(timed(ctx, IESH_K_PROPAGATE, [&] { return launch_cheb(d, dt, mx, ctx->stream); }));
+        if (d.propagator == IESH_PROP_OVERLAP) {
+            CU(timed(ctx, IESH_K_PROPAGATE, [&] { return launch_overlap(d, dt, ctx->stream); }));
+        } else {
+            CU(timed(ctx, IESH_K_COUPLING,
+                     [&] { return launch_coupling(d, dt, ctx->model.mass, tol, mx, ctx->stream); }));
+            CU(timed(ctx, IESH_K_PROPAGATE, [&] { return launch_cheb(d, dt, mx, ctx->stream); }));
+        }
         CU(timed(ctx, IESH_K_HOP, [&] {
             return launch_hop(d, dt, ctx->model.mass, seed, ctx->opt.skip_bound, nullptr, ctx->stream, mx);
         }));

@@ -50,6 +50,12 @@ struct DevState {
     const double *eps, *z0;    // bath [M]: energies and sqrt(Gamma/2pi) sqrt(w_k)
     const float *epsdiff;      // [M][M] eps_a - eps_b rounded to FP32 (mixed path)
     const double *poled;       // [M][M] poled[k M + o] = eps_o - eps_k (secular sums)
+    // root offsets from their origin poles (lam_i = eps[ro_i] + rt_i, rt_i
+    // unrounded) and the coupling factor f(x), at this and the previous step
+    double *rt, *rt_prev;      // [n][N]
+    int32_t *ro, *ro_prev;     // [n][N]
+    double *fx, *fx_prev;      // [n]
+    int propagator;            // 0 Chebyshev of the averaged generator, 1 overlap
     // work list: when live != nullptr the step kernels visit trajectory
     // live[w] for work item w < *n_live (compacted on the device)
     const int32_t *live;

@@ -34,5 +34,8 @@ size_t cheb_tc_smem_bytes(int N, int Ne);
 bool cheb_tc_eligible(int N, int Ne);
 void configure_cheb_tc();
 cudaError_t launch_cheb_tc(const DevState &s, double dt, cudaStream_t st);
+// diabatic-basis (overlap) propagator variant: build O^T, then apply
+size_t overlap_build_smem(int N, int M);
+cudaError_t launch_overlap(const DevState &s, double dt, cudaStream_t st);
 
 }  // namespace iesh

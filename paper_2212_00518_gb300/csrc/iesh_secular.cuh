@@ -155,7 +155,8 @@ __device__ bool sec_iterate(int M, const R *__restrict__ eps, const R *__restric
     return false;
 }
 
-// Root r (0..M) of the secular equation, lam and q0 = 1/sqrt(g'(lam)).
+// Root r (0..M) of the secular equation, lam and q0 = 1/sqrt(g'(lam)), and
+// optionally its origin pole o and offset tau = lam - eps_o (unrounded).
 // Cold start: the sign of g at the middle of the pole gap picks the nearer
 // pole as origin and the half-gap as bracket.  Warm start (previous root
 // `guess`, which lies in the same gap): origin = pole nearer the guess,
@@ -165,7 +166,8 @@ __device__ bool sec_iterate(int M, const R *__restrict__ eps, const R *__restric
 template <class R, bool TAB = false>
 __device__ void secular_root(int r, int M, const R *__restrict__ eps, const R *__restrict__ z2,
                              const R *__restrict__ diff, R h,
-                             R Z2, bool warm, R guess, R &lam, R &q0, uint32_t &st)
+                             R Z2, bool warm, R guess, R &lam, R &q0, uint32_t &st,
+                             int *o_out = nullptr, R *tau_out = nullptr)
 {
     int o, kind;
     R lo, hi, D = 0, tau;
@@ -222,6 +224,8 @@ __device__ void secular_root(int r, int M, const R *__restrict__ eps, const R *_
     if (!conv) st |= ST_SECULAR;
     lam = eps[o] + tau;
     q0 = R(1) / sqrt(e.gp);
+    if (o_out) *o_out = o;  // lam = eps[o] + tau with tau exact
+    if (tau_out) *tau_out = tau;
 }
 
 

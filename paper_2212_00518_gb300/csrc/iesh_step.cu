@@ -92,7 +92,10 @@ __global__ void __launch_bounds__(512, 1) k_eigen(DevState s, ModelDev md, doubl
             guess = 2.0 * l - s.lam_prev[t * N + r];
             s.lam_prev[t * N + r] = l;
             s.q0_prev[t * N + r] = s.q0[t * N + r];
+            s.rt_prev[t * N + r] = s.rt[t * N + r];
+            s.ro_prev[t * N + r] = s.ro[t * N + r];
             if (r < 4) s.geo_prev[t * 4 + r] = s.geo[t * 4 + r];
+            if (r == 0) s.fx_prev[t] = s.fx[t];
         }
         lam_s[r] = l;
         mv = model_eval(md, x);
@@ -111,22 +114,32 @@ __global__ void __launch_bounds__(512, 1) k_eigen(DevState s, ModelDev md, doubl
     uint32_t st = 0;
     if (act) {
         const double Z2 = red_s[0];
-        double l, q;
+        double l, q, rt_r = 0.0;
+        int ro_r = 0;
         if (Z2 > 0.0) {
             // an extrapolation outside the root's pole gap falls back to lam
             const double glo = r > 0 ? eps_s[r - 1] : -INFINITY, ghi = r < M ? eps_s[r] : INFINITY;
             if (!(guess > glo && guess < ghi)) guess = lam_s[r];
-            secular_root<double, true>(r, M, eps_s, z2_s, s.poled, mv.h, Z2, mode == 1, guess, l, q, st);
+            secular_root<double, true>(r, M, eps_s, z2_s, s.poled, mv.h, Z2, mode == 1, guess, l, q, st,
+                                       &ro_r, &rt_r);
         } else {
             // no coupling: the eigenvalues are h and the bath energies
             int pos = 0;
             for (int k = 0; k < M; ++k) pos += (eps_s[k] < mv.h);
             l = (r < pos) ? eps_s[r] : (r == pos ? mv.h : eps_s[r - 1]);
             q = (r == pos) ? 1.0 : 0.0;
+            ro_r = (r < pos) ? r : (r == pos ? (r < M ? r : M - 1) : r - 1);
+            rt_r = l - eps_s[ro_r];
         }
         s.lam[t * N + r] = l;
         s.q0[t * N + r] = q;
-        if (mode == 0) s.lam_prev[t * N + r] = l;
+        s.rt[t * N + r] = rt_r;
+        s.ro[t * N + r] = ro_r;
+        if (mode == 0) {
+            s.lam_prev[t * N + r] = l;
+            s.rt_prev[t * N + r] = rt_r;
+            s.ro_prev[t * N + r] = ro_r;
+        }
         lam_s[r] = l;
         q0_s[r] = q;
         if (st) atomicOr(&s.status[t], st);
@@ -158,7 +171,11 @@ __global__ void __launch_bounds__(512, 1) k_eigen(DevState s, ModelDev md, doubl
         s.geo[t * 4 + 1] = mv.dh;
         s.geo[t * 4 + 2] = kappa;
         s.geo[t * 4 + 3] = mv.U0;
-        if (mode == 0) s.vprev[t] = p / md.mass;
+        s.fx[t] = mv.f;
+        if (mode == 0) {
+            s.vprev[t] = p / md.mass;
+            s.fx_prev[t] = mv.f;
+        }
         if (!isfinite(x) || !isfinite(p) || !isfinite(F)) atomicOr(&s.status[t], ST_NAN);
     }
 }

@@ -24,9 +24,12 @@ TRAJ_SINGULAR = 0x2
 TRAJ_NAN = 0x4
 TRAJ_DONE = 0x8
 TRAJ_PROP_RANGE = 0x10
+TRAJ_TC_WAIT = 0x20
 
 PREC_FP64 = 0
 PREC_MIXED = 1
+PROP_AVERAGED = 0  # exponential of the step-averaged adiabatic generator
+PROP_OVERLAP = 1   # diabatic-basis variant (overlap of the two ends' orbitals)
 IESH_NOALLOC_SCRATCH_BYTES = 32 << 20
 _KIND = {"harmonic": 0, "erpenbeck": 1, "morse_image": 2}
 _DISC = {"gl": 0, "trapezoid": 1}
@@ -55,7 +58,8 @@ class _EoccModel(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("skip_bound", ctypes.c_int),
                 ("record_every", ctypes.c_int), ("max_records", ctypes.c_int),
-                ("z_done", ctypes.c_double), ("compact_every", ctypes.c_int)]
+                ("z_done", ctypes.c_double), ("compact_every", ctypes.c_int),
+                ("propagator", ctypes.c_int)]
 
 
 EXPORTS = ["iesh_create", "iesh_destroy", "iesh_bath", "iesh_init_state", "iesh_set_state",
@@ -172,7 +176,7 @@ class Context:
     """A batch of IESH trajectories on one GPU (wraps iesh_ctx)."""
 
     def __init__(self, model, max_traj, precision=PREC_FP64, skip_bound=False, record_every=0,
-                 max_records=0, z_done=0.0, compact_every=0, stream=None):
+                 max_records=0, z_done=0.0, compact_every=0, stream=None, propagator=PROP_AVERAGED):
         self.L = load()
         self.model = dict(model)
         self.N = int(model["M"]) + 1
@@ -181,8 +185,9 @@ class Context:
         self.max_traj = int(max_traj)
         self.n = 0
         self._m = model_struct(model)
+        self.propagator = int(propagator)
         self._o = _Options(precision, int(bool(skip_bound)), int(record_every), int(max_records),
-                           float(z_done), int(compact_every))
+                           float(z_done), int(compact_every), self.propagator)
         self.stream = current_stream_handle() if stream is None else stream
         h = _vp()
         rc = self.L.iesh_create(ctypes.byref(h), ctypes.byref(self._m), ctypes.byref(self._o),
