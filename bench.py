@@ -174,7 +174,8 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     def measure(precision, sample_clocks, propagator=0):
-        c = P.Context(md, n, precision=precision, stream=stream.cuda_stream, propagator=propagator)
+        c = P.Context(md, n, precision=precision, stream=stream.cuda_stream, propagator=propagator,
+                      skip_bound=args.skip_bound)
         c.set_state(x, p, occ, C if precision == P.PREC_FP64 else C.astype(np.complex64))
         for _ in range(args.warmup):
             c.run(dt, 1, seed)
@@ -256,7 +257,7 @@ def run_ours(args):
                                    f"Ne={md['Ne']}, {n} trajectories per GPU, kT 0.005-0.01, "
                                    f"dt={dt} a.u., FP64 path",
                        "trajectories_per_gpu": n, "n_orbitals": N, "n_electrons": Ne,
-                       "precision": "fp64", "skip_bound": False,
+                       "precision": "fp64", "skip_bound": bool(args.skip_bound),
                        "l2": "working set > L2 (coefficients + coupling matrices "
                              f"{(n * Ne * N * 16 + n * N * N * 8) / 1e9:.2f} GB)",
                        "status_nonzero": bad},
@@ -501,6 +502,9 @@ def main():
     ap.add_argument("--cpu-steps", dest="cpu_steps", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--skip-bound", dest="skip_bound", action="store_true",
+                    help="skip the ratio solves when the exact hop-probability bound is below "
+                         "the uniform (Sec. II C; hop decisions unchanged)")
     ap.add_argument("--no-overlap", action="store_true",
                     help="skip the diabatic-basis propagator variant")
     ap.add_argument("--workload", choices=["dw", "paper", "scatter", "eocc"], default="dw",
