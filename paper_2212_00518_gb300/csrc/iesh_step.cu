@@ -753,7 +753,9 @@ __host__ __device__ inline size_t hop_region_bytes(int N, int Ne, bool f32)
 {
     size_t a = (size_t)16 * Ne * Ne;
     if (f32) {
-        const size_t b = (size_t)8 * Ne * Ne + (size_t)8 * (N - Ne) * Ne;
+        // FP32 factors + one pass of substitution rows (at most 128 quad-lane groups)
+        const int rows = (N - Ne) < 128 ? (N - Ne) : 128;
+        const size_t b = (size_t)8 * Ne * Ne + (size_t)8 * rows * Ne;
         if (b > a) a = b;
     }
     return (a + 15) & ~(size_t)15;
@@ -980,12 +982,13 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
             __syncthreads();
             if (threadIdx.x < Ne) dinv32[threadIdx.x] = make_float2((float)dv.x, (float)dv.y);
             __syncthreads();
-            float2 *Y = reinterpret_cast<float2 *>(hop_smem + (size_t)8 * Ne * Ne);  // [nu][Ne]
+            // substitution rows of one pass: group grp owns row grp (reused each pass)
+            float2 *Y = reinterpret_cast<float2 *>(hop_smem + (size_t)8 * Ne * Ne);  // [min(nu, ngrp)][Ne]
             for (int u0 = 0; u0 < nu; u0 += ngrp) {
                 const int u = u0 + grp;
                 const bool live = u < nu;
                 const int m = live ? unocc[u] : 0;
-                float2 *y = Y + (size_t)(live ? u : 0) * Ne;
+                float2 *y = Y + (size_t)(live ? grp : 0) * Ne;
                 // y U = c_m  (U_ij = A[perm[i]][j], i <= j)
                 for (int jc = 0; jc < Ne; ++jc) {
                     float2 acc = make_float2(0.f, 0.f);
