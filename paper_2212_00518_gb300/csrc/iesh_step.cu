@@ -746,17 +746,29 @@ __device__ __forceinline__ float2 cfmsf(float2 acc, float2 a, float2 b)  // acc 
 {
     return make_float2(fmaf(-a.x, b.x, fmaf(a.y, b.y, acc.x)), fmaf(-a.x, b.y, fmaf(-a.y, b.x, acc.y)));
 }
+// FP32 factorisation (mixed path): the same operations in single precision.
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) { return cmulf(a, b); }
+__device__ __forceinline__ float2 cfms(float2 acc, float2 a, float2 b) { return cfmsf(acc, a, b); }
+__device__ __forceinline__ float2 crcp(float2 a)
+{
+    const float d = 1.0f / fmaf(a.x, a.x, a.y * a.y);
+    return make_float2(a.x * d, -a.y * d);
+}
+__device__ __forceinline__ int pivot_key(float2 v)  // max(|re|, |im|), monotonic
+{
+    const int a = __float_as_int(v.x) & 0x7fffffff, b = __float_as_int(v.y) & 0x7fffffff;
+    return a > b ? a : b;
+}
 
-// Bytes of the matrix region: S / LU in FP64, and in the mixed path also the
-// FP32 copy of the factors followed by the FP32 substitution rows.
+// Bytes of the matrix region: S / LU in FP64; in the mixed path the FP32
+// factors followed by one pass of FP32 substitution rows (at most 128
+// quad-lane groups).
 __host__ __device__ inline size_t hop_region_bytes(int N, int Ne, bool f32)
 {
     size_t a = (size_t)16 * Ne * Ne;
     if (f32) {
-        // FP32 factors + one pass of substitution rows (at most 128 quad-lane groups)
         const int rows = (N - Ne) < 128 ? (N - Ne) : 128;
-        const size_t b = (size_t)8 * Ne * Ne + (size_t)8 * rows * Ne;
-        if (b > a) a = b;
+        a = (size_t)8 * Ne * Ne + (size_t)8 * rows * Ne;
     }
     return (a + 15) & ~(size_t)15;
 }
@@ -768,9 +780,10 @@ size_t hop_smem_bytes(int N, int Ne, bool f32)
 }
 size_t hop_smem_bytes(int N, int Ne) { return hop_smem_bytes(N, Ne, false); }
 
-// CT: coefficient type.  double2: the FP64 path.  float2: the mixed path --
-// S is widened to FP64 and factorised in FP64 (the overlap inverse), then
-// L and U are rounded to FP32 for the substitutions over the unoccupied rows.
+// CT: coefficient type, also the type of the factorisation.  double2: the
+// FP64 path.  float2: the mixed path -- S (read from the FP32 coefficients)
+// is factorised and substituted in FP32; |det S| for the skip bound and the
+// hop probabilities from the ratios are formed in FP64.
 // MAXT/MINB: launch bounds of the instantiation (512 x 1 for large S, 256 x
 // 3 when three CTAs fit in shared memory).
 template <class CT, int MAXT, int MINB>
@@ -784,8 +797,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
     const int N = s.N, Ne = s.Ne, nu = N - Ne;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const size_t abytes = hop_region_bytes(N, Ne, kF32);
-    double2 *A = reinterpret_cast<double2 *>(hop_smem);           // [Ne][Ne] physical rows
-    double2 *dinv = reinterpret_cast<double2 *>(hop_smem + abytes); // [Ne] 1/U_kk, logical k
+    CT *A = reinterpret_cast<CT *>(hop_smem);                     // [Ne][Ne] physical rows
+    CT *dinv = reinterpret_cast<CT *>(hop_smem + abytes);         // [Ne] 1/U_kk, logical k
     double *lam_s = reinterpret_cast<double *>(dinv + Ne);         // [N]
     double *q0_s = lam_s + N;                                     // [N]
     double *red = q0_s + N;                                       // [64]
@@ -817,7 +830,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
     __syncthreads();
     for (int idx = threadIdx.x; idx < Ne * Ne; idx += blockDim.x) {
         const int a = idx / Ne, e = idx - a * Ne;
-        A[idx] = to_d2(Ct[(int64_t)e * N + occ_s[a]]);
+        A[idx] = Ct[(int64_t)e * N + occ_s[a]];
     }
     if (threadIdx.x == 0) {
         int u = 0;
@@ -865,7 +878,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
             singular = true;
             break;
         }
-        const double2 pv = A[pr * Ne + kc];
+        const CT pv = A[pr * Ne + kc];
         // remove pr from the row list (every thread does the same edit on a
         // private copy of the position; thread 0 writes it after the barrier)
         int ppos = 0;
@@ -874,7 +887,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
         // multipliers of the remaining rows: only the warps that form them
         // take the FP64 reciprocal (the FP64 pipe charges every issuing warp)
         if (threadIdx.x < nr) {
-            const double2 pinv = crcp(pv);
+            const CT pinv = crcp(pv);
             for (int q = threadIdx.x; q < nr; q += blockDim.x) {
                 const int r = rows[q];
                 if (r != pr) A[r * Ne + kc] = cmul(A[r * Ne + kc], pinv);
@@ -899,7 +912,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
                 const int c = kc + 1 + cc;
                 // list position qq of the list without pr: entry nr-1 moved into ppos
                 const int r = rows[(qq == ppos) ? nr - 1 : qq];
-                const double2 nv = cfms(A[r * Ne + c], A[r * Ne + kc], A[pr * Ne + c]);
+                const CT nv = cfms(A[r * Ne + c], A[r * Ne + kc], A[pr * Ne + c]);
                 A[r * Ne + c] = nv;
                 if (cc == 0) {
                     const int m2 = pivot_key(nv);
@@ -944,7 +957,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
         // |det S| = prod |U_kk| from the stored reciprocals, as a sum of logs
         double lg = 0.0;
         for (int kc = threadIdx.x; kc < Ne; kc += blockDim.x) {
-            const double2 u = dinv[kc];  // 1/U_kk
+            const double2 u = to_d2(dinv[kc]);  // 1/U_kk
             lg -= 0.5 * log(u.x * u.x + u.y * u.y);
         }
         const double det_abs = exp(block_sum(lg, red));
@@ -957,7 +970,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
         }
         const double sd = block_sum(part, red);
         const double bound = 2.0 * dt * fabs(v) * sd / det_abs;
-        if (bound * (1.0 + 1e-9) < zeta) do_ratios = false;
+        // margin for the rounding of |det S|: FP64 factors, or FP32 (mixed)
+        if (bound * (kF32 ? 1.0 + 1e-5 : 1.0 + 1e-9) < zeta) do_ratios = false;
     }
 
     double *scr = s.scratch + t * s.scratch_stride;
@@ -967,21 +981,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
     const unsigned quad = 0xFu << (lane & ~3);
     if (do_ratios) {
         if constexpr (kF32) {
-            // round L, U and 1/U_kk to FP32 in place (chunked so that every
-            // double2 is read before its bytes are overwritten)
-            float2 *A32 = reinterpret_cast<float2 *>(A);
-            for (int base = 0; base < Ne * Ne; base += blockDim.x) {
-                const int i = base + threadIdx.x;
-                const double2 dv = (i < Ne * Ne) ? A[i] : make_double2(0.0, 0.0);
-                __syncthreads();
-                if (i < Ne * Ne) A32[i] = make_float2((float)dv.x, (float)dv.y);
-                __syncthreads();
-            }
+            float2 *A32 = reinterpret_cast<float2 *>(A);  // FP32 factors
             float2 *dinv32 = reinterpret_cast<float2 *>(dinv);
-            const double2 dv = (threadIdx.x < Ne) ? dinv[threadIdx.x] : make_double2(0.0, 0.0);
-            __syncthreads();
-            if (threadIdx.x < Ne) dinv32[threadIdx.x] = make_float2((float)dv.x, (float)dv.y);
-            __syncthreads();
             // substitution rows of one pass: group grp owns row grp (reused each pass)
             float2 *Y = reinterpret_cast<float2 *>(hop_smem + (size_t)8 * Ne * Ne);  // [min(nu, ngrp)][Ne]
             for (int u0 = 0; u0 < nu; u0 += ngrp) {
