@@ -372,11 +372,15 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
     A(epsdiff, (size_t)M * M)
     double *poled = nullptr;
     A(poled, (size_t)M * M)
+    float2 *poledf = nullptr;
+    A(poledf, (size_t)M * M)
 #undef A
     d.eps = eps;
     d.z0 = z0;
     d.epsdiff = epsdiff;
     d.poled = poled;
+    d.poledf = poledf;
+    d.eigen_dfloat = ctx->mixed ? 1 : 0;
     d.propagator = opt->propagator;
     d.live = (opt->compact_every > 0) ? ctx->live : nullptr;
     d.n_live = ctx->n_live;
@@ -387,14 +391,22 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
         for (int a = 0; a < M; ++a)
             for (int b = 0; b < M; ++b) ed[(size_t)a * M + b] = (float)(ctx->eps_h[a] - ctx->eps_h[b]);
         std::vector<double> pd((size_t)M * M);
+        std::vector<float2> pf((size_t)M * M);
         for (int k = 0; k < M; ++k)
-            for (int o = 0; o < M; ++o) pd[(size_t)k * M + o] = ctx->eps_h[o] - ctx->eps_h[k];
+            for (int o = 0; o < M; ++o) {
+                const double v = ctx->eps_h[o] - ctx->eps_h[k];
+                const float hi = (float)v;
+                pd[(size_t)k * M + o] = v;
+                pf[(size_t)k * M + o] = make_float2(hi, (float)(v - (double)hi));
+            }
         // on the context stream, after the zero fills of dalloc (a stream created
         // non-blocking is not ordered with the legacy default stream)
         cudaError_t e0 = cudaMemcpyAsync(epsdiff, ed.data(), ed.size() * sizeof(float), cudaMemcpyHostToDevice,
                                          ctx->stream);
         if (e0 == cudaSuccess)
             e0 = cudaMemcpyAsync(poled, pd.data(), pd.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+        if (e0 == cudaSuccess)
+            e0 = cudaMemcpyAsync(poledf, pf.data(), pf.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->stream);
         if (e0 == cudaSuccess) e0 = cudaStreamSynchronize(ctx->stream);
         if (e0 != cudaSuccess) {
             *out = ctx;

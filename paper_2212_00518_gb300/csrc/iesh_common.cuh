@@ -50,6 +50,8 @@ struct DevState {
     const double *eps, *z0;    // bath [M]: energies and sqrt(Gamma/2pi) sqrt(w_k)
     const float *epsdiff;      // [M][M] eps_a - eps_b rounded to FP32 (mixed path)
     const double *poled;       // [M][M] poled[k M + o] = eps_o - eps_k (secular sums)
+    const float2 *poledf;      // [M][M] the same as double-float pairs (hi, lo)
+    int eigen_dfloat;          // 1: secular sums in double-float (mixed path)
     // root offsets from their origin poles (lam_i = eps[ro_i] + rt_i, rt_i
     // unrounded) and the coupling factor f(x), at this and the previous step
     double *rt, *rt_prev;      // [n][N]

@@ -118,7 +118,8 @@ __global__ void k_eocc_fwd(int64_t B, int M, int Ne, EoccConst kc, const R *__re
     const int r = threadIdx.x;
     if (r < Ne) {
         R lam, qp;
-        secular_root<R>(r, P, pole, wt, nullptr, hp, Z2, false, R(0), lam, qp, st);
+        const Poles<R> pp = {P, pole, wt, nullptr, nullptr, nullptr};
+        secular_root<R>(r, pp, hp, Z2, false, R(0), lam, qp, st);
         const R qm = decoupled ? R(0) : tt * qp / (lam - hm);
         const R Q0 = (ad.c[0] * qp - ad.c[1] * qm) / c;
         const R Q1 = (ad.c[1] * qp + ad.c[0] * qm) / c;

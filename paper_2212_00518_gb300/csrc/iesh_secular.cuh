@@ -46,6 +46,68 @@ __device__ __forceinline__ double pole_recip<double>(double d)
     return fma(r, fma(e, e, e), r);
 }
 
+// Double-float numbers (hi + lo, two FP32 values, about 48 significant bits)
+// for the secular sums of the mixed-precision path: the FP32 pipe is 64x
+// wider than the FP64 pipe on this part.  Error-free transformations:
+// Knuth's TwoSum, Dekker's Fast2Sum (|a| >= |b|) and the FMA product error.
+struct dfl {
+    float hi, lo;
+};
+__device__ __forceinline__ dfl dfl_two_sum(float a, float b)
+{
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dfl dfl_fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+// a + b with an error of a few units of 2^-46 (|a| + |b|)
+__device__ __forceinline__ dfl dfl_add(dfl a, dfl b)
+{
+    dfl s = dfl_two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return dfl_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ dfl dfl_mul(dfl a, dfl b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return dfl_fast_two_sum(p, e);
+}
+// 1/a: the rounded FP32 reciprocal r0 corrected by r0 (1 - a r0)
+__device__ __forceinline__ dfl dfl_rcp(dfl a)
+{
+    const float r0 = __frcp_rn(a.hi);
+    float e = fmaf(-a.hi, r0, 1.0f);
+    e = fmaf(-a.lo, r0, e);
+    return dfl_fast_two_sum(r0, r0 * e);
+}
+__device__ __forceinline__ dfl dfl_from(double x)
+{
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double dfl_value(dfl a) { return (double)a.hi + (double)a.lo; }
+
+// Pole data of the secular sums.  diff (optional): FP64 table of the pole
+// differences diff[k M + o] = eps_o - eps_k; ddf, z2df (double-float mode):
+// the same differences and z_k^2 as double-float pairs.
+template <class R>
+struct Poles {
+    int M;
+    const R *__restrict__ eps, *__restrict__ z2, *__restrict__ diff;
+    const float2 *__restrict__ ddf, *__restrict__ z2df;
+};
+
+// Evaluation modes of the secular sums: EV_PLAIN (eps_o - eps_k formed per
+// term), EV_TABLE (FP64 table), EV_DFLOAT (double-float sums on the FP32
+// pipe; the origin term and everything outside the sums stay FP64).
+enum { EV_PLAIN = 0, EV_TABLE = 1, EV_DFLOAT = 2 };
+
 // ============================================================= eigenpairs
 // The one-electron Hamiltonian of Sec. II B is an arrowhead matrix:
 // diag(h, eps_1..eps_M) bordered by z_k = V_k(x).  Its eigenvalues are the
@@ -62,27 +124,46 @@ struct Sec {
 
 // With ABS the sum of |z_k^2 / (lam - eps_k)| over k != o (the scale of the
 // rounding error of g, for the stopping test) is accumulated into e.sabs;
-// without it e.sabs is left at zero for the caller to fill in.  With TAB the
-// pole differences eps_o - eps_k come from the table diff[k M + o] (the same
-// rounded FP64 differences, one load instead of one FP64 subtraction).
-template <class R, bool ABS, bool TAB>
-__device__ __forceinline__ Sec<R> sec_eval(int M, const R *__restrict__ eps, const R *__restrict__ z2,
-                                           const R *__restrict__ diff, int o, R tau, R eomh)
+// without it e.sabs is left at zero for the caller to fill in.  EV selects
+// how the sums over k != o are formed (see EV_*); the terms k != o have
+// |lam - eps_k| >= half a pole gap, so their double-float range is safe.
+template <class R, bool ABS, int EV>
+__device__ __forceinline__ Sec<R> sec_eval(const Poles<R> &P, int o, R tau, R eomh)
 {
-    const R eo = eps[o];
+    const int M = P.M;
     R s1 = 0, s2 = 0, sa = 0;
+    if constexpr (EV == EV_DFLOAT) {
+        const dfl td = dfl_from((double)tau);
+        dfl d1 = {0.f, 0.f}, d2 = {0.f, 0.f}, da = {0.f, 0.f};
+#pragma unroll 2
+        for (int k = 0; k < M; ++k) {
+            const float2 dk = P.ddf[(size_t)k * M + o], zk = P.z2df[k];
+            const dfl r = dfl_rcp(dfl_add({dk.x, dk.y}, td));  // 1 / (lam - eps_k)
+            const dfl q = dfl_mul({zk.x, zk.y}, r);
+            if (k != o) {
+                d1 = dfl_add(d1, q);
+                d2 = dfl_add(d2, dfl_mul(q, r));
+                if (ABS) da = dfl_add(da, q.hi < 0.f ? dfl{-q.hi, -q.lo} : q);
+            }
+        }
+        s1 = (R)dfl_value(d1);
+        s2 = (R)dfl_value(d2);
+        sa = (R)dfl_value(da);
+    } else {
+        const R eo = P.eps[o];
 #pragma unroll 4
-    for (int k = 0; k < M; ++k) {
-        const R dko = TAB ? diff[(size_t)k * M + o] : (eo - eps[k]);
-        const R r = pole_recip<R>(dko + tau);
-        const R q = z2[k] * r;
-        if (k != o) {
-            s1 += q;
-            s2 = fma(q, r, s2);
-            if (ABS) sa += fabs(q);
+        for (int k = 0; k < M; ++k) {
+            const R dko = EV == EV_TABLE ? P.diff[(size_t)k * M + o] : (eo - P.eps[k]);
+            const R r = pole_recip<R>(dko + tau);
+            const R q = P.z2[k] * r;
+            if (k != o) {
+                s1 += q;
+                s2 = fma(q, r, s2);
+                if (ABS) sa += fabs(q);
+            }
         }
     }
-    const R qo = z2[o] / tau;
+    const R qo = P.z2[o] / tau;
     Sec<R> e;
     e.g = (eomh + tau) - s1 - qo;
     e.gp_rest = R(1) + s2;
@@ -98,26 +179,26 @@ __device__ __forceinline__ Sec<R> sec_eval(int M, const R *__restrict__ eps, con
 // linear term for the two outermost roots (kind 2: below all poles, kind 3:
 // above), matched in value and slope; each model root is safeguarded by the
 // bracket [lo, hi] of sign changes.  On return e is evaluated at tau.
-template <class R, bool TAB>
-__device__ bool sec_iterate(int M, const R *__restrict__ eps, const R *__restrict__ z2,
-                            const R *__restrict__ diff, R h, int o, int kind, R D, R &lo, R &hi, R &tau,
+template <class R, int EV>
+__device__ bool sec_iterate(const Poles<R> &P, R h, int o, int kind, R D, R &lo, R &hi, R &tau,
                             Sec<R> &e, bool have)
 {
-    const R u = Roundoff<R>::u;
-    const R eomh = eps[o] - h;
-    const R s = z2[o];
+    // rounding unit of the sums: 2^-44 covers the double-float sums
+    const R u = EV == EV_DFLOAT ? R(5.684341886080802e-14) : Roundoff<R>::u;
+    const R eomh = P.eps[o] - h;
+    const R s = P.z2[o];
     // the non-origin part of the error scale varies slowly with tau (those
     // poles are at least half a gap away): take it from the first evaluation
     R sa_rest;
     if (have) {
         sa_rest = e.sabs;
     } else {
-        e = sec_eval<R, true, TAB>(M, eps, z2, diff, o, tau, eomh);
+        e = sec_eval<R, true, EV>(P, o, tau, eomh);
         sa_rest = e.sabs;
         have = true;
     }
     for (int it = 0; it < 80; ++it) {
-        if (!have) e = sec_eval<R, false, TAB>(M, eps, z2, diff, o, tau, eomh);
+        if (!have) e = sec_eval<R, false, EV>(P, o, tau, eomh);
         have = false;
         e.sabs = sa_rest + fabs(e.qo) + fabs(eomh) + fabs(tau);
         if (fabs(e.g) <= R(8) * u * e.sabs) return true;
@@ -147,11 +228,11 @@ __device__ bool sec_iterate(int M, const R *__restrict__ eps, const R *__restric
         const bool tiny = fabs(tn - tau) <= R(2) * u * fabs(tn);
         tau = tn;
         if (tiny) {
-            e = sec_eval<R, false, TAB>(M, eps, z2, diff, o, tau, eomh);
+            e = sec_eval<R, false, EV>(P, o, tau, eomh);
             return true;
         }
     }
-    e = sec_eval<R, false, TAB>(M, eps, z2, diff, o, tau, eomh);
+    e = sec_eval<R, false, EV>(P, o, tau, eomh);
     return false;
 }
 
@@ -162,13 +243,13 @@ __device__ bool sec_iterate(int M, const R *__restrict__ eps, const R *__restric
 // `guess`, which lies in the same gap): origin = pole nearer the guess,
 // bracket = the whole gap, started at the guess; if the root ends in the
 // far half of the gap it is refined once more about the other pole.
-// TAB: diff holds the pole differences (see sec_eval); otherwise it is unused.
-template <class R, bool TAB = false>
-__device__ void secular_root(int r, int M, const R *__restrict__ eps, const R *__restrict__ z2,
-                             const R *__restrict__ diff, R h,
-                             R Z2, bool warm, R guess, R &lam, R &q0, uint32_t &st,
-                             int *o_out = nullptr, R *tau_out = nullptr)
+// EV: how the secular sums are formed (see sec_eval).
+template <class R, int EV = EV_PLAIN>
+__device__ void secular_root(int r, const Poles<R> &P, R h, R Z2, bool warm, R guess, R &lam, R &q0,
+                             uint32_t &st, int *o_out = nullptr, R *tau_out = nullptr)
 {
+    const int M = P.M;
+    const R *__restrict__ eps = P.eps;
     int o, kind;
     R lo, hi, D = 0, tau;
     Sec<R> e;
@@ -182,22 +263,22 @@ __device__ void secular_root(int r, int M, const R *__restrict__ eps, const R *_
             } else {
                 o = r; kind = 1; lo = -D; hi = 0; tau = guess - eps[r];
             }
-            conv = sec_iterate<R, TAB>(M, eps, z2, diff, h, o, kind, D, lo, hi, tau, e, false);
+            conv = sec_iterate<R, EV>(P, h, o, kind, D, lo, hi, tau, e, false);
             if (kind == 0 && tau > R(0.5) * D) {
                 o = r; kind = 1; lo = fmin(lo - D, -R(0.5) * D); hi = 0; tau = tau - D;
-                conv = sec_iterate<R, TAB>(M, eps, z2, diff, h, o, kind, D, lo, hi, tau, e, false);
+                conv = sec_iterate<R, EV>(P, h, o, kind, D, lo, hi, tau, e, false);
             } else if (kind == 1 && tau < -R(0.5) * D) {
                 o = L; kind = 0; lo = 0; hi = fmax(hi + D, R(0.5) * D); tau = tau + D;
-                conv = sec_iterate<R, TAB>(M, eps, z2, diff, h, o, kind, D, lo, hi, tau, e, false);
+                conv = sec_iterate<R, EV>(P, h, o, kind, D, lo, hi, tau, e, false);
             }
         } else {
-            const Sec<R> em = sec_eval<R, true, TAB>(M, eps, z2, diff, L, R(0.5) * D, eps[L] - h);
+            const Sec<R> em = sec_eval<R, true, EV>(P, L, R(0.5) * D, eps[L] - h);
             if (em.g >= R(0)) {
                 o = L; kind = 0; lo = 0; hi = R(0.5) * D; tau = R(0.5) * D; e = em; have = true;
             } else {
                 o = r; kind = 1; lo = -R(0.5) * D; hi = 0; tau = -R(0.5) * D;
             }
-            conv = sec_iterate<R, TAB>(M, eps, z2, diff, h, o, kind, D, lo, hi, tau, e, have);
+            conv = sec_iterate<R, EV>(P, h, o, kind, D, lo, hi, tau, e, have);
         }
     } else {
         if (r == 0) {
@@ -219,7 +300,7 @@ __device__ void secular_root(int r, int M, const R *__restrict__ eps, const R *_
             const R tg = guess - eps[o];
             if (tg > lo && tg < hi) tau = tg;
         }
-        conv = sec_iterate<R, TAB>(M, eps, z2, diff, h, o, kind, D, lo, hi, tau, e, false);
+        conv = sec_iterate<R, EV>(P, h, o, kind, D, lo, hi, tau, e, false);
     }
     if (!conv) st |= ST_SECULAR;
     lam = eps[o] + tau;

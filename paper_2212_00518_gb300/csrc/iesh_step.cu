@@ -58,6 +58,8 @@ __device__ __forceinline__ void slot_tree_sum(double *red, int r, bool inslot, i
 // mode 0: eigenpairs and force at the stored position (cold start);
 // mode 1: full first half of a step (kick, drift, eigenpairs, force, kick).
 // tpb trajectories per CTA, one thread per root.
+// DF: the secular sums in double-float arithmetic (mixed path).
+template <bool DF>
 __global__ void __launch_bounds__(512, 1) k_eigen(DevState s, ModelDev md, double dt, int mode, int tpb)
 {
     extern __shared__ double sh[];
@@ -68,11 +70,12 @@ __global__ void __launch_bounds__(512, 1) k_eigen(DevState s, ModelDev md, doubl
     const bool act = t >= 0 && !(s.status[t] & ST_DONE);
     const int P = eigen_pow2(N);                         // reduction width
     double *eps_s = sh;                                  // [M], shared by the slots
-    const int per = M + 2 * N + P;
+    const int per = M + 2 * N + P + (DF ? M : 0);
     double *z2_s = eps_s + M + (slot < tpb ? slot : 0) * per;  // [M]
     double *lam_s = z2_s + M;                            // [N]
     double *q0_s = lam_s + N;                            // [N]
     double *red_s = q0_s + N;                            // [P] slot reductions
+    float2 *z2df_s = reinterpret_cast<float2 *>(red_s + P);  // [M] z_k^2 as double-float (DF)
     const bool inslot = slot < tpb;
     for (int k = threadIdx.x; k < M; k += blockDim.x) eps_s[k] = s.eps[k];
     double x = 0.0, p = 0.0, guess = 0.0;
@@ -102,6 +105,10 @@ __global__ void __launch_bounds__(512, 1) k_eigen(DevState s, ModelDev md, doubl
         for (int k = r; k < M; k += N) {
             const double z = s.z0[k] * mv.f;
             z2_s[k] = z * z;
+            if (DF) {
+                const dfl zd = dfl_from(z * z);
+                z2df_s[k] = make_float2(zd.hi, zd.lo);
+            }
         }
     }
     __syncthreads();
@@ -120,8 +127,11 @@ __global__ void __launch_bounds__(512, 1) k_eigen(DevState s, ModelDev md, doubl
             // an extrapolation outside the root's pole gap falls back to lam
             const double glo = r > 0 ? eps_s[r - 1] : -INFINITY, ghi = r < M ? eps_s[r] : INFINITY;
             if (!(guess > glo && guess < ghi)) guess = lam_s[r];
-            secular_root<double, true>(r, M, eps_s, z2_s, s.poled, mv.h, Z2, mode == 1, guess, l, q, st,
-                                       &ro_r, &rt_r);
+            const Poles<double> pp = {M, eps_s, z2_s, s.poled, s.poledf, z2df_s};
+            if (DF)
+                secular_root<double, EV_DFLOAT>(r, pp, mv.h, Z2, mode == 1, guess, l, q, st, &ro_r, &rt_r);
+            else
+                secular_root<double, EV_TABLE>(r, pp, mv.h, Z2, mode == 1, guess, l, q, st, &ro_r, &rt_r);
         } else {
             // no coupling: the eigenvalues are h and the bath energies
             int pos = 0;
@@ -1335,8 +1345,11 @@ cudaError_t launch_eigen(const DevState &s, const ModelDev &md, double dt, int m
     if (s.n == 0) return cudaSuccess;
     const int tpb = eigen_tpb(s.N);
     const int threads = round32(tpb * s.N);
-    const size_t smem = (size_t)(s.M + tpb * (s.M + 2 * s.N + eigen_pow2(s.N))) * sizeof(double);
-    k_eigen<<<(unsigned)((s.n + tpb - 1) / tpb), threads, smem, st>>>(s, md, dt, mode, tpb);
+    const bool df = s.eigen_dfloat != 0;
+    const size_t smem =
+        (size_t)(s.M + tpb * (s.M + 2 * s.N + eigen_pow2(s.N) + (df ? s.M : 0))) * sizeof(double);
+    if (df) k_eigen<true><<<(unsigned)((s.n + tpb - 1) / tpb), threads, smem, st>>>(s, md, dt, mode, tpb);
+    else k_eigen<false><<<(unsigned)((s.n + tpb - 1) / tpb), threads, smem, st>>>(s, md, dt, mode, tpb);
     return cudaGetLastError();
 }
 
