@@ -309,7 +309,7 @@ def run_ours(args):
             line["mixed"] = {
                 "value": world * n * args.steps / (ms_m / 1e3), "unit": UNIT,
                 "ms_per_step": ms_m / args.steps, "speedup_vs_fp64": ms / ms_m,
-                "dtype": "f32 coupling, propagation, overlap LU and ratio solves; f64 eigenpairs, forces, hop probabilities, rescale",
+                "dtype": "f32 coupling, propagation, overlap LU and ratio solves; double-float secular sums; f64 eigen iteration, forces, hop probabilities, rescale",
                 "kernel_time_share": {k: round(v[0] / tot_m, 4) for k, v in prof_m.items() if v[1]},
                 "roofline_propagate": roof_m,
                 "gpu_launches": int(sum(v[1] for v in prof_m.values())),

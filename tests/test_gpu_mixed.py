@@ -1,7 +1,7 @@
 """GPU parity of the mixed-precision path (IESH_PREC_MIXED) with the FP64 oracle.
 
-Mixed path: eigenpairs, forces, the hop probabilities from the ratios and
-the rescale in FP64; coupling generator, Chebyshev propagation,
+Mixed path: eigen iteration (with double-float pole sums), forces, the hop
+probabilities from the ratios and the rescale in FP64; coupling generator, Chebyshev propagation,
 coefficients, the LU of the overlap matrix and the ratio substitutions in
 FP32.  The propagator runs on the tensor cores (3xTF32,
 tcgen05) for N <= 128 and Ne <= 56 and as a register-tiled SIMT kernel
