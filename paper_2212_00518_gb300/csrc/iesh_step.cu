@@ -786,7 +786,7 @@ __host__ __device__ inline size_t hop_region_bytes(int N, int Ne, bool f32)
 size_t hop_smem_bytes(int N, int Ne, bool f32)
 {
     return hop_region_bytes(N, Ne, f32) + (size_t)16 * Ne + (size_t)(2 * N + 64) * 8 +
-           (size_t)(64 + 64 + 3 * Ne + 2 * N) * 4;
+           (size_t)(64 + 64 + 4 * Ne + 2 * N) * 4;
 }
 size_t hop_smem_bytes(int N, int Ne) { return hop_smem_bytes(N, Ne, false); }
 
@@ -819,6 +819,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
     int *rows = perm + Ne;                                        // [Ne] rows not yet pivots
     int *isocc = rows + Ne;                                       // [N]
     int *unocc = isocc + N;                                       // [N - Ne] ascending
+    int *pos_of = unocc + (N - Ne);                               // [Ne] position of a row in rows
     __shared__ int s_flag, s_hop_a, s_hop_m;
 
     const CT *Ct = reinterpret_cast<const CT *>(s.C) + (int64_t)t * Ne * N;
@@ -862,7 +863,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
         cand_v[warp] = bv;
         cand_i[warp] = bi;
         if (warp == 0)
-            for (int r = 0; r < Ne; ++r) rows[r] = r;
+            for (int r = 0; r < Ne; ++r) rows[r] = pos_of[r] = r;
     }
     __syncthreads();
 
@@ -874,14 +875,20 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
     int nr = Ne;
     for (int kc = 0; kc < Ne; ++kc) {
         const int buf = kc & 1;
+        // largest per-warp candidate (ties: lowest row), by a butterfly
         int bv = -1;
         int pr = Ne;
-        for (int w = 0; w < nwarp; ++w) {
-            const int vv = cand_v[buf * 32 + w];
-            const int i = cand_i[buf * 32 + w];
-            if (vv > bv || (vv == bv && i < pr)) {
-                bv = vv;
-                pr = i;
+        if (lane < nwarp) {
+            bv = cand_v[buf * 32 + lane];
+            pr = cand_i[buf * 32 + lane];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, pr, o);
+            if (ov > bv || (ov == bv && oi < pr)) {
+                bv = ov;
+                pr = oi;
             }
         }
         if (bv <= 0) {  // zero pivot column
@@ -889,11 +896,9 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
             break;
         }
         const CT pv = A[pr * Ne + kc];
-        // remove pr from the row list (every thread does the same edit on a
-        // private copy of the position; thread 0 writes it after the barrier)
-        int ppos = 0;
-        for (int q = 0; q < nr; ++q)
-            if (rows[q] == pr) ppos = q;
+        // remove pr from the row list: the last entry moves into its position
+        // (thread 0 writes the list after the barrier; readers redirect)
+        const int ppos = pos_of[pr];
         // multipliers of the remaining rows: only the warps that form them
         // take the FP64 reciprocal (the FP64 pipe charges every issuing warp)
         if (threadIdx.x < nr) {
@@ -907,7 +912,9 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
         __syncthreads();
         if (threadIdx.x == 0) {
             perm[kc] = pr;
-            rows[ppos] = rows[nr - 1];
+            const int last = rows[nr - 1];
+            rows[ppos] = last;
+            pos_of[last] = ppos;
         }
         const int nrow = nr - 1;  // rows to update (the list without pr)
         const int ncol = Ne - kc - 1;
@@ -1000,7 +1007,14 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
                 const bool live = u < nu;
                 const int m = live ? unocc[u] : 0;
                 float2 *y = Y + (size_t)(live ? grp : 0) * Ne;
-                // y U = c_m  (U_ij = A[perm[i]][j], i <= j)
+                // right-hand side c_m gathered up front (all loads in flight)
+                if (live)
+                    for (int i = sub; i < Ne; i += 4) {
+                        const CT c = Ct[(int64_t)i * N + m];
+                        y[i] = make_float2(c.x, c.y);
+                    }
+                __syncwarp(quad);
+                // y U = c_m  (U_ij = A[perm[i]][j], i <= j), in place
                 for (int jc = 0; jc < Ne; ++jc) {
                     float2 acc = make_float2(0.f, 0.f);
                     if (live)
@@ -1010,7 +1024,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
                     acc.x += __shfl_xor_sync(quad, acc.x, 2);
                     acc.y += __shfl_xor_sync(quad, acc.y, 2);
                     if (live && sub == (jc & 3)) {
-                        const CT c = Ct[(int64_t)jc * N + m];
+                        const float2 c = y[jc];
                         y[jc] = cmulf(make_float2(c.x + acc.x, c.y + acc.y), dinv32[jc]);
                     }
                 }
