@@ -19,8 +19,6 @@
 
 namespace iesh {
 
-constexpr double kU = 1.1102230246251565e-16;  // unit roundoff 2^-53
-
 // Trajectories per CTA of k_eigen: fill warps with one thread per root.
 int eigen_tpb(int N)
 {
@@ -794,8 +792,8 @@ size_t hop_smem_bytes(int N, int Ne) { return hop_smem_bytes(N, Ne, false); }
 // FP64 path.  float2: the mixed path -- S (read from the FP32 coefficients)
 // is factorised and substituted in FP32; |det S| for the skip bound and the
 // hop probabilities from the ratios are formed in FP64.
-// MAXT/MINB: launch bounds of the instantiation (512 x 1 for large S, 256 x
-// 3 when three CTAs fit in shared memory).
+// MAXT/MINB: launch bounds of the instantiation: 512 x 1 for large S;
+// 256 x 3 (FP64) or 256 x 4 (mixed, 64 registers) when that many CTAs fit.
 template <class CT, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, double mass, uint64_t seed,
                                                     int skip_bound, double *g_out)
@@ -1476,7 +1474,6 @@ void configure_hop_smem()
 {
     allow_max_smem(k_hop<float2, 512, 1>);
     allow_max_smem(k_hop<double2, 512, 1>);
-    allow_max_smem(k_hop<float2, 256, 3>);
     allow_max_smem(k_hop<float2, 256, 4>);
     allow_max_smem(k_hop<double2, 256, 3>);
     allow_max_smem(k_cheb_f32t<4>);
