@@ -121,3 +121,44 @@ def test_mixed_hop_decisions_on_hop_rich_case(P):
     agree = np.mean([np.array_equal(st["occ"][t], ref["occ"][t]) and hops[t] == ref["hops"][t]
                      for t in range(n)])
     assert agree >= 0.9, agree
+
+
+@pytest.mark.parametrize("name", ["paper40", "dw100", "dw200"])
+def test_mixed_eigenpairs_double_float_accuracy(P, name):
+    """The mixed path forms the secular pole sums in double-float arithmetic
+    (about 48 bits).  Stated error of the eigenpairs against the oracle's
+    Jacobi eigenpairs: 1e-12 relative for lambda, 1e-11 for q0, after a
+    cold start and after 5 warm-started steps."""
+    md, dt, shift = CASES[name]
+    n = 4
+    x, p, occ, C = _state(md, n, 17, 0.5, shift)
+    B = O.bind(md)
+    ctx = P.Context(md, n, precision=P.PREC_MIXED)
+    ctx.set_state(x, p, occ, C.astype(np.complex64))
+    for steps in (0, 5):
+        if steps:
+            ctx.run(dt, steps, seed=1)
+        xs = ctx.get_state()["x"]
+        lam, q0, _ = ctx.eigen()
+        for t in range(n):
+            lo, Qo = O.eigen(B, xs[t])[:2]
+            scale = np.abs(lo).max()
+            assert np.abs(lam[t] - lo).max() <= 1e-12 * scale
+            assert np.abs(q0[t] - Qo[0]).max() <= 1e-11
+
+
+def test_mixed_two_lead_eigenpairs(P):
+    md = W.morse_image(50, bias=0.1)
+    n = 4
+    x = np.linspace(W.angstrom(1.8), W.angstrom(6.0), n)
+    p = np.zeros(n)
+    occ = W.lowest_occupations(n, md["Ne"])
+    C = W.unit_coefficients(occ, 51).astype(np.complex64)
+    ctx = P.Context(md, n, precision=P.PREC_MIXED)
+    ctx.set_state(x, p, occ, C)
+    lam, q0, _ = ctx.eigen()
+    B = O.bind(md)
+    for t in range(n):
+        lo, Qo = O.eigen(B, x[t])[:2]
+        assert np.abs(lam[t] - lo).max() <= 1e-12 * np.abs(lo).max()
+        assert np.abs(q0[t] - Qo[0]).max() <= 1e-11
