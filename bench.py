@@ -31,7 +31,9 @@ import iesh_inputs as W  # noqa: E402
 METRIC = "IESH trajectory-steps/s (batched, 1 GB300) vs plain FP64 path; % of roofline"
 UNIT = "traj-steps/s"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 nominal FP64 rate (recipe's nominal table)
+# FP64 peak derived from the unit counts and clocks: 2 DFMA per clock per SM
+# (ncu's dfma peak counter), 152 SMs, 2.07 GHz maximum SM clock
+FP64_NOMINAL_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 SIMT at the maximum SM clock
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 tensor rate
 # DRAM bytes (read + write) per trajectory of the dominant kernel, from the ncu capture in
@@ -264,8 +266,8 @@ def run_ours(args):
             "roofline": {"bound": "alu", "kernel": "k_cheb (Chebyshev exponential integrator)",
                          "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                          "frac": (achieved / FP64_NOMINAL_TFLOPS) if achieved else None,
-                         "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak in "
-                                        "MEASURED_PEAKS.json)",
+                         "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (no measured "
+                                        "FP64 peak in MEASURED_PEAKS.json; a DFMA probe measured 1.20)",
                          "traffic": KCHEB_FP64_TRAFFIC_PER_TRAJ * n if args.M == 100 else None,
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
                                            "1024-trajectory capture scaled to the launch",
