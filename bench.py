@@ -409,8 +409,9 @@ def _timed_steps(torch, stream, fn, warmup, steps):
 
 
 def run_workload(args):
-    """Secondary measurements (one JSON line each): the M=200 mixed batch,
-    the paper-shaped timing grid, the uneven scattering batch, E_occ."""
+    """Secondary measurements (one JSON line each): the paper-shaped timing
+    grid, the uneven scattering batch, the desorption/scattering ensembles of
+    the desorption model, E_occ."""
     import torch
 
     import paper_2212_00518_gb300 as P
@@ -458,7 +459,8 @@ def run_workload(args):
         live_steps = ub.run(ub.steps_done + 64 * args.steps)
         sec = time.perf_counter() - t0
         line.update(metric=METRIC + " [uneven scattering batch]", value=live_steps / sec,
-                    dtype="mixed (f32 propagation, f64 eigen/LU/rescale)",
+                    dtype="mixed (f32 coupling, propagation, LU and ratio solves; double-float secular sums; "
+                          "f64 eigen iteration, forces, rescale)",
                     config={"workload": "16384 Morse + image-charge scattering trajectories, M in "
                                         "{50, 100, 200} (Ne = M/2), bias 0 / 0.05 / 0.1 a.u. (two "
                                         "leads), E_inc 0.2-1.5 eV from 5 angstrom, dt 0.1 fs, "
@@ -467,6 +469,70 @@ def run_workload(args):
                             "contexts": len(groups), "live_after": ub.live(),
                             "steps_timed": 64 * args.steps})
         ub.close()
+    elif args.workload == "erpenbeck":
+        # Sec. III C desorption and Sec. III D scattering on the desorption model
+        # with the paper's converged settings: 100 GL states, band 64 eV,
+        # Gamma = 1 eV, dt = 0.1 fs, threshold 5 angstrom; mixed precision.
+        dt = 0.1 * W.FS_AU
+        thr = W.angstrom(5.0)
+        kT = 300 * W.KB_HARTREE_PER_K
+        md = W.desorption(1.0, 100, band_ev=64.0)
+        warm = P.Context(md, 64, precision=P.PREC_MIXED, stream=stream.cuda_stream)
+        warm.init_state(64, kT_nuc=kT, kT_el=kT, seed=99)
+        warm.run(dt, max(1, args.warmup), 0)
+        warm.close()
+
+        def timed_run(ctx, n_steps):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            ctx.run(dt, n_steps, 1)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            return ev0.elapsed_time(ev1) / 1e3
+
+        n_des, steps_des = 2048, 2000  # 200 fs
+        c = P.Context(md, n_des, precision=P.PREC_MIXED, z_done=thr, compact_every=64,
+                      stream=stream.cuda_stream)
+        c.init_state(n_des, kT_nuc=kT, kT_el=kT, seed=1)
+        sec = timed_run(c, steps_des)
+        st = c.get_state()
+        ns = c.counters()[0]
+        done = (st["status"] & P.iesh.TRAJ_DONE) != 0
+        pdes = {f"{t} fs": float(np.mean(done & (ns <= int(round(t * W.FS_AU / dt)))))
+                for t in (50, 100, 150, 200)}
+        des = {"trajectories": n_des, "steps": steps_des, "live_traj_steps": int(ns.sum()),
+               "live_traj_steps_per_s": float(ns.sum()) / sec, "seconds": sec, "P_des": pdes}
+        c.close()
+        scat = []
+        for E in (0.25, 0.5, 1.0, 1.5):
+            n_sc = 1024
+            mds, x, p, occ, C = W.erpenbeck_scattering(n_sc, E, M=100, band_ev=64.0)
+            c = P.Context(mds, n_sc, precision=P.PREC_MIXED, z_done=thr, compact_every=64,
+                          stream=stream.cuda_stream)
+            c.set_state(x, p, occ, C.astype(np.complex64))
+            sec = timed_run(c, 3000)  # 300 fs
+            st = c.get_state()
+            ns = c.counters()[0]
+            done = (st["status"] & P.iesh.TRAJ_DONE) != 0
+            loss = W.ev(E) - st["p"][done] ** 2 / (2 * mds["mass"])
+            scat.append({"E_inc_eV": E, "rebounded": float(done.mean()),
+                         "KE_loss_eV": float(loss.mean() / W.ev(1.0)) if done.any() else None,
+                         "KE_loss_se_eV": float(loss.std() / np.sqrt(max(done.sum(), 1)) / W.ev(1.0)),
+                         "live_traj_steps_per_s": float(ns.sum()) / sec})
+            c.close()
+        line.update(metric=METRIC + " [desorption model: Sec. III C desorption, Sec. III D scattering]",
+                    value=des["live_traj_steps_per_s"],
+                    dtype="mixed (f32 coupling, propagation, LU and ratio solves; double-float "
+                          "secular sums; f64 eigen iteration, forces, rescale)",
+                    config={"workload": "desorption model (Table II), 100 GL states, band 64 eV, "
+                                        "Gamma 1 eV, dt 0.1 fs, threshold 5 angstrom, work list "
+                                        "compacted every 64 steps; desorption: 2048 trajectories, "
+                                        "Wigner 300 K nuclei and canonical 300 K electrons, 200 fs; "
+                                        "scattering: 1024 trajectories per E_inc from 5 angstrom, "
+                                        "0 K electrons, up to 300 fs",
+                            "value_is": "desorption live trajectory-steps/s"},
+                    results={"desorption": des, "scattering": scat})
     elif args.workload == "eocc":
         from paper_2212_00518_gb300 import eocc as E
         wl = W.eocc_workload(M=300, B=65536, seed=5)
@@ -509,7 +575,7 @@ def main():
                          "the uniform (Sec. II C; hop decisions unchanged)")
     ap.add_argument("--no-overlap", action="store_true",
                     help="skip the diabatic-basis propagator variant")
-    ap.add_argument("--workload", choices=["dw", "paper", "scatter", "eocc"], default="dw",
+    ap.add_argument("--workload", choices=["dw", "paper", "scatter", "erpenbeck", "eocc"], default="dw",
                     help="dw: the double-well batch (default, --M/--n-traj); the others print "
                          "secondary measurements")
     ap.add_argument("--autotune", action="store_true")

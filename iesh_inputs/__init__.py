@@ -170,6 +170,19 @@ def eocc_workload(M=300, B=65536, seed=5, Ne=None, band=(-0.5, 0.5)):
 
 
 # ----------------------------------------------------- uneven scattering batch
+def erpenbeck_scattering(n, E_inc_ev, M=100, Gamma_ev=1.0, band_ev=64.0, z0_ang=5.0):
+    """Scattering on the desorption model (Sec. III D): every trajectory starts
+    at z0 moving toward the surface with kinetic energy E_inc, electrons in
+    the Ne lowest orbitals (0 K) with unit coefficients.  Returns
+    (model, x, p, occ, C); C is [n][Ne][N] complex128."""
+    md = desorption(Gamma_ev, M, band_ev=band_ev)
+    x = np.full(n, angstrom(z0_ang))
+    p = np.full(n, -np.sqrt(2.0 * md["mass"] * ev(E_inc_ev)))
+    occ = lowest_occupations(n, md["Ne"])
+    C = unit_coefficients(occ, md["M"] + 1)
+    return md, x, p, occ, C
+
+
 def scattering_batch(n=16384, seed=4, M_choices=(50, 100, 200), biases=(0.0, 0.05, 0.1),
                      e_range_ev=(0.2, 1.5), z0_ang=5.0, Gamma_ev=1.0, band_ev=64.0):
     """Scattering trajectories of the Morse + image-charge model with uneven

@@ -71,6 +71,7 @@ typedef double complex cplx;
 #define ORC_ST_JACOBI_NONCONV 1u
 #define ORC_ST_SINGULAR 2u
 #define ORC_ST_NAN 4u
+#define ORC_ST_DONE 8u /* left the region: x > z_done at the end of a step (Sec. III C) */
 
 /* ------------------------------------------------------------------------ */
 /* Cyclic Jacobi for a real symmetric matrix (row-major, destroyed).         */
@@ -876,6 +877,8 @@ typedef struct {
     double dt;
     uint64_t seed, step0;
     int brute, prop, record_every, n_rec;
+    double z_done;  /* a trajectory finishes at the end of the first step with x > z_done (0: never) */
+    int64_t *steps; /* steps taken per trajectory (optional) */
     double *x, *p, *F;
     int *occ;
     cplx *C;
@@ -902,9 +905,11 @@ static void *run_range(void *arg)
         t.hops = 0;
         t.frustrated = 0;
         traj_prepare(md, &t);
+        int64_t taken = 0;
         for (int64_t s = 0; s < J->n_steps; s++) {
             traj_step(md, &t, J->dt, J->seed, (uint32_t)i, J->step0 + (uint64_t)s, J->brute, J->prop,
                       NULL, NULL, NULL);
+            taken = s + 1;
             if (J->record_every > 0 && ((s + 1) % J->record_every) == 0) {
                 int64_t r = (s + 1) / J->record_every - 1;
                 if (r < J->n_rec) {
@@ -914,7 +919,12 @@ static void *run_range(void *arg)
                     J->pop_wf[r * J->n_traj + i] = b;
                 }
             }
+            if (J->z_done > 0.0 && t.x > J->z_done) {
+                t.status |= ORC_ST_DONE;
+                break;
+            }
         }
+        if (J->steps) J->steps[i] = taken;
         J->x[i] = t.x;
         J->p[i] = t.p;
         J->F[i] = t.F;
@@ -939,7 +949,7 @@ int orc_run(int kind, double mass, const double *par, double Vbar, int M, int Ne
             int *occ, cplx *C, double dt, int64_t n_steps, uint64_t seed, uint64_t step0,
             int brute, int record_every, int n_rec, double *pop_sh, double *pop_wf,
             uint32_t *status, int64_t *hops, int64_t *frustrated, double *lam_out, int n_threads,
-            int prop)
+            int prop, double z_done, int64_t *steps)
 {
     orc_model md;
     make_model(&md, kind, mass, par, Vbar, M, Ne, eps, sqw);
@@ -958,6 +968,8 @@ int orc_run(int kind, double mass, const double *par, double Vbar, int M, int Ne
         J->step0 = step0;
         J->brute = brute;
         J->prop = prop;
+        J->z_done = z_done;
+        J->steps = steps;
         J->record_every = record_every;
         J->n_rec = n_rec;
         J->x = x; J->p = p; J->F = F; J->occ = occ; J->C = C;

@@ -70,7 +70,7 @@ def lib():
                               ctypes.c_int, _dp, _dp, ctypes.c_int64, _dp, _dp, _dp, _ip, _vp,
                               ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
                               ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _u32p, _i64p,
-                              _i64p, _dp, ctypes.c_int, ctypes.c_int]
+                              _i64p, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _i64p]
         L.orc_step_one.argtypes = [ctypes.c_int, ctypes.c_double, _dp, ctypes.c_double,
                                    ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _ip, _vp,
                                    ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
@@ -316,9 +316,11 @@ def step_one(model_or_bound, x, p, occ, C, dt, seed, traj, n, brute=False, prop=
 
 
 def run(model_or_bound, x, p, occ, C, dt, n_steps, seed, step0=0, brute=False,
-        record_every=0, n_threads=None, prop=0):
+        record_every=0, n_threads=None, prop=0, z_done=0.0):
     """Advance a batch: x, p [n]; occ [n][Ne]; C [n][N][Ne].  prop selects the
-    electronic propagator (0 averaged-generator exponential, 1 overlap).
+    electronic propagator (0 averaged-generator exponential, 1 overlap).  With
+    z_done > 0 a trajectory stops at the end of the first step with
+    x > z_done (status bit 8); "steps" holds the steps each one took.
     Returns a dict."""
     B = model_or_bound if isinstance(model_or_bound, _Bound) else _Bound(model_or_bound)
     x = _c(x).copy()
@@ -332,6 +334,7 @@ def run(model_or_bound, x, p, occ, C, dt, n_steps, seed, step0=0, brute=False,
     hops = np.zeros(n, dtype=np.int64)
     frus = np.zeros(n, dtype=np.int64)
     lam = np.zeros((n, B.N))
+    steps = np.zeros(n, dtype=np.int64)
     n_rec = int(n_steps // record_every) if record_every else 0
     psh = np.zeros((max(n_rec, 1), n))
     pwf = np.zeros((max(n_rec, 1), n))
@@ -341,9 +344,10 @@ def run(model_or_bound, x, p, occ, C, dt, n_steps, seed, step0=0, brute=False,
                   _d(p), _d(F), occ.ctypes.data_as(_ip), C.ctypes.data, float(dt), int(n_steps),
                   int(seed), int(step0), int(brute), int(record_every), n_rec, _d(psh), _d(pwf),
                   status.ctypes.data_as(_u32p), hops.ctypes.data_as(_i64p),
-                  frus.ctypes.data_as(_i64p), _d(lam), int(n_threads), int(prop))
+                  frus.ctypes.data_as(_i64p), _d(lam), int(n_threads), int(prop), float(z_done),
+                  steps.ctypes.data_as(_i64p))
     return dict(x=x, p=p, F=F, occ=occ, C=C, status=status, hops=hops, frustrated=frus,
-                lam=lam, pop_sh=psh[:n_rec], pop_wf=pwf[:n_rec])
+                lam=lam, pop_sh=psh[:n_rec], pop_wf=pwf[:n_rec], steps=steps)
 
 
 def propagate_overlap(lam0, Q0, lam1, Q1, dt, C):

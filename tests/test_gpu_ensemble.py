@@ -89,3 +89,62 @@ def test_identical_hop_decisions_over_ten_thousand_steps(P):
     assert hops.sum() > 50
     assert np.array_equal(hops, ref["hops"]) and np.array_equal(fr, ref["frustrated"])
     assert np.array_equal(st["occ"], ref["occ"])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_desorption_curve_matches_oracle(P, precision):
+    """P_des(t) of Sec. III C: the fraction of trajectories that have passed
+    x > 5 angstrom by time t, from the library's finished-trajectory flag and
+    step counters, against the oracle's first-passage steps on matched
+    ensembles (Wigner 300 K nuclei and canonical 300 K electrons sampled on
+    the device; the same states start the oracle)."""
+    md = W.desorption(1.0, 16, band_ev=16.0, mu_ev=0.0)
+    n, steps, seed = 128, 1000, 11
+    kT = 300 * W.KB_HARTREE_PER_K
+    thr = W.angstrom(5.0)
+    dt = 0.1 * W.FS_AU
+    ctx = P.Context(md, n, precision=precision, z_done=thr)
+    ctx.init_state(n, kT_nuc=kT, kT_el=kT, seed=seed)
+    st0 = ctx.get_state()
+    ctx.run(dt, steps, seed=3)
+    st = ctx.get_state()
+    ns = ctx.counters()[0]
+    C0 = np.transpose(st0["C"].astype(np.complex128), (0, 2, 1))
+    ref = O.run(O.bind(md), st0["x"], st0["p"], st0["occ"].astype(np.int32), C0, dt, steps, seed=3,
+                z_done=thr)
+    done_g = (st["status"] & P.iesh.TRAJ_DONE) != 0
+    done_o = (ref["status"] & 8) != 0
+    assert done_o.mean() > 0.02, "ensemble must desorb"
+    for t_fs in (25, 50, 75, 100):
+        k = int(round(t_fs * W.FS_AU / dt))
+        pg = np.mean(done_g & (ns <= k))
+        po = np.mean(done_o & (ref["steps"] <= k))
+        se = math.sqrt(max(po * (1 - po), 1.0 / n) / n)
+        assert abs(pg - po) <= 3 * math.sqrt(2) * se, (t_fs, pg, po)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_scattering_energy_loss_matches_oracle(P, precision):
+    """Sec. III D scattering on the desorption model: start at 5 angstrom
+    toward the surface with E_inc = 1 eV, electrons at 0 K, stop on the
+    rebound through 5 angstrom; the kinetic-energy loss of the rebounded
+    trajectories against the oracle's (matched ensembles, 3 standard errors)."""
+    n, E_inc = 64, 1.0
+    md, x, p, occ, C = W.erpenbeck_scattering(n, E_inc, M=16, band_ev=16.0)
+    thr = W.angstrom(5.0)
+    dt = 0.1 * W.FS_AU
+    steps = 3000  # 300 fs
+    ctx = P.Context(md, n, precision=precision, z_done=thr)
+    ctx.set_state(x, p, occ, C if precision == 0 else C.astype(np.complex64))
+    ctx.run(dt, steps, seed=5)
+    st = ctx.get_state()
+    ref = O.run(O.bind(md), x, p, occ.astype(np.int32), np.transpose(C, (0, 2, 1)), dt, steps, seed=5,
+                z_done=thr)
+    done_g = (st["status"] & P.iesh.TRAJ_DONE) != 0
+    done_o = (ref["status"] & 8) != 0
+    assert done_o.mean() > 0.9 and done_g.mean() > 0.9
+    e_inc = W.ev(E_inc)
+    lg = e_inc - st["p"][done_g] ** 2 / (2 * md["mass"])
+    lo = e_inc - ref["p"][done_o] ** 2 / (2 * md["mass"])
+    se = math.sqrt(max(lo.var(), 1e-12) / len(lo))
+    assert abs(lg.mean() - lo.mean()) <= 3 * math.sqrt(2) * se + 1e-9 * e_inc, (lg.mean(), lo.mean())
