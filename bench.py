@@ -533,6 +533,46 @@ def run_workload(args):
                                         "0 K electrons, up to 300 fs",
                             "value_is": "desorption live trajectory-steps/s"},
                     results={"desorption": des, "scattering": scat})
+    elif args.workload == "relaxation":
+        # Sec. III B double-well relaxation: 40 bath states, band 10 Gamma,
+        # 1000 trajectories from Boltzmann nuclei at 5 kT and canonical
+        # electrons at kT, dt = 100 a.u., 10^5 steps (10^7 a.u.); 1 - P_d
+        # (hole-impurity population) and the mean kinetic energy every 1000
+        # steps, GL and trapezoid baths.
+        kT, dt, n, chunks, every = 9.5e-4, 100.0, 1000, 100, 1000
+        res = {}
+        total_steps, total_sec = 0, 0.0
+        for disc in ("gl", "trapezoid"):
+            md = W.double_well_paper(40, disc=disc)
+            c = P.Context(md, n, precision=P.PREC_MIXED, stream=stream.cuda_stream)
+            c.init_state(n, kT_nuc=5 * kT, kT_el=kT, seed=7)
+            hole, ke = [], []
+            torch.cuda.synchronize()
+            for _ in range(chunks):
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                c.run(dt, every, 0)
+                ev1.record(stream)
+                st = c.get_state()  # synchronises
+                total_sec += ev0.elapsed_time(ev1) / 1e3
+                total_steps += n * every
+                lam, q0, _ = c.eigen()
+                # wavefunction impurity population sum_e |sum_i q0_i C_ie|^2
+                amp = np.einsum("ti,tei->te", q0, st["C"])
+                hole.append(float(1.0 - np.mean(np.sum(np.abs(amp) ** 2, axis=1))))
+                ke.append(float(np.mean(st["p"] ** 2) / (2 * md["mass"])))
+            res[disc] = {"t_au": [dt * every * (k + 1) for k in range(chunks)], "hole_population": hole,
+                         "kinetic_energy": ke, "KE_over_kT_final": ke[-1] / kT}
+            c.close()
+        line.update(metric=METRIC + " [double-well relaxation, Sec. III B]", value=total_steps / total_sec,
+                    dtype="mixed (f32 coupling, propagation, LU and ratio solves; double-float "
+                          "secular sums; f64 eigen iteration, forces, rescale)",
+                    config={"workload": "paper double well (m=2000, w=2e-4, g=20.6097, dG=-3.8e-3, "
+                                        "Gamma=6.4e-3, 40 states, band 10 Gamma), 1000 trajectories, "
+                                        "Boltzmann 5 kT nuclei, canonical kT electrons, dt=100, "
+                                        "10^5 steps, GL and trapezoid discretisations",
+                            "classical_KE_limit": kT / 2},
+                    results=res)
     elif args.workload == "eocc":
         from paper_2212_00518_gb300 import eocc as E
         wl = W.eocc_workload(M=300, B=65536, seed=5)
@@ -575,7 +615,8 @@ def main():
                          "the uniform (Sec. II C; hop decisions unchanged)")
     ap.add_argument("--no-overlap", action="store_true",
                     help="skip the diabatic-basis propagator variant")
-    ap.add_argument("--workload", choices=["dw", "paper", "scatter", "erpenbeck", "eocc"], default="dw",
+    ap.add_argument("--workload", choices=["dw", "paper", "scatter", "erpenbeck", "relaxation", "eocc"],
+                    default="dw",
                     help="dw: the double-well batch (default, --M/--n-traj); the others print "
                          "secondary measurements")
     ap.add_argument("--autotune", action="store_true")

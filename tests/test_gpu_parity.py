@@ -31,6 +31,7 @@ MODELS = {
     "dw20": (W.double_well(20), 0.01, 1.0),
     "dw100": (W.double_well(100), 0.01, 1.0),
     "paper40": (W.double_well_paper(40), 5 * 9.5e-4, 10.0),
+    "paper40trap": (W.double_well_paper(40, disc="trapezoid"), 5 * 9.5e-4, 10.0),
     "desorb50": (W.desorption(1.0, 50), None, 4.0),
     "image50": (W.morse_image(50), None, 4.0),
 }
@@ -64,7 +65,7 @@ def _close(a, b, scale, rtol=RTOL, what=""):
 
 
 # ------------------------------------------------------------------ bath
-@pytest.mark.parametrize("name", ["dw100", "paper40", "image50"])
+@pytest.mark.parametrize("name", ["dw100", "paper40", "paper40trap", "image50"])
 def test_bath_matches_oracle(P, name):
     md = MODELS[name][0]
     ctx = P.Context(md, 1)
