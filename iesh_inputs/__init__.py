@@ -169,6 +169,30 @@ def eocc_workload(M=300, B=65536, seed=5, Ne=None, band=(-0.5, 0.5)):
                 R=R, theta=theta, x=x)
 
 
+def two_orbital(M=40, seed=5, mass=2000.0, omega=0.01, Ne=None, band=(-0.5, 0.5), vscale=1.0):
+    """Two-orbital dynamics model: the occupied-energy model's electrons
+    (eocc_workload) with a harmonic restraint of frequency omega on each of
+    the six coordinates around x0 = R (the coupling centres).  vscale scales
+    both couplings."""
+    wl = eocc_workload(M=M, B=1, seed=seed, Ne=Ne, band=band)
+    return dict(M=wl["M"], Ne=wl["Ne"], band=wl["band"], Vbar=vscale * np.asarray(wl["Vbar"]),
+                R=np.asarray(wl["R"]), theta=np.asarray(wl["theta"]), mass=float(mass),
+                omega=float(omega), x0=np.asarray(wl["R"]).copy())
+
+
+def two_orbital_state(md, n, seed, kT=0.01, occ="random", weight=0.5):
+    """Thermal positions/momenta around x0 ([n][6]), occupations and
+    coefficients ([n][Ne][N], N = M + 2)."""
+    rng = np.random.default_rng(seed)
+    s = np.sqrt(kT / (md["mass"] * md["omega"] ** 2))
+    x = md["x0"][None, :] + rng.normal(0.0, s, (n, 6))
+    p = rng.normal(0.0, np.sqrt(md["mass"] * kT), (n, 6))
+    N = md["M"] + 2
+    o = random_occupations(n, N, md["Ne"], seed + 1) if occ == "random" else lowest_occupations(n, md["Ne"])
+    C = mixed_coefficients(o, N, seed + 2, weight)
+    return x, p, o, C
+
+
 # ----------------------------------------------------- uneven scattering batch
 def erpenbeck_scattering(n, E_inc_ev, M=100, Gamma_ev=1.0, band_ev=64.0, z0_ang=5.0):
     """Scattering on the desorption model (Sec. III D): every trajectory starts

@@ -1129,6 +1129,218 @@ int orc_eocc(int M, int Ne, const double *eps, const double *sqw, const double *
     return rc;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Two adsorbate orbitals over six nuclear coordinates (reading R10 of the  */
+/* two-orbital variant): the electronic Hamiltonian of the occupied-energy  */
+/* model (eocc_build) plus a harmonic restraint U0 = m w^2 |x - x0|^2 / 2   */
+/* on every coordinate (one mass).  The same IESH step as traj_step in six  */
+/* dimensions: velocity Verlet, dense eigenpairs (gauge: the combination    */
+/* c1 Q_1j + c2 Q_2j of the impurity components positive), T^a = Q^T dH/dx_a */
+/* Q, the averaged generator with v.d, hop probabilities with v.d, and the  */
+/* rescale along the NAC vector d_{m, s_a} with the smaller root.            */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int M, Ne;
+    const double *eps, *sqw, *Vbar, *R, *th; /* bath, couplings, theta[16] */
+    double mass, omega;
+    const double *x0;                        /* [6] restraint centres */
+} orc_model2;
+
+typedef struct {
+    double x[6], p[6], F[6], v_prev[6];
+    int *occ;
+    cplx *C;            /* [N][Ne] */
+    double *lam, *Q;    /* [N], [N][N] */
+    double *d;          /* [6][N][N] */
+    uint32_t status;
+    int64_t hops, frustrated;
+} orc_traj2;
+
+static void traj2_eigen(const orc_model2 *md, orc_traj2 *t)
+{
+    const int M = md->M, N = M + 2;
+    double *H = malloc(sizeof(double) * N * N), *V = malloc(sizeof(double) * N * N);
+    double *ev = malloc(sizeof(double) * N), *dHx = malloc(sizeof(double) * 6 * N * N);
+    int *idx = malloc(sizeof(int) * N);
+    eocc_build(M, md->eps, md->sqw, md->Vbar, md->R, t->x, md->th, H, dHx, NULL);
+    if (orc_jacobi_sym(N, H, ev, V) != 0) t->status |= ORC_ST_JACOBI_NONCONV;
+    for (int i = 0; i < N; i++) idx[i] = i;
+    for (int i = 0; i < N; i++)
+        for (int j = i + 1; j < N; j++)
+            if (ev[idx[j]] < ev[idx[i]]) { int tt = idx[i]; idx[i] = idx[j]; idx[j] = tt; }
+    /* coupling amplitudes c_a = Vbar_a f_a(x) (H[a][2] / sqw[0]) */
+    const double c1 = H[0 * N + 2] / md->sqw[0], c2 = H[1 * N + 2] / md->sqw[0];
+    for (int j = 0; j < N; j++) {
+        const int c = idx[j];
+        const double sgn = (c1 * V[0 * N + c] + c2 * V[1 * N + c]) < 0.0 ? -1.0 : 1.0;
+        t->lam[j] = ev[c];
+        for (int r = 0; r < N; r++) t->Q[r * N + j] = sgn * V[r * N + c];
+    }
+    /* T^a = Q^T dH/dx_a Q, d^a_jk = T^a_jk / (lam_k - lam_j); forces */
+    double *T = malloc(sizeof(double) * N * N), *tmp = malloc(sizeof(double) * N * N);
+    for (int a = 0; a < 6; a++) {
+        const double *D = dHx + (size_t)a * N * N;
+        for (int r = 0; r < N; r++)
+            for (int k = 0; k < N; k++) {
+                double sum = 0.0;
+                for (int q = 0; q < N; q++) sum += D[r * N + q] * t->Q[q * N + k];
+                tmp[r * N + k] = sum;
+            }
+        for (int j = 0; j < N; j++)
+            for (int k = 0; k < N; k++) {
+                double sum = 0.0;
+                for (int r = 0; r < N; r++) sum += t->Q[r * N + j] * tmp[r * N + k];
+                T[j * N + k] = sum;
+            }
+        for (int j = 0; j < N; j++)
+            for (int k = 0; k < N; k++)
+                t->d[(size_t)a * N * N + j * N + k] = (j == k) ? 0.0 : T[j * N + k] / (t->lam[k] - t->lam[j]);
+        double f = -md->mass * md->omega * md->omega * (t->x[a] - md->x0[a]);
+        for (int q = 0; q < md->Ne; q++) f -= T[t->occ[q] * N + t->occ[q]];
+        t->F[a] = f;
+    }
+    free(H); free(V); free(ev); free(dHx); free(idx); free(T); free(tmp);
+}
+
+/* v . d for the six-dimensional NAC tensor */
+static void vdot_d(int N, const double *d, const double *v, double *out)
+{
+    for (int j = 0; j < N * N; j++) {
+        double s = 0.0;
+        for (int a = 0; a < 6; a++) s += v[a] * d[(size_t)a * N * N + j];
+        out[j] = s;
+    }
+}
+
+static void traj2_step(const orc_model2 *md, orc_traj2 *t, double dt, uint64_t seed, uint32_t traj,
+                       uint64_t n)
+{
+    const int N = md->M + 2, Ne = md->Ne;
+    const double m = md->mass;
+    double *lam0 = malloc(sizeof(double) * N), *d0v = malloc(sizeof(double) * N * N);
+    double *d1v = malloc(sizeof(double) * N * N);
+    memcpy(lam0, t->lam, sizeof(double) * N);
+    vdot_d(N, t->d, t->v_prev, d0v);
+    for (int a = 0; a < 6; a++) {
+        t->p[a] += 0.5 * dt * t->F[a];
+        t->x[a] += dt * t->p[a] / m;
+    }
+    traj2_eigen(md, t);
+    double v1[6];
+    for (int a = 0; a < 6; a++) {
+        t->p[a] += 0.5 * dt * t->F[a];
+        v1[a] = t->p[a] / m;
+    }
+    vdot_d(N, t->d, v1, d1v);
+    if (orc_propagate(N, Ne, lam0, d0v, 1.0, t->lam, d1v, 1.0, dt, t->C) != 0)
+        t->status |= ORC_ST_JACOBI_NONCONV;
+    double *g = malloc(sizeof(double) * Ne * N);
+    cplx detS;
+    if (orc_hop_probs(N, Ne, t->occ, t->C, d1v, 1.0, dt, 0, g, NULL, &detS) != 0) t->status |= ORC_ST_SINGULAR;
+    const double zeta = orc_hop_uniform(seed, traj, n);
+    char *isocc = calloc(N, 1);
+    for (int a = 0; a < Ne; a++) isocc[t->occ[a]] = 1;
+    double cum = 0.0;
+    int ha = -1, hm = -1;
+    for (int a = 0; a < Ne && ha < 0; a++)
+        for (int mm = 0; mm < N; mm++) {
+            if (isocc[mm]) continue;
+            cum += g[a * N + mm];
+            if (cum > zeta) { ha = a; hm = mm; break; }
+        }
+    if (ha >= 0) {
+        /* p' = p + alpha d, d = d_{m, s_a} (vector), energy conserved, the
+         * smaller |alpha| (alpha -> 0 as dE -> 0) */
+        const int sa = t->occ[ha];
+        double dv[6], pd = 0.0, dd = 0.0;
+        for (int a = 0; a < 6; a++) {
+            dv[a] = t->d[(size_t)a * N * N + hm * N + sa];
+            pd += t->p[a] * dv[a];
+            dd += dv[a] * dv[a];
+        }
+        const double dE = t->lam[hm] - t->lam[sa];
+        const double disc = pd * pd - 2.0 * m * dd * dE;
+        if (dd > 0.0 && disc >= 0.0) {
+            const double alpha = (-pd + (pd >= 0.0 ? 1.0 : -1.0) * sqrt(disc)) / dd;
+            for (int a = 0; a < 6; a++) t->p[a] += alpha * dv[a];
+            t->occ[ha] = hm;
+            for (int i = 0; i < Ne; i++)
+                for (int j = i + 1; j < Ne; j++)
+                    if (t->occ[j] < t->occ[i]) { int tt = t->occ[i]; t->occ[i] = t->occ[j]; t->occ[j] = tt; }
+            traj2_eigen(md, t); /* forces on the new surface */
+            t->hops++;
+        } else {
+            t->frustrated++;
+        }
+    }
+    for (int a = 0; a < 6; a++) {
+        t->v_prev[a] = t->p[a] / m;
+        if (!isfinite(t->x[a]) || !isfinite(t->p[a])) t->status |= ORC_ST_NAN;
+    }
+    free(lam0); free(d0v); free(d1v); free(g); free(isocc);
+}
+
+/* Two-orbital trajectories: x, p [n][6]; occ [n][Ne]; C [n][N][Ne], N = M + 2.
+ * Returns final state, forces F [n][6], eigenvalues lam [n][N] (optional),
+ * status, hops, frustrated. */
+int orc_run2(int M, int Ne, const double *eps, const double *sqw, const double *Vbar, const double *R,
+             const double *th, double mass, double omega, const double *x0, int64_t n_traj, double *x,
+             double *p, double *F, int *occ, cplx *C, double dt, int64_t n_steps, uint64_t seed,
+             uint32_t *status, int64_t *hops, int64_t *frustrated, double *lam_out)
+{
+    orc_model2 md = {M, Ne, eps, sqw, Vbar, R, th, mass, omega, x0};
+    const int N = M + 2;
+    orc_traj2 t;
+    t.occ = malloc(sizeof(int) * Ne);
+    t.C = malloc(sizeof(cplx) * N * Ne);
+    t.lam = malloc(sizeof(double) * N);
+    t.Q = malloc(sizeof(double) * N * N);
+    t.d = malloc(sizeof(double) * 6 * N * N);
+    for (int64_t i = 0; i < n_traj; i++) {
+        memcpy(t.x, x + 6 * i, sizeof(double) * 6);
+        memcpy(t.p, p + 6 * i, sizeof(double) * 6);
+        memcpy(t.occ, occ + i * Ne, sizeof(int) * Ne);
+        memcpy(t.C, C + i * N * Ne, sizeof(cplx) * N * Ne);
+        t.status = 0;
+        t.hops = t.frustrated = 0;
+        traj2_eigen(&md, &t);
+        for (int a = 0; a < 6; a++) t.v_prev[a] = t.p[a] / mass;
+        for (int64_t s2 = 0; s2 < n_steps; s2++) traj2_step(&md, &t, dt, seed, (uint32_t)i, (uint64_t)s2);
+        memcpy(x + 6 * i, t.x, sizeof(double) * 6);
+        memcpy(p + 6 * i, t.p, sizeof(double) * 6);
+        memcpy(F + 6 * i, t.F, sizeof(double) * 6);
+        memcpy(occ + i * Ne, t.occ, sizeof(int) * Ne);
+        memcpy(C + i * N * Ne, t.C, sizeof(cplx) * N * Ne);
+        status[i] = t.status;
+        hops[i] = t.hops;
+        frustrated[i] = t.frustrated;
+        if (lam_out) memcpy(lam_out + i * N, t.lam, sizeof(double) * N);
+    }
+    free(t.occ); free(t.C); free(t.lam); free(t.Q); free(t.d);
+    return 0;
+}
+
+/* Eigenpairs (gauge-fixed), NAC tensor d [6][N][N] and forces [6] at one
+ * geometry x[6] for the occupations occ (sorted). */
+int orc_eigen2(int M, int Ne, const double *eps, const double *sqw, const double *Vbar, const double *R,
+               const double *th, double mass, double omega, const double *x0, const double *x,
+               const int *occ, double *lam, double *Q, double *d, double *F)
+{
+    orc_model2 md = {M, Ne, eps, sqw, Vbar, R, th, mass, omega, x0};
+    const int N = M + 2;
+    orc_traj2 t;
+    memcpy(t.x, x, sizeof(double) * 6);
+    t.occ = (int *)occ;
+    t.lam = lam;
+    t.Q = Q;
+    t.d = d;
+    t.status = 0;
+    traj2_eigen(&md, &t);
+    memcpy(F, t.F, sizeof(double) * 6);
+    (void)N;
+    return (int)t.status;
+}
+
 /* Determinant through an output pointer (out[0] real, out[1] imaginary). */
 void orc_det_x(int n, const cplx *A_in, double *out)
 {

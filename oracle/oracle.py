@@ -78,6 +78,11 @@ def lib():
         L.orc_propagate_overlap.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp,
                                             ctypes.c_double, _vp]
         L.orc_select.argtypes = [ctypes.c_int, ctypes.c_int, _ip, _dp, ctypes.c_double]
+        L.orc_run2.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, ctypes.c_double,
+                               ctypes.c_double, _dp, ctypes.c_int64, _dp, _dp, _dp, _ip, _vp,
+                               ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, _u32p, _i64p, _i64p, _dp]
+        L.orc_eigen2.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, ctypes.c_double,
+                                 ctypes.c_double, _dp, _dp, _ip, _dp, _dp, _dp, _dp]
         L.orc_eocc.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_int64,
                                _dp, _dp, _dp, _dp, _dp]
         _lib = L
@@ -357,6 +362,45 @@ def propagate_overlap(lam0, Q0, lam1, Q1, dt, C):
     lib().orc_propagate_overlap(N, C.shape[1], _d(_c(lam0)), _d(_c(Q0)), _d(_c(lam1)), _d(_c(Q1)),
                                 float(dt), C.ctypes.data)
     return C
+
+
+# ----------------------------------------------------- two-orbital dynamics
+def _two_bath(md):
+    eps, sqw = bath(dict(band=md["band"], M=md["M"], mu=0.0, disc="gl"))
+    return _c(eps), _c(sqw)
+
+
+def eigen2(md, x, occ):
+    """Two-orbital model at x[6]: lam[N], Q[N][N], d[6][N][N], F[6] (N = M + 2)."""
+    eps, sqw = _two_bath(md)
+    N = md["M"] + 2
+    lam, Q, d, F = np.zeros(N), np.zeros((N, N)), np.zeros((6, N, N)), np.zeros(6)
+    lib().orc_eigen2(md["M"], md["Ne"], _d(eps), _d(sqw), _d(_c(md["Vbar"])), _d(_c(md["R"])),
+                     _d(_c(md["theta"])), float(md["mass"]), float(md["omega"]), _d(_c(md["x0"])),
+                     _d(_c(x)), _c(occ, np.int32).ctypes.data_as(_ip), _d(lam), _d(Q), _d(d), _d(F))
+    return lam, Q, d, F
+
+
+def run2(md, x, p, occ, C, dt, n_steps, seed):
+    """Two-orbital IESH batch: x, p [n][6]; occ [n][Ne]; C [n][N][Ne]."""
+    eps, sqw = _two_bath(md)
+    x = _c(x).copy()
+    p = _c(p).copy()
+    n = x.shape[0]
+    occ = _c(occ, np.int32).copy()
+    C = _c(C, np.complex128).copy()
+    N = md["M"] + 2
+    F = np.zeros((n, 6))
+    status = np.zeros(n, np.uint32)
+    hops = np.zeros(n, np.int64)
+    frus = np.zeros(n, np.int64)
+    lam = np.zeros((n, N))
+    lib().orc_run2(md["M"], md["Ne"], _d(eps), _d(sqw), _d(_c(md["Vbar"])), _d(_c(md["R"])),
+                   _d(_c(md["theta"])), float(md["mass"]), float(md["omega"]), _d(_c(md["x0"])), n,
+                   _d(x), _d(p), _d(F), occ.ctypes.data_as(_ip), C.ctypes.data, float(dt), int(n_steps),
+                   int(seed), status.ctypes.data_as(_u32p), hops.ctypes.data_as(_i64p),
+                   frus.ctypes.data_as(_i64p), _d(lam))
+    return dict(x=x, p=p, F=F, occ=occ, C=C, status=status, hops=hops, frustrated=frus, lam=lam)
 
 
 # ------------------------------------------------------------- occupied energy

@@ -607,3 +607,91 @@ def test_population_invariants():
         Cu = O.unit_coefficients(B0.N, o[0])[None]
         r = O.run(B0, np.array([8.0]), np.array([0.0]), o, Cu, 1e-9, 1, seed=0, record_every=1)
         assert abs(r["pop_sh"][0, 0] - want) < 1e-12 and abs(r["pop_wf"][0, 0] - want) < 1e-12
+
+
+# ------------------------------------------------------ two-orbital dynamics
+def _two_energy(md, x, occ):
+    lam = O.eigen2(md, x, occ)[0]
+    u0 = 0.5 * md["mass"] * md["omega"] ** 2 * np.sum((x - md["x0"]) ** 2)
+    return u0 + lam[occ].sum()
+
+
+def test_two_orbital_force_is_minus_energy_gradient():
+    md = W.two_orbital(12, seed=5)
+    x, p, occ, C = W.two_orbital_state(md, 2, 3)
+    for t in range(2):
+        F = O.eigen2(md, x[t], occ[t])[3]
+        h = 1e-5
+        for a in range(6):
+            e = np.zeros(6)
+            e[a] = h
+            fd = -(_two_energy(md, x[t] + e, occ[t]) - _two_energy(md, x[t] - e, occ[t])) / (2 * h)
+            assert abs(F[a] - fd) < 1e-7 * max(1.0, abs(fd)), (a, F[a], fd)
+
+
+def test_two_orbital_nac_matches_fd_of_eigenvectors():
+    """d^a_jk = <j| d/dx_a k> in the gauge c1 Q_1j + c2 Q_2j > 0."""
+    md = W.two_orbital(10, seed=6)
+    x = W.two_orbital_state(md, 1, 4)[0][0]
+    occ = np.arange(md["Ne"])
+    lam, Q, d, _ = O.eigen2(md, x, occ)
+    h = 1e-6
+    for a in (0, 4):
+        e = np.zeros(6)
+        e[a] = h
+        Qp = O.eigen2(md, x + e, occ)[1]
+        Qm = O.eigen2(md, x - e, occ)[1]
+        fd = Q.T @ (Qp - Qm) / (2 * h)
+        gap = np.abs(lam[:, None] - lam[None, :]) + np.eye(len(lam))
+        ok = gap > 1e-3  # well-separated pairs (FD of near-degenerate pairs is ill-conditioned)
+        assert np.abs((fd - d[a])[ok]).max() < 1e-6 * max(1.0, np.abs(d[a][ok]).max())
+
+
+def test_two_orbital_steps_conserve_energy_and_norm():
+    """Velocity Verlet with hops rescaled along the NAC vector (strong
+    coupling, many hops): the total energy U0 + sum_occ lam + p^2 / 2m stays
+    within the Verlet error of the avoided crossings (the rescale itself is
+    exact), and the coefficient columns stay orthonormal."""
+    md = W.two_orbital(10, seed=7, vscale=1.0, omega=0.01)
+    n, steps, dt = 6, 200, 5.0
+    x, p, occ, C = W.two_orbital_state(md, n, 8, kT=0.01, weight=1.0)
+    e0 = np.array([_two_energy(md, x[t], occ[t]) + (p[t] ** 2).sum() / (2 * md["mass"]) for t in range(n)])
+    r = O.run2(md, x, p, occ, np.transpose(C, (0, 2, 1)), dt, steps, seed=2)
+    e1 = np.array([_two_energy(md, r["x"][t], r["occ"][t]) + (r["p"][t] ** 2).sum() / (2 * md["mass"])
+                   for t in range(n)])
+    assert r["hops"].sum() > 0, "case must hop"
+    assert np.abs(e1 - e0).max() < 2e-4 * np.abs(e0).max()
+    for t in range(n):
+        G = r["C"][t].conj().T @ r["C"][t]
+        assert np.abs(G - np.eye(md["Ne"])).max() < 1e-10
+
+
+def test_two_orbital_verlet_error_is_second_order():
+    """Without coupling (no NAC, no hop; the occupied levels h_a(x) still
+    drive the nuclei) the energy error after a fixed time falls as dt^2.  The
+    impurity levels sit deep inside the occupied range, so the summed
+    occupied energy has no kink (a level crossing the Fermi boundary would
+    make the surface non-smooth)."""
+    md = W.two_orbital(8, seed=11, vscale=0.0, omega=0.01)
+    md["theta"] = md["theta"].copy()
+    md["theta"][0:2] = [-0.30, -0.25]
+    x, p, occ, C = W.two_orbital_state(md, 1, 12, kT=0.01, occ="lowest", weight=0.0)
+    e0 = _two_energy(md, x[0], occ[0]) + (p[0] ** 2).sum() / (2 * md["mass"])
+    errs = []
+    for dt in (8.0, 4.0):
+        r = O.run2(md, x, p, occ, np.transpose(C, (0, 2, 1)), dt, int(800 / dt), seed=1)
+        assert r["hops"].sum() == 0
+        e1 = _two_energy(md, r["x"][0], r["occ"][0]) + (r["p"][0] ** 2).sum() / (2 * md["mass"])
+        errs.append(abs(e1 - e0))
+    assert 2.5 < errs[0] / errs[1] < 6.0, errs
+
+
+def test_two_orbital_zero_coupling_is_phase_only():
+    md = W.two_orbital(8, seed=9, vscale=0.0)
+    x, p, occ, C = W.two_orbital_state(md, 2, 10)
+    r = O.run2(md, x, p, occ, np.transpose(C, (0, 2, 1)), 5.0, 10, seed=1)
+    assert r["hops"].sum() == 0 and r["frustrated"].sum() == 0
+    lam = O.eigen2(md, r["x"][0], r["occ"][0])[0]
+    h = md["theta"][0:2] + np.array([md["theta"][2:8] @ r["x"][0], md["theta"][8:14] @ r["x"][0]])
+    eps = O.bath(dict(band=md["band"], M=md["M"], mu=0.0, disc="gl"))[0]
+    assert np.abs(np.sort(np.concatenate([h, eps])) - lam).max() < 1e-13
