@@ -1163,13 +1163,14 @@ static void traj2_eigen(const orc_model2 *md, orc_traj2 *t)
     double *ev = malloc(sizeof(double) * N), *dHx = malloc(sizeof(double) * 6 * N * N);
     int *idx = malloc(sizeof(int) * N);
     eocc_build(M, md->eps, md->sqw, md->Vbar, md->R, t->x, md->th, H, dHx, NULL);
+    /* coupling amplitudes c_a = Vbar_a f_a(x) = H[a][2] / sqw[0], read before
+     * the Jacobi sweeps overwrite H */
+    const double c1 = H[0 * N + 2] / md->sqw[0], c2 = H[1 * N + 2] / md->sqw[0];
     if (orc_jacobi_sym(N, H, ev, V) != 0) t->status |= ORC_ST_JACOBI_NONCONV;
     for (int i = 0; i < N; i++) idx[i] = i;
     for (int i = 0; i < N; i++)
         for (int j = i + 1; j < N; j++)
             if (ev[idx[j]] < ev[idx[i]]) { int tt = idx[i]; idx[i] = idx[j]; idx[j] = tt; }
-    /* coupling amplitudes c_a = Vbar_a f_a(x) (H[a][2] / sqw[0]) */
-    const double c1 = H[0 * N + 2] / md->sqw[0], c2 = H[1 * N + 2] / md->sqw[0];
     for (int j = 0; j < N; j++) {
         const int c = idx[j];
         const double sgn = (c1 * V[0 * N + c] + c2 * V[1 * N + c]) < 0.0 ? -1.0 : 1.0;

@@ -647,13 +647,41 @@ def test_two_orbital_nac_matches_fd_of_eigenvectors():
         assert np.abs((fd - d[a])[ok]).max() < 1e-6 * max(1.0, np.abs(d[a][ok]).max())
 
 
+def _two_c(md, x):
+    """Coupling amplitudes c_a = vbar_a f_a(x), written out from the model."""
+    th, R = md["theta"], md["R"]
+    return np.array([md["Vbar"][a] * np.exp(-0.5 * np.sum((x[3 * a:3 * a + 3] - R[3 * a:3 * a + 3]) ** 2)
+                                            / th[14 + a] ** 2) for a in range(2)])
+
+
+def test_two_orbital_gauge_is_the_coupled_combination_and_continuous():
+    """Eigenvector j is signed so that its component on the coupled
+    combination c_0|0> + c_1|1> is positive, and that choice is continuous
+    along a path: consecutive eigenvector matrices overlap with a positive
+    diagonal near 1 (the convention d_jj = 0 of the NACs and the adiabatic
+    coefficients rely on)."""
+    md = W.two_orbital(12, seed=5)
+    x0 = W.two_orbital_state(md, 1, 11)[0][0]
+    occ = np.arange(md["Ne"])
+    step = np.array([0.004, -0.003, 0.002, 0.003, 0.001, -0.004])
+    Qprev = None
+    for i in range(12):
+        x = x0 + i * step
+        lam, Q, _, _ = O.eigen2(md, x, occ)
+        c = _two_c(md, x)
+        assert np.all(c[0] * Q[0] + c[1] * Q[1] > 0)
+        if Qprev is not None:
+            assert np.all(np.diag(Qprev.T @ Q) > 0.9)
+        Qprev = Q
+
+
 def test_two_orbital_steps_conserve_energy_and_norm():
     """Velocity Verlet with hops rescaled along the NAC vector (strong
     coupling, many hops): the total energy U0 + sum_occ lam + p^2 / 2m stays
     within the Verlet error of the avoided crossings (the rescale itself is
     exact), and the coefficient columns stay orthonormal."""
     md = W.two_orbital(10, seed=7, vscale=1.0, omega=0.01)
-    n, steps, dt = 6, 200, 5.0
+    n, steps, dt = 6, 400, 2.5
     x, p, occ, C = W.two_orbital_state(md, n, 8, kT=0.01, weight=1.0)
     e0 = np.array([_two_energy(md, x[t], occ[t]) + (p[t] ** 2).sum() / (2 * md["mass"]) for t in range(n)])
     r = O.run2(md, x, p, occ, np.transpose(C, (0, 2, 1)), dt, steps, seed=2)
