@@ -281,6 +281,77 @@ iesh_status iesh_eocc_backward(iesh_eocc_ctx *ctx, int64_t B, int precision, con
                                const void *theta, const void *saved, const void *gE, void *dx,
                                void *dtheta_per, void *dtheta);
 
+/* ---------------------------------------------------------------------
+ * IESH dynamics of a two-orbital adsorbate over six nuclear coordinates.
+ *
+ * The electrons are those of the occupied-energy model above: orbital a =
+ * 0, 1 with level h_a(x) = theta[a] + sum_al theta[2 + 6a + al] x[al] and
+ * coupling vbar[a] sqrt(w_k) f_a(x), f_a = exp(-|x_a - R_a|^2 /
+ * (2 theta[14+a]^2)), to bath state k of the split Gauss-Legendre band
+ * (Appendix A, n_bath / 2 nodes below mu); N = n_bath + 2 orbitals.  The
+ * nuclei move on U0 = mass omega^2 |x - x0|^2 / 2 plus the occupied
+ * eigenvalues (the classical IESH Hamiltonian of Sec. II B), one mass for
+ * all six coordinates.  A step is the one-coordinate step of iesh_run in
+ * six dimensions (Sec. II B, II C): velocity Verlet, eigenpairs of the
+ * rank-two arrowhead, Hellmann-Feynman forces, the exponential of the
+ * step-averaged generator built from v . d (the NAC vectors projected on
+ * the velocity at each end of the step), hop probabilities from
+ * determinant ratios with v . d, and on a hop the momentum change
+ * p' = p + alpha d_{m, s_a} along the NAC vector that conserves the energy
+ * with the smaller |alpha|; no such alpha: the hop is frustrated.
+ *
+ * Eigenvector gauge: the component of eigenvector j on the coupled
+ * combination c_0 |0> + c_1 |1> (c_a = vbar[a] f_a) is >= 0.
+ * Layouts: x, p, F [n][6]; occ [n][Ne] int16 ascending; C [n][Ne][N]
+ * complex double; pointers host or device as for iesh_*.  FP64 only. */
+typedef struct iesh2_ctx iesh2_ctx;
+typedef struct {
+    int n_bath;        /* M (2..254) */
+    int n_elec;        /* Ne (1..min(M + 1, 112)) */
+    double band_lo, band_hi, mu; /* band and split point of the bath */
+    double mass;       /* nuclear mass (all six coordinates) */
+    double omega;      /* restraint frequency */
+    double x0[6];      /* restraint centres */
+    double theta[16];  /* eps_0, eps_1, g_{0,0..5}, g_{1,0..5}, sigma_0, sigma_1 */
+    double vbar[2];    /* coupling amplitudes */
+    double R[6];       /* coupling centres */
+} iesh2_model;
+
+/* Create a context for up to max_traj trajectories; skip_bound as in
+ * iesh_options.  On failure *out may hold a context carrying the message
+ * (destroy it). */
+iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int64_t max_traj, int skip_bound,
+                         void *cuda_stream);
+iesh_status iesh2_destroy(iesh2_ctx *ctx);
+const char *iesh2_last_error(const iesh2_ctx *ctx);
+
+/* Replace the state of n_traj trajectories and compute eigenpairs and
+ * forces there; counters are reset.  Returns after the copies finished. */
+iesh_status iesh2_set_state(iesh2_ctx *ctx, int64_t n_traj, const double *x, const double *p,
+                            const int16_t *occ, const void *C);
+iesh_status iesh2_get_state(iesh2_ctx *ctx, double *x, double *p, int16_t *occ, void *C,
+                            uint32_t *status);
+
+/* n_steps steps of length dt; the hop uniform of trajectory t at its step n
+ * is Philox4x32-10 with key = seed, counter = (t, 0, n_lo, n_hi). */
+iesh_status iesh2_run(iesh2_ctx *ctx, double dt, int64_t n_steps, uint64_t seed);
+
+/* Eigenvalues lam[n][N], adsorbate components Q[n][2][N] (row a: component
+ * on adsorbate orbital a of each eigenvector) and forces F[n][6] at the
+ * current positions and occupations. */
+iesh_status iesh2_get_eigen(iesh2_ctx *ctx, double *lam, double *Q, double *F);
+
+/* Hop probabilities g[n][Ne][N] of the current state (velocity p / mass),
+ * as used by the step; the state is not changed. */
+iesh_status iesh2_hop_probabilities(iesh2_ctx *ctx, double dt, double *g);
+
+/* Steps taken, accepted and frustrated hops per trajectory. */
+iesh_status iesh2_get_counters(iesh2_ctx *ctx, int64_t *nstep, int32_t *hops, int32_t *frustrated);
+
+/* Kernel timing, as iesh_profile / iesh_profile_read. */
+iesh_status iesh2_profile(iesh2_ctx *ctx, int enable);
+iesh_status iesh2_profile_read(iesh2_ctx *ctx, double *ms, int64_t *launches);
+
 /* Last error message of the context (never NULL). */
 const char *iesh_last_error(const iesh_ctx *ctx);
 

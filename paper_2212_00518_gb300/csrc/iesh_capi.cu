@@ -12,6 +12,7 @@
 
 #include "../../include/iesh.h"
 #include "iesh_common.cuh"
+#include "iesh_host.h"
 #include "iesh_kernels.h"
 
 using namespace iesh;
@@ -31,53 +32,14 @@ struct iesh_ctx {
     std::string err;
     int32_t *live = nullptr, *n_live = nullptr;  // device work list
     int64_t steps_since_init = 0;
-    // kernel timing
-    bool prof = false;
-    struct Rec {
-        int cls;
-        cudaEvent_t a, b;
-    };
-    std::vector<Rec> recs;
-    std::vector<cudaEvent_t> pool;
-    double prof_ms[IESH_K_COUNT] = {0};
-    int64_t prof_n[IESH_K_COUNT] = {0};
+    KernelTimer timer;  // kernel timing
 };
 
-static cudaEvent_t ev_get(iesh_ctx *c)
-{
-    if (!c->pool.empty()) {
-        cudaEvent_t e = c->pool.back();
-        c->pool.pop_back();
-        return e;
-    }
-    cudaEvent_t e;
-    cudaEventCreate(&e);
-    return e;
-}
-
-// Launch `fn` (returning cudaError_t) bracketed by events when profiling.
+// Launch `fn` (returning cudaError_t), bracketed by events when profiling.
 template <class Fn>
 static cudaError_t timed(iesh_ctx *c, int cls, Fn fn)
 {
-    if (!c->prof) return fn();
-    cudaEvent_t a = ev_get(c), b = ev_get(c);
-    cudaEventRecord(a, c->stream);
-    cudaError_t e = fn();
-    cudaEventRecord(b, c->stream);
-    c->recs.push_back({cls, a, b});
-    if (c->recs.size() > 4096) {  // fold finished records to bound memory
-        cudaEventSynchronize(b);
-        for (auto &r : c->recs) {
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, r.a, r.b);
-            c->prof_ms[r.cls] += ms;
-            c->prof_n[r.cls] += 1;
-            c->pool.push_back(r.a);
-            c->pool.push_back(r.b);
-        }
-        c->recs.clear();
-    }
-    return e;
+    return c->timer.run(c->stream, cls, fn);
 }
 
 static const double kPi = 3.14159265358979323846;
@@ -151,8 +113,8 @@ static void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w
 
 // One lead: n states on [a, b], split Gauss-Legendre at mu with n_lo nodes
 // below it (Appendix A), or the left-endpoint trapezoid rule.
-static void lead_bath(int disc, int n, double a, double b, double mu, int n_lo,
-                      std::vector<double> &eps, std::vector<double> &w)
+void iesh::lead_bath(int disc, int n, double a, double b, double mu, int n_lo, std::vector<double> &eps,
+                     std::vector<double> &w)
 {
     eps.clear();
     w.clear();
@@ -232,16 +194,6 @@ static iesh_status dalloc(iesh_ctx *ctx, T **p, size_t count)
     return IESH_OK;
 }
 
-static bool is_host_ptr(const void *p)
-{
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return true;
-    }
-    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
-}
-
 static iesh_status copy_in(iesh_ctx *ctx, void *dst, const void *src, size_t bytes)
 {
     if (!bytes) return IESH_OK;
@@ -283,11 +235,7 @@ iesh_status iesh_destroy(iesh_ctx *ctx)
 {
     if (!ctx) return IESH_OK;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    for (auto &r : ctx->recs) {
-        cudaEventDestroy(r.a);
-        cudaEventDestroy(r.b);
-    }
-    for (auto e : ctx->pool) cudaEventDestroy(e);
+    ctx->timer.release();
     for (void *p : ctx->allocs) cudaFree(p);
     delete ctx;
     return IESH_OK;
@@ -689,16 +637,7 @@ iesh_status iesh_profile(iesh_ctx *ctx, int enable)
 {
     if (!ctx) return IESH_EINVAL;
     CU(cudaStreamSynchronize(ctx->stream));
-    for (auto &r : ctx->recs) {
-        ctx->pool.push_back(r.a);
-        ctx->pool.push_back(r.b);
-    }
-    ctx->recs.clear();
-    for (int i = 0; i < IESH_K_COUNT; ++i) {
-        ctx->prof_ms[i] = 0.0;
-        ctx->prof_n[i] = 0;
-    }
-    ctx->prof = enable != 0;
+    ctx->timer.reset(enable != 0);
     return IESH_OK;
 }
 
@@ -706,18 +645,10 @@ iesh_status iesh_profile_read(iesh_ctx *ctx, double *ms, int64_t *launches)
 {
     if (!ctx) return IESH_EINVAL;
     CU(cudaStreamSynchronize(ctx->stream));
-    for (auto &r : ctx->recs) {
-        float m = 0.f;
-        CU(cudaEventElapsedTime(&m, r.a, r.b));
-        ctx->prof_ms[r.cls] += m;
-        ctx->prof_n[r.cls] += 1;
-        ctx->pool.push_back(r.a);
-        ctx->pool.push_back(r.b);
-    }
-    ctx->recs.clear();
+    CU(ctx->timer.fold());
     for (int i = 0; i < IESH_K_COUNT; ++i) {
-        if (ms) ms[i] = ctx->prof_ms[i];
-        if (launches) launches[i] = ctx->prof_n[i];
+        if (ms) ms[i] = ctx->timer.ms[i];
+        if (launches) launches[i] = ctx->timer.n[i];
     }
     return IESH_OK;
 }

@@ -65,6 +65,14 @@ struct DevState {
     // kernel shapes (0 = built-in choice): propagator electrons per thread
     // and column groups per CTA, threads of the hop kernel
     int cheb_ept, cheb_G, hop_threads;
+    // two adsorbate orbitals over six nuclear coordinates: x, p, F and vprev
+    // are [n][6]; q0 holds the components Q_0j on orbital 0 and q2 the
+    // components Q_1j on orbital 1; geo2 [n][8] holds h_0, h_1 and, with the
+    // velocity after the second half kick, grad h_a . v and grad log f_a . v
+    double *q2, *q2_prev;      // [n][N]
+    double *geo2;              // [n][8]
+    double *x_prev;            // [n][6] start of the step
+    int32_t *hop_pair;         // [n] a N + m of the selected hop, or -1
 };
 
 // Trajectory visited by work item w, or -1 when w is past the batch or the

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <vector>
+
 #include "iesh_common.cuh"
 
 namespace iesh {
@@ -15,7 +17,7 @@ cudaError_t launch_coupling(const DevState &s, double dt, double mass, double to
 cudaError_t launch_cheb(const DevState &s, double dt, bool mixed, cudaStream_t st);
 size_t hop_smem_bytes(int N, int Ne);
 cudaError_t launch_hop(const DevState &s, double dt, double mass, uint64_t seed, int skip_bound,
-                       double *g_out, cudaStream_t st, bool mixed = false);
+                       double *g_out, cudaStream_t st, bool mixed = false, bool ext = false);
 cudaError_t launch_init_nuclear(const DevState &s, double mass, uint64_t seed, double kT,
                                 int wigner, double omega, double x_eq, cudaStream_t st);
 cudaError_t launch_sample_occ(const DevState &s, uint64_t seed, double kT, cudaStream_t st);
@@ -23,6 +25,9 @@ cudaError_t launch_unit_coeffs(const DevState &s, bool fp32, cudaStream_t st);
 cudaError_t launch_compact(const DevState &s, int32_t *live, int32_t *n_live, cudaStream_t st);
 cudaError_t launch_live_init(int64_t n, int32_t *live, int32_t *n_live, cudaStream_t st);
 void configure_hop_smem();
+// Bath of one lead: energies and weights (Gauss-Legendre split at mu, or trapezoid)
+void lead_bath(int disc, int n, double a, double b, double mu, int n_lo, std::vector<double> &eps,
+               std::vector<double> &w);
 void cheb_shape(int N, int Ne, int &ept, int &G);
 // FP32 (mixed-precision) propagator: 4 electrons per thread, G column groups
 constexpr size_t kCheb32MaxSmem = 110 * 1024;

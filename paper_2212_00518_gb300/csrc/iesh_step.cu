@@ -16,6 +16,7 @@
 #include "iesh_common.cuh"
 #include "iesh_kernels.h"
 #include "iesh_secular.cuh"
+#include "iesh_cheb.cuh"
 
 namespace iesh {
 
@@ -212,62 +213,6 @@ __device__ __forceinline__ double nac(double lj, double qj, double lk, double qk
                                       double dh, double kap)
 {
     return qj * qk * (dh + kap * (lj + lk - 2.0 * h)) * pole_recip<double>(lk - lj);
-}
-
-// Bessel J_0..J_K(rho) by Miller's backward recurrence normalised with
-// J_0 + 2 sum_{k>=1} J_2k = 1.
-__device__ void bessel_j(double rho, int K, double *J)
-{
-    if (rho == 0.0) {
-        J[0] = 1.0;
-        for (int k = 1; k <= K; ++k) J[k] = 0.0;
-        return;
-    }
-    int top = (K > (int)rho ? K : (int)rho) + 24 + (int)(2.0 * sqrt((double)K + rho + 1.0));
-    top += top & 1;
-    double jp1 = 0.0, j = 1e-280, norm = 0.0;
-    const double inv = 2.0 / rho;
-    for (int k = top; k >= 1; --k) {
-        const double jm1 = k * inv * j - jp1;
-        jp1 = j;
-        j = jm1;
-        const int km = k - 1;
-        if (km <= K) J[km] = j;
-        if (km >= 2 && (km & 1) == 0) norm += 2.0 * j;
-        if (fabs(j) > 1e250) {
-            j *= 1e-250;
-            jp1 *= 1e-250;
-            norm *= 1e-250;
-            for (int q = km; q <= K && q <= top; ++q)
-                if (q >= km) J[q] *= 1e-250;
-        }
-    }
-    norm += j;  // J_0
-    const double sc = 1.0 / norm;
-    for (int k = 0; k <= K; ++k) J[k] *= sc;
-}
-
-// Chebyshev degree and coefficients for a spectrum inside [lo, hi] (in units
-// of dt): the smallest K whose tail bound 2 sum_{k>K} (rho/2)^k / k! is below
-// tol, and J_0..J_K(rho).  Called by one thread per trajectory.
-__device__ void cheb_setup(const DevState &s, int64_t t, double lo, double hi, double tol)
-{
-    double *cb = s.cheb + t * kChebStride;
-    const double c = 0.5 * (lo + hi), rho = 0.5 * (hi - lo);
-    int K = 0;
-    double term = rho * 0.5;  // (rho/2)^{K+1} / (K+1)!
-    while (K < kChebMax - 2) {
-        const double ratio = (rho * 0.5) / (K + 2);
-        const double tail = (ratio < 1.0) ? 2.0 * term / (1.0 - ratio) : 1e300;
-        if (tail <= tol) break;
-        ++K;
-        term *= (rho * 0.5) / (K + 1);
-    }
-    if (K >= kChebMax - 2) atomicOr(&s.status[t], ST_PROP);
-    cb[0] = c;
-    cb[1] = rho;
-    cb[2] = (double)K;
-    bessel_j(rho, K, cb + 3);
 }
 
 __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double mass, double tol)
@@ -781,12 +726,12 @@ __host__ __device__ inline size_t hop_region_bytes(int N, int Ne, bool f32)
     return (a + 15) & ~(size_t)15;
 }
 
-size_t hop_smem_bytes(int N, int Ne, bool f32)
+size_t hop_smem_bytes(int N, int Ne, bool f32, bool ext)
 {
-    return hop_region_bytes(N, Ne, f32) + (size_t)16 * Ne + (size_t)(2 * N + 64) * 8 +
+    return hop_region_bytes(N, Ne, f32) + (size_t)16 * Ne + (size_t)((ext ? 3 : 2) * N + 64) * 8 +
            (size_t)(64 + 64 + 4 * Ne + 2 * N) * 4;
 }
-size_t hop_smem_bytes(int N, int Ne) { return hop_smem_bytes(N, Ne, false); }
+size_t hop_smem_bytes(int N, int Ne) { return hop_smem_bytes(N, Ne, false, false); }
 
 // CT: coefficient type, also the type of the factorisation.  double2: the
 // FP64 path.  float2: the mixed path -- S (read from the FP32 coefficients)
@@ -794,7 +739,14 @@ size_t hop_smem_bytes(int N, int Ne) { return hop_smem_bytes(N, Ne, false); }
 // hop probabilities from the ratios are formed in FP64.
 // MAXT/MINB: launch bounds of the instantiation: 512 x 1 for large S;
 // 256 x 3 (FP64) or 256 x 4 (mixed, 64 registers) when that many CTAs fit.
-template <class CT, int MAXT, int MINB>
+// EXT: two adsorbate orbitals over six coordinates.  The coupling that
+// enters g is the velocity-projected v . d_{m, s_a} = T^v_{m s_a} /
+// (lam_{s_a} - lam_m) with T^v_jk = sum_a Q_aj Q_ak [grad h_a . v +
+// (grad log f_a . v) (lam_j + lam_k - 2 h_a)] (the one-orbital closed form
+// per adsorbate orbital, since c_a B_k = (lam_k - h_a) Q_ak on an
+// eigenvector); the kernel stops after the selection and writes the chosen
+// (a, m) to hop_pair for the six-dimensional rescale.
+template <class CT, int MAXT, int MINB, bool EXT = false>
 __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, double mass, uint64_t seed,
                                                     int skip_bound, double *g_out)
 {
@@ -810,7 +762,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
     double *lam_s = reinterpret_cast<double *>(dinv + Ne);         // [N]
     double *q0_s = lam_s + N;                                     // [N]
     double *red = q0_s + N;                                       // [64]
-    int *cand_v = reinterpret_cast<int *>(red + 64);              // [2][32] pivot key per warp
+    double *q2_s = red + 64;                                      // [N] (EXT)
+    int *cand_v = reinterpret_cast<int *>(q2_s + (EXT ? N : 0));  // [2][32] pivot key per warp
     int *cand_i = reinterpret_cast<int *>(cand_v + 64);           // [2][32] row per warp
     int *occ_s = cand_i + 64;                                     // [Ne]
     int *perm = occ_s + Ne;                                       // [Ne] pivot k -> row
@@ -824,6 +777,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         lam_s[i] = s.lam[t * N + i];
         q0_s[i] = s.q0[t * N + i];
+        if constexpr (EXT) q2_s[i] = s.q2[t * N + i];
         isocc[i] = 0;
     }
     __syncthreads();
@@ -961,8 +915,21 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
         __syncthreads();
     }
     if (singular && threadIdx.x == 0) atomicOr(&s.status[t], ST_SINGULAR);
-    const double v = s.p[t] / mass;
-    const double geo_h = s.geo[t * 4], geo_dh = s.geo[t * 4 + 1], geo_k = s.geo[t * 4 + 2];
+    // the six-coordinate coupling carries its velocity: v = 1 there
+    const double v = EXT ? 1.0 : s.p[t] / mass;
+    const double *gv = EXT ? s.geo2 + t * 8 : s.geo + t * 4;
+    const double geo_h = gv[0], geo_dh = gv[1], geo_k = gv[2];
+    // NAC d_{m, sa} (times v for EXT) of a candidate (target m, source sa)
+    auto hop_nac = [&](int m, int sa) -> double {
+        if constexpr (EXT) {
+            const double lm = lam_s[m], ls = lam_s[sa], lsum = lm + ls;
+            const double T = q0_s[m] * q0_s[sa] * (gv[2] + gv[4] * (lsum - 2.0 * gv[0])) +
+                             q2_s[m] * q2_s[sa] * (gv[3] + gv[5] * (lsum - 2.0 * gv[1]));
+            return T * pole_recip<double>(ls - lm);
+        } else {
+            return nac(lam_s[m], q0_s[m], lam_s[sa], q0_s[sa], geo_h, geo_dh, geo_k);
+        }
+    };
     const U4 rn = draw(seed, (uint32_t)t, kStreamHop, (uint64_t)s.nstep[t]);
     const double zeta = u53(rn.v[0], rn.v[1]);
     __syncthreads();
@@ -981,7 +948,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
         for (int idx = threadIdx.x; idx < Ne * nu; idx += blockDim.x) {
             const int a = idx / nu, m = unocc[idx - a * nu];
             const int sa = occ_s[a];
-            part += fabs(nac(lam_s[m], q0_s[m], lam_s[sa], q0_s[sa], geo_h, geo_dh, geo_k));
+            part += fabs(hop_nac(m, sa));
         }
         const double sd = block_sum(part, red);
         const double bound = 2.0 * dt * fabs(v) * sd / det_abs;
@@ -1044,7 +1011,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
                     for (int i = sub; i < Ne; i += 4) {
                         const int a = perm[i];
                         const int sa = occ_s[a];
-                        const double d = nac(lam_s[m], q0_s[m], lam_s[sa], q0_s[sa], geo_h, geo_dh, geo_k);
+                        const double d = hop_nac(m, sa);
                         const double gam = -2.0 * dt * v * (double)y[i].x * d;
                         G[(int64_t)a * N + m] = gam > 0.0 ? gam : 0.0;
                     }
@@ -1089,7 +1056,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
                     for (int i = sub; i < Ne; i += 4) {
                         const int a = perm[i];
                         const int sa = occ_s[a];
-                        const double d = nac(lam_s[m], q0_s[m], lam_s[sa], q0_s[sa], geo_h, geo_dh, geo_k);
+                        const double d = hop_nac(m, sa);
                         const double gam = -2.0 * dt * v * Y[(int64_t)i * N + m].x * d;
                         G[(int64_t)a * N + m] = gam > 0.0 ? gam : 0.0;
                     }
@@ -1137,6 +1104,10 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
         __syncthreads();
     }
 
+    if constexpr (EXT) {  // rescale and bookkeeping in the six-coordinate acceptance kernel
+        if (threadIdx.x == 0) s.hop_pair[t] = s_hop_a >= 0 ? s_hop_a * N + s_hop_m : -1;
+        return;
+    }
     // ---- hop, rescale, force, counters (thread 0)
     if (threadIdx.x == 0) {
         double p = s.p[t];
@@ -1476,14 +1447,17 @@ void configure_hop_smem()
     allow_max_smem(k_hop<double2, 512, 1>);
     allow_max_smem(k_hop<float2, 256, 4>);
     allow_max_smem(k_hop<double2, 256, 3>);
+    allow_max_smem(k_hop<double2, 512, 1, true>);
+    allow_max_smem(k_hop<double2, 256, 3, true>);
     allow_max_smem(k_cheb_f32t<4>);
 }
 
 cudaError_t launch_hop(const DevState &s, double dt, double mass, uint64_t seed, int skip_bound,
-                       double *g_out, cudaStream_t st, bool mixed)
+                       double *g_out, cudaStream_t st, bool mixed, bool ext)
 {
     if (s.n == 0) return cudaSuccess;
-    const size_t smem = hop_smem_bytes(s.N, s.Ne, mixed);
+    if (ext && mixed) return cudaErrorInvalidValue;
+    const size_t smem = hop_smem_bytes(s.N, s.Ne, mixed, ext);
     // 256-thread CTAs (three per SM) when two or more fit in shared memory,
     // else one CTA of 512
     int threads = (2 * smem + 2048 <= 227 * 1024) ? 256 : 512;
@@ -1497,7 +1471,10 @@ cudaError_t launch_hop(const DevState &s, double dt, double mass, uint64_t seed,
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kern<<<(unsigned)s.n, threads, smem, st>>>(s, dt, mass, seed, skip_bound, g_out);
     };
-    if (mixed) {
+    if (ext) {
+        if (threads == 256) go(k_hop<double2, 256, 3, true>);
+        else go(k_hop<double2, 512, 1, true>);
+    } else if (mixed) {
         if (threads == 256) go(k_hop<float2, 256, 4>);
         else go(k_hop<float2, 512, 1>);
     } else {

@@ -1,0 +1,770 @@
+// iesh_two.cu -- IESH dynamics of a two-orbital adsorbate over six nuclear
+// coordinates (FP64): kernels and the iesh2_* C-ABI.
+//
+// Electrons: adsorbate orbitals a = 0, 1 with levels h_a(x), each coupled to
+// bath state k by c_a(x) sqrt(w_k), c_a = vbar_a f_a(x) (the occupied-energy
+// model).  Both border vectors are proportional to sqrt(w_k), so with
+// c^2 = c_0^2 + c_1^2 the combination |+> = (c_0|0> + c_1|1>)/c couples to
+// the bath and |-> = (-c_1|0> + c_0|1>)/c couples only to |+> (through
+// t = c_0 c_1 (h_1 - h_0) / c^2).  Eliminating |-> and the bath leaves one
+// arrowhead secular equation with the M bath poles and one more pole at
+// h_- = <-|H|-> of weight t^2 (M + 2 roots, one per orbital):
+//   lam - h_+ - sum_k c^2 w_k / (lam - eps_k) - t^2 / (lam - h_-) = 0,
+// root j has q_+ = 1/sqrt(g'(lam)) (> 0: the gauge), q_- = t q_+ / (lam - h_-)
+// and adsorbate components Q_0j = (c_0 q_+ - c_1 q_-)/c, Q_1j = (c_1 q_+ + c_0 q_-)/c.
+// With t = 0, |-> is itself an eigenvector (lam = h_-); with c = 0 the
+// Hamiltonian is diagonal.
+//
+// Derivative couplings: on an eigenvector c_a B_k = (lam_k - h_a) Q_ak
+// (B_k = sum_k' sqrt(w_k') X_k'k), so for every direction y the matrix
+// T^y = Q^T (dH/dy) Q is the one-orbital closed form summed over the two
+// adsorbate orbitals,
+//   T^y_jk = sum_a Q_aj Q_ak [dh_a/dy + (dlog f_a/dy) (lam_j + lam_k - 2 h_a)],
+// d^y_jk = T^y_jk / (lam_k - lam_j), and the Hellmann-Feynman force is
+// F_y = -dU0/dy - sum_{j occupied} T^y_jj.
+//
+// One step (Sec. II B, II C in six dimensions):
+//   k2_eigen      kick + drift, eigenpairs, forces, second kick, the
+//                 velocity-projected scalars for the hop kernel;
+//   k2_build_w    W = dt/2 (D0 + D1), D_e = v_e . d at the two ends of the step,
+//                 its Gershgorin interval and the Chebyshev coefficients;
+//   k_cheb        (shared with the one-coordinate model) the exponential;
+//   k_hop<EXT>    determinant ratios, g_{a->m} with v . d, the selection;
+//   k2_accept     the six-dimensional momentum change along d_{m, s_a},
+//                 occupations, force on the new surface, counters.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/iesh.h"
+#include "iesh_cheb.cuh"
+#include "iesh_common.cuh"
+#include "iesh_host.h"
+#include "iesh_kernels.h"
+#include "iesh_secular.cuh"
+
+using namespace iesh;
+
+namespace {
+
+// Model constants passed by value to the kernels.
+struct Model2Dev {
+    double th[16];  // eps_0, eps_1, g_{0,0..5}, g_{1,0..5}, sigma_0, sigma_1
+    double vbar[2], R[6], x0[6];
+    double mass, omega;
+};
+
+// Adsorbate quantities at one geometry: levels h_a, coupling amplitudes c_a
+// and kap[y] = dlog f_a/dy for the three coordinates y of orbital a.
+struct Ads2 {
+    double h[2], c[2], kap[6];
+};
+
+__device__ __forceinline__ Ads2 ads2_eval(const Model2Dev &md, const double *x)
+{
+    Ads2 o;
+    for (int a = 0; a < 2; ++a) {
+        double h = md.th[a];
+        for (int y = 0; y < 6; ++y) h += md.th[2 + 6 * a + y] * x[y];
+        const double sg = md.th[14 + a];
+        double r2 = 0.0;
+        for (int q = 0; q < 3; ++q) {
+            const double d = x[3 * a + q] - md.R[3 * a + q];
+            r2 += d * d;
+            o.kap[3 * a + q] = -d / (sg * sg);
+        }
+        o.h[a] = h;
+        o.c[a] = md.vbar[a] * exp(-0.5 * r2 / (sg * sg));
+    }
+    return o;
+}
+
+// grad h_a . v and grad log f_a . v
+__device__ __forceinline__ void ads2_project(const Model2Dev &md, const Ads2 &ad, const double *v,
+                                             double hv[2], double kv[2])
+{
+    for (int a = 0; a < 2; ++a) {
+        double s = 0.0;
+        for (int y = 0; y < 6; ++y) s += md.th[2 + 6 * a + y] * v[y];
+        hv[a] = s;
+        double k = 0.0;
+        for (int q = 0; q < 3; ++q) k += ad.kap[3 * a + q] * v[3 * a + q];
+        kv[a] = k;
+    }
+}
+
+// Velocity-projected scalars of the hop kernel: h_0, h_1, grad h_a . v,
+// grad log f_a . v at momentum p.
+__device__ __forceinline__ void write_geo2(const DevState &s, int64_t t, const Model2Dev &md,
+                                           const Ads2 &ad, const double *p)
+{
+    double v[6], hv[2], kv[2];
+    for (int y = 0; y < 6; ++y) v[y] = p[y] / md.mass;
+    ads2_project(md, ad, v, hv, kv);
+    double *g = s.geo2 + t * 8;
+    g[0] = ad.h[0];
+    g[1] = ad.h[1];
+    g[2] = hv[0];
+    g[3] = hv[1];
+    g[4] = kv[0];
+    g[5] = kv[1];
+}
+
+// Force component y on the occupied surface from the occupied sums
+// S_a = sum Q_aj^2 and U_a = sum Q_aj^2 (lam_j - h_a).
+__device__ __forceinline__ double force2(const Model2Dev &md, const Ads2 &ad, const double *x, int y,
+                                         const double S[2], const double U[2])
+{
+    const int a = y / 3;
+    double f = -md.mass * md.omega * md.omega * (x[y] - md.x0[y]);
+    f -= S[0] * md.th[2 + y] + S[1] * md.th[8 + y];
+    f -= 2.0 * U[a] * ad.kap[y];
+    return f;
+}
+
+// Occupied sums over the orbital list occ (block-wide; all threads call).
+__device__ __forceinline__ void occ_sums(const double *lam, const double *Q0, const double *Q1,
+                                         const int16_t *occ, int Ne, const Ads2 &ad, double *red,
+                                         double S[2], double U[2])
+{
+    double s0 = 0.0, s1 = 0.0, u0 = 0.0, u1 = 0.0;
+    for (int q = threadIdx.x; q < Ne; q += blockDim.x) {
+        const int j = occ[q];
+        const double a2 = Q0[j] * Q0[j], b2 = Q1[j] * Q1[j];
+        s0 += a2;
+        s1 += b2;
+        u0 += a2 * (lam[j] - ad.h[0]);
+        u1 += b2 * (lam[j] - ad.h[1]);
+    }
+    S[0] = block_sum(s0, red);
+    S[1] = block_sum(s1, red);
+    U[0] = block_sum(u0, red);
+    U[1] = block_sum(u1, red);
+}
+
+// mode 0: eigenpairs and forces at x (state set-up).  mode 1: a step's
+// kick + drift, eigenpairs at the new x, forces and the second kick.
+// One CTA per trajectory, one thread per root (N <= 256 threads).
+__global__ void __launch_bounds__(256) k2_eigen(DevState s, Model2Dev md, double dt, int mode)
+{
+    extern __shared__ double e2_sh[];
+    const int64_t t = traj_of(s, blockIdx.x);
+    if (t < 0 || (s.status[t] & ST_DONE)) return;
+    const int N = s.N, M = s.M, Ne = s.Ne;
+    double *pole = e2_sh;          // [M + 1] sorted poles
+    double *wt = pole + (M + 1);   // [M + 1] their weights
+    double *lam_s = wt + (M + 1);  // [N]
+    double *Q0_s = lam_s + N;      // [N]
+    double *Q1_s = Q0_s + N;       // [N]
+    double *red = Q1_s + N;        // [32]
+    __shared__ double xs[6], ps[6], s_Z2;
+    __shared__ int s_pos;
+    const int tid = threadIdx.x;
+    if (tid < 6) {
+        double x = s.x[t * 6 + tid], p = s.p[t * 6 + tid];
+        if (mode == 1) {
+            s.x_prev[t * 6 + tid] = x;
+            p += 0.5 * dt * s.F[t * 6 + tid];
+            x += dt * p / md.mass;
+        }
+        xs[tid] = x;
+        ps[tid] = p;
+    }
+    if (mode == 1)
+        for (int i = tid; i < N; i += blockDim.x) {
+            s.lam_prev[t * N + i] = s.lam[t * N + i];
+            s.q0_prev[t * N + i] = s.q0[t * N + i];
+            s.q2_prev[t * N + i] = s.q2[t * N + i];
+        }
+    __syncthreads();
+    const Ads2 ad = ads2_eval(md, xs);
+    const double c0 = ad.c[0], c1 = ad.c[1], csq = c0 * c0 + c1 * c1;
+    uint32_t st = 0;
+    if (!(csq > 0.0)) {
+        // no coupling: diagonal Hamiltonian, sorted (ties: adsorbate first)
+        const double h0 = ad.h[0], h1 = ad.h[1];
+        if (tid < N) {
+            double lam, q0 = 0.0, q1 = 0.0;
+            int idx;
+            if (tid < M) {
+                lam = s.eps[tid];
+                idx = tid + (h0 <= lam) + (h1 <= lam);
+            } else {
+                const double h = tid == M ? h0 : h1;
+                int below = 0;
+                for (int k = 0; k < M; ++k) below += (s.eps[k] < h);
+                lam = h;
+                if (tid == M) {
+                    idx = below + (h1 < h0);
+                    q0 = 1.0;
+                } else {
+                    idx = below + (h0 <= h1);
+                    q1 = 1.0;
+                }
+            }
+            lam_s[idx] = lam;
+            Q0_s[idx] = q0;
+            Q1_s[idx] = q1;
+        }
+    } else {
+        const double c = sqrt(csq);
+        const double hp = (c0 * c0 * ad.h[0] + c1 * c1 * ad.h[1]) / csq;
+        const double hm = (c1 * c1 * ad.h[0] + c0 * c0 * ad.h[1]) / csq;
+        const double tt = c0 * c1 * (ad.h[1] - ad.h[0]) / csq;
+        const bool decoupled = !(tt * tt > 0.0);
+        if (tid == 0) {
+            int pos = 0;
+            for (int k = 0; k < M; ++k) pos += (s.eps[k] < hm);
+            s_pos = pos;
+        }
+        __syncthreads();
+        const int pos = s_pos;
+        const int P = decoupled ? M : M + 1;
+        for (int k = tid; k < M; k += blockDim.x) {
+            const int slot = (decoupled || k < pos) ? k : k + 1;
+            pole[slot] = s.eps[k];
+            wt[slot] = csq * (s.z0[k] * s.z0[k]);
+        }
+        if (!decoupled && tid == 0) {
+            pole[pos] = hm;
+            wt[pos] = tt * tt;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double z2 = 0.0;
+            for (int k = 0; k < P; ++k) z2 += wt[k];
+            s_Z2 = z2;
+        }
+        __syncthreads();
+        const int r = tid;
+        double lam = 0.0, qp = 0.0, qm = 0.0;
+        if (r <= P) {
+            int o;
+            double tau;
+            const Poles<double> pp = {P, pole, wt, nullptr, nullptr, nullptr};
+            secular_root<double>(r, pp, hp, s_Z2, false, 0.0, lam, qp, st, &o, &tau);
+            if (!decoupled) {
+                // lam - h_-: the exact offset when the origin pole is h_- itself
+                const double lmh = (o == pos) ? tau : (pole[o] - hm) + tau;
+                qm = tt * qp / lmh;
+            }
+        }
+        if (!decoupled) {
+            if (r < N) {
+                lam_s[r] = lam;
+                Q0_s[r] = (c0 * qp - c1 * qm) / c;
+                Q1_s[r] = (c1 * qp + c0 * qm) / c;
+            }
+        } else {
+            // M + 1 roots of the |+> arrowhead plus the decoupled |-> at h_-
+            if (r <= M) lam_s[r] = lam;  // staging for the count below
+            __syncthreads();
+            int below = 0;
+            if (r == M + 1)
+                for (int k = 0; k <= M; ++k) below += (lam_s[k] < hm);
+            __syncthreads();
+            if (r <= M) {
+                const int idx = r + (lam >= hm);
+                lam_s[idx] = lam;
+                Q0_s[idx] = c0 * qp / c;
+                Q1_s[idx] = c1 * qp / c;
+            } else if (r == M + 1) {
+                lam_s[below] = hm;
+                // (-c_1, c_0) / c; a unit adsorbate vector (+) when one coupling vanishes
+                Q0_s[below] = c0 == 0.0 ? 1.0 : (c1 == 0.0 ? 0.0 : -c1 / c);
+                Q1_s[below] = c0 == 0.0 ? 0.0 : (c1 == 0.0 ? 1.0 : c0 / c);
+            }
+        }
+    }
+    if (st) atomicOr(&s.status[t], st);
+    __syncthreads();
+    for (int i = tid; i < N; i += blockDim.x) {
+        s.lam[t * N + i] = lam_s[i];
+        s.q0[t * N + i] = Q0_s[i];
+        s.q2[t * N + i] = Q1_s[i];
+    }
+    double S[2], U[2];
+    occ_sums(lam_s, Q0_s, Q1_s, s.occ + t * Ne, Ne, ad, red, S, U);
+    if (tid < 6) {
+        const double F = force2(md, ad, xs, tid, S, U);
+        double p = ps[tid];
+        if (mode == 1) p += 0.5 * dt * F;
+        ps[tid] = p;
+        s.x[t * 6 + tid] = xs[tid];
+        s.p[t * 6 + tid] = p;
+        s.F[t * 6 + tid] = F;
+        if (mode == 0) s.vprev[t * 6 + tid] = p / md.mass;
+    }
+    __syncthreads();
+    if (tid == 0) write_geo2(s, t, md, ad, ps);
+}
+
+// W[j N + k] = dt/2 (D0_jk + D1_jk), D_e = T^{v_e}_jk / (lam_k - lam_j) at
+// the start (x_prev, v_prev) and the end (x, p / mass) of the step; the
+// Gershgorin interval of dt diag((lam0 + lam1)/2) - i W; the Chebyshev set-up.
+__global__ void __launch_bounds__(256) k2_build_w(DevState s, Model2Dev md, double dt, double tol)
+{
+    extern __shared__ double w2_sh[];
+    const int64_t t = traj_of(s, blockIdx.x);
+    if (t < 0 || (s.status[t] & ST_DONE)) return;
+    const int N = s.N;
+    double *l0 = w2_sh, *a0 = l0 + N, *b0 = a0 + N, *l1 = b0 + N, *a1 = l1 + N, *b1 = a1 + N;
+    double *red = b1 + N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        l0[i] = s.lam_prev[t * N + i];
+        a0[i] = s.q0_prev[t * N + i];
+        b0[i] = s.q2_prev[t * N + i];
+        l1[i] = s.lam[t * N + i];
+        a1[i] = s.q0[t * N + i];
+        b1[i] = s.q2[t * N + i];
+    }
+    double x0[6], v0[6], x1[6], v1[6];
+    for (int y = 0; y < 6; ++y) {
+        x0[y] = s.x_prev[t * 6 + y];
+        v0[y] = s.vprev[t * 6 + y];
+        x1[y] = s.x[t * 6 + y];
+        v1[y] = s.p[t * 6 + y] / md.mass;
+    }
+    const Ads2 e0 = ads2_eval(md, x0), e1 = ads2_eval(md, x1);
+    double hv0[2], kv0[2], hv1[2], kv1[2];
+    ads2_project(md, e0, v0, hv0, kv0);
+    ads2_project(md, e1, v1, hv1, kv1);
+    __syncthreads();
+    const double hdt = 0.5 * dt;
+    double *W = s.scratch + t * s.scratch_stride;
+    double lo = __longlong_as_double(0x7ff0000000000000ll), hi = -lo;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const double lk0 = l0[k], ak0 = a0[k], bk0 = b0[k], lk1 = l1[k], ak1 = a1[k], bk1 = b1[k];
+        double Rk = 0.0;
+        for (int j = 0; j < N; ++j) {
+            double w = 0.0;
+            if (j != k) {
+                const double s0 = l0[j] + lk0, s1 = l1[j] + lk1;
+                const double T0 = a0[j] * ak0 * (hv0[0] + kv0[0] * (s0 - 2.0 * e0.h[0])) +
+                                  b0[j] * bk0 * (hv0[1] + kv0[1] * (s0 - 2.0 * e0.h[1]));
+                const double T1 = a1[j] * ak1 * (hv1[0] + kv1[0] * (s1 - 2.0 * e1.h[0])) +
+                                  b1[j] * bk1 * (hv1[1] + kv1[1] * (s1 - 2.0 * e1.h[1]));
+                w = hdt * (T0 * pole_recip<double>(lk0 - l0[j]) + T1 * pole_recip<double>(lk1 - l1[j]));
+            }
+            W[(int64_t)j * N + k] = w;
+            Rk += fabs(w);
+        }
+        const double Lk = hdt * (lk0 + lk1);
+        lo = fmin(lo, Lk - Rk);
+        hi = fmax(hi, Lk + Rk);
+    }
+    lo = block_min(lo, red);
+    hi = block_max(hi, red);
+    if (threadIdx.x == 0) cheb_setup(s, t, lo, hi, tol);
+}
+
+// Hop acceptance: p' = p + alpha d with d = d_{m, s_a} (six components),
+// alpha the energy-conserving root of smaller magnitude; occupations, the
+// force on the new surface, counters, v_prev and the non-finite check.
+__global__ void __launch_bounds__(64) k2_accept(DevState s, Model2Dev md)
+{
+    const int64_t t = traj_of(s, blockIdx.x);
+    if (t < 0 || (s.status[t] & ST_DONE)) return;
+    const int N = s.N, Ne = s.Ne;
+    __shared__ double xs[6], ps[6], red[32];
+    __shared__ int s_hopped;
+    const int tid = threadIdx.x;
+    if (tid < 6) {
+        xs[tid] = s.x[t * 6 + tid];
+        ps[tid] = s.p[t * 6 + tid];
+    }
+    __syncthreads();
+    const Ads2 ad = ads2_eval(md, xs);
+    if (tid == 0) {
+        s_hopped = 0;
+        const int pair = s.hop_pair[t];
+        if (pair >= 0) {
+            const int a = pair / N, m = pair - a * N;
+            int16_t *occ = s.occ + t * Ne;
+            const int sa = occ[a];
+            const double *lam = s.lam + t * N, *Q0 = s.q0 + t * N, *Q1 = s.q2 + t * N;
+            const double lm = lam[m], ls = lam[sa], lsum = lm + ls;
+            const double A0 = Q0[m] * Q0[sa], A1 = Q1[m] * Q1[sa];
+            double d[6], pd = 0.0, dd = 0.0;
+            for (int y = 0; y < 6; ++y) {
+                const double kp0 = y < 3 ? ad.kap[y] : 0.0, kp1 = y < 3 ? 0.0 : ad.kap[y];
+                const double T = A0 * (md.th[2 + y] + kp0 * (lsum - 2.0 * ad.h[0])) +
+                                 A1 * (md.th[8 + y] + kp1 * (lsum - 2.0 * ad.h[1]));
+                d[y] = T / (ls - lm);
+                pd += ps[y] * d[y];
+                dd += d[y] * d[y];
+            }
+            const double dE = lm - ls;
+            const double disc = pd * pd - 2.0 * md.mass * dd * dE;
+            if (dd > 0.0 && disc >= 0.0) {
+                const double alpha = (-pd + (pd >= 0.0 ? 1.0 : -1.0) * sqrt(disc)) / dd;
+                for (int y = 0; y < 6; ++y) ps[y] += alpha * d[y];
+                // replace s_a by m and keep the list ascending
+                int b = a;
+                occ[b] = (int16_t)m;
+                while (b > 0 && occ[b - 1] > occ[b]) {
+                    const int16_t tmp = occ[b - 1];
+                    occ[b - 1] = occ[b];
+                    occ[b] = tmp;
+                    --b;
+                }
+                while (b < Ne - 1 && occ[b + 1] < occ[b]) {
+                    const int16_t tmp = occ[b + 1];
+                    occ[b + 1] = occ[b];
+                    occ[b] = tmp;
+                    ++b;
+                }
+                s.hops[t] += 1;
+                s_hopped = 1;
+            } else {
+                s.frus[t] += 1;
+            }
+        }
+    }
+    __syncthreads();
+    if (s_hopped) {  // uniform over the CTA
+        double S[2], U[2];
+        occ_sums(s.lam + t * N, s.q0 + t * N, s.q2 + t * N, s.occ + t * Ne, Ne, ad, red, S, U);
+        if (tid < 6) s.F[t * 6 + tid] = force2(md, ad, xs, tid, S, U);
+    }
+    if (tid < 6) {
+        s.p[t * 6 + tid] = ps[tid];
+        s.vprev[t * 6 + tid] = ps[tid] / md.mass;
+    }
+    if (tid == 0) {
+        if (s_hopped) write_geo2(s, t, md, ad, ps);  // projections at the new momentum
+        s.nstep[t] += 1;
+        bool bad = false;
+        for (int y = 0; y < 6; ++y) bad |= !isfinite(xs[y]) || !isfinite(ps[y]);
+        if (bad) atomicOr(&s.status[t], ST_NAN);
+    }
+}
+
+constexpr int kEigen2MaxThreads = 256;
+
+size_t eigen2_smem(int N, int M) { return (size_t)(2 * (M + 1) + 3 * N + 32) * sizeof(double); }
+
+}  // namespace
+
+struct iesh2_ctx {
+    iesh2_model model;
+    int64_t max_traj = 0;
+    cudaStream_t stream = nullptr;
+    int N = 0, M = 0, Ne = 0;
+    int skip_bound = 0;
+    Model2Dev md;
+    DevState ds;
+    std::vector<void *> allocs;
+    bool have_state = false;
+    std::string err;
+    KernelTimer timer;
+};
+
+namespace {
+
+iesh_status fail2(iesh2_ctx *c, iesh_status s, const char *fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define CU2(call)                                                                           \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail2(ctx, IESH_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),  \
+                         __FILE__, __LINE__);                                               \
+    } while (0)
+
+template <class T>
+iesh_status dalloc2(iesh2_ctx *ctx, T **p, size_t count)
+{
+    void *q = nullptr;
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess)
+        return fail2(ctx, IESH_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    ctx->allocs.push_back(q);
+    *p = (T *)q;
+    CU2(cudaMemsetAsync(q, 0, bytes, ctx->stream));
+    return IESH_OK;
+}
+
+iesh_status copy_out2(iesh2_ctx *ctx, void *dst, const void *src, size_t bytes, bool &sync)
+{
+    if (!bytes || !dst) return IESH_OK;
+    CU2(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, ctx->stream));
+    if (is_host_ptr(dst)) sync = true;
+    return IESH_OK;
+}
+
+cudaError_t launch_eigen2(iesh2_ctx *ctx, double dt, int mode)
+{
+    const DevState &d = ctx->ds;
+    if (d.n == 0) return cudaSuccess;
+    const int threads = std::min(kEigen2MaxThreads, (d.N + 31) & ~31);
+    k2_eigen<<<(unsigned)d.n, threads, eigen2_smem(d.N, d.M), ctx->stream>>>(d, ctx->md, dt, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_w2(iesh2_ctx *ctx, double dt, double tol)
+{
+    const DevState &d = ctx->ds;
+    if (d.n == 0) return cudaSuccess;
+    const int threads = std::min(256, (d.N + 31) & ~31);
+    k2_build_w<<<(unsigned)d.n, threads, (size_t)(6 * d.N + 32) * sizeof(double), ctx->stream>>>(
+        d, ctx->md, dt, tol);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accept2(iesh2_ctx *ctx)
+{
+    const DevState &d = ctx->ds;
+    if (d.n == 0) return cudaSuccess;
+    k2_accept<<<(unsigned)d.n, 64, 0, ctx->stream>>>(d, ctx->md);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *iesh2_last_error(const iesh2_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+iesh_status iesh2_destroy(iesh2_ctx *ctx)
+{
+    if (!ctx) return IESH_OK;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    ctx->timer.release();
+    for (void *p : ctx->allocs) cudaFree(p);
+    delete ctx;
+    return IESH_OK;
+}
+
+iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int64_t max_traj, int skip_bound,
+                         void *cuda_stream)
+{
+    if (!out) return IESH_EINVAL;
+    *out = nullptr;
+    if (!model || max_traj < 1) return IESH_EINVAL;
+    iesh2_ctx *ctx = new iesh2_ctx();
+    *out = ctx;
+    ctx->model = *model;
+    ctx->max_traj = max_traj;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->skip_bound = skip_bound;
+    const int M = model->n_bath, Ne = model->n_elec, N = M + 2;
+    if (M < 2 || N > kMaxOrbitals) return fail2(ctx, IESH_EINVAL, "n_bath %d outside 2..%d", M, kMaxOrbitals - 2);
+    if (Ne < 1 || Ne > N - 1) return fail2(ctx, IESH_EINVAL, "n_elec %d outside 1..N-1", Ne);
+    if (Ne > kMaxHopElectrons) return fail2(ctx, IESH_EINVAL, "n_elec %d above %d", Ne, kMaxHopElectrons);
+    if (!(model->mass > 0.0)) return fail2(ctx, IESH_EINVAL, "mass must be positive");
+    if (!(model->band_hi > model->band_lo)) return fail2(ctx, IESH_EINVAL, "empty band");
+    if (!(model->theta[14] != 0.0 && model->theta[15] != 0.0))
+        return fail2(ctx, IESH_EINVAL, "coupling widths theta[14], theta[15] must be nonzero");
+    ctx->N = N;
+    ctx->M = M;
+    ctx->Ne = Ne;
+    Model2Dev &k = ctx->md;
+    for (int i = 0; i < 16; ++i) k.th[i] = model->theta[i];
+    for (int a = 0; a < 2; ++a) k.vbar[a] = model->vbar[a];
+    for (int i = 0; i < 6; ++i) {
+        k.R[i] = model->R[i];
+        k.x0[i] = model->x0[i];
+    }
+    k.mass = model->mass;
+    k.omega = model->omega;
+    // split Gauss-Legendre bath at mu, M/2 nodes below (Appendix A)
+    std::vector<double> eps, w;
+    lead_bath(IESH_DISC_GL_SPLIT, M, model->band_lo, model->band_hi, model->mu, M / 2, eps, w);
+    for (int i = 1; i < M; ++i)
+        if (!(eps[i] > eps[i - 1])) return fail2(ctx, IESH_EINVAL, "bath energies must be distinct");
+    std::vector<double> sq(M);
+    for (int i = 0; i < M; ++i) sq[i] = std::sqrt(w[i]);
+
+    DevState &d = ctx->ds;
+    memset(&d, 0, sizeof d);
+    d.N = N;
+    d.M = M;
+    d.Ne = Ne;
+    const size_t T = (size_t)max_traj;
+    d.scratch_stride = std::max<int64_t>((int64_t)N * N, 3LL * Ne * N + Ne);
+    d.scratch_stride = (d.scratch_stride + 31) & ~31LL;
+    iesh_status st;
+    double *eps_d = nullptr, *sq_d = nullptr, *Cd = nullptr;
+#define A2(ptr, cnt) if ((st = dalloc2(ctx, &(ptr), (cnt))) != IESH_OK) return st;
+    A2(d.x, T * 6) A2(d.p, T * 6) A2(d.F, T * 6) A2(d.vprev, T * 6) A2(d.x_prev, T * 6)
+    A2(d.occ, T * Ne)
+    A2(Cd, T * Ne * N * 2)
+    A2(d.lam, T * N) A2(d.q0, T * N) A2(d.q2, T * N)
+    A2(d.lam_prev, T * N) A2(d.q0_prev, T * N) A2(d.q2_prev, T * N)
+    A2(d.geo2, T * 8)
+    A2(d.hop_pair, T)
+    A2(d.status, T) A2(d.nstep, T) A2(d.hops, T) A2(d.frus, T)
+    A2(d.scratch, T * (size_t)d.scratch_stride)
+    A2(d.cheb, T * kChebStride)
+    A2(eps_d, (size_t)M) A2(sq_d, (size_t)M)
+#undef A2
+    d.C = Cd;
+    d.eps = eps_d;
+    d.z0 = sq_d;
+    configure_hop_smem();
+    CU2(cudaMemcpyAsync(eps_d, eps.data(), M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CU2(cudaMemcpyAsync(sq_d, sq.data(), M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CU2(cudaStreamSynchronize(ctx->stream));
+    return IESH_OK;
+}
+
+iesh_status iesh2_set_state(iesh2_ctx *ctx, int64_t n_traj, const double *x, const double *p,
+                            const int16_t *occ, const void *C)
+{
+    if (!ctx) return IESH_EINVAL;
+    if (n_traj < 0 || n_traj > ctx->max_traj)
+        return fail2(ctx, IESH_EINVAL, "n_traj %lld outside 0..%lld", (long long)n_traj,
+                     (long long)ctx->max_traj);
+    if (!x || !p || !occ || !C) return fail2(ctx, IESH_EINVAL, "set_state needs x, p, occ and C");
+    DevState &d = ctx->ds;
+    d.n = n_traj;
+    const size_t n = (size_t)n_traj;
+    if (n) {
+        CU2(cudaMemsetAsync(d.status, 0, n * sizeof(uint32_t), ctx->stream));
+        CU2(cudaMemsetAsync(d.nstep, 0, n * sizeof(int64_t), ctx->stream));
+        CU2(cudaMemsetAsync(d.hops, 0, n * sizeof(int32_t), ctx->stream));
+        CU2(cudaMemsetAsync(d.frus, 0, n * sizeof(int32_t), ctx->stream));
+        CU2(cudaMemcpyAsync(d.x, x, n * 6 * sizeof(double), cudaMemcpyDefault, ctx->stream));
+        CU2(cudaMemcpyAsync(d.p, p, n * 6 * sizeof(double), cudaMemcpyDefault, ctx->stream));
+        CU2(cudaMemcpyAsync(d.occ, occ, n * ctx->Ne * sizeof(int16_t), cudaMemcpyDefault, ctx->stream));
+        CU2(cudaMemcpyAsync(d.C, C, n * ctx->Ne * ctx->N * 16, cudaMemcpyDefault, ctx->stream));
+    }
+    CU2(launch_eigen2(ctx, 0.0, 0));
+    // host sources may be pageable: the copies above must finish before return
+    CU2(cudaStreamSynchronize(ctx->stream));
+    ctx->have_state = true;
+    return IESH_OK;
+}
+
+iesh_status iesh2_get_state(iesh2_ctx *ctx, double *x, double *p, int16_t *occ, void *C, uint32_t *status)
+{
+    if (!ctx) return IESH_EINVAL;
+    const DevState &d = ctx->ds;
+    const size_t n = (size_t)d.n;
+    bool sync = false;
+    iesh_status st;
+    if ((st = copy_out2(ctx, x, d.x, n * 6 * sizeof(double), sync)) != IESH_OK) return st;
+    if ((st = copy_out2(ctx, p, d.p, n * 6 * sizeof(double), sync)) != IESH_OK) return st;
+    if ((st = copy_out2(ctx, occ, d.occ, n * ctx->Ne * sizeof(int16_t), sync)) != IESH_OK) return st;
+    if ((st = copy_out2(ctx, C, d.C, n * ctx->Ne * ctx->N * 16, sync)) != IESH_OK) return st;
+    if ((st = copy_out2(ctx, status, d.status, n * sizeof(uint32_t), sync)) != IESH_OK) return st;
+    if (sync) CU2(cudaStreamSynchronize(ctx->stream));
+    return IESH_OK;
+}
+
+iesh_status iesh2_get_eigen(iesh2_ctx *ctx, double *lam, double *Q, double *F)
+{
+    if (!ctx) return IESH_EINVAL;
+    const DevState &d = ctx->ds;
+    const size_t n = (size_t)d.n, N = (size_t)ctx->N;
+    bool sync = false;
+    iesh_status st;
+    if ((st = copy_out2(ctx, lam, d.lam, n * N * sizeof(double), sync)) != IESH_OK) return st;
+    if (Q && n) {
+        // rows of [n][2][N]: orbital-0 components, then orbital-1 components
+        CU2(cudaMemcpy2DAsync(Q, 2 * N * sizeof(double), d.q0, N * sizeof(double), N * sizeof(double), n,
+                              cudaMemcpyDefault, ctx->stream));
+        CU2(cudaMemcpy2DAsync(Q + N, 2 * N * sizeof(double), d.q2, N * sizeof(double), N * sizeof(double), n,
+                              cudaMemcpyDefault, ctx->stream));
+        if (is_host_ptr(Q)) sync = true;
+    }
+    if ((st = copy_out2(ctx, F, d.F, n * 6 * sizeof(double), sync)) != IESH_OK) return st;
+    if (sync) CU2(cudaStreamSynchronize(ctx->stream));
+    return IESH_OK;
+}
+
+iesh_status iesh2_run(iesh2_ctx *ctx, double dt, int64_t n_steps, uint64_t seed)
+{
+    if (!ctx) return IESH_EINVAL;
+    if (!ctx->have_state) return fail2(ctx, IESH_ESTATE, "run before set_state");
+    if (!(dt > 0.0) || n_steps < 0) return fail2(ctx, IESH_EINVAL, "need dt > 0 and n_steps >= 0");
+    const DevState &d = ctx->ds;
+    const cudaStream_t st = ctx->stream;
+    for (int64_t k = 0; k < n_steps; ++k) {
+        CU2(ctx->timer.run(st, IESH_K_EIGEN, [&] { return launch_eigen2(ctx, dt, 1); }));
+        CU2(ctx->timer.run(st, IESH_K_COUPLING, [&] { return launch_build_w2(ctx, dt, 1e-15); }));
+        CU2(ctx->timer.run(st, IESH_K_PROPAGATE, [&] { return launch_cheb(d, dt, false, st); }));
+        CU2(ctx->timer.run(st, IESH_K_HOP, [&] {
+            return launch_hop(d, dt, ctx->md.mass, seed, ctx->skip_bound, nullptr, st, false, true);
+        }));
+        CU2(ctx->timer.run(st, IESH_K_OTHER, [&] { return launch_accept2(ctx); }));
+    }
+    return IESH_OK;
+}
+
+iesh_status iesh2_hop_probabilities(iesh2_ctx *ctx, double dt, double *g)
+{
+    if (!ctx || !g) return IESH_EINVAL;
+    if (!ctx->have_state) return fail2(ctx, IESH_ESTATE, "hop_probabilities before set_state");
+    const DevState &d = ctx->ds;
+    const size_t bytes = (size_t)d.n * ctx->Ne * ctx->N * sizeof(double);
+    if (!bytes) return IESH_OK;
+    double *dst = g, *tmp = nullptr;
+    const bool host = is_host_ptr(g);
+    if (host) {
+        CU2(cudaMallocAsync((void **)&tmp, bytes, ctx->stream));
+        dst = tmp;
+    }
+    CU2(launch_hop(d, dt, ctx->md.mass, 0, 0, dst, ctx->stream, false, true));
+    if (host) {
+        CU2(cudaMemcpyAsync(g, tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        CU2(cudaFreeAsync(tmp, ctx->stream));
+        CU2(cudaStreamSynchronize(ctx->stream));
+    }
+    return IESH_OK;
+}
+
+iesh_status iesh2_get_counters(iesh2_ctx *ctx, int64_t *nstep, int32_t *hops, int32_t *frustrated)
+{
+    if (!ctx) return IESH_EINVAL;
+    const DevState &d = ctx->ds;
+    const size_t n = (size_t)d.n;
+    bool sync = false;
+    iesh_status st;
+    if ((st = copy_out2(ctx, nstep, d.nstep, n * sizeof(int64_t), sync)) != IESH_OK) return st;
+    if ((st = copy_out2(ctx, hops, d.hops, n * sizeof(int32_t), sync)) != IESH_OK) return st;
+    if ((st = copy_out2(ctx, frustrated, d.frus, n * sizeof(int32_t), sync)) != IESH_OK) return st;
+    if (sync) CU2(cudaStreamSynchronize(ctx->stream));
+    return IESH_OK;
+}
+
+iesh_status iesh2_profile(iesh2_ctx *ctx, int enable)
+{
+    if (!ctx) return IESH_EINVAL;
+    CU2(cudaStreamSynchronize(ctx->stream));
+    ctx->timer.reset(enable != 0);
+    return IESH_OK;
+}
+
+iesh_status iesh2_profile_read(iesh2_ctx *ctx, double *ms, int64_t *launches)
+{
+    if (!ctx) return IESH_EINVAL;
+    CU2(cudaStreamSynchronize(ctx->stream));
+    CU2(ctx->timer.fold());
+    for (int i = 0; i < IESH_K_COUNT; ++i) {
+        if (ms) ms[i] = ctx->timer.ms[i];
+        if (launches) launches[i] = ctx->timer.n[i];
+    }
+    return IESH_OK;
+}
+
+}  // extern "C"

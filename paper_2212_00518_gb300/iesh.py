@@ -55,6 +55,14 @@ class _EoccModel(ctypes.Structure):
                 ("vbar", ctypes.c_double * 2), ("R", ctypes.c_double * 6)]
 
 
+class _Model2(ctypes.Structure):
+    _fields_ = [("n_bath", ctypes.c_int), ("n_elec", ctypes.c_int), ("band_lo", ctypes.c_double),
+                ("band_hi", ctypes.c_double), ("mu", ctypes.c_double), ("mass", ctypes.c_double),
+                ("omega", ctypes.c_double), ("x0", ctypes.c_double * 6),
+                ("theta", ctypes.c_double * 16), ("vbar", ctypes.c_double * 2),
+                ("R", ctypes.c_double * 6)]
+
+
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("skip_bound", ctypes.c_int),
                 ("record_every", ctypes.c_int), ("max_records", ctypes.c_int),
@@ -68,7 +76,10 @@ EXPORTS = ["iesh_create", "iesh_destroy", "iesh_bath", "iesh_init_state", "iesh_
            "iesh_profile_read", "iesh_get_live", "iesh_set_kernel_shape",
            "iesh_get_kernel_shape", "iesh_hop_probabilities_noalloc", "iesh_eocc_create",
            "iesh_eocc_destroy", "iesh_eocc_last_error", "iesh_eocc_forward",
-           "iesh_eocc_backward", "iesh_last_error", "iesh_status_string"]
+           "iesh_eocc_backward", "iesh_last_error", "iesh_status_string", "iesh2_create",
+           "iesh2_destroy", "iesh2_last_error", "iesh2_set_state", "iesh2_get_state", "iesh2_run",
+           "iesh2_get_eigen", "iesh2_hop_probabilities", "iesh2_get_counters", "iesh2_profile",
+           "iesh2_profile_read"]
 KERNEL_CLASSES = ["eigen", "coupling", "propagate", "hop", "other"]
 
 _lib = None
@@ -112,13 +123,27 @@ def load(path=LIB_PATH):
     L.iesh_eocc_forward.argtypes = [_vp, ctypes.c_int64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
     L.iesh_eocc_backward.argtypes = [_vp, ctypes.c_int64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp,
                                      _vp, _vp]
+    L.iesh2_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_Model2), ctypes.c_int64,
+                               ctypes.c_int, _vp]
+    L.iesh2_destroy.argtypes = [_vp]
+    L.iesh2_last_error.argtypes = [_vp]
+    L.iesh2_last_error.restype = ctypes.c_char_p
+    L.iesh2_set_state.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp]
+    L.iesh2_get_state.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+    L.iesh2_run.argtypes = [_vp, ctypes.c_double, ctypes.c_int64, ctypes.c_uint64]
+    L.iesh2_get_eigen.argtypes = [_vp, _vp, _vp, _vp]
+    L.iesh2_hop_probabilities.argtypes = [_vp, ctypes.c_double, _vp]
+    L.iesh2_get_counters.argtypes = [_vp, _vp, _vp, _vp]
+    L.iesh2_profile.argtypes = [_vp, ctypes.c_int]
+    L.iesh2_profile_read.argtypes = [_vp, _vp, _vp]
     L.iesh_last_error.argtypes = [_vp]
     L.iesh_last_error.restype = ctypes.c_char_p
     L.iesh_status_string.argtypes = [ctypes.c_int]
     L.iesh_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype if name in (
-            "iesh_last_error", "iesh_status_string", "iesh_eocc_last_error") else ctypes.c_int
+            "iesh_last_error", "iesh_status_string", "iesh_eocc_last_error",
+            "iesh2_last_error") else ctypes.c_int
     _lib = L
     return L
 

@@ -23,12 +23,12 @@ def lib():
 def _declared(header):
     src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(iesh_[a-z0-9_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(iesh2?_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_library_exports_every_declared_symbol(lib):
     names = _declared("iesh.h")
-    assert "iesh_run" in names and "iesh_create" in names
+    assert "iesh_run" in names and "iesh_create" in names and "iesh2_run" in names
     for n in names:
         assert hasattr(lib, n), n
 
@@ -60,3 +60,23 @@ def test_invalid_models_rejected_without_device(lib):
     assert lib.iesh_create(None, None, None, 1, None) == 1
     assert lib.iesh_run(None, 1.0, 1, 0) == 1
     assert lib.iesh_destroy(None) == 0
+
+
+def test_invalid_two_orbital_models_rejected_without_device(lib):
+    from paper_2212_00518_gb300 import two
+    for bad in (dict(M=1), dict(M=255), dict(Ne=0), dict(Ne=22), dict(mass=0.0),
+                dict(band=(0.5, -0.5))):
+        md = W.two_orbital(20)
+        md.update(bad)
+        h = ctypes.c_void_p()
+        rc = lib.iesh2_create(ctypes.byref(h), ctypes.byref(two.model_struct(md)), 16, 0, None)
+        assert rc == 1, (bad, rc)
+        assert lib.iesh2_last_error(h)
+        lib.iesh2_destroy(h)
+    md = W.two_orbital(20)
+    md["theta"] = md["theta"].copy()
+    md["theta"][14] = 0.0
+    h = ctypes.c_void_p()
+    assert lib.iesh2_create(ctypes.byref(h), ctypes.byref(two.model_struct(md)), 16, 0, None) == 1
+    lib.iesh2_destroy(h)
+    assert lib.iesh2_create(None, None, 1, 0, None) == 1
