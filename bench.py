@@ -573,6 +573,43 @@ def run_workload(args):
                                         "10^5 steps, GL and trapezoid discretisations",
                             "classical_KE_limit": kT / 2},
                     results=res)
+    elif args.workload == "two":
+        # Two adsorbate orbitals over six coordinates: 100 GL bath states
+        # (N = 102), Ne = 51, thermal nuclei around the restraint centres,
+        # random occupations with half the coefficient weight off them.
+        from paper_2212_00518_gb300 import two
+        n, dt = 4096, 2.0
+        md = W.two_orbital(100, seed=5)
+        x, p, occ, C = W.two_orbital_state(md, n, 3, kT=0.01, weight=0.5)
+        c = two.TwoOrbitalContext(md, n, stream=stream.cuda_stream)
+        c.set_state(x, p, occ.astype(np.int16), C)
+        c.run(dt, max(3, args.warmup), 0)
+        c.profile(True)
+        ms = _timed_steps(torch, stream, lambda: c.run(dt, 1, 0), 0, args.steps)
+        prof = c.profile_read()
+        c.profile(False)
+        tot = sum(v[0] for v in prof.values())
+        _, hops, frus = c.counters()
+        st = c.get_state()
+        c.close()
+        # oracle on one host core: a bounded sample of the same workload
+        from oracle import oracle as O
+        t0 = time.perf_counter()
+        ns = 16
+        O.run2(md, x[:ns], p[:ns], occ[:ns], np.transpose(C[:ns], (0, 2, 1)), dt, 5, 0)
+        cpu = ns * 5 / (time.perf_counter() - t0)
+        line.update(metric=METRIC + " [two adsorbate orbitals, six coordinates]", value=n * args.steps / (ms / 1e3),
+                    dtype="f64",
+                    config={"workload": "two-orbital adsorbate, 100 GL bath states (N=102), Ne=51, "
+                                        "six coordinates, 4096 trajectories, dt=2, thermal nuclei "
+                                        "kT=0.01 around the restraint centres",
+                            "value_is": "trajectory-steps/s, inputs resident"},
+                    cpu_baseline={"value": cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                  "sample": f"{ns} trajectories x 5 steps"},
+                    results={"ms_per_step": ms / args.steps,
+                             "kernel_share": {k: v[0] / tot for k, v in prof.items() if tot > 0},
+                             "hops": int(hops.sum()), "frustrated": int(frus.sum()),
+                             "status_nonzero": int(np.count_nonzero(st["status"]))})
     elif args.workload == "eocc":
         from paper_2212_00518_gb300 import eocc as E
         wl = W.eocc_workload(M=300, B=65536, seed=5)
@@ -615,7 +652,8 @@ def main():
                          "the uniform (Sec. II C; hop decisions unchanged)")
     ap.add_argument("--no-overlap", action="store_true",
                     help="skip the diabatic-basis propagator variant")
-    ap.add_argument("--workload", choices=["dw", "paper", "scatter", "erpenbeck", "relaxation", "eocc"],
+    ap.add_argument("--workload", choices=["dw", "paper", "scatter", "erpenbeck", "relaxation", "eocc",
+                                           "two"],
                     default="dw",
                     help="dw: the double-well batch (default, --M/--n-traj); the others print "
                          "secondary measurements")

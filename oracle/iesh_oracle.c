@@ -49,6 +49,14 @@
  *      fixed diabatic basis is H(x); over a step the propagator is the
  *      symmetric product of the half-step exponentials at the two ends,
  *      which is second order in dt like R3 and exact for frozen nuclei.
+ *   R10 two adsorbate orbitals over six nuclear coordinates: one mass for
+ *      all coordinates, a harmonic restraint U0 = m w^2 |x - x0|^2 / 2, the
+ *      step of R3-R7 with the velocity-projected couplings v . d in the
+ *      generator and the hop probabilities, the momentum change of a hop
+ *      along the NAC vector d_{m,s_a} (Sec. II B: rescale in the direction
+ *      of the NAC) with the energy-conserving root of smaller magnitude, and
+ *      eigenvectors signed so that their component on the coupled
+ *      combination c_0|0> + c_1|1> of the adsorbate orbitals is positive.
  *
  * Impurity populations (traj_populations): the paper defers the definition
  * of the diabatic population P_d to another work, so two readings are
@@ -1130,9 +1138,9 @@ int orc_eocc(int M, int Ne, const double *eps, const double *sqw, const double *
 }
 
 /* ------------------------------------------------------------------------ */
-/* Two adsorbate orbitals over six nuclear coordinates (reading R10 of the  */
-/* two-orbital variant): the electronic Hamiltonian of the occupied-energy  */
-/* model (eocc_build) plus a harmonic restraint U0 = m w^2 |x - x0|^2 / 2   */
+/* Two adsorbate orbitals over six nuclear coordinates (reading R10): the   */
+/* electronic Hamiltonian of the occupied-energy model (eocc_build) plus a  */
+/* harmonic restraint U0 = m w^2 |x - x0|^2 / 2                             */
 /* on every coordinate (one mass).  The same IESH step as traj_step in six  */
 /* dimensions: velocity Verlet, dense eigenpairs (gauge: the combination    */
 /* c1 Q_1j + c2 Q_2j of the impurity components positive), T^a = Q^T dH/dx_a */
