@@ -581,35 +581,42 @@ def run_workload(args):
         n, dt = 4096, 2.0
         md = W.two_orbital(100, seed=5)
         x, p, occ, C = W.two_orbital_state(md, n, 3, kT=0.01, weight=0.5)
-        c = two.TwoOrbitalContext(md, n, stream=stream.cuda_stream)
-        c.set_state(x, p, occ.astype(np.int16), C)
-        c.run(dt, max(3, args.warmup), 0)
-        c.profile(True)
-        ms = _timed_steps(torch, stream, lambda: c.run(dt, 1, 0), 0, args.steps)
-        prof = c.profile_read()
-        c.profile(False)
-        tot = sum(v[0] for v in prof.values())
-        _, hops, frus = c.counters()
-        st = c.get_state()
-        c.close()
+        res = {}
+        for prec, name in ((P.PREC_FP64, "fp64"), (P.PREC_MIXED, "mixed")):
+            c = two.TwoOrbitalContext(md, n, precision=prec, stream=stream.cuda_stream)
+            c.set_state(x, p, occ.astype(np.int16), C if prec == P.PREC_FP64 else C.astype(np.complex64))
+            c.run(dt, max(3, args.warmup), 0)
+            c.profile(True)
+            ms = _timed_steps(torch, stream, lambda: c.run(dt, 1, 0), 0, args.steps)
+            prof = c.profile_read()
+            c.profile(False)
+            tot = sum(v[0] for v in prof.values())
+            _, hops, frus = c.counters()
+            st = c.get_state()
+            c.close()
+            res[name] = {"traj_steps_per_s": n * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                         "kernel_share": {k: v[0] / tot for k, v in prof.items() if tot > 0},
+                         "hops": int(hops.sum()), "frustrated": int(frus.sum()),
+                         "status_nonzero": int(np.count_nonzero(st["status"]))}
+        res["mixed"]["speedup_vs_fp64"] = res["mixed"]["traj_steps_per_s"] / res["fp64"]["traj_steps_per_s"]
         # oracle on one host core: a bounded sample of the same workload
         from oracle import oracle as O
         t0 = time.perf_counter()
         ns = 16
         O.run2(md, x[:ns], p[:ns], occ[:ns], np.transpose(C[:ns], (0, 2, 1)), dt, 5, 0)
         cpu = ns * 5 / (time.perf_counter() - t0)
-        line.update(metric=METRIC + " [two adsorbate orbitals, six coordinates]", value=n * args.steps / (ms / 1e3),
-                    dtype="f64",
+        line.update(metric=METRIC + " [two adsorbate orbitals, six coordinates]",
+                    value=res["fp64"]["traj_steps_per_s"], dtype="f64",
                     config={"workload": "two-orbital adsorbate, 100 GL bath states (N=102), Ne=51, "
                                         "six coordinates, 4096 trajectories, dt=2, thermal nuclei "
                                         "kT=0.01 around the restraint centres",
-                            "value_is": "trajectory-steps/s, inputs resident"},
+                            "value_is": "FP64 trajectory-steps/s, inputs resident; mixed under results"},
                     cpu_baseline={"value": cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
                                   "sample": f"{ns} trajectories x 5 steps"},
-                    results={"ms_per_step": ms / args.steps,
-                             "kernel_share": {k: v[0] / tot for k, v in prof.items() if tot > 0},
-                             "hops": int(hops.sum()), "frustrated": int(frus.sum()),
-                             "status_nonzero": int(np.count_nonzero(st["status"]))})
+                    mixed={"value": res["mixed"]["traj_steps_per_s"],
+                           "dtype": "mixed (f32 coefficients, generator, propagation, LU and ratio "
+                                    "solves; f64 eigenpairs, forces, probabilities, rescale)"},
+                    results=res)
     elif args.workload == "eocc":
         from paper_2212_00518_gb300 import eocc as E
         wl = W.eocc_workload(M=300, B=65536, seed=5)

@@ -303,7 +303,10 @@ iesh_status iesh_eocc_backward(iesh_eocc_ctx *ctx, int64_t B, int precision, con
  * Eigenvector gauge: the component of eigenvector j on the coupled
  * combination c_0 |0> + c_1 |1> (c_a = vbar[a] f_a) is >= 0.
  * Layouts: x, p, F [n][6]; occ [n][Ne] int16 ascending; C [n][Ne][N]
- * complex double; pointers host or device as for iesh_*.  FP64 only. */
+ * complex, double for IESH_PREC_FP64 and float for IESH_PREC_MIXED (the
+ * one-coordinate split: FP64 eigenpairs, forces, hop probabilities and
+ * rescale; FP32 coefficients, coupling generator, propagation and overlap
+ * LU); pointers host or device as for iesh_*. */
 typedef struct iesh2_ctx iesh2_ctx;
 typedef struct {
     int n_bath;        /* M (2..254) */
@@ -317,11 +320,11 @@ typedef struct {
     double R[6];       /* coupling centres */
 } iesh2_model;
 
-/* Create a context for up to max_traj trajectories; skip_bound as in
- * iesh_options.  On failure *out may hold a context carrying the message
- * (destroy it). */
-iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int64_t max_traj, int skip_bound,
-                         void *cuda_stream);
+/* Create a context for up to max_traj trajectories; precision
+ * IESH_PREC_FP64 or IESH_PREC_MIXED; skip_bound as in iesh_options.  On
+ * failure *out may hold a context carrying the message (destroy it). */
+iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int precision, int64_t max_traj,
+                         int skip_bound, void *cuda_stream);
 iesh_status iesh2_destroy(iesh2_ctx *ctx);
 const char *iesh2_last_error(const iesh2_ctx *ctx);
 

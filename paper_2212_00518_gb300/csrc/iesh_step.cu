@@ -1449,6 +1449,8 @@ void configure_hop_smem()
     allow_max_smem(k_hop<double2, 256, 3>);
     allow_max_smem(k_hop<double2, 512, 1, true>);
     allow_max_smem(k_hop<double2, 256, 3, true>);
+    allow_max_smem(k_hop<float2, 512, 1, true>);
+    allow_max_smem(k_hop<float2, 256, 4, true>);
     allow_max_smem(k_cheb_f32t<4>);
 }
 
@@ -1456,7 +1458,6 @@ cudaError_t launch_hop(const DevState &s, double dt, double mass, uint64_t seed,
                        double *g_out, cudaStream_t st, bool mixed, bool ext)
 {
     if (s.n == 0) return cudaSuccess;
-    if (ext && mixed) return cudaErrorInvalidValue;
     const size_t smem = hop_smem_bytes(s.N, s.Ne, mixed, ext);
     // 256-thread CTAs (three per SM) when two or more fit in shared memory,
     // else one CTA of 512
@@ -1471,7 +1472,10 @@ cudaError_t launch_hop(const DevState &s, double dt, double mass, uint64_t seed,
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         kern<<<(unsigned)s.n, threads, smem, st>>>(s, dt, mass, seed, skip_bound, g_out);
     };
-    if (ext) {
+    if (ext && mixed) {
+        if (threads == 256) go(k_hop<float2, 256, 4, true>);
+        else go(k_hop<float2, 512, 1, true>);
+    } else if (ext) {
         if (threads == 256) go(k_hop<double2, 256, 3, true>);
         else go(k_hop<double2, 512, 1, true>);
     } else if (mixed) {

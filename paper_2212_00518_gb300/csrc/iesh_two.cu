@@ -1,5 +1,5 @@
 // iesh_two.cu -- IESH dynamics of a two-orbital adsorbate over six nuclear
-// coordinates (FP64): kernels and the iesh2_* C-ABI.
+// coordinates: kernels and the iesh2_* C-ABI.
 //
 // Electrons: adsorbate orbitals a = 0, 1 with levels h_a(x), each coupled to
 // bath state k by c_a(x) sqrt(w_k), c_a = vbar_a f_a(x) (the occupied-energy
@@ -22,6 +22,11 @@
 //   T^y_jk = sum_a Q_aj Q_ak [dh_a/dy + (dlog f_a/dy) (lam_j + lam_k - 2 h_a)],
 // d^y_jk = T^y_jk / (lam_k - lam_j), and the Hellmann-Feynman force is
 // F_y = -dU0/dy - sum_{j occupied} T^y_jj.
+//
+// Precision: FP64, or mixed (the one-coordinate model's split): FP64
+// eigenpairs, forces, hop probabilities and rescale; FP32 coefficients,
+// coupling generator, propagation (tensor cores where the trajectory fits
+// one CTA) and overlap LU.
 //
 // One step (Sec. II B, II C in six dimensions):
 //   k2_eigen      kick + drift, eigenpairs, forces, second kick, the
@@ -166,6 +171,10 @@ __global__ void __launch_bounds__(256) k2_eigen(DevState s, Model2Dev md, double
     __shared__ double xs[6], ps[6], s_Z2;
     __shared__ int s_pos;
     const int tid = threadIdx.x;
+    // warm start of root tid: the previous roots extrapolated linearly (each
+    // thread reads its own entries before it overwrites them below)
+    double guess = 0.0;
+    if (mode == 1 && tid < N) guess = 2.0 * s.lam[t * N + tid] - s.lam_prev[t * N + tid];
     if (tid < 6) {
         double x = s.x[t * 6 + tid], p = s.p[t * 6 + tid];
         if (mode == 1) {
@@ -248,7 +257,7 @@ __global__ void __launch_bounds__(256) k2_eigen(DevState s, Model2Dev md, double
             int o;
             double tau;
             const Poles<double> pp = {P, pole, wt, nullptr, nullptr, nullptr};
-            secular_root<double>(r, pp, hp, s_Z2, false, 0.0, lam, qp, st, &o, &tau);
+            secular_root<double>(r, pp, hp, s_Z2, mode == 1, guess, lam, qp, st, &o, &tau);
             if (!decoupled) {
                 // lam - h_-: the exact offset when the origin pole is h_- itself
                 const double lmh = (o == pos) ? tau : (pole[o] - hm) + tau;
@@ -288,6 +297,7 @@ __global__ void __launch_bounds__(256) k2_eigen(DevState s, Model2Dev md, double
         s.lam[t * N + i] = lam_s[i];
         s.q0[t * N + i] = Q0_s[i];
         s.q2[t * N + i] = Q1_s[i];
+        if (mode == 0) s.lam_prev[t * N + i] = lam_s[i];  // no extrapolation at the first step
     }
     double S[2], U[2];
     occ_sums(lam_s, Q0_s, Q1_s, s.occ + t * Ne, Ne, ad, red, S, U);
@@ -358,6 +368,79 @@ __global__ void __launch_bounds__(256) k2_build_w(DevState s, Model2Dev md, doub
         const double Lk = hdt * (lk0 + lk1);
         lo = fmin(lo, Lk - Rk);
         hi = fmax(hi, Lk + Rk);
+    }
+    lo = block_min(lo, red);
+    hi = block_max(hi, red);
+    if (threadIdx.x == 0) cheb_setup(s, t, lo, hi, tol);
+}
+
+// Mixed precision: the same W in FP32, rows padded to Np = N rounded up to 4
+// with zeros (the layout of the FP32 propagators).  Eigenvalue differences
+// are formed in FP64 and rounded once, so nearly degenerate pairs keep FP32
+// relative accuracy; numerators in FP32 from lam - h_a rounded from FP64.
+__global__ void __launch_bounds__(256) k2_build_w_f32(DevState s, Model2Dev md, double dt, double tol)
+{
+    extern __shared__ double w2_sh[];
+    const int64_t t = traj_of(s, blockIdx.x);
+    if (t < 0 || (s.status[t] & ST_DONE)) return;
+    const int N = s.N, Np = (N + 3) & ~3;
+    double *l0 = w2_sh, *l1 = l0 + N, *red = l1 + N;         // [N], [N], [32]
+    float *a0 = reinterpret_cast<float *>(red + 32), *b0 = a0 + N, *a1 = b0 + N, *b1 = a1 + N;
+    float *m00 = b1 + N, *m01 = m00 + N, *m10 = m01 + N, *m11 = m10 + N;  // lam - h_a per end
+    double x0[6], v0[6], x1[6], v1[6];
+    for (int y = 0; y < 6; ++y) {
+        x0[y] = s.x_prev[t * 6 + y];
+        v0[y] = s.vprev[t * 6 + y];
+        x1[y] = s.x[t * 6 + y];
+        v1[y] = s.p[t * 6 + y] / md.mass;
+    }
+    const Ads2 e0 = ads2_eval(md, x0), e1 = ads2_eval(md, x1);
+    double hv0[2], kv0[2], hv1[2], kv1[2];
+    ads2_project(md, e0, v0, hv0, kv0);
+    ads2_project(md, e1, v1, hv1, kv1);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double la = s.lam_prev[t * N + i], lb = s.lam[t * N + i];
+        l0[i] = la;
+        l1[i] = lb;
+        a0[i] = (float)s.q0_prev[t * N + i];
+        b0[i] = (float)s.q2_prev[t * N + i];
+        a1[i] = (float)s.q0[t * N + i];
+        b1[i] = (float)s.q2[t * N + i];
+        m00[i] = (float)(la - e0.h[0]);
+        m01[i] = (float)(la - e0.h[1]);
+        m10[i] = (float)(lb - e1.h[0]);
+        m11[i] = (float)(lb - e1.h[1]);
+    }
+    const float hdt = (float)(0.5 * dt);
+    const float H00 = (float)hv0[0], K00 = (float)kv0[0], H01 = (float)hv0[1], K01 = (float)kv0[1];
+    const float H10 = (float)hv1[0], K10 = (float)kv1[0], H11 = (float)hv1[1], K11 = (float)kv1[1];
+    __syncthreads();
+    float *W = reinterpret_cast<float *>(s.scratch + t * s.scratch_stride);  // [N][Np]
+    double lo = __longlong_as_double(0x7ff0000000000000ll), hi = -lo;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const double lk0 = l0[k], lk1 = l1[k];
+        const float ak0 = a0[k], bk0 = b0[k], ak1 = a1[k], bk1 = b1[k];
+        const float nk00 = m00[k], nk01 = m01[k], nk10 = m10[k], nk11 = m11[k];
+        float Rk = 0.0f;
+        for (int j = 0; j < N; ++j) {
+            float w = 0.0f;
+            if (j != k) {
+                const float T0 = a0[j] * ak0 * (H00 + K00 * (m00[j] + nk00)) +
+                                 b0[j] * bk0 * (H01 + K01 * (m01[j] + nk01));
+                const float T1 = a1[j] * ak1 * (H10 + K10 * (m10[j] + nk10)) +
+                                 b1[j] * bk1 * (H11 + K11 * (m11[j] + nk11));
+                w = hdt * (T0 / (float)(lk0 - l0[j]) + T1 / (float)(lk1 - l1[j]));
+            }
+            W[(int64_t)j * Np + k] = w;
+            Rk += fabsf(w);
+        }
+        if (k < Np - N)
+            for (int j = 0; j < N; ++j) W[(int64_t)j * Np + N + k] = 0.0f;  // row padding
+        // margin for the FP32 rounding of the row sum
+        const double R = (double)Rk * (1.0 + 1e-5);
+        const double Lk = 0.5 * dt * (lk0 + lk1);
+        lo = fmin(lo, Lk - R);
+        hi = fmax(hi, Lk + R);
     }
     lo = block_min(lo, red);
     hi = block_max(hi, red);
@@ -458,6 +541,7 @@ struct iesh2_ctx {
     cudaStream_t stream = nullptr;
     int N = 0, M = 0, Ne = 0;
     int skip_bound = 0;
+    bool mixed = false;
     Model2Dev md;
     DevState ds;
     std::vector<void *> allocs;
@@ -525,10 +609,17 @@ cudaError_t launch_build_w2(iesh2_ctx *ctx, double dt, double tol)
     const DevState &d = ctx->ds;
     if (d.n == 0) return cudaSuccess;
     const int threads = std::min(256, (d.N + 31) & ~31);
-    k2_build_w<<<(unsigned)d.n, threads, (size_t)(6 * d.N + 32) * sizeof(double), ctx->stream>>>(
-        d, ctx->md, dt, tol);
+    if (ctx->mixed)
+        k2_build_w_f32<<<(unsigned)d.n, threads,
+                         (size_t)(2 * d.N + 32) * sizeof(double) + (size_t)8 * d.N * sizeof(float),
+                         ctx->stream>>>(d, ctx->md, dt, tol);
+    else
+        k2_build_w<<<(unsigned)d.n, threads, (size_t)(6 * d.N + 32) * sizeof(double), ctx->stream>>>(
+            d, ctx->md, dt, tol);
     return cudaGetLastError();
 }
+
+size_t coeff_bytes(const iesh2_ctx *ctx) { return ctx->mixed ? 8 : 16; }
 
 cudaError_t launch_accept2(iesh2_ctx *ctx)
 {
@@ -554,8 +645,8 @@ iesh_status iesh2_destroy(iesh2_ctx *ctx)
     return IESH_OK;
 }
 
-iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int64_t max_traj, int skip_bound,
-                         void *cuda_stream)
+iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int precision, int64_t max_traj,
+                         int skip_bound, void *cuda_stream)
 {
     if (!out) return IESH_EINVAL;
     *out = nullptr;
@@ -574,6 +665,9 @@ iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int64_t max_
     if (!(model->band_hi > model->band_lo)) return fail2(ctx, IESH_EINVAL, "empty band");
     if (!(model->theta[14] != 0.0 && model->theta[15] != 0.0))
         return fail2(ctx, IESH_EINVAL, "coupling widths theta[14], theta[15] must be nonzero");
+    if (precision != IESH_PREC_FP64 && precision != IESH_PREC_MIXED)
+        return fail2(ctx, IESH_EINVAL, "unknown precision %d", precision);
+    ctx->mixed = precision == IESH_PREC_MIXED;
     ctx->N = N;
     ctx->M = M;
     ctx->Ne = Ne;
@@ -621,6 +715,7 @@ iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int64_t max_
     d.eps = eps_d;
     d.z0 = sq_d;
     configure_hop_smem();
+    configure_cheb_tc();
     CU2(cudaMemcpyAsync(eps_d, eps.data(), M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CU2(cudaMemcpyAsync(sq_d, sq.data(), M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CU2(cudaStreamSynchronize(ctx->stream));
@@ -646,7 +741,7 @@ iesh_status iesh2_set_state(iesh2_ctx *ctx, int64_t n_traj, const double *x, con
         CU2(cudaMemcpyAsync(d.x, x, n * 6 * sizeof(double), cudaMemcpyDefault, ctx->stream));
         CU2(cudaMemcpyAsync(d.p, p, n * 6 * sizeof(double), cudaMemcpyDefault, ctx->stream));
         CU2(cudaMemcpyAsync(d.occ, occ, n * ctx->Ne * sizeof(int16_t), cudaMemcpyDefault, ctx->stream));
-        CU2(cudaMemcpyAsync(d.C, C, n * ctx->Ne * ctx->N * 16, cudaMemcpyDefault, ctx->stream));
+        CU2(cudaMemcpyAsync(d.C, C, n * ctx->Ne * ctx->N * coeff_bytes(ctx), cudaMemcpyDefault, ctx->stream));
     }
     CU2(launch_eigen2(ctx, 0.0, 0));
     // host sources may be pageable: the copies above must finish before return
@@ -665,7 +760,7 @@ iesh_status iesh2_get_state(iesh2_ctx *ctx, double *x, double *p, int16_t *occ, 
     if ((st = copy_out2(ctx, x, d.x, n * 6 * sizeof(double), sync)) != IESH_OK) return st;
     if ((st = copy_out2(ctx, p, d.p, n * 6 * sizeof(double), sync)) != IESH_OK) return st;
     if ((st = copy_out2(ctx, occ, d.occ, n * ctx->Ne * sizeof(int16_t), sync)) != IESH_OK) return st;
-    if ((st = copy_out2(ctx, C, d.C, n * ctx->Ne * ctx->N * 16, sync)) != IESH_OK) return st;
+    if ((st = copy_out2(ctx, C, d.C, n * ctx->Ne * ctx->N * coeff_bytes(ctx), sync)) != IESH_OK) return st;
     if ((st = copy_out2(ctx, status, d.status, n * sizeof(uint32_t), sync)) != IESH_OK) return st;
     if (sync) CU2(cudaStreamSynchronize(ctx->stream));
     return IESH_OK;
@@ -699,12 +794,15 @@ iesh_status iesh2_run(iesh2_ctx *ctx, double dt, int64_t n_steps, uint64_t seed)
     if (!(dt > 0.0) || n_steps < 0) return fail2(ctx, IESH_EINVAL, "need dt > 0 and n_steps >= 0");
     const DevState &d = ctx->ds;
     const cudaStream_t st = ctx->stream;
+    const bool mx = ctx->mixed;
+    // Chebyshev truncation at the rounding level of the propagation's precision
+    const double tol = mx ? 1e-7 : 1e-15;
     for (int64_t k = 0; k < n_steps; ++k) {
         CU2(ctx->timer.run(st, IESH_K_EIGEN, [&] { return launch_eigen2(ctx, dt, 1); }));
-        CU2(ctx->timer.run(st, IESH_K_COUPLING, [&] { return launch_build_w2(ctx, dt, 1e-15); }));
-        CU2(ctx->timer.run(st, IESH_K_PROPAGATE, [&] { return launch_cheb(d, dt, false, st); }));
+        CU2(ctx->timer.run(st, IESH_K_COUPLING, [&] { return launch_build_w2(ctx, dt, tol); }));
+        CU2(ctx->timer.run(st, IESH_K_PROPAGATE, [&] { return launch_cheb(d, dt, mx, st); }));
         CU2(ctx->timer.run(st, IESH_K_HOP, [&] {
-            return launch_hop(d, dt, ctx->md.mass, seed, ctx->skip_bound, nullptr, st, false, true);
+            return launch_hop(d, dt, ctx->md.mass, seed, ctx->skip_bound, nullptr, st, mx, true);
         }));
         CU2(ctx->timer.run(st, IESH_K_OTHER, [&] { return launch_accept2(ctx); }));
     }
@@ -724,7 +822,7 @@ iesh_status iesh2_hop_probabilities(iesh2_ctx *ctx, double dt, double *g)
         CU2(cudaMallocAsync((void **)&tmp, bytes, ctx->stream));
         dst = tmp;
     }
-    CU2(launch_hop(d, dt, ctx->md.mass, 0, 0, dst, ctx->stream, false, true));
+    CU2(launch_hop(d, dt, ctx->md.mass, 0, 0, dst, ctx->stream, ctx->mixed, true));
     if (host) {
         CU2(cudaMemcpyAsync(g, tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream));
         CU2(cudaFreeAsync(tmp, ctx->stream));

@@ -123,8 +123,8 @@ def load(path=LIB_PATH):
     L.iesh_eocc_forward.argtypes = [_vp, ctypes.c_int64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
     L.iesh_eocc_backward.argtypes = [_vp, ctypes.c_int64, ctypes.c_int, _vp, _vp, _vp, _vp, _vp,
                                      _vp, _vp]
-    L.iesh2_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_Model2), ctypes.c_int64,
-                               ctypes.c_int, _vp]
+    L.iesh2_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_Model2), ctypes.c_int,
+                               ctypes.c_int64, ctypes.c_int, _vp]
     L.iesh2_destroy.argtypes = [_vp]
     L.iesh2_last_error.argtypes = [_vp]
     L.iesh2_last_error.restype = ctypes.c_char_p

@@ -1,6 +1,6 @@
 """IESH dynamics of a two-orbital adsorbate over six nuclear coordinates
 (include/iesh.h, iesh2_*): ctypes marshalling only; every step runs in the
-library's CUDA kernels (FP64)."""
+library's CUDA kernels (FP64 or the mixed-precision split)."""
 import ctypes
 
 import numpy as np
@@ -29,10 +29,12 @@ def model_struct(md):
 
 class TwoOrbitalContext:
     """A batch of two-orbital trajectories on one GPU (wraps iesh2_ctx).
-    N = M + 2 orbitals; x, p, F are [n][6]; C is complex128 [n][Ne][N]."""
+    N = M + 2 orbitals; x, p, F are [n][6]; C is [n][Ne][N], complex128
+    (FP64) or complex64 (mixed precision)."""
 
-    def __init__(self, model, max_traj, skip_bound=False, stream=None):
+    def __init__(self, model, max_traj, precision=_I.PREC_FP64, skip_bound=False, stream=None):
         self.L = _I.load()
+        self.precision = int(precision)
         self.model = dict(model)
         self.N = int(model["M"]) + 2
         self.Ne = int(model["Ne"])
@@ -41,7 +43,7 @@ class TwoOrbitalContext:
         self._m = model_struct(model)
         self.stream = _I.current_stream_handle() if stream is None else stream
         h = _I._vp()
-        rc = self.L.iesh2_create(ctypes.byref(h), ctypes.byref(self._m), self.max_traj,
+        rc = self.L.iesh2_create(ctypes.byref(h), ctypes.byref(self._m), self.precision, self.max_traj,
                                  int(bool(skip_bound)), _I._vp(self.stream) if self.stream else None)
         self._h = h
         if rc != _I.IESH_OK:
@@ -66,6 +68,10 @@ class TwoOrbitalContext:
             raise _I.IeshError(f"{what}: {_I.STATUS_NAMES.get(rc, rc)}: "
                                f"{self.L.iesh2_last_error(self._h).decode()}")
 
+    @property
+    def cdtype(self):
+        return np.complex128 if self.precision == _I.PREC_FP64 else np.complex64
+
     def set_state(self, x, p, occ, C):
         n = int(x.shape[0])
         self._check(self.L.iesh2_set_state(self._h, n, _I._ptr(x), _I._ptr(p), _I._ptr(occ),
@@ -77,7 +83,7 @@ class TwoOrbitalContext:
         x = np.zeros((n, 6)) if x is None else x
         p = np.zeros((n, 6)) if p is None else p
         occ = np.zeros((n, self.Ne), np.int16) if occ is None else occ
-        C = np.zeros((n, self.Ne, self.N), np.complex128) if C is None else C
+        C = np.zeros((n, self.Ne, self.N), self.cdtype) if C is None else C
         status = np.zeros(n, np.uint32) if status is None else status
         self._check(self.L.iesh2_get_state(self._h, _I._ptr(x), _I._ptr(p), _I._ptr(occ), _I._ptr(C),
                                            _I._ptr(status)), "iesh2_get_state")

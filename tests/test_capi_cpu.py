@@ -69,7 +69,7 @@ def test_invalid_two_orbital_models_rejected_without_device(lib):
         md = W.two_orbital(20)
         md.update(bad)
         h = ctypes.c_void_p()
-        rc = lib.iesh2_create(ctypes.byref(h), ctypes.byref(two.model_struct(md)), 16, 0, None)
+        rc = lib.iesh2_create(ctypes.byref(h), ctypes.byref(two.model_struct(md)), 0, 16, 0, None)
         assert rc == 1, (bad, rc)
         assert lib.iesh2_last_error(h)
         lib.iesh2_destroy(h)
@@ -77,6 +77,10 @@ def test_invalid_two_orbital_models_rejected_without_device(lib):
     md["theta"] = md["theta"].copy()
     md["theta"][14] = 0.0
     h = ctypes.c_void_p()
-    assert lib.iesh2_create(ctypes.byref(h), ctypes.byref(two.model_struct(md)), 16, 0, None) == 1
+    assert lib.iesh2_create(ctypes.byref(h), ctypes.byref(two.model_struct(md)), 0, 16, 0, None) == 1
     lib.iesh2_destroy(h)
-    assert lib.iesh2_create(None, None, 1, 0, None) == 1
+    h = ctypes.c_void_p()
+    assert lib.iesh2_create(ctypes.byref(h), ctypes.byref(two.model_struct(W.two_orbital(20))), 7, 16, 0,
+                            None) == 1
+    lib.iesh2_destroy(h)
+    assert lib.iesh2_create(None, None, 0, 1, 0, None) == 1

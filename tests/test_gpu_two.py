@@ -158,3 +158,64 @@ def test_energy_conserved_with_hops_on_gpu(P):
     Cn = ctx.get_state()["C"]
     G = np.einsum("tei,tfi->tef", Cn.conj(), Cn)
     assert np.abs(G - np.eye(md["Ne"])[None]).max() < 1e-10
+
+
+# ------------------------------------------------------------ mixed precision
+# FP64 eigenpairs, forces, probabilities and rescale; FP32 coefficients,
+# generator, propagation (3xTF32 tensor cores for N <= 128, Ne <= 56) and
+# overlap LU.  Bounds as for the one-coordinate mixed path.
+def _mixed(P, md, x, p, occ, C):
+    C32 = C.astype(np.complex64)
+    ctx = _ctx(P, md, x, p, occ, C32, precision=1)
+    return ctx, C32.astype(np.complex128)
+
+
+@pytest.mark.parametrize("name", ["M12", "M40", "strong", "one_coupling"])
+def test_mixed_hop_probabilities(P, name):
+    md = CASES[name]
+    n, dt = 4, 20.0
+    x, p, occ, C = W.two_orbital_state(md, n, 13, weight=0.6)
+    ctx, Cr = _mixed(P, md, x, p, occ, C)
+    g = ctx.hop_probabilities(dt)
+    for t in range(n):
+        d = O.eigen2(md, x[t], occ[t])[2]
+        dv = np.tensordot(p[t] / md["mass"], d, axes=1)
+        gref = O.hop_probs(occ[t], Cr[t].T, dv, 1.0, dt)[0]
+        assert np.abs(g[t] - gref).max() <= 2e-6 * np.abs(gref).max()
+
+
+@pytest.mark.parametrize("name", ["M12", "M40", "M100", "strong", "one_coupling", "no_coupling"])
+def test_mixed_one_step(P, name):
+    md = CASES[name]
+    n, dt = 6, 5.0
+    x, p, occ, C = W.two_orbital_state(md, n, 17, weight=0.6)
+    ctx, Cr = _mixed(P, md, x, p, occ, C)
+    ctx.run(dt, 1, seed=3)
+    st = ctx.get_state()
+    ref = O.run2(md, x, p, occ, np.transpose(Cr, (0, 2, 1)), dt, 1, seed=3)
+    assert np.all(st["status"] == 0)
+    assert np.array_equal(st["occ"], ref["occ"])
+    assert np.abs(st["x"] - ref["x"]).max() <= 1e-12 * (1 + np.abs(ref["x"]).max())
+    assert np.abs(st["p"] - ref["p"]).max() <= 1e-11 * (1 + np.abs(ref["p"]).max())
+    assert np.abs(np.transpose(st["C"], (0, 2, 1)) - ref["C"]).max() <= 1e-6
+
+
+@pytest.mark.parametrize("name", ["M12", "strong"])
+def test_mixed_100_steps(P, name):
+    """Hop decisions agree unless a uniform falls within the FP32 error of a
+    cumulative boundary: at least 7 of 8 trajectories identical; on those, C
+    within 3e-5 after 100 steps."""
+    md = CASES[name]
+    n, steps, dt = 8, 100, 5.0
+    x, p, occ, C = W.two_orbital_state(md, n, 19, kT=0.01, weight=1.0)
+    ctx, Cr = _mixed(P, md, x, p, occ, C)
+    ctx.run(dt, steps, seed=5)
+    st = ctx.get_state()
+    _, hops, _ = ctx.counters()
+    ref = O.run2(md, x, p, occ, np.transpose(Cr, (0, 2, 1)), dt, steps, seed=5)
+    assert ref["hops"].sum() > 0
+    same = [t for t in range(n) if np.array_equal(st["occ"][t], ref["occ"][t]) and hops[t] == ref["hops"][t]]
+    assert len(same) >= n - 1
+    Cg = np.transpose(st["C"], (0, 2, 1))
+    assert np.abs(Cg[same] - ref["C"][same]).max() <= 3e-5
+    assert np.abs(st["x"][same] - ref["x"][same]).max() <= 1e-6 * np.abs(ref["x"]).max()
