@@ -578,7 +578,7 @@ def run_workload(args):
         # (N = 102), Ne = 51, thermal nuclei around the restraint centres,
         # random occupations with half the coefficient weight off them.
         from paper_2212_00518_gb300 import two
-        n, dt = 4096, 2.0
+        n, dt = args.n_traj, 2.0
         md = W.two_orbital(100, seed=5)
         x, p, occ, C = W.two_orbital_state(md, n, 3, kT=0.01, weight=0.5)
         res = {}
@@ -608,7 +608,7 @@ def run_workload(args):
         line.update(metric=METRIC + " [two adsorbate orbitals, six coordinates]",
                     value=res["fp64"]["traj_steps_per_s"], dtype="f64",
                     config={"workload": "two-orbital adsorbate, 100 GL bath states (N=102), Ne=51, "
-                                        "six coordinates, 4096 trajectories, dt=2, thermal nuclei "
+                                        f"six coordinates, {n} trajectories, dt=2, thermal nuclei "
                                         "kT=0.01 around the restraint centres",
                             "value_is": "FP64 trajectory-steps/s, inputs resident; mixed under results"},
                     cpu_baseline={"value": cpu, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -75,6 +75,14 @@ struct DevState {
     int32_t *hop_pair;         // [n] a N + m of the selected hop, or -1
 };
 
+// Smallest power of two >= n (width of the fixed-order tree reductions).
+__host__ __device__ inline int eigen_pow2(int n)
+{
+    int p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+
 // Trajectory visited by work item w, or -1 when w is past the batch or the
 // live count.
 __device__ __forceinline__ int64_t traj_of(const DevState &s, int64_t w)

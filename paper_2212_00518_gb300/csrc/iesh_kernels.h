@@ -29,6 +29,8 @@ void configure_hop_smem();
 void lead_bath(int disc, int n, double a, double b, double mu, int n_lo, std::vector<double> &eps,
                std::vector<double> &w);
 void cheb_shape(int N, int Ne, int &ept, int &G);
+// Trajectories per CTA of the eigen kernels (slots of N threads, <= 512 threads)
+int eigen_tpb(int N);
 // FP32 (mixed-precision) propagator: 4 electrons per thread, G column groups
 constexpr size_t kCheb32MaxSmem = 110 * 1024;
 size_t cheb32_smem_bytes(int N, int G);

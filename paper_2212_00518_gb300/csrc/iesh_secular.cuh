@@ -205,18 +205,18 @@ __device__ bool sec_iterate(const Poles<R> &P, R h, int o, int kind, R D, R &lo,
         if (e.g < R(0)) lo = tau;
         else hi = tau;
         R tn;
-        if (kind == 0) {
-            const R tp = tau - D;
+        if (kind <= 1) {
+            // model root of c tau^2 + B tau + s D = 0 in the gap, by the form
+            // without cancellation for the sign of B (B < 0 happens when the
+            // origin pole's weight s is small against the other end's)
+            const R sg = kind == 0 ? R(1) : R(-1);
+            const R tp = tau - sg * D;
             const R t = e.gp_rest * tp * tp;
-            const R c = e.g + s / tau + t / tp;
+            const R c = sg * (e.g + s / tau + t / tp);
             const R B = c * D + s + t;
-            tn = R(2) * s * D / (B + sqrt(fmax(B * B - R(4) * c * s * D, R(0))));
-        } else if (kind == 1) {
-            const R tp = tau + D;
-            const R t = e.gp_rest * tp * tp;
-            const R c = -(e.g + s / tau + t / tp);
-            const R B = c * D + s + t;
-            tn = -R(2) * s * D / (B + sqrt(fmax(B * B - R(4) * c * s * D, R(0))));
+            const R sq = sqrt(fmax(B * B - R(4) * c * s * D, R(0)));
+            if (B >= R(0) || c == R(0)) tn = sg * R(2) * s * D / (B + sq);
+            else tn = sg * (B - sq) / (R(2) * c);
         } else {
             const R ee = e.gp_rest;
             const R c = e.g - ee * tau + s / tau;

@@ -36,13 +36,6 @@ int eigen_tpb(int N)
     return best;
 }
 
-__host__ __device__ inline int eigen_pow2(int n)
-{
-    int p = 1;
-    while (p < n) p <<= 1;
-    return p;
-}
-
 // red[0] <- sum of red[0..P) (P a power of two >= the slot width), halving
 // the active range each round; every thread of the CTA must call it.
 __device__ __forceinline__ void slot_tree_sum(double *red, int r, bool inslot, int P)

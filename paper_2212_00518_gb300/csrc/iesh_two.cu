@@ -63,6 +63,7 @@ struct Model2Dev {
     double th[16];  // eps_0, eps_1, g_{0,0..5}, g_{1,0..5}, sigma_0, sigma_1
     double vbar[2], R[6], x0[6];
     double mass, omega;
+    double wsum;    // sum_k w_k of the bath
 };
 
 // Adsorbate quantities at one geometry: levels h_a, coupling amplitudes c_a
@@ -153,63 +154,120 @@ __device__ __forceinline__ void occ_sums(const double *lam, const double *Q0, co
     U[1] = block_sum(u1, red);
 }
 
+// Per-trajectory scalars of the eigen kernel (one slot's shared record).
+struct Eig2Slot {
+    Ads2 ad;
+    double x[6], p[6];
+    double c, hp, hm, tt;
+    int pos, case_;  // pos: bath poles below h_-; case_: 0 general, 1 |-> decoupled, 2 no coupling
+};
+
 // mode 0: eigenpairs and forces at x (state set-up).  mode 1: a step's
 // kick + drift, eigenpairs at the new x, forces and the second kick.
-// One CTA per trajectory, one thread per root (N <= 256 threads).
-__global__ void __launch_bounds__(256) k2_eigen(DevState s, Model2Dev md, double dt, int mode)
+// tpb trajectories per CTA (slots of N threads), one thread per root; every
+// barrier is reached by all threads of the CTA.
+__global__ void __launch_bounds__(512, 1) k2_eigen(DevState s, Model2Dev md, double dt, int mode, int tpb)
 {
     extern __shared__ double e2_sh[];
-    const int64_t t = traj_of(s, blockIdx.x);
-    if (t < 0 || (s.status[t] & ST_DONE)) return;
     const int N = s.N, M = s.M, Ne = s.Ne;
-    double *pole = e2_sh;          // [M + 1] sorted poles
-    double *wt = pole + (M + 1);   // [M + 1] their weights
-    double *lam_s = wt + (M + 1);  // [N]
-    double *Q0_s = lam_s + N;      // [N]
-    double *Q1_s = Q0_s + N;       // [N]
-    double *red = Q1_s + N;        // [32]
-    __shared__ double xs[6], ps[6], s_Z2;
-    __shared__ int s_pos;
-    const int tid = threadIdx.x;
-    // warm start of root tid: the previous roots extrapolated linearly (each
-    // thread reads its own entries before it overwrites them below)
-    double guess = 0.0;
-    if (mode == 1 && tid < N) guess = 2.0 * s.lam[t * N + tid] - s.lam_prev[t * N + tid];
-    if (tid < 6) {
-        double x = s.x[t * 6 + tid], p = s.p[t * 6 + tid];
+    const int slot = threadIdx.x / N;
+    const int r = threadIdx.x - slot * N;
+    const bool inslot = slot < tpb;
+    const int64_t t = inslot ? traj_of(s, (int64_t)blockIdx.x * tpb + slot) : -1;
+    const bool act = t >= 0 && !(s.status[t] & ST_DONE);
+    const int Pw = eigen_pow2(N);                          // reduction width
+    const int per = 2 * (M + 1) + 3 * N + 4 * Pw;
+    double *eps_s = e2_sh;                                 // [M] bath energies, shared
+    double *pole = eps_s + M + (inslot ? slot : 0) * per;  // [M + 1] sorted poles
+    double *wt = pole + (M + 1);                           // [M + 1] their weights
+    double *lam_s = wt + (M + 1);                          // [N]
+    double *Q0_s = lam_s + N;                              // [N]
+    double *Q1_s = Q0_s + N;                               // [N]
+    double *red = Q1_s + N;                                // [4][Pw] reductions / staging
+    Eig2Slot *sl = reinterpret_cast<Eig2Slot *>(e2_sh + M + tpb * per) + (inslot ? slot : 0);
+    for (int k = threadIdx.x; k < M; k += blockDim.x) eps_s[k] = s.eps[k];
+    // warm start: the previous roots extrapolated linearly (each thread reads
+    // its own entries before it overwrites them)
+    double guess = 0.0, lam_old = 0.0;
+    if (act) {
         if (mode == 1) {
-            s.x_prev[t * 6 + tid] = x;
-            p += 0.5 * dt * s.F[t * 6 + tid];
-            x += dt * p / md.mass;
+            lam_old = s.lam[t * N + r];
+            guess = 2.0 * lam_old - s.lam_prev[t * N + r];
+            s.lam_prev[t * N + r] = lam_old;
+            s.q0_prev[t * N + r] = s.q0[t * N + r];
+            s.q2_prev[t * N + r] = s.q2[t * N + r];
         }
-        xs[tid] = x;
-        ps[tid] = p;
+        if (r < 6) {
+            double x = s.x[t * 6 + r], p = s.p[t * 6 + r];
+            if (mode == 1) {
+                s.x_prev[t * 6 + r] = x;
+                p += 0.5 * dt * s.F[t * 6 + r];
+                x += dt * p / md.mass;
+            }
+            sl->x[r] = x;
+            sl->p[r] = p;
+        }
     }
-    if (mode == 1)
-        for (int i = tid; i < N; i += blockDim.x) {
-            s.lam_prev[t * N + i] = s.lam[t * N + i];
-            s.q0_prev[t * N + i] = s.q0[t * N + i];
-            s.q2_prev[t * N + i] = s.q2[t * N + i];
-        }
     __syncthreads();
-    const Ads2 ad = ads2_eval(md, xs);
-    const double c0 = ad.c[0], c1 = ad.c[1], csq = c0 * c0 + c1 * c1;
+    // adsorbate quantities and the rotation of the pair (one thread per slot)
+    if (act && r == 0) {
+        const Ads2 ad = ads2_eval(md, sl->x);
+        sl->ad = ad;
+        const double c0 = ad.c[0], c1 = ad.c[1], csq = c0 * c0 + c1 * c1;
+        if (!(csq > 0.0)) {
+            sl->case_ = 2;
+        } else {
+            const double hm = (c1 * c1 * ad.h[0] + c0 * c0 * ad.h[1]) / csq;
+            const double tt = c0 * c1 * (ad.h[1] - ad.h[0]) / csq;
+            sl->c = sqrt(csq);
+            sl->hp = (c0 * c0 * ad.h[0] + c1 * c1 * ad.h[1]) / csq;
+            sl->hm = hm;
+            sl->tt = tt;
+            sl->case_ = (tt * tt > 0.0) ? 0 : 1;
+            int lo = 0, hi = M;  // bath energies below h_- (ascending: bisection)
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (eps_s[mid] < hm) lo = mid + 1;
+                else hi = mid;
+            }
+            sl->pos = lo;
+        }
+    }
+    __syncthreads();
+    const Ads2 &ad = sl->ad;
+    const double c0 = ad.c[0], c1 = ad.c[1];
+    const int cs = act ? sl->case_ : 2;
+    const int pos = sl->pos;
+    const double c = sl->c, hm = sl->hm, tt = sl->tt;
+    if (act && cs != 2) {
+        for (int k = r; k < M; k += N) {
+            const int q = (cs == 1 || k < pos) ? k : k + 1;
+            pole[q] = eps_s[k];
+            wt[q] = (c0 * c0 + c1 * c1) * (s.z0[k] * s.z0[k]);
+        }
+        if (cs == 0 && r == 0) {
+            pole[pos] = hm;
+            wt[pos] = tt * tt;
+        }
+    }
+    __syncthreads();
     uint32_t st = 0;
-    if (!(csq > 0.0)) {
-        // no coupling: diagonal Hamiltonian, sorted (ties: adsorbate first)
-        const double h0 = ad.h[0], h1 = ad.h[1];
-        if (tid < N) {
-            double lam, q0 = 0.0, q1 = 0.0;
+    double lam = 0.0, qp = 0.0;
+    if (act) {
+        if (cs == 2) {
+            // no coupling: diagonal Hamiltonian, sorted (ties: adsorbate first)
+            const double h0 = ad.h[0], h1 = ad.h[1];
+            double q0 = 0.0, q1 = 0.0;
             int idx;
-            if (tid < M) {
-                lam = s.eps[tid];
-                idx = tid + (h0 <= lam) + (h1 <= lam);
+            if (r < M) {
+                lam = eps_s[r];
+                idx = r + (h0 <= lam) + (h1 <= lam);
             } else {
-                const double h = tid == M ? h0 : h1;
+                const double h = r == M ? h0 : h1;
                 int below = 0;
-                for (int k = 0; k < M; ++k) below += (s.eps[k] < h);
+                for (int k = 0; k < M; ++k) below += (eps_s[k] < h);
                 lam = h;
-                if (tid == M) {
+                if (r == M) {
                     idx = below + (h1 < h0);
                     q0 = 1.0;
                 } else {
@@ -220,99 +278,101 @@ __global__ void __launch_bounds__(256) k2_eigen(DevState s, Model2Dev md, double
             lam_s[idx] = lam;
             Q0_s[idx] = q0;
             Q1_s[idx] = q1;
-        }
-    } else {
-        const double c = sqrt(csq);
-        const double hp = (c0 * c0 * ad.h[0] + c1 * c1 * ad.h[1]) / csq;
-        const double hm = (c1 * c1 * ad.h[0] + c0 * c0 * ad.h[1]) / csq;
-        const double tt = c0 * c1 * (ad.h[1] - ad.h[0]) / csq;
-        const bool decoupled = !(tt * tt > 0.0);
-        if (tid == 0) {
-            int pos = 0;
-            for (int k = 0; k < M; ++k) pos += (s.eps[k] < hm);
-            s_pos = pos;
-        }
-        __syncthreads();
-        const int pos = s_pos;
-        const int P = decoupled ? M : M + 1;
-        for (int k = tid; k < M; k += blockDim.x) {
-            const int slot = (decoupled || k < pos) ? k : k + 1;
-            pole[slot] = s.eps[k];
-            wt[slot] = csq * (s.z0[k] * s.z0[k]);
-        }
-        if (!decoupled && tid == 0) {
-            pole[pos] = hm;
-            wt[pos] = tt * tt;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double z2 = 0.0;
-            for (int k = 0; k < P; ++k) z2 += wt[k];
-            s_Z2 = z2;
-        }
-        __syncthreads();
-        const int r = tid;
-        double lam = 0.0, qp = 0.0, qm = 0.0;
-        if (r <= P) {
-            int o;
-            double tau;
-            const Poles<double> pp = {P, pole, wt, nullptr, nullptr, nullptr};
-            secular_root<double>(r, pp, hp, s_Z2, mode == 1, guess, lam, qp, st, &o, &tau);
-            if (!decoupled) {
-                // lam - h_-: the exact offset when the origin pole is h_- itself
-                const double lmh = (o == pos) ? tau : (pole[o] - hm) + tau;
-                qm = tt * qp / lmh;
-            }
-        }
-        if (!decoupled) {
-            if (r < N) {
-                lam_s[r] = lam;
-                Q0_s[r] = (c0 * qp - c1 * qm) / c;
-                Q1_s[r] = (c1 * qp + c0 * qm) / c;
-            }
         } else {
-            // M + 1 roots of the |+> arrowhead plus the decoupled |-> at h_-
-            if (r <= M) lam_s[r] = lam;  // staging for the count below
-            __syncthreads();
-            int below = 0;
-            if (r == M + 1)
-                for (int k = 0; k <= M; ++k) below += (lam_s[k] < hm);
-            __syncthreads();
-            if (r <= M) {
-                const int idx = r + (lam >= hm);
-                lam_s[idx] = lam;
-                Q0_s[idx] = c0 * qp / c;
-                Q1_s[idx] = c1 * qp / c;
-            } else if (r == M + 1) {
-                lam_s[below] = hm;
-                // (-c_1, c_0) / c; a unit adsorbate vector (+) when one coupling vanishes
-                Q0_s[below] = c0 == 0.0 ? 1.0 : (c1 == 0.0 ? 0.0 : -c1 / c);
-                Q1_s[below] = c0 == 0.0 ? 0.0 : (c1 == 0.0 ? 1.0 : c0 / c);
+            const int P = cs == 1 ? M : M + 1;
+            // Z2 = sum of the pole weights: c^2 sum_k w_k (+ t^2)
+            const double Z2 = c * c * md.wsum + (cs == 0 ? tt * tt : 0.0);
+            if (r <= P) {
+                int o;
+                double tau;
+                // an extrapolation outside the root's pole gap falls back to the last root
+                const double glo = r > 0 ? pole[r - 1] : -INFINITY, ghi = r < P ? pole[r] : INFINITY;
+                if (!(guess > glo && guess < ghi)) guess = lam_old;
+                const Poles<double> pp = {P, pole, wt, nullptr, nullptr, nullptr};
+                secular_root<double>(r, pp, sl->hp, Z2, mode == 1, guess, lam, qp, st, &o, &tau);
+                if (cs == 0) {
+                    // lam - h_-: the exact offset when the origin pole is h_- itself
+                    const double lmh = (o == pos) ? tau : (pole[o] - hm) + tau;
+                    const double qm = tt * qp / lmh;
+                    lam_s[r] = lam;
+                    Q0_s[r] = (c0 * qp - c1 * qm) / c;
+                    Q1_s[r] = (c1 * qp + c0 * qm) / c;
+                } else {
+                    red[r] = lam;  // staged: the decoupled |-> is placed below
+                }
             }
         }
+        if (st) atomicOr(&s.status[t], st);
     }
-    if (st) atomicOr(&s.status[t], st);
     __syncthreads();
-    for (int i = tid; i < N; i += blockDim.x) {
-        s.lam[t * N + i] = lam_s[i];
-        s.q0[t * N + i] = Q0_s[i];
-        s.q2[t * N + i] = Q1_s[i];
-        if (mode == 0) s.lam_prev[t * N + i] = lam_s[i];  // no extrapolation at the first step
+    if (act && cs == 1) {
+        // M + 1 roots of the |+> arrowhead plus the decoupled |-> at h_-
+        if (r <= M) {
+            const int idx = r + (lam >= hm);
+            lam_s[idx] = lam;
+            Q0_s[idx] = c0 * qp / c;
+            Q1_s[idx] = c1 * qp / c;
+        } else {
+            int below = 0;
+            for (int k = 0; k <= M; ++k) below += (red[k] < hm);
+            lam_s[below] = hm;
+            // (-c_1, c_0) / c; a unit adsorbate vector (+) when one coupling vanishes
+            Q0_s[below] = c0 == 0.0 ? 1.0 : (c1 == 0.0 ? 0.0 : -c1 / c);
+            Q1_s[below] = c0 == 0.0 ? 0.0 : (c1 == 0.0 ? 1.0 : c0 / c);
+        }
     }
-    double S[2], U[2];
-    occ_sums(lam_s, Q0_s, Q1_s, s.occ + t * Ne, Ne, ad, red, S, U);
-    if (tid < 6) {
-        const double F = force2(md, ad, xs, tid, S, U);
-        double p = ps[tid];
+    __syncthreads();
+    // occupied sums S_a = sum Q_aj^2, U_a = sum Q_aj^2 (lam_j - h_a) by a
+    // fixed-order tree over the slot (thread a takes electron a)
+    if (inslot) {
+        double a2 = 0.0, b2 = 0.0, u0 = 0.0, u1 = 0.0;
+        if (act) {
+            s.lam[t * N + r] = lam_s[r];
+            s.q0[t * N + r] = Q0_s[r];
+            s.q2[t * N + r] = Q1_s[r];
+            if (mode == 0) s.lam_prev[t * N + r] = lam_s[r];  // no extrapolation at the first step
+            if (r < Ne) {
+                const int j = s.occ[t * Ne + r];
+                a2 = Q0_s[j] * Q0_s[j];
+                b2 = Q1_s[j] * Q1_s[j];
+                u0 = a2 * (lam_s[j] - ad.h[0]);
+                u1 = b2 * (lam_s[j] - ad.h[1]);
+            }
+        }
+        red[r] = a2;
+        red[Pw + r] = b2;
+        red[2 * Pw + r] = u0;
+        red[3 * Pw + r] = u1;
+        if (r < Pw - N) {
+            red[N + r] = 0.0;
+            red[Pw + N + r] = 0.0;
+            red[2 * Pw + N + r] = 0.0;
+            red[3 * Pw + N + r] = 0.0;
+        }
+    }
+    __syncthreads();
+    for (int w = Pw >> 1; w > 0; w >>= 1) {
+        if (inslot && r < w) {
+            red[r] += red[r + w];
+            red[Pw + r] += red[Pw + r + w];
+            red[2 * Pw + r] += red[2 * Pw + r + w];
+            red[3 * Pw + r] += red[3 * Pw + r + w];
+        }
+        __syncthreads();
+    }
+    if (act && r < 6) {
+        const double S[2] = {red[0], red[Pw]}, U[2] = {red[2 * Pw], red[3 * Pw]};
+        const double F = force2(md, ad, sl->x, r, S, U);
+        double p = sl->p[r];
         if (mode == 1) p += 0.5 * dt * F;
-        ps[tid] = p;
-        s.x[t * 6 + tid] = xs[tid];
-        s.p[t * 6 + tid] = p;
-        s.F[t * 6 + tid] = F;
-        if (mode == 0) s.vprev[t * 6 + tid] = p / md.mass;
+        s.x[t * 6 + r] = sl->x[r];
+        s.p[t * 6 + r] = p;
+        s.F[t * 6 + r] = F;
+        if (mode == 0) s.vprev[t * 6 + r] = p / md.mass;
+        sl->p[r] = p;
     }
     __syncthreads();
-    if (tid == 0) write_geo2(s, t, md, ad, ps);
+    if (act && r == 0) write_geo2(s, t, md, ad, sl->p);
 }
 
 // W[j N + k] = dt/2 (D0_jk + D1_jk), D_e = T^{v_e}_jk / (lam_k - lam_j) at
@@ -529,9 +589,12 @@ __global__ void __launch_bounds__(64) k2_accept(DevState s, Model2Dev md)
     }
 }
 
-constexpr int kEigen2MaxThreads = 256;
-
-size_t eigen2_smem(int N, int M) { return (size_t)(2 * (M + 1) + 3 * N + 32) * sizeof(double); }
+// Shared memory of k2_eigen with tpb slots.
+size_t eigen2_smem(int N, int M, int tpb)
+{
+    const int per = 2 * (M + 1) + 3 * N + 4 * eigen_pow2(N);
+    return (size_t)(M + tpb * per) * sizeof(double) + (size_t)tpb * sizeof(Eig2Slot);
+}
 
 }  // namespace
 
@@ -599,8 +662,10 @@ cudaError_t launch_eigen2(iesh2_ctx *ctx, double dt, int mode)
 {
     const DevState &d = ctx->ds;
     if (d.n == 0) return cudaSuccess;
-    const int threads = std::min(kEigen2MaxThreads, (d.N + 31) & ~31);
-    k2_eigen<<<(unsigned)d.n, threads, eigen2_smem(d.N, d.M), ctx->stream>>>(d, ctx->md, dt, mode);
+    const int tpb = eigen_tpb(d.N);
+    const int threads = (tpb * d.N + 31) & ~31;
+    const unsigned blocks = (unsigned)((d.n + tpb - 1) / tpb);
+    k2_eigen<<<blocks, threads, eigen2_smem(d.N, d.M, tpb), ctx->stream>>>(d, ctx->md, dt, mode, tpb);
     return cudaGetLastError();
 }
 
@@ -686,7 +751,11 @@ iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int precisio
     for (int i = 1; i < M; ++i)
         if (!(eps[i] > eps[i - 1])) return fail2(ctx, IESH_EINVAL, "bath energies must be distinct");
     std::vector<double> sq(M);
-    for (int i = 0; i < M; ++i) sq[i] = std::sqrt(w[i]);
+    k.wsum = 0.0;
+    for (int i = 0; i < M; ++i) {
+        sq[i] = std::sqrt(w[i]);
+        k.wsum += sq[i] * sq[i];
+    }
 
     DevState &d = ctx->ds;
     memset(&d, 0, sizeof d);
@@ -716,6 +785,9 @@ iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int precisio
     d.z0 = sq_d;
     configure_hop_smem();
     configure_cheb_tc();
+    // the slots of the eigen kernel can pass the 48 KiB default (N near 65)
+    CU2(cudaFuncSetAttribute(k2_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)eigen2_smem(N, M, eigen_tpb(N))));
     CU2(cudaMemcpyAsync(eps_d, eps.data(), M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CU2(cudaMemcpyAsync(sq_d, sq.data(), M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CU2(cudaStreamSynchronize(ctx->stream));
