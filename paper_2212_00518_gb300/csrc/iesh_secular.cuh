@@ -96,17 +96,24 @@ __device__ __forceinline__ double dfl_value(dfl a) { return (double)a.hi + (doub
 // Pole data of the secular sums.  diff (optional): FP64 table of the pole
 // differences diff[k M + o] = eps_o - eps_k; ddf, z2df (double-float mode):
 // the same differences and z_k^2 as double-float pairs.
+// Two-orbital double-float mode (EV_TWO_DF): the M poles are nb bath poles
+// with one extra pole h_- inserted at index hpos (hpos < 0: none); ddf is
+// the bath table [nb][nb], hdf[k] = h_- - eps_k as double-float pairs, and
+// z2df the weights of all M poles in sorted order.
 template <class R>
 struct Poles {
     int M;
     const R *__restrict__ eps, *__restrict__ z2, *__restrict__ diff;
     const float2 *__restrict__ ddf, *__restrict__ z2df;
+    int nb, hpos;
+    R hm;
+    const float2 *__restrict__ hdf;
 };
 
 // Evaluation modes of the secular sums: EV_PLAIN (eps_o - eps_k formed per
 // term), EV_TABLE (FP64 table), EV_DFLOAT (double-float sums on the FP32
 // pipe; the origin term and everything outside the sums stay FP64).
-enum { EV_PLAIN = 0, EV_TABLE = 1, EV_DFLOAT = 2 };
+enum { EV_PLAIN = 0, EV_TABLE = 1, EV_DFLOAT = 2, EV_TWO_DF = 3 };
 
 // ============================================================= eigenpairs
 // The one-electron Hamiltonian of Sec. II B is an arrowhead matrix:
@@ -149,6 +156,35 @@ __device__ __forceinline__ Sec<R> sec_eval(const Poles<R> &P, int o, R tau, R eo
         s1 = (R)dfl_value(d1);
         s2 = (R)dfl_value(d2);
         sa = (R)dfl_value(da);
+    } else if constexpr (EV == EV_TWO_DF) {
+        // bath poles in double-float from the bath table (origin a bath pole)
+        // or from hdf (origin h_-); the h_- term itself in R
+        const dfl td = dfl_from((double)tau);
+        const bool oh = o == P.hpos;
+        const int ob = oh ? 0 : ((P.hpos >= 0 && o > P.hpos) ? o - 1 : o);
+        dfl d1 = {0.f, 0.f}, d2 = {0.f, 0.f}, da = {0.f, 0.f};
+#pragma unroll 2
+        for (int k = 0; k < P.nb; ++k) {
+            const int q = (P.hpos >= 0 && k >= P.hpos) ? k + 1 : k;
+            const float2 dk = oh ? P.hdf[k] : P.ddf[(size_t)k * P.nb + ob], zk = P.z2df[q];
+            const dfl r = dfl_rcp(dfl_add({dk.x, dk.y}, td));  // 1 / (lam - eps_k)
+            const dfl qv = dfl_mul({zk.x, zk.y}, r);
+            if (q != o) {
+                d1 = dfl_add(d1, qv);
+                d2 = dfl_add(d2, dfl_mul(qv, r));
+                if (ABS) da = dfl_add(da, qv.hi < 0.f ? dfl{-qv.hi, -qv.lo} : qv);
+            }
+        }
+        s1 = (R)dfl_value(d1);
+        s2 = (R)dfl_value(d2);
+        sa = (R)dfl_value(da);
+        if (P.hpos >= 0 && !oh) {
+            const R r = pole_recip<R>((P.eps[o] - P.hm) + tau);
+            const R qv = P.z2[P.hpos] * r;
+            s1 += qv;
+            s2 = fma(qv, r, s2);
+            if (ABS) sa += fabs(qv);
+        }
     } else {
         const R eo = P.eps[o];
 #pragma unroll 4
@@ -184,7 +220,7 @@ __device__ bool sec_iterate(const Poles<R> &P, R h, int o, int kind, R D, R &lo,
                             Sec<R> &e, bool have)
 {
     // rounding unit of the sums: 2^-44 covers the double-float sums
-    const R u = EV == EV_DFLOAT ? R(5.684341886080802e-14) : Roundoff<R>::u;
+    const R u = (EV == EV_DFLOAT || EV == EV_TWO_DF) ? R(5.684341886080802e-14) : Roundoff<R>::u;
     const R eomh = P.eps[o] - h;
     const R s = P.z2[o];
     // the non-origin part of the error scale varies slowly with tau (those

@@ -24,9 +24,10 @@
 // F_y = -dU0/dy - sum_{j occupied} T^y_jj.
 //
 // Precision: FP64, or mixed (the one-coordinate model's split): FP64
-// eigenpairs, forces, hop probabilities and rescale; FP32 coefficients,
-// coupling generator, propagation (tensor cores where the trajectory fits
-// one CTA) and overlap LU.
+// eigenpairs (the secular sums over the bath poles in double-float),
+// forces, hop probabilities and rescale; FP32 coefficients, coupling
+// generator, propagation (tensor cores where the trajectory fits one CTA)
+// and overlap LU.
 //
 // One step (Sec. II B, II C in six dimensions):
 //   k2_eigen      kick + drift, eigenpairs, forces, second kick, the
@@ -165,7 +166,10 @@ struct Eig2Slot {
 // mode 0: eigenpairs and forces at x (state set-up).  mode 1: a step's
 // kick + drift, eigenpairs at the new x, forces and the second kick.
 // tpb trajectories per CTA (slots of N threads), one thread per root; every
-// barrier is reached by all threads of the CTA.
+// barrier is reached by all threads of the CTA.  DF: the secular sums over
+// the bath poles in double-float arithmetic (mixed path; the bath
+// differences from the context's table, those to h_- per trajectory).
+template <bool DF>
 __global__ void __launch_bounds__(512, 1) k2_eigen(DevState s, Model2Dev md, double dt, int mode, int tpb)
 {
     extern __shared__ double e2_sh[];
@@ -176,7 +180,7 @@ __global__ void __launch_bounds__(512, 1) k2_eigen(DevState s, Model2Dev md, dou
     const int64_t t = inslot ? traj_of(s, (int64_t)blockIdx.x * tpb + slot) : -1;
     const bool act = t >= 0 && !(s.status[t] & ST_DONE);
     const int Pw = eigen_pow2(N);                          // reduction width
-    const int per = 2 * (M + 1) + 3 * N + 4 * Pw;
+    const int per = 2 * (M + 1) + 3 * N + 4 * Pw + (DF ? 2 * M + 1 : 0);
     double *eps_s = e2_sh;                                 // [M] bath energies, shared
     double *pole = eps_s + M + (inslot ? slot : 0) * per;  // [M + 1] sorted poles
     double *wt = pole + (M + 1);                           // [M + 1] their weights
@@ -184,6 +188,8 @@ __global__ void __launch_bounds__(512, 1) k2_eigen(DevState s, Model2Dev md, dou
     double *Q0_s = lam_s + N;                              // [N]
     double *Q1_s = Q0_s + N;                               // [N]
     double *red = Q1_s + N;                                // [4][Pw] reductions / staging
+    float2 *z2df = reinterpret_cast<float2 *>(red + 4 * Pw);  // [M + 1] weights as double-float (DF)
+    float2 *hdf = z2df + (M + 1);                          // [M] h_- - eps_k as double-float (DF)
     Eig2Slot *sl = reinterpret_cast<Eig2Slot *>(e2_sh + M + tpb * per) + (inslot ? slot : 0);
     for (int k = threadIdx.x; k < M; k += blockDim.x) eps_s[k] = s.eps[k];
     // warm start: the previous roots extrapolated linearly (each thread reads
@@ -242,12 +248,25 @@ __global__ void __launch_bounds__(512, 1) k2_eigen(DevState s, Model2Dev md, dou
     if (act && cs != 2) {
         for (int k = r; k < M; k += N) {
             const int q = (cs == 1 || k < pos) ? k : k + 1;
+            const double w = (c0 * c0 + c1 * c1) * (s.z0[k] * s.z0[k]);
             pole[q] = eps_s[k];
-            wt[q] = (c0 * c0 + c1 * c1) * (s.z0[k] * s.z0[k]);
+            wt[q] = w;
+            if (DF) {
+                const dfl wd = dfl_from(w);
+                z2df[q] = make_float2(wd.hi, wd.lo);
+                if (cs == 0) {
+                    const dfl hd = dfl_from(hm - eps_s[k]);
+                    hdf[k] = make_float2(hd.hi, hd.lo);
+                }
+            }
         }
         if (cs == 0 && r == 0) {
             pole[pos] = hm;
             wt[pos] = tt * tt;
+            if (DF) {
+                const dfl wd = dfl_from(tt * tt);
+                z2df[pos] = make_float2(wd.hi, wd.lo);
+            }
         }
     }
     __syncthreads();
@@ -288,8 +307,13 @@ __global__ void __launch_bounds__(512, 1) k2_eigen(DevState s, Model2Dev md, dou
                 // an extrapolation outside the root's pole gap falls back to the last root
                 const double glo = r > 0 ? pole[r - 1] : -INFINITY, ghi = r < P ? pole[r] : INFINITY;
                 if (!(guess > glo && guess < ghi)) guess = lam_old;
-                const Poles<double> pp = {P, pole, wt, nullptr, nullptr, nullptr};
-                secular_root<double>(r, pp, sl->hp, Z2, mode == 1, guess, lam, qp, st, &o, &tau);
+                if (DF) {
+                    const Poles<double> pp = {P, pole, wt, nullptr, s.poledf, z2df, M, cs == 0 ? pos : -1, hm, hdf};
+                    secular_root<double, EV_TWO_DF>(r, pp, sl->hp, Z2, mode == 1, guess, lam, qp, st, &o, &tau);
+                } else {
+                    const Poles<double> pp = {P, pole, wt, nullptr, nullptr, nullptr};
+                    secular_root<double>(r, pp, sl->hp, Z2, mode == 1, guess, lam, qp, st, &o, &tau);
+                }
                 if (cs == 0) {
                     // lam - h_-: the exact offset when the origin pole is h_- itself
                     const double lmh = (o == pos) ? tau : (pole[o] - hm) + tau;
@@ -590,9 +614,9 @@ __global__ void __launch_bounds__(64) k2_accept(DevState s, Model2Dev md)
 }
 
 // Shared memory of k2_eigen with tpb slots.
-size_t eigen2_smem(int N, int M, int tpb)
+size_t eigen2_smem(int N, int M, int tpb, bool df)
 {
-    const int per = 2 * (M + 1) + 3 * N + 4 * eigen_pow2(N);
+    const int per = 2 * (M + 1) + 3 * N + 4 * eigen_pow2(N) + (df ? 2 * M + 1 : 0);
     return (size_t)(M + tpb * per) * sizeof(double) + (size_t)tpb * sizeof(Eig2Slot);
 }
 
@@ -665,7 +689,9 @@ cudaError_t launch_eigen2(iesh2_ctx *ctx, double dt, int mode)
     const int tpb = eigen_tpb(d.N);
     const int threads = (tpb * d.N + 31) & ~31;
     const unsigned blocks = (unsigned)((d.n + tpb - 1) / tpb);
-    k2_eigen<<<blocks, threads, eigen2_smem(d.N, d.M, tpb), ctx->stream>>>(d, ctx->md, dt, mode, tpb);
+    const size_t smem = eigen2_smem(d.N, d.M, tpb, ctx->mixed);
+    if (ctx->mixed) k2_eigen<true><<<blocks, threads, smem, ctx->stream>>>(d, ctx->md, dt, mode, tpb);
+    else k2_eigen<false><<<blocks, threads, smem, ctx->stream>>>(d, ctx->md, dt, mode, tpb);
     return cudaGetLastError();
 }
 
@@ -779,17 +805,35 @@ iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int precisio
     A2(d.scratch, T * (size_t)d.scratch_stride)
     A2(d.cheb, T * kChebStride)
     A2(eps_d, (size_t)M) A2(sq_d, (size_t)M)
+    float2 *poledf = nullptr;
+    if (ctx->mixed) A2(poledf, (size_t)M * M)
 #undef A2
     d.C = Cd;
     d.eps = eps_d;
     d.z0 = sq_d;
+    d.poledf = poledf;
+    d.eigen_dfloat = ctx->mixed ? 1 : 0;
     configure_hop_smem();
     configure_cheb_tc();
     // the slots of the eigen kernel can pass the 48 KiB default (N near 65)
-    CU2(cudaFuncSetAttribute(k2_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)eigen2_smem(N, M, eigen_tpb(N))));
+    CU2(cudaFuncSetAttribute(k2_eigen<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)eigen2_smem(N, M, eigen_tpb(N), false)));
+    CU2(cudaFuncSetAttribute(k2_eigen<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)eigen2_smem(N, M, eigen_tpb(N), true)));
     CU2(cudaMemcpyAsync(eps_d, eps.data(), M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CU2(cudaMemcpyAsync(sq_d, sq.data(), M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<float2> pf;
+    if (ctx->mixed) {
+        // bath pole differences eps_o - eps_k as double-float pairs, [k][o]
+        pf.resize((size_t)M * M);
+        for (int kk = 0; kk < M; ++kk)
+            for (int o = 0; o < M; ++o) {
+                const double v = eps[o] - eps[kk];
+                const float hi = (float)v;
+                pf[(size_t)kk * M + o] = make_float2(hi, (float)(v - (double)hi));
+            }
+        CU2(cudaMemcpyAsync(poledf, pf.data(), pf.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->stream));
+    }
     CU2(cudaStreamSynchronize(ctx->stream));
     return IESH_OK;
 }

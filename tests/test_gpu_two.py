@@ -170,6 +170,26 @@ def _mixed(P, md, x, p, occ, C):
     return ctx, C32.astype(np.complex128)
 
 
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_eigenpairs_and_forces(P, name):
+    """The mixed path's secular sums over the bath poles run in double-float
+    (about 48 bits): eigenvalues within 1e-12 of the band, components 1e-11,
+    forces 1e-10 relative."""
+    md = CASES[name]
+    n = 5
+    x, p, occ, C = W.two_orbital_state(md, n, 11)
+    ctx, _ = _mixed(P, md, x, p, occ, C)
+    ctx.run(2.0, 3, seed=1)  # warm-started roots as well
+    st = ctx.get_state()
+    lam, Q, F = ctx.eigen()
+    assert np.all(st["status"] == 0)
+    for t in range(n):
+        rl, rQ, _, rF = O.eigen2(md, st["x"][t], st["occ"][t])
+        assert np.abs(lam[t] - rl).max() <= 1e-12
+        assert np.abs(Q[t] - rQ[0:2]).max() <= 1e-11
+        assert np.abs(F[t] - rF).max() <= 1e-10 * max(1.0, np.abs(rF).max())
+
+
 @pytest.mark.parametrize("name", ["M12", "M40", "strong", "one_coupling"])
 def test_mixed_hop_probabilities(P, name):
     md = CASES[name]
