@@ -76,6 +76,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
+    // per-trajectory scalars in FP32, formed once (FP64 work costs every warp
+    // that issues it): 2 J_k, 1 / rho, sin c, cos c
+    __shared__ float s_cj[kChebMax], s_sc[3];
     const int64_t t = traj_of(s, t_base + blockIdx.x);
     if (t < 0 || (s.status[t] & ST_DONE)) return;  // uniform over the CTA
     const int N = s.N, Ne = s.Ne, Np = (N + 3) & ~3;
@@ -134,7 +137,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
     const double c = cb[0], rho = cb[1];
     const int K = (int)cb[2];
     const double *J = cb + 3;
-    const float inv_rho = (float)(rho > 0.0 ? 1.0 / rho : 0.0);
+    for (int q = tid; q <= K; q += kTcThreads) s_cj[q] = (float)(2.0 * J[q]);
+    if (tid == 0) {
+        double scd, ccd;
+        sincos(c, &scd, &ccd);
+        s_sc[0] = (float)(rho > 0.0 ? 1.0 / rho : 0.0);
+        s_sc[1] = (float)scd;
+        s_sc[2] = (float)ccd;
+    }
     float2 *C = reinterpret_cast<float2 *>(s.C) + (int64_t)t * Ne * N;
     const float Lc = rowok ? (float)(0.5 * dt * (s.lam_prev[t * N + j] + s.lam[t * N + j]) - c) : 0.0f;
     const float J0 = (float)J[0];
@@ -178,6 +188,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
     const uint32_t aHi = tc::smem_addr(Ahi), aLo = tc::smem_addr(Alo);
     const uint32_t bHi = tc::smem_addr(Bhi), bLo = tc::smem_addr(Blo);
     const uint32_t my_lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    const float inv_rho = s_sc[0];  // written before the barrier above
 
     bool ok = true;
     for (int k = 0; k < K; ++k) {
@@ -200,7 +211,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
             break;
         }
         tc::fence_after_sync();
-        const float cj = (float)(2.0 * J[k + 1]);
+        const float cj = s_cj[k + 1];
         const int ph = (k + 1) & 3;  // (-i)^(k+1)
         const bool first = k == 0;
         // D entries in flight four chunks at a time, one wait per group
@@ -271,9 +282,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
         tc::mbar_wait(&mbar, 0u, kTcWaitLimit);
         tc::mbar_wait(&mbar, 1u, kTcWaitLimit);
     } else if (rowok) {
-        double scd, ccd;
-        sincos(c, &scd, &ccd);
-        const float sc = (float)scd, cc = (float)ccd;
+        const float sc = s_sc[1], cc = s_sc[2];
 #pragma unroll
         for (int ch = 0; ch < kTcMaxChunks; ++ch)
 #pragma unroll

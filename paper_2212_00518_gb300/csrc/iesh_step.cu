@@ -493,7 +493,17 @@ __global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int
     const double c = cb[0], rho = cb[1];
     const int K = (int)cb[2];
     const double *J = cb + 3;
-    const float inv_rho = (float)(rho > 0.0 ? 1.0 / rho : 0.0);
+    // per-trajectory scalars in FP32, formed once (FP64 work costs every warp
+    // that issues it): 2 J_k, 1 / rho, sin c, cos c
+    __shared__ float s_cj[kChebMax], s_sc[3];
+    for (int q = threadIdx.x; q <= K; q += blockDim.x) s_cj[q] = (float)(2.0 * J[q]);
+    if (threadIdx.x == 0) {
+        double scd, ccd;
+        sincos(c, &scd, &ccd);
+        s_sc[0] = (float)(rho > 0.0 ? 1.0 / rho : 0.0);
+        s_sc[1] = (float)scd;
+        s_sc[2] = (float)ccd;
+    }
     const float *__restrict__ W = reinterpret_cast<const float *>(s.scratch + t * s.scratch_stride);
     float2 *C = reinterpret_cast<float2 *>(s.C) + (int64_t)t * Ne * N;
     float Lc[RQ], acc[RQ][NR];
@@ -520,6 +530,7 @@ __global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int
         }
     }
     __syncthreads();
+    const float inv_rho = s_sc[0];
     for (int k = 0; k < K; ++k) {
         const float *cur = (k & 1) ? buf1 : buf0;  // t_k
         float *nxt = (k & 1) ? buf0 : buf1;        // t_(k-1), becomes t_(k+1)
@@ -550,7 +561,7 @@ __global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int
 #pragma unroll
                     for (int q = 0; q < NR; ++q) y[r][q] = fmaf(wr[r], tv[q], y[r][q]);
             }
-            const float cj = (float)(2.0 * J[k + 1]);
+            const float cj = s_cj[k + 1];
             const int ph = (k + 1) & 3;  // (-i)^(k+1)
 #pragma unroll
             for (int r = 0; r < RQ; ++r) {
@@ -607,9 +618,7 @@ __global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int
         __syncthreads();
     }
     if (act) {
-        double scd, ccd;
-        sincos(c, &scd, &ccd);
-        const float sc = (float)scd, cc = (float)ccd;
+        const float sc = s_sc[1], cc = s_sc[2];
 #pragma unroll
         for (int r = 0; r < RQ; ++r) {
             const int j = j0 + r;
