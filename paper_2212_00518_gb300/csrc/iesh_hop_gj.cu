@@ -1,0 +1,252 @@
+// iesh_hop_gj.cu -- hop probabilities of the mixed-precision path by
+// Gauss-Jordan column elimination in registers (N <= 128, Ne <= 56).
+//
+// The candidate that puts orbital m in slot a has amplitude det S *
+// R_{m a}, R = C_u S^{-1} (Sec. II B, determinant ratios).  Right-multiplying
+// the N x Ne matrix Z = C^T (Z_{o e} = C_e(o): the rows of the occupied
+// orbitals form S, the others C_u) by S^{-1} turns the S rows into the
+// identity and leaves R in the unoccupied rows.  This is done by column
+// operations: step i takes slot i's orbital s_i as the pivot row, chooses
+// the pivot column j among the columns not chosen yet by the largest
+// |Z_{s_i j}| (partial pivoting), scales column j by 1 / Z_{s_i j} and
+// subtracts Z_{s_i c} times the scaled column from every other column c.
+// After the Ne steps column j(i) belongs to slot i: R_{m i} = Z_{m j(i)}.
+//
+// Compared with an LU of S and two triangular solves per unoccupied orbital
+// this does about twice the arithmetic, but every step is the same rank-one
+// update of a register-resident matrix: 256 threads, thread (tr, tc) =
+// (tid / 8, tid % 8) holds Z_{rc} for r = tr + 32 k (k < 4) and c = tc + 8 q
+// (q < 7); the zero padding beyond N and Ne stays zero under every update.
+// Per step the 8 lanes that hold the pivot row choose the pivot with a
+// shuffle reduction, the scaled pivot column and the pivot row pass through
+// shared memory, and every thread updates its 28 entries.  FP32 throughout
+// (the coefficients are FP32 in the mixed path), the couplings d_{m, s_a}
+// included: their numerators from lam - h rounded once from FP64, their
+// eigenvalue gaps from double-float (hi, lo) eigenvalues, so nearly
+// degenerate pairs keep FP32 relative accuracy.  The selection and the
+// rescale are FP64 as in k_hop.  The skip bound of
+// Sec. II C saves no work here (the elimination is the ratio solve) and is
+// not applied; hop decisions are the same either way.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "iesh_common.cuh"
+#include "iesh_hop.cuh"
+#include "iesh_kernels.h"
+
+namespace iesh {
+
+namespace {
+
+constexpr int kGjThreads = 256, kGjTR = 32, kGjTC = 8, kGjRPT = 4, kGjCPT = 7;
+constexpr int kGjMaxN = kGjTR * kGjRPT;   // 128 orbitals
+constexpr int kGjMaxNe = kGjTC * kGjCPT;  // 56 electrons
+
+// z[k][q] for a CTA-uniform k (or q): a uniform switch, so the register
+// array is never indexed at run time.
+__device__ __forceinline__ float2 pick_row(const float2 (&z)[kGjRPT][kGjCPT], int k, int q)
+{
+    switch (k) {
+    case 0: return z[0][q];
+    case 1: return z[1][q];
+    case 2: return z[2][q];
+    default: return z[3][q];
+    }
+}
+__device__ __forceinline__ float2 pick_col(const float2 (&z)[kGjRPT][kGjCPT], int k, int q)
+{
+    switch (q) {
+    case 0: return z[k][0];
+    case 1: return z[k][1];
+    case 2: return z[k][2];
+    case 3: return z[k][3];
+    case 4: return z[k][4];
+    case 5: return z[k][5];
+    default: return z[k][6];
+    }
+}
+static_assert(kGjRPT == 4 && kGjCPT == 7, "pick_row / pick_col cover 4 x 7 register tiles");
+
+template <bool EXT>
+__global__ void __launch_bounds__(kGjThreads, 2) k_hop_gj(DevState s, double dt, double mass, uint64_t seed,
+                                                          double *g_out)
+{
+    const int64_t t = traj_of(s, blockIdx.x);
+    if (t < 0 || (s.status[t] & ST_DONE)) return;
+    const int N = s.N, Ne = s.Ne;
+    const int tid = threadIdx.x, tr = tid >> 3, tc = tid & 7;
+    __shared__ float2 colbuf[kGjMaxN], rowbuf[kGjMaxNe];
+    __shared__ double lam_s[kGjMaxN], q0_s[kGjMaxN], red[64];
+    __shared__ int occ_s[kGjMaxNe], slot_of[kGjMaxNe], isocc[kGjMaxN], unocc[kGjMaxN];
+    __shared__ int s_j, s_hop_a, s_hop_m;
+    __shared__ float2 s_pv;
+    // FP32 coupling data: adsorbate components, lam - h_a, lam as (hi, lo)
+    __shared__ float qa_s[kGjMaxN], qb_s[EXT ? kGjMaxN : 1], ma_s[kGjMaxN], mb_s[EXT ? kGjMaxN : 1];
+    __shared__ float2 ld_s[kGjMaxN];
+    const double *gv = EXT ? s.geo2 + t * 8 : s.geo + t * 4;  // h, h', kappa (EXT: h_0, h_1, projections)
+
+    for (int i = tid; i < N; i += kGjThreads) {
+        const double l = s.lam[t * N + i], qa = s.q0[t * N + i];
+        lam_s[i] = l;
+        q0_s[i] = qa;
+        qa_s[i] = (float)qa;
+        ma_s[i] = (float)(l - gv[0]);
+        const float lh = (float)l;
+        ld_s[i] = make_float2(lh, (float)(l - (double)lh));
+        if constexpr (EXT) {
+            qb_s[i] = (float)s.q2[t * N + i];
+            mb_s[i] = (float)(l - gv[1]);
+        }
+        isocc[i] = 0;
+    }
+    if (tid == 0) {
+        s_hop_a = -1;
+        s_hop_m = -1;
+    }
+    __syncthreads();
+    for (int a = tid; a < Ne; a += kGjThreads) {
+        occ_s[a] = s.occ[t * Ne + a];
+        isocc[occ_s[a]] = 1;
+    }
+    const float2 *Ct = reinterpret_cast<const float2 *>(s.C) + (int64_t)t * Ne * N;
+    float2 z[kGjRPT][kGjCPT];
+#pragma unroll
+    for (int k = 0; k < kGjRPT; ++k)
+#pragma unroll
+        for (int q = 0; q < kGjCPT; ++q) {
+            const int r = tr + kGjTR * k, c = tc + kGjTC * q;
+            z[k][q] = (r < N && c < Ne) ? Ct[(int64_t)c * N + r] : make_float2(0.f, 0.f);
+        }
+    __syncthreads();
+    if (tid == 0) {
+        int u = 0;
+        for (int m = 0; m < N; ++m)
+            if (!isocc[m]) unocc[u++] = m;
+    }
+
+    // ---- elimination
+    unsigned used = 0;  // bit q: my column tc + 8 q is a pivot column already
+    bool singular = false;
+    for (int i = 0; i < Ne; ++i) {
+        const int p = occ_s[i], trp = p & (kGjTR - 1), kp = p / kGjTR;
+        if (tr == trp) {  // the 8 lanes holding row p (one aligned group of a warp)
+            int bk = -1, bc = kGjMaxNe;
+            float2 bv = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < kGjCPT; ++q) {
+                const float2 v = pick_row(z, kp, q);
+                const int key = ((used >> q) & 1u) ? -1 : pivot_key(v);
+                if (key > bk) {  // ascending columns: ties keep the lower one
+                    bk = key;
+                    bc = tc + kGjTC * q;
+                    bv = v;
+                }
+            }
+            const unsigned grp = 0xFFu << ((tid & 31) & ~7);
+#pragma unroll
+            for (int o = 1; o < kGjTC; o <<= 1) {
+                const int ok = __shfl_xor_sync(grp, bk, o), oc = __shfl_xor_sync(grp, bc, o);
+                const float ox = __shfl_xor_sync(grp, bv.x, o), oy = __shfl_xor_sync(grp, bv.y, o);
+                if (ok > bk || (ok == bk && oc < bc)) {
+                    bk = ok;
+                    bc = oc;
+                    bv = make_float2(ox, oy);
+                }
+            }
+            if (tc == 0) {
+                s_j = bk > 0 ? bc : -1;  // key 0: the row of S is zero in every free column
+                s_pv = bv;
+            }
+        }
+        __syncthreads();
+        const int j = s_j;
+        if (j < 0) {  // uniform: every thread read the same s_j
+            singular = true;
+            break;
+        }
+        const float2 pv = s_pv;
+        const int qj = j / kGjTC;
+        if (tc == (j & (kGjTC - 1))) {
+            const float2 pinv = crcp(pv);
+#pragma unroll
+            for (int k = 0; k < kGjRPT; ++k) colbuf[tr + kGjTR * k] = cmul(pick_col(z, k, qj), pinv);
+            used |= 1u << qj;
+        }
+        if (tr == trp) {
+#pragma unroll
+            for (int q = 0; q < kGjCPT; ++q) {
+                float2 v = pick_row(z, kp, q);
+                // the pivot column itself: z - (pv - 1) z / pv = z / pv
+                if (tc + kGjTC * q == j) v = make_float2(pv.x - 1.f, pv.y);
+                rowbuf[tc + kGjTC * q] = v;
+            }
+        }
+        if (tid == 0) slot_of[j] = i;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kGjRPT; ++k) {
+            const float2 cb = colbuf[tr + kGjTR * k];
+#pragma unroll
+            for (int q = 0; q < kGjCPT; ++q) z[k][q] = cfms(z[k][q], rowbuf[tc + kGjTC * q], cb);
+        }
+    }
+    if (singular && tid == 0) atomicOr(&s.status[t], ST_SINGULAR);
+
+    // ---- probabilities g_{a->m} = max(0, -2 dt v Re(R_ma) d_{m, s_a})
+    const double v = EXT ? 1.0 : s.p[t] / mass;  // the six-coordinate coupling carries its velocity
+    const double geo_h = gv[0], geo_dh = gv[1], geo_k = gv[2];
+    const float fac = (float)(-2.0 * dt * v);
+    // numerator factors: h' + kappa (.) (EXT: the two orbitals' projections)
+    const float ha = (float)(EXT ? gv[2] : gv[1]), ka = (float)(EXT ? gv[4] : gv[2]);
+    const float hb = (float)(EXT ? gv[3] : 0.0), kb = (float)(EXT ? gv[5] : 0.0);
+    double *scr = s.scratch + t * s.scratch_stride;
+    double *G = g_out ? g_out + (int64_t)t * Ne * N : scr + 2 * (int64_t)Ne * N;  // [Ne][N]
+    if (!singular) {
+#pragma unroll
+        for (int k = 0; k < kGjRPT; ++k) {
+            const int m = tr + kGjTR * k;
+            if (m < N && !isocc[m]) {
+#pragma unroll
+                for (int q = 0; q < kGjCPT; ++q) {
+                    const int c = tc + kGjTC * q;
+                    if (c < Ne) {
+                        const int a = slot_of[c], sa = occ_s[a];
+                        // T_{m s_a} (times v for EXT) and lam_{s_a} - lam_m in FP32
+                        float T = qa_s[m] * qa_s[sa] * fmaf(ka, ma_s[m] + ma_s[sa], ha);
+                        if constexpr (EXT) T = fmaf(qb_s[m] * qb_s[sa], fmaf(kb, mb_s[m] + mb_s[sa], hb), T);
+                        const float2 lm = ld_s[m], ls = ld_s[sa];
+                        const float gap = (ls.x - lm.x) + (ls.y - lm.y);
+                        const float gam = fac * z[k][q].x * (T / gap);
+                        G[(int64_t)a * N + m] = gam > 0.f ? (double)gam : 0.0;
+                    }
+                }
+            }
+        }
+        if (g_out)
+            for (int idx = tid; idx < Ne * Ne; idx += kGjThreads) G[(int64_t)(idx / Ne) * N + occ_s[idx % Ne]] = 0.0;
+    } else if (g_out) {
+        for (int idx = tid; idx < Ne * N; idx += kGjThreads) G[idx] = 0.0;
+    }
+    __syncthreads();
+    if (g_out) return;
+    const U4 rn = draw(seed, (uint32_t)t, kStreamHop, (uint64_t)s.nstep[t]);
+    const double zeta = u53(rn.v[0], rn.v[1]);
+    hop_finish<float2, EXT>(s, t, mass, zeta, !singular, G, red, scr, unocc, occ_s, lam_s, q0_s, geo_h, geo_dh,
+                            geo_k, s_hop_a, s_hop_m, Ct);
+}
+
+}  // namespace
+
+bool hop_gj_eligible(int N, int Ne) { return N <= kGjMaxN && Ne <= kGjMaxNe && Ne < N; }
+
+cudaError_t launch_hop_gj(const DevState &s, double dt, double mass, uint64_t seed, double *g_out,
+                          cudaStream_t st, bool ext)
+{
+    if (s.n == 0) return cudaSuccess;
+    if (!hop_gj_eligible(s.N, s.Ne)) return cudaErrorInvalidValue;
+    if (ext) k_hop_gj<true><<<(unsigned)s.n, kGjThreads, 0, st>>>(s, dt, mass, seed, g_out);
+    else k_hop_gj<false><<<(unsigned)s.n, kGjThreads, 0, st>>>(s, dt, mass, seed, g_out);
+    return cudaGetLastError();
+}
+
+}  // namespace iesh

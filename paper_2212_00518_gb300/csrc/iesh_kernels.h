@@ -25,6 +25,11 @@ cudaError_t launch_unit_coeffs(const DevState &s, bool fp32, cudaStream_t st);
 cudaError_t launch_compact(const DevState &s, int32_t *live, int32_t *n_live, cudaStream_t st);
 cudaError_t launch_live_init(int64_t n, int32_t *live, int32_t *n_live, cudaStream_t st);
 void configure_hop_smem();
+// mixed-path hop probabilities by Gauss-Jordan elimination in registers
+// (N <= 128, Ne <= 56)
+bool hop_gj_eligible(int N, int Ne);
+cudaError_t launch_hop_gj(const DevState &s, double dt, double mass, uint64_t seed, double *g_out,
+                          cudaStream_t st, bool ext);
 // Bath of one lead: energies and weights (Gauss-Legendre split at mu, or trapezoid)
 void lead_bath(int disc, int n, double a, double b, double mu, int n_lo, std::vector<double> &eps,
                std::vector<double> &w);

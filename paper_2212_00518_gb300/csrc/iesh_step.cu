@@ -17,6 +17,7 @@
 #include "iesh_kernels.h"
 #include "iesh_secular.cuh"
 #include "iesh_cheb.cuh"
+#include "iesh_hop.cuh"
 
 namespace iesh {
 
@@ -199,15 +200,6 @@ __global__ void k_force(DevState s)
 }
 
 // ============================================================ couplings
-// d_jk = <j|d_x k> = T_jk / (lam_k - lam_j) with the closed form of
-// T = Q^T (dH/dx) Q for the arrowhead: T_jk = q0_j q0_k [h' + kappa
-// (lam_j + lam_k - 2h)], kappa = f'/f (all couplings share f(x)).
-__device__ __forceinline__ double nac(double lj, double qj, double lk, double qk, double h,
-                                      double dh, double kap)
-{
-    return qj * qk * (dh + kap * (lj + lk - 2.0 * h)) * pole_recip<double>(lk - lj);
-}
-
 __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double mass, double tol)
 {
     extern __shared__ double sh[];
@@ -668,53 +660,6 @@ void cheb32_shape(int N, int Ne, int &G)
 // warps); per column it scales its rows, updates them, and records the
 // largest candidate of the next column, so one block barrier per column
 // suffices.  Complex products are written as explicit FMAs.
-__device__ __forceinline__ double2 cmul(double2 a, double2 b)
-{
-    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 cfms(double2 acc, double2 a, double2 b)  // acc - a b
-{
-    return make_double2(fma(-a.x, b.x, fma(a.y, b.y, acc.x)), fma(-a.x, b.y, fma(-a.y, b.x, acc.y)));
-}
-__device__ __forceinline__ double2 crcp(double2 a)
-{
-    const double m = fma(a.x, a.x, a.y * a.y);
-    const double d = m >= 2.2250738585072014e-308 ? pole_recip<double>(m) : 1.0 / m;
-    return make_double2(a.x * d, -a.y * d);
-}
-// Pivot key of a complex entry: max(|re|, |im|) to 20 mantissa bits, from
-// the high words of the doubles (integer ops: the FP64 pipe is the
-// bottleneck of the factorisation).  Monotonic in the magnitude; 0 only for
-// zero (or below 2^-1042) entries; -1 marks "no candidate".
-__device__ __forceinline__ int pivot_key(double2 v)
-{
-    const int a = __double2hiint(v.x) & 0x7fffffff, b = __double2hiint(v.y) & 0x7fffffff;
-    return a > b ? a : b;
-}
-__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
-__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
-__device__ __forceinline__ float2 cmulf(float2 a, float2 b)
-{
-    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ float2 cfmsf(float2 acc, float2 a, float2 b)  // acc - a b
-{
-    return make_float2(fmaf(-a.x, b.x, fmaf(a.y, b.y, acc.x)), fmaf(-a.x, b.y, fmaf(-a.y, b.x, acc.y)));
-}
-// FP32 factorisation (mixed path): the same operations in single precision.
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) { return cmulf(a, b); }
-__device__ __forceinline__ float2 cfms(float2 acc, float2 a, float2 b) { return cfmsf(acc, a, b); }
-__device__ __forceinline__ float2 crcp(float2 a)
-{
-    const float d = 1.0f / fmaf(a.x, a.x, a.y * a.y);
-    return make_float2(a.x * d, -a.y * d);
-}
-__device__ __forceinline__ int pivot_key(float2 v)  // max(|re|, |im|), monotonic
-{
-    const int a = __float_as_int(v.x) & 0x7fffffff, b = __float_as_int(v.y) & 0x7fffffff;
-    return a > b ? a : b;
-}
-
 // Bytes of the matrix region: S / LU in FP64; in the mixed path the FP32
 // factors followed by one pass of FP32 substitution rows (at most 128
 // quad-lane groups).
@@ -1073,113 +1018,8 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
     __syncthreads();
     if (g_out) return;
 
-    // ---- stochastic selection in the order (slot a ascending, m ascending)
-    if (do_ratios) {
-        double *slot_sum = (Ne <= 64) ? red : scr + 3 * (int64_t)Ne * N;
-        for (int a = threadIdx.x; a < Ne; a += blockDim.x) {
-            double sa = 0.0;
-            for (int u = 0; u < nu; ++u) sa += G[(int64_t)a * N + unocc[u]];
-            slot_sum[a] = sa;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double cum = 0.0;
-            int a_hit = -1;
-            for (int a = 0; a < Ne; ++a) {
-                if (cum + slot_sum[a] > zeta) {
-                    a_hit = a;
-                    break;
-                }
-                cum += slot_sum[a];
-            }
-            if (a_hit >= 0) {
-                for (int u = 0; u < nu; ++u) {
-                    cum += G[(int64_t)a_hit * N + unocc[u]];
-                    if (cum > zeta) {
-                        s_hop_a = a_hit;
-                        s_hop_m = unocc[u];
-                        break;
-                    }
-                }
-            }
-        }
-        __syncthreads();
-    }
-
-    if constexpr (EXT) {  // rescale and bookkeeping in the six-coordinate acceptance kernel
-        if (threadIdx.x == 0) s.hop_pair[t] = s_hop_a >= 0 ? s_hop_a * N + s_hop_m : -1;
-        return;
-    }
-    // ---- hop, rescale, force, counters (thread 0)
-    if (threadIdx.x == 0) {
-        double p = s.p[t];
-        if (s_hop_a >= 0) {
-            const int a = s_hop_a, m = s_hop_m;
-            const double dE = lam_s[m] - lam_s[occ_s[a]];
-            const double p2 = p * p - 2.0 * mass * dE;
-            if (p2 >= 0.0) {
-                p = (p >= 0.0 ? 1.0 : -1.0) * sqrt(p2);
-                // replace s_a by m and keep the list sorted
-                int b = a;
-                occ_s[b] = m;
-                while (b > 0 && occ_s[b - 1] > occ_s[b]) {
-                    const int tmp = occ_s[b - 1];
-                    occ_s[b - 1] = occ_s[b];
-                    occ_s[b] = tmp;
-                    --b;
-                }
-                while (b < Ne - 1 && occ_s[b + 1] < occ_s[b]) {
-                    const int tmp = occ_s[b + 1];
-                    occ_s[b + 1] = occ_s[b];
-                    occ_s[b] = tmp;
-                    ++b;
-                }
-                for (int q = 0; q < Ne; ++q) s.occ[t * Ne + q] = (int16_t)occ_s[q];
-                double F = -s.dU0[t];
-                for (int q = 0; q < Ne; ++q) {
-                    const int i = occ_s[q];
-                    F -= q0_s[i] * q0_s[i] * (geo_dh + 2.0 * geo_k * (lam_s[i] - geo_h));
-                }
-                s.F[t] = F;
-                s.p[t] = p;
-                s.hops[t] += 1;
-            } else {
-                s.frus[t] += 1;
-            }
-        }
-        s.vprev[t] = p / mass;
-        const int64_t ns = s.nstep[t] + 1;
-        s.nstep[t] = ns;
-        if (s.z_done > 0.0 && s.x[t] > s.z_done) atomicOr(&s.status[t], ST_DONE);
-    }
-    // ---- observables
-    if (s.record_every > 0) {
-        __syncthreads();
-        const int64_t ns = s.nstep[t];
-        if (ns % s.record_every == 0) {
-            const int64_t r = ns / s.record_every - 1;
-            if (r < s.max_records) {
-                double psh = 0.0, pwf = 0.0;
-                for (int a = threadIdx.x; a < Ne; a += blockDim.x) {
-                    const double q = q0_s[occ_s[a]];
-                    psh += q * q;
-                    double ar = 0.0, ai = 0.0;
-                    for (int i = 0; i < N; ++i) {
-                        const double2 cv = to_d2(Ct[(int64_t)a * N + i]);
-                        ar = fma(q0_s[i], cv.x, ar);
-                        ai = fma(q0_s[i], cv.y, ai);
-                    }
-                    pwf += ar * ar + ai * ai;
-                }
-                psh = block_sum(psh, red);
-                pwf = block_sum(pwf, red);
-                if (threadIdx.x == 0) {
-                    s.rec_sh[r * s.n + t] = psh;
-                    s.rec_wf[r * s.n + t] = pwf;
-                }
-            }
-        }
-    }
+    hop_finish<CT, EXT>(s, t, mass, zeta, do_ratios, G, red, scr, unocc, occ_s, lam_s, q0_s, geo_h, geo_dh,
+                        geo_k, s_hop_a, s_hop_m, Ct);
 }
 
 // ========================================================== work list
@@ -1460,6 +1300,10 @@ cudaError_t launch_hop(const DevState &s, double dt, double mass, uint64_t seed,
                        double *g_out, cudaStream_t st, bool mixed, bool ext)
 {
     if (s.n == 0) return cudaSuccess;
+    // mixed path: the register-resident Gauss-Jordan kernel where it fits,
+    // unless a hop CTA size was requested
+    if (mixed && s.hop_threads == 0 && hop_gj_eligible(s.N, s.Ne))
+        return launch_hop_gj(s, dt, mass, seed, g_out, st, ext);
     const size_t smem = hop_smem_bytes(s.N, s.Ne, mixed, ext);
     // 256-thread CTAs (three per SM) when two or more fit in shared memory,
     // else one CTA of 512

@@ -4,11 +4,14 @@ Times candidate shapes of the Chebyshev propagator (electrons per thread x
 column groups per CTA) and of the hop kernel (threads per CTA) on a scratch
 context with the same model, precision and batch size, from the caller's
 state, and sets the fastest on the context.  Results do not depend on the
-shape (every output keeps its summation order), so tuning only changes
-speed.  A mixed-precision context whose default propagator is the
-tensor-core kernel keeps it (its arithmetic differs from the SIMT shapes);
-only the hop kernel is tuned then.  Choices are cached per (N, Ne,
-precision, batch size) in-process.
+propagator shape (every output keeps its summation order).  A
+mixed-precision context whose default propagator is the tensor-core kernel
+keeps it (its arithmetic differs from the SIMT shapes); only the hop kernel
+is tuned then.  The hop candidates are the built-in choice (0: in the mixed
+path the register-resident Gauss-Jordan kernel where it fits) and LU CTAs
+of 256 or 512 threads; the mixed path's two hop algorithms round the FP32
+ratios differently (hop probabilities agree to about 1e-7 relative).
+Choices are cached per (N, Ne, precision, batch size) in-process.
 """
 import numpy as np
 
@@ -81,7 +84,7 @@ def autotune(ctx, x, p, occ, C, dt, steps=3, seed=0):
     cands = [default] if default[0] == 8 else cheb_candidates(ctx.N, ctx.Ne, precision=ctx.precision)
     for ept, G in cands:
         times_cheb[(ept, G)] = trial(ept, G, 0)[0]
-    for hop in (256, 512):
+    for hop in (0, 256, 512):
         ept, G = min(times_cheb, key=times_cheb.get)
         times_hop[hop] = trial(ept, G, hop)[1]
     torch.cuda.synchronize()
