@@ -18,8 +18,9 @@
 // (tid / 8, tid % 8) holds Z_{rc} for r = tr + 32 k (k < 4) and c = tc + 8 q
 // (q < 7); the zero padding beyond N and Ne stays zero under every update.
 // Per step the 8 lanes that hold the pivot row choose the pivot with a
-// shuffle reduction, the scaled pivot column and the pivot row pass through
-// shared memory, and every thread updates its 28 entries.  FP32 throughout
+// shuffle reduction and publish the pivot row through shared memory, each
+// thread takes the pivot column's entries of its rows by a shuffle within its
+// warp, and every thread updates its 28 entries: one barrier per step.  FP32 throughout
 // (the coefficients are FP32 in the mixed path), the couplings d_{m, s_a}
 // included: their numerators from lam - h rounded once from FP64, their
 // eigenvalue gaps from double-float (hi, lo) eigenvalues, so nearly
@@ -75,11 +76,11 @@ __global__ void __launch_bounds__(kGjThreads, 2) k_hop_gj(DevState s, double dt,
     if (t < 0 || (s.status[t] & ST_DONE)) return;
     const int N = s.N, Ne = s.Ne;
     const int tid = threadIdx.x, tr = tid >> 3, tc = tid & 7;
-    __shared__ float2 colbuf[kGjMaxN], rowbuf[kGjMaxNe];
+    __shared__ float2 rowbuf[2][kGjMaxNe];
     __shared__ double lam_s[kGjMaxN], q0_s[kGjMaxN], red[64];
     __shared__ int occ_s[kGjMaxNe], slot_of[kGjMaxNe], isocc[kGjMaxN], unocc[kGjMaxN];
-    __shared__ int s_j, s_hop_a, s_hop_m;
-    __shared__ float2 s_pv;
+    __shared__ int s_j[2], s_hop_a, s_hop_m;
+    __shared__ float2 s_pv[2];
     // FP32 coupling data: adsorbate components, lam - h_a, lam as (hi, lo)
     __shared__ float qa_s[kGjMaxN], qb_s[EXT ? kGjMaxN : 1], ma_s[kGjMaxN], mb_s[EXT ? kGjMaxN : 1];
     __shared__ float2 ld_s[kGjMaxN];
@@ -124,71 +125,79 @@ __global__ void __launch_bounds__(kGjThreads, 2) k_hop_gj(DevState s, double dt,
             if (!isocc[m]) unocc[u++] = m;
     }
 
-    // ---- elimination
+    // ---- elimination: one barrier per step.  The 8 lanes holding the next
+    // pivot row choose its pivot right after their own update and publish
+    // the pivot and the row (double-buffered); every thread takes column j
+    // of its rows from the lane of its row class that holds it (a shuffle).
     unsigned used = 0;  // bit q: my column tc + 8 q is a pivot column already
     bool singular = false;
-    for (int i = 0; i < Ne; ++i) {
-        const int p = occ_s[i], trp = p & (kGjTR - 1), kp = p / kGjTR;
-        if (tr == trp) {  // the 8 lanes holding row p (one aligned group of a warp)
-            int bk = -1, bc = kGjMaxNe;
-            float2 bv = make_float2(0.f, 0.f);
+    auto search = [&](int i) {
+        const int p = occ_s[i], kp = p / kGjTR;
+        if (tr != (p & (kGjTR - 1))) return;  // the 8 lanes holding row p (an aligned group)
+        int bk = -1, bc = kGjMaxNe;
+        float2 bv = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int q = 0; q < kGjCPT; ++q) {
-                const float2 v = pick_row(z, kp, q);
-                const int key = ((used >> q) & 1u) ? -1 : pivot_key(v);
-                if (key > bk) {  // ascending columns: ties keep the lower one
-                    bk = key;
-                    bc = tc + kGjTC * q;
-                    bv = v;
-                }
-            }
-            const unsigned grp = 0xFFu << ((tid & 31) & ~7);
-#pragma unroll
-            for (int o = 1; o < kGjTC; o <<= 1) {
-                const int ok = __shfl_xor_sync(grp, bk, o), oc = __shfl_xor_sync(grp, bc, o);
-                const float ox = __shfl_xor_sync(grp, bv.x, o), oy = __shfl_xor_sync(grp, bv.y, o);
-                if (ok > bk || (ok == bk && oc < bc)) {
-                    bk = ok;
-                    bc = oc;
-                    bv = make_float2(ox, oy);
-                }
-            }
-            if (tc == 0) {
-                s_j = bk > 0 ? bc : -1;  // key 0: the row of S is zero in every free column
-                s_pv = bv;
+        for (int q = 0; q < kGjCPT; ++q) {
+            const float2 v = pick_row(z, kp, q);
+            const int key = ((used >> q) & 1u) ? -1 : pivot_key(v);
+            if (key > bk) {  // ascending columns: ties keep the lower one
+                bk = key;
+                bc = tc + kGjTC * q;
+                bv = v;
             }
         }
-        __syncthreads();
-        const int j = s_j;
+        const unsigned grp = 0xFFu << ((tid & 31) & ~7);
+#pragma unroll
+        for (int o = 1; o < kGjTC; o <<= 1) {
+            const int ok = __shfl_xor_sync(grp, bk, o), oc = __shfl_xor_sync(grp, bc, o);
+            const float ox = __shfl_xor_sync(grp, bv.x, o), oy = __shfl_xor_sync(grp, bv.y, o);
+            if (ok > bk || (ok == bk && oc < bc)) {
+                bk = ok;
+                bc = oc;
+                bv = make_float2(ox, oy);
+            }
+        }
+        const int buf = i & 1;
+        if (tc == 0) {
+            s_j[buf] = bk > 0 ? bc : -1;  // key 0: the row of S is zero in every free column
+            s_pv[buf] = bv;
+        }
+#pragma unroll
+        for (int q = 0; q < kGjCPT; ++q) {
+            float2 v = pick_row(z, kp, q);
+            // the pivot column itself: z - (pv - 1) z / pv = z / pv
+            if (tc + kGjTC * q == bc) v = make_float2(bv.x - 1.f, bv.y);
+            rowbuf[buf][tc + kGjTC * q] = v;
+        }
+    };
+    search(0);
+    __syncthreads();
+    const int src0 = (tid & 31) & ~7;  // first lane of my row class
+    for (int i = 0; i < Ne; ++i) {
+        const int buf = i & 1;
+        const int j = s_j[buf];
         if (j < 0) {  // uniform: every thread read the same s_j
             singular = true;
             break;
         }
-        const float2 pv = s_pv;
+        const float2 pinv = crcp(s_pv[buf]);
         const int qj = j / kGjTC;
-        if (tc == (j & (kGjTC - 1))) {
-            const float2 pinv = crcp(pv);
-#pragma unroll
-            for (int k = 0; k < kGjRPT; ++k) colbuf[tr + kGjTR * k] = cmul(pick_col(z, k, qj), pinv);
-            used |= 1u << qj;
-        }
-        if (tr == trp) {
-#pragma unroll
-            for (int q = 0; q < kGjCPT; ++q) {
-                float2 v = pick_row(z, kp, q);
-                // the pivot column itself: z - (pv - 1) z / pv = z / pv
-                if (tc + kGjTC * q == j) v = make_float2(pv.x - 1.f, pv.y);
-                rowbuf[tc + kGjTC * q] = v;
-            }
-        }
+        if (tc == (j & (kGjTC - 1))) used |= 1u << qj;
         if (tid == 0) slot_of[j] = i;
-        __syncthreads();
+        float2 cb[kGjRPT];
 #pragma unroll
         for (int k = 0; k < kGjRPT; ++k) {
-            const float2 cb = colbuf[tr + kGjTR * k];
-#pragma unroll
-            for (int q = 0; q < kGjCPT; ++q) z[k][q] = cfms(z[k][q], rowbuf[tc + kGjTC * q], cb);
+            const float2 v = pick_col(z, k, qj);
+            const float vx = __shfl_sync(0xffffffffu, v.x, src0 | (j & (kGjTC - 1)));
+            const float vy = __shfl_sync(0xffffffffu, v.y, src0 | (j & (kGjTC - 1)));
+            cb[k] = cmul(make_float2(vx, vy), pinv);
         }
+#pragma unroll
+        for (int k = 0; k < kGjRPT; ++k)
+#pragma unroll
+            for (int q = 0; q < kGjCPT; ++q) z[k][q] = cfms(z[k][q], rowbuf[buf][tc + kGjTC * q], cb[k]);
+        if (i + 1 < Ne) search(i + 1);
+        __syncthreads();
     }
     if (singular && tid == 0) atomicOr(&s.status[t], ST_SINGULAR);
 
