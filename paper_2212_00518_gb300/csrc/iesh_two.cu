@@ -460,16 +460,18 @@ __global__ void __launch_bounds__(256) k2_build_w(DevState s, Model2Dev md, doub
 
 // Mixed precision: the same W in FP32, rows padded to Np = N rounded up to 4
 // with zeros (the layout of the FP32 propagators).  Eigenvalue differences
-// are formed in FP64 and rounded once, so nearly degenerate pairs keep FP32
-// relative accuracy; numerators in FP32 from lam - h_a rounded from FP64.
+// come from double-float eigenvalues (hi, lo), (hi_k - hi_j) + (lo_k - lo_j),
+// so nearly degenerate pairs keep FP32 relative accuracy without FP64
+// arithmetic per element; numerators in FP32 from lam - h_a rounded from FP64.
 __global__ void __launch_bounds__(256) k2_build_w_f32(DevState s, Model2Dev md, double dt, double tol)
 {
     extern __shared__ double w2_sh[];
     const int64_t t = traj_of(s, blockIdx.x);
     if (t < 0 || (s.status[t] & ST_DONE)) return;
     const int N = s.N, Np = (N + 3) & ~3;
-    double *l0 = w2_sh, *l1 = l0 + N, *red = l1 + N;         // [N], [N], [32]
-    float *a0 = reinterpret_cast<float *>(red + 32), *b0 = a0 + N, *a1 = b0 + N, *b1 = a1 + N;
+    double *red = w2_sh;                                              // [32]
+    float2 *l0 = reinterpret_cast<float2 *>(red + 32), *l1 = l0 + N;  // lam as (hi, lo) per end
+    float *a0 = reinterpret_cast<float *>(l1 + N), *b0 = a0 + N, *a1 = b0 + N, *b1 = a1 + N;
     float *m00 = b1 + N, *m01 = m00 + N, *m10 = m01 + N, *m11 = m10 + N;  // lam - h_a per end
     double x0[6], v0[6], x1[6], v1[6];
     for (int y = 0; y < 6; ++y) {
@@ -484,8 +486,9 @@ __global__ void __launch_bounds__(256) k2_build_w_f32(DevState s, Model2Dev md, 
     ads2_project(md, e1, v1, hv1, kv1);
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         const double la = s.lam_prev[t * N + i], lb = s.lam[t * N + i];
-        l0[i] = la;
-        l1[i] = lb;
+        const float ha = (float)la, hb = (float)lb;
+        l0[i] = make_float2(ha, (float)(la - (double)ha));
+        l1[i] = make_float2(hb, (float)(lb - (double)hb));
         a0[i] = (float)s.q0_prev[t * N + i];
         b0[i] = (float)s.q2_prev[t * N + i];
         a1[i] = (float)s.q0[t * N + i];
@@ -502,7 +505,7 @@ __global__ void __launch_bounds__(256) k2_build_w_f32(DevState s, Model2Dev md, 
     float *W = reinterpret_cast<float *>(s.scratch + t * s.scratch_stride);  // [N][Np]
     double lo = __longlong_as_double(0x7ff0000000000000ll), hi = -lo;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const double lk0 = l0[k], lk1 = l1[k];
+        const float2 lk0 = l0[k], lk1 = l1[k];
         const float ak0 = a0[k], bk0 = b0[k], ak1 = a1[k], bk1 = b1[k];
         const float nk00 = m00[k], nk01 = m01[k], nk10 = m10[k], nk11 = m11[k];
         float Rk = 0.0f;
@@ -513,7 +516,9 @@ __global__ void __launch_bounds__(256) k2_build_w_f32(DevState s, Model2Dev md, 
                                  b0[j] * bk0 * (H01 + K01 * (m01[j] + nk01));
                 const float T1 = a1[j] * ak1 * (H10 + K10 * (m10[j] + nk10)) +
                                  b1[j] * bk1 * (H11 + K11 * (m11[j] + nk11));
-                w = hdt * (T0 / (float)(lk0 - l0[j]) + T1 / (float)(lk1 - l1[j]));
+                const float g0 = (lk0.x - l0[j].x) + (lk0.y - l0[j].y);
+                const float g1 = (lk1.x - l1[j].x) + (lk1.y - l1[j].y);
+                w = hdt * (T0 / g0 + T1 / g1);
             }
             W[(int64_t)j * Np + k] = w;
             Rk += fabsf(w);
@@ -522,7 +527,7 @@ __global__ void __launch_bounds__(256) k2_build_w_f32(DevState s, Model2Dev md, 
             for (int j = 0; j < N; ++j) W[(int64_t)j * Np + N + k] = 0.0f;  // row padding
         // margin for the FP32 rounding of the row sum
         const double R = (double)Rk * (1.0 + 1e-5);
-        const double Lk = 0.5 * dt * (lk0 + lk1);
+        const double Lk = 0.5 * dt * (s.lam_prev[t * N + k] + s.lam[t * N + k]);
         lo = fmin(lo, Lk - R);
         hi = fmax(hi, Lk + R);
     }
@@ -702,7 +707,7 @@ cudaError_t launch_build_w2(iesh2_ctx *ctx, double dt, double tol)
     const int threads = std::min(256, (d.N + 31) & ~31);
     if (ctx->mixed)
         k2_build_w_f32<<<(unsigned)d.n, threads,
-                         (size_t)(2 * d.N + 32) * sizeof(double) + (size_t)8 * d.N * sizeof(float),
+                         (size_t)32 * sizeof(double) + (size_t)2 * d.N * sizeof(float2) + (size_t)8 * d.N * sizeof(float),
                          ctx->stream>>>(d, ctx->md, dt, tol);
     else
         k2_build_w<<<(unsigned)d.n, threads, (size_t)(6 * d.N + 32) * sizeof(double), ctx->stream>>>(
