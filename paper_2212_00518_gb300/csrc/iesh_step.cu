@@ -26,7 +26,7 @@ int eigen_tpb(int N)
 {
     int best = 1;
     double be = 0.0;
-    for (int t = 1; t * N <= 512; ++t) {
+    for (int t = 1; t * N <= 256; ++t) {
         const int thr = t * N, thr32 = (thr + 31) & ~31;
         const double eff = (double)thr / thr32 + 1e-4 * t;
         if (eff > be) {
@@ -53,7 +53,7 @@ __device__ __forceinline__ void slot_tree_sum(double *red, int r, bool inslot, i
 // tpb trajectories per CTA, one thread per root.
 // DF: the secular sums in double-float arithmetic (mixed path).
 template <bool DF>
-__global__ void __launch_bounds__(512, 1) k_eigen(DevState s, ModelDev md, double dt, int mode, int tpb)
+__global__ void __launch_bounds__(256, 2) k_eigen(DevState s, ModelDev md, double dt, int mode, int tpb)
 {
     extern __shared__ double sh[];
     const int N = s.N, M = s.M, Ne = s.Ne;
