@@ -1,9 +1,10 @@
 """GPU parity of the mixed-precision path (IESH_PREC_MIXED) with the FP64 oracle.
 
 Mixed path: eigen iteration (with double-float pole sums), forces, the hop
-probabilities from the ratios and the rescale in FP64; coupling generator, Chebyshev propagation,
-coefficients, the LU of the overlap matrix and the ratio substitutions in
-FP32.  The propagator runs on the tensor cores (3xTF32,
+selection and the rescale in FP64; coupling generator, Chebyshev propagation,
+coefficients and the determinant ratios in FP32 (a Gauss-Jordan elimination
+in registers for N <= 128, Ne <= 56, with the couplings in g also FP32; an
+LU with substitutions otherwise, or when a hop CTA size is set).  The propagator runs on the tensor cores (3xTF32,
 tcgen05) for N <= 128 and Ne <= 56 and as a register-tiled SIMT kernel
 otherwise; both are checked here.  Stated error per output (against the FP64 oracle,
 from shared states; measured values on GB300 in brackets):
@@ -74,6 +75,30 @@ def test_mixed_one_step(P, name, kernel):
         assert np.array_equal(st["occ"][t], r["occ"])
         assert abs(st["x"][t] - r["x"]) <= 1e-13 * (1 + abs(r["x"]))
         assert np.abs(st["C"][t].T - r["C"]).max() <= 1e-6
+
+
+@pytest.mark.parametrize("name", ["paper40", "dw100"])
+def test_mixed_hop_kernels_agree(P, name):
+    """The mixed path's two ratio algorithms: the built-in Gauss-Jordan
+    elimination in registers (N <= 128, Ne <= 56) and the LU kernel (chosen
+    by a hop CTA size of 256 or 512 threads) each match the oracle's hop
+    probabilities within the mixed bound, and so each other."""
+    md, dt, shift = CASES[name]
+    n = 8
+    x, p, occ, C = _state(md, n, 15, 0.6, shift)
+    B = O.bind(md)
+    gref = np.array([O.hop_probs(occ[t], C[t].T, O.eigen(B, x[t])[3], p[t] / md["mass"], dt)[0]
+                     for t in range(n)])
+    got = {}
+    for hop in (0, 256, 512):
+        ctx = P.Context(md, n, precision=P.PREC_MIXED)
+        ctx.set_kernel_shape(0, 0, hop)
+        ctx.set_state(x, p, occ, C.astype(np.complex64))
+        got[hop] = ctx.hop_probabilities(dt)
+        ctx.close()
+        assert np.abs(got[hop] - gref).max() <= 2e-6 * np.abs(gref).max(), hop
+    assert np.abs(got[0] - got[256]).max() <= 2e-6 * np.abs(gref).max()
+    assert np.abs(got[256] - got[512]).max() <= 1e-7 * np.abs(gref).max()
 
 
 @pytest.mark.parametrize("name,kernel", [("paper40", "default"), ("dw100", "default"), ("dw100", "simt")])

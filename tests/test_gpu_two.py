@@ -239,3 +239,25 @@ def test_mixed_100_steps(P, name):
     Cg = np.transpose(st["C"], (0, 2, 1))
     assert np.abs(Cg[same] - ref["C"][same]).max() <= 3e-5
     assert np.abs(st["x"][same] - ref["x"][same]).max() <= 1e-6 * np.abs(ref["x"]).max()
+
+
+def test_mixed_large_system_lu_and_simt(P):
+    """N = 142 orbitals, Ne = 71: past the register Gauss-Jordan kernel and
+    the tensor-core propagator, so the mixed path runs the LU hop kernel and
+    the SIMT FP32 propagator; one step against the oracle."""
+    md = W.two_orbital(140, seed=8, Ne=71)
+    n, dt = 4, 5.0
+    x, p, occ, C = W.two_orbital_state(md, n, 29, weight=0.6)
+    ctx, Cr = _mixed(P, md, x, p, occ, C)
+    g = ctx.hop_probabilities(dt)
+    for t in range(n):
+        d = O.eigen2(md, x[t], occ[t])[2]
+        dv = np.tensordot(p[t] / md["mass"], d, axes=1)
+        gref = O.hop_probs(occ[t], Cr[t].T, dv, 1.0, dt)[0]
+        assert np.abs(g[t] - gref).max() <= 2e-6 * np.abs(gref).max()
+    ctx.run(dt, 1, seed=3)
+    st = ctx.get_state()
+    ref = O.run2(md, x, p, occ, np.transpose(Cr, (0, 2, 1)), dt, 1, seed=3)
+    assert np.all(st["status"] == 0)
+    assert np.array_equal(st["occ"], ref["occ"])
+    assert np.abs(np.transpose(st["C"], (0, 2, 1)) - ref["C"]).max() <= 1e-6
