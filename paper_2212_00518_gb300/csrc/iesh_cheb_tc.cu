@@ -212,7 +212,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
         }
         tc::fence_after_sync();
         const float cj = s_cj[k + 1];
-        const int ph = (k + 1) & 3;  // (-i)^(k+1)
+        const int ph = (k + 1) & 3;  // (-i)^(k+1) = (1, 0), (0, -1), (-1, 0), (0, 1)
+        const float ca = ph == 0 ? cj : (ph == 2 ? -cj : 0.f), cb = ph == 1 ? -cj : (ph == 3 ? cj : 0.f);
         const bool first = k == 0;
         // D entries in flight four chunks at a time, one wait per group
         float dv[16];
@@ -246,19 +247,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
                         const float ni = first ? xi : fmaf(2.f, xi, -pp[1]);
                         pp[0] = own_r;
                         pp[1] = own_i;
-                        if (ph == 0) {
-                            aa[0] = fmaf(cj, nr, aa[0]);
-                            aa[1] = fmaf(cj, ni, aa[1]);
-                        } else if (ph == 1) {
-                            aa[0] = fmaf(cj, ni, aa[0]);
-                            aa[1] = fmaf(-cj, nr, aa[1]);
-                        } else if (ph == 2) {
-                            aa[0] = fmaf(-cj, nr, aa[0]);
-                            aa[1] = fmaf(-cj, ni, aa[1]);
-                        } else {
-                            aa[0] = fmaf(-cj, ni, aa[0]);
-                            aa[1] = fmaf(cj, nr, aa[1]);
-                        }
+                        // acc += cj (-i)^(k+1) n without a branch: (ca, cb) = cj (-i)^(k+1)
+                        aa[0] = fmaf(ca, nr, fmaf(-cb, ni, aa[0]));
+                        aa[1] = fmaf(ca, ni, fmaf(cb, nr, aa[1]));
                         float hi, lo;
                         tc::split_tf32(nr, hi, lo);
                         *reinterpret_cast<float *>(b0) = hi;

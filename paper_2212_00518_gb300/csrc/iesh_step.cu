@@ -554,7 +554,8 @@ __global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int
                     for (int q = 0; q < NR; ++q) y[r][q] = fmaf(wr[r], tv[q], y[r][q]);
             }
             const float cj = s_cj[k + 1];
-            const int ph = (k + 1) & 3;  // (-i)^(k+1)
+            const int ph = (k + 1) & 3;  // (-i)^(k+1) = (1, 0), (0, -1), (-1, 0), (0, 1)
+            const float ca = ph == 0 ? cj : (ph == 2 ? -cj : 0.f), cb = ph == 1 ? -cj : (ph == 3 ? cj : 0.f);
 #pragma unroll
             for (int r = 0; r < RQ; ++r) {
                 if (j0 + r < N) {
@@ -586,19 +587,9 @@ __global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int
                             ni = fmaf(2.f, xi, -prv[2 * e + 1]);
                         }
                         float *a = acc[r] + 2 * e;
-                        if (ph == 0) {
-                            a[0] = fmaf(cj, nr, a[0]);
-                            a[1] = fmaf(cj, ni, a[1]);
-                        } else if (ph == 1) {
-                            a[0] = fmaf(cj, ni, a[0]);
-                            a[1] = fmaf(-cj, nr, a[1]);
-                        } else if (ph == 2) {
-                            a[0] = fmaf(-cj, nr, a[0]);
-                            a[1] = fmaf(-cj, ni, a[1]);
-                        } else {
-                            a[0] = fmaf(-cj, ni, a[0]);
-                            a[1] = fmaf(cj, nr, a[1]);
-                        }
+                        // acc += cj (-i)^(k+1) n without a branch: (ca, cb) = cj (-i)^(k+1)
+                        a[0] = fmaf(ca, nr, fmaf(-cb, ni, a[0]));
+                        a[1] = fmaf(ca, ni, fmaf(cb, nr, a[1]));
                         nw[2 * e] = nr;
                         nw[2 * e + 1] = ni;
                     }
