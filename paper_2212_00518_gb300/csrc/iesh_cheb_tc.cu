@@ -95,10 +95,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
     if (tid == 0) tc::mbar_init(&mbar, 1);
     if (warp == 0) tc::tmem_alloc(&tmem_slot, (uint32_t)sh.ncols);
 
-    // A operand: W (rows j, columns i; stored [N][Np]) split into TF32 hi/lo.
-    // One warp writes one 128-byte core matrix at a time; each thread keeps
-    // 8 loads in flight (the loop is bound by the L2 latency otherwise).
+    // A operand: (2 / rho) W (rows j, columns i; stored [N][Np]) as TF32
+    // high part (the FP32 value itself) and low part.  The scale folds the
+    // recurrence's 2 / rho into the contraction.  One warp writes one
+    // 128-byte core matrix at a time; each thread keeps 8 loads in flight
+    // (the loop is bound by the L2 latency otherwise).
     const float *__restrict__ W = reinterpret_cast<const float *>(s.scratch + t * s.scratch_stride);
+    const double rho0 = s.cheb[t * kChebStride + 1];
+    const float w2 = rho0 > 0.0 ? 2.0f / (float)rho0 : 0.0f;
     {
         const int kch = sh.Kp / 4, ncm = (kTcM / 8) * kch;
         constexpr int kBatch = 8, kWarps = kTcThreads / 32;
@@ -109,7 +113,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
                 const int cm = cm0 + b * kWarps;
                 const int rg = cm / kch, kc = cm - rg * kch;
                 const int row = rg * 8 + (lane >> 2), k = kc * 4 + (lane & 3);
-                v[b] = (cm < ncm && row < N && k < N) ? W[(int64_t)row * Np + k] : 0.0f;
+                v[b] = (cm < ncm && row < N && k < N) ? w2 * W[(int64_t)row * Np + k] : 0.0f;
             }
 #pragma unroll
             for (int b = 0; b < kBatch; ++b) {
@@ -117,10 +121,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
                 if (cm < ncm) {
                     const int rg = cm / kch, kc = cm - rg * kch;
                     const int row = rg * 8 + (lane >> 2), k = kc * 4 + (lane & 3);
-                    float hi, lo;
-                    tc::split_tf32(v[b], hi, lo);
-                    *reinterpret_cast<float *>(Ahi + offA(sh, row, k)) = hi;
-                    *reinterpret_cast<float *>(Alo + offA(sh, row, k)) = lo;
+                    *reinterpret_cast<float *>(Ahi + offA(sh, row, k)) = v[b];
+                    *reinterpret_cast<float *>(Alo + offA(sh, row, k)) = tc::lo_tf32(v[b]);
                 }
             }
         }
@@ -141,12 +143,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
     if (tid == 0) {
         double scd, ccd;
         sincos(c, &scd, &ccd);
-        s_sc[0] = (float)(rho > 0.0 ? 1.0 / rho : 0.0);
         s_sc[1] = (float)scd;
         s_sc[2] = (float)ccd;
     }
     float2 *C = reinterpret_cast<float2 *>(s.C) + (int64_t)t * Ne * N;
-    const float Lc = rowok ? (float)(0.5 * dt * (s.lam_prev[t * N + j] + s.lam[t * N + j]) - c) : 0.0f;
+    // 2 (L_j - c) / rho, the diagonal's share of 2 X
+    const float Lc = rowok ? w2 * (float)(0.5 * dt * (s.lam_prev[t * N + j] + s.lam[t * N + j]) - c) : 0.0f;
     const float J0 = (float)J[0];
 
     // T_0 = C: my row, my columns.  B entry (col, j) of this thread sits at
@@ -169,13 +171,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
             acc[4 * ch + 2 * h + 1] = J0 * v.y;  // single products: no contraction possible
             if (mine) {
                 unsigned char *b0 = Bhi + (col >> 3) * sh.sboB + (col & 7) * 16 + jb;
-                float hi, lo;
-                tc::split_tf32(v.x, hi, lo);
-                *reinterpret_cast<float *>(b0) = hi;
-                *reinterpret_cast<float *>(b0 + loB) = lo;
-                tc::split_tf32(v.y, hi, lo);
-                *reinterpret_cast<float *>(b0 + 16) = hi;
-                *reinterpret_cast<float *>(b0 + loB + 16) = lo;
+                *reinterpret_cast<float *>(b0) = v.x;
+                *reinterpret_cast<float *>(b0 + loB) = tc::lo_tf32(v.x);
+                *reinterpret_cast<float *>(b0 + 16) = v.y;
+                *reinterpret_cast<float *>(b0 + loB + 16) = tc::lo_tf32(v.y);
             }
         }
     }
@@ -188,7 +187,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
     const uint32_t aHi = tc::smem_addr(Ahi), aLo = tc::smem_addr(Alo);
     const uint32_t bHi = tc::smem_addr(Bhi), bLo = tc::smem_addr(Blo);
     const uint32_t my_lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-    const float inv_rho = s_sc[0];  // written before the barrier above
 
     bool ok = true;
     for (int k = 0; k < K; ++k) {
@@ -235,28 +233,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
                         const float *d = dv + 4 * (ch & 3) + 2 * h;
                         float *pp = prv + 4 * ch + 2 * h, *aa = acc + 4 * ch + 2 * h;
                         unsigned char *b0 = Bhi + (col >> 3) * sh.sboB + (col & 7) * 16 + jb;
-                        // T_k exactly (hi + lo)
-                        const float own_r = *reinterpret_cast<const float *>(b0) +
-                                            *reinterpret_cast<const float *>(b0 + loB);
-                        const float own_i = *reinterpret_cast<const float *>(b0 + 16) +
-                                            *reinterpret_cast<const float *>(b0 + loB + 16);
-                        // (X t)_j = ((L_j - c) t_j - i (W t)_j) / rho, (W t)_j = D_j
-                        const float xr = fmaf(Lc, own_r, d[1]) * inv_rho;
-                        const float xi = fmaf(Lc, own_i, -d[0]) * inv_rho;
-                        const float nr = first ? xr : fmaf(2.f, xr, -pp[0]);
-                        const float ni = first ? xi : fmaf(2.f, xi, -pp[1]);
+                        // T_k exactly: the high operand is the FP32 value
+                        const float own_r = *reinterpret_cast<const float *>(b0);
+                        const float own_i = *reinterpret_cast<const float *>(b0 + 16);
+                        // 2 (X t)_j = 2 ((L_j - c) t_j - i (W t)_j) / rho, D_j = 2 (W t)_j / rho
+                        const float xr = fmaf(Lc, own_r, d[1]);
+                        const float xi = fmaf(Lc, own_i, -d[0]);
+                        const float nr = first ? 0.5f * xr : xr - pp[0];
+                        const float ni = first ? 0.5f * xi : xi - pp[1];
                         pp[0] = own_r;
                         pp[1] = own_i;
                         // acc += cj (-i)^(k+1) n without a branch: (ca, cb) = cj (-i)^(k+1)
                         aa[0] = fmaf(ca, nr, fmaf(-cb, ni, aa[0]));
                         aa[1] = fmaf(ca, ni, fmaf(cb, nr, aa[1]));
-                        float hi, lo;
-                        tc::split_tf32(nr, hi, lo);
-                        *reinterpret_cast<float *>(b0) = hi;
-                        *reinterpret_cast<float *>(b0 + loB) = lo;
-                        tc::split_tf32(ni, hi, lo);
-                        *reinterpret_cast<float *>(b0 + 16) = hi;
-                        *reinterpret_cast<float *>(b0 + loB + 16) = lo;
+                        *reinterpret_cast<float *>(b0) = nr;
+                        *reinterpret_cast<float *>(b0 + loB) = tc::lo_tf32(nr);
+                        *reinterpret_cast<float *>(b0 + 16) = ni;
+                        *reinterpret_cast<float *>(b0 + loB + 16) = tc::lo_tf32(ni);
                     }
                 }
             }

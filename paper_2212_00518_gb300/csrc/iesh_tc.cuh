@@ -120,12 +120,13 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 // Split x = hi + lo exactly, hi rounded to TF32 (10 stored mantissa bits),
 // so that the three products hi*hi + hi*lo + lo*hi of the 3xTF32 scheme
 // reproduce an FP32 product to about 2^-22.
-__device__ __forceinline__ void split_tf32(float x, float &hi, float &lo)
+// Low part of an FP32 value against its TF32 reading: a .tf32 operand of
+// the tensor cores uses the top 19 bits of each 32-bit element (sign,
+// exponent, 10 mantissa bits) and ignores the low 13, so storing x itself as
+// the high operand and x - trunc(x) as the low one splits x exactly.
+__device__ __forceinline__ float lo_tf32(float x)
 {
-    const uint32_t u = __float_as_uint(x);
-    const uint32_t r = (u + 0x1000u) & 0xFFFFE000u;  // round half away in magnitude
-    hi = __uint_as_float(r);
-    lo = x - hi;
+    return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
 }
 
 }  // namespace tc
