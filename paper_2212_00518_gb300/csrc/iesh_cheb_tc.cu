@@ -13,7 +13,10 @@
 // up to 16).  FP32 accuracy comes from the 3xTF32 split: W = W_hi + W_lo and
 // T = T_hi + T_lo with TF32 high parts, D = W_hi T_hi + W_hi T_lo + W_lo T_hi
 // accumulated in FP32 in tensor memory (the dropped W_lo T_lo term is about
-// 2^-22 of |W| |T|).
+// 2^-22 of |W| |T|).  A .tf32 operand uses the top 19 bits of each 32-bit
+// element, so the high planes hold the FP32 values themselves (read as
+// their truncation) and the low planes x - trunc(x).  W enters scaled by
+// 2 / rho, which folds the recurrence's factor into the contraction.
 //
 // One CTA per trajectory, 512 threads: warp w reads TMEM lanes 32 (w % 4)
 // .. +31, i.e. orbital row j = 32 (w % 4) + lane, and owns the column
@@ -21,7 +24,7 @@
 // 3 x K/8 MMAs and commits them to an mbarrier; every thread waits (bounded),
 // loads its D entries from tensor memory, forms T_{k+1} for its row and
 // columns (T_{k-1} and the Chebyshev sum kept in registers, T_k read back
-// from the B operand as hi + lo), and
+// from the high plane of the B operand), and
 // rewrites its entries of the B operand in place (nobody else reads them
 // once the MMAs of the order have completed).
 //
