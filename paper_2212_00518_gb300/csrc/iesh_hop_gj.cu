@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kGjThreads, 2) k_hop_gj(DevState s, double dt,
                         if constexpr (EXT) T = fmaf(qb_s[m] * qb_s[sa], fmaf(kb, mb_s[m] + mb_s[sa], hb), T);
                         const float2 lm = ld_s[m], ls = ld_s[sa];
                         const float gap = (ls.x - lm.x) + (ls.y - lm.y);
-                        const float gam = fac * z[k][q].x * (T / gap);
+                        const float gam = fac * z[k][q].x * __fdividef(T, gap);  // at most 2 ulp
                         G[(int64_t)a * N + m] = gam > 0.f ? (double)gam : 0.0;
                     }
                 }

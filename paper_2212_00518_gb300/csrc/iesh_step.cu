@@ -292,8 +292,9 @@ __global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, doub
             if (j != k) {
                 const float den0 = E0[org[j]] + (tk0 - tau[j]);
                 const float den1 = E1[org[N + j]] + (tk1 - tau[N + j]);
-                const float d0 = qf[j] * qk0 * (dh0 + k0 * (lmh[j] + mk0)) / den0;
-                const float d1 = qf[N + j] * qk1 * (dh1 + k1 * (lmh[N + j] + mk1)) / den1;
+                // fast division (at most 2 ulp): the gaps are far from the range limits
+                const float d0 = __fdividef(qf[j] * qk0 * (dh0 + k0 * (lmh[j] + mk0)), den0);
+                const float d1 = __fdividef(qf[N + j] * qk1 * (dh1 + k1 * (lmh[N + j] + mk1)), den1);
                 w = a0 * d0 + a1 * d1;
             }
             W[(int64_t)j * Np + k] = w;

@@ -518,7 +518,8 @@ __global__ void __launch_bounds__(256) k2_build_w_f32(DevState s, Model2Dev md, 
                                  b1[j] * bk1 * (H11 + K11 * (m11[j] + nk11));
                 const float g0 = (lk0.x - l0[j].x) + (lk0.y - l0[j].y);
                 const float g1 = (lk1.x - l1[j].x) + (lk1.y - l1[j].y);
-                w = hdt * (T0 / g0 + T1 / g1);
+                // fast division (at most 2 ulp): the gaps are far from the range limits
+                w = hdt * (__fdividef(T0, g0) + __fdividef(T1, g1));
             }
             W[(int64_t)j * Np + k] = w;
             Rk += fabsf(w);
