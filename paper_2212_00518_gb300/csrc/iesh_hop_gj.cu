@@ -134,39 +134,52 @@ __global__ void __launch_bounds__(kGjThreads, 2) k_hop_gj(DevState s, double dt,
     auto search = [&](int i) {
         const int p = occ_s[i], kp = p / kGjTR;
         if (tr != (p & (kGjTR - 1))) return;  // the 8 lanes holding row p (an aligned group)
+        float2 row[kGjCPT];  // my entries of row p (kp is uniform: one switch)
+        switch (kp) {
+        case 0:
+#pragma unroll
+            for (int q = 0; q < kGjCPT; ++q) row[q] = z[0][q];
+            break;
+        case 1:
+#pragma unroll
+            for (int q = 0; q < kGjCPT; ++q) row[q] = z[1][q];
+            break;
+        case 2:
+#pragma unroll
+            for (int q = 0; q < kGjCPT; ++q) row[q] = z[2][q];
+            break;
+        default:
+#pragma unroll
+            for (int q = 0; q < kGjCPT; ++q) row[q] = z[3][q];
+        }
         int bk = -1, bc = kGjMaxNe;
-        float2 bv = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < kGjCPT; ++q) {
-            const float2 v = pick_row(z, kp, q);
-            const int key = ((used >> q) & 1u) ? -1 : pivot_key(v);
+            const int key = ((used >> q) & 1u) ? -1 : pivot_key(row[q]);
             if (key > bk) {  // ascending columns: ties keep the lower one
                 bk = key;
                 bc = tc + kGjTC * q;
-                bv = v;
             }
         }
         const unsigned grp = 0xFFu << ((tid & 31) & ~7);
 #pragma unroll
         for (int o = 1; o < kGjTC; o <<= 1) {
             const int ok = __shfl_xor_sync(grp, bk, o), oc = __shfl_xor_sync(grp, bc, o);
-            const float ox = __shfl_xor_sync(grp, bv.x, o), oy = __shfl_xor_sync(grp, bv.y, o);
             if (ok > bk || (ok == bk && oc < bc)) {
                 bk = ok;
                 bc = oc;
-                bv = make_float2(ox, oy);
             }
         }
         const int buf = i & 1;
-        if (tc == 0) {
-            s_j[buf] = bk > 0 ? bc : -1;  // key 0: the row of S is zero in every free column
-            s_pv[buf] = bv;
-        }
+        if (tc == 0) s_j[buf] = bk > 0 ? bc : -1;  // key 0: the row of S is zero in every free column
 #pragma unroll
         for (int q = 0; q < kGjCPT; ++q) {
-            float2 v = pick_row(z, kp, q);
-            // the pivot column itself: z - (pv - 1) z / pv = z / pv
-            if (tc + kGjTC * q == bc) v = make_float2(bv.x - 1.f, bv.y);
+            float2 v = row[q];
+            if (tc + kGjTC * q == bc) {  // the lane holding the pivot
+                s_pv[buf] = v;
+                // the pivot column itself: z - (pv - 1) z / pv = z / pv
+                v = make_float2(v.x - 1.f, v.y);
+            }
             rowbuf[buf][tc + kGjTC * q] = v;
         }
     };
