@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
     __syncthreads();
 
     const double *cb = s.cheb + t * kChebStride;
-    const double c = cb[0], rho = cb[1];
+    const double c = cb[0];
     const int K = (int)cb[2];
     const double *J = cb + 3;
     for (int q = tid; q <= K; q += kTcThreads) s_cj[q] = (float)(2.0 * J[q]);

@@ -117,9 +117,8 @@ __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence
 // Generic-proxy shared-memory writes become visible to the tensor cores.
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Split x = hi + lo exactly, hi rounded to TF32 (10 stored mantissa bits),
-// so that the three products hi*hi + hi*lo + lo*hi of the 3xTF32 scheme
-// reproduce an FP32 product to about 2^-22.
+// The three products hi*hi + hi*lo + lo*hi of the 3xTF32 scheme reproduce
+// an FP32 product to about 2^-22.
 // Low part of an FP32 value against its TF32 reading: a .tf32 operand of
 // the tensor cores uses the top 19 bits of each 32-bit element (sign,
 // exponent, 10 mantissa bits) and ignores the low 13, so storing x itself as

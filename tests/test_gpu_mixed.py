@@ -4,9 +4,10 @@ Mixed path: eigen iteration (with double-float pole sums), forces, the hop
 selection and the rescale in FP64; coupling generator, Chebyshev propagation,
 coefficients and the determinant ratios in FP32 (a Gauss-Jordan elimination
 in registers for N <= 128, Ne <= 56, with the couplings in g also FP32; an
-LU with substitutions otherwise, or when a hop CTA size is set).  The propagator runs on the tensor cores (3xTF32,
-tcgen05) for N <= 128 and Ne <= 56 and as a register-tiled SIMT kernel
-otherwise; both are checked here.  Stated error per output (against the FP64 oracle,
+LU with substitutions otherwise, or when a hop CTA size is set).  The
+propagator runs on the tensor cores (3xTF32, tcgen05) for N <= 128 and
+Ne <= 56 and as a register-tiled SIMT kernel otherwise, or when a propagator
+shape (4, G) is set; both are checked here.  Stated error per output (against the FP64 oracle,
 from shared states; measured values on GB300 in brackets):
   hop probabilities g      relative to max g        2e-6   [3.8e-7]
   coefficients C, 1 step   absolute (unit columns)  1e-6   [1.8e-7]
@@ -49,7 +50,8 @@ def _state(md, n, seed, weight, shift):
     return x + shift, p, occ, C
 
 
-@pytest.mark.parametrize("name,kernel", [(k, "default") for k in CASES] + [("dw100", "simt"), ("paper40", "simt")])
+@pytest.mark.parametrize("name,kernel", [(k, "default") for k in CASES] +
+                         [("dw100", "simt"), ("paper40", "simt"), ("dw200", "simt")])
 def test_mixed_one_step(P, name, kernel):
     md, dt, shift = CASES[name]
     n = 8
@@ -72,6 +74,35 @@ def test_mixed_one_step(P, name, kernel):
     st = ctx.get_state()
     for t in range(n):
         r = O.step_one(B, x[t], p[t], occ[t].astype(np.int32), C[t].T, dt, seed=9, traj=t, n=0)
+        assert np.array_equal(st["occ"][t], r["occ"])
+        assert abs(st["x"][t] - r["x"]) <= 1e-13 * (1 + abs(r["x"]))
+        assert np.abs(st["C"][t].T - r["C"]).max() <= 1e-6
+
+
+@pytest.mark.parametrize("M,Ne,n", [(128, 1, 6), (200, 100, 4), (200, 33, 4), (160, 80, 4), (255, 112, 2),
+                                     (120, 60, 4)])
+def test_mixed_large_and_ragged_shapes(P, M, Ne, n):
+    """Mixed step on shapes past the tensor-core kernel (N > 128 or
+    Ne > 56): one orbital past a 128-row tile (N = 129, Ne = 1), the M = 200
+    bath with Ne = 100 and with a ragged Ne = 33, Ne = 80 at N = 161, the
+    largest sizes (N = 256, Ne = 112) and N = 121 with Ne = 60 > 56.  The
+    SIMT propagator and the LU ratio kernel serve them; one step against the
+    oracle."""
+    md = W.double_well(M, Ne)
+    N = M + 1
+    x, p = W.thermal_harmonic(n, md["mass"], md["par"][0], 0.01, 21)
+    occ = W.random_occupations(n, N, Ne, 22)
+    C = W.mixed_coefficients(occ, N, 23, 0.6)
+    B = O.bind(md)
+    ctx = P.Context(md, n, precision=P.PREC_MIXED)
+    assert ctx.kernel_shape()[0] == 4
+    ctx.set_state(x, p, occ, C.astype(np.complex64))
+    ctx.run(1.0, 1, seed=4)
+    st = ctx.get_state()
+    ctx.close()
+    assert np.all(st["status"] == 0)
+    for t in range(n):
+        r = O.step_one(B, x[t], p[t], occ[t].astype(np.int32), C[t].T, 1.0, seed=4, traj=t, n=0)
         assert np.array_equal(st["occ"][t], r["occ"])
         assert abs(st["x"][t] - r["x"]) <= 1e-13 * (1 + abs(r["x"]))
         assert np.abs(st["C"][t].T - r["C"]).max() <= 1e-6
@@ -101,10 +132,13 @@ def test_mixed_hop_kernels_agree(P, name):
     assert np.abs(got[256] - got[512]).max() <= 1e-7 * np.abs(gref).max()
 
 
-@pytest.mark.parametrize("name,kernel", [("paper40", "default"), ("dw100", "default"), ("dw100", "simt")])
+@pytest.mark.parametrize("name,kernel", [("paper40", "default"), ("dw100", "default"), ("dw100", "simt"),
+                                         ("dw200", "default")])
 def test_mixed_100_steps(P, name, kernel):
     md, dt, shift = CASES[name]
     n, steps, every = 8, 100, 20
+    if md["M"] + 1 > 128:  # the FP64 oracle takes about 0.1 s per step here
+        n, steps, every = 4, 40, 20
     x, p, occ, C = _state(md, n, 5, 0.6, shift)
     B = O.bind(md)
     ctx = P.Context(md, n, precision=P.PREC_MIXED, record_every=every, max_records=steps // every)
