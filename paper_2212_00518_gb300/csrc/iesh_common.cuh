@@ -75,6 +75,22 @@ struct DevState {
     int32_t *hop_pair;         // [n] a N + m of the selected hop, or -1
 };
 
+// 16-byte asynchronous copy global -> shared, cached in L2 only (both
+// addresses 16-byte aligned); completion by commit groups.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Wait until at most `Pending` of this thread's committed groups are in flight.
+template <int Pending>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(Pending) : "memory");
+}
+
 // Smallest power of two >= n (width of the fixed-order tree reductions).
 __host__ __device__ inline int eigen_pow2(int n)
 {

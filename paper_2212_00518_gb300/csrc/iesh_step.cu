@@ -456,7 +456,10 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
 // owns rows 4rq..4rq+3 and CE electrons (2 CE reals) of the CTA's block of
 // G*CE electrons.  Per orbital i it loads W[i][4rq..4rq+3] as one float4
 // (W_ji = -W_ij; W rows padded to a multiple of 4) and 2CE reals of t_k[i]
-// as float4 broadcasts from shared memory, for 8 CE FFMAs.  t_k and
+// as float4 broadcasts from shared memory, for 8 CE FFMAs.  W reaches shared
+// memory by cp.async in chunks of 8 rows, in a ring of 4 chunks filled 3
+// chunks ahead (one barrier per chunk), so the loop reads it at shared-
+// memory latency instead of L2's.  t_k and
 // t_(k-1) live in two shared buffers: t_(k+1) overwrites t_(k-1) in place
 // (each thread rewrites only its own entries), so one barrier per order
 // suffices and neither is held in registers.  Row j of a buffer starts at
@@ -522,6 +525,20 @@ __global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int
             for (int h = 0; h < NV; ++h) d4[h] = make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
         }
     }
+    // W ring: chunk g (rows 8 (g % nwc) ..) in slot g % 4, one commit group each
+    float *wring = buf1 + cheb32_row(Np, W2);
+    const int nwc = (N + kCheb32WRows - 1) / kCheb32WRows, gtot = K * nwc;
+    auto fetch = [&](int g) {
+        if (g < gtot) {
+            const int c = g % nwc;
+            const int nv = min(kCheb32WRows, N - kCheb32WRows * c) * Np / 4;  // float4 of the chunk
+            float *dst = wring + (g % kCheb32WRing) * kCheb32WRows * Np;
+            const float *src = W + (int64_t)kCheb32WRows * c * Np;
+            for (int v = threadIdx.x; v < nv; v += blockDim.x) cp_async16(dst + 4 * v, src + 4 * v);
+        }
+        cp_async_commit();
+    };
+    for (int g = 0; g < kCheb32WRing - 1; ++g) fetch(g);
     __syncthreads();
     const float inv_rho = s_sc[0];
     for (int k = 0; k < K; ++k) {
@@ -532,28 +549,40 @@ __global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int
         for (int r = 0; r < RQ; ++r)
 #pragma unroll
             for (int q = 0; q < NR; ++q) y[r][q] = 0.f;
-        if (act) {
-            const float *col = cur + NR * cg;
-            const float *wcol = W + j0;
-#pragma unroll 2
-            for (int i = 0; i < N; ++i) {
-                const float4 w = *reinterpret_cast<const float4 *>(wcol + (int64_t)i * Np);
-                const float4 *tr = reinterpret_cast<const float4 *>(col + cheb32_row(i, W2));
-                float tv[NR];
+        const float *col = cur + NR * cg;
+        for (int c = 0; c < nwc; ++c) {
+            const int g = k * nwc + c;
+            // chunk g has landed for every thread (two newer groups may be in
+            // flight) and every thread is done with chunk g - 1, whose slot
+            // takes chunk g + 3
+            cp_async_wait<kCheb32WRing - 2>();
+            __syncthreads();
+            fetch(g + kCheb32WRing - 1);
+            if (act) {
+                const float *wcol = wring + (g % kCheb32WRing) * kCheb32WRows * Np + j0;
+                const int i0 = kCheb32WRows * c, rows = min(kCheb32WRows, N - i0);
+#pragma unroll 4
+                for (int ii = 0; ii < rows; ++ii) {
+                    const float4 w = *reinterpret_cast<const float4 *>(wcol + ii * Np);
+                    const float4 *tr = reinterpret_cast<const float4 *>(col + cheb32_row(i0 + ii, W2));
+                    float tv[NR];
 #pragma unroll
-                for (int h = 0; h < NV; ++h) {
-                    const float4 a4 = tr[h];
-                    tv[4 * h] = a4.x;
-                    tv[4 * h + 1] = a4.y;
-                    tv[4 * h + 2] = a4.z;
-                    tv[4 * h + 3] = a4.w;
+                    for (int h = 0; h < NV; ++h) {
+                        const float4 a4 = tr[h];
+                        tv[4 * h] = a4.x;
+                        tv[4 * h + 1] = a4.y;
+                        tv[4 * h + 2] = a4.z;
+                        tv[4 * h + 3] = a4.w;
+                    }
+                    const float wr[RQ] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int r = 0; r < RQ; ++r)
+#pragma unroll
+                        for (int q = 0; q < NR; ++q) y[r][q] = fmaf(wr[r], tv[q], y[r][q]);
                 }
-                const float wr[RQ] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                for (int r = 0; r < RQ; ++r)
-#pragma unroll
-                    for (int q = 0; q < NR; ++q) y[r][q] = fmaf(wr[r], tv[q], y[r][q]);
             }
+        }
+        if (act) {
             const float cj = s_cj[k + 1];
             const int ph = (k + 1) & 3;  // (-i)^(k+1) = (1, 0), (0, -1), (-1, 0), (0, 1)
             const float ca = ph == 0 ? cj : (ph == 2 ? -cj : 0.f), cb = ph == 1 ? -cj : (ph == 3 ? cj : 0.f);
@@ -601,6 +630,7 @@ __global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int
         }
         __syncthreads();
     }
+    cp_async_wait<0>();  // no copy outlives the CTA
     if (act) {
         const float sc = s_sc[1], cc = s_sc[2];
 #pragma unroll
@@ -621,7 +651,8 @@ __global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int
 size_t cheb32_smem_bytes(int N, int G)
 {
     const int Np = (N + 3) & ~3;
-    return (size_t)2 * (Np * 8 * G + Np) * sizeof(float);  // two buffers of padded rows
+    // two buffers of padded rows and the ring of W chunks
+    return ((size_t)2 * (Np * 8 * G + Np) + (size_t)kCheb32WRing * kCheb32WRows * Np) * sizeof(float);
 }
 void cheb32_shape(int N, int Ne, int &G)
 {
