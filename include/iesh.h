@@ -187,7 +187,7 @@ iesh_status iesh_get_live(iesh_ctx *ctx, int64_t *n_live);
  * cheb_G column groups per CTA of the propagator (cheb_G * N <= 1024).
  * Mixed contexts: cheb_ept must be 4 (each thread holds 4 orbitals x 4
  * electrons) and cheb_G * ceil(N/4) <= 256, with 8 * Np * (8 cheb_G + 1)
- * + 128 * Np bytes of shared memory (Np = N rounded up to a multiple of 4;
+ * + 192 * Np bytes of shared memory (Np = N rounded up to a multiple of 4;
  * the second term stages W) at most 110 KiB.  hop_threads (256 or 512): threads of the LU hop kernel; 0
  * restores the built-in choice, which for mixed contexts with N <= 128 and
  * Ne <= 56 is a Gauss-Jordan elimination of all determinant ratios in

@@ -38,8 +38,8 @@ void cheb_shape(int N, int Ne, int &ept, int &G);
 int eigen_tpb(int N);
 // FP32 (mixed-precision) propagator: 4 electrons per thread, G column groups
 constexpr size_t kCheb32MaxSmem = 110 * 1024;
-constexpr int kCheb32WRows = 8;  // rows of W per chunk staged in shared memory
-constexpr int kCheb32WRing = 4;  // chunks in the ring (filled 3 ahead)
+constexpr int kCheb32WRows = 16; // rows of W per chunk staged in shared memory
+constexpr int kCheb32WRing = 3;  // chunks in the ring (filled 2 ahead)
 size_t cheb32_smem_bytes(int N, int G);
 void cheb32_shape(int N, int Ne, int &G);
 // FP32 propagator on the tensor cores (3xTF32), N <= 128 and Ne <= 56

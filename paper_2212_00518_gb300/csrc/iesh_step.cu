@@ -457,9 +457,9 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
 // G*CE electrons.  Per orbital i it loads W[i][4rq..4rq+3] as one float4
 // (W_ji = -W_ij; W rows padded to a multiple of 4) and 2CE reals of t_k[i]
 // as float4 broadcasts from shared memory, for 8 CE FFMAs.  W reaches shared
-// memory by cp.async in chunks of 8 rows, in a ring of 4 chunks filled 3
-// chunks ahead (one barrier per chunk), so the loop reads it at shared-
-// memory latency instead of L2's.  t_k and
+// memory by cp.async in chunks of kCheb32WRows rows, in a ring of
+// kCheb32WRing chunks filled kCheb32WRing - 1 chunks ahead (one barrier per
+// chunk), so the loop reads it at shared-memory latency instead of L2's.  t_k and
 // t_(k-1) live in two shared buffers: t_(k+1) overwrites t_(k-1) in place
 // (each thread rewrites only its own entries), so one barrier per order
 // suffices and neither is held in registers.  Row j of a buffer starts at
@@ -525,7 +525,8 @@ __global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int
             for (int h = 0; h < NV; ++h) d4[h] = make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
         }
     }
-    // W ring: chunk g (rows 8 (g % nwc) ..) in slot g % 4, one commit group each
+    // W ring: chunk g (rows kCheb32WRows (g % nwc) ..) in slot g % kCheb32WRing,
+    // one commit group each
     float *wring = buf1 + cheb32_row(Np, W2);
     const int nwc = (N + kCheb32WRows - 1) / kCheb32WRows, gtot = K * nwc;
     auto fetch = [&](int g) {
@@ -552,9 +553,9 @@ __global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int
         const float *col = cur + NR * cg;
         for (int c = 0; c < nwc; ++c) {
             const int g = k * nwc + c;
-            // chunk g has landed for every thread (two newer groups may be in
-            // flight) and every thread is done with chunk g - 1, whose slot
-            // takes chunk g + 3
+            // chunk g has landed for every thread (kCheb32WRing - 2 newer groups
+            // may be in flight) and every thread is done with chunk g - 1,
+            // whose slot takes chunk g + kCheb32WRing - 1
             cp_async_wait<kCheb32WRing - 2>();
             __syncthreads();
             fetch(g + kCheb32WRing - 1);

@@ -26,14 +26,14 @@ def cheb_candidates(N, Ne, limit=6, precision=0):
     FP64: (ept, G) with ept 1 or 2 electrons per thread and G * N <= 1024
     threads.  Mixed precision: (4, G), 4 orbitals x 4 electrons per thread
     and G * ceil(N / 4) <= 256 threads, two buffers of Np x (8G + 1) floats
-    (Np = N rounded up to a multiple of 4) and a ring of 4 x 8 rows of W
-    (32 Np floats) in at most 110 KiB."""
+    (Np = N rounded up to a multiple of 4) and a ring of 3 x 16 rows of W
+    (48 Np floats) in at most 110 KiB."""
     out = []
     if precision == _I.PREC_MIXED:
         nq = -(-N // 4)
         Np = 4 * nq
         for G in range(1, 256 // nq + 1):
-            if G > 1 and (2 * (Np * 8 * G + Np) + 32 * Np) * 4 > 110 * 1024:
+            if G > 1 and (2 * (Np * 8 * G + Np) + 48 * Np) * 4 > 110 * 1024:
                 break
             nb = 4 * G
             if nb > 4 * Ne + 3:
