@@ -28,6 +28,11 @@ void configure_hop_smem();
 // mixed-path hop probabilities by Gauss-Jordan elimination in registers
 // (N <= 128, Ne <= 56)
 bool hop_gj_eligible(int N, int Ne);
+// the same elimination with the rows past 128 in shared memory: N <= 256, Ne <= 112
+bool hop_gjl_eligible(int N, int Ne);
+void configure_hop_gjl();
+cudaError_t launch_hop_gjl(const DevState &s, double dt, double mass, uint64_t seed, double *g_out,
+                           cudaStream_t st, bool ext);
 cudaError_t launch_hop_gj(const DevState &s, double dt, double mass, uint64_t seed, double *g_out,
                           cudaStream_t st, bool ext);
 // Bath of one lead: energies and weights (Gauss-Legendre split at mu, or trapezoid)

@@ -1318,6 +1318,7 @@ void configure_hop_smem()
     allow_max_smem(k_hop<float2, 512, 1, true>);
     allow_max_smem(k_hop<float2, 256, 4, true>);
     allow_max_smem(k_cheb_f32t<4>);
+    configure_hop_gjl();
 }
 
 cudaError_t launch_hop(const DevState &s, double dt, double mass, uint64_t seed, int skip_bound,
@@ -1328,6 +1329,8 @@ cudaError_t launch_hop(const DevState &s, double dt, double mass, uint64_t seed,
     // unless a hop CTA size was requested
     if (mixed && s.hop_threads == 0 && hop_gj_eligible(s.N, s.Ne))
         return launch_hop_gj(s, dt, mass, seed, g_out, st, ext);
+    if (mixed && s.hop_threads == 0 && hop_gjl_eligible(s.N, s.Ne))
+        return launch_hop_gjl(s, dt, mass, seed, g_out, st, ext);
     const size_t smem = hop_smem_bytes(s.N, s.Ne, mixed, ext);
     // 256-thread CTAs (three per SM) when two or more fit in shared memory,
     // else one CTA of 512

@@ -3,8 +3,9 @@
 Mixed path: eigen iteration (with double-float pole sums), forces, the hop
 selection and the rescale in FP64; coupling generator, Chebyshev propagation,
 coefficients and the determinant ratios in FP32 (a Gauss-Jordan elimination
-in registers for N <= 128, Ne <= 56, with the couplings in g also FP32; an
-LU with substitutions otherwise, or when a hop CTA size is set).  The
+in registers for N <= 128, Ne <= 56, with the rows past 128 in shared memory
+for N <= 256, Ne <= 112, the couplings in g also FP32; an LU with
+substitutions when a hop CTA size is set).  The
 propagator runs on the tensor cores (3xTF32, tcgen05) for N <= 128 and
 Ne <= 56 and as a register-tiled SIMT kernel otherwise, or when a propagator
 shape (4, G) is set; both are checked here.  Stated error per output (against the FP64 oracle,
@@ -86,8 +87,9 @@ def test_mixed_large_and_ragged_shapes(P, M, Ne, n):
     Ne > 56): one orbital past a 128-row tile (N = 129, Ne = 1), the M = 200
     bath with Ne = 100 and with a ragged Ne = 33, Ne = 80 at N = 161, the
     largest sizes (N = 256, Ne = 112) and N = 121 with Ne = 60 > 56.  The
-    SIMT propagator and the LU ratio kernel serve them; one step against the
-    oracle."""
+    SIMT propagator and the Gauss-Jordan kernel with shared-memory rows serve
+    them; one step against the oracle, and the hop probabilities against the
+    LU kernel's."""
     md = W.double_well(M, Ne)
     N = M + 1
     x, p = W.thermal_harmonic(n, md["mass"], md["par"][0], 0.01, 21)
@@ -97,6 +99,11 @@ def test_mixed_large_and_ragged_shapes(P, M, Ne, n):
     ctx = P.Context(md, n, precision=P.PREC_MIXED)
     assert ctx.kernel_shape()[0] == 4
     ctx.set_state(x, p, occ, C.astype(np.complex64))
+    g_gj = ctx.hop_probabilities(1.0)
+    ctx.set_kernel_shape(0, 0, 512)
+    g_lu = ctx.hop_probabilities(1.0)
+    ctx.set_kernel_shape(0, 0, 0)
+    assert np.abs(g_gj - g_lu).max() <= 2e-6 * max(np.abs(g_lu).max(), 1e-300)
     ctx.run(1.0, 1, seed=4)
     st = ctx.get_state()
     ctx.close()
@@ -108,11 +115,12 @@ def test_mixed_large_and_ragged_shapes(P, M, Ne, n):
         assert np.abs(st["C"][t].T - r["C"]).max() <= 1e-6
 
 
-@pytest.mark.parametrize("name", ["paper40", "dw100"])
+@pytest.mark.parametrize("name", ["paper40", "dw100", "dw200"])
 def test_mixed_hop_kernels_agree(P, name):
     """The mixed path's two ratio algorithms: the built-in Gauss-Jordan
-    elimination in registers (N <= 128, Ne <= 56) and the LU kernel (chosen
-    by a hop CTA size of 256 or 512 threads) each match the oracle's hop
+    elimination (in registers for N <= 128, Ne <= 56; with the rows past 128
+    in shared memory up to N = 256, Ne = 112) and the LU kernel (chosen by a
+    hop CTA size of 256 or 512 threads) each match the oracle's hop
     probabilities within the mixed bound, and so each other."""
     md, dt, shift = CASES[name]
     n = 8
