@@ -188,12 +188,13 @@ iesh_status iesh_get_live(iesh_ctx *ctx, int64_t *n_live);
  * Mixed contexts: cheb_ept must be 4 (each thread holds 4 orbitals x 4
  * electrons) and cheb_G * ceil(N/4) <= 256, with 8 * Np * (8 cheb_G + 1)
  * + 192 * Np bytes of shared memory (Np = N rounded up to a multiple of 4;
- * the second term stages W) at most 110 KiB.  hop_threads (256 or 512): threads of the LU hop kernel; 0
- * restores the built-in choice, which for mixed contexts with N <= 128 and
- * Ne <= 56 is a Gauss-Jordan elimination of all determinant ratios in
- * registers (the skip bound saves no work there and is not applied; its
- * FP32 ratios round differently from the LU's, about 1e-7 relative);
- * IESH_EINVAL otherwise.  The propagator shapes do not change results
+ * the second term stages W) at most 110 KiB.  hop_threads (256 or 512):
+ * threads of the LU hop kernel; 0 restores the built-in choice, which for
+ * mixed contexts is a Gauss-Jordan elimination of all determinant ratios,
+ * in registers for N <= 128 and Ne <= 56 and with the rows past 128 in
+ * shared memory up to N = 256, Ne = 112 (the skip bound saves no work
+ * there and is not applied; its FP32 ratios round differently from the
+ * LU's, about 1e-7 relative); IESH_EINVAL otherwise.  The propagator shapes do not change results
  * (each output keeps a fixed summation order).  Used by the autotuner of
  * the Python package. */
 iesh_status iesh_set_kernel_shape(iesh_ctx *ctx, int cheb_ept, int cheb_G, int hop_threads);
