@@ -560,12 +560,14 @@ __global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int
             __syncthreads();
             fetch(g + kCheb32WRing - 1);
             if (act) {
-                const float *wcol = wring + (g % kCheb32WRing) * kCheb32WRows * Np + j0;
+                // row i of the chunk: W at wp + i Np, t_k at tp + i W2 (+ 4 per
+                // row quad); walked by quads with the strides in registers
+                const float *wp = wring + (g % kCheb32WRing) * kCheb32WRows * Np + j0;
                 const int i0 = kCheb32WRows * c, rows = min(kCheb32WRows, N - i0);
-#pragma unroll 4
-                for (int ii = 0; ii < rows; ++ii) {
-                    const float4 w = *reinterpret_cast<const float4 *>(wcol + ii * Np);
-                    const float4 *tr = reinterpret_cast<const float4 *>(col + cheb32_row(i0 + ii, W2));
+                const float *tp = col + cheb32_row(i0, W2);  // i0 is a multiple of 4
+                auto row = [&](const float *wr_p, const float *tr_p) {
+                    const float4 w = *reinterpret_cast<const float4 *>(wr_p);
+                    const float4 *tr = reinterpret_cast<const float4 *>(tr_p);
                     float tv[NR];
 #pragma unroll
                     for (int h = 0; h < NV; ++h) {
@@ -580,7 +582,18 @@ __global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int
                     for (int r = 0; r < RQ; ++r)
 #pragma unroll
                         for (int q = 0; q < NR; ++q) y[r][q] = fmaf(wr[r], tv[q], y[r][q]);
+                };
+                const int Np2 = 2 * Np, Np3 = 3 * Np, Wd2 = 2 * W2, Wd3 = 3 * W2;
+                int u = 0;
+                for (; u + 4 <= rows; u += 4) {
+                    row(wp, tp);
+                    row(wp + Np, tp + W2);
+                    row(wp + Np2, tp + Wd2);
+                    row(wp + Np3, tp + Wd3);
+                    wp += 4 * Np;
+                    tp += 4 * W2 + 4;
                 }
+                for (int r = 0; u + r < rows; ++r) row(wp + r * Np, tp + r * W2);
             }
         }
         if (act) {
