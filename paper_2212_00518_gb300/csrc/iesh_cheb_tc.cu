@@ -100,35 +100,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
 
     // A operand: (2 / rho) W (rows j, columns i; stored [N][Np]) as TF32
     // high part (the FP32 value itself) and low part.  The scale folds the
-    // recurrence's 2 / rho into the contraction.  One warp writes one
-    // 128-byte core matrix at a time; each thread keeps 8 loads in flight
-    // (the loop is bound by the L2 latency otherwise).
+    // recurrence's 2 / rho into the contraction.  Every 16-byte piece (row
+    // j, 4 consecutive columns: one core-matrix row) is copied by cp.async
+    // into the high plane, all of them in flight at once, zero-filled past
+    // N rows and Np columns; each thread then scales its own pieces in
+    // place and forms their low parts.
     const float *__restrict__ W = reinterpret_cast<const float *>(s.scratch + t * s.scratch_stride);
     const double rho0 = s.cheb[t * kChebStride + 1];
     const float w2 = rho0 > 0.0 ? 2.0f / (float)rho0 : 0.0f;
-    {
-        const int kch = sh.Kp / 4, ncm = (kTcM / 8) * kch;
-        constexpr int kBatch = 8, kWarps = kTcThreads / 32;
-        for (int cm0 = warp; cm0 < ncm; cm0 += kBatch * kWarps) {
-            float v[kBatch];
-#pragma unroll
-            for (int b = 0; b < kBatch; ++b) {
-                const int cm = cm0 + b * kWarps;
-                const int rg = cm / kch, kc = cm - rg * kch;
-                const int row = rg * 8 + (lane >> 2), k = kc * 4 + (lane & 3);
-                v[b] = (cm < ncm && row < N && k < N) ? w2 * W[(int64_t)row * Np + k] : 0.0f;
-            }
-#pragma unroll
-            for (int b = 0; b < kBatch; ++b) {
-                const int cm = cm0 + b * kWarps;
-                if (cm < ncm) {
-                    const int rg = cm / kch, kc = cm - rg * kch;
-                    const int row = rg * 8 + (lane >> 2), k = kc * 4 + (lane & 3);
-                    *reinterpret_cast<float *>(Ahi + offA(sh, row, k)) = v[b];
-                    *reinterpret_cast<float *>(Alo + offA(sh, row, k)) = tc::lo_tf32(v[b]);
-                }
-            }
-        }
+    // piece pc: 8-row group pc / (8 kch), then column quad, then row, so that
+    // 8 consecutive threads fill one 128-byte core matrix
+    const int kch = sh.Kp / 4, npc = kTcM * kch;  // 16-byte pieces of a plane
+    auto piece = [&](int pc, int &row, int &kc) {
+        const int rg = pc / (8 * kch), w = pc - rg * 8 * kch;
+        kc = w >> 3;
+        row = 8 * rg + (w & 7);
+    };
+    for (int pc = tid; pc < npc; pc += kTcThreads) {
+        int row, kc;
+        piece(pc, row, kc);
+        const bool in = row < N && 4 * kc < Np;
+        cp_async16_zfill(Ahi + offA(sh, row, 4 * kc), in ? W + (int64_t)row * Np + 4 * kc : W, in ? 16u : 0u);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    for (int pc = tid; pc < npc; pc += kTcThreads) {
+        int row, kc;
+        piece(pc, row, kc);
+        float4 *h = reinterpret_cast<float4 *>(Ahi + offA(sh, row, 4 * kc));
+        const float4 v = *h;
+        const float4 a = make_float4(w2 * v.x, w2 * v.y, w2 * v.z, w2 * v.w);
+        *h = a;
+        *reinterpret_cast<float4 *>(Alo + offA(sh, row, 4 * kc)) =
+            make_float4(tc::lo_tf32(a.x), tc::lo_tf32(a.y), tc::lo_tf32(a.z), tc::lo_tf32(a.w));
     }
     // B operand rows (columns of T) beyond 2Ne and K entries beyond N stay zero
     {

@@ -83,6 +83,13 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
                  "l"(gsrc)
                  : "memory");
 }
+// The same with src_bytes (0 or 16) read and the rest zero-filled.
+__device__ __forceinline__ void cp_async16_zfill(void *smem_dst, const void *gsrc, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+                 "l"(gsrc), "r"(src_bytes)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 // Wait until at most `Pending` of this thread's committed groups are in flight.
 template <int Pending>
