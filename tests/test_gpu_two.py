@@ -241,10 +241,11 @@ def test_mixed_100_steps(P, name):
     assert np.abs(st["x"][same] - ref["x"][same]).max() <= 1e-6 * np.abs(ref["x"]).max()
 
 
-def test_mixed_large_system_lu_and_simt(P):
+def test_mixed_large_system_shared_rows_and_simt(P):
     """N = 142 orbitals, Ne = 71: past the register Gauss-Jordan kernel and
-    the tensor-core propagator, so the mixed path runs the LU hop kernel and
-    the SIMT FP32 propagator; one step against the oracle."""
+    the tensor-core propagator, so the mixed path runs the Gauss-Jordan
+    kernel with the rows past 128 in shared memory (its six-coordinate
+    variant) and the SIMT FP32 propagator; one step against the oracle."""
     md = W.two_orbital(140, seed=8, Ne=71)
     n, dt = 4, 5.0
     x, p, occ, C = W.two_orbital_state(md, n, 29, weight=0.6)
