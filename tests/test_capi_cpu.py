@@ -84,3 +84,25 @@ def test_invalid_two_orbital_models_rejected_without_device(lib):
                             None) == 1
     lib.iesh2_destroy(h)
     assert lib.iesh2_create(None, None, 0, 1, 0, None) == 1
+
+
+@pytest.mark.parametrize("N", [2, 21, 61, 101, 129, 201, 256])
+def test_tuner_shapes_within_documented_limits(N):
+    """The autotuner proposes only propagator shapes that iesh_set_kernel_shape
+    accepts by its documented limits: mixed (4, G) with G * ceil(N/4) <= 256
+    threads and 8 Np (8G + 1) + 192 Np bytes of shared memory (two buffers
+    and the ring of W rows) within 110 KiB for G > 1; FP64 (ept, G) with
+    ept in {1, 2} and G * N <= 1024."""
+    from paper_2212_00518_gb300 import tuning
+    from paper_2212_00518_gb300 import iesh as I
+    Np = -(-N // 4) * 4
+    for Ne in (1, N // 2, N - 1):
+        if Ne < 1:
+            continue
+        mixed = tuning.cheb_candidates(N, Ne, precision=I.PREC_MIXED)
+        assert mixed and all(ept == 4 for ept, _ in mixed)
+        for _, G in mixed:
+            assert G * -(-N // 4) <= 256
+            assert G == 1 or 8 * Np * (8 * G + 1) + 192 * Np <= 110 * 1024
+        fp64 = tuning.cheb_candidates(N, Ne, precision=I.PREC_FP64)
+        assert fp64 and all(ept in (1, 2) and G * N <= 1024 for ept, G in fp64)
