@@ -25,7 +25,7 @@
  *     diabatic evolution split symmetrically, exp(-i H(x_1) dt/2)
  *     exp(-i H(x_0) dt/2), written in the adiabatic frame as
  *     c <- exp(-i L_1 dt/2) Q_1^T Q_0 exp(-i L_0 dt/2) c with the dense
- *     eigenvector matrices Q_0, Q_1 of the two ends of the step (reading R9).
+ *     eigenvector matrices Q_0, Q_1 of the two ends of the step (reading R15).
  *
  * Readings of the paper that the code takes (the paper is silent or garbled):
  *   R1 NAC sign: d_jk = <j|d_x k> = T_jk / (lambda_k - lambda_j), the TDSE is
@@ -44,12 +44,22 @@
  *      generator stored for the next step uses the post-hop velocity.
  *   R8 Gauss-Legendre split discretisation: M/2 nodes in each half, weights
  *      positive, V_k = sqrt(Gamma / 2 pi) sqrt(w_k) f(x).
- *   R9 diabatic-basis propagation (an alternative to the exponential of the
+ *   R9 the hop-probability upper bound of Sec. II C is taken as
+ *      2 dt |v| sum_{a,m} |d_{m,s_a}| / |det S|; only the GPU path uses it.
+ *   R10 desorption-model coupling factor f(x) = (1-q)/2 (1 - tanh((x-x~)/a~))
+ *      + q (Sec. III C prints its brackets garbled).
+ *   R11 impurity population: both the occupied-surface value
+ *      sum_{i in s} q0_i^2 and the wavefunction value sum_e |sum_i q0_i C_ie|^2.
+ *   R12 thermal electrons at fixed Ne: exact canonical sampling.
+ *   R13 bias: two leads, each discretised with its own split point +-V/2.
+ *   R14 Morse + image-charge adsorbate with a Gaussian coupling factor (the
+ *      scattering workload; constants supplied by the caller).
+ *   R15 diabatic-basis propagation (an alternative to the exponential of the
  *      averaged adiabatic generator): the electronic Hamiltonian in the
  *      fixed diabatic basis is H(x); over a step the propagator is the
  *      symmetric product of the half-step exponentials at the two ends,
  *      which is second order in dt like R3 and exact for frozen nuclei.
- *   R10 two adsorbate orbitals over six nuclear coordinates: one mass for
+ *   R16 two adsorbate orbitals over six nuclear coordinates: one mass for
  *      all coordinates, a harmonic restraint U0 = m w^2 |x - x0|^2 / 2, the
  *      step of R3-R7 with the velocity-projected couplings v . d in the
  *      generator and the hop probabilities, the momentum change of a hop
@@ -463,7 +473,7 @@ int orc_propagate(int N, int Ne, const double *lam0, const double *d0, double v0
     return rc;
 }
 
-/* Diabatic-basis propagator variant (reading R9) in the adiabatic frame:
+/* Diabatic-basis propagator variant (reading R15) in the adiabatic frame:
  * C <- exp(-i L1 dt/2) O exp(-i L0 dt/2) C with O = Q1^T Q0, the overlaps of
  * the adiabatic orbitals at the end of the step with those at its start
  * (Q[k*N + i] = component k of orbital i).  C is [N][Ne]. */
@@ -1138,7 +1148,7 @@ int orc_eocc(int M, int Ne, const double *eps, const double *sqw, const double *
 }
 
 /* ------------------------------------------------------------------------ */
-/* Two adsorbate orbitals over six nuclear coordinates (reading R10): the   */
+/* Two adsorbate orbitals over six nuclear coordinates (reading R16): the   */
 /* electronic Hamiltonian of the occupied-energy model (eocc_build) plus a  */
 /* harmonic restraint U0 = m w^2 |x - x0|^2 / 2                             */
 /* on every coordinate (one mass).  The same IESH step as traj_step in six  */

@@ -356,7 +356,7 @@ def run(model_or_bound, x, p, occ, C, dt, n_steps, seed, step0=0, brute=False,
 
 
 def propagate_overlap(lam0, Q0, lam1, Q1, dt, C):
-    """C[N][Ne] <- exp(-i L1 dt/2) Q1^T Q0 exp(-i L0 dt/2) C (reading R9)."""
+    """C[N][Ne] <- exp(-i L1 dt/2) Q1^T Q0 exp(-i L0 dt/2) C (reading R15)."""
     N = len(lam0)
     C = _c(C, np.complex128).copy()
     lib().orc_propagate_overlap(N, C.shape[1], _d(_c(lam0)), _d(_c(Q0)), _d(_c(lam1)), _d(_c(Q1)),

@@ -278,7 +278,7 @@ def _H_diabatic(md, B, x):
 
 
 def test_overlap_propagator_is_the_diabatic_strang_product():
-    """Reading R9: in the diabatic basis the overlap propagator is
+    """Reading R15: in the diabatic basis the overlap propagator is
     exp(-i H(x1) dt/2) exp(-i H(x0) dt/2); checked against scipy's expm of
     the dense diabatic Hamiltonians, with the adiabatic frames of both ends."""
     md = W.double_well_paper(16)
@@ -484,6 +484,57 @@ def test_boltzmann_sampler_moments():
     assert abs(xs[:, 0].mean()) < 5 * sx / math.sqrt(len(xs))
     assert abs(xs[:, 0].std() / sx - 1) < 5 / math.sqrt(2 * len(xs))
     assert abs(xs[:, 1].std() / sp - 1) < 5 / math.sqrt(2 * len(xs))
+
+
+def _wigner_moments(m, w, x_eq, kT, n, seed):
+    """Sample variances of x and p from the oracle's Wigner branch."""
+    xs = np.array([O.sample_nuclear(seed, t, m, w, x_eq, kT, wigner=True) for t in range(n)])
+    return xs[:, 0].mean(), xs[:, 0].var(), xs[:, 1].var()
+
+
+def test_wigner_sampler_printed_Q_at_300K():
+    """Sec. III C: at 300 K the Wigner density of the m = 10.54 u Morse well is
+    the classical Boltzmann density widened by Q ~ 1.9 (printed to two digits).
+    The factor is read from the sampler's own variances, var(x) m w^2 / kT and
+    var(p) / (m kT), with w from finite differences of the model's U0."""
+    gold = {r[0]: (float(r[1]), float(r[2])) for r in _golden("desorption_model_pins.txt")}
+    md = W.desorption(mass_u=10.54)
+    x0, m = md["par"][1], md["mass"]
+    hh = 1e-4
+    w = math.sqrt((O.model_eval(md, x0 + hh)[1] - O.model_eval(md, x0 - hh)[1]) / (2 * hh) / m)
+    kT = 300.0 * W.KB_HARTREE_PER_K
+    n = 100000
+    mean, vx, vp = _wigner_moments(m, w, x0, kT, n, 11)
+    sig = math.sqrt(2.0 / n)  # relative standard error of a Gaussian sample variance
+    val, tol = gold["wigner_Q_10p54u"]
+    Qx = vx * m * w * w / kT
+    Qp = vp / (m * kT)
+    assert abs(Qx - val) < tol + 5 * sig * val, Qx
+    assert abs(Qp - val) < tol + 5 * sig * val, Qp
+    assert abs(mean - x0) < 5 * math.sqrt(vx / n)
+
+
+def test_wigner_sampler_limits():
+    """High temperature: the Wigner density becomes the classical Boltzmann
+    density (Q -> 1).  Low temperature: it becomes the harmonic ground state,
+    var(x) = 1 / (2 m w) and var(p) = m w / 2 (hbar = 1)."""
+    m, w = 2000.0, 0.002
+    n = 40000
+    sig = 5 * math.sqrt(2.0 / n)
+    kT = 200 * w  # Q = 1 + (w/kT)^2 / 12 + ... = 1.000002
+    _, vx, vp = _wigner_moments(m, w, 0.0, kT, n, 12)
+    assert abs(vx * m * w * w / kT - 1) < sig
+    assert abs(vp / (m * kT) - 1) < sig
+    kT = w / 60  # coth(30) = 1 to 1e-25
+    _, vx, vp = _wigner_moments(m, w, 0.0, kT, n, 13)
+    assert abs(vx * 2 * m * w - 1) < sig
+    assert abs(vp * 2 / (m * w) - 1) < sig
+    # between the limits the factor grows monotonically as kT falls
+    qs = []
+    for kT in (2 * w, w, 0.5 * w):
+        _, vx, _ = _wigner_moments(m, w, 0.0, kT, n, 14)
+        qs.append(vx * m * w * w / kT)
+    assert qs[0] < qs[1] < qs[2]
 
 
 # ------------------------------------------------------- occupied energy
