@@ -180,6 +180,25 @@ def two_orbital(M=40, seed=5, mass=2000.0, omega=0.01, Ne=None, band=(-0.5, 0.5)
                 omega=float(omega), x0=np.asarray(wl["R"]).copy())
 
 
+def two_orbital_profiled(M=40, seed=5, center=(-0.2, 0.25), width=(0.3, 0.15), **kw):
+    """The two-orbital dynamics model with an own Lorentzian bath profile for
+    each adsorbate orbital (centre and width in hartree, per orbital), so
+    that the two border vectors of the Hamiltonian are not parallel."""
+    md = two_orbital(M=M, seed=seed, **kw)
+    md["profile"] = dict(center=[float(c) for c in center], width=[float(w) for w in width])
+    return md
+
+
+def random_symmetric(B, n, seed, spread=1.0):
+    """B random symmetric n x n matrices [B][n][n] (Gaussian entries, a
+    diagonal spread out by `spread` so that eigenvalues are distinct)."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((B, n, n))
+    A = 0.5 * (A + np.transpose(A, (0, 2, 1)))
+    A += spread * np.eye(n)[None] * np.linspace(-1.0, 1.0, n)[None, :, None] * n ** 0.5
+    return A
+
+
 def two_orbital_state(md, n, seed, kT=0.01, occ="random", weight=0.5):
     """Thermal positions/momenta around x0 ([n][6]), occupations and
     coefficients ([n][Ne][N], N = M + 2)."""

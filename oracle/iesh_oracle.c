@@ -1162,6 +1162,9 @@ typedef struct {
     const double *eps, *sqw, *Vbar, *R, *th; /* bath, couplings, theta[16] */
     double mass, omega;
     const double *x0;                        /* [6] restraint centres */
+    /* own bath profiles (reading R17): Vk[a][k] couples orbital a to bath
+     * state k at f_a = 1; NULL: Vbar_a sqw_k for both (reading R16) */
+    const double *Vk;
 } orc_model2;
 
 typedef struct {
@@ -1172,7 +1175,44 @@ typedef struct {
     double *d;          /* [6][N][N] */
     uint32_t status;
     int64_t hops, frustrated;
+    double *Qprev;      /* [N][N] eigenvectors of the previous call (R17 gauge) */
+    int have_prev;
 } orc_traj2;
+
+/* Electronic Hamiltonian of the two-orbital model with its own bath profile
+ * for each orbital (reading R17): H_aa = h_a(x), H_{a,2+k} = Vk[a][k] f_a(x),
+ * H_{2+k,2+k} = eps_k, and dH/dx_y (6 matrices); c[a] = f_a(x) |Vk[a]|, the
+ * coupling amplitude of orbital a. */
+static void gen2_build(const orc_model2 *md, const double *x, double *H, double *dHdx, double *c)
+{
+    const int M = md->M, N = M + 2;
+    const double *th = md->th, *R = md->R;
+    memset(H, 0, sizeof(double) * N * N);
+    memset(dHdx, 0, sizeof(double) * 6 * N * N);
+    for (int a = 0; a < 2; a++) {
+        double h = th[a];
+        for (int al = 0; al < 6; al++) h += th[2 + 6 * a + al] * x[al];
+        H[a * N + a] = h;
+        for (int al = 0; al < 6; al++) dHdx[al * N * N + a * N + a] = th[2 + 6 * a + al];
+        const double sg = th[14 + a];
+        double r2 = 0.0;
+        for (int q = 0; q < 3; q++) r2 += (x[3 * a + q] - R[3 * a + q]) * (x[3 * a + q] - R[3 * a + q]);
+        const double f = exp(-0.5 * r2 / (sg * sg));
+        double nv = 0.0;
+        for (int k = 0; k < M; k++) {
+            const double V = md->Vk[a * M + k] * f;
+            nv += md->Vk[a * M + k] * md->Vk[a * M + k];
+            H[a * N + 2 + k] = H[(2 + k) * N + a] = V;
+            for (int q = 0; q < 3; q++) {
+                const double dv = V * (-(x[3 * a + q] - R[3 * a + q]) / (sg * sg));
+                dHdx[(3 * a + q) * N * N + a * N + 2 + k] = dv;
+                dHdx[(3 * a + q) * N * N + (2 + k) * N + a] = dv;
+            }
+        }
+        c[a] = f * sqrt(nv);
+    }
+    for (int k = 0; k < M; k++) H[(2 + k) * N + 2 + k] = md->eps[k];
+}
 
 static void traj2_eigen(const orc_model2 *md, orc_traj2 *t)
 {
@@ -1180,20 +1220,42 @@ static void traj2_eigen(const orc_model2 *md, orc_traj2 *t)
     double *H = malloc(sizeof(double) * N * N), *V = malloc(sizeof(double) * N * N);
     double *ev = malloc(sizeof(double) * N), *dHx = malloc(sizeof(double) * 6 * N * N);
     int *idx = malloc(sizeof(int) * N);
-    eocc_build(M, md->eps, md->sqw, md->Vbar, md->R, t->x, md->th, H, dHx, NULL);
-    /* coupling amplitudes c_a = Vbar_a f_a(x) = H[a][2] / sqw[0], read before
-     * the Jacobi sweeps overwrite H */
-    const double c1 = H[0 * N + 2] / md->sqw[0], c2 = H[1 * N + 2] / md->sqw[0];
+    double c1, c2;
+    if (md->Vk) {
+        double cc[2];
+        gen2_build(md, t->x, H, dHx, cc);
+        c1 = cc[0];
+        c2 = cc[1];
+    } else {
+        eocc_build(M, md->eps, md->sqw, md->Vbar, md->R, t->x, md->th, H, dHx, NULL);
+        /* coupling amplitudes c_a = Vbar_a f_a(x) = H[a][2] / sqw[0], read
+         * before the Jacobi sweeps overwrite H */
+        c1 = H[0 * N + 2] / md->sqw[0];
+        c2 = H[1 * N + 2] / md->sqw[0];
+    }
     if (orc_jacobi_sym(N, H, ev, V) != 0) t->status |= ORC_ST_JACOBI_NONCONV;
     for (int i = 0; i < N; i++) idx[i] = i;
     for (int i = 0; i < N; i++)
         for (int j = i + 1; j < N; j++)
             if (ev[idx[j]] < ev[idx[i]]) { int tt = idx[i]; idx[i] = idx[j]; idx[j] = tt; }
+    /* gauge: R16, the combination c1 Q_0j + c2 Q_1j >= 0; R17 (own bath
+     * profiles), after the first call: overlap with the previous call's
+     * eigenvector j >= 0 */
+    const int by_overlap = md->Vk && t->Qprev && t->have_prev;
     for (int j = 0; j < N; j++) {
         const int c = idx[j];
-        const double sgn = (c1 * V[0 * N + c] + c2 * V[1 * N + c]) < 0.0 ? -1.0 : 1.0;
+        double key = c1 * V[0 * N + c] + c2 * V[1 * N + c];
+        if (by_overlap) {
+            key = 0.0;
+            for (int r = 0; r < N; r++) key += t->Qprev[r * N + j] * V[r * N + c];
+        }
+        const double sgn = key < 0.0 ? -1.0 : 1.0;
         t->lam[j] = ev[c];
         for (int r = 0; r < N; r++) t->Q[r * N + j] = sgn * V[r * N + c];
+    }
+    if (md->Vk && t->Qprev) {
+        memcpy(t->Qprev, t->Q, sizeof(double) * N * N);
+        t->have_prev = 1;
     }
     /* T^a = Q^T dH/dx_a Q, d^a_jk = T^a_jk / (lam_k - lam_j); forces */
     double *T = malloc(sizeof(double) * N * N), *tmp = malloc(sizeof(double) * N * N);
@@ -1302,12 +1364,13 @@ static void traj2_step(const orc_model2 *md, orc_traj2 *t, double dt, uint64_t s
 /* Two-orbital trajectories: x, p [n][6]; occ [n][Ne]; C [n][N][Ne], N = M + 2.
  * Returns final state, forces F [n][6], eigenvalues lam [n][N] (optional),
  * status, hops, frustrated. */
-int orc_run2(int M, int Ne, const double *eps, const double *sqw, const double *Vbar, const double *R,
-             const double *th, double mass, double omega, const double *x0, int64_t n_traj, double *x,
-             double *p, double *F, int *occ, cplx *C, double dt, int64_t n_steps, uint64_t seed,
-             uint32_t *status, int64_t *hops, int64_t *frustrated, double *lam_out)
+static int run2_any(const orc_model2 *mdp, int64_t n_traj, double *x, double *p, double *F, int *occ,
+                    cplx *C, double dt, int64_t n_steps, uint64_t seed, uint32_t *status, int64_t *hops,
+                    int64_t *frustrated, double *lam_out, double *Qad_out)
 {
-    orc_model2 md = {M, Ne, eps, sqw, Vbar, R, th, mass, omega, x0};
+    const orc_model2 md = *mdp;
+    const int M = md.M, Ne = md.Ne;
+    const double mass = md.mass;
     const int N = M + 2;
     orc_traj2 t;
     t.occ = malloc(sizeof(int) * Ne);
@@ -1315,7 +1378,9 @@ int orc_run2(int M, int Ne, const double *eps, const double *sqw, const double *
     t.lam = malloc(sizeof(double) * N);
     t.Q = malloc(sizeof(double) * N * N);
     t.d = malloc(sizeof(double) * 6 * N * N);
+    t.Qprev = md.Vk ? malloc(sizeof(double) * N * N) : NULL;
     for (int64_t i = 0; i < n_traj; i++) {
+        t.have_prev = 0;
         memcpy(t.x, x + 6 * i, sizeof(double) * 6);
         memcpy(t.p, p + 6 * i, sizeof(double) * 6);
         memcpy(t.occ, occ + i * Ne, sizeof(int) * Ne);
@@ -1334,9 +1399,38 @@ int orc_run2(int M, int Ne, const double *eps, const double *sqw, const double *
         hops[i] = t.hops;
         frustrated[i] = t.frustrated;
         if (lam_out) memcpy(lam_out + i * N, t.lam, sizeof(double) * N);
+        if (Qad_out) {
+            memcpy(Qad_out + (2 * i + 0) * N, t.Q, sizeof(double) * N);
+            memcpy(Qad_out + (2 * i + 1) * N, t.Q + N, sizeof(double) * N);
+        }
     }
-    free(t.occ); free(t.C); free(t.lam); free(t.Q); free(t.d);
+    free(t.occ); free(t.C); free(t.lam); free(t.Q); free(t.d); free(t.Qprev);
     return 0;
+}
+
+int orc_run2(int M, int Ne, const double *eps, const double *sqw, const double *Vbar, const double *R,
+             const double *th, double mass, double omega, const double *x0, int64_t n_traj, double *x,
+             double *p, double *F, int *occ, cplx *C, double dt, int64_t n_steps, uint64_t seed,
+             uint32_t *status, int64_t *hops, int64_t *frustrated, double *lam_out)
+{
+    orc_model2 md = {M, Ne, eps, sqw, Vbar, R, th, mass, omega, x0, NULL};
+    return run2_any(&md, n_traj, x, p, F, occ, C, dt, n_steps, seed, status, hops, frustrated,
+                    lam_out, NULL);
+}
+
+/* The same with an own bath profile for each orbital (reading R17): Vk
+ * [2][M] couples orbital a to bath state k at f_a = 1.  Eigenvector gauge:
+ * the rule of R16 (with c_a = f_a |Vk[a]|) at the start, then continuity
+ * (overlap with the previous step's eigenvector >= 0).  Qad_out [n][2][N]
+ * (optional): the adsorbate rows of the final eigenvectors. */
+int orc_run2g(int M, int Ne, const double *eps, const double *Vk, const double *R, const double *th,
+              double mass, double omega, const double *x0, int64_t n_traj, double *x, double *p,
+              double *F, int *occ, cplx *C, double dt, int64_t n_steps, uint64_t seed, uint32_t *status,
+              int64_t *hops, int64_t *frustrated, double *lam_out, double *Qad_out)
+{
+    orc_model2 md = {M, Ne, eps, NULL, NULL, R, th, mass, omega, x0, Vk};
+    return run2_any(&md, n_traj, x, p, F, occ, C, dt, n_steps, seed, status, hops, frustrated,
+                    lam_out, Qad_out);
 }
 
 /* Eigenpairs (gauge-fixed), NAC tensor d [6][N][N] and forces [6] at one
@@ -1345,7 +1439,7 @@ int orc_eigen2(int M, int Ne, const double *eps, const double *sqw, const double
                const double *th, double mass, double omega, const double *x0, const double *x,
                const int *occ, double *lam, double *Q, double *d, double *F)
 {
-    orc_model2 md = {M, Ne, eps, sqw, Vbar, R, th, mass, omega, x0};
+    orc_model2 md = {M, Ne, eps, sqw, Vbar, R, th, mass, omega, x0, NULL};
     const int N = M + 2;
     orc_traj2 t;
     memcpy(t.x, x, sizeof(double) * 6);
@@ -1354,10 +1448,69 @@ int orc_eigen2(int M, int Ne, const double *eps, const double *sqw, const double
     t.Q = Q;
     t.d = d;
     t.status = 0;
+    t.Qprev = NULL;
+    t.have_prev = 0;
     traj2_eigen(&md, &t);
     memcpy(F, t.F, sizeof(double) * 6);
     (void)N;
     return (int)t.status;
+}
+
+/* Own-profile model (reading R17) at one geometry: eigenpairs signed by the
+ * overlap with Qref [N][N] (the previous step's eigenvectors; NULL: the
+ * rule of R16), NAC tensor d [6][N][N] and forces F [6]. */
+int orc_eigen2g(int M, int Ne, const double *eps, const double *Vk, const double *R, const double *th,
+                double mass, double omega, const double *x0, const double *x, const int *occ,
+                const double *Qref, double *lam, double *Q, double *d, double *F)
+{
+    orc_model2 md = {M, Ne, eps, NULL, NULL, R, th, mass, omega, x0, Vk};
+    const int N = M + 2;
+    orc_traj2 t;
+    memcpy(t.x, x, sizeof(double) * 6);
+    t.occ = (int *)occ;
+    t.lam = lam;
+    t.Q = Q;
+    t.d = d;
+    t.status = 0;
+    t.Qprev = malloc(sizeof(double) * N * N);
+    t.have_prev = Qref != NULL;
+    if (Qref) memcpy(t.Qprev, Qref, sizeof(double) * N * N);
+    traj2_eigen(&md, &t);
+    memcpy(F, t.F, sizeof(double) * 6);
+    free(t.Qprev);
+    return (int)t.status;
+}
+
+/* Dense symmetric eigenproblem of each of B matrices A [B][n][n] (the
+ * definition: A v = lambda v): eigenvalues ascending lam [B][n] and unit
+ * eigenvectors as rows V [B][n][n] (row j belongs to lam_j), each signed so
+ * that its component of largest magnitude (the first on a tie) is positive.
+ * The oracle's own cyclic Jacobi method. */
+int orc_syev(int64_t B, int n, const double *A, double *lam, double *V)
+{
+    double *H = malloc(sizeof(double) * n * n), *Z = malloc(sizeof(double) * n * n);
+    double *ev = malloc(sizeof(double) * n);
+    int *idx = malloc(sizeof(int) * n);
+    int rc = 0;
+    for (int64_t b = 0; b < B; b++) {
+        memcpy(H, A + (size_t)b * n * n, sizeof(double) * n * n);
+        if (orc_jacobi_sym(n, H, ev, Z) != 0) rc = -1;
+        for (int i = 0; i < n; i++) idx[i] = i;
+        for (int i = 0; i < n; i++)
+            for (int j = i + 1; j < n; j++)
+                if (ev[idx[j]] < ev[idx[i]]) { int tt = idx[i]; idx[i] = idx[j]; idx[j] = tt; }
+        for (int j = 0; j < n; j++) {
+            const int c = idx[j];
+            int big = 0;
+            for (int r = 1; r < n; r++)
+                if (fabs(Z[r * n + c]) > fabs(Z[big * n + c])) big = r;
+            const double sgn = Z[big * n + c] < 0.0 ? -1.0 : 1.0;
+            lam[(size_t)b * n + j] = ev[c];
+            for (int r = 0; r < n; r++) V[((size_t)b * n + j) * n + r] = sgn * Z[r * n + c];
+        }
+    }
+    free(H); free(Z); free(ev); free(idx);
+    return rc;
 }
 
 /* Determinant through an output pointer (out[0] real, out[1] imaginary). */

@@ -85,6 +85,13 @@ def lib():
                                  ctypes.c_double, _dp, _dp, _ip, _dp, _dp, _dp, _dp]
         L.orc_eocc.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_int64,
                                _dp, _dp, _dp, _dp, _dp]
+        L.orc_run2g.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_double,
+                                ctypes.c_double, _dp, ctypes.c_int64, _dp, _dp, _dp, _ip, _vp,
+                                ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, _u32p, _i64p, _i64p,
+                                _dp, _dp]
+        L.orc_eigen2g.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_double,
+                                  ctypes.c_double, _dp, _dp, _ip, _dp, _dp, _dp, _dp, _dp]
+        L.orc_syev.argtypes = [ctypes.c_int64, ctypes.c_int, _dp, _dp, _dp]
         _lib = L
     return _lib
 
@@ -370,9 +377,39 @@ def _two_bath(md):
     return _c(eps), _c(sqw)
 
 
-def eigen2(md, x, occ):
-    """Two-orbital model at x[6]: lam[N], Q[N][N], d[6][N][N], F[6] (N = M + 2)."""
+def two_couplings(md, eps, sqw):
+    """Vk[2][M]: coupling of adsorbate orbital a to bath state k at f_a = 1.
+    Without a "profile" entry both orbitals couple as Vbar_a sqrt(w_k)
+    (parallel border vectors, reading R16); with profile = dict(center,
+    width) orbital a's coupling carries its own Lorentzian energy profile,
+    Vbar_a sqrt(w_k) / sqrt(1 + ((eps_k - center_a) / width_a)^2)
+    (reading R17)."""
+    Vbar = _c(md["Vbar"])
+    prof = md.get("profile")
+    if prof is None:
+        return np.vstack([Vbar[0] * sqw, Vbar[1] * sqw])
+    out = np.zeros((2, eps.shape[0]))
+    for a in range(2):
+        u = (eps - prof["center"][a]) / prof["width"][a]
+        out[a] = Vbar[a] * sqw / np.sqrt(1.0 + u * u)
+    return out
+
+
+def eigen2(md, x, occ, Qref=None):
+    """Two-orbital model at x[6]: lam[N], Q[N][N], d[6][N][N], F[6] (N = M + 2).
+    With an own bath profile per orbital (md["profile"], reading R17) the
+    eigenvectors are signed by their overlap with Qref [N][N] (the previous
+    step's) when given, else by the rule of R16."""
     eps, sqw = _two_bath(md)
+    if md.get("profile") is not None:
+        N = md["M"] + 2
+        Vk = _c(two_couplings(md, eps, sqw))
+        lam, Q, d, F = np.zeros(N), np.zeros((N, N)), np.zeros((6, N, N)), np.zeros(6)
+        lib().orc_eigen2g(md["M"], md["Ne"], _d(eps), _d(Vk), _d(_c(md["R"])), _d(_c(md["theta"])),
+                          float(md["mass"]), float(md["omega"]), _d(_c(md["x0"])), _d(_c(x)),
+                          _c(occ, np.int32).ctypes.data_as(_ip),
+                          None if Qref is None else _d(_c(Qref)), _d(lam), _d(Q), _d(d), _d(F))
+        return lam, Q, d, F
     N = md["M"] + 2
     lam, Q, d, F = np.zeros(N), np.zeros((N, N)), np.zeros((6, N, N)), np.zeros(6)
     lib().orc_eigen2(md["M"], md["Ne"], _d(eps), _d(sqw), _d(_c(md["Vbar"])), _d(_c(md["R"])),
@@ -395,6 +432,16 @@ def run2(md, x, p, occ, C, dt, n_steps, seed):
     hops = np.zeros(n, np.int64)
     frus = np.zeros(n, np.int64)
     lam = np.zeros((n, N))
+    if md.get("profile") is not None:
+        Vk = _c(two_couplings(md, eps, sqw))
+        Qad = np.zeros((n, 2, N))
+        lib().orc_run2g(md["M"], md["Ne"], _d(eps), _d(Vk), _d(_c(md["R"])), _d(_c(md["theta"])),
+                        float(md["mass"]), float(md["omega"]), _d(_c(md["x0"])), n, _d(x), _d(p),
+                        _d(F), occ.ctypes.data_as(_ip), C.ctypes.data, float(dt), int(n_steps),
+                        int(seed), status.ctypes.data_as(_u32p), hops.ctypes.data_as(_i64p),
+                        frus.ctypes.data_as(_i64p), _d(lam), _d(Qad))
+        return dict(x=x, p=p, F=F, occ=occ, C=C, status=status, hops=hops, frustrated=frus,
+                    lam=lam, Qad=Qad)
     lib().orc_run2(md["M"], md["Ne"], _d(eps), _d(sqw), _d(_c(md["Vbar"])), _d(_c(md["R"])),
                    _d(_c(md["theta"])), float(md["mass"]), float(md["omega"]), _d(_c(md["x0"])), n,
                    _d(x), _d(p), _d(F), occ.ctypes.data_as(_ip), C.ctypes.data, float(dt), int(n_steps),
@@ -420,3 +467,16 @@ def eocc(eps, sqw, Vbar, R, x, theta, Ne, grad=True):
                         _d(theta), _d(E), _d(dx) if grad else None, _d(dth) if grad else None)
     assert rc == 0
     return E, dx, dth
+
+
+# -------------------------------------------------- dense symmetric eigenproblem
+def syev(A):
+    """Eigenvalues ascending lam [B][n] and unit eigenvectors as rows V
+    [B][n][n] of the symmetric matrices A [B][n][n] (cyclic Jacobi), each
+    eigenvector signed so that its largest-magnitude component is positive."""
+    A = _c(A)
+    B, n, _ = A.shape
+    lam = np.zeros((B, n))
+    V = np.zeros((B, n, n))
+    rc = lib().orc_syev(B, n, _d(A), _d(lam), _d(V))
+    return lam, V, rc
