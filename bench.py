@@ -36,10 +36,14 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_NOMINAL_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 SIMT at the maximum SM clock
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 tensor rate
-# DRAM bytes (read + write) per trajectory of the dominant kernel, from the ncu capture in
-# profiles/iesh_fp64_step_M100.md (1024-trajectory launch, scaled per trajectory; the
-# traffic is per-trajectory W and C streams, so it grows in proportion to the batch).
-KCHEB_FP64_TRAFFIC_PER_TRAJ = (169.147904e6 + 48.495360e6) / 1024
+# DRAM bytes (read + write) per trajectory of one launch of the dominant kernel, by
+# (kernel, N, Ne), from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the named batch size, divided by it: the traffic is per-trajectory streams of C and
+# W, so it scales with the batch.  A shape or kernel not in the table reports null.
+DRAM_BYTES_PER_TRAJ = {
+    # k_cheb<2, double>, 1024-trajectory capture
+    ("k_cheb", 101, 50): (169.147904e6 + 48.495360e6) / 1024,
+}
 
 
 def measured_peaks():
@@ -127,9 +131,26 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- replicas
-def replica_seed(seed, rank):
-    """Philox key of a replica: independent streams per rank."""
-    return seed + rank
+def replica_traj_base(rank, n_per_rank):
+    """Global id of a replica's first trajectory.  Every rank uses the same
+    Philox key; its trajectories draw with global ids rank * n_per_rank + t,
+    so an N-GPU job computes the same trajectories as one GPU holding the
+    whole batch."""
+    return rank * n_per_rank
+
+
+def replica_slice(rank, n_per_rank):
+    """The rank's trajectories within the whole job's batch."""
+    return slice(rank * n_per_rank, (rank + 1) * n_per_rank)
+
+
+def replica_state(M, n, world, rank, dt=1.0):
+    """The rank's slice of the whole job's seeded initial state (the batch of
+    n * world trajectories that one GPU would run)."""
+    md, kT, dt = workload(M, n * world, dt)
+    x, p, occ, C = initial_state(md, kT, n * world, seed=1000)
+    sl = replica_slice(rank, n)
+    return md, dt, x[sl].copy(), p[sl].copy(), occ[sl].copy(), C[sl].copy()
 
 
 def aggregate(ms_local, e2e_local, n_per_rank, steps, world, dist=None, device="cpu"):
@@ -146,6 +167,23 @@ def aggregate(ms_local, e2e_local, n_per_rank, steps, world, dist=None, device="
 
 
 # ------------------------------------------------------------- our arm
+def useful_flops(N, Ne):
+    """Algorithmic work of one trajectory-step (flops): unitary application
+    8 N^2 Ne, ratio GEMM 8 (N - Ne) Ne^2, overlap LU (8/3) Ne^3, warm-started
+    secular eigensolver about 8 x 3 N^2, coupling generation about 10 N^2."""
+    prop = 8.0 * N * N * Ne
+    step = prop + 8.0 * (N - Ne) * Ne * Ne + 8.0 / 3.0 * Ne ** 3 + 24.0 * N * N + 10.0 * N * N
+    return prop, step
+
+
+def tf32_peak():
+    bf16 = measured_peaks().get("bf16_tflops")
+    if bf16:
+        return bf16 * TF32_PER_BF16, ("of measured: MEASURED_PEAKS.json bf16_tflops x nominal "
+                                      "TF32/BF16 ratio 1.1/2.25")
+    return 1900.0 * TF32_PER_BF16, "of fallback: 1.9 PFLOP/s bf16 x 1.1/2.25"
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -163,21 +201,25 @@ def run_ours(args):
         B.build()
     if world > 1:
         dist.barrier()
-
-    md, kT, dt = workload(args.M, args.n_traj, args.dt)
-    n = args.n_traj
-    x, p, occ, C = initial_state(md, kT, n, seed=1000 + rank)
     stream = torch.cuda.current_stream()
-    seed = replica_seed(args.seed, rank)
+    seed = args.seed
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    def measure(precision, sample_clocks, propagator=0):
+    def agg(ms=0.0, sec=0.0):
+        a = aggregate(ms, sec, 1, 1, world, dist if world > 1 else None, "cuda")
+        return a["ms"], a["e2e_s"]
+
+    def config_state(M, n):
+        return replica_state(M, n, world, rank, args.dt)
+
+    def measure(md, dt, x, p, occ, C, precision, sample_clocks=False, propagator=0, e2e=True):
+        n = x.shape[0]
         c = P.Context(md, n, precision=precision, stream=stream.cuda_stream, propagator=propagator,
-                      skip_bound=args.skip_bound)
+                      skip_bound=args.skip_bound, traj_base=replica_traj_base(rank, n))
         c.set_state(x, p, occ, C if precision == P.PREC_FP64 else C.astype(np.complex64))
         for _ in range(args.warmup):
             c.run(dt, 1, seed)
@@ -196,149 +238,196 @@ def run_ours(args):
         barrier()
         if clk:
             clk.__exit__()
-        ms_ = ev0.elapsed_time(ev1)
-        prof_ = c.profile_read()
+        ms, _ = agg(ms=ev0.elapsed_time(ev1))
+        prof = c.profile_read()
         c.profile(False)
-        ms_ = aggregate(ms_, 0.0, n, args.steps, world, dist if world > 1 else None, "cuda")["ms"]
-        return c, ms_, prof_, clk
+        out = dict(ms=ms, prof=prof, K=c.propagator_terms(), tc=c.kernel_shape()[0] == 8,
+                   status=c.get_state()["status"], clocks=clk.summary() if clk else None, n=n)
+        if e2e:
+            # end to end through the C-ABI: every step loads the whole state from a
+            # pinned host checkpoint, advances one step and writes it back
+            blob = torch.from_numpy(c.checkpoint_save()).pin_memory()
+            steps = max(1, min(args.steps, args.e2e_steps))
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                c.checkpoint_load(blob)
+                c.run(dt, 1, seed)
+                c.checkpoint_save(blob)
+            barrier()
+            _, sec = agg(sec=time.perf_counter() - t0)
+            out["e2e"] = {"value": world * n * steps / sec, "unit": UNIT,
+                          "h2d_bytes_per_step": int(blob.numel()),
+                          "d2h_bytes_per_step": int(blob.numel()),
+                          "steps": steps,
+                          "what": "per step: iesh_checkpoint_load from pinned host memory, "
+                                  "iesh_run(1 step), iesh_checkpoint_save to pinned host memory "
+                                  "(the whole trajectory state, bit-exact resume)"}
+        c.close()
+        return out
 
-    ctx, ms, prof, clk = measure(P.PREC_FP64, True)
-    st = ctx.get_state()
-    K = ctx.propagator_terms()
-    bad = int(np.count_nonzero(st["status"]))
-    mixed = None
-    if not args.no_mixed:
-        cm, ms_m, prof_m, _ = measure(P.PREC_MIXED, False)
-        Km = cm.propagator_terms()
-        bad_m = int(np.count_nonzero(cm.get_state()["status"]))
-        tc_m = cm.kernel_shape()[0] == 8  # tensor-core propagator in use
-        cm.close()
-        mixed = (ms_m, prof_m, Km, bad_m, tc_m)
-    overlap = None
-    if not args.no_overlap:
-        co, ms_o, prof_o, _ = measure(P.PREC_FP64, False, propagator=P.iesh.PROP_OVERLAP)
-        bad_o = int(np.count_nonzero(co.get_state()["status"]))
-        co.close()
-        overlap = (ms_o, prof_o, bad_o)
+    def shares(prof):
+        tot = max(1e-9, sum(u[0] for u in prof.values()))
+        return {k: round(v[0] / tot, 4) for k, v in prof.items() if v[1]}
 
-    # ---- end to end through the C-ABI with pinned host buffers
+    def fp64_roofline(r, N, Ne):
+        """The FP64 propagator k_cheb against the derived FP64 peak: useful work
+        8 N^2 Ne per trajectory-step (achieved, frac) and executed work K 4 N^2 Ne
+        (executed_*, the FP64 pipe's utilisation)."""
+        n = r["n"]
+        pm, pn = r["prof"]["propagate"]
+        t = pm / pn / 1e3 if pn else None
+        prop_w, step_w = useful_flops(N, Ne)
+        ach = prop_w * n / t / 1e12 if t else None
+        exe = float(np.sum(r["K"].astype(np.float64))) * 4.0 * N * N * Ne / t / 1e12 if t else None
+        tr = DRAM_BYTES_PER_TRAJ.get(("k_cheb", N, Ne))
+        step_s = r["ms"] / args.steps / 1e3
+        return {"bound": "alu", "kernel": "k_cheb (Chebyshev exponential integrator, FP64)",
+                "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_NOMINAL_TFLOPS if ach else None,
+                "achieved_is": "algorithmic 8 N^2 Ne flops per trajectory-step (unitary "
+                               "application) x trajectories / mean k_cheb launch time",
+                "executed_achieved": exe,
+                "executed_frac": exe / FP64_NOMINAL_TFLOPS if exe else None,
+                "executed_is": "K 4 N^2 Ne flops actually issued (K Chebyshev orders of a real "
+                               "N x N by complex N x Ne product)",
+                "mean_cheb_terms": float(r["K"].mean()),
+                "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (no measured FP64 "
+                               "peak in MEASURED_PEAKS.json; a DFMA probe measured 1.20)",
+                "traffic": tr * n if tr else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per "
+                                  "trajectory of a capture at this shape, times the batch"
+                                  if tr else "no capture at this shape",
+                "step_useful_tflops": step_w * n / step_s / 1e12,
+                "step_useful_frac": step_w * n / step_s / 1e12 / FP64_NOMINAL_TFLOPS,
+                "kernel_time_share": shares(r["prof"])}
+
+    def mixed_roofline(r, N, Ne):
+        n = r["n"]
+        pm, pn = r["prof"]["propagate"]
+        t = pm / pn / 1e3 if pn else None
+        prop_w, step_w = useful_flops(N, Ne)
+        ach = prop_w * n / t / 1e12 if t else None
+        exe = float(np.sum(r["K"].astype(np.float64))) * 4.0 * N * N * Ne / t / 1e12 if t else None
+        ptf, src = tf32_peak()
+        step_s = r["ms"] / args.steps / 1e3
+        # time bound of the whole step: FP32/TF32 contractions on the tensor cores,
+        # eigen and coupling generation on the FP64 pipe
+        w_tc = prop_w + 8.0 * (N - Ne) * Ne * Ne + 8.0 / 3.0 * Ne ** 3
+        w_64 = step_w - w_tc
+        t_star = w_tc / (ptf * 1e12) + w_64 / (FP64_NOMINAL_TFLOPS * 1e12)
+        if r["tc"]:
+            Kp, NB = (N + 7) // 8 * 8, (2 * Ne + 15) // 16 * 16
+            roof = {"bound": "tensor", "kernel": "k_cheb_tc (tcgen05 kind::tf32, 3xTF32)",
+                    "peak": ptf, "peak_source": src,
+                    "executed_tensor_tflops": exe * 3 * (128 * Kp * NB) / (N * N * 2 * Ne) if exe else None}
+        else:
+            roof = {"bound": "alu", "kernel": "k_cheb_f32t (register-tiled FP32 SIMT)",
+                    "peak": FP32_NOMINAL_TFLOPS,
+                    "peak_source": "nominal FP32 SIMT (152 SMs x 128 FMA x 2 x 2.07 GHz)",
+                    "tf32_tensor_frac": ach / ptf if ach else None}
+        roof.update({"achieved": ach, "unit": "TFLOP/s",
+                     "frac": ach / roof["peak"] if ach else None,
+                     "achieved_is": "algorithmic 8 N^2 Ne flops per trajectory-step x "
+                                    "trajectories / mean propagator launch time",
+                     "executed_fp32_tflops": exe, "mean_cheb_terms": float(r["K"].mean()),
+                     "step_roofline_time_frac": n * t_star / step_s,
+                     "step_roofline_is": "t* = (8N^2Ne + 8(N-Ne)Ne^2 + 8/3 Ne^3) / P_TF32 + "
+                                         "(24 N^2 + 10 N^2) / P_FP64 per trajectory-step, "
+                                         "divided by the measured time per trajectory-step"})
+        return roof
+
+    MIXED_DTYPE = ("f32 coefficients, coupling generator, propagation (3xTF32 tensor cores for "
+                   "N <= 128, FP32 SIMT above), overlap LU or Gauss-Jordan ratios; double-float "
+                   "secular sums; f64 eigen iteration, forces, hop selection and rescale")
+
+    # ---------------------------------------------- headline: M = args.M
+    n = args.n_traj
+    md, dt, x, p, occ, C = config_state(args.M, n)
     N, Ne = md["M"] + 1, md["Ne"]
-    hx = torch.from_numpy(st["x"]).pin_memory()
-    hp = torch.from_numpy(st["p"]).pin_memory()
-    hocc = torch.from_numpy(st["occ"]).pin_memory()
-    hC = torch.from_numpy(st["C"].view(np.float64)).pin_memory()
-    hst = torch.zeros(n, dtype=torch.int32).pin_memory()
-    e2e_steps = max(1, min(args.steps, args.e2e_steps))
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ctx.set_state(hx, hp, hocc, hC)
-        ctx.run(dt, 1, seed)
-        ctx.get_state(hx, hp, hocc, hC, hst)
-    barrier()
-    e2e_s = aggregate(0.0, time.perf_counter() - t0, n, e2e_steps, world,
-                      dist if world > 1 else None, "cuda")["e2e_s"]
-    h2d = n * (8 + 8 + 2 * Ne + 16 * Ne * N)
-    d2h = h2d + 4 * n
+    r64 = measure(md, dt, x, p, occ, C, P.PREC_FP64, sample_clocks=True)
+    rmx = None if args.no_mixed else measure(md, dt, x, p, occ, C, P.PREC_MIXED)
+    rov = None if args.no_overlap else measure(md, dt, x, p, occ, C, P.PREC_FP64,
+                                               propagator=P.iesh.PROP_OVERLAP, e2e=False)
+    # ---------------------------------------------- config 3: M = 200, Ne = 100
+    c3 = None
+    if not args.no_config3 and args.M != 200:
+        n3 = args.c3_traj
+        md3, dt3, x3, p3, occ3, C3 = config_state(200, n3)
+        c3_64 = measure(md3, dt3, x3, p3, occ3, C3, P.PREC_FP64, sample_clocks=True)
+        c3_mx = measure(md3, dt3, x3, p3, occ3, C3, P.PREC_MIXED, sample_clocks=True)
+        c3 = (md3, dt3, n3, c3_64, c3_mx)
 
-    clocks = clk.summary() if clk else None
     if rank == 0:
-        value = world * n * args.steps / (ms / 1e3)
-        # dominant kernel: the Chebyshev propagator (FP64 DFMA pipe)
-        prop_ms, prop_n = prof["propagate"]
-        flops_launch = float(np.sum(K.astype(np.float64))) * 4.0 * N * N * Ne
-        achieved = flops_launch / (prop_ms / prop_n / 1e3) / 1e12 if prop_n else None
-        kernel_share = {k: round(v[0] / max(1e-9, sum(u[0] for u in prof.values())), 4)
-                        for k, v in prof.items() if v[1]}
+        value = world * n * args.steps / (r64["ms"] / 1e3)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r64["ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"double-well Newns-Anderson IESH, M={args.M} bath states, "
-                                   f"Ne={md['Ne']}, {n} trajectories per GPU, kT 0.005-0.01, "
+                                   f"Ne={Ne}, {n} trajectories per GPU, kT 0.005-0.01, "
                                    f"dt={dt} a.u., FP64 path",
                        "trajectories_per_gpu": n, "n_orbitals": N, "n_electrons": Ne,
                        "precision": "fp64", "skip_bound": bool(args.skip_bound),
                        "l2": "working set > L2 (coefficients + coupling matrices "
                              f"{(n * Ne * N * 16 + n * N * N * 8) / 1e9:.2f} GB)",
-                       "status_nonzero": bad},
-            "roofline": {"bound": "alu", "kernel": "k_cheb (Chebyshev exponential integrator)",
-                         "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                         "frac": (achieved / FP64_NOMINAL_TFLOPS) if achieved else None,
-                         "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (no measured "
-                                        "FP64 peak in MEASURED_PEAKS.json; a DFMA probe measured 1.20)",
-                         "traffic": KCHEB_FP64_TRAFFIC_PER_TRAJ * n if args.M == 100 else None,
-                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, "
-                                           "1024-trajectory capture scaled to the launch",
-                         "mean_cheb_terms": float(K.mean()),
-                         "kernel_time_share": kernel_share},
-            "e2e": {"value": world * n * e2e_steps / e2e_s, "unit": UNIT,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": int(sum(v[1] for v in prof.values())),
-            "clocks": clocks,
+                       "replicas": "rank r holds global trajectories [r n, (r+1) n) of one "
+                                   "seeded batch, Philox ids = global ids",
+                       "status_nonzero": int(np.count_nonzero(r64["status"]))},
+            "roofline": fp64_roofline(r64, N, Ne),
+            "e2e": r64["e2e"],
+            "gpu_launches": int(sum(v[1] for v in r64["prof"].values())),
+            "clocks": r64["clocks"],
             "impl": "ours",
         }
-        if mixed is not None:
-            ms_m, prof_m, Km, bad_m, tc_m = mixed
-            pm_ms, pm_n = prof_m["propagate"]
-            fl_m = float(np.sum(Km.astype(np.float64))) * 4.0 * N * N * Ne
-            ach_m = fl_m / (pm_ms / pm_n / 1e3) / 1e12 if pm_n else None
-            tot_m = max(1e-9, sum(u[0] for u in prof_m.values()))
-            if tc_m:
-                bf16 = measured_peaks().get("bf16_tflops")
-                peak_m = bf16 * TF32_PER_BF16 if bf16 else 1900.0 * TF32_PER_BF16
-                # executed tensor work: 3 TF32 products (3xTF32) on the padded tile
-                Kp, NB = (N + 7) // 8 * 8, (2 * Ne + 15) // 16 * 16
-                exe = ach_m * 3 * (128 * Kp * NB) / (N * N * 2 * Ne) if ach_m else None
-                roof_m = {"bound": "tensor", "kernel": "k_cheb_tc (tcgen05 kind::tf32, 3xTF32)",
-                          "achieved": ach_m, "peak": peak_m, "unit": "TFLOP/s",
-                          "frac": ach_m / peak_m if ach_m else None,
-                          "peak_source": ("of measured: MEASURED_PEAKS.json bf16_tflops x nominal "
-                                          "TF32/BF16 ratio 1.1/2.25" if bf16 else
-                                          "of fallback: 1.9 PFLOP/s bf16 x 1.1/2.25"),
-                          "executed_tflops": exe,
-                          "note": "achieved counts the FP32 contraction 4 N^2 Ne per order; the "
-                                  "kernel executes 3 TF32 products per FP32 product on a "
-                                  f"128 x {Kp} x {NB} tile",
-                          "mean_cheb_terms": float(Km.mean())}
-            else:
-                roof_m = {"bound": "alu", "kernel": "k_cheb_f32t (register-tiled FP32 SIMT)",
-                          "achieved": ach_m, "peak": FP32_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                          "frac": ach_m / FP32_NOMINAL_TFLOPS if ach_m else None,
-                          "peak_source": "nominal FP32 SIMT (152 SMs x 128 FMA x 2 x 2.07 GHz)",
-                          "mean_cheb_terms": float(Km.mean())}
+        if rmx is not None:
             line["mixed"] = {
-                "value": world * n * args.steps / (ms_m / 1e3), "unit": UNIT,
-                "ms_per_step": ms_m / args.steps, "speedup_vs_fp64": ms / ms_m,
-                "dtype": "f32 coupling, propagation, overlap LU and ratio solves; double-float secular sums; f64 eigen iteration, forces, hop probabilities, rescale",
-                "kernel_time_share": {k: round(v[0] / tot_m, 4) for k, v in prof_m.items() if v[1]},
-                "roofline_propagate": roof_m,
-                "gpu_launches": int(sum(v[1] for v in prof_m.values())),
-                "status_nonzero": bad_m,
+                "value": world * n * args.steps / (rmx["ms"] / 1e3), "unit": UNIT,
+                "ms_per_step": rmx["ms"] / args.steps, "speedup_vs_fp64": r64["ms"] / rmx["ms"],
+                "dtype": MIXED_DTYPE, "kernel_time_share": shares(rmx["prof"]),
+                "roofline_propagate": mixed_roofline(rmx, N, Ne), "e2e": rmx["e2e"],
+                "gpu_launches": int(sum(v[1] for v in rmx["prof"].values())),
+                "status_nonzero": int(np.count_nonzero(rmx["status"])),
             }
-        if overlap is not None:
-            ms_o, prof_o, bad_o = overlap
-            tot_o = max(1e-9, sum(u[0] for u in prof_o.values()))
-            po_ms, po_n = prof_o["propagate"]
-            # one real N x N by N x 2Ne contraction per step (4 N^2 Ne flops)
+        if rov is not None:
+            po_ms, po_n = rov["prof"]["propagate"]
             ach_o = 4.0 * N * N * Ne * n / (po_ms / po_n / 1e3) / 1e12 if po_n else None
             line["overlap"] = {
-                "value": world * n * args.steps / (ms_o / 1e3), "unit": UNIT,
-                "ms_per_step": ms_o / args.steps, "speedup_vs_fp64": ms / ms_o,
+                "value": world * n * args.steps / (rov["ms"] / 1e3), "unit": UNIT,
+                "ms_per_step": rov["ms"] / args.steps, "speedup_vs_fp64": r64["ms"] / rov["ms"],
                 "dtype": "f64",
                 "propagator": "diabatic-basis variant: exp(-i L1 dt/2) Q1^T Q0 exp(-i L0 dt/2), "
                               "O from the arrowhead's closed form (second order, like the "
                               "averaged generator)",
-                "kernel_time_share": {k: round(v[0] / tot_o, 4) for k, v in prof_o.items() if v[1]},
+                "kernel_time_share": shares(rov["prof"]),
                 "propagate_tflops": ach_o,
-                "gpu_launches": int(sum(v[1] for v in prof_o.values())),
-                "status_nonzero": bad_o,
+                "gpu_launches": int(sum(v[1] for v in rov["prof"].values())),
+                "status_nonzero": int(np.count_nonzero(rov["status"])),
+            }
+        if c3 is not None:
+            md3, dt3, n3, a, b = c3
+            N3, Ne3 = md3["M"] + 1, md3["Ne"]
+            line["config3"] = {
+                "workload": f"double-well Newns-Anderson IESH, M=200 bath states, Ne={Ne3}, "
+                            f"{n3} trajectories per GPU, kT 0.005-0.01, dt={dt3} a.u.",
+                "fp64": {"value": world * n3 * args.steps / (a["ms"] / 1e3), "unit": UNIT,
+                         "ms_per_step": a["ms"] / args.steps, "dtype": "f64",
+                         "roofline": fp64_roofline(a, N3, Ne3), "e2e": a["e2e"],
+                         "clocks": a["clocks"],
+                         "status_nonzero": int(np.count_nonzero(a["status"]))},
+                "mixed": {"value": world * n3 * args.steps / (b["ms"] / 1e3), "unit": UNIT,
+                          "ms_per_step": b["ms"] / args.steps, "dtype": MIXED_DTYPE,
+                          "kernel_time_share": shares(b["prof"]),
+                          "roofline_propagate": mixed_roofline(b, N3, Ne3), "e2e": b["e2e"],
+                          "clocks": b["clocks"],
+                          "status_nonzero": int(np.count_nonzero(b["status"]))},
+                "speedup_mixed_vs_fp64": a["ms"] / b["ms"],
             }
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args, md, kT, dt)
+            md0, kT0, _ = workload(args.M, n, args.dt)
+            line["cpu_baseline"] = cpu_baseline(args, md0, kT0, dt)
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -654,6 +743,9 @@ def main():
     ap.add_argument("--cpu-steps", dest="cpu_steps", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-config3", dest="no_config3", action="store_true",
+                    help="skip the M=200, Ne=100 comparison (FP64 and mixed)")
+    ap.add_argument("--c3-traj", dest="c3_traj", type=int, default=8192)
     ap.add_argument("--skip-bound", dest="skip_bound", action="store_true",
                     help="skip the ratio solves when the exact hop-probability bound is below "
                          "the uniform (Sec. II C; hop decisions unchanged)")

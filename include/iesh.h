@@ -55,7 +55,13 @@ typedef enum {
     IESH_ECUDA = 2,    /* a CUDA runtime call failed */
     IESH_ENOMEM = 3,   /* device allocation failed */
     IESH_ESTATE = 4,   /* call not allowed in the current state (e.g. run before init) */
-    IESH_EUNSUPPORTED = 5 /* option combination not built */
+    IESH_EUNSUPPORTED = 5, /* option combination not built */
+    /* Returned only by iesh_check, which summarises the per-trajectory status
+     * words of the batch (a numerical failure never aborts a batch): */
+    IESH_ENONCONV = 6, /* some trajectory carries IESH_TRAJ_SECULAR_NONCONV */
+    IESH_ESINGULAR = 7,/* some trajectory carries IESH_TRAJ_SINGULAR */
+    IESH_ENORM = 8,    /* some trajectory carries IESH_TRAJ_NORM_DRIFT */
+    IESH_ENAN = 9      /* some trajectory carries IESH_TRAJ_NAN */
 } iesh_status;
 
 /* Per-trajectory status bits (uint32). */
@@ -69,6 +75,12 @@ typedef enum {
 
 #define IESH_TRAJ_TC_WAIT 0x20u        /* a tensor-core completion wait gave up (the
                                           step's coefficients were not updated) */
+#define IESH_TRAJ_NORM_DRIFT 0x40u     /* after some step, an electron's coefficient
+                                          column had | ||c_e||^2 - 1 | above
+                                          iesh_options.norm_tol: the propagation
+                                          (unitary in exact arithmetic, Sec. II C)
+                                          lost accuracy; sticky until the next
+                                          init/set_state */
 
 /* Model kinds (Sec. II A; Sec. III B double well; Sec. III C desorption model). */
 enum {
@@ -119,6 +131,15 @@ typedef struct {
                           diabatic-basis variant, exp(-i L1 dt/2) Q1^T Q0
                           exp(-i L0 dt/2) in the adiabatic frame (FP64 only; needs a
                           nonzero coupling factor f(x), else IESH_TRAJ_PROP_RANGE) */
+    int64_t traj_base; /* global id of trajectory 0: trajectory t draws its random
+                          numbers with id traj_base + t (see iesh_run), so that a
+                          batch split over several contexts or GPUs, each given the
+                          id of its first trajectory, reproduces the undivided batch */
+    double prop_tol;   /* truncation tolerance of the Chebyshev series of the
+                          propagator (0: 1e-15 for FP64, 1e-7 for the mixed path) */
+    double norm_tol;   /* IESH_TRAJ_NORM_DRIFT threshold, checked after every step
+                          of iesh_run (0: 1e-8 for FP64, 1e-3 for the mixed path;
+                          < 0: no check) */
 } iesh_options;
 
 /* Create a context for up to max_traj trajectories of `model`.  Discretises
@@ -157,10 +178,46 @@ iesh_status iesh_get_state(iesh_ctx *ctx, double *x, double *p, int16_t *occ, vo
                            uint32_t *status);
 
 /* Advance every live trajectory by n_steps steps of length dt (steps 1-6
- * above).  The hop uniform of trajectory t at its step n is drawn from
- * Philox4x32-10 with key = seed and counter = (t, 0, n_lo, n_hi).
- * Asynchronous on the context stream. */
+ * above).  The hop uniform of trajectory t at its step n (the count of steps
+ * it has taken, kept across iesh_run calls and checkpoints) is drawn from
+ * Philox4x32-10 with key = seed and counter = (g_lo, 256 g_hi, n_lo, n_hi),
+ * g = traj_base + t its global id (for g < 2^32: (g, 0, n_lo, n_hi)); the
+ * thermal samples of iesh_init_state use streams 1 (nuclei) and 2
+ * (electrons) in the second word.  Asynchronous on the context stream. */
 iesh_status iesh_run(iesh_ctx *ctx, double dt, int64_t n_steps, uint64_t seed);
+
+/* Checkpoint / resume.  A checkpoint holds the complete per-trajectory state
+ * of the context's n trajectories: x, p, occupations, coefficients, the
+ * eigenpairs and model values of the current and previous step (the
+ * previous step's generator enters the step average of Sec. II C), forces,
+ * status words, step counters (the Philox counters of the hop uniforms),
+ * hop counters and population records.  Resuming from it continues the run
+ * bit for bit.  The blob is opaque and versioned; it may live in host or
+ * device memory (caller-owned).
+ * iesh_checkpoint_bytes: *bytes receives the size for the current batch.
+ * iesh_checkpoint_save: writes it (bytes must be at least that size);
+ *   returns after the copies finished.
+ * iesh_checkpoint_load: restores a checkpoint written by a context of the
+ *   same model sizes, precision, propagator and record layout (else
+ *   IESH_EINVAL) with at most max_traj trajectories. */
+iesh_status iesh_checkpoint_bytes(iesh_ctx *ctx, size_t *bytes);
+iesh_status iesh_checkpoint_save(iesh_ctx *ctx, void *buf, size_t bytes);
+iesh_status iesh_checkpoint_load(iesh_ctx *ctx, const void *buf, size_t bytes);
+
+/* Observables of every trajectory at its current state (Sec. III C/D):
+ * ke[n] = p^2 / 2m, epot[n] = U0(x) + sum_{i in s} lambda_i (the classical
+ * IESH Hamiltonian of Sec. II B without the kinetic term), and the impurity
+ * populations pop_sh[n] = sum_{i in s} q0_i^2 and pop_wf[n] =
+ * sum_e |sum_i q0_i c_ie|^2.  Any pointer may be NULL. */
+iesh_status iesh_observables(iesh_ctx *ctx, double *ke, double *epot, double *pop_sh,
+                             double *pop_wf);
+
+/* Summary of the batch's status words: bits[0] = OR over the trajectories,
+ * bits[1 + b] = number of trajectories with bit b set (b < 8); bits may be
+ * NULL.  Synchronises the context stream.  Returns IESH_ENAN, IESH_ENONCONV,
+ * IESH_ESINGULAR or IESH_ENORM (checked in this order) when some trajectory
+ * carries the matching bit, else IESH_OK. */
+iesh_status iesh_check(iesh_ctx *ctx, uint32_t *bits);
 
 /* Eigenvalues lam[n][N], impurity components q0[n][N] (> 0) of the
  * eigenvectors and the force F[n] at the current positions. */
@@ -231,11 +288,16 @@ iesh_status iesh_profile_read(iesh_ctx *ctx, double *ms, int64_t *launches);
  * without waiting.
  *
  * Working memory is a fixed array of IESH_NOALLOC_SCRATCH_BYTES inside the
- * library, resident on every device that has used this call until the
- * process exits; one call needs 16 n Ne N + 48 n bytes (plus alignment), and
- * a larger request returns IESH_EINVAL before any work is queued.  The first
- * call on a device looks up that array's device address (with the device
- * current); make this first call before any stream capture.  All calls share
+ * library's device module.  It is resident on every device where that
+ * module is loaded (under lazy module loading, from the first use of any
+ * of the library's kernels on that device; with CUDA_MODULE_LOADING=EAGER,
+ * on every device the process initialises), even in processes that never
+ * call this function, and stays there until the process exits.  One call
+ * needs 16 n Ne N + 48 n bytes (plus alignment), and a larger request
+ * returns IESH_EINVAL before any work is queued.  The first call on a
+ * device, with that device current, looks up the array's device address
+ * and sets the hop kernels' shared-memory limits; make this first call
+ * before any stream capture.  All calls share
  * the one array and each call overwrites it: calls that overlap on the GPU
  * (different streams or host threads without ordering) race and give wrong
  * results.  Trajectories with a singular overlap matrix get g = 0.  On error

@@ -33,6 +33,8 @@ struct iesh_ctx {
     int32_t *live = nullptr, *n_live = nullptr;  // device work list
     int64_t steps_since_init = 0;
     KernelTimer timer;  // kernel timing
+    double *obs = nullptr;        // [4][max_traj] observables
+    uint32_t *summary = nullptr;  // [9] status summary
 };
 
 // Launch `fn` (returning cudaError_t), bracketed by events when profiling.
@@ -221,6 +223,10 @@ const char *iesh_status_string(iesh_status s)
     case IESH_ENOMEM: return "IESH_ENOMEM";
     case IESH_ESTATE: return "IESH_ESTATE";
     case IESH_EUNSUPPORTED: return "IESH_EUNSUPPORTED";
+    case IESH_ENONCONV: return "IESH_ENONCONV";
+    case IESH_ESINGULAR: return "IESH_ESINGULAR";
+    case IESH_ENORM: return "IESH_ENORM";
+    case IESH_ENAN: return "IESH_ENAN";
     }
     return "IESH_?";
 }
@@ -268,6 +274,10 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
         st = fail(ctx, IESH_EINVAL, "unknown propagator %d", opt->propagator);
     else if (opt->propagator == IESH_PROP_OVERLAP && opt->precision != IESH_PREC_FP64)
         st = fail(ctx, IESH_EUNSUPPORTED, "the overlap propagator is FP64 only");
+    else if (!(opt->prop_tol >= 0.0 && opt->prop_tol < 1.0))
+        st = fail(ctx, IESH_EINVAL, "prop_tol must be in [0, 1)");
+    else if (opt->norm_tol != opt->norm_tol) st = fail(ctx, IESH_EINVAL, "norm_tol is NaN");
+    else if (opt->traj_base < 0) st = fail(ctx, IESH_EINVAL, "traj_base must be >= 0");
     if (st != IESH_OK) {
         *out = ctx;  // let the caller read the message, then destroy
         return st;
@@ -313,6 +323,8 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
     A(d.cheb, T * kChebStride)
     A(ctx->live, T)
     A(ctx->n_live, 1)
+    A(ctx->obs, 4 * T)
+    A(ctx->summary, 9)
     A(d.rec_sh, std::max<size_t>(1, T * d.max_records))
     A(d.rec_wf, std::max<size_t>(1, T * d.max_records))
     A(eps, (size_t)M) A(z0, (size_t)M)
@@ -332,6 +344,7 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
     d.propagator = opt->propagator;
     d.live = (opt->compact_every > 0) ? ctx->live : nullptr;
     d.n_live = ctx->n_live;
+    d.traj_base = (uint64_t)opt->traj_base;
     configure_hop_smem();
     configure_cheb_tc();
     {
@@ -533,7 +546,9 @@ iesh_status iesh_run(iesh_ctx *ctx, double dt, int64_t n_steps, uint64_t seed)
     const DevState &d = ctx->ds;
     const bool mx = ctx->mixed;
     // Chebyshev truncation: FP64 rounding level, or FP32 level for the mixed path
-    const double tol = mx ? 1e-7 : 1e-15;
+    const double tol = ctx->opt.prop_tol > 0.0 ? ctx->opt.prop_tol : (mx ? 1e-7 : 1e-15);
+    // unitarity check of the coefficient columns after each step
+    const double ntol = ctx->opt.norm_tol != 0.0 ? ctx->opt.norm_tol : (mx ? 1e-3 : 1e-8);
     for (int64_t k = 0; k < n_steps; ++k) {
         CU(timed(ctx, IESH_K_EIGEN, [&] { return launch_eigen(d, ctx->md, dt, 1, ctx->stream); }));
         if (d.propagator == IESH_PROP_OVERLAP) {
@@ -546,6 +561,8 @@ iesh_status iesh_run(iesh_ctx *ctx, double dt, int64_t n_steps, uint64_t seed)
         CU(timed(ctx, IESH_K_HOP, [&] {
             return launch_hop(d, dt, ctx->model.mass, seed, ctx->opt.skip_bound, nullptr, ctx->stream, mx);
         }));
+        if (ntol > 0.0)
+            CU(timed(ctx, IESH_K_OTHER, [&] { return launch_norm_check(d, mx, ntol, ctx->stream); }));
         ++ctx->steps_since_init;
         if (ctx->opt.compact_every > 0 && ctx->steps_since_init % ctx->opt.compact_every == 0)
             CU(timed(ctx, IESH_K_OTHER,
@@ -672,6 +689,161 @@ iesh_status iesh_hop_probabilities(iesh_ctx *ctx, double dt, double *g)
         CU(cudaFreeAsync(tmp, ctx->stream));
         CU(cudaStreamSynchronize(ctx->stream));
     }
+    return IESH_OK;
+}
+
+// ------------------------------------------------------------ checkpoint
+// Blob layout: a 64-byte header, then every per-trajectory array of the
+// first n trajectories in a fixed order, each section padded to 16 bytes,
+// then the population records [max_records][n].
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int32_t N, Ne, mixed, propagator;
+    int64_t n, max_records, record_every, steps_since_init;
+};
+static_assert(sizeof(CkptHeader) <= 64, "checkpoint header");
+constexpr size_t kCkptHeader = 64;
+constexpr char kCkptMagic[8] = {'I', 'E', 'S', 'H', 'C', 'K', 'P', '1'};
+
+struct Section {
+    void *dev;
+    size_t bytes;
+};
+
+std::vector<Section> ckpt_sections(iesh_ctx *ctx, int64_t n)
+{
+    DevState &d = ctx->ds;
+    const size_t N = ctx->N, Ne = ctx->Ne, T = (size_t)n;
+    const size_t cb = ctx->mixed ? 8 : 16;
+    std::vector<Section> v = {
+        {d.x, 8 * T}, {d.p, 8 * T}, {d.F, 8 * T}, {d.dU0, 8 * T}, {d.vprev, 8 * T},
+        {d.occ, 2 * T * Ne}, {d.C, cb * T * Ne * N},
+        {d.lam, 8 * T * N}, {d.q0, 8 * T * N}, {d.lam_prev, 8 * T * N}, {d.q0_prev, 8 * T * N},
+        {d.geo, 32 * T}, {d.geo_prev, 32 * T},
+        {d.rt, 8 * T * N}, {d.rt_prev, 8 * T * N}, {d.ro, 4 * T * N}, {d.ro_prev, 4 * T * N},
+        {d.fx, 8 * T}, {d.fx_prev, 8 * T},
+        {d.status, 4 * T}, {d.nstep, 8 * T}, {d.hops, 4 * T}, {d.frus, 4 * T},
+        {d.cheb, 8 * T * kChebStride},
+    };
+    if (d.max_records > 0) {
+        v.push_back({d.rec_sh, 8 * T * d.max_records});
+        v.push_back({d.rec_wf, 8 * T * d.max_records});
+    }
+    return v;
+}
+
+size_t ckpt_bytes(iesh_ctx *ctx, int64_t n)
+{
+    size_t b = kCkptHeader;
+    for (auto &s : ckpt_sections(ctx, n)) b += (s.bytes + 15) & ~(size_t)15;
+    return b;
+}
+}  // namespace
+
+iesh_status iesh_checkpoint_bytes(iesh_ctx *ctx, size_t *bytes)
+{
+    if (!ctx || !bytes) return IESH_EINVAL;
+    *bytes = ckpt_bytes(ctx, ctx->ds.n);
+    return IESH_OK;
+}
+
+iesh_status iesh_checkpoint_save(iesh_ctx *ctx, void *buf, size_t bytes)
+{
+    if (!ctx || !buf) return IESH_EINVAL;
+    if (!ctx->have_state) return fail(ctx, IESH_ESTATE, "checkpoint_save before a state exists");
+    const int64_t n = ctx->ds.n;
+    const size_t need = ckpt_bytes(ctx, n);
+    if (bytes < need) return fail(ctx, IESH_EINVAL, "checkpoint needs %zu bytes, got %zu", need, bytes);
+    CkptHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, kCkptMagic, 8);
+    h.N = ctx->N;
+    h.Ne = ctx->Ne;
+    h.mixed = ctx->mixed ? 1 : 0;
+    h.propagator = ctx->opt.propagator;
+    h.n = n;
+    h.max_records = ctx->ds.max_records;
+    h.record_every = ctx->ds.record_every;
+    h.steps_since_init = ctx->steps_since_init;
+    char *out = (char *)buf;
+    CU(cudaMemcpyAsync(out, &h, sizeof h, cudaMemcpyDefault, ctx->stream));
+    size_t off = kCkptHeader;
+    for (auto &s : ckpt_sections(ctx, n)) {
+        if (s.bytes) CU(cudaMemcpyAsync(out + off, s.dev, s.bytes, cudaMemcpyDefault, ctx->stream));
+        off += (s.bytes + 15) & ~(size_t)15;
+    }
+    CU(cudaStreamSynchronize(ctx->stream));  // the header copy reads a stack variable
+    return IESH_OK;
+}
+
+iesh_status iesh_checkpoint_load(iesh_ctx *ctx, const void *buf, size_t bytes)
+{
+    if (!ctx || !buf) return IESH_EINVAL;
+    if (bytes < kCkptHeader) return fail(ctx, IESH_EINVAL, "checkpoint shorter than its header");
+    CkptHeader h;
+    CU(cudaMemcpyAsync(&h, buf, sizeof h, cudaMemcpyDefault, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (memcmp(h.magic, kCkptMagic, 8) != 0) return fail(ctx, IESH_EINVAL, "not an IESH checkpoint");
+    if (h.N != ctx->N || h.Ne != ctx->Ne || h.mixed != (ctx->mixed ? 1 : 0) ||
+        h.propagator != ctx->opt.propagator || h.max_records != ctx->ds.max_records ||
+        h.record_every != ctx->ds.record_every)
+        return fail(ctx, IESH_EINVAL,
+                    "checkpoint of N=%d, Ne=%d, mixed=%d, propagator=%d, records %lld/%lld does "
+                    "not match this context", h.N, h.Ne, h.mixed, h.propagator,
+                    (long long)h.max_records, (long long)h.record_every);
+    if (h.n < 0 || h.n > ctx->max_traj)
+        return fail(ctx, IESH_EINVAL, "checkpoint holds %lld trajectories, context at most %lld",
+                    (long long)h.n, (long long)ctx->max_traj);
+    if (bytes < ckpt_bytes(ctx, h.n)) return fail(ctx, IESH_EINVAL, "checkpoint truncated");
+    DevState &d = ctx->ds;
+    d.n = h.n;
+    const char *in = (const char *)buf;
+    size_t off = kCkptHeader;
+    for (auto &s : ckpt_sections(ctx, h.n)) {
+        if (s.bytes) CU(cudaMemcpyAsync(s.dev, in + off, s.bytes, cudaMemcpyDefault, ctx->stream));
+        off += (s.bytes + 15) & ~(size_t)15;
+    }
+    ctx->steps_since_init = h.steps_since_init;
+    // the work list is rebuilt from the restored status words (the list's
+    // order never changes results)
+    CU(launch_live_init(h.n, ctx->live, ctx->n_live, ctx->stream));
+    if (ctx->opt.compact_every > 0) CU(launch_compact(d, ctx->live, ctx->n_live, ctx->stream));
+    if (is_host_ptr(buf)) CU(cudaStreamSynchronize(ctx->stream));
+    ctx->have_state = true;
+    return IESH_OK;
+}
+
+iesh_status iesh_observables(iesh_ctx *ctx, double *ke, double *epot, double *pop_sh, double *pop_wf)
+{
+    if (!ctx) return IESH_EINVAL;
+    if (!ctx->have_state) return fail(ctx, IESH_ESTATE, "observables before a state exists");
+    const DevState &d = ctx->ds;
+    const int64_t n = d.n;
+    CU(launch_observables(d, ctx->mixed, ctx->model.mass, ctx->obs, ctx->stream));
+    bool sync = false;
+    iesh_status st;
+    double *outs[4] = {ke, epot, pop_sh, pop_wf};
+    for (int k = 0; k < 4; ++k)
+        if ((st = copy_out(ctx, outs[k], ctx->obs + k * n, n * sizeof(double), sync)) != IESH_OK) return st;
+    if (sync) CU(cudaStreamSynchronize(ctx->stream));
+    return IESH_OK;
+}
+
+iesh_status iesh_check(iesh_ctx *ctx, uint32_t *bits)
+{
+    if (!ctx) return IESH_EINVAL;
+    uint32_t h[9] = {0};
+    if (ctx->have_state) {
+        CU(launch_status_summary(ctx->ds.status, ctx->ds.n, ctx->summary, ctx->stream));
+        CU(cudaMemcpyAsync(h, ctx->summary, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    if (bits) memcpy(bits, h, sizeof h);
+    if (h[0] & IESH_TRAJ_NAN) return IESH_ENAN;
+    if (h[0] & IESH_TRAJ_SECULAR_NONCONV) return IESH_ENONCONV;
+    if (h[0] & IESH_TRAJ_SINGULAR) return IESH_ESINGULAR;
+    if (h[0] & IESH_TRAJ_NORM_DRIFT) return IESH_ENORM;
     return IESH_OK;
 }
 

@@ -19,6 +19,7 @@ enum : uint32_t {
     ST_DONE = 0x8u,
     ST_PROP = 0x10u,
     ST_TC_WAIT = 0x20u,
+    ST_NORM = 0x40u,
 };
 
 // Model constants passed by value to every kernel.
@@ -73,6 +74,10 @@ struct DevState {
     double *geo2;              // [n][8]
     double *x_prev;            // [n][6] start of the step
     int32_t *hop_pair;         // [n] a N + m of the selected hop, or -1
+    // global id of trajectory 0 in the Philox counters (trajectory t draws
+    // with id traj_base + t), so that a batch split over several contexts
+    // or devices reproduces the undivided batch
+    uint64_t traj_base;
 };
 
 // 16-byte asynchronous copy global -> shared, cached in L2 only (both
@@ -209,6 +214,16 @@ __device__ __forceinline__ U4 draw(uint64_t seed, uint32_t traj, uint32_t stream
 {
     return philox4x32_10(traj, stream, (uint32_t)n, (uint32_t)(n >> 32), (uint32_t)seed,
                          (uint32_t)(seed >> 32));
+}
+
+// Draw of local trajectory t of a batch whose trajectory 0 has global id
+// s.traj_base.  Counter (gid_lo, stream + 256 gid_hi, n_lo, n_hi): for global
+// ids below 2^32 this is the layout above with traj = gid.
+__device__ __forceinline__ U4 draw_traj(const DevState &s, uint64_t seed, int64_t t,
+                                        uint32_t stream, uint64_t n)
+{
+    const uint64_t gid = s.traj_base + (uint64_t)t;
+    return draw(seed, (uint32_t)gid, stream + ((uint32_t)(gid >> 32) << 8), n);
 }
 
 // ------------------------------------------------------------ reductions

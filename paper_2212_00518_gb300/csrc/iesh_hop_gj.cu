@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kGjThreads, 2) k_hop_gj(DevState s, double dt,
     }
     __syncthreads();
     if (g_out) return;
-    const U4 rn = draw(seed, (uint32_t)t, kStreamHop, (uint64_t)s.nstep[t]);
+    const U4 rn = draw_traj(s, seed, t, kStreamHop, (uint64_t)s.nstep[t]);
     const double zeta = u53(rn.v[0], rn.v[1]);
     hop_finish<float2, EXT>(s, t, mass, zeta, !singular, G, red, scr, unocc, occ_s, lam_s, q0_s, geo_h, geo_dh,
                             geo_k, s_hop_a, s_hop_m, Ct);
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(kGlThreads, 1) k_hop_gjl(DevState s, double dt
     }
     __syncthreads();
     if (g_out) return;
-    const U4 rn = draw(seed, (uint32_t)t, kStreamHop, (uint64_t)s.nstep[t]);
+    const U4 rn = draw_traj(s, seed, t, kStreamHop, (uint64_t)s.nstep[t]);
     const double zeta = u53(rn.v[0], rn.v[1]);
     hop_finish<float2, EXT>(s, t, mass, zeta, !singular, G, red, scr, unocc, occ_s, lam_s, q0_s, geo_h, geo_dh,
                             geo_k, s_hop_a, s_hop_m, Ct);

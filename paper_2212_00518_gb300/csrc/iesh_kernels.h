@@ -53,6 +53,13 @@ size_t cheb_tc_smem_bytes(int N, int Ne);
 bool cheb_tc_eligible(int N, int Ne);
 void configure_cheb_tc();
 cudaError_t launch_cheb_tc(const DevState &s, double dt, cudaStream_t st);
+// unitarity check of the coefficient columns (sets ST_NORM), observables
+// out[4][n] = (kinetic energy, potential energy, occupied-surface and
+// wavefunction impurity populations), batch status summary out[9]
+cudaError_t launch_norm_check(const DevState &s, bool fp32, double tol, cudaStream_t st);
+cudaError_t launch_observables(const DevState &s, bool fp32, double mass, double *out,
+                               cudaStream_t st);
+cudaError_t launch_status_summary(const uint32_t *status, int64_t n, uint32_t *out, cudaStream_t st);
 // diabatic-basis (overlap) propagator variant: build O^T, then apply
 size_t overlap_build_smem(int N, int M);
 cudaError_t launch_overlap(const DevState &s, double dt, cudaStream_t st);

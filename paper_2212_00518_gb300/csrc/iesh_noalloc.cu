@@ -23,10 +23,13 @@ using namespace iesh;
 
 namespace {
 
-// Working memory of iesh_hop_probabilities_noalloc.  It is loaded with the
-// library on every device that uses it and stays resident until the process
-// exits.  In host code the name is only a stand-in for the device array; the
-// device address comes from cudaGetSymbolAddress.
+// Working memory of iesh_hop_probabilities_noalloc.  It is part of the
+// library's device module, so it is resident on every device where that
+// module is loaded (with lazy module loading: from the first launch of any
+// of the library's kernels on the device), whether or not this entry point
+// is called, and it stays there until the process exits.  In host code the
+// name is only a stand-in for the device array; the device address comes
+// from cudaGetSymbolAddress.
 static __device__ __align__(256) double g_noalloc_scratch[IESH_NOALLOC_SCRATCH_BYTES / sizeof(double)];
 
 constexpr int kMaxDevices = 64;
@@ -111,6 +114,9 @@ extern "C" iesh_status iesh_hop_probabilities_noalloc(const iesh_model *model, i
                 snprintf(buf, sizeof buf, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
                 return report(err, err_len, IESH_ECUDA, buf);
             }
+            // the hop kernels' shared-memory limits (process-wide function
+            // attributes), set once here so that no later call changes them
+            configure_hop_smem();
             g_scratch_addr[dev] = (double *)addr;
         }
         base = g_scratch_addr[dev];

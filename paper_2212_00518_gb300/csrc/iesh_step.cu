@@ -914,7 +914,7 @@ __global__ void __launch_bounds__(MAXT, MINB) k_hop(DevState s, double dt, doubl
             return nac(lam_s[m], q0_s[m], lam_s[sa], q0_s[sa], geo_h, geo_dh, geo_k);
         }
     };
-    const U4 rn = draw(seed, (uint32_t)t, kStreamHop, (uint64_t)s.nstep[t]);
+    const U4 rn = draw_traj(s, seed, t, kStreamHop, (uint64_t)s.nstep[t]);
     const double zeta = u53(rn.v[0], rn.v[1]);
     __syncthreads();
 
@@ -1124,7 +1124,7 @@ __global__ void k_init_nuclear(DevState s, double mass, uint64_t seed, double kT
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= s.n) return;
-    const U4 o = draw(seed, (uint32_t)t, kStreamNuc, 0);
+    const U4 o = draw_traj(s, seed, t, kStreamNuc, 0);
     const double u1 = u53(o.v[0], o.v[1]), u2 = u53(o.v[2], o.v[3]);
     const double r = sqrt(-2.0 * log(1.0 - u1));
     double sn, cs;
@@ -1170,7 +1170,7 @@ __global__ void k_sample_occ(DevState s, uint64_t seed, double kT)
     if (threadIdx.x == 0) {
         int n = Ne, cnt = 0;
         for (int k = 0; k < N && n > 0; ++k) {
-            const U4 o = draw(seed, (uint32_t)t, kStreamElec, (uint64_t)k);
+            const U4 o = draw_traj(s, seed, t, kStreamElec, (uint64_t)k);
             const double u = u53(o.v[0], o.v[1]);
             const double lw = -(s.lam[t * N + k] - ref) / kT;
             const double pk = exp(lw + LZ[(int64_t)(k + 1) * W1 + n - 1] - LZ[(int64_t)k * W1 + n]);
@@ -1349,13 +1349,21 @@ cudaError_t launch_hop(const DevState &s, double dt, double mass, uint64_t seed,
     // else one CTA of 512
     int threads = (2 * smem + 2048 <= 227 * 1024) ? 256 : 512;
     if (s.hop_threads > 0) threads = s.hop_threads;
-    // the shared-memory limit is a function attribute, not a stream operation;
-    // set it outside stream capture (contexts set it when they are created)
+    // The shared-memory limit is a process-wide function attribute, not a
+    // stream operation.  configure_hop_smem() raises it to the device's opt-in
+    // maximum when a context is created; here it is only ever raised (outside
+    // stream capture), never lowered, so that a small launch cannot take the
+    // room away from a larger one captured later.
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cs);
     auto go = [&](auto kern) {
-        if (cs == cudaStreamCaptureStatusNone)
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cs == cudaStreamCaptureStatusNone) {
+            cudaFuncAttributes fa;
+            if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess &&
+                fa.maxDynamicSharedSizeBytes < (int)smem)
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaGetLastError();
+        }
         kern<<<(unsigned)s.n, threads, smem, st>>>(s, dt, mass, seed, skip_bound, g_out);
     };
     if (ext && mixed) {

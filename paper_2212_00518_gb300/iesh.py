@@ -18,13 +18,15 @@ LIB_PATH = os.path.join(_HERE, "_build", "libiesh.so")
 
 IESH_OK = 0
 STATUS_NAMES = {0: "IESH_OK", 1: "IESH_EINVAL", 2: "IESH_ECUDA", 3: "IESH_ENOMEM",
-                4: "IESH_ESTATE", 5: "IESH_EUNSUPPORTED"}
+                4: "IESH_ESTATE", 5: "IESH_EUNSUPPORTED", 6: "IESH_ENONCONV",
+                7: "IESH_ESINGULAR", 8: "IESH_ENORM", 9: "IESH_ENAN"}
 TRAJ_SECULAR_NONCONV = 0x1
 TRAJ_SINGULAR = 0x2
 TRAJ_NAN = 0x4
 TRAJ_DONE = 0x8
 TRAJ_PROP_RANGE = 0x10
 TRAJ_TC_WAIT = 0x20
+TRAJ_NORM_DRIFT = 0x40
 
 PREC_FP64 = 0
 PREC_MIXED = 1
@@ -67,7 +69,8 @@ class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("skip_bound", ctypes.c_int),
                 ("record_every", ctypes.c_int), ("max_records", ctypes.c_int),
                 ("z_done", ctypes.c_double), ("compact_every", ctypes.c_int),
-                ("propagator", ctypes.c_int)]
+                ("propagator", ctypes.c_int), ("traj_base", ctypes.c_int64),
+                ("prop_tol", ctypes.c_double), ("norm_tol", ctypes.c_double)]
 
 
 EXPORTS = ["iesh_create", "iesh_destroy", "iesh_bath", "iesh_init_state", "iesh_set_state",
@@ -79,7 +82,8 @@ EXPORTS = ["iesh_create", "iesh_destroy", "iesh_bath", "iesh_init_state", "iesh_
            "iesh_eocc_backward", "iesh_last_error", "iesh_status_string", "iesh2_create",
            "iesh2_destroy", "iesh2_last_error", "iesh2_set_state", "iesh2_get_state", "iesh2_run",
            "iesh2_get_eigen", "iesh2_hop_probabilities", "iesh2_get_counters", "iesh2_profile",
-           "iesh2_profile_read"]
+           "iesh2_profile_read", "iesh_checkpoint_bytes", "iesh_checkpoint_save",
+           "iesh_checkpoint_load", "iesh_observables", "iesh_check"]
 KERNEL_CLASSES = ["eigen", "coupling", "propagate", "hop", "other"]
 
 _lib = None
@@ -136,6 +140,11 @@ def load(path=LIB_PATH):
     L.iesh2_get_counters.argtypes = [_vp, _vp, _vp, _vp]
     L.iesh2_profile.argtypes = [_vp, ctypes.c_int]
     L.iesh2_profile_read.argtypes = [_vp, _vp, _vp]
+    L.iesh_checkpoint_bytes.argtypes = [_vp, _vp]
+    L.iesh_checkpoint_save.argtypes = [_vp, _vp, ctypes.c_size_t]
+    L.iesh_checkpoint_load.argtypes = [_vp, _vp, ctypes.c_size_t]
+    L.iesh_observables.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    L.iesh_check.argtypes = [_vp, _vp]
     L.iesh_last_error.argtypes = [_vp]
     L.iesh_last_error.restype = ctypes.c_char_p
     L.iesh_status_string.argtypes = [ctypes.c_int]
@@ -201,7 +210,8 @@ class Context:
     """A batch of IESH trajectories on one GPU (wraps iesh_ctx)."""
 
     def __init__(self, model, max_traj, precision=PREC_FP64, skip_bound=False, record_every=0,
-                 max_records=0, z_done=0.0, compact_every=0, stream=None, propagator=PROP_AVERAGED):
+                 max_records=0, z_done=0.0, compact_every=0, stream=None, propagator=PROP_AVERAGED,
+                 traj_base=0, prop_tol=0.0, norm_tol=0.0):
         self.L = load()
         self.model = dict(model)
         self.N = int(model["M"]) + 1
@@ -212,7 +222,8 @@ class Context:
         self._m = model_struct(model)
         self.propagator = int(propagator)
         self._o = _Options(precision, int(bool(skip_bound)), int(record_every), int(max_records),
-                           float(z_done), int(compact_every), self.propagator)
+                           float(z_done), int(compact_every), self.propagator, int(traj_base),
+                           float(prop_tol), float(norm_tol))
         self.stream = current_stream_handle() if stream is None else stream
         h = _vp()
         rc = self.L.iesh_create(ctypes.byref(h), ctypes.byref(self._m), ctypes.byref(self._o),
@@ -337,6 +348,46 @@ class Context:
         self._check(self.L.iesh_profile_read(self._h, ms.ctypes.data, n.ctypes.data),
                     "iesh_profile_read")
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def checkpoint_bytes(self):
+        b = ctypes.c_size_t(0)
+        self._check(self.L.iesh_checkpoint_bytes(self._h, ctypes.addressof(b)),
+                    "iesh_checkpoint_bytes")
+        return b.value
+
+    def checkpoint_save(self, buf=None):
+        """Write the checkpoint of the whole batch into `buf` (host numpy
+        uint8 array or CUDA tensor), by default a new host array."""
+        nb = self.checkpoint_bytes()
+        buf = np.zeros(nb, np.uint8) if buf is None else buf
+        size = buf.nbytes if isinstance(buf, np.ndarray) else buf.numel() * buf.element_size()
+        self._check(self.L.iesh_checkpoint_save(self._h, _ptr(buf), int(size)),
+                    "iesh_checkpoint_save")
+        return buf
+
+    def checkpoint_load(self, buf):
+        size = buf.nbytes if isinstance(buf, np.ndarray) else buf.numel() * buf.element_size()
+        self._check(self.L.iesh_checkpoint_load(self._h, _ptr(buf), int(size)),
+                    "iesh_checkpoint_load")
+        hdr = np.asarray(buf[:64].cpu() if hasattr(buf, "cpu") else buf[:64]).view(np.int64)
+        self.n = int(hdr[3])
+
+    def observables(self):
+        """Per trajectory: kinetic energy, potential energy U0 + sum of the
+        occupied eigenvalues, occupied-surface and wavefunction impurity
+        populations."""
+        out = [np.zeros(self.n) for _ in range(4)]
+        self._check(self.L.iesh_observables(self._h, *(o.ctypes.data for o in out)),
+                    "iesh_observables")
+        return dict(ke=out[0], epot=out[1], pop_sh=out[2], pop_wf=out[3])
+
+    def check(self):
+        """(status code, OR of the status words, per-bit trajectory counts)."""
+        bits = np.zeros(9, np.uint32)
+        rc = self.L.iesh_check(self._h, bits.ctypes.data)
+        if rc not in (0, 6, 7, 8, 9):
+            self._check(rc, "iesh_check")
+        return STATUS_NAMES.get(rc, rc), int(bits[0]), bits[1:].copy()
 
     def records(self, max_records):
         sh = np.zeros((max_records, self.n))

@@ -39,8 +39,32 @@ def test_binding_covers_every_declared_symbol():
 
 
 def test_status_strings(lib):
+    from paper_2212_00518_gb300 import iesh
     assert lib.iesh_status_string(0) == b"IESH_OK"
     assert lib.iesh_status_string(1) == b"IESH_EINVAL"
+    for code, name in iesh.STATUS_NAMES.items():
+        assert lib.iesh_status_string(code) == name.encode()
+
+
+def test_invalid_options_rejected_without_device(lib):
+    from paper_2212_00518_gb300 import iesh
+    md = iesh.model_struct(W.double_well(20))
+    for kw in (dict(prop_tol=1.0), dict(prop_tol=-1e-3), dict(traj_base=-1),
+               dict(norm_tol=float("nan"))):
+        opt = iesh._Options(iesh.PREC_FP64, 0, 0, 0, 0.0)
+        for k, v in kw.items():
+            setattr(opt, k, v)
+        h = ctypes.c_void_p()
+        rc = lib.iesh_create(ctypes.byref(h), ctypes.byref(md), ctypes.byref(opt), 16, None)
+        assert rc == 1, (kw, rc)
+        assert lib.iesh_last_error(h)
+        lib.iesh_destroy(h)
+    # entry points refuse a null context
+    for fn in ("iesh_checkpoint_bytes", "iesh_checkpoint_save", "iesh_checkpoint_load",
+               "iesh_observables", "iesh_check"):
+        f = getattr(lib, fn)
+        args = [0 if t is ctypes.c_size_t else None for t in f.argtypes]
+        assert f(*args) == 1, fn
 
 
 def test_invalid_models_rejected_without_device(lib):

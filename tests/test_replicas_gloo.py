@@ -1,7 +1,9 @@
 """Host logic of the multi-GPU benchmark (replicas only: independent
 trajectory batches per rank, no data-path collective) with two gloo ranks
-on the CPU: per-rank Philox keys differ, the job time is the maximum over
-ranks and the throughput sums the ranks' trajectories."""
+on the CPU: the ranks hold consecutive slices of one seeded batch and draw
+with its global trajectory ids (so N GPUs compute the trajectories one GPU
+would), the job time is the maximum over ranks and the throughput sums the
+ranks' trajectories."""
 import os
 import socket
 
@@ -29,9 +31,12 @@ def _worker(rank, world, port, out):
     ms_local = [120.0, 150.0][rank]
     e2e_local = [1.5, 1.2][rank]
     agg = bench.aggregate(ms_local, e2e_local, 4096, 10, world, dist, "cpu")
-    seeds = [None] * world
-    dist.all_gather_object(seeds, bench.replica_seed(7, rank))
-    out[rank] = (agg["ms"], agg["e2e_s"], agg["value"], tuple(seeds))
+    n = 6
+    md, dt, x, p, occ, C = bench.replica_state(20, n, world, rank)
+    mine = (bench.replica_traj_base(rank, n), x, p, occ, C)
+    parts = [None] * world
+    dist.all_gather_object(parts, mine)
+    out[rank] = (agg["ms"], agg["e2e_s"], agg["value"], parts)
     dist.destroy_process_group()
 
 
@@ -46,11 +51,18 @@ def test_two_rank_aggregation():
     for p in procs:
         p.join(120)
         assert p.exitcode == 0
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    import numpy as np
+    _, _, x1, p1, occ1, C1 = bench.replica_state(20, 12, 1, 0)  # the job on one GPU
     for r in range(2):
-        ms, e2e, value, seeds = out[r]
+        ms, e2e, value, parts = out[r]
         assert ms == 150.0 and e2e == 1.5
         assert value == pytest.approx(2 * 4096 * 10 / 0.150)
-        assert seeds[0] != seeds[1]
+        assert [q[0] for q in parts] == [0, 6]  # global ids of each rank's first trajectory
+        for whole, k in ((x1, 1), (p1, 2), (occ1, 3), (C1, 4)):
+            assert np.array_equal(np.concatenate([q[k] for q in parts]), whole)
 
 
 def test_single_rank_aggregation_of_host_time_only():
