@@ -66,7 +66,12 @@
  *      along the NAC vector d_{m,s_a} (Sec. II B: rescale in the direction
  *      of the NAC) with the energy-conserving root of smaller magnitude, and
  *      eigenvectors signed so that their component on the coupled
- *      combination c_0|0> + c_1|1> of the adsorbate orbitals is positive.
+ *      combination c_0|0> + c_1|1> of the adsorbate orbitals is positive
+ *      at set-up.
+ *   R17 own bath profile per adsorbate orbital (non-parallel couplings)
+ *      and, for both two-orbital models, the gauge after set-up: each
+ *      eigenvector keeps a non-negative overlap with the previous step's
+ *      (the rule of R16 flips the |->-like eigenvector where h_0 = h_1).
  *
  * Impurity populations (traj_populations): the paper defers the definition
  * of the diabatic population P_d to another work, so two readings are
@@ -1153,7 +1158,8 @@ int orc_eocc(int M, int Ne, const double *eps, const double *sqw, const double *
 /* harmonic restraint U0 = m w^2 |x - x0|^2 / 2                             */
 /* on every coordinate (one mass).  The same IESH step as traj_step in six  */
 /* dimensions: velocity Verlet, dense eigenpairs (gauge: the combination    */
-/* c1 Q_1j + c2 Q_2j of the impurity components positive), T^a = Q^T dH/dx_a */
+/* c1 Q_1j + c2 Q_2j of the impurity components positive at set-up, then    */
+/* continuity with the previous step's eigenvectors), T^a = Q^T dH/dx_a      */
 /* Q, the averaged generator with v.d, hop probabilities with v.d, and the  */
 /* rescale along the NAC vector d_{m, s_a} with the smaller root.            */
 /* ------------------------------------------------------------------------ */
@@ -1238,10 +1244,12 @@ static void traj2_eigen(const orc_model2 *md, orc_traj2 *t)
     for (int i = 0; i < N; i++)
         for (int j = i + 1; j < N; j++)
             if (ev[idx[j]] < ev[idx[i]]) { int tt = idx[i]; idx[i] = idx[j]; idx[j] = tt; }
-    /* gauge: R16, the combination c1 Q_0j + c2 Q_1j >= 0; R17 (own bath
-     * profiles), after the first call: overlap with the previous call's
-     * eigenvector j >= 0 */
-    const int by_overlap = md->Vk && t->Qprev && t->have_prev;
+    /* gauge (R16, R17): at the first call the combination c1 Q_0j + c2 Q_1j
+     * >= 0; afterwards continuity, the overlap with the previous call's
+     * eigenvector j >= 0.  (The combination rule alone flips the
+     * |->-like eigenvector where h_0 = h_1, because its component on the
+     * coupled combination passes through zero there.) */
+    const int by_overlap = t->Qprev && t->have_prev;
     for (int j = 0; j < N; j++) {
         const int c = idx[j];
         double key = c1 * V[0 * N + c] + c2 * V[1 * N + c];
@@ -1253,7 +1261,7 @@ static void traj2_eigen(const orc_model2 *md, orc_traj2 *t)
         t->lam[j] = ev[c];
         for (int r = 0; r < N; r++) t->Q[r * N + j] = sgn * V[r * N + c];
     }
-    if (md->Vk && t->Qprev) {
+    if (t->Qprev) {
         memcpy(t->Qprev, t->Q, sizeof(double) * N * N);
         t->have_prev = 1;
     }
@@ -1378,7 +1386,7 @@ static int run2_any(const orc_model2 *mdp, int64_t n_traj, double *x, double *p,
     t.lam = malloc(sizeof(double) * N);
     t.Q = malloc(sizeof(double) * N * N);
     t.d = malloc(sizeof(double) * 6 * N * N);
-    t.Qprev = md.Vk ? malloc(sizeof(double) * N * N) : NULL;
+    t.Qprev = malloc(sizeof(double) * N * N);
     for (int64_t i = 0; i < n_traj; i++) {
         t.have_prev = 0;
         memcpy(t.x, x + 6 * i, sizeof(double) * 6);
@@ -1419,10 +1427,11 @@ int orc_run2(int M, int Ne, const double *eps, const double *sqw, const double *
 }
 
 /* The same with an own bath profile for each orbital (reading R17): Vk
- * [2][M] couples orbital a to bath state k at f_a = 1.  Eigenvector gauge:
- * the rule of R16 (with c_a = f_a |Vk[a]|) at the start, then continuity
- * (overlap with the previous step's eigenvector >= 0).  Qad_out [n][2][N]
- * (optional): the adsorbate rows of the final eigenvectors. */
+ * [2][M] couples orbital a to bath state k at f_a = 1.  Eigenvector gauge
+ * as in orc_run2: the rule of R16 (with c_a = f_a |Vk[a]|) at the start,
+ * then continuity (overlap with the previous step's eigenvector >= 0).
+ * Qad_out [n][2][N] (optional): the adsorbate rows of the final
+ * eigenvectors. */
 int orc_run2g(int M, int Ne, const double *eps, const double *Vk, const double *R, const double *th,
               double mass, double omega, const double *x0, int64_t n_traj, double *x, double *p,
               double *F, int *occ, cplx *C, double dt, int64_t n_steps, uint64_t seed, uint32_t *status,

@@ -159,3 +159,30 @@ def test_profiled_run_conserves_energy_through_hops():
     for t in range(n):
         G = r["C"][t].conj().T @ r["C"][t]
         assert np.abs(G - np.eye(md["Ne"])).max() <= 1e-9
+
+
+def test_continuity_gauge_through_a_level_crossing():
+    """Parallel couplings (reading R16), a straight path on which the two
+    adsorbate levels cross (h_0 = h_1, where the coupling t of |-> to |+>
+    vanishes): the R16 sign rule alone flips the |->-like eigenvector, the
+    continuity gauge used after set-up (reading R17) keeps every overlap of
+    consecutive eigenvectors near +1, and a run across the crossing agrees
+    with the flat-profile model, which always signs by continuity."""
+    md = W.two_orbital(40, seed=6, vscale=1.0)
+    x, p, occ, C = W.two_orbital_state(md, 6, 31, weight=0.8)
+    th = md["theta"]
+    r = O.run2(md, x, p, occ, np.transpose(C, (0, 2, 1)), 2.0, 1, 2)
+    x0, x1 = r["x"][3], O.run2(md, x, p, occ, np.transpose(C, (0, 2, 1)), 2.0, 2, 2)["x"][3]
+    dh = lambda y: th[0] + th[2:8] @ y - th[1] - th[8:14] @ y
+    assert dh(x0) * dh(x1) < 0, "the path must cross h_0 = h_1"
+    flat = dict(md, profile=dict(center=[0.0, 0.0], width=[1e30, 1e30]))
+    _, Qa, _, _ = O.eigen2(flat, x0, occ[3])
+    _, Qr, _, _ = O.eigen2(md, x1, occ[3])  # R16 rule alone at x1
+    _, Qc, _, _ = O.eigen2(flat, x1, occ[3], Qref=Qa)  # continuity
+    assert np.einsum("rj,rj->j", Qa, Qr).min() < -0.9
+    assert np.einsum("rj,rj->j", Qa, Qc).min() > 0.9
+    Ct = np.transpose(C, (0, 2, 1))
+    a = O.run2(md, x, p, occ, Ct, 2.0, 20, 2)
+    b = O.run2(flat, x, p, occ, Ct, 2.0, 20, 2)
+    assert np.array_equal(a["occ"], b["occ"])
+    assert np.abs(a["C"] - b["C"]).max() <= 1e-10
