@@ -71,7 +71,9 @@
  *   R17 own bath profile per adsorbate orbital (non-parallel couplings)
  *      and, for both two-orbital models, the gauge after set-up: each
  *      eigenvector keeps a non-negative overlap with the previous step's
- *      (the rule of R16 flips the |->-like eigenvector where h_0 = h_1).
+ *      where that overlap is at least 1/2 in magnitude, else the rule of
+ *      R16 (which alone flips the |->-like eigenvector where h_0 = h_1;
+ *      continuity alone is undecided at exact crossings).
  *
  * Impurity populations (traj_populations): the paper defers the definition
  * of the diabatic population P_d to another work, so two readings are
@@ -1158,8 +1160,9 @@ int orc_eocc(int M, int Ne, const double *eps, const double *sqw, const double *
 /* harmonic restraint U0 = m w^2 |x - x0|^2 / 2                             */
 /* on every coordinate (one mass).  The same IESH step as traj_step in six  */
 /* dimensions: velocity Verlet, dense eigenpairs (gauge: the combination    */
-/* c1 Q_1j + c2 Q_2j of the impurity components positive at set-up, then    */
-/* continuity with the previous step's eigenvectors), T^a = Q^T dH/dx_a      */
+/* c1 Q_1j + c2 Q_2j of the impurity components positive, after set-up      */
+/* overruled by a decisive overlap with the previous step's eigenvector),   */
+/* T^a = Q^T dH/dx_a                                                        */
 /* Q, the averaged generator with v.d, hop probabilities with v.d, and the  */
 /* rescale along the NAC vector d_{m, s_a} with the smaller root.            */
 /* ------------------------------------------------------------------------ */
@@ -1244,18 +1247,22 @@ static void traj2_eigen(const orc_model2 *md, orc_traj2 *t)
     for (int i = 0; i < N; i++)
         for (int j = i + 1; j < N; j++)
             if (ev[idx[j]] < ev[idx[i]]) { int tt = idx[i]; idx[i] = idx[j]; idx[j] = tt; }
-    /* gauge (R16, R17): at the first call the combination c1 Q_0j + c2 Q_1j
-     * >= 0; afterwards continuity, the overlap with the previous call's
-     * eigenvector j >= 0.  (The combination rule alone flips the
-     * |->-like eigenvector where h_0 = h_1, because its component on the
-     * coupled combination passes through zero there.) */
+    /* gauge (R16, R17): the combination c1 Q_0j + c2 Q_1j >= 0 at the first
+     * call; afterwards continuity, the overlap with the previous call's
+     * eigenvector j >= 0, wherever that overlap is decisive (|overlap| >=
+     * 1/2), else (an eigenvalue crossing within the step) the combination
+     * rule again.  The combination rule alone flips the |->-like
+     * eigenvector where h_0 = h_1 (its component on the coupled combination
+     * passes through zero); continuity alone is undecided at an exact
+     * crossing, e.g. of a decoupled orbital with a bath level. */
     const int by_overlap = t->Qprev && t->have_prev;
     for (int j = 0; j < N; j++) {
         const int c = idx[j];
         double key = c1 * V[0 * N + c] + c2 * V[1 * N + c];
         if (by_overlap) {
-            key = 0.0;
-            for (int r = 0; r < N; r++) key += t->Qprev[r * N + j] * V[r * N + c];
+            double ov = 0.0;
+            for (int r = 0; r < N; r++) ov += t->Qprev[r * N + j] * V[r * N + c];
+            if (fabs(ov) >= 0.5) key = ov;
         }
         const double sgn = key < 0.0 ? -1.0 : 1.0;
         t->lam[j] = ev[c];
@@ -1428,8 +1435,7 @@ int orc_run2(int M, int Ne, const double *eps, const double *sqw, const double *
 
 /* The same with an own bath profile for each orbital (reading R17): Vk
  * [2][M] couples orbital a to bath state k at f_a = 1.  Eigenvector gauge
- * as in orc_run2: the rule of R16 (with c_a = f_a |Vk[a]|) at the start,
- * then continuity (overlap with the previous step's eigenvector >= 0).
+ * as in orc_run2, the rule of R16 with c_a = f_a |Vk[a]|.
  * Qad_out [n][2][N] (optional): the adsorbate rows of the final
  * eigenvectors. */
 int orc_run2g(int M, int Ne, const double *eps, const double *Vk, const double *R, const double *th,
