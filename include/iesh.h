@@ -240,6 +240,37 @@ iesh_status iesh_get_records(iesh_ctx *ctx, double *pop_sh, double *pop_wf, int6
  * list is off).  Synchronises the context stream. */
 iesh_status iesh_get_live(iesh_ctx *ctx, int64_t *n_live);
 
+/* ---------------------------------------------------------------------
+ * Uneven batches in one launch.
+ *
+ * Trajectories of different bath sizes (one context per model) and
+ * lifetimes (a trajectory ends when it leaves the surface, Sec. III D) run
+ * together: iesh_ensemble_create captures, once, a CUDA graph whose single
+ * device-side loop (a conditional while node) advances every context by
+ * `chunk` steps, compacts every context's work list of live trajectories
+ * on the device, and decides on the device whether to go on.
+ * iesh_ensemble_run enqueues one launch of that graph on cuda_stream: it
+ * returns at once, and the device keeps looping until no trajectory of any
+ * context is live or max_steps more steps have run (whole chunks; the
+ * count is the loop's own and does not include iesh_run steps).  Finished
+ * trajectories cost no work (their CTAs exit at once); results are bit
+ * for bit those of iesh_run with the same seed.  Each context needs
+ * compact_every > 0, a state (init_state / set_state / checkpoint_load) and
+ * profiling off; the graph holds the contexts' batch sizes at creation, so
+ * create the ensemble after the set-up and create it again after changing a
+ * batch.  The contexts' earlier work is waited for, and their later calls
+ * wait for the loop.  iesh_ensemble_status synchronises cuda_stream and
+ * returns the loop's total steps and the live trajectories after the last
+ * chunk; exact live trajectory-steps are the sum of iesh_get_counters'
+ * step counts.  The contexts must outlive the ensemble. */
+typedef struct iesh_ensemble iesh_ensemble;
+iesh_status iesh_ensemble_create(iesh_ensemble **out, iesh_ctx *const *ctxs, int n_ctx, double dt,
+                                 int64_t chunk, uint64_t seed, void *cuda_stream);
+iesh_status iesh_ensemble_run(iesh_ensemble *ens, int64_t max_steps);
+iesh_status iesh_ensemble_status(iesh_ensemble *ens, int64_t *steps_done, int64_t *live);
+iesh_status iesh_ensemble_destroy(iesh_ensemble *ens);
+const char *iesh_ensemble_last_error(const iesh_ensemble *ens);
+
 /* Kernel shapes.  FP64 contexts: cheb_ept (1 or 2) electrons per thread and
  * cheb_G column groups per CTA of the propagator (cheb_G * N <= 1024).
  * Mixed contexts: cheb_ept must be 4 (each thread holds 4 orbitals x 4
@@ -310,6 +341,34 @@ iesh_status iesh_hop_probabilities_noalloc(const iesh_model *model, int64_t n, c
                                            size_t err_len);
 
 /* ---------------------------------------------------------------------
+ * Batched dense symmetric eigensolver.
+ *
+ * The paper obtains the eigenpairs of the one-electron Hamiltonian by a
+ * dense symmetric diagonalisation at every step (Sec. II C, implementation
+ * details); the arrowhead secular solver of iesh_run is its fast path for
+ * a single adsorbate orbital.  This call is the general method: for each
+ * of B symmetric n x n matrices A[b] (row-major, both triangles stored;
+ * n <= 256) it computes the eigenvalues lam[b][0..n-1] in ascending order
+ * and, if V is not NULL, the orthonormal eigenvectors as rows V[b][j][0..n-1]
+ * (A v_j = lam_j v_j), each signed so that its component of largest
+ * magnitude (the first on a tie) is positive.  Householder reduction to
+ * tridiagonal form (one CTA per matrix, the matrix in shared memory up to
+ * about 200 KB), implicit-shift QL iterations with the rotations applied to
+ * the rows of the reflector product (one thread per matrix), ordering.
+ * precision: IESH_PREC_FP64 (double arrays) or IESH_PREC_MIXED (float
+ * arrays, FP32 arithmetic).  info[b] (device, may be NULL) is set to 0, or
+ * to 1 when an eigenvalue needed more than 60 QL iterations (the output of
+ * that matrix is then unreliable).  work: caller-owned device workspace of
+ * at least iesh_syev_work_bytes(B, n, precision, V != NULL) bytes.  All
+ * array pointers are device memory.  Asynchronous on cuda_stream (a
+ * cudaStream_t, NULL = legacy default stream); allocates nothing.  On error
+ * a message is written to err (err_len bytes, may be NULL). */
+size_t iesh_syev_work_bytes(int64_t B, int n, int precision, int vectors);
+iesh_status iesh_syev_batched(int64_t B, int n, int precision, const void *A, void *lam, void *V,
+                              uint32_t *info, void *work, size_t work_bytes, void *cuda_stream,
+                              char *err, size_t err_len);
+
+/* ---------------------------------------------------------------------
  * Occupied-orbital energy of a two-orbital adsorbate, E_occ = sum of the Ne
  * lowest eigenvalues of the one-electron Hamiltonian (the electronic part
  * of the classical IESH Hamiltonian, Sec. II B, at ground-state occupation),
@@ -367,7 +426,13 @@ iesh_status iesh_eocc_backward(iesh_eocc_ctx *ctx, int64_t B, int precision, con
  * with the smaller |alpha|; no such alpha: the hop is frustrated.
  *
  * Eigenvector gauge: the component of eigenvector j on the coupled
- * combination c_0 |0> + c_1 |1> (c_a = vbar[a] f_a) is >= 0.
+ * combination c_0 |0> + c_1 |1> (c_a = vbar[a] f_a; with profile 1, c_a =
+ * vbar[a] f_a |profile_a|) is >= 0, except that in a step an eigenvector
+ * whose overlap with the previous step's eigenvector j is at least 1/2 in
+ * magnitude keeps that overlap positive (continuity: the combination passes
+ * through zero for the |->-like eigenvector where h_0 = h_1, and for
+ * non-parallel couplings elsewhere too; at an eigenvalue crossing within
+ * the step the overlap decides nothing and the combination rule stands).
  * Layouts: x, p, F [n][6]; occ [n][Ne] int16 ascending; C [n][Ne][N]
  * complex, double for IESH_PREC_FP64 and float for IESH_PREC_MIXED (the
  * one-coordinate split: FP64 eigenpairs, forces, hop probabilities and
@@ -384,6 +449,15 @@ typedef struct {
     double theta[16];  /* eps_0, eps_1, g_{0,0..5}, g_{1,0..5}, sigma_0, sigma_1 */
     double vbar[2];    /* coupling amplitudes */
     double R[6];       /* coupling centres */
+    int profile;       /* 0: both orbitals couple to bath state k as vbar_a sqrt(w_k) f_a
+                          (parallel border vectors); 1: each orbital with its own
+                          Lorentzian bath profile, vbar_a sqrt(w_k) f_a / sqrt(1 +
+                          ((eps_k - prof_center[a]) / prof_width[a])^2) (the border
+                          vectors are not parallel) */
+    double prof_center[2], prof_width[2];
+    int eigensolver;   /* 0: the rank-two arrowhead secular solver for profile 0, the
+                          dense symmetric eigensolver (as iesh_syev_batched, FP64) for
+                          profile 1; 1: the dense solver always */
 } iesh2_model;
 
 /* Create a context for up to max_traj trajectories; precision

@@ -211,6 +211,55 @@ static iesh_status copy_out(iesh_ctx *ctx, void *dst, const void *src, size_t by
     return IESH_OK;
 }
 
+// ------------------------------------------------------------- ensemble
+// Condition of the ensemble's device loop: after each chunk, continue while
+// some context has a live trajectory and the step cap is not reached.
+__global__ void k_ensemble_cond(cudaGraphConditionalHandle h, const int32_t *const *n_live, int n_ctx,
+                                int64_t *steps, const int64_t *max_steps, int64_t chunk, int64_t *live_out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t live = 0;
+    for (int c = 0; c < n_ctx; ++c) live += *n_live[c];
+    const int64_t st = *steps + chunk;
+    *steps = st;
+    *live_out = live;
+    cudaGraphSetConditional(h, (live > 0 && st < *max_steps) ? 1u : 0u);
+}
+
+struct iesh_ensemble {
+    std::vector<iesh_ctx *> ctxs;
+    cudaStream_t stream = nullptr;   // launch stream (the caller's)
+    cudaStream_t capture = nullptr;  // own stream for building the loop body
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const int32_t **n_live_dev = nullptr;  // [n_ctx] device pointers of the live counts
+    int64_t *counters = nullptr;           // device: steps, max_steps, live
+    cudaEvent_t ev = nullptr;
+    int64_t chunk = 0;
+    std::string err;
+};
+
+static iesh_status efail(iesh_ensemble *e, iesh_status s, const char *fmt, ...)
+{
+    if (e) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        e->err = buf;
+    }
+    return s;
+}
+
+#define CUE(call)                                                                            \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return efail(ens, IESH_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                         __FILE__, __LINE__);                                                \
+    } while (0)
+
 // ----------------------------------------------------------------- C-ABI
 extern "C" {
 
@@ -538,37 +587,45 @@ iesh_status iesh_get_records(iesh_ctx *ctx, double *pop_sh, double *pop_wf, int6
     return IESH_OK;
 }
 
-iesh_status iesh_run(iesh_ctx *ctx, double dt, int64_t n_steps, uint64_t seed)
+// Enqueue n_steps steps on stream st (the context's own stream for
+// iesh_run, the ensemble's capture stream for iesh_ensemble_create).  With
+// compact_on_cadence the work list is compacted every compact_every steps.
+static iesh_status enqueue_steps(iesh_ctx *ctx, double dt, int64_t n_steps, uint64_t seed, cudaStream_t st,
+                                 bool compact_on_cadence)
 {
-    if (!ctx) return IESH_EINVAL;
-    if (!ctx->have_state) return fail(ctx, IESH_ESTATE, "run before init_state/set_state");
-    if (!(dt > 0.0) || n_steps < 0) return fail(ctx, IESH_EINVAL, "need dt > 0 and n_steps >= 0");
     const DevState &d = ctx->ds;
     const bool mx = ctx->mixed;
     // Chebyshev truncation: FP64 rounding level, or FP32 level for the mixed path
     const double tol = ctx->opt.prop_tol > 0.0 ? ctx->opt.prop_tol : (mx ? 1e-7 : 1e-15);
     // unitarity check of the coefficient columns after each step
     const double ntol = ctx->opt.norm_tol != 0.0 ? ctx->opt.norm_tol : (mx ? 1e-3 : 1e-8);
+    auto tm = [&](int cls, auto fn) { return ctx->timer.run(st, cls, fn); };
     for (int64_t k = 0; k < n_steps; ++k) {
-        CU(timed(ctx, IESH_K_EIGEN, [&] { return launch_eigen(d, ctx->md, dt, 1, ctx->stream); }));
+        CU(tm(IESH_K_EIGEN, [&] { return launch_eigen(d, ctx->md, dt, 1, st); }));
         if (d.propagator == IESH_PROP_OVERLAP) {
-            CU(timed(ctx, IESH_K_PROPAGATE, [&] { return launch_overlap(d, dt, ctx->stream); }));
+            CU(tm(IESH_K_PROPAGATE, [&] { return launch_overlap(d, dt, st); }));
         } else {
-            CU(timed(ctx, IESH_K_COUPLING,
-                     [&] { return launch_coupling(d, dt, ctx->model.mass, tol, mx, ctx->stream); }));
-            CU(timed(ctx, IESH_K_PROPAGATE, [&] { return launch_cheb(d, dt, mx, ctx->stream); }));
+            CU(tm(IESH_K_COUPLING, [&] { return launch_coupling(d, dt, ctx->model.mass, tol, mx, st); }));
+            CU(tm(IESH_K_PROPAGATE, [&] { return launch_cheb(d, dt, mx, st); }));
         }
-        CU(timed(ctx, IESH_K_HOP, [&] {
-            return launch_hop(d, dt, ctx->model.mass, seed, ctx->opt.skip_bound, nullptr, ctx->stream, mx);
+        CU(tm(IESH_K_HOP, [&] {
+            return launch_hop(d, dt, ctx->model.mass, seed, ctx->opt.skip_bound, nullptr, st, mx);
         }));
-        if (ntol > 0.0)
-            CU(timed(ctx, IESH_K_OTHER, [&] { return launch_norm_check(d, mx, ntol, ctx->stream); }));
+        if (ntol > 0.0) CU(tm(IESH_K_OTHER, [&] { return launch_norm_check(d, mx, ntol, st); }));
+        if (!compact_on_cadence) continue;
         ++ctx->steps_since_init;
         if (ctx->opt.compact_every > 0 && ctx->steps_since_init % ctx->opt.compact_every == 0)
-            CU(timed(ctx, IESH_K_OTHER,
-                     [&] { return launch_compact(d, ctx->live, ctx->n_live, ctx->stream); }));
+            CU(tm(IESH_K_OTHER, [&] { return launch_compact(d, ctx->live, ctx->n_live, st); }));
     }
     return IESH_OK;
+}
+
+iesh_status iesh_run(iesh_ctx *ctx, double dt, int64_t n_steps, uint64_t seed)
+{
+    if (!ctx) return IESH_EINVAL;
+    if (!ctx->have_state) return fail(ctx, IESH_ESTATE, "run before init_state/set_state");
+    if (!(dt > 0.0) || n_steps < 0) return fail(ctx, IESH_EINVAL, "need dt > 0 and n_steps >= 0");
+    return enqueue_steps(ctx, dt, n_steps, seed, ctx->stream, true);
 }
 
 iesh_status iesh_get_live(iesh_ctx *ctx, int64_t *n_live)
@@ -844,6 +901,126 @@ iesh_status iesh_check(iesh_ctx *ctx, uint32_t *bits)
     if (h[0] & IESH_TRAJ_SECULAR_NONCONV) return IESH_ENONCONV;
     if (h[0] & IESH_TRAJ_SINGULAR) return IESH_ESINGULAR;
     if (h[0] & IESH_TRAJ_NORM_DRIFT) return IESH_ENORM;
+    return IESH_OK;
+}
+
+// ------------------------------------------------------------- ensemble
+const char *iesh_ensemble_last_error(const iesh_ensemble *ens)
+{
+    return ens ? ens->err.c_str() : "null ensemble";
+}
+
+iesh_status iesh_ensemble_destroy(iesh_ensemble *ens)
+{
+    if (!ens) return IESH_OK;
+    if (ens->stream) cudaStreamSynchronize(ens->stream);
+    if (ens->capture) cudaStreamSynchronize(ens->capture);
+    if (ens->exec) cudaGraphExecDestroy(ens->exec);
+    if (ens->graph) cudaGraphDestroy(ens->graph);
+    if (ens->n_live_dev) cudaFree(ens->n_live_dev);
+    if (ens->counters) cudaFree(ens->counters);
+    if (ens->ev) cudaEventDestroy(ens->ev);
+    if (ens->capture) cudaStreamDestroy(ens->capture);
+    delete ens;
+    return IESH_OK;
+}
+
+iesh_status iesh_ensemble_create(iesh_ensemble **out, iesh_ctx *const *ctxs, int n_ctx, double dt,
+                                 int64_t chunk, uint64_t seed, void *cuda_stream)
+{
+    if (!out) return IESH_EINVAL;
+    *out = nullptr;
+    iesh_ensemble *ens = new iesh_ensemble();
+    *out = ens;
+    ens->stream = (cudaStream_t)cuda_stream;
+    ens->chunk = chunk;
+    if (!ctxs || n_ctx < 1) return efail(ens, IESH_EINVAL, "need at least one context");
+    if (!(dt > 0.0) || chunk < 1) return efail(ens, IESH_EINVAL, "need dt > 0 and chunk >= 1");
+    for (int c = 0; c < n_ctx; ++c) {
+        iesh_ctx *ctx = ctxs[c];
+        if (!ctx) return efail(ens, IESH_EINVAL, "context %d is NULL", c);
+        if (!ctx->have_state) return efail(ens, IESH_ESTATE, "context %d has no state", c);
+        if (ctx->opt.compact_every <= 0)
+            return efail(ens, IESH_EINVAL, "context %d has no work list (compact_every = 0)", c);
+        if (ctx->timer.on) return efail(ens, IESH_ESTATE, "context %d has profiling on", c);
+        ens->ctxs.push_back(ctx);
+    }
+    CUE(cudaStreamCreateWithFlags(&ens->capture, cudaStreamNonBlocking));
+    CUE(cudaEventCreateWithFlags(&ens->ev, cudaEventDisableTiming));
+    CUE(cudaMalloc((void **)&ens->n_live_dev, n_ctx * sizeof(int32_t *)));
+    CUE(cudaMalloc((void **)&ens->counters, 3 * sizeof(int64_t)));
+    std::vector<const int32_t *> nl;
+    for (auto *ctx : ens->ctxs) nl.push_back(ctx->n_live);
+    CUE(cudaMemcpy(ens->n_live_dev, nl.data(), n_ctx * sizeof(int32_t *), cudaMemcpyHostToDevice));
+    CUE(cudaMemset(ens->counters, 0, 3 * sizeof(int64_t)));
+    // graph: one while node; its body advances every context by `chunk`
+    // steps, compacts every work list and sets the loop condition
+    CUE(cudaGraphCreate(&ens->graph, 0));
+    cudaGraphConditionalHandle h;
+    CUE(cudaGraphConditionalHandleCreate(&h, ens->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CUE(cudaGraphAddNode(&node, ens->graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CUE(cudaStreamBeginCaptureToGraph(ens->capture, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    for (auto *ctx : ens->ctxs) {
+        iesh_status st = enqueue_steps(ctx, dt, chunk, seed, ens->capture, false);
+        if (st == IESH_OK) {
+            cudaError_t e = launch_compact(ctx->ds, ctx->live, ctx->n_live, ens->capture);
+            if (e != cudaSuccess) st = fail(ctx, IESH_ECUDA, "launch_compact: %s", cudaGetErrorString(e));
+        }
+        if (st != IESH_OK) {
+            cudaGraph_t g;
+            cudaStreamEndCapture(ens->capture, &g);
+            return efail(ens, st, "capturing a context's steps: %s", ctx->err.c_str());
+        }
+    }
+    k_ensemble_cond<<<1, 32, 0, ens->capture>>>(h, ens->n_live_dev, n_ctx, ens->counters, ens->counters + 1,
+                                                chunk, ens->counters + 2);
+    CUE(cudaGetLastError());
+    CUE(cudaStreamEndCapture(ens->capture, &body));
+    CUE(cudaGraphInstantiate(&ens->exec, ens->graph, 0));
+    return IESH_OK;
+}
+
+iesh_status iesh_ensemble_run(iesh_ensemble *ens, int64_t max_steps)
+{
+    if (!ens || !ens->exec) return IESH_EINVAL;
+    if (max_steps < 1) return efail(ens, IESH_EINVAL, "max_steps must be >= 1");
+    // the contexts' earlier work (set-up, copies) comes first
+    for (auto *ctx : ens->ctxs) {
+        CUE(cudaEventRecord(ens->ev, ctx->stream));
+        CUE(cudaStreamWaitEvent(ens->stream, ens->ev, 0));
+    }
+    // step cap counted from the device loop's own step counter
+    int64_t now = 0;
+    CUE(cudaMemcpyAsync(&now, ens->counters, sizeof now, cudaMemcpyDeviceToHost, ens->stream));
+    CUE(cudaStreamSynchronize(ens->stream));
+    const int64_t cap = now + max_steps;
+    CUE(cudaMemcpyAsync(ens->counters + 1, &cap, sizeof cap, cudaMemcpyHostToDevice, ens->stream));
+    CUE(cudaStreamSynchronize(ens->stream));  // the copy reads a host stack variable
+    CUE(cudaGraphLaunch(ens->exec, ens->stream));
+    // later calls on the contexts come after the loop
+    CUE(cudaEventRecord(ens->ev, ens->stream));
+    for (auto *ctx : ens->ctxs) {
+        CUE(cudaStreamWaitEvent(ctx->stream, ens->ev, 0));
+        ctx->steps_since_init = 0;  // the loop compacts at the end of every chunk
+    }
+    return IESH_OK;
+}
+
+iesh_status iesh_ensemble_status(iesh_ensemble *ens, int64_t *steps_done, int64_t *live)
+{
+    if (!ens) return IESH_EINVAL;
+    int64_t h[3] = {0, 0, 0};
+    CUE(cudaMemcpyAsync(h, ens->counters, sizeof h, cudaMemcpyDeviceToHost, ens->stream));
+    CUE(cudaStreamSynchronize(ens->stream));
+    if (steps_done) *steps_done = h[0];
+    if (live) *live = h[2];
     return IESH_OK;
 }
 

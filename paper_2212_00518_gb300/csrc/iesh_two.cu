@@ -54,6 +54,7 @@
 #include "iesh_host.h"
 #include "iesh_kernels.h"
 #include "iesh_secular.cuh"
+#include "iesh_syev.cuh"
 
 using namespace iesh;
 
@@ -65,6 +66,11 @@ struct Model2Dev {
     double vbar[2], R[6], x0[6];
     double mass, omega;
     double wsum;    // sum_k w_k of the bath
+    // dense-solver models: the coupling of orbital a to bath state k is
+    // vbar_a f_a(x) prof[a M + k] (prof = sqrt(w_k) times the orbital's own
+    // bath profile), pnorm[a] = |prof[a]|
+    const double *prof;
+    double pnorm[2];
 };
 
 // Adsorbate quantities at one geometry: levels h_a, coupling amplitudes c_a
@@ -157,8 +163,8 @@ __device__ __forceinline__ void occ_sums(const double *lam, const double *Q0, co
 
 // Per-trajectory scalars of the eigen kernel (one slot's shared record).
 struct Eig2Slot {
-    Ads2 ad;
-    double x[6], p[6];
+    Ads2 ad, adp;  // at the step's end and start (mode 1)
+    double x[6], p[6], xp[6];
     double c, hp, hm, tt;
     int pos, case_;  // pos: bath poles below h_-; case_: 0 general, 1 |-> decoupled, 2 no coupling
 };
@@ -207,6 +213,7 @@ __global__ void __launch_bounds__(256, 2) k2_eigen(DevState s, Model2Dev md, dou
             double x = s.x[t * 6 + r], p = s.p[t * 6 + r];
             if (mode == 1) {
                 s.x_prev[t * 6 + r] = x;
+                sl->xp[r] = x;
                 p += 0.5 * dt * s.F[t * 6 + r];
                 x += dt * p / md.mass;
             }
@@ -219,6 +226,7 @@ __global__ void __launch_bounds__(256, 2) k2_eigen(DevState s, Model2Dev md, dou
     if (act && r == 0) {
         const Ads2 ad = ads2_eval(md, sl->x);
         sl->ad = ad;
+        if (mode == 1) sl->adp = ads2_eval(md, sl->xp);
         const double c0 = ad.c[0], c1 = ad.c[1], csq = c0 * c0 + c1 * c1;
         if (!(csq > 0.0)) {
             sl->case_ = 2;
@@ -343,6 +351,31 @@ __global__ void __launch_bounds__(256, 2) k2_eigen(DevState s, Model2Dev md, dou
             // (-c_1, c_0) / c; a unit adsorbate vector (+) when one coupling vanishes
             Q0_s[below] = c0 == 0.0 ? 1.0 : (c1 == 0.0 ? 0.0 : -c1 / c);
             Q1_s[below] = c0 == 0.0 ? 0.0 : (c1 == 0.0 ? 1.0 : c0 / c);
+        }
+    }
+    __syncthreads();
+    // In a step, an eigenvector whose overlap with the previous step's is
+    // decisive (|overlap| >= 1/2) keeps it non-negative (the positive |+>
+    // component alone flips the |->-like eigenvector where h_0 = h_1 and t
+    // changes sign); at an eigenvalue crossing within the step the positive
+    // |+> component stands.  The bath rows follow from the adsorbate rows,
+    // B_kj = sqrt(w_k) A_j / (lam_j - eps_k) with A_j = c_0 Q_0j + c_1 Q_1j;
+    // FP32 sums (only the comparison with -1/2 is used).
+    if (act && mode == 1 && cs != 2) {
+        const double q0 = Q0_s[r], q1 = Q1_s[r], lj = lam_s[r];
+        const double p0 = s.q0_prev[t * N + r], p1 = s.q2_prev[t * N + r], lp = s.lam_prev[t * N + r];
+        const Ads2 &adp = sl->adp;
+        const float Aj = (float)(c0 * q0 + c1 * q1), Ap = (float)(adp.c[0] * p0 + adp.c[1] * p1);
+        float acc = 0.0f;
+        for (int k = 0; k < M; ++k) {
+            const float den = (float)(lj - eps_s[k]) * (float)(lp - eps_s[k]);
+            const float w = (float)(s.z0[k] * s.z0[k]);
+            if (den != 0.0f) acc += w / den;
+        }
+        const float ov = (float)(q0 * p0 + q1 * p1) + Aj * Ap * acc;
+        if (ov <= -0.5f) {
+            Q0_s[r] = -q0;
+            Q1_s[r] = -q1;
         }
     }
     __syncthreads();
@@ -619,6 +652,186 @@ __global__ void __launch_bounds__(64) k2_accept(DevState s, Model2Dev md)
     }
 }
 
+// ------------------------------------------------ dense eigensolver path
+// Two adsorbate orbitals whose couplings to the bath are not parallel (each
+// orbital with its own bath profile) have no rank-two secular reduction;
+// their eigenpairs come from the dense symmetric eigensolver of
+// iesh_syev.cuh in three launches per step:
+//   k2g_reduce  kick + drift (mode 1), H(x) built in shared memory (or in
+//               the trajectory's scratch for large N), Householder reduction
+//               with row 1 of the reflector product tracked;
+//   k2g_ql      QL iterations, one trajectory per thread, rotating the
+//               adsorbate rows (row 0 of P is e_0, row 1 tracked);
+//   k2g_finish  ascending order, gauge, forces, second kick.
+// Everything after the eigenpairs (couplings, propagation, hops, rescale) is
+// the rank-two path's: those kernels read only the eigenvalues and the two
+// adsorbate rows, because the closed form of Q^T (dH/dy) Q above holds for
+// any couplings of the form f_a(x) times a fixed vector over the bath.
+//
+// Gauge (reading R17): eigenvector j has sum_a c_a |prof_a| Q_aj >= 0, the
+// rank-two path's rule; in a step, a decisive overlap with the previous
+// step's eigenvector j (|overlap| >= 1/2) overrules it and is made
+// non-negative.  The overlap uses the eigenvectors' bath rows, which follow
+// from the adsorbate rows: B_kj = sum_a V_ak Q_aj / (lam_j - eps_k).
+
+// Scratch of a trajectory: d[N], e[N], tracked rows Y[N][2], then the matrix
+// (N x (N | 1)) when it does not fit in shared memory.
+constexpr size_t kDenseSmemCap = 200 * 1024;
+
+__host__ __device__ inline int dense_lda(int N) { return N | 1; }
+
+__host__ __device__ inline bool dense_in_smem(int N)
+{
+    return (size_t)N * dense_lda(N) * 8 + (size_t)(6 * N + 8) * 8 <= kDenseSmemCap;
+}
+
+__global__ void __launch_bounds__(256) k2g_reduce(DevState s, Model2Dev md, double dt, int mode)
+{
+    extern __shared__ __align__(16) double g2_sh[];
+    __shared__ double xs[6];
+    const int64_t t = traj_of(s, blockIdx.x);
+    if (t < 0 || (s.status[t] & ST_DONE)) return;
+    const int N = s.N, M = s.M, lda = dense_lda(N), tid = threadIdx.x;
+    if (mode == 1)
+        for (int i = tid; i < N; i += blockDim.x) {
+            s.lam_prev[t * N + i] = s.lam[t * N + i];
+            s.q0_prev[t * N + i] = s.q0[t * N + i];
+            s.q2_prev[t * N + i] = s.q2[t * N + i];
+        }
+    if (tid < 6) {
+        double x = s.x[t * 6 + tid];
+        if (mode == 1) {
+            double p = s.p[t * 6 + tid];
+            s.x_prev[t * 6 + tid] = x;
+            p += 0.5 * dt * s.F[t * 6 + tid];
+            x += dt * p / md.mass;
+            s.x[t * 6 + tid] = x;
+            s.p[t * 6 + tid] = p;
+        }
+        xs[tid] = x;
+    }
+    __syncthreads();
+    const Ads2 ad = ads2_eval(md, xs);
+    double *v = g2_sh, *w = v + N, *r1 = w + N, *d = r1 + N, *e = d + N, *tau = e + N, *sh = tau + N;
+    double *out = s.scratch + t * s.scratch_stride;  // d, e, Y
+    double *A = dense_in_smem(N) ? sh + 8 : out + 4 * N;
+    for (int idx = tid; idx < N * lda; idx += blockDim.x) A[idx] = 0.0;
+    __syncthreads();
+    if (tid < 2) A[(size_t)tid * lda + tid] = ad.h[tid];
+    for (int k = tid; k < M; k += blockDim.x) {
+        const double v0 = ad.c[0] * md.prof[k], v1 = ad.c[1] * md.prof[M + k];
+        A[(size_t)(2 + k) * lda + 2 + k] = s.eps[k];
+        A[(size_t)k + 2] = v0;
+        A[(size_t)(2 + k) * lda] = v0;
+        A[(size_t)lda + 2 + k] = v1;
+        A[(size_t)(2 + k) * lda + 1] = v1;
+    }
+    __syncthreads();
+    householder_tridiag<double>(A, lda, N, d, e, tau, v, w, r1, sh);
+    for (int i = tid; i < N; i += blockDim.x) {
+        out[i] = d[i];
+        out[N + i] = e[i];
+        out[2 * N + 2 * i] = i == 0 ? 1.0 : 0.0;
+        out[2 * N + 2 * i + 1] = r1[i];
+    }
+}
+
+__global__ void __launch_bounds__(128) k2g_ql(DevState s)
+{
+    const int64_t t = traj_of(s, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (t < 0 || (s.status[t] & ST_DONE)) return;
+    const int N = s.N;
+    double *b = s.scratch + t * s.scratch_stride;
+    if (!ql_implicit<double>(N, b, b + N, b + 2 * N, 2)) atomicOr(&s.status[t], ST_SECULAR);
+}
+
+__global__ void __launch_bounds__(256) k2g_finish(DevState s, Model2Dev md, double dt, int mode)
+{
+    extern __shared__ __align__(16) double f2_sh[];
+    __shared__ double xs[6], ps[6], xp[6], red[32];
+    const int64_t t = traj_of(s, blockIdx.x);
+    if (t < 0 || (s.status[t] & ST_DONE)) return;
+    const int N = s.N, M = s.M, Ne = s.Ne, tid = threadIdx.x;
+    double *ev = f2_sh, *y0 = ev + N, *y1 = y0 + N, *lam_s = y1 + N, *Q0_s = lam_s + N, *Q1_s = Q0_s + N;
+    const double *b = s.scratch + t * s.scratch_stride;
+    if (tid < 6) {
+        xs[tid] = s.x[t * 6 + tid];
+        ps[tid] = s.p[t * 6 + tid];
+        xp[tid] = s.x_prev[t * 6 + tid];
+    }
+    for (int i = tid; i < N; i += blockDim.x) {
+        ev[i] = b[i];
+        y0[i] = b[2 * N + 2 * i];
+        y1[i] = b[2 * N + 2 * i + 1];
+    }
+    __syncthreads();
+    const Ads2 ad = ads2_eval(md, xs);
+    for (int i = tid; i < N; i += blockDim.x) {  // ascending, ties by index
+        const double li = ev[i];
+        int r = 0;
+        for (int j = 0; j < N; ++j) r += (ev[j] < li) || (ev[j] == li && j < i);
+        lam_s[r] = li;
+        Q0_s[r] = y0[i];
+        Q1_s[r] = y1[i];
+    }
+    __syncthreads();
+    {
+        const double g0 = ad.c[0] * md.pnorm[0], g1 = ad.c[1] * md.pnorm[1];
+        for (int j = tid; j < N; j += blockDim.x)
+            if (g0 * Q0_s[j] + g1 * Q1_s[j] < 0.0) {
+                Q0_s[j] = -Q0_s[j];
+                Q1_s[j] = -Q1_s[j];
+            }
+    }
+    if (mode == 1) {
+        // overlap with the previous step's eigenvector j (bath rows rebuilt
+        // from the adsorbate rows; FP32 sums: only the comparison with -1/2
+        // is used)
+        const Ads2 adp = ads2_eval(md, xp);
+        for (int j = tid; j < N; j += blockDim.x) {
+            const double q0 = Q0_s[j], q1 = Q1_s[j], lj = lam_s[j];
+            const double p0 = s.q0_prev[t * N + j], p1 = s.q2_prev[t * N + j], lp = s.lam_prev[t * N + j];
+            const float a0 = (float)(ad.c[0] * q0), a1 = (float)(ad.c[1] * q1);
+            const float b0 = (float)(adp.c[0] * p0), b1 = (float)(adp.c[1] * p1);
+            float ov = (float)(q0 * p0 + q1 * p1);
+            for (int k = 0; k < M; ++k) {
+                const float f0 = (float)md.prof[k], f1 = (float)md.prof[M + k];
+                const float den = (float)(lj - s.eps[k]) * (float)(lp - s.eps[k]);
+                if (den != 0.0f) ov += (a0 * f0 + a1 * f1) * (b0 * f0 + b1 * f1) / den;
+            }
+            if (ov <= -0.5f) {
+                Q0_s[j] = -q0;
+                Q1_s[j] = -q1;
+            }
+        }
+    }
+    __syncthreads();
+    for (int j = tid; j < N; j += blockDim.x) {
+        s.lam[t * N + j] = lam_s[j];
+        s.q0[t * N + j] = Q0_s[j];
+        s.q2[t * N + j] = Q1_s[j];
+        if (mode == 0) s.lam_prev[t * N + j] = lam_s[j];
+    }
+    double S[2], U[2];
+    occ_sums(lam_s, Q0_s, Q1_s, s.occ + t * Ne, Ne, ad, red, S, U);
+    if (tid < 6) {
+        const double F = force2(md, ad, xs, tid, S, U);
+        double p = ps[tid];
+        if (mode == 1) p += 0.5 * dt * F;
+        s.p[t * 6 + tid] = p;
+        s.F[t * 6 + tid] = F;
+        if (mode == 0) s.vprev[t * 6 + tid] = p / md.mass;
+        ps[tid] = p;
+    }
+    __syncthreads();
+    if (tid == 0) write_geo2(s, t, md, ad, ps);
+}
+
+size_t dense_reduce_smem(int N)
+{
+    return (size_t)(6 * N + 8) * sizeof(double) + (dense_in_smem(N) ? (size_t)N * dense_lda(N) * sizeof(double) : 0);
+}
+
 // Shared memory of k2_eigen with tpb slots.
 size_t eigen2_smem(int N, int M, int tpb, bool df)
 {
@@ -635,6 +848,7 @@ struct iesh2_ctx {
     int N = 0, M = 0, Ne = 0;
     int skip_bound = 0;
     bool mixed = false;
+    bool dense = false;  // eigenpairs from the dense symmetric eigensolver
     Model2Dev md;
     DevState ds;
     std::vector<void *> allocs;
@@ -692,6 +906,15 @@ cudaError_t launch_eigen2(iesh2_ctx *ctx, double dt, int mode)
 {
     const DevState &d = ctx->ds;
     if (d.n == 0) return cudaSuccess;
+    if (ctx->dense) {
+        k2g_reduce<<<(unsigned)d.n, 256, dense_reduce_smem(d.N), ctx->stream>>>(d, ctx->md, dt, mode);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k2g_ql<<<(unsigned)((d.n + 127) / 128), 128, 0, ctx->stream>>>(d);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k2g_finish<<<(unsigned)d.n, 256, (size_t)6 * d.N * sizeof(double), ctx->stream>>>(d, ctx->md, dt, mode);
+        return cudaGetLastError();
+    }
     const int tpb = eigen_tpb(d.N);
     const int threads = (tpb * d.N + 31) & ~31;
     const unsigned blocks = (unsigned)((d.n + tpb - 1) / tpb);
@@ -764,7 +987,14 @@ iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int precisio
         return fail2(ctx, IESH_EINVAL, "coupling widths theta[14], theta[15] must be nonzero");
     if (precision != IESH_PREC_FP64 && precision != IESH_PREC_MIXED)
         return fail2(ctx, IESH_EINVAL, "unknown precision %d", precision);
+    if (model->profile != 0 && model->profile != 1)
+        return fail2(ctx, IESH_EINVAL, "unknown coupling profile %d", model->profile);
+    if (model->profile == 1 && !(model->prof_width[0] > 0.0 && model->prof_width[1] > 0.0))
+        return fail2(ctx, IESH_EINVAL, "profile widths must be positive");
+    if (model->eigensolver != 0 && model->eigensolver != 1)
+        return fail2(ctx, IESH_EINVAL, "unknown eigensolver %d", model->eigensolver);
     ctx->mixed = precision == IESH_PREC_MIXED;
+    ctx->dense = model->profile == 1 || model->eigensolver == 1;
     ctx->N = N;
     ctx->M = M;
     ctx->Ne = Ne;
@@ -796,9 +1026,11 @@ iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int precisio
     d.Ne = Ne;
     const size_t T = (size_t)max_traj;
     d.scratch_stride = std::max<int64_t>((int64_t)N * N, 3LL * Ne * N + Ne);
+    if (ctx->dense)  // d, e, tracked rows and the matrix when it is not in shared memory
+        d.scratch_stride = std::max<int64_t>(d.scratch_stride, 4LL * N + (int64_t)N * dense_lda(N));
     d.scratch_stride = (d.scratch_stride + 31) & ~31LL;
     iesh_status st;
-    double *eps_d = nullptr, *sq_d = nullptr, *Cd = nullptr;
+    double *eps_d = nullptr, *sq_d = nullptr, *Cd = nullptr, *prof_d = nullptr;
 #define A2(ptr, cnt) if ((st = dalloc2(ctx, &(ptr), (cnt))) != IESH_OK) return st;
     A2(d.x, T * 6) A2(d.p, T * 6) A2(d.F, T * 6) A2(d.vprev, T * 6) A2(d.x_prev, T * 6)
     A2(d.occ, T * Ne)
@@ -810,7 +1042,7 @@ iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int precisio
     A2(d.status, T) A2(d.nstep, T) A2(d.hops, T) A2(d.frus, T)
     A2(d.scratch, T * (size_t)d.scratch_stride)
     A2(d.cheb, T * kChebStride)
-    A2(eps_d, (size_t)M) A2(sq_d, (size_t)M)
+    A2(eps_d, (size_t)M) A2(sq_d, (size_t)M) A2(prof_d, (size_t)2 * M)
     float2 *poledf = nullptr;
     if (ctx->mixed) A2(poledf, (size_t)M * M)
 #undef A2
@@ -828,6 +1060,32 @@ iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int precisio
                              (int)eigen2_smem(N, M, eigen_tpb(N), true)));
     CU2(cudaMemcpyAsync(eps_d, eps.data(), M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CU2(cudaMemcpyAsync(sq_d, sq.data(), M * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    // coupling profiles of the dense path: sqrt(w_k), times the Lorentzian
+    // 1 / sqrt(1 + ((eps_k - centre_a) / width_a)^2) of each orbital (profile 1)
+    std::vector<double> prof((size_t)2 * M);
+    for (int a = 0; a < 2; ++a) {
+        double nrm = 0.0;
+        for (int i = 0; i < M; ++i) {
+            double v = sq[i];
+            if (model->profile == 1) {
+                const double u = (eps[i] - model->prof_center[a]) / model->prof_width[a];
+                v /= std::sqrt(1.0 + u * u);
+            }
+            prof[(size_t)a * M + i] = v;
+            nrm += v * v;
+        }
+        k.pnorm[a] = std::sqrt(nrm);
+    }
+    k.prof = prof_d;
+    CU2(cudaMemcpyAsync(prof_d, prof.data(), prof.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    if (ctx->dense && dense_reduce_smem(N) > 48 * 1024) {
+        // process-wide attribute: only ever raised
+        cudaFuncAttributes fa;
+        CU2(cudaFuncGetAttributes(&fa, k2g_reduce));
+        if (fa.maxDynamicSharedSizeBytes < (int)dense_reduce_smem(N))
+            CU2(cudaFuncSetAttribute(k2g_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(kDenseSmemCap + 2048)));
+    }
     std::vector<float2> pf;
     if (ctx->mixed) {
         // bath pole differences eps_o - eps_k as double-float pairs, [k][o]

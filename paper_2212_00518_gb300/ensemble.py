@@ -1,9 +1,15 @@
 """Uneven batches: trajectories of different bath sizes (one context per
 model) and lifetimes (trajectories end on leaving the surface), advanced
 together.  Each context keeps a device work list of its live trajectories,
-compacted on the device every `compact_every` steps, and the step kernels of
-all contexts for a chunk of steps are captured once into one CUDA graph and
-replayed until every trajectory has finished or the step cap is reached.
+compacted on the device every `compact_every` steps.
+
+Two drivers: the device loop (default) is one launch of a CUDA graph whose
+conditional while node repeats a chunk of steps of every context plus the
+compactions until no trajectory is live or the step cap is reached (the
+library's iesh_ensemble); the host loop captures one chunk with
+torch.cuda.graph and replays it, checking the live count on the host
+between chunks.  Live trajectory-steps are counted exactly, from the
+trajectories' own step counters.
 """
 import numpy as np
 
@@ -39,6 +45,7 @@ class UnevenBatch:
                                   occ, C)
                 self.ctxs.append(ctx)
         self.graph = None
+        self.ens = None
         self.steps_done = 0
 
     def _eager_chunk(self):
@@ -58,26 +65,43 @@ class UnevenBatch:
     def live(self):
         return sum(c.live_count() for c in self.ctxs)
 
-    def run(self, max_steps, use_graph=True):
-        """Advance until all trajectories finished or max_steps; returns the
-        number of live trajectory-steps executed."""
+    def live_steps(self):
+        """Trajectory-steps taken so far by live trajectories (a trajectory's
+        step counter stops when it finishes)."""
+        return int(sum(int(c.counters()[0].sum()) for c in self.ctxs))
+
+    def run(self, max_steps, use_graph=True, device_loop=True):
+        """Advance until all trajectories finished or max_steps (counted from
+        the start, whole chunks); returns the number of live trajectory-steps
+        executed by this call.  device_loop: one launch of the library's
+        device-side loop; else a host loop replaying a captured chunk
+        (use_graph) or running it eagerly."""
         torch = self.torch
-        live_steps = 0
-        with torch.cuda.stream(self.stream):
-            while self.steps_done < max_steps:
-                n_live = self.live()
-                if n_live == 0:
-                    break
-                if use_graph:
-                    if self.graph is None:
-                        self.capture()
-                    self.graph.replay()
-                else:
-                    self._eager_chunk()
-                live_steps += n_live * self.chunk
-                self.steps_done += self.chunk
+        before = self.live_steps()
+        if device_loop and use_graph:
+            if self.ens is None:
+                self.ens = _I.Ensemble(self.ctxs, self.dt, self.chunk, seed=self.seed,
+                                       stream=self.stream.cuda_stream)
+            todo = max_steps - self.steps_done
+            if todo > 0 and self.live() > 0:
+                start, _ = self.ens.status()
+                self.ens.run(todo)
+                done, _ = self.ens.status()  # synchronises the stream
+                self.steps_done += done - start
+        else:
+            with torch.cuda.stream(self.stream):
+                while self.steps_done < max_steps:
+                    if self.live() == 0:
+                        break
+                    if use_graph:
+                        if self.graph is None:
+                            self.capture()
+                        self.graph.replay()
+                    else:
+                        self._eager_chunk()
+                    self.steps_done += self.chunk
         torch.cuda.synchronize()
-        return live_steps
+        return self.live_steps() - before
 
     def results(self):
         """Per trajectory (in the batch's original order): x, p, occ-free
@@ -99,5 +123,8 @@ class UnevenBatch:
         return dict(x=x, p=p, hops=hops, nstep=nstep, status=status)
 
     def close(self):
+        if self.ens is not None:
+            self.ens.close()
+            self.ens = None
         for c in self.ctxs:
             c.close()

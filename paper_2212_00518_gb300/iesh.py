@@ -62,7 +62,9 @@ class _Model2(ctypes.Structure):
                 ("band_hi", ctypes.c_double), ("mu", ctypes.c_double), ("mass", ctypes.c_double),
                 ("omega", ctypes.c_double), ("x0", ctypes.c_double * 6),
                 ("theta", ctypes.c_double * 16), ("vbar", ctypes.c_double * 2),
-                ("R", ctypes.c_double * 6)]
+                ("R", ctypes.c_double * 6), ("profile", ctypes.c_int),
+                ("prof_center", ctypes.c_double * 2), ("prof_width", ctypes.c_double * 2),
+                ("eigensolver", ctypes.c_int)]
 
 
 class _Options(ctypes.Structure):
@@ -83,7 +85,9 @@ EXPORTS = ["iesh_create", "iesh_destroy", "iesh_bath", "iesh_init_state", "iesh_
            "iesh2_destroy", "iesh2_last_error", "iesh2_set_state", "iesh2_get_state", "iesh2_run",
            "iesh2_get_eigen", "iesh2_hop_probabilities", "iesh2_get_counters", "iesh2_profile",
            "iesh2_profile_read", "iesh_checkpoint_bytes", "iesh_checkpoint_save",
-           "iesh_checkpoint_load", "iesh_observables", "iesh_check"]
+           "iesh_checkpoint_load", "iesh_observables", "iesh_check", "iesh_syev_work_bytes",
+           "iesh_syev_batched", "iesh_ensemble_create", "iesh_ensemble_run",
+           "iesh_ensemble_status", "iesh_ensemble_destroy", "iesh_ensemble_last_error"]
 KERNEL_CLASSES = ["eigen", "coupling", "propagate", "hop", "other"]
 
 _lib = None
@@ -145,6 +149,16 @@ def load(path=LIB_PATH):
     L.iesh_checkpoint_load.argtypes = [_vp, _vp, ctypes.c_size_t]
     L.iesh_observables.argtypes = [_vp, _vp, _vp, _vp, _vp]
     L.iesh_check.argtypes = [_vp, _vp]
+    L.iesh_ensemble_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, _vp]
+    L.iesh_ensemble_run.argtypes = [_vp, ctypes.c_int64]
+    L.iesh_ensemble_status.argtypes = [_vp, _vp, _vp]
+    L.iesh_ensemble_destroy.argtypes = [_vp]
+    L.iesh_ensemble_last_error.argtypes = [_vp]
+    L.iesh_ensemble_last_error.restype = ctypes.c_char_p
+    L.iesh_syev_work_bytes.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.iesh_syev_batched.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp,
+                                    _vp, ctypes.c_size_t, _vp, ctypes.c_char_p, ctypes.c_size_t]
     L.iesh_last_error.argtypes = [_vp]
     L.iesh_last_error.restype = ctypes.c_char_p
     L.iesh_status_string.argtypes = [ctypes.c_int]
@@ -152,7 +166,8 @@ def load(path=LIB_PATH):
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype if name in (
             "iesh_last_error", "iesh_status_string", "iesh_eocc_last_error",
-            "iesh2_last_error") else ctypes.c_int
+            "iesh2_last_error", "iesh_ensemble_last_error") else ctypes.c_int
+    L.iesh_syev_work_bytes.restype = ctypes.c_size_t
     _lib = L
     return L
 
@@ -412,6 +427,74 @@ def hop_probabilities_noalloc(model, x, p, occ, C, lam, q0, dt, g, stream=None):
     if rc != IESH_OK:
         raise IeshError(f"iesh_hop_probabilities_noalloc: {STATUS_NAMES.get(rc, rc)}: "
                         f"{err.value.decode()}")
+
+
+class Ensemble:
+    """Contexts advanced together by one device-side loop (wraps
+    iesh_ensemble): every context by `chunk` steps per iteration, work lists
+    compacted on the device, until no trajectory is live or the step cap."""
+
+    def __init__(self, contexts, dt, chunk, seed=0, stream=None):
+        self.L = load()
+        self.contexts = list(contexts)
+        arr = (_vp * len(self.contexts))(*[c._h.value for c in self.contexts])
+        self.stream = current_stream_handle() if stream is None else stream
+        h = _vp()
+        rc = self.L.iesh_ensemble_create(ctypes.byref(h), arr, len(self.contexts), float(dt),
+                                         int(chunk), int(seed), _vp(self.stream) if self.stream else None)
+        self._h = h
+        if rc != IESH_OK:
+            msg = self.L.iesh_ensemble_last_error(h).decode() if h.value else ""
+            self.L.iesh_ensemble_destroy(h)
+            self._h = None
+            raise IeshError(f"iesh_ensemble_create: {STATUS_NAMES.get(rc, rc)}: {msg}")
+
+    def _check(self, rc, what):
+        if rc != IESH_OK:
+            raise IeshError(f"{what}: {STATUS_NAMES.get(rc, rc)}: "
+                            f"{self.L.iesh_ensemble_last_error(self._h).decode()}")
+
+    def run(self, max_steps):
+        """One graph launch (asynchronous)."""
+        self._check(self.L.iesh_ensemble_run(self._h, int(max_steps)), "iesh_ensemble_run")
+
+    def status(self):
+        """(loop steps so far, live trajectories after the last chunk)."""
+        s, l = ctypes.c_int64(0), ctypes.c_int64(0)
+        self._check(self.L.iesh_ensemble_status(self._h, ctypes.addressof(s), ctypes.addressof(l)),
+                    "iesh_ensemble_status")
+        return s.value, l.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.L.iesh_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def syev_batched(A, lam, V=None, info=None, work=None, stream=None):
+    """Eigenvalues lam [B][n] (ascending) and eigenvector rows V [B][n][n] of
+    the symmetric matrices A [B][n][n] (CUDA tensors, float64 or float32; see
+    iesh_syev_batched in iesh.h).  work: a CUDA uint8 tensor of at least
+    iesh_syev_work_bytes bytes (allocated here when None)."""
+    import torch
+    L = load()
+    B, n = int(A.shape[0]), int(A.shape[1])
+    prec = PREC_FP64 if A.dtype == torch.float64 else PREC_MIXED
+    need = L.iesh_syev_work_bytes(B, n, prec, int(V is not None))
+    if work is None:
+        work = torch.empty(max(need, 1), dtype=torch.uint8, device=A.device)
+    err = ctypes.create_string_buffer(512)
+    s = current_stream_handle() if stream is None else stream
+    rc = L.iesh_syev_batched(B, n, prec, _ptr(A), _ptr(lam), _ptr(V), _ptr(info), _ptr(work),
+                             int(work.numel()), _vp(s) if s else None, err, len(err))
+    if rc != IESH_OK:
+        raise IeshError(f"iesh_syev_batched: {STATUS_NAMES.get(rc, rc)}: {err.value.decode()}")
 
 
 def vbar(model):

@@ -24,6 +24,13 @@ def model_struct(md):
         m.theta[i] = float(md["theta"][i])
     for a in range(2):
         m.vbar[a] = float(md["Vbar"][a])
+    prof = md.get("profile")
+    if prof is not None:  # own Lorentzian bath profile per orbital
+        m.profile = 1
+        for a in range(2):
+            m.prof_center[a] = float(prof["center"][a])
+            m.prof_width[a] = float(prof["width"][a])
+    m.eigensolver = 1 if md.get("eigensolver") == "dense" else 0
     return m
 
 

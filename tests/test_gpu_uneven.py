@@ -60,18 +60,100 @@ def test_compaction_does_not_change_results(P, precision):
     assert np.all(c1[0][done] < 96) and np.all(c1[0][~done] == 96)
 
 
-def test_graph_replay_matches_eager(P):
+def test_graph_replay_and_device_loop_match_eager(P):
+    """Eager chunks, a host loop replaying one captured chunk, and the
+    device-side loop (one graph launch) give the same bits."""
     from paper_2212_00518_gb300.ensemble import UnevenBatch
     groups = W.scattering_batch(96, seed=4, M_choices=(20, 30), biases=(0.0, 0.05))
-    res = []
-    for use_graph in (False, True):
-        ub = UnevenBatch(groups, dt=0.1 * W.FS_AU, z_done=W.angstrom(5.6), precision=1,
+    for g in groups:  # every other trajectory moves away from the surface
+        g["p"] = np.where(np.arange(g["p"].shape[0]) % 2 == 0, -g["p"], g["p"])
+    res, steps = [], []
+    for use_graph, device_loop in ((False, False), (True, False), (True, True)):
+        ub = UnevenBatch(groups, dt=0.1 * W.FS_AU, z_done=W.angstrom(5.3), precision=1,
                          compact_every=16, seed=2)
-        ub.run(64, use_graph=use_graph)
+        steps.append(ub.run(64, use_graph=use_graph, device_loop=device_loop))
         res.append(ub.results())
         ub.close()
-    for k in res[0]:
-        assert np.array_equal(res[0][k], res[1][k]), k
+    done = (res[0]["status"] & P.iesh.TRAJ_DONE) != 0
+    assert 0 < done.sum() < 96, "batch must be uneven"
+    for r in res[1:]:
+        for k in res[0]:
+            assert np.array_equal(res[0][k], r[k]), k
+    assert steps[0] == steps[1] == steps[2] == int(res[0]["nstep"].sum())
+
+
+def _leaving_groups(seed):
+    """Morse + image-charge scattering near the exit: per (M, bias) group,
+    trajectories between 9 and 9.9 angstrom moving outward at 0.05-1.5 eV,
+    so that they leave (z > 10 angstrom) at different steps; coefficients
+    partly off the occupied orbitals."""
+    rng = np.random.default_rng(seed)
+    groups, idx0 = [], 0
+    for M, n in ((50, 6), (100, 4), (200, 2)):
+        for V in (0.0, 0.1):
+            md = W.morse_image(M, bias=V)
+            x = W.angstrom(rng.uniform(9.0, 9.9, n))
+            e = W.ev(rng.uniform(0.05, 1.5, n))
+            p = np.sqrt(2 * md["mass"] * e)
+            occ = W.lowest_occupations(n, md["Ne"])
+            C = W.mixed_coefficients(occ, M + 1, int(rng.integers(1 << 30)), 0.3)
+            groups.append(dict(model=md, idx=np.arange(idx0, idx0 + n), x=x, p=p, occ=occ, C=C))
+            idx0 += n
+    return groups
+
+
+@pytest.fixture(scope="module")
+def leaving_reference():
+    """The FP64 oracle on the groups of _leaving_groups (stopping each
+    trajectory at the end of the step that takes it past 10 angstrom)."""
+    groups = _leaving_groups(12)
+    dt, steps, z_done = 0.5 * W.FS_AU, 64, W.angstrom(10.0)
+    out = []
+    for g in groups:
+        md = g["model"]
+        out.append(O.run(O.bind(md), g["x"], g["p"], g["occ"].astype(np.int32),
+                         np.transpose(g["C"], (0, 2, 1)), dt, steps, seed=6, z_done=z_done,
+                         n_threads=len(g["x"])))
+    return groups, out, dt, steps, z_done
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_uneven_device_loop_matches_oracle_until_trajectories_leave(P, precision, leaving_reference):
+    """M in {50, 100, 200}, biases 0 and 0.1, one device loop over six
+    contexts with their work lists compacted every 8 steps (8 compactions);
+    trajectories leave at different steps.  Per trajectory against the
+    oracle: steps taken and the finished flag exactly, occupations, hop
+    counts, and x, p, C at the FP64 parity tolerances (mixed: the mixed-path
+    bounds, with C's scaled by the Chebyshev order: at dt = 0.5 fs across a
+    64 eV band a step takes K of several tens of orders, each adding about
+    2^-24 of FP32 rounding, so C is held to 4 steps K_max 2^-24).  Live
+    trajectory-steps equal the oracle's steps taken."""
+    from paper_2212_00518_gb300.ensemble import UnevenBatch
+    groups, ref, dt, steps, z_done = leaving_reference
+    ub = UnevenBatch([dict(g) for g in groups], dt=dt, z_done=z_done, precision=precision,
+                     compact_every=8, seed=6)
+    # the groups' own occupations and coefficients instead of the 0 K start
+    for g, ctx in zip(groups, ub.ctxs):
+        ctx.set_state(g["x"], g["p"], g["occ"], g["C"] if precision == 0 else g["C"].astype(np.complex64))
+    live_steps = ub.run(steps)
+    left_early = 0
+    for g, ctx, r in zip(groups, ub.ctxs, ref):
+        st = ctx.get_state()
+        ns, hops, _ = ctx.counters()
+        done = (st["status"] & P.iesh.TRAJ_DONE) != 0
+        assert np.array_equal(ns, r["steps"]), (g["model"]["M"], ns, r["steps"])
+        assert np.array_equal(done, (r["status"] & 8) != 0)
+        assert np.array_equal(st["occ"], r["occ"]) and np.array_equal(hops, r["hops"])
+        xt, pt = (1e-10, 1e-9) if precision == 0 else (1e-7, 1e-5)
+        assert np.abs(st["x"] - r["x"]).max() <= xt * np.abs(r["x"]).max()
+        assert np.abs(st["p"] - r["p"]).max() <= pt * np.abs(r["p"]).max()
+        kmax = int(ctx.propagator_terms().max())
+        ct = 1e-8 if precision == 0 else 4 * steps * kmax * 2.0 ** -24
+        assert np.abs(np.transpose(st["C"], (0, 2, 1)) - r["C"]).max() <= ct
+        left_early += int(np.count_nonzero(done & (ns <= steps - 8)))
+    assert left_early >= 4, "trajectories must finish before the last compactions"
+    assert live_steps == sum(int(r["steps"].sum()) for r in ref)
+    ub.close()
 
 
 @pytest.mark.parametrize("precision", [0, 1])
