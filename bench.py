@@ -733,6 +733,52 @@ def run_workload(args):
                            "dtype": "mixed (f32 coefficients, generator, propagation, LU and ratio "
                                     "solves; f64 eigenpairs, forces, probabilities, rescale)"},
                     results=res)
+    elif args.workload == "syev":
+        # the batched dense symmetric eigensolver (eigenvalues and eigenvectors)
+        # and the two-orbital dynamics that takes its eigenpairs from it
+        from paper_2212_00518_gb300 import two
+        res = {}
+        for n in (64, 102, 256):
+            B = 8192 if n <= 102 else 2048
+            A = W.random_symmetric(B, n, seed=n)
+            for dtype, name in ((torch.float64, "fp64"), (torch.float32, "fp32")):
+                tA = torch.tensor(A, dtype=dtype, device="cuda")
+                lam = torch.empty((B, n), dtype=dtype, device="cuda")
+                V = torch.empty((B, n, n), dtype=dtype, device="cuda")
+                prec = P.PREC_FP64 if dtype == torch.float64 else P.PREC_MIXED
+                work = torch.empty(P.iesh.load().iesh_syev_work_bytes(B, n, prec, 1), dtype=torch.uint8,
+                                   device="cuda")
+                ms = _timed_steps(torch, stream, lambda: P.iesh.syev_batched(tA, lam, V, work=work),
+                                  args.warmup, args.steps)
+                sec = ms / args.steps / 1e3
+                flops = B * (8.0 / 3.0 + 6.0) * n ** 3  # reduction + P + about 6 n^3 for the rotations
+                res[f"n{n}_{name}"] = {"matrices": B, "matrices_per_s": B / sec, "ms": 1e3 * sec,
+                                       "approx_tflops": flops / sec / 1e12}
+        n, dt = args.n_traj, 2.0
+        md = W.two_orbital_profiled(100, seed=5)
+        x, p, occ, C = W.two_orbital_state(md, n, 3, kT=0.01, weight=0.5)
+        dyn = {}
+        for prec, name in ((P.PREC_FP64, "fp64"), (P.PREC_MIXED, "mixed")):
+            c = two.TwoOrbitalContext(md, n, precision=prec, stream=stream.cuda_stream)
+            c.set_state(x, p, occ.astype(np.int16), C if prec == P.PREC_FP64 else C.astype(np.complex64))
+            c.run(dt, max(3, args.warmup), 0)
+            c.profile(True)
+            ms = _timed_steps(torch, stream, lambda: c.run(dt, 1, 0), 0, args.steps)
+            prof = c.profile_read()
+            c.profile(False)
+            tot = sum(v[0] for v in prof.values())
+            dyn[name] = {"traj_steps_per_s": n * args.steps / (ms / 1e3),
+                         "kernel_share": {k: v[0] / tot for k, v in prof.items() if tot > 0},
+                         "status_nonzero": int(np.count_nonzero(c.get_state()["status"]))}
+            c.close()
+        line.update(metric="batched dense symmetric eigensolver, matrices/s (eigenvalues + eigenvectors)",
+                    unit="matrices/s", value=res["n102_fp64"]["matrices_per_s"], dtype="f64",
+                    config={"workload": "random symmetric matrices n in {64, 102, 256} (8192, 8192, 2048 "
+                                        "per batch), FP64 and FP32; two-orbital dynamics with own bath "
+                                        f"profiles (non-parallel couplings), 100 GL states, {n} trajectories, "
+                                        "dt=2, eigenpairs from the dense solver",
+                            "value_is": "n=102 FP64 matrices/s"},
+                    results={"syev": res, "two_orbital_profiled": dyn})
     elif args.workload == "eocc":
         from paper_2212_00518_gb300 import eocc as E
         wl = W.eocc_workload(M=300, B=65536, seed=5)
@@ -779,7 +825,7 @@ def main():
     ap.add_argument("--no-overlap", action="store_true",
                     help="skip the diabatic-basis propagator variant")
     ap.add_argument("--workload", choices=["dw", "paper", "scatter", "erpenbeck", "relaxation", "eocc",
-                                           "two"],
+                                           "two", "syev"],
                     default="dw",
                     help="dw: the double-well batch (default, --M/--n-traj); the others print "
                          "secondary measurements")

@@ -366,11 +366,13 @@ __global__ void __launch_bounds__(256, 2) k2_eigen(DevState s, Model2Dev md, dou
         const double p0 = s.q0_prev[t * N + r], p1 = s.q2_prev[t * N + r], lp = s.lam_prev[t * N + r];
         const Ads2 &adp = sl->adp;
         const float Aj = (float)(c0 * q0 + c1 * q1), Ap = (float)(adp.c[0] * p0 + adp.c[1] * p1);
+        const float ljf = (float)lj, lpf = (float)lp;
         float acc = 0.0f;
         for (int k = 0; k < M; ++k) {
-            const float den = (float)(lj - eps_s[k]) * (float)(lp - eps_s[k]);
+            const float ek = (float)eps_s[k];
+            const float den = (ljf - ek) * (lpf - ek);
             const float w = (float)(s.z0[k] * s.z0[k]);
-            if (den != 0.0f) acc += w / den;
+            if (den != 0.0f) acc += __fdividef(w, den);
         }
         const float ov = (float)(q0 * p0 + q1 * p1) + Aj * Ap * acc;
         if (ov <= -0.5f) {
@@ -793,11 +795,12 @@ __global__ void __launch_bounds__(256) k2g_finish(DevState s, Model2Dev md, doub
             const double p0 = s.q0_prev[t * N + j], p1 = s.q2_prev[t * N + j], lp = s.lam_prev[t * N + j];
             const float a0 = (float)(ad.c[0] * q0), a1 = (float)(ad.c[1] * q1);
             const float b0 = (float)(adp.c[0] * p0), b1 = (float)(adp.c[1] * p1);
+            const float ljf = (float)lj, lpf = (float)lp;
             float ov = (float)(q0 * p0 + q1 * p1);
             for (int k = 0; k < M; ++k) {
-                const float f0 = (float)md.prof[k], f1 = (float)md.prof[M + k];
-                const float den = (float)(lj - s.eps[k]) * (float)(lp - s.eps[k]);
-                if (den != 0.0f) ov += (a0 * f0 + a1 * f1) * (b0 * f0 + b1 * f1) / den;
+                const float f0 = (float)md.prof[k], f1 = (float)md.prof[M + k], ek = (float)s.eps[k];
+                const float den = (ljf - ek) * (lpf - ek);
+                if (den != 0.0f) ov += __fdividef((a0 * f0 + a1 * f1) * (b0 * f0 + b1 * f1), den);
             }
             if (ov <= -0.5f) {
                 Q0_s[j] = -q0;
