@@ -739,7 +739,7 @@ def run_workload(args):
         from paper_2212_00518_gb300 import two
         res = {}
         for n in (64, 102, 256):
-            B = 8192 if n <= 102 else 2048
+            B = 4096 if n <= 102 else 1024
             A = W.random_symmetric(B, n, seed=n)
             for dtype, name in ((torch.float64, "fp64"), (torch.float32, "fp32")):
                 tA = torch.tensor(A, dtype=dtype, device="cuda")
@@ -773,7 +773,7 @@ def run_workload(args):
             c.close()
         line.update(metric="batched dense symmetric eigensolver, matrices/s (eigenvalues + eigenvectors)",
                     unit="matrices/s", value=res["n102_fp64"]["matrices_per_s"], dtype="f64",
-                    config={"workload": "random symmetric matrices n in {64, 102, 256} (8192, 8192, 2048 "
+                    config={"workload": "random symmetric matrices n in {64, 102, 256} (4096, 4096, 1024 "
                                         "per batch), FP64 and FP32; two-orbital dynamics with own bath "
                                         f"profiles (non-parallel couplings), 100 GL states, {n} trajectories, "
                                         "dt=2, eigenpairs from the dense solver",

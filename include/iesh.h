@@ -353,8 +353,10 @@ iesh_status iesh_hop_probabilities_noalloc(const iesh_model *model, int64_t n, c
  * (A v_j = lam_j v_j), each signed so that its component of largest
  * magnitude (the first on a tie) is positive.  Householder reduction to
  * tridiagonal form (one CTA per matrix, the matrix in shared memory up to
- * about 200 KB), implicit-shift QL iterations with the rotations applied to
- * the rows of the reflector product (one thread per matrix), ordering.
+ * about 200 KB), implicit-shift QL iterations (one thread per matrix for
+ * eigenvalues only; with eigenvectors one CTA per matrix, the rotations of
+ * each sweep applied to all rows of the reflector product in parallel),
+ * ordering.
  * precision: IESH_PREC_FP64 (double arrays) or IESH_PREC_MIXED (float
  * arrays, FP32 arithmetic).  info[b] (device, may be NULL) is set to 0, or
  * to 1 when an eigenvalue needed more than 60 QL iterations (the output of
@@ -494,6 +496,13 @@ iesh_status iesh2_get_counters(iesh2_ctx *ctx, int64_t *nstep, int32_t *hops, in
 /* Kernel timing, as iesh_profile / iesh_profile_read. */
 iesh_status iesh2_profile(iesh2_ctx *ctx, int enable);
 iesh_status iesh2_profile_read(iesh2_ctx *ctx, double *ms, int64_t *launches);
+
+/* Diagnostic: r[i] = the reciprocal 1 / d[i] as the FP64 kernels form it
+ * for pole distances and eigenvalue gaps (the PTX reciprocal estimate
+ * refined by the geometric series r0 (1 + e + e^2), e = 1 - d r0), for
+ * comparison with a correctly rounded division.  d, r: device arrays of n
+ * doubles (normal numbers); asynchronous on cuda_stream. */
+iesh_status iesh_diag_reciprocal(int64_t n, const double *d, double *r, void *cuda_stream);
 
 /* Last error message of the context (never NULL). */
 const char *iesh_last_error(const iesh_ctx *ctx);

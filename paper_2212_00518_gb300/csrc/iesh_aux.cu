@@ -3,8 +3,10 @@
 // of the C-ABI in iesh_capi.cu).
 #include <cuda_runtime.h>
 
+#include "../../include/iesh.h"
 #include "iesh_common.cuh"
 #include "iesh_kernels.h"
+#include "iesh_secular.cuh"
 
 namespace iesh {
 
@@ -151,4 +153,20 @@ cudaError_t launch_status_summary(const uint32_t *status, int64_t n, uint32_t *o
     return cudaGetLastError();
 }
 
+// The refined reciprocal of the secular sums and the couplings, element by
+// element (diagnostic for iesh_diag_reciprocal).
+__global__ void k_diag_recip(int64_t n, const double *__restrict__ d, double *__restrict__ r)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) r[i] = pole_recip<double>(d[i]);
+}
+
 }  // namespace iesh
+
+extern "C" iesh_status iesh_diag_reciprocal(int64_t n, const double *d, double *r, void *cuda_stream)
+{
+    if (n < 0 || (n > 0 && (!d || !r))) return IESH_EINVAL;
+    if (n == 0) return IESH_OK;
+    iesh::k_diag_recip<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)cuda_stream>>>(n, d, r);
+    return cudaGetLastError() == cudaSuccess ? IESH_OK : IESH_ECUDA;
+}

@@ -140,44 +140,57 @@ __device__ __forceinline__ Sec<R> sec_eval(const Poles<R> &P, int o, R tau, R eo
     const int M = P.M;
     R s1 = 0, s2 = 0, sa = 0;
     if constexpr (EV == EV_DFLOAT) {
+        // two accumulator sets (even and odd poles), added at the end: the
+        // double-float additions are a serial chain, two chains run at once
         const dfl td = dfl_from((double)tau);
-        dfl d1 = {0.f, 0.f}, d2 = {0.f, 0.f}, da = {0.f, 0.f};
-#pragma unroll 2
-        for (int k = 0; k < M; ++k) {
+        dfl d1[2] = {{0.f, 0.f}, {0.f, 0.f}}, d2[2] = {{0.f, 0.f}, {0.f, 0.f}}, da[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        auto term = [&](int k, int h) {
             const float2 dk = P.ddf[(size_t)k * M + o], zk = P.z2df[k];
             const dfl r = dfl_rcp(dfl_add({dk.x, dk.y}, td));  // 1 / (lam - eps_k)
             const dfl q = dfl_mul({zk.x, zk.y}, r);
             if (k != o) {
-                d1 = dfl_add(d1, q);
-                d2 = dfl_add(d2, dfl_mul(q, r));
-                if (ABS) da = dfl_add(da, q.hi < 0.f ? dfl{-q.hi, -q.lo} : q);
+                d1[h] = dfl_add(d1[h], q);
+                d2[h] = dfl_add(d2[h], dfl_mul(q, r));
+                if (ABS) da[h] = dfl_add(da[h], q.hi < 0.f ? dfl{-q.hi, -q.lo} : q);
             }
+        };
+        int k = 0;
+        for (; k + 1 < M; k += 2) {
+            term(k, 0);
+            term(k + 1, 1);
         }
-        s1 = (R)dfl_value(d1);
-        s2 = (R)dfl_value(d2);
-        sa = (R)dfl_value(da);
+        if (k < M) term(k, 0);
+        s1 = (R)dfl_value(dfl_add(d1[0], d1[1]));
+        s2 = (R)dfl_value(dfl_add(d2[0], d2[1]));
+        sa = (R)dfl_value(dfl_add(da[0], da[1]));
     } else if constexpr (EV == EV_TWO_DF) {
         // bath poles in double-float from the bath table (origin a bath pole)
-        // or from hdf (origin h_-); the h_- term itself in R
+        // or from hdf (origin h_-); the h_- term itself in R.  Two
+        // accumulator sets, as above
         const dfl td = dfl_from((double)tau);
         const bool oh = o == P.hpos;
         const int ob = oh ? 0 : ((P.hpos >= 0 && o > P.hpos) ? o - 1 : o);
-        dfl d1 = {0.f, 0.f}, d2 = {0.f, 0.f}, da = {0.f, 0.f};
-#pragma unroll 2
-        for (int k = 0; k < P.nb; ++k) {
+        dfl d1[2] = {{0.f, 0.f}, {0.f, 0.f}}, d2[2] = {{0.f, 0.f}, {0.f, 0.f}}, da[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        auto term = [&](int k, int h) {
             const int q = (P.hpos >= 0 && k >= P.hpos) ? k + 1 : k;
             const float2 dk = oh ? P.hdf[k] : P.ddf[(size_t)k * P.nb + ob], zk = P.z2df[q];
             const dfl r = dfl_rcp(dfl_add({dk.x, dk.y}, td));  // 1 / (lam - eps_k)
             const dfl qv = dfl_mul({zk.x, zk.y}, r);
             if (q != o) {
-                d1 = dfl_add(d1, qv);
-                d2 = dfl_add(d2, dfl_mul(qv, r));
-                if (ABS) da = dfl_add(da, qv.hi < 0.f ? dfl{-qv.hi, -qv.lo} : qv);
+                d1[h] = dfl_add(d1[h], qv);
+                d2[h] = dfl_add(d2[h], dfl_mul(qv, r));
+                if (ABS) da[h] = dfl_add(da[h], qv.hi < 0.f ? dfl{-qv.hi, -qv.lo} : qv);
             }
+        };
+        int k = 0;
+        for (; k + 1 < P.nb; k += 2) {
+            term(k, 0);
+            term(k + 1, 1);
         }
-        s1 = (R)dfl_value(d1);
-        s2 = (R)dfl_value(d2);
-        sa = (R)dfl_value(da);
+        if (k < P.nb) term(k, 0);
+        s1 = (R)dfl_value(dfl_add(d1[0], d1[1]));
+        s2 = (R)dfl_value(dfl_add(d2[0], d2[1]));
+        sa = (R)dfl_value(dfl_add(da[0], da[1]));
         if (P.hpos >= 0 && !oh) {
             const R r = pole_recip<R>((P.eps[o] - P.hm) + tau);
             const R qv = P.z2[P.hpos] * r;

@@ -1,7 +1,9 @@
 // iesh_syev.cu -- batched dense symmetric eigensolver behind the C-ABI
 // (iesh_syev_batched): one matrix per CTA for the Householder reduction and
-// the back-transformation set-up, one matrix per thread for the QL
-// iterations, one matrix per CTA for the ordering and the output.
+// the back-transformation set-up; the QL iterations one matrix per thread
+// (eigenvalues only) or per CTA (with eigenvectors: the rotations of each
+// sweep applied to all rows of P in parallel); one matrix per CTA for the
+// ordering and the output.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -96,7 +98,7 @@ __global__ void __launch_bounds__(kSyevThreads) k_syev_reduce(int64_t B, int n, 
 // QL iterations, one matrix per thread; the rotations act on the n rows of
 // P (stored as P^T, i.e. entry i of row r at Pt[i n + r]).
 template <class T>
-__global__ void __launch_bounds__(128) k_syev_ql(int64_t B, int n, T *__restrict__ work, size_t wstride,
+__global__ void __launch_bounds__(32) k_syev_ql(int64_t B, int n, T *__restrict__ work, size_t wstride,
                                                  int vectors, uint32_t *__restrict__ info)
 {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -106,6 +108,31 @@ __global__ void __launch_bounds__(128) k_syev_ql(int64_t B, int n, T *__restrict
     T *Pt = wk + 3 * n + (syev_in_smem<T>(n) ? 0 : (size_t)n * lda);
     const bool ok = ql_implicit<T>(n, wk, wk + n, vectors ? Pt : nullptr, vectors ? n : 0);
     if (info) info[b] = ok ? 0u : 1u;
+}
+
+// QL iterations with all n rows of P, one matrix per CTA (see
+// ql_implicit_rows): the scalar recurrence by one thread, the rotations of
+// each sweep applied to the rows of P by all threads.
+template <class T>
+__global__ void __launch_bounds__(128) k_syev_qlv(int64_t B, int n, T *__restrict__ work, size_t wstride,
+                                                  uint32_t *__restrict__ info)
+{
+    extern __shared__ __align__(16) unsigned char qlv_sh[];
+    __shared__ int flags[4];
+    const int64_t b = blockIdx.x;
+    if (b >= B) return;
+    T *wk = work + b * wstride;
+    const int lda = syev_lda<T>(n);
+    T *Pt = wk + 3 * n + (syev_in_smem<T>(n) ? 0 : (size_t)n * lda);
+    T *d = reinterpret_cast<T *>(qlv_sh), *e = d + n, *rc = e + n, *rs = rc + n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        d[i] = wk[i];
+        e[i] = wk[n + i];
+    }
+    __syncthreads();
+    const bool ok = ql_implicit_rows<T>(n, d, e, Pt, n, rc, rs, flags);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) wk[i] = d[i];
+    if (threadIdx.x == 0 && info) info[b] = ok ? 0u : 1u;
 }
 
 // Ascending order (ties by index), eigenvectors as rows, each signed so that
@@ -178,7 +205,12 @@ iesh_status syev_run(int64_t B, int n, const T *A, T *lam, T *V, uint32_t *info,
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        k_syev_ql<T><<<(unsigned)((B + 127) / 128), 128, 0, st>>>(B, n, wk, wstride, vectors ? 1 : 0, info);
+        // eigenvalues only: one matrix per thread; with eigenvectors: one per
+        // CTA, the rotations applied to all rows of P in parallel
+        if (vectors)
+            k_syev_qlv<T><<<(unsigned)B, 128, (size_t)4 * n * sizeof(T), st>>>(B, n, wk, wstride, info);
+        else
+            k_syev_ql<T><<<(unsigned)((B + 31) / 32), 32, 0, st>>>(B, n, wk, wstride, 0, info);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {

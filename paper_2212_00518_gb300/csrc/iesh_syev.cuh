@@ -32,6 +32,47 @@ struct SyevEps<float> {
 
 constexpr int kSyevMaxIter = 60;  // QL iterations per eigenvalue before giving up
 
+// Plane rotation taking (g, f) to (r, 0): r = sqrt(f^2 + g^2), s = f / r,
+// c = g / r.  Where f^2 + g^2 is far from under- and overflow (binary
+// exponent within +-960 for double, +-100 for float) one reciprocal square
+// root gives all three (each within a few units in the last place); else
+// the scaled hypot and two divisions.  Returns r; s and c are left
+// untouched when r == 0.
+__device__ __forceinline__ double syev_rot(double f, double g, double &s, double &c)
+{
+    const double q = fma(f, f, g * g);
+    const int ex = (__double2hiint(q) >> 20) & 0x7ff;  // biased exponent of q
+    if (ex > 1023 - 960 && ex < 1023 + 960) {
+        const double ir = rsqrt(q);
+        s = f * ir;
+        c = g * ir;
+        return q * ir;
+    }
+    const double r = hypot(f, g);
+    if (r != 0.0) {
+        s = f / r;
+        c = g / r;
+    }
+    return r;
+}
+__device__ __forceinline__ float syev_rot(float f, float g, float &s, float &c)
+{
+    const float q = fmaf(f, f, g * g);
+    const int ex = (__float_as_int(q) >> 23) & 0xff;
+    if (ex > 127 - 100 && ex < 127 + 100) {
+        const float ir = rsqrtf(q);
+        s = f * ir;
+        c = g * ir;
+        return q * ir;
+    }
+    const float r = hypotf(f, g);
+    if (r != 0.0f) {
+        s = f / r;
+        c = g / r;
+    }
+    return r;
+}
+
 template <class T>
 __device__ __forceinline__ T syev_warp_sum(T v)
 {
@@ -172,7 +213,7 @@ __device__ bool ql_implicit(int n, T *d, T *e, T *Y, int R)
             bool restart = false;
             for (int i = m - 1; i >= l; --i) {
                 const T f = s * e[i], b = c * e[i];
-                r = hypot(f, g);
+                r = syev_rot(f, g, s, c);
                 e[i + 1] = r;
                 if (r == T(0)) {  // the bulge vanished: split the matrix here
                     d[i + 1] -= p;
@@ -180,8 +221,6 @@ __device__ bool ql_implicit(int n, T *d, T *e, T *Y, int R)
                     restart = true;
                     break;
                 }
-                s = f / r;
-                c = g / r;
                 g = d[i + 1] - p;
                 r = (d[i] - g) * s + T(2) * c * b;
                 p = s * r;
@@ -200,6 +239,100 @@ __device__ bool ql_implicit(int n, T *d, T *e, T *Y, int R)
         }
     }
     return true;
+}
+
+// The same iteration with all n rows of the reflector product tracked, by a
+// CTA: thread 0 runs the scalar recurrence of a sweep (the rotations of one
+// implicit QL step, i = m-1 down to l) and stores each rotation's (c, s) in
+// shared memory; then every thread applies the sweep to its own rows r of
+// P, entry i of row r at P[i ld + r] (so a warp's threads touch consecutive
+// addresses), carrying entry i+1 of the previous rotation in a register.
+// d, e in shared memory (d, e, rc, rs: n entries each; flags: 4 ints).
+// Every thread calls; the result (false: an eigenvalue needed more than
+// kSyevMaxIter iterations) is the same in every thread.
+template <class T>
+__device__ bool ql_implicit_rows(int n, T *d, T *e, T *P, int ld, T *rc, T *rs, int *flags)
+{
+    const int tid = threadIdx.x;
+    // flags[0]: next sweep's l, flags[1]: its m (l == m: done), flags[2]: failed
+    int l = 0, iter = 0;
+    if (tid == 0) flags[2] = 0;
+    for (;;) {
+        if (tid == 0) {
+            int ls = -1, ms = -1;
+            while (l < n) {
+                int m = l;
+                for (; m < n - 1; ++m) {
+                    const T dd = fabs(d[m]) + fabs(d[m + 1]);
+                    if (fabs(e[m]) <= SyevEps<T>::u * dd) break;
+                }
+                if (m == l) {  // d[l] converged
+                    ++l;
+                    iter = 0;
+                    continue;
+                }
+                if (++iter > kSyevMaxIter) {
+                    flags[2] = 1;
+                    l = n;
+                    break;
+                }
+                T g = (d[l + 1] - d[l]) / (T(2) * e[l]);
+                T r = hypot(g, T(1));
+                g = d[m] - d[l] + e[l] / (g + copysign(r, g));
+                T sn = 1, cs = 1, p = 0;
+                int i = m - 1;
+                bool split = false;
+                for (; i >= l; --i) {
+                    const T f = sn * e[i], b = cs * e[i];
+                    r = syev_rot(f, g, sn, cs);
+                    e[i + 1] = r;
+                    if (r == T(0)) {
+                        d[i + 1] -= p;
+                        e[m] = 0;
+                        split = true;
+                        break;
+                    }
+                    g = d[i + 1] - p;
+                    r = (d[i] - g) * sn + T(2) * cs * b;
+                    p = sn * r;
+                    d[i + 1] = g + p;
+                    g = cs * r - b;
+                    rc[i] = cs;
+                    rs[i] = sn;
+                }
+                if (split) {
+                    // rotations m-1 .. i+1 were taken; apply those, restart at l
+                    ls = i + 1;
+                    ms = m;
+                    break;
+                }
+                d[l] -= p;
+                e[l] = g;
+                e[m] = 0;
+                ls = l;
+                ms = m;
+                break;
+            }
+            flags[0] = ls;
+            flags[1] = ms;
+        }
+        __syncthreads();
+        const int ls = flags[0], ms = flags[1];
+        if (ls < 0) break;  // every eigenvalue converged (or the cap was hit)
+        for (int row = tid; row < n; row += blockDim.x) {
+            T yj = P[(size_t)ms * ld + row];
+            for (int i = ms - 1; i >= ls; --i) {
+                const T yi = P[(size_t)i * ld + row];
+                P[(size_t)(i + 1) * ld + row] = rs[i] * yi + rc[i] * yj;
+                yj = rc[i] * yi - rs[i] * yj;
+            }
+            P[(size_t)ls * ld + row] = yj;
+        }
+        __syncthreads();
+    }
+    const bool ok = flags[2] == 0;
+    __syncthreads();
+    return ok;
 }
 
 }  // namespace iesh

@@ -738,7 +738,7 @@ __global__ void __launch_bounds__(256) k2g_reduce(DevState s, Model2Dev md, doub
     }
 }
 
-__global__ void __launch_bounds__(128) k2g_ql(DevState s)
+__global__ void __launch_bounds__(32) k2g_ql(DevState s)
 {
     const int64_t t = traj_of(s, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
     if (t < 0 || (s.status[t] & ST_DONE)) return;
@@ -913,7 +913,9 @@ cudaError_t launch_eigen2(iesh2_ctx *ctx, double dt, int mode)
         k2g_reduce<<<(unsigned)d.n, 256, dense_reduce_smem(d.N), ctx->stream>>>(d, ctx->md, dt, mode);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        k2g_ql<<<(unsigned)((d.n + 127) / 128), 128, 0, ctx->stream>>>(d);
+        // one warp per CTA: few trajectories per warp-wide FP64 recurrence,
+        // so spread the warps over as many SMs as possible
+        k2g_ql<<<(unsigned)((d.n + 31) / 32), 32, 0, ctx->stream>>>(d);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         k2g_finish<<<(unsigned)d.n, 256, (size_t)6 * d.N * sizeof(double), ctx->stream>>>(d, ctx->md, dt, mode);
         return cudaGetLastError();

@@ -87,7 +87,8 @@ EXPORTS = ["iesh_create", "iesh_destroy", "iesh_bath", "iesh_init_state", "iesh_
            "iesh2_profile_read", "iesh_checkpoint_bytes", "iesh_checkpoint_save",
            "iesh_checkpoint_load", "iesh_observables", "iesh_check", "iesh_syev_work_bytes",
            "iesh_syev_batched", "iesh_ensemble_create", "iesh_ensemble_run",
-           "iesh_ensemble_status", "iesh_ensemble_destroy", "iesh_ensemble_last_error"]
+           "iesh_ensemble_status", "iesh_ensemble_destroy", "iesh_ensemble_last_error",
+           "iesh_diag_reciprocal"]
 KERNEL_CLASSES = ["eigen", "coupling", "propagate", "hop", "other"]
 
 _lib = None
@@ -152,6 +153,7 @@ def load(path=LIB_PATH):
     L.iesh_ensemble_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int,
                                        ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, _vp]
     L.iesh_ensemble_run.argtypes = [_vp, ctypes.c_int64]
+    L.iesh_diag_reciprocal.argtypes = [ctypes.c_int64, _vp, _vp, _vp]
     L.iesh_ensemble_status.argtypes = [_vp, _vp, _vp]
     L.iesh_ensemble_destroy.argtypes = [_vp]
     L.iesh_ensemble_last_error.argtypes = [_vp]
