@@ -95,44 +95,116 @@ __global__ void __launch_bounds__(kSyevThreads) k_syev_reduce(int64_t B, int n, 
     }
 }
 
-// QL iterations, one matrix per thread; the rotations act on the n rows of
-// P (stored as P^T, i.e. entry i of row r at Pt[i n + r]).
+// QL iterations for eigenvalues only: L matrices per warp in lockstep
+// (ql_lockstep), four warps per CTA; matrix b = (warp index) L + lane.
 template <class T>
-__global__ void __launch_bounds__(32) k_syev_ql(int64_t B, int n, T *__restrict__ work, size_t wstride,
-                                                 int vectors, uint32_t *__restrict__ info)
+__global__ void __launch_bounds__(128) k_syev_ql(int64_t B, int n, T *__restrict__ work, size_t wstride,
+                                                 int L, uint32_t *__restrict__ info)
 {
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B) return;
-    T *wk = work + b * wstride;
-    const int lda = syev_lda<T>(n);
-    T *Pt = wk + 3 * n + (syev_in_smem<T>(n) ? 0 : (size_t)n * lda);
-    const bool ok = ql_implicit<T>(n, wk, wk + n, vectors ? Pt : nullptr, vectors ? n : 0);
-    if (info) info[b] = ok ? 0u : 1u;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (gw * L >= B) return;  // the whole warp: no matrix
+    const int64_t b = gw * L + lane;
+    const bool valid = lane < L && b < B;
+    T *wk = work + (valid ? b : 0) * wstride;
+    const bool ok = ql_lockstep<T, 0>(n, wk, wk + n, 1, nullptr, 0, 0, valid);
+    if (valid && info) info[b] = ok ? 0u : 1u;
 }
 
-// QL iterations with all n rows of P, one matrix per CTA (see
-// ql_implicit_rows): the scalar recurrence by one thread, the rotations of
-// each sweep applied to the rows of P by all threads.
+// QL iterations with all n rows of P, L matrices per CTA, as a two-stage
+// pipeline: warp 0 runs the lockstep recurrence of the L matrices (lane j:
+// matrix blockIdx.x L + j) and stores sweep t+1's rotations in one shared
+// buffer, (c, s) of rotation i of lane j at [i L + j], while the other warps
+// apply sweep t's rotations from the other buffer to the rows of each
+// matrix's P (entry i of row r at Pt[i n + r]), one (matrix, row) per thread
+// at a time, entry i+1 carried in a register and entry i-1 loaded ahead.
 template <class T>
-__global__ void __launch_bounds__(128) k_syev_qlv(int64_t B, int n, T *__restrict__ work, size_t wstride,
-                                                  uint32_t *__restrict__ info)
+__global__ void __launch_bounds__(1024) k_syev_qlv(int64_t B, int n, T *__restrict__ work, size_t wstride, int L,
+                                                   uint32_t *__restrict__ info)
 {
     extern __shared__ __align__(16) unsigned char qlv_sh[];
-    __shared__ int flags[4];
-    const int64_t b = blockIdx.x;
-    if (b >= B) return;
-    T *wk = work + b * wstride;
+    __shared__ int s_low[2][32], s_m[2][32], s_more[2];
+    T *rot = reinterpret_cast<T *>(qlv_sh);  // [buffer][c | s][i L + j]
+    const size_t plane = (size_t)L * n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t b0 = (int64_t)blockIdx.x * L;
     const int lda = syev_lda<T>(n);
-    T *Pt = wk + 3 * n + (syev_in_smem<T>(n) ? 0 : (size_t)n * lda);
-    T *d = reinterpret_cast<T *>(qlv_sh), *e = d + n, *rc = e + n, *rs = rc + n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        d[i] = wk[i];
-        e[i] = wk[n + i];
+    const size_t poff = 3 * (size_t)n + (syev_in_smem<T>(n) ? 0 : (size_t)n * lda);
+    QlLane<T> q;
+    T *d = nullptr, *e = nullptr;
+    if (warp == 0) {
+        q.live = lane < L && b0 + lane < B;
+        T *wk = work + (q.live ? b0 + lane : 0) * wstride;
+        d = wk;
+        e = wk + n;
     }
+    const bool valid = q.live;
+    auto produce = [&](int buf) {  // warp 0: the next sweep into buffer buf
+        const bool more = ql_lockstep_next<T>(n, d, e, 1, q);
+        int low = -1;
+        if (more) {
+            T *rc = rot + (size_t)buf * 2 * plane;
+            low = ql_lockstep_sweep<T, 0>(n, d, e, 1, (T *)nullptr, 0, 0, rc + lane, rc + plane + lane, L, q);
+        }
+        s_low[buf][lane] = low;
+        s_m[buf][lane] = q.m;
+        if (lane == 0) s_more[buf] = more ? 1 : 0;
+    };
+    if (warp == 0) produce(0);
     __syncthreads();
-    const bool ok = ql_implicit_rows<T>(n, d, e, Pt, n, rc, rs, flags);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) wk[i] = d[i];
-    if (threadIdx.x == 0 && info) info[b] = ok ? 0u : 1u;
+    for (int t = 0;; ++t) {
+        const int cb = t & 1;
+        if (!s_more[cb]) break;
+        if (warp == 0) {
+            produce(cb ^ 1);
+        } else {
+            const T *rc = rot + (size_t)cb * 2 * plane, *rs = rc + plane;
+            for (int it = tid - 32; it < L * n; it += blockDim.x - 32) {
+                const int j = it / n, r = it - j * n;
+                const int low = s_low[cb][j], m = s_m[cb][j];
+                if (low < 0) continue;
+                T *Pt = work + (b0 + j) * wstride + poff;
+                T yj = Pt[(size_t)m * n + r];
+                T yi = Pt[(size_t)(m - 1) * n + r];
+                for (int i = m - 1; i >= low; --i) {
+                    const T ynext = i > low ? Pt[(size_t)(i - 1) * n + r] : T(0);
+                    const T c = rc[(size_t)i * L + j], sn = rs[(size_t)i * L + j];
+                    Pt[(size_t)(i + 1) * n + r] = sn * yi + c * yj;
+                    yj = c * yi - sn * yj;
+                    yi = ynext;
+                }
+                Pt[(size_t)low * n + r] = yj;
+            }
+        }
+        __syncthreads();
+    }
+    if (warp == 0 && valid && info) info[b0 + lane] = q.ok ? 0u : 1u;
+}
+
+// Matrices per CTA of k_syev_qlv.  FP64: twice the lockstep width for B
+// matrices, since the FP64 recurrence warp is then amortised over more rows;
+// FP32: a quarter of it, since the FP32 recurrence is cheap and fewer
+// matrices per CTA keep more CTAs (and their rows) in flight.  Halved until
+// the two rotation buffers (4 L n entries) fit in kQlvSmemCap bytes.
+// Threads: warp 0 plus about one applying thread per six (matrix, row)
+// items.  These choices measured best at n = 102 and 256 in both precisions
+// in a sweep over L and the thread count.
+constexpr size_t kQlvSmemCap = 96 * 1024;
+
+template <class T>
+int qlv_lanes(int64_t B, int n, int sms)
+{
+    int L = sizeof(T) == 8 ? ql_lockstep_lanes(B, sms) * 2 : ql_lockstep_lanes(B, sms) / 4;
+    if (L > 32) L = 32;
+    if (L < 1) L = 1;
+    while (L > 1 && (size_t)4 * L * n * sizeof(T) > kQlvSmemCap) L >>= 1;
+    return L;
+}
+
+inline int qlv_threads(int L, int n)
+{
+    const int t = 32 + (L * n / 6 + 31) / 32 * 32;
+    return t < 128 ? 128 : (t > 1024 ? 1024 : t);
 }
 
 // Ascending order (ties by index), eigenvectors as rows, each signed so that
@@ -205,13 +277,31 @@ iesh_status syev_run(int64_t B, int n, const T *A, T *lam, T *V, uint32_t *info,
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        // eigenvalues only: one matrix per thread; with eigenvectors: one per
-        // CTA, the rotations applied to all rows of P in parallel
-        if (vectors)
-            k_syev_qlv<T><<<(unsigned)B, 128, (size_t)4 * n * sizeof(T), st>>>(B, n, wk, wstride, info);
-        else
-            k_syev_ql<T><<<(unsigned)((B + 31) / 32), 32, 0, st>>>(B, n, wk, wstride, 0, info);
-        e = cudaGetLastError();
+        // eigenvalues only: L matrices per warp in lockstep; with
+        // eigenvectors: one per CTA, the rotations applied to all rows of P
+        // in parallel
+        int dev = 0, sms = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess && vectors) {
+            const int L = qlv_lanes<T>(B, n, sms);
+            const size_t qsm = (size_t)4 * L * n * sizeof(T);
+            if (qsm > 48 * 1024) {
+                cudaFuncAttributes fa;
+                e = cudaFuncGetAttributes(&fa, k_syev_qlv<T>);
+                if (e == cudaSuccess && fa.maxDynamicSharedSizeBytes < (int)qsm)
+                    e = cudaFuncSetAttribute(k_syev_qlv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kQlvSmemCap);
+            }
+            if (e == cudaSuccess)
+                k_syev_qlv<T><<<(unsigned)((B + L - 1) / L), qlv_threads(L, n), qsm, st>>>(B, n, wk, wstride, L,
+                                                                                          info);
+        } else if (e == cudaSuccess) {
+            const int L = ql_lockstep_lanes(B, sms);
+            const int64_t warps = (B + L - 1) / L;
+            k_syev_ql<T><<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(B, n, wk, wstride, L, info);
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
         k_syev_out<T><<<(unsigned)B, kSyevThreads, 0, st>>>(B, n, wk, wstride, vectors ? 1 : 0, lam, V);

@@ -1,8 +1,9 @@
 // iesh_syev.cuh -- device building blocks of the batched dense symmetric
 // eigensolver (internal): Householder reduction to tridiagonal form by one
-// CTA, and implicit-shift QL iterations on the tridiagonal matrix by one
-// thread, with the rotations applied to selected rows of the reflector
-// product.
+// CTA, and implicit-shift QL iterations on the tridiagonal matrix (one
+// matrix per lane of a warp in lockstep, or one per CTA with every row of
+// the reflector product rotated), with the rotations applied to selected
+// rows of the reflector product.
 //
 // Method (Householder 1958 reduction; the QL algorithm with implicit
 // Wilkinson shifts of Bowdler, Martin, Reinsch and Wilkinson 1968):
@@ -184,155 +185,158 @@ __device__ void householder_tridiag(T *A, int lda, int n, T *d, T *e, T *tau, T 
     __syncthreads();
 }
 
-// Implicit-shift QL on the symmetric tridiagonal matrix (d, e) of order n
-// (e[i] = T_{i,i+1}, e[n-1] = 0), by one thread.  The eigenvalues overwrite
-// d, in no particular order; e is destroyed.  Every plane rotation that acts
-// on Z's columns i, i+1 is applied to entries i, i+1 of the R tracked rows
-// Y (entry i of row q at Y[i * R + q]).  Returns false when an eigenvalue
-// needed more than kSyevMaxIter iterations.
+// Implicit-shift QL on symmetric tridiagonal matrices of order n, one per
+// lane of a warp, the lanes in lockstep.  A thread-per-matrix loop diverges
+// at once (every matrix deflates after its own number of sweeps, and each
+// sweep has its own length), and a divergent warp issues one instruction per
+// lane; the FP64 pipe then costs a full warp slot per lane-instruction.  So
+// the whole warp works on eigenvalue l together: it scans for each lane's
+// first negligible off-diagonal entry m, runs one sweep i = max(m) - 1 .. l
+// in which lane j takes part while i < m_j, and repeats until every lane has
+// deflated d[l]; then l + 1.  A lane computes exactly what it would compute
+// alone (the same rotations in the same order).
+//
+// Lane data: d[i ld], e[i ld] (e[i] = T_{i,i+1}, e[n-1] = 0).  The
+// eigenvalues overwrite d, in no particular order; e is destroyed.  Every
+// lane of the warp calls (the votes need the full warp); a lane that is not
+// live touches no memory.
+
+// Per-lane state of the lockstep iteration between sweeps.
 template <class T>
-__device__ bool ql_implicit(int n, T *d, T *e, T *Y, int R)
+struct QlLane {
+    int l = 0, iter = 0, m = 0;
+    bool live = false, ok = true, act = false;
+};
+
+// Advance to the next sweep: for the warp's current l, each live lane's m
+// (first index >= l with |e[m]| <= u (|d[m]| + |d[m+1]|), else n - 1); a
+// lane takes part (act) when m != l.  When no lane does, l moves on.
+// Returns false once l == n (warp-uniform): every eigenvalue has converged
+// or its lane has given up after kSyevMaxIter sweeps (ok = false).
+template <class T>
+__device__ bool ql_lockstep_next(int n, const T *d, const T *e, int ld, QlLane<T> &q)
 {
-    for (int l = 0; l < n; ++l) {
-        int iter = 0;
-        for (;;) {
-            // first negligible off-diagonal entry at or after l
-            int m = l;
-            for (; m < n - 1; ++m) {
-                const T dd = fabs(d[m]) + fabs(d[m + 1]);
-                if (fabs(e[m]) <= SyevEps<T>::u * dd) break;
-            }
-            if (m == l) break;  // d[l] is an eigenvalue
-            if (++iter > kSyevMaxIter) return false;
-            // Wilkinson shift: the eigenvalue of the leading 2 x 2 block nearer
-            // d[l], entering as g = d[m] - shift
-            T g = (d[l + 1] - d[l]) / (T(2) * e[l]);
-            T r = hypot(g, T(1));
-            g = d[m] - d[l] + e[l] / (g + copysign(r, g));
-            T s = 1, c = 1, p = 0;
-            bool restart = false;
-            for (int i = m - 1; i >= l; --i) {
-                const T f = s * e[i], b = c * e[i];
-                r = syev_rot(f, g, s, c);
-                e[i + 1] = r;
-                if (r == T(0)) {  // the bulge vanished: split the matrix here
-                    d[i + 1] -= p;
-                    e[m] = 0;
-                    restart = true;
-                    break;
-                }
-                g = d[i + 1] - p;
-                r = (d[i] - g) * s + T(2) * c * b;
-                p = s * r;
-                d[i + 1] = g + p;
-                g = c * r - b;
-                for (int q = 0; q < R; ++q) {
-                    const T yi = Y[(size_t)i * R + q], yj = Y[(size_t)(i + 1) * R + q];
-                    Y[(size_t)(i + 1) * R + q] = s * yi + c * yj;
-                    Y[(size_t)i * R + q] = c * yi - s * yj;
+    constexpr unsigned kFull = 0xffffffffu;
+    for (; q.l < n; ++q.l, q.iter = 0) {
+        int m = n - 1;
+        bool found = !q.live;
+        for (int k = q.l;; ++k) {
+            if (!found) {
+                if (k >= n - 1) {
+                    found = true;
+                } else {
+                    const T dd = fabs(d[(size_t)k * ld]) + fabs(d[(size_t)(k + 1) * ld]);
+                    if (fabs(e[(size_t)k * ld]) <= SyevEps<T>::u * dd) {
+                        m = k;
+                        found = true;
+                    }
                 }
             }
-            if (restart) continue;
-            d[l] -= p;
-            e[l] = g;
-            e[m] = 0;
+            if (__all_sync(kFull, found)) break;
         }
+        q.m = m;
+        q.act = q.live && m != q.l;
+        if (q.act && ++q.iter > kSyevMaxIter) {
+            q.ok = false;
+            q.live = false;
+            q.act = false;
+        }
+        if (__any_sync(kFull, q.act)) return true;
     }
-    return true;
+    return false;
 }
 
-// The same iteration with all n rows of the reflector product tracked, by a
-// CTA: thread 0 runs the scalar recurrence of a sweep (the rotations of one
-// implicit QL step, i = m-1 down to l) and stores each rotation's (c, s) in
-// shared memory; then every thread applies the sweep to its own rows r of
-// P, entry i of row r at P[i ld + r] (so a warp's threads touch consecutive
-// addresses), carrying entry i+1 of the previous rotation in a register.
-// d, e in shared memory (d, e, rc, rs: n entries each; flags: 4 ints).
-// Every thread calls; the result (false: an eigenvalue needed more than
-// kSyevMaxIter iterations) is the same in every thread.
-template <class T>
-__device__ bool ql_implicit_rows(int n, T *d, T *e, T *P, int ld, T *rc, T *rs, int *flags)
+// One sweep i = max(m) - 1 .. l of the active lanes (Wilkinson shift: the
+// eigenvalue of the leading 2 x 2 block nearer d[l]).  Every rotation that
+// acts on Z's columns i, i+1 is applied to entries i, i+1 of the R tracked
+// rows (entry i of row q at Y[i yld + q yq]; entry i+1 of the previous
+// rotation carried in a register) and, when rc is given, stored as
+// (rc, rs)[i rld].  Returns the lowest index the sweep's rotations reached
+// (l, or i + 1 when the bulge vanished at i and the matrix split there), or
+// -1 in a lane that took no part.
+template <class T, int R>
+__device__ int ql_lockstep_sweep(const int n, T *d, T *e, int ld, T *Y, int yld, int yq, T *rc, T *rs, int rld,
+                                 const QlLane<T> &q)
 {
-    const int tid = threadIdx.x;
-    // flags[0]: next sweep's l, flags[1]: its m (l == m: done), flags[2]: failed
-    int l = 0, iter = 0;
-    if (tid == 0) flags[2] = 0;
-    for (;;) {
-        if (tid == 0) {
-            int ls = -1, ms = -1;
-            while (l < n) {
-                int m = l;
-                for (; m < n - 1; ++m) {
-                    const T dd = fabs(d[m]) + fabs(d[m + 1]);
-                    if (fabs(e[m]) <= SyevEps<T>::u * dd) break;
-                }
-                if (m == l) {  // d[l] converged
-                    ++l;
-                    iter = 0;
-                    continue;
-                }
-                if (++iter > kSyevMaxIter) {
-                    flags[2] = 1;
-                    l = n;
-                    break;
-                }
-                T g = (d[l + 1] - d[l]) / (T(2) * e[l]);
-                T r = hypot(g, T(1));
-                g = d[m] - d[l] + e[l] / (g + copysign(r, g));
-                T sn = 1, cs = 1, p = 0;
-                int i = m - 1;
-                bool split = false;
-                for (; i >= l; --i) {
-                    const T f = sn * e[i], b = cs * e[i];
-                    r = syev_rot(f, g, sn, cs);
-                    e[i + 1] = r;
-                    if (r == T(0)) {
-                        d[i + 1] -= p;
-                        e[m] = 0;
-                        split = true;
-                        break;
-                    }
-                    g = d[i + 1] - p;
-                    r = (d[i] - g) * sn + T(2) * cs * b;
-                    p = sn * r;
-                    d[i + 1] = g + p;
-                    g = cs * r - b;
-                    rc[i] = cs;
-                    rs[i] = sn;
-                }
-                if (split) {
-                    // rotations m-1 .. i+1 were taken; apply those, restart at l
-                    ls = i + 1;
-                    ms = m;
-                    break;
-                }
-                d[l] -= p;
-                e[l] = g;
-                e[m] = 0;
-                ls = l;
-                ms = m;
-                break;
-            }
-            flags[0] = ls;
-            flags[1] = ms;
-        }
-        __syncthreads();
-        const int ls = flags[0], ms = flags[1];
-        if (ls < 0) break;  // every eigenvalue converged (or the cap was hit)
-        for (int row = tid; row < n; row += blockDim.x) {
-            T yj = P[(size_t)ms * ld + row];
-            for (int i = ms - 1; i >= ls; --i) {
-                const T yi = P[(size_t)i * ld + row];
-                P[(size_t)(i + 1) * ld + row] = rs[i] * yi + rc[i] * yj;
-                yj = rc[i] * yi - rs[i] * yj;
-            }
-            P[(size_t)ls * ld + row] = yj;
-        }
-        __syncthreads();
+    constexpr unsigned kFull = 0xffffffffu;
+    const int l = q.l, m = q.m;
+    const int mx = __reduce_max_sync(kFull, q.act ? m : 0);
+    T g = 0, s = 1, c = 1, p = 0, yj[R > 0 ? R : 1];
+    if (q.act) {
+        const T dl = d[(size_t)l * ld], el = e[(size_t)l * ld];
+        g = (d[(size_t)(l + 1) * ld] - dl) / (T(2) * el);
+        const T r = hypot(g, T(1));
+        g = d[(size_t)m * ld] - dl + el / (g + copysign(r, g));
+#pragma unroll
+        for (int k = 0; k < R; ++k) yj[k] = Y[(size_t)m * yld + k * yq];
     }
-    const bool ok = flags[2] == 0;
-    __syncthreads();
-    return ok;
+    bool run = q.act;
+    int low = q.act ? l : -1;
+    for (int i = mx - 1; i >= l; --i) {
+        if (run && i < m) {
+            const T ei = e[(size_t)i * ld];
+            const T f = s * ei, b = c * ei;
+            T r = syev_rot(f, g, s, c);
+            e[(size_t)(i + 1) * ld] = r;
+            if (r == T(0)) {  // the bulge vanished: split here, rescan
+                d[(size_t)(i + 1) * ld] -= p;
+                e[(size_t)m * ld] = 0;
+#pragma unroll
+                for (int k = 0; k < R; ++k) Y[(size_t)(i + 1) * yld + k * yq] = yj[k];
+                run = false;
+                low = i + 1;
+            } else {
+                g = d[(size_t)(i + 1) * ld] - p;
+                r = (d[(size_t)i * ld] - g) * s + T(2) * c * b;
+                p = s * r;
+                d[(size_t)(i + 1) * ld] = g + p;
+                g = c * r - b;
+                if (rc) {
+                    rc[(size_t)i * rld] = c;
+                    rs[(size_t)i * rld] = s;
+                }
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const T yi = Y[(size_t)i * yld + k * yq];
+                    Y[(size_t)(i + 1) * yld + k * yq] = s * yi + c * yj[k];
+                    yj[k] = c * yi - s * yj[k];
+                }
+            }
+        }
+    }
+    if (run) {
+        d[(size_t)l * ld] -= p;
+        e[(size_t)l * ld] = g;
+        e[(size_t)m * ld] = 0;
+#pragma unroll
+        for (int k = 0; k < R; ++k) Y[(size_t)l * yld + k * yq] = yj[k];
+    }
+    return low;
+}
+
+// The whole iteration with R tracked rows.  Returns false in a lane whose
+// eigenvalue needed more than kSyevMaxIter iterations.
+template <class T, int R>
+__device__ bool ql_lockstep(int n, T *d, T *e, int ld, T *Y, int yld, int yq, bool valid)
+{
+    QlLane<T> q;
+    q.live = valid;
+    while (ql_lockstep_next<T>(n, d, e, ld, q))
+        ql_lockstep_sweep<T, R>(n, d, e, ld, Y, yld, yq, (T *)nullptr, (T *)nullptr, 0, q);
+    return q.ok;
+}
+
+// Lanes per warp for ql_lockstep over `items` matrices on a GPU with `sms`
+// SMs: the FP64 pipe of each SM sub-partition takes one warp instruction at
+// a time whatever its active lanes, so the matrices are spread over one warp
+// per sub-partition (4 per SM) first and packed into wider warps only when
+// there are more of them.  A power of two in [1, 32].
+__host__ __device__ inline int ql_lockstep_lanes(int64_t items, int sms)
+{
+    const int64_t slots = 4LL * (sms > 0 ? sms : 1);
+    int L = 1;
+    while (L < 32 && (int64_t)L * slots < items) L <<= 1;
+    return L;
 }
 
 }  // namespace iesh

@@ -662,8 +662,9 @@ __global__ void __launch_bounds__(64) k2_accept(DevState s, Model2Dev md)
 //   k2g_reduce  kick + drift (mode 1), H(x) built in shared memory (or in
 //               the trajectory's scratch for large N), Householder reduction
 //               with row 1 of the reflector product tracked;
-//   k2g_ql      QL iterations, one trajectory per thread, rotating the
-//               adsorbate rows (row 0 of P is e_0, row 1 tracked);
+//   k2g_ql      QL iterations, trajectories in lockstep across a warp,
+//               rotating the adsorbate rows (row 0 of P is e_0, row 1
+//               tracked);
 //   k2g_finish  ascending order, gauge, forces, second kick.
 // Everything after the eigenpairs (couplings, propagation, hops, rescale) is
 // the rank-two path's: those kernels read only the eigenvalues and the two
@@ -738,13 +739,19 @@ __global__ void __launch_bounds__(256) k2g_reduce(DevState s, Model2Dev md, doub
     }
 }
 
-__global__ void __launch_bounds__(32) k2g_ql(DevState s)
+// L trajectories per warp in lockstep (ql_lockstep), four warps per CTA:
+// work item (warp index) L + lane.
+__global__ void __launch_bounds__(128) k2g_ql(DevState s, int L)
 {
-    const int64_t t = traj_of(s, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
-    if (t < 0 || (s.status[t] & ST_DONE)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (gw * L >= s.n) return;  // the whole warp: past the batch
+    const int64_t t = lane < L ? traj_of(s, gw * L + lane) : -1;
+    const bool valid = t >= 0 && !(s.status[t] & ST_DONE);
     const int N = s.N;
-    double *b = s.scratch + t * s.scratch_stride;
-    if (!ql_implicit<double>(N, b, b + N, b + 2 * N, 2)) atomicOr(&s.status[t], ST_SECULAR);
+    double *b = s.scratch + (valid ? t : 0) * s.scratch_stride;
+    const bool ok = ql_lockstep<double, 2>(N, b, b + N, 1, b + 2 * N, 2, 1, valid);
+    if (valid && !ok) atomicOr(&s.status[t], ST_SECULAR);
 }
 
 __global__ void __launch_bounds__(256) k2g_finish(DevState s, Model2Dev md, double dt, int mode)
@@ -852,6 +859,7 @@ struct iesh2_ctx {
     int skip_bound = 0;
     bool mixed = false;
     bool dense = false;  // eigenpairs from the dense symmetric eigensolver
+    int sms = 1;         // SMs of the context's device
     Model2Dev md;
     DevState ds;
     std::vector<void *> allocs;
@@ -913,9 +921,9 @@ cudaError_t launch_eigen2(iesh2_ctx *ctx, double dt, int mode)
         k2g_reduce<<<(unsigned)d.n, 256, dense_reduce_smem(d.N), ctx->stream>>>(d, ctx->md, dt, mode);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        // one warp per CTA: few trajectories per warp-wide FP64 recurrence,
-        // so spread the warps over as many SMs as possible
-        k2g_ql<<<(unsigned)((d.n + 31) / 32), 32, 0, ctx->stream>>>(d);
+        const int L = ql_lockstep_lanes(d.n, ctx->sms);
+        const int64_t warps = (d.n + L - 1) / L;
+        k2g_ql<<<(unsigned)((warps + 3) / 4), 128, 0, ctx->stream>>>(d, L);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         k2g_finish<<<(unsigned)d.n, 256, (size_t)6 * d.N * sizeof(double), ctx->stream>>>(d, ctx->md, dt, mode);
         return cudaGetLastError();
@@ -1000,6 +1008,12 @@ iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int precisio
         return fail2(ctx, IESH_EINVAL, "unknown eigensolver %d", model->eigensolver);
     ctx->mixed = precision == IESH_PREC_MIXED;
     ctx->dense = model->profile == 1 || model->eigensolver == 1;
+    {
+        int dev = 0, sms = 0;
+        CU2(cudaGetDevice(&dev));
+        CU2(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        ctx->sms = sms;
+    }
     ctx->N = N;
     ctx->M = M;
     ctx->Ne = Ne;
