@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kSyevThreads) k_syev_reduce(int64_t B, int n, 
         A[(size_t)i * lda + j] = src[idx];
     }
     __syncthreads();
-    householder_tridiag<T>(A, lda, n, d, e, tau, vec, vec + n, nullptr, vec + 2 * n);
+    householder_tridiag<T>(A, lda, n, d, e, tau, vec, vec + n, nullptr, vec + 2 * n, sm);
     if (!vectors) return;
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Pt[idx] = (idx / n == idx % n) ? T(1) : T(0);
     __syncthreads();
@@ -78,12 +78,18 @@ __global__ void __launch_bounds__(kSyevThreads) k_syev_reduce(int64_t B, int n, 
         if (t == T(0)) continue;  // uniform: tau is in global memory written before the barrier
         for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) v[i] = A[(size_t)i * lda + k];
         __syncthreads();
-        for (int c = k + 1 + warp; c < n; c += nw) {  // z_c = (P_sub^T v)_c = sum_r Pt[c][r] v_r
-            const T *row = Pt + (size_t)c * n;
+        // z_c = (P_sub^T v)_c = sum_r Pt[c][r] v_r, 8 lanes per row c (three
+        // FP64 additions per reduction instead of a warp's five)
+        for (int c0 = k + 1 + 4 * warp; c0 < n; c0 += 4 * nw) {
+            const int c = c0 + (lane >> 3);
             T acc = 0;
-            for (int r = k + 1 + lane; r < n; r += 32) acc = fma(row[r], v[r], acc);
-            acc = syev_warp_sum(acc);
-            if (lane == 0) z[c] = t * acc;
+            if (c < n) {
+                const T *row = Pt + (size_t)c * n;
+                for (int r = k + 1 + (lane & 7); r < n; r += 8) acc = fma(row[r], v[r], acc);
+            }
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if ((lane & 7) == 0 && c < n) z[c] = t * acc;
         }
         __syncthreads();
         for (int c = k + 1 + warp; c < n; c += nw) {

@@ -90,9 +90,17 @@ __device__ __forceinline__ T syev_warp_sum(T v)
 // of A below the diagonal the reflector vector v_k (a zero tau_k: H_k = I).
 // r1 (optional, n entries) receives row 1 of P (row 0 of P is e_0 because
 // every reflector leaves index 0 alone).  v, w: n entries each; sh: 6
-// entries; all of these in shared memory.
+// entries; all of these in shared memory.  lower_only (for A in shared
+// memory): read and update only the lower triangle (j <= i) of the trailing
+// matrix, and form w = A v one thread per row, the upper half of each row
+// read down the columns.  A warp per row spends five FP64 additions per row
+// on its reduction, more than its three or four FMAs at n near 100, and on
+// this GPU an FP64 instruction costs the same whatever its active lanes; a
+// thread per row has no reduction, and its column-wise reads of shared
+// memory (odd lda) are conflict-free.  The upper triangle is left stale.
 template <class T>
-__device__ void householder_tridiag(T *A, int lda, int n, T *d, T *e, T *tau, T *v, T *w, T *r1, T *sh)
+__device__ void householder_tridiag(T *A, int lda, int n, T *d, T *e, T *tau, T *v, T *w, T *r1, T *sh,
+                                    bool lower_only)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     if (r1)
@@ -133,13 +141,24 @@ __device__ void householder_tridiag(T *A, int lda, int n, T *d, T *e, T *tau, T 
             A[(size_t)i * lda + k] = vi;
         }
         __syncthreads();
-        // w = t A_sub v, one warp per row
-        for (int i = k + 1 + warp; i < n; i += nw) {
-            const T *row = A + (size_t)i * lda;
-            T acc = 0;
-            for (int j = k + 1 + lane; j < n; j += 32) acc = fma(row[j], v[j], acc);
-            acc = syev_warp_sum(acc);
-            if (lane == 0) w[i] = t * acc;
+        // w = t A_sub v
+        if (lower_only) {
+            for (int i = k + 1 + tid; i < n; i += blockDim.x) {
+                T acc = 0;
+                for (int j = k + 1; j < n; ++j) {
+                    const T a = j <= i ? A[(size_t)i * lda + j] : A[(size_t)j * lda + i];
+                    acc = fma(a, v[j], acc);
+                }
+                w[i] = t * acc;
+            }
+        } else {  // A in global memory: a warp per row, coalesced
+            for (int i = k + 1 + warp; i < n; i += nw) {
+                const T *row = A + (size_t)i * lda;
+                T acc = 0;
+                for (int j = k + 1 + lane; j < n; j += 32) acc = fma(row[j], v[j], acc);
+                acc = syev_warp_sum(acc);
+                if (lane == 0) w[i] = t * acc;
+            }
         }
         __syncthreads();
         // w -= (t/2)(v.w) v (then A_sub - v w^T - w v^T = H_k A_sub H_k);
@@ -167,7 +186,8 @@ __device__ void householder_tridiag(T *A, int lda, int n, T *d, T *e, T *tau, T 
         for (int i = k + 1 + warp; i < n; i += nw) {
             T *row = A + (size_t)i * lda;
             const T vi = v[i], wi = w[i];
-            for (int j = k + 1 + lane; j < n; j += 32) row[j] = fma(-vi, w[j], fma(-wi, v[j], row[j]));
+            const int jend = lower_only ? i + 1 : n;
+            for (int j = k + 1 + lane; j < jend; j += 32) row[j] = fma(-vi, w[j], fma(-wi, v[j], row[j]));
         }
         __syncthreads();
     }

@@ -730,7 +730,7 @@ __global__ void __launch_bounds__(256) k2g_reduce(DevState s, Model2Dev md, doub
         A[(size_t)(2 + k) * lda + 1] = v1;
     }
     __syncthreads();
-    householder_tridiag<double>(A, lda, N, d, e, tau, v, w, r1, sh);
+    householder_tridiag<double>(A, lda, N, d, e, tau, v, w, r1, sh, dense_in_smem(N));
     for (int i = tid; i < N; i += blockDim.x) {
         out[i] = d[i];
         out[N + i] = e[i];
