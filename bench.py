@@ -755,10 +755,12 @@ def run_workload(args):
                 res[f"n{n}_{name}"] = {"matrices": B, "matrices_per_s": B / sec, "ms": 1e3 * sec,
                                        "approx_tflops": flops / sec / 1e12}
         n, dt = args.n_traj, 2.0
-        md = W.two_orbital_profiled(100, seed=5)
-        x, p, occ, C = W.two_orbital_state(md, n, 3, kT=0.01, weight=0.5)
+        md0 = W.two_orbital_profiled(100, seed=5)
+        x, p, occ, C = W.two_orbital_state(md0, n, 3, kT=0.01, weight=0.5)
         dyn = {}
-        for prec, name in ((P.PREC_FP64, "fp64"), (P.PREC_MIXED, "mixed")):
+        for prec, solver, name in ((P.PREC_FP64, "nested", "fp64"), (P.PREC_MIXED, "nested", "mixed"),
+                                   (P.PREC_FP64, "dense", "fp64_dense"), (P.PREC_MIXED, "dense", "mixed_dense")):
+            md = dict(md0, eigensolver="dense") if solver == "dense" else md0
             c = two.TwoOrbitalContext(md, n, precision=prec, stream=stream.cuda_stream)
             c.set_state(x, p, occ.astype(np.int16), C if prec == P.PREC_FP64 else C.astype(np.complex64))
             c.run(dt, max(3, args.warmup), 0)
@@ -790,7 +792,8 @@ def run_workload(args):
                     config={"workload": "random symmetric matrices n in {64, 102, 256} (4096, 4096, 1024 "
                                         "per batch), FP64 and FP32; two-orbital dynamics with own bath "
                                         f"profiles (non-parallel couplings), 100 GL states, {n} trajectories, "
-                                        "dt=2, eigenpairs from the dense solver",
+                                        "dt=2, eigenpairs from two nested secular equations (default) "
+                                        "and from the dense solver",
                             "value_is": "n=102 FP64 matrices/s"},
                     results={"syev": res, "two_orbital_profiled": dyn})
     elif args.workload == "eocc":

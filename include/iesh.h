@@ -273,10 +273,13 @@ const char *iesh_ensemble_last_error(const iesh_ensemble *ens);
 
 /* Kernel shapes.  FP64 contexts: cheb_ept (1 or 2) electrons per thread and
  * cheb_G column groups per CTA of the propagator (cheb_G * N <= 1024).
- * Mixed contexts: cheb_ept must be 4 (each thread holds 4 orbitals x 4
- * electrons) and cheb_G * ceil(N/4) <= 256, with 8 * Np * (8 cheb_G + 1)
- * + 192 * Np bytes of shared memory (Np = N rounded up to a multiple of 4;
- * the second term stages W) at most 110 KiB.  hop_threads (256 or 512):
+ * Mixed contexts: cheb_ept 4 (each thread holds 4 orbitals x 4 electrons,
+ * two CTAs per SM) with cheb_G * ceil(N/4) <= 256 and 8 * Np * (8 cheb_G +
+ * 1) + 192 * Np bytes of shared memory (Np = N rounded up to a multiple of
+ * 4; the second term stages W) at most 110 KiB; or cheb_ept 32 (8 orbitals
+ * x 4 electrons per thread, one CTA per SM) with cheb_G * ceil(ceil(N/4)/2)
+ * <= 256 and the same shared memory at most 220 KiB; or cheb_ept 8 with
+ * cheb_G 1, the tensor-core kernel (N <= 128, Ne <= 56).  hop_threads (256 or 512):
  * threads of the LU hop kernel; 0 restores the built-in choice, which for
  * mixed contexts is a Gauss-Jordan elimination of all determinant ratios,
  * in registers for N <= 128 and Ne <= 56 and with the rows past 128 in
@@ -457,9 +460,11 @@ typedef struct {
                           ((eps_k - prof_center[a]) / prof_width[a])^2) (the border
                           vectors are not parallel) */
     double prof_center[2], prof_width[2];
-    int eigensolver;   /* 0: the rank-two arrowhead secular solver for profile 0, the
-                          dense symmetric eigensolver (as iesh_syev_batched, FP64) for
-                          profile 1; 1: the dense solver always */
+    int eigensolver;   /* 0: secular equations, the rank-two arrowhead reduction for
+                          profile 0, two nested arrowheads (orbital 1 with the bath,
+                          then orbital 0 against those eigenvectors) for profile 1;
+                          1: the dense symmetric eigensolver (as iesh_syev_batched,
+                          FP64) always */
 } iesh2_model;
 
 /* Create a context for up to max_traj trajectories; precision

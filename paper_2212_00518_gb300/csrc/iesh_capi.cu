@@ -646,14 +646,14 @@ iesh_status iesh_set_kernel_shape(iesh_ctx *ctx, int cheb_ept, int cheb_G, int h
 {
     if (!ctx) return IESH_EINVAL;
     if (ctx->opt.precision == IESH_PREC_MIXED) {
-        const int nq = (ctx->N + 3) / 4;
-        const bool simt = cheb_ept == 4 && cheb_G > 0 && cheb_G * nq <= 256 &&
-                          cheb32_smem_bytes(ctx->N, cheb_G) <= kCheb32MaxSmem;
+        const bool simt = (cheb_ept == 4 && cheb32_shape_ok(ctx->N, cheb_G, 1)) ||
+                          (cheb_ept == 32 && cheb32_shape_ok(ctx->N, cheb_G, 2));
         const bool tc = cheb_ept == 8 && cheb_G == 1 && cheb_tc_eligible(ctx->N, ctx->Ne);
         if (!((cheb_ept == 0 && cheb_G == 0) || simt || tc))
             return fail(ctx, IESH_EINVAL,
                         "mixed propagator shape (%d, %d) invalid for N=%d, Ne=%d (need ept 4 with "
-                        "G*ceil(N/4) <= 256, or ept 8, G 1 for the tensor-core kernel: N <= 128, Ne <= 56)",
+                        "G*ceil(N/4) <= 256, ept 32 with G*ceil(ceil(N/4)/2) <= 256, each within its "
+                        "shared-memory cap, or ept 8, G 1 for the tensor-core kernel: N <= 128, Ne <= 56)",
                         cheb_ept, cheb_G, ctx->N, ctx->Ne);
     } else if (cheb_ept < 0 || cheb_ept > 2 || cheb_G < 0 || (cheb_ept > 0) != (cheb_G > 0) ||
                cheb_G * ctx->N > 1024) {
@@ -676,8 +676,9 @@ iesh_status iesh_get_kernel_shape(iesh_ctx *ctx, int *cheb_ept, int *cheb_G, int
             e = 8;
             g = 1;
         } else if (ctx->opt.precision == IESH_PREC_MIXED) {
-            e = 4;
-            cheb32_shape(ctx->N, ctx->Ne, g);
+            const int qpt = ctx->N > kCheb32WideMinN ? 2 : 1;
+            e = qpt == 2 ? 32 : 4;
+            cheb32_shape(ctx->N, ctx->Ne, g, qpt);
         } else {
             cheb_shape(ctx->N, ctx->Ne, e, g);
         }

@@ -41,12 +41,16 @@ void lead_bath(int disc, int n, double a, double b, double mu, int n_lo, std::ve
 void cheb_shape(int N, int Ne, int &ept, int &G);
 // Trajectories per CTA of the eigen kernels (slots of N threads, <= 512 threads)
 int eigen_tpb(int N);
-// FP32 (mixed-precision) propagator: 4 electrons per thread, G column groups
+// FP32 (mixed-precision) propagator: 4 electrons per thread, G column
+// groups; one row quad per thread (two CTAs per SM) or two (one CTA per SM)
 constexpr size_t kCheb32MaxSmem = 110 * 1024;
+constexpr size_t kCheb32WideMaxSmem = 220 * 1024;
+constexpr int kCheb32WideMinN = 224;  // default to two row quads per thread past this N
 constexpr int kCheb32WRows = 16; // rows of W per chunk staged in shared memory
 constexpr int kCheb32WRing = 3;  // chunks in the ring (filled 2 ahead)
 size_t cheb32_smem_bytes(int N, int G);
-void cheb32_shape(int N, int Ne, int &G);
+void cheb32_shape(int N, int Ne, int &G, int qpt = 1);
+bool cheb32_shape_ok(int N, int G, int qpt);
 // FP32 propagator on the tensor cores (3xTF32), N <= 128 and Ne <= 56
 constexpr size_t kChebTcMaxSmem = 224 * 1024;
 size_t cheb_tc_smem_bytes(int N, int Ne);

@@ -100,6 +100,11 @@ __device__ __forceinline__ double dfl_value(dfl a) { return (double)a.hi + (doub
 // with one extra pole h_- inserted at index hpos (hpos < 0: none); ddf is
 // the bath table [nb][nb], hdf[k] = h_- - eps_k as double-float pairs, and
 // z2df the weights of all M poles in sorted order.
+// Nested double-float mode (EV_NESTED): the M poles are roots mu_k = eps_{ob[k]}
+// + tau_k of an inner arrowhead over nb bath poles; ddf is the bath table
+// [nb][nb], hdf[k] = tau_k as a double-float pair and ob[k] its bath pole,
+// so mu_o - mu_k = (eps_{ob[o]} - eps_{ob[k]}) + (tau_o - tau_k) keeps its
+// relative accuracy however close the two roots are.
 template <class R>
 struct Poles {
     int M;
@@ -108,12 +113,24 @@ struct Poles {
     int nb, hpos;
     R hm;
     const float2 *__restrict__ hdf;
+    const int *__restrict__ ob;
 };
 
 // Evaluation modes of the secular sums: EV_PLAIN (eps_o - eps_k formed per
 // term), EV_TABLE (FP64 table), EV_DFLOAT (double-float sums on the FP32
-// pipe; the origin term and everything outside the sums stay FP64).
-enum { EV_PLAIN = 0, EV_TABLE = 1, EV_DFLOAT = 2, EV_TWO_DF = 3 };
+// pipe; the origin term and everything outside the sums stay FP64), EV_TWO_DF
+// and EV_NESTED (double-float, see Poles).
+enum { EV_PLAIN = 0, EV_TABLE = 1, EV_DFLOAT = 2, EV_TWO_DF = 3, EV_NESTED = 4 };
+
+// mu_o - mu_k + td for the nested poles (EV_NESTED), in double-float.
+template <class R>
+__device__ __forceinline__ dfl nested_gap(const Poles<R> &P, int o, int k, dfl td)
+{
+    const float2 e = P.ddf[(size_t)P.ob[k] * P.nb + P.ob[o]];  // eps_ob[o] - eps_ob[k]
+    const float2 to = P.hdf[o], tk = P.hdf[k];
+    const dfl dtau = dfl_add({to.x, to.y}, {-tk.x, -tk.y});
+    return dfl_add(dfl_add({e.x, e.y}, dtau), td);
+}
 
 // ============================================================= eigenpairs
 // The one-electron Hamiltonian of Sec. II B is an arrowhead matrix:
@@ -153,6 +170,28 @@ __device__ __forceinline__ Sec<R> sec_eval(const Poles<R> &P, int o, R tau, R eo
                 d2[h] = dfl_add(d2[h], dfl_mul(q, r));
                 if (ABS) da[h] = dfl_add(da[h], q.hi < 0.f ? dfl{-q.hi, -q.lo} : q);
             }
+        };
+        int k = 0;
+        for (; k + 1 < M; k += 2) {
+            term(k, 0);
+            term(k + 1, 1);
+        }
+        if (k < M) term(k, 0);
+        s1 = (R)dfl_value(dfl_add(d1[0], d1[1]));
+        s2 = (R)dfl_value(dfl_add(d2[0], d2[1]));
+        sa = (R)dfl_value(dfl_add(da[0], da[1]));
+    } else if constexpr (EV == EV_NESTED) {
+        // two accumulator sets, as above
+        const dfl td = dfl_from((double)tau);
+        dfl d1[2] = {{0.f, 0.f}, {0.f, 0.f}}, d2[2] = {{0.f, 0.f}, {0.f, 0.f}}, da[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        auto term = [&](int k, int h) {
+            if (k == o) return;
+            const dfl r = dfl_rcp(nested_gap(P, o, k, td));  // 1 / (lam - mu_k)
+            const float2 zk = P.z2df[k];
+            const dfl q = dfl_mul({zk.x, zk.y}, r);
+            d1[h] = dfl_add(d1[h], q);
+            d2[h] = dfl_add(d2[h], dfl_mul(q, r));
+            if (ABS) da[h] = dfl_add(da[h], q.hi < 0.f ? dfl{-q.hi, -q.lo} : q);
         };
         int k = 0;
         for (; k + 1 < M; k += 2) {
@@ -233,7 +272,8 @@ __device__ bool sec_iterate(const Poles<R> &P, R h, int o, int kind, R D, R &lo,
                             Sec<R> &e, bool have)
 {
     // rounding unit of the sums: 2^-44 covers the double-float sums
-    const R u = (EV == EV_DFLOAT || EV == EV_TWO_DF) ? R(5.684341886080802e-14) : Roundoff<R>::u;
+    const R u = (EV == EV_DFLOAT || EV == EV_TWO_DF || EV == EV_NESTED) ? R(5.684341886080802e-14)
+                                                                       : Roundoff<R>::u;
     const R eomh = P.eps[o] - h;
     const R s = P.z2[o];
     // the non-origin part of the error scale varies slowly with tau (those

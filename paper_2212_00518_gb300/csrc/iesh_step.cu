@@ -452,39 +452,52 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
     }
 }
 
-// FP32 propagator, register-tiled: thread (row quad rq, column group cg)
-// owns rows 4rq..4rq+3 and CE electrons (2 CE reals) of the CTA's block of
-// G*CE electrons.  Per orbital i it loads W[i][4rq..4rq+3] as one float4
-// (W_ji = -W_ij; W rows padded to a multiple of 4) and 2CE reals of t_k[i]
-// as float4 broadcasts from shared memory, for 8 CE FFMAs.  W reaches shared
-// memory by cp.async in chunks of kCheb32WRows rows, in a ring of
-// kCheb32WRing chunks filled kCheb32WRing - 1 chunks ahead (one barrier per
-// chunk), so the loop reads it at shared-memory latency instead of L2's.  t_k and
-// t_(k-1) live in two shared buffers: t_(k+1) overwrites t_(k-1) in place
-// (each thread rewrites only its own entries), so one barrier per order
-// suffices and neither is held in registers.  Row j of a buffer starts at
-// j W2 + 4 floor(j/4): the 4-float gap after every row quad puts the row
-// quads of consecutive threads 4 banks apart, so the per-thread row
-// accesses of the recurrence are conflict-free float4 accesses.
+// FP32 propagator, register-tiled: thread (row slot rq, column group cg)
+// owns QPT row quads, rows 4q..4q+3 for q = rq + h nqh (h < QPT, nqh =
+// ceil(nq / QPT) for nq row quads), and CE electrons (2 CE reals) of the
+// CTA's block of G*CE electrons.  Per orbital i it loads W[i][4q..4q+3] as
+// one float4 per quad (W_ji = -W_ij; W rows padded to a multiple of 4) and
+// 2CE reals of t_k[i] as float4 broadcasts from shared memory, for
+// 8 CE QPT FFMAs.  The quads of a thread are nqh apart so that, quad by
+// quad, a warp's float4 loads of W are consecutive (conflict-free).  QPT = 2
+// doubles the FFMAs per shared load and per loop instruction; its register
+// tile (64 accumulators and 64 Chebyshev sums per thread) allows one CTA
+// per SM.  W reaches shared memory by cp.async in chunks of kCheb32WRows
+// rows, in a ring of kCheb32WRing chunks filled kCheb32WRing - 1 chunks
+// ahead (one barrier per chunk), so the loop reads it at shared-memory
+// latency instead of L2's.  t_k and t_(k-1) live in two shared buffers:
+// t_(k+1) overwrites t_(k-1) in place (each thread rewrites only its own
+// entries), so one barrier per order suffices and neither is held in
+// registers.  Row j of a buffer starts at j W2 + 4 floor(j/4): the 4-float
+// gap after every row quad puts the row quads of consecutive threads 4
+// banks apart, so the per-thread row accesses of the recurrence are
+// conflict-free float4 accesses.
 __device__ __forceinline__ int cheb32_row(int j, int W2) { return j * W2 + ((j >> 2) << 2); }
 
-template <int CE>
-__global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int G, int64_t t_base)
+template <int CE, int QPT>
+__global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1) k_cheb_f32t(DevState s, double dt, int G, int64_t t_base)
 {
-    constexpr int RQ = 4, NR = 2 * CE, NV = NR / 4;  // NV float4 per row
+    constexpr int RQ = 4 * QPT, NR = 2 * CE, NV = NR / 4;  // NV float4 per row
     extern __shared__ __align__(16) unsigned char cheb32_smem[];
     const int64_t t = traj_of(s, t_base + blockIdx.y);
     if (t < 0 || (s.status[t] & ST_DONE)) return;
     const int N = s.N, Ne = s.Ne, Np = (N + 3) & ~3;
-    const int nq = (N + RQ - 1) / RQ;
+    const int nq = (N + 3) / 4, nqh = (nq + QPT - 1) / QPT;
     const int W2 = NR * G;
     float *buf0 = reinterpret_cast<float *>(cheb32_smem);
     float *buf1 = buf0 + cheb32_row(Np, W2);
-    const int cg = threadIdx.x / nq, rq = threadIdx.x - cg * nq;
+    const int cg = threadIdx.x / nqh, rq = threadIdx.x - cg * nqh;
     const bool act = cg < G;
-    const int j0 = rq * RQ;
+    // quad h of this thread: first row j0(h); its first buffer entry mine(h)
+    // (my columns); W offset wo(h), row 0 for a quad past the matrix (read,
+    // never used)
+    auto j0 = [&](int h) { return 4 * (rq + h * nqh); };
+    auto wo = [&](int h) {
+        if constexpr (QPT == 1) return 4 * rq;  // rq < nqh = nq
+        return rq + h * nqh < nq ? 4 * (rq + h * nqh) : 0;
+    };
+    auto mine = [&](int h) { return cheb32_row(wo(h), W2) + NR * cg; };
     const int e0 = blockIdx.x * (CE * G) + cg * CE;
-    const int mine = cheb32_row(j0, W2) + NR * cg;  // my first row, my columns
     const double *cb = s.cheb + t * kChebStride;
     const double c = cb[0], rho = cb[1];
     const int K = (int)cb[2];
@@ -505,26 +518,28 @@ __global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int
     float Lc[RQ], acc[RQ][NR];
     const float J0 = (float)J[0];
 #pragma unroll
-    for (int r = 0; r < RQ; ++r) {
-        const int j = j0 + r;
-        const bool ok = act && j < N;
-        Lc[r] = ok ? (float)(0.5 * dt * (s.lam_prev[t * N + j] + s.lam[t * N + j]) - c) : 0.f;
-        float v[NR];
+    for (int h = 0; h < QPT; ++h)
 #pragma unroll
-        for (int e = 0; e < CE; ++e) {
-            float2 ce = make_float2(0.f, 0.f);
-            if (ok && e0 + e < Ne) ce = C[(int64_t)(e0 + e) * N + j];
-            v[2 * e] = ce.x;
-            v[2 * e + 1] = ce.y;
-            acc[r][2 * e] = J0 * ce.x;
-            acc[r][2 * e + 1] = J0 * ce.y;  // single products: no contraction possible
-        }
-        if (ok) {
-            float4 *d4 = reinterpret_cast<float4 *>(buf0 + mine + r * W2);
+        for (int r4 = 0; r4 < 4; ++r4) {
+            const int r = 4 * h + r4, j = j0(h) + r4;
+            const bool ok = act && j < N;
+            Lc[r] = ok ? (float)(0.5 * dt * (s.lam_prev[t * N + j] + s.lam[t * N + j]) - c) : 0.f;
+            float v[NR];
 #pragma unroll
-            for (int h = 0; h < NV; ++h) d4[h] = make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+            for (int e = 0; e < CE; ++e) {
+                float2 ce = make_float2(0.f, 0.f);
+                if (ok && e0 + e < Ne) ce = C[(int64_t)(e0 + e) * N + j];
+                v[2 * e] = ce.x;
+                v[2 * e + 1] = ce.y;
+                acc[r][2 * e] = J0 * ce.x;
+                acc[r][2 * e + 1] = J0 * ce.y;  // single products: no contraction possible
+            }
+            if (ok) {
+                float4 *d4 = reinterpret_cast<float4 *>(buf0 + mine(h) + r4 * W2);
+#pragma unroll
+                for (int g = 0; g < NV; ++g) d4[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+            }
         }
-    }
     // W ring: chunk g (rows kCheb32WRows (g % nwc) ..) in slot g % kCheb32WRing,
     // one commit group each
     float *wring = buf1 + cheb32_row(Np, W2);
@@ -562,26 +577,32 @@ __global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int
             if (act) {
                 // row i of the chunk: W at wp + i Np, t_k at tp + i W2 (+ 4 per
                 // row quad); walked by quads with the strides in registers
-                const float *wp = wring + (g % kCheb32WRing) * kCheb32WRows * Np + j0;
+                const float *wp = wring + (g % kCheb32WRing) * kCheb32WRows * Np + wo(0);
+                const int dwo = QPT == 2 ? wo(1) - wo(0) : 0;  // the second quad's W, relative
                 const int i0 = kCheb32WRows * c, rows = min(kCheb32WRows, N - i0);
                 const float *tp = col + cheb32_row(i0, W2);  // i0 is a multiple of 4
                 auto row = [&](const float *wr_p, const float *tr_p) {
-                    const float4 w = *reinterpret_cast<const float4 *>(wr_p);
+                    float4 w[QPT];
+                    w[0] = *reinterpret_cast<const float4 *>(wr_p);
+                    if constexpr (QPT == 2) w[1] = *reinterpret_cast<const float4 *>(wr_p + dwo);
                     const float4 *tr = reinterpret_cast<const float4 *>(tr_p);
                     float tv[NR];
 #pragma unroll
-                    for (int h = 0; h < NV; ++h) {
-                        const float4 a4 = tr[h];
-                        tv[4 * h] = a4.x;
-                        tv[4 * h + 1] = a4.y;
-                        tv[4 * h + 2] = a4.z;
-                        tv[4 * h + 3] = a4.w;
+                    for (int g4 = 0; g4 < NV; ++g4) {
+                        const float4 a4 = tr[g4];
+                        tv[4 * g4] = a4.x;
+                        tv[4 * g4 + 1] = a4.y;
+                        tv[4 * g4 + 2] = a4.z;
+                        tv[4 * g4 + 3] = a4.w;
                     }
-                    const float wr[RQ] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-                    for (int r = 0; r < RQ; ++r)
+                    for (int h = 0; h < QPT; ++h) {
+                        const float wr[4] = {w[h].x, w[h].y, w[h].z, w[h].w};
 #pragma unroll
-                        for (int q = 0; q < NR; ++q) y[r][q] = fmaf(wr[r], tv[q], y[r][q]);
+                        for (int r4 = 0; r4 < 4; ++r4)
+#pragma unroll
+                            for (int q = 0; q < NR; ++q) y[4 * h + r4][q] = fmaf(wr[r4], tv[q], y[4 * h + r4][q]);
+                    }
                 };
                 const int Np2 = 2 * Np, Np3 = 3 * Np, Wd2 = 2 * W2, Wd3 = 3 * W2;
                 int u = 0;
@@ -601,46 +622,50 @@ __global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int
             const int ph = (k + 1) & 3;  // (-i)^(k+1) = (1, 0), (0, -1), (-1, 0), (0, 1)
             const float ca = ph == 0 ? cj : (ph == 2 ? -cj : 0.f), cb = ph == 1 ? -cj : (ph == 3 ? cj : 0.f);
 #pragma unroll
-            for (int r = 0; r < RQ; ++r) {
-                if (j0 + r < N) {
-                    const float4 *o4 = reinterpret_cast<const float4 *>(cur + mine + r * W2);
-                    float4 *d4 = reinterpret_cast<float4 *>(nxt + mine + r * W2);
-                    float own[NR], prv[NR], nw[NR];
+            for (int h = 0; h < QPT; ++h)
 #pragma unroll
-                    for (int h = 0; h < NV; ++h) {
-                        const float4 a4 = o4[h];
-                        own[4 * h] = a4.x;
-                        own[4 * h + 1] = a4.y;
-                        own[4 * h + 2] = a4.z;
-                        own[4 * h + 3] = a4.w;
-                        float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (k > 0) b4 = d4[h];
-                        prv[4 * h] = b4.x;
-                        prv[4 * h + 1] = b4.y;
-                        prv[4 * h + 2] = b4.z;
-                        prv[4 * h + 3] = b4.w;
-                    }
+                for (int r4 = 0; r4 < 4; ++r4) {
+                    const int r = 4 * h + r4;
+                    if (j0(h) + r4 < N) {
+                        const float4 *o4 = reinterpret_cast<const float4 *>(cur + mine(h) + r4 * W2);
+                        float4 *d4 = reinterpret_cast<float4 *>(nxt + mine(h) + r4 * W2);
+                        float own[NR], prv[NR], nw[NR];
 #pragma unroll
-                    for (int e = 0; e < CE; ++e) {
-                        // (X t)_j = ((L_j - c) t_j - i (W t)_j) / rho and (W t)_j = -y
-                        const float xr = fmaf(Lc[r], own[2 * e], -y[r][2 * e + 1]) * inv_rho;
-                        const float xi = fmaf(Lc[r], own[2 * e + 1], y[r][2 * e]) * inv_rho;
-                        float nr = xr, ni = xi;
-                        if (k > 0) {
-                            nr = fmaf(2.f, xr, -prv[2 * e]);
-                            ni = fmaf(2.f, xi, -prv[2 * e + 1]);
+                        for (int g4 = 0; g4 < NV; ++g4) {
+                            const float4 a4 = o4[g4];
+                            own[4 * g4] = a4.x;
+                            own[4 * g4 + 1] = a4.y;
+                            own[4 * g4 + 2] = a4.z;
+                            own[4 * g4 + 3] = a4.w;
+                            float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (k > 0) b4 = d4[g4];
+                            prv[4 * g4] = b4.x;
+                            prv[4 * g4 + 1] = b4.y;
+                            prv[4 * g4 + 2] = b4.z;
+                            prv[4 * g4 + 3] = b4.w;
                         }
-                        float *a = acc[r] + 2 * e;
-                        // acc += cj (-i)^(k+1) n without a branch: (ca, cb) = cj (-i)^(k+1)
-                        a[0] = fmaf(ca, nr, fmaf(-cb, ni, a[0]));
-                        a[1] = fmaf(ca, ni, fmaf(cb, nr, a[1]));
-                        nw[2 * e] = nr;
-                        nw[2 * e + 1] = ni;
-                    }
 #pragma unroll
-                    for (int h = 0; h < NV; ++h) d4[h] = make_float4(nw[4 * h], nw[4 * h + 1], nw[4 * h + 2], nw[4 * h + 3]);
+                        for (int e = 0; e < CE; ++e) {
+                            // (X t)_j = ((L_j - c) t_j - i (W t)_j) / rho and (W t)_j = -y
+                            const float xr = fmaf(Lc[r], own[2 * e], -y[r][2 * e + 1]) * inv_rho;
+                            const float xi = fmaf(Lc[r], own[2 * e + 1], y[r][2 * e]) * inv_rho;
+                            float nr = xr, ni = xi;
+                            if (k > 0) {
+                                nr = fmaf(2.f, xr, -prv[2 * e]);
+                                ni = fmaf(2.f, xi, -prv[2 * e + 1]);
+                            }
+                            float *a = acc[r] + 2 * e;
+                            // acc += cj (-i)^(k+1) n without a branch: (ca, cb) = cj (-i)^(k+1)
+                            a[0] = fmaf(ca, nr, fmaf(-cb, ni, a[0]));
+                            a[1] = fmaf(ca, ni, fmaf(cb, nr, a[1]));
+                            nw[2 * e] = nr;
+                            nw[2 * e + 1] = ni;
+                        }
+#pragma unroll
+                        for (int g4 = 0; g4 < NV; ++g4)
+                            d4[g4] = make_float4(nw[4 * g4], nw[4 * g4 + 1], nw[4 * g4 + 2], nw[4 * g4 + 3]);
+                    }
                 }
-            }
         }
         __syncthreads();
     }
@@ -648,32 +673,42 @@ __global__ void __launch_bounds__(256, 2) k_cheb_f32t(DevState s, double dt, int
     if (act) {
         const float sc = s_sc[1], cc = s_sc[2];
 #pragma unroll
-        for (int r = 0; r < RQ; ++r) {
-            const int j = j0 + r;
+        for (int h = 0; h < QPT; ++h)
 #pragma unroll
-            for (int e = 0; e < CE; ++e)
-                if (j < N && e0 + e < Ne) {
-                    const float ar = acc[r][2 * e], ai = acc[r][2 * e + 1];
-                    C[(int64_t)(e0 + e) * N + j] = make_float2(fmaf(cc, ar, sc * ai), fmaf(cc, ai, -(sc * ar)));
-                }
-        }
+            for (int r4 = 0; r4 < 4; ++r4) {
+                const int r = 4 * h + r4, j = j0(h) + r4;
+#pragma unroll
+                for (int e = 0; e < CE; ++e)
+                    if (j < N && e0 + e < Ne) {
+                        const float ar = acc[r][2 * e], ai = acc[r][2 * e + 1];
+                        C[(int64_t)(e0 + e) * N + j] = make_float2(fmaf(cc, ar, sc * ai), fmaf(cc, ai, -(sc * ar)));
+                    }
+            }
     }
 }
 
-// Column groups of k_cheb_f32t: fill the CTA (row quads x groups <= 256)
-// and waste few electron slots; two CTAs must fit in an SM's shared memory.
+// Column groups of k_cheb_f32t: fill the CTA (row slots x groups <= 256)
+// and waste few electron slots; with one row quad per thread two CTAs must
+// fit in an SM's shared memory, with two quads one.
 size_t cheb32_smem_bytes(int N, int G)
 {
     const int Np = (N + 3) & ~3;
     // two buffers of padded rows and the ring of W chunks
     return ((size_t)2 * (Np * 8 * G + Np) + (size_t)kCheb32WRing * kCheb32WRows * Np) * sizeof(float);
 }
-void cheb32_shape(int N, int Ne, int &G)
+bool cheb32_shape_ok(int N, int G, int qpt)
 {
-    const int nq = (N + 3) / 4;
+    const int nqh = ((N + 3) / 4 + qpt - 1) / qpt;
+    return (qpt == 1 || qpt == 2) && G >= 1 && G * nqh <= 256 &&
+           cheb32_smem_bytes(N, G) <= (qpt == 1 ? kCheb32MaxSmem : kCheb32WideMaxSmem);
+}
+void cheb32_shape(int N, int Ne, int &G, int qpt)
+{
+    const int nq = ((N + 3) / 4 + qpt - 1) / qpt;
     double best = -1.0;
     G = 1;
-    for (int g = 1; g * nq <= 256 && (g == 1 || cheb32_smem_bytes(N, g) <= kCheb32MaxSmem); ++g) {
+    for (int g = 1; g == 1 || cheb32_shape_ok(N, g, qpt); ++g) {
+        if (g * nq > 256) break;
         const int nb = 4 * g, thr = g * nq, thr32 = (thr + 31) & ~31;
         const int blocks = (Ne + nb - 1) / nb;
         const double eff = (double)thr / thr32 * (double)Ne / (blocks * nb) + 1e-4 * g;
@@ -1269,16 +1304,22 @@ cudaError_t launch_cheb(const DevState &s, double dt, bool mixed, cudaStream_t s
         // tensor cores (3xTF32) when the trajectory fits one CTA, unless a
         // SIMT shape was requested
         if (s.cheb_ept == 8 || (s.cheb_ept == 0 && cheb_tc_eligible(s.N, s.Ne))) return launch_cheb_tc(s, dt, st);
+        // SIMT: one row quad per thread (cheb_ept 4) or two (cheb_ept 32); by
+        // default two past N = 224, where its one CTA per SM measured faster
+        // (N = 256: 24.5 against 29.9 ms per step at 4096 trajectories; at
+        // N = 201 it measured 29.4 against 26.2 ms)
+        const int qpt = s.cheb_ept == 32 || (s.cheb_ept == 0 && s.N > kCheb32WideMinN) ? 2 : 1;
         int G;
-        cheb32_shape(s.N, s.Ne, G);
-        if (s.cheb_G > 0 && s.cheb_ept == 4) G = s.cheb_G;
-        const int nb = 4 * G, nq = (s.N + 3) / 4;
+        cheb32_shape(s.N, s.Ne, G, qpt);
+        if (s.cheb_G > 0 && (s.cheb_ept == 4 || s.cheb_ept == 32)) G = s.cheb_G;
+        const int nb = 4 * G, nqh = ((s.N + 3) / 4 + qpt - 1) / qpt;
         const size_t smem = cheb32_smem_bytes(s.N, G);
-        const int threads = (G * nq + 31) & ~31;
+        const int threads = (G * nqh + 31) & ~31;
         for (int64_t t0 = 0; t0 < s.n; t0 += 65535) {
             const int64_t cnt = (s.n - t0 < 65535) ? s.n - t0 : 65535;
             dim3 grid((unsigned)((s.Ne + nb - 1) / nb), (unsigned)cnt);
-            k_cheb_f32t<4><<<grid, threads, smem, st>>>(s, dt, G, t0);
+            if (qpt == 2) k_cheb_f32t<4, 2><<<grid, threads, smem, st>>>(s, dt, G, t0);
+            else k_cheb_f32t<4, 1><<<grid, threads, smem, st>>>(s, dt, G, t0);
             const cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }
@@ -1330,7 +1371,8 @@ void configure_hop_smem()
     allow_max_smem(k_hop<double2, 256, 3, true>);
     allow_max_smem(k_hop<float2, 512, 1, true>);
     allow_max_smem(k_hop<float2, 256, 4, true>);
-    allow_max_smem(k_cheb_f32t<4>);
+    allow_max_smem(k_cheb_f32t<4, 1>);
+    allow_max_smem(k_cheb_f32t<4, 2>);
     configure_hop_gjl();
 }
 

@@ -71,6 +71,11 @@ struct Model2Dev {
     // bath profile), pnorm[a] = |prof[a]|
     const double *prof;
     double pnorm[2];
+    // nested secular path: the step-1 roots of every trajectory [n][M + 1],
+    // kept for the next step's warm start; prof_0k prof_1k as double-float
+    // pairs (mixed path)
+    double *mu;
+    const float2 *ppdf;
 };
 
 // Adsorbate quantities at one geometry: levels h_a, coupling amplitudes c_a
@@ -688,13 +693,13 @@ __host__ __device__ inline bool dense_in_smem(int N)
     return (size_t)N * dense_lda(N) * 8 + (size_t)(6 * N + 8) * 8 <= kDenseSmemCap;
 }
 
-__global__ void __launch_bounds__(256) k2g_reduce(DevState s, Model2Dev md, double dt, int mode)
+// Mode 1: the step's previous eigenpairs are kept, then the first kick and
+// the drift; xs receives the geometry at which the eigenpairs are wanted.
+// Block-wide; ends with a barrier.
+__device__ __forceinline__ void kick_drift2(const DevState &s, const Model2Dev &md, int64_t t, double dt,
+                                            int mode, double *xs)
 {
-    extern __shared__ __align__(16) double g2_sh[];
-    __shared__ double xs[6];
-    const int64_t t = traj_of(s, blockIdx.x);
-    if (t < 0 || (s.status[t] & ST_DONE)) return;
-    const int N = s.N, M = s.M, lda = dense_lda(N), tid = threadIdx.x;
+    const int N = s.N, tid = threadIdx.x;
     if (mode == 1)
         for (int i = tid; i < N; i += blockDim.x) {
             s.lam_prev[t * N + i] = s.lam[t * N + i];
@@ -714,6 +719,16 @@ __global__ void __launch_bounds__(256) k2g_reduce(DevState s, Model2Dev md, doub
         xs[tid] = x;
     }
     __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k2g_reduce(DevState s, Model2Dev md, double dt, int mode)
+{
+    extern __shared__ __align__(16) double g2_sh[];
+    __shared__ double xs[6];
+    const int64_t t = traj_of(s, blockIdx.x);
+    if (t < 0 || (s.status[t] & ST_DONE)) return;
+    const int N = s.N, M = s.M, lda = dense_lda(N), tid = threadIdx.x;
+    kick_drift2(s, md, t, dt, mode, xs);
     const Ads2 ad = ads2_eval(md, xs);
     double *v = g2_sh, *w = v + N, *r1 = w + N, *d = r1 + N, *e = d + N, *tau = e + N, *sh = tau + N;
     double *out = s.scratch + t * s.scratch_stride;  // d, e, Y
@@ -837,6 +852,188 @@ __global__ void __launch_bounds__(256) k2g_finish(DevState s, Model2Dev md, doub
     if (tid == 0) write_geo2(s, t, md, ad, ps);
 }
 
+// ------------------------------------------------ nested secular path
+// The same eigenpairs without the O(N^3) reduction: H is diag(h_0, h_1,
+// eps) bordered by V_0k = c_0 prof_0k and V_1k = c_1 prof_1k, and a
+// similarity by the eigenvectors of one bordered block leaves another
+// arrowhead (two nested secular equations, one root per thread each).
+//   Step 1: orbital 1 with the bath, poles eps_k and weights V_1k^2: M + 1
+//     roots mu_j; eigenvector w_j has orbital-1 component s_j = 1 /
+//     sqrt(f_1'(mu_j)) and bath components V_1k s_j / (mu_j - eps_k).
+//   Step 2: in the basis {|0>, w_j}, H is diag(h_0, mu) bordered by c_j =
+//     <0|H|w_j> = s_j sum_k V_0k V_1k / (mu_j - eps_k); its N = M + 2 roots
+//     are the eigenvalues of H, the border component q_i = 1 / sqrt(f_2'(
+//     lam_i)) is Q_0i, and Q_1i = sum_j <1|w_j><w_j|i> = q_i sum_j s_j c_j /
+//     (lam_i - mu_j).
+// Every difference between a root and a pole is formed about the root's
+// origin pole (pole difference + offset) and keeps its relative accuracy;
+// the step-2 pole differences mu_o - mu_k are differences of computed
+// roots, which perturbs the step-2 arrowhead at the rounding level of its
+// entries.  The eigenpairs go to the trajectory's scratch in the dense
+// path's layout (lam[N], then Q_0i, Q_1i pairs from 2N), ascending, for
+// k2g_finish (gauge, forces, second kick).
+// Mode 1 starts both root searches from the previous step's roots (warm
+// start, as the one-orbital kernel): the step-1 roots kept in md.mu and the
+// eigenvalues.  DF (mixed path): the step-1 sums over the bath poles in
+// double-float from the pole-difference table, as k_eigen<true>.
+// (Without a register budget the compiler settles on 80 registers and
+// spills; 128 keeps everything in registers with two 256-thread CTAs per SM.)
+template <bool DF>
+__global__ void __maxnreg__(128) k2n_eigen(DevState s, Model2Dev md, double dt, int mode)
+{
+    extern __shared__ __align__(16) double n2_sh[];
+    __shared__ double xs[6], red[32];
+    const int64_t t = traj_of(s, blockIdx.x);
+    if (t < 0 || (s.status[t] & ST_DONE)) return;
+    const int N = s.N, M = s.M, M1 = M + 1, tid = threadIdx.x;
+    const bool warm = mode == 1;
+    // previous roots, read before kick_drift2 moves lam to lam_prev (it
+    // leaves lam itself alone)
+    const double g1 = (warm && tid < M1) ? md.mu[t * M1 + tid] : 0.0;
+    const double g2 = (warm && tid < N) ? s.lam[t * N + tid] : 0.0;
+    kick_drift2(s, md, t, dt, mode, xs);
+    const Ads2 ad = ads2_eval(md, xs);
+    double *eps_s = n2_sh, *z2 = eps_s + M, *mu = z2 + M, *sv = mu + M1, *c2 = sv + M1, *cs = c2 + M1,
+           *tau1 = cs + M1;
+    int *o1 = reinterpret_cast<int *>(tau1 + M1);
+    float2 *z2df = reinterpret_cast<float2 *>(tau1 + 2 * M1);  // [M] (DF)
+    // DF: tau1, c_j^2 and s_j c_j as double-float pairs for the step-2 sums
+    float2 *t1df = z2df + M, *c2df = t1df + M1, *csdf = c2df + M1;
+    double z1 = 0.0;
+    for (int k = tid; k < M; k += blockDim.x) {
+        eps_s[k] = s.eps[k];
+        const double v1 = ad.c[1] * md.prof[M + k];
+        z2[k] = v1 * v1;
+        if (DF) {
+            const dfl zd = dfl_from(v1 * v1);
+            z2df[k] = make_float2(zd.hi, zd.lo);
+        }
+        z1 += v1 * v1;
+    }
+    const double Z1 = block_sum(z1, red);  // ends with a barrier: eps_s, z2 complete
+    uint32_t st = 0;
+    // step 1: orbital 1 and the bath
+    if (tid < M1) {
+        double l, q, tau = 0.0;
+        int o = 0;
+        if (Z1 > 0.0) {
+            if (DF) {
+                const Poles<double> pp = {M, eps_s, z2, nullptr, s.poledf, z2df, 0, -1, 0.0, nullptr};
+                secular_root<double, EV_DFLOAT>(tid, pp, ad.h[1], Z1, warm, g1, l, q, st, &o, &tau);
+            } else {
+                const Poles<double> pp = {M, eps_s, z2, nullptr, nullptr, nullptr, 0, -1, 0.0, nullptr};
+                secular_root<double, EV_PLAIN>(tid, pp, ad.h[1], Z1, warm, g1, l, q, st, &o, &tau);
+            }
+        } else {
+            // orbital 1 uncoupled: the roots are h_1 (s = 1) and the bath energies
+            int pos = 0;
+            for (int k = 0; k < M; ++k) pos += (eps_s[k] < ad.h[1]);
+            l = tid < pos ? eps_s[tid] : (tid == pos ? ad.h[1] : eps_s[tid - 1]);
+            q = tid == pos ? 1.0 : 0.0;
+            o = tid < pos ? tid : (tid == pos ? -1 : tid - 1);  // bath root: its pole
+        }
+        mu[tid] = l;
+        sv[tid] = q;
+        o1[tid] = o;
+        tau1[tid] = tau;
+        if (DF) {
+            const dfl td = dfl_from(tau);
+            t1df[tid] = make_float2(td.hi, td.lo);
+        }
+        md.mu[t * M1 + tid] = l;
+    }
+    __syncthreads();
+    // couplings of orbital 0 to the step-1 eigenvectors
+    double zc = 0.0;
+    if (tid < M1) {
+        const int o = o1[tid];
+        double cj;
+        if (Z1 > 0.0) {
+            const double tau = tau1[tid];
+            double gs = 0.0;
+            if (DF) {
+                // sum_k prof_0k prof_1k / ((eps_o - eps_k) + tau) in double-float
+                const dfl td = dfl_from(tau);
+                dfl a[2] = {{0.f, 0.f}, {0.f, 0.f}};
+                auto term = [&](int k, int h) {
+                    const float2 dk = s.poledf[(size_t)k * M + o], pk = md.ppdf[k];
+                    const dfl r = dfl_rcp(dfl_add({dk.x, dk.y}, td));
+                    a[h] = dfl_add(a[h], dfl_mul({pk.x, pk.y}, r));
+                };
+                int k = 0;
+                for (; k + 1 < M; k += 2) {
+                    term(k, 0);
+                    term(k + 1, 1);
+                }
+                if (k < M) term(k, 0);
+                gs = dfl_value(dfl_add(a[0], a[1]));
+            } else {
+                const double eo = eps_s[o];
+                for (int k = 0; k < M; ++k)
+                    gs += md.prof[k] * md.prof[M + k] * pole_recip<double>((eo - eps_s[k]) + tau);
+            }
+            cj = ad.c[0] * ad.c[1] * sv[tid] * gs;
+        } else {
+            cj = o >= 0 ? ad.c[0] * md.prof[o] : 0.0;  // w_j is bath state o, or orbital 1
+        }
+        c2[tid] = cj * cj;
+        cs[tid] = cj * sv[tid];
+        if (DF) {
+            const dfl a = dfl_from(cj * cj), b = dfl_from(cj * sv[tid]);
+            c2df[tid] = make_float2(a.hi, a.lo);
+            csdf[tid] = make_float2(b.hi, b.lo);
+        }
+        zc = cj * cj;
+    }
+    const double Z2 = block_sum(zc, red);  // ends with a barrier: mu, c2, cs complete
+    // step 2: orbital 0 against the step-1 eigenvectors
+    if (tid < N) {
+        double l, q0, q1 = 0.0, tau = 0.0;
+        int o = 0;
+        if (Z2 > 0.0 && DF && Z1 > 0.0) {
+            // the step-1 roots carry their bath pole: double-float sums
+            const Poles<double> pp = {M1, mu, c2, nullptr, s.poledf, c2df, M, -1, 0.0, t1df, o1};
+            secular_root<double, EV_NESTED>(tid, pp, ad.h[0], Z2, warm, g2, l, q0, st, &o, &tau);
+            const dfl td = dfl_from(tau);
+            dfl a[2] = {{0.f, 0.f}, {0.f, 0.f}};
+            auto term = [&](int j, int h) {
+                if (j == o) return;
+                const dfl r = dfl_rcp(nested_gap(pp, o, j, td));
+                const float2 cj = csdf[j];
+                a[h] = dfl_add(a[h], dfl_mul({cj.x, cj.y}, r));
+            };
+            int j = 0;
+            for (; j + 1 < M1; j += 2) {
+                term(j, 0);
+                term(j + 1, 1);
+            }
+            if (j < M1) term(j, 0);
+            q1 = q0 * (dfl_value(dfl_add(a[0], a[1])) + cs[o] / tau);
+        } else if (Z2 > 0.0) {
+            const Poles<double> pp = {M1, mu, c2, nullptr, nullptr, nullptr, 0, -1, 0.0, nullptr};
+            secular_root<double, EV_PLAIN>(tid, pp, ad.h[0], Z2, warm, g2, l, q0, st, &o, &tau);
+            const double mo = mu[o];
+            double ss = 0.0;
+            for (int j = 0; j < M1; ++j) ss += cs[j] * pole_recip<double>((mo - mu[j]) + tau);
+            q1 = q0 * ss;
+        } else {
+            // orbital 0 uncoupled: the roots are h_0 (Q_0 = 1) and the mu_j (Q_1 = s_j)
+            int pos = 0;
+            for (int j = 0; j < M1; ++j) pos += (mu[j] < ad.h[0]);
+            l = tid < pos ? mu[tid] : (tid == pos ? ad.h[0] : mu[tid - 1]);
+            q0 = tid == pos ? 1.0 : 0.0;
+            q1 = tid < pos ? sv[tid] : (tid == pos ? 0.0 : sv[tid - 1]);
+        }
+        double *out = s.scratch + t * s.scratch_stride;
+        out[tid] = l;
+        out[2 * N + 2 * tid] = q0;
+        out[2 * N + 2 * tid + 1] = q1;
+    }
+    if (st) atomicOr(&s.status[t], st);
+}
+
+size_t nested_smem(int M) { return (size_t)(3 * M + 9 * (M + 1)) * sizeof(double); }
+
 size_t dense_reduce_smem(int N)
 {
     return (size_t)(6 * N + 8) * sizeof(double) + (dense_in_smem(N) ? (size_t)N * dense_lda(N) * sizeof(double) : 0);
@@ -859,6 +1056,7 @@ struct iesh2_ctx {
     int skip_bound = 0;
     bool mixed = false;
     bool dense = false;  // eigenpairs from the dense symmetric eigensolver
+    bool nested = false; // eigenpairs from two nested secular equations
     int sms = 1;         // SMs of the context's device
     Model2Dev md;
     DevState ds;
@@ -917,6 +1115,15 @@ cudaError_t launch_eigen2(iesh2_ctx *ctx, double dt, int mode)
 {
     const DevState &d = ctx->ds;
     if (d.n == 0) return cudaSuccess;
+    if (ctx->nested) {
+        const int threads = (d.N + 31) & ~31;
+        if (ctx->mixed) k2n_eigen<true><<<(unsigned)d.n, threads, nested_smem(d.M), ctx->stream>>>(d, ctx->md, dt, mode);
+        else k2n_eigen<false><<<(unsigned)d.n, threads, nested_smem(d.M), ctx->stream>>>(d, ctx->md, dt, mode);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k2g_finish<<<(unsigned)d.n, 256, (size_t)6 * d.N * sizeof(double), ctx->stream>>>(d, ctx->md, dt, mode);
+        return cudaGetLastError();
+    }
     if (ctx->dense) {
         k2g_reduce<<<(unsigned)d.n, 256, dense_reduce_smem(d.N), ctx->stream>>>(d, ctx->md, dt, mode);
         cudaError_t e = cudaGetLastError();
@@ -1007,7 +1214,8 @@ iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int precisio
     if (model->eigensolver != 0 && model->eigensolver != 1)
         return fail2(ctx, IESH_EINVAL, "unknown eigensolver %d", model->eigensolver);
     ctx->mixed = precision == IESH_PREC_MIXED;
-    ctx->dense = model->profile == 1 || model->eigensolver == 1;
+    ctx->dense = model->eigensolver == 1;
+    ctx->nested = model->profile == 1 && model->eigensolver == 0;
     {
         int dev = 0, sms = 0;
         CU2(cudaGetDevice(&dev));
@@ -1061,6 +1269,10 @@ iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int precisio
     A2(d.status, T) A2(d.nstep, T) A2(d.hops, T) A2(d.frus, T)
     A2(d.scratch, T * (size_t)d.scratch_stride)
     A2(d.cheb, T * kChebStride)
+    double *mu_d = nullptr;
+    float2 *ppdf_d = nullptr;
+    if (ctx->nested) A2(mu_d, T * (size_t)(M + 1))
+    if (ctx->nested && ctx->mixed) A2(ppdf_d, (size_t)M)
     A2(eps_d, (size_t)M) A2(sq_d, (size_t)M) A2(prof_d, (size_t)2 * M)
     float2 *poledf = nullptr;
     if (ctx->mixed) A2(poledf, (size_t)M * M)
@@ -1096,6 +1308,8 @@ iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int precisio
         k.pnorm[a] = std::sqrt(nrm);
     }
     k.prof = prof_d;
+    k.mu = mu_d;
+    k.ppdf = ppdf_d;
     CU2(cudaMemcpyAsync(prof_d, prof.data(), prof.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     if (ctx->dense && dense_reduce_smem(N) > 48 * 1024) {
         // process-wide attribute: only ever raised
@@ -1116,6 +1330,17 @@ iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int precisio
                 pf[(size_t)kk * M + o] = make_float2(hi, (float)(v - (double)hi));
             }
         CU2(cudaMemcpyAsync(poledf, pf.data(), pf.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    std::vector<float2> ppf;
+    if (ppdf_d) {
+        // prof_0k prof_1k as double-float pairs (the nested path's couplings)
+        ppf.resize((size_t)M);
+        for (int kk = 0; kk < M; ++kk) {
+            const double v = prof[kk] * prof[(size_t)M + kk];
+            const float hi = (float)v;
+            ppf[kk] = make_float2(hi, (float)(v - (double)hi));
+        }
+        CU2(cudaMemcpyAsync(ppdf_d, ppf.data(), ppf.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->stream));
     }
     CU2(cudaStreamSynchronize(ctx->stream));
     return IESH_OK;

@@ -27,20 +27,24 @@ def cheb_candidates(N, Ne, limit=6, precision=0):
     threads.  Mixed precision: (4, G), 4 orbitals x 4 electrons per thread
     and G * ceil(N / 4) <= 256 threads, two buffers of Np x (8G + 1) floats
     (Np = N rounded up to a multiple of 4) and a ring of 3 x 16 rows of W
-    (48 Np floats) in at most 110 KiB."""
+    (48 Np floats) in at most 110 KiB; or (32, G), 8 orbitals x 4
+    electrons per thread, G * ceil(ceil(N / 4) / 2) <= 256 threads, the same
+    buffers in at most 220 KiB."""
     out = []
     if precision == _I.PREC_MIXED:
         nq = -(-N // 4)
         Np = 4 * nq
-        for G in range(1, 256 // nq + 1):
-            if G > 1 and (2 * (Np * 8 * G + Np) + 48 * Np) * 4 > 110 * 1024:
-                break
-            nb = 4 * G
-            if nb > 4 * Ne + 3:
-                break
-            thr32 = (G * nq + 31) // 32 * 32
-            eff = G * nq / thr32 * Ne / (-(-Ne // nb) * nb)
-            out.append((eff, nb, 4, G))
+        # (4, G): one row quad per thread, 110 KiB; (32, G): two, 220 KiB
+        for ept, nqh, cap in ((4, nq, 110), (32, -(-nq // 2), 220)):
+            for G in range(1, 256 // nqh + 1):
+                if G > 1 and (2 * (Np * 8 * G + Np) + 48 * Np) * 4 > cap * 1024:
+                    break
+                nb = 4 * G
+                if nb > 4 * Ne + 3:
+                    break
+                thr32 = (G * nqh + 31) // 32 * 32
+                eff = G * nqh / thr32 * Ne / (-(-Ne // nb) * nb)
+                out.append((eff, nb, ept, G))
         out.sort(key=lambda r: (-r[0], -r[1]))
         return [(ept, G) for _, _, ept, G in out[:limit]]
     for ept in (2, 1):

@@ -115,8 +115,9 @@ def test_tuner_shapes_within_documented_limits(N):
     """The autotuner proposes only propagator shapes that iesh_set_kernel_shape
     accepts by its documented limits: mixed (4, G) with G * ceil(N/4) <= 256
     threads and 8 Np (8G + 1) + 192 Np bytes of shared memory (two buffers
-    and the ring of W rows) within 110 KiB for G > 1; FP64 (ept, G) with
-    ept in {1, 2} and G * N <= 1024."""
+    and the ring of W rows) within 110 KiB for G > 1, or (32, G) with
+    G * ceil(ceil(N/4)/2) <= 256 and the same bytes within 220 KiB; FP64
+    (ept, G) with ept in {1, 2} and G * N <= 1024."""
     from paper_2212_00518_gb300 import tuning
     from paper_2212_00518_gb300 import iesh as I
     Np = -(-N // 4) * 4
@@ -124,9 +125,11 @@ def test_tuner_shapes_within_documented_limits(N):
         if Ne < 1:
             continue
         mixed = tuning.cheb_candidates(N, Ne, precision=I.PREC_MIXED)
-        assert mixed and all(ept == 4 for ept, _ in mixed)
-        for _, G in mixed:
-            assert G * -(-N // 4) <= 256
-            assert G == 1 or 8 * Np * (8 * G + 1) + 192 * Np <= 110 * 1024
+        assert mixed and all(ept in (4, 32) for ept, _ in mixed)
+        for ept, G in mixed:
+            nq = -(-N // 4)
+            rows, cap = (nq, 110) if ept == 4 else (-(-nq // 2), 220)
+            assert G * rows <= 256
+            assert G == 1 or 8 * Np * (8 * G + 1) + 192 * Np <= cap * 1024
         fp64 = tuning.cheb_candidates(N, Ne, precision=I.PREC_FP64)
         assert fp64 and all(ept in (1, 2) and G * N <= 1024 for ept, G in fp64)

@@ -1,7 +1,8 @@
 """GPU parity of the batched dense symmetric eigensolver (iesh_syev_batched)
 and of the two-orbital dynamics whose orbitals couple to the bath with their
 own profiles (non-parallel border vectors, reading R17), which take their
-eigenpairs from it.
+eigenpairs from two nested secular equations by default or from the dense
+solver; both are checked against the oracle's dense Jacobi.
 
 Tolerances follow from the method's backward error: Householder reduction
 and QL rotations give the eigenpairs of A + E with |E| <= c n u |A| (u the
@@ -131,9 +132,19 @@ def _ctx(P, md, x, p, occ, C, **kw):
     return ctx
 
 
+SOLVERS = ("nested", "dense")
+
+
+def _solver(md, solver):
+    """The model with the dense solver forced, or as is (the nested secular
+    equations are the default for own profiles)."""
+    return dict(md, eigensolver="dense") if solver == "dense" else md
+
+
+@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("name", list(CASES))
-def test_profiled_eigenpairs_and_forces(P, name):
-    md = CASES[name]
+def test_profiled_eigenpairs_and_forces(P, name, solver):
+    md = _solver(CASES[name], solver)
     n = 3
     x, p, occ, C = W.two_orbital_state(md, n, 11)
     ctx = _ctx(P, md, x, p, occ, C)
@@ -146,9 +157,10 @@ def test_profiled_eigenpairs_and_forces(P, name):
         assert np.abs(F[t] - rF).max() <= 1e-9 * max(1.0, np.abs(rF).max())
 
 
+@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("name", ["M20", "M100", "strong", "M200"])
-def test_profiled_one_step(P, name):
-    md = CASES[name]
+def test_profiled_one_step(P, name, solver):
+    md = _solver(CASES[name], solver)
     n, dt = 4, 5.0
     x, p, occ, C = W.two_orbital_state(md, n, 17, weight=0.6)
     ctx = _ctx(P, md, x, p, occ, C)
@@ -165,8 +177,9 @@ def test_profiled_one_step(P, name):
         assert np.abs(Q[t] - ref["Qad"][t]).max() <= 1e-10
 
 
-def test_profiled_100_steps_with_hops(P):
-    md = W.two_orbital_profiled(16, seed=7, vscale=3.0)
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_profiled_100_steps_with_hops(P, solver):
+    md = _solver(W.two_orbital_profiled(16, seed=7, vscale=3.0), solver)
     n, steps, dt = 8, 100, 5.0
     x, p, occ, C = W.two_orbital_state(md, n, 19, kT=0.01, weight=1.0)
     ctx = _ctx(P, md, x, p, occ, C)
@@ -201,11 +214,13 @@ def test_dense_path_equals_secular_path_on_parallel_couplings(P):
     assert np.abs(sa["C"] - sb["C"]).max() <= 1e-8
 
 
+@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("name", ["M20", "strong", "M100"])
-def test_profiled_mixed_one_step(P, name):
-    """Mixed precision with the dense FP64 eigensolver: the one-coordinate
-    mixed bounds (C within 1e-6 after one step)."""
-    md = CASES[name]
+def test_profiled_mixed_one_step(P, name, solver):
+    """Mixed precision with FP64 eigenpairs (nested secular equations or the
+    dense solver): the one-coordinate mixed bounds (C within 1e-6 after one
+    step)."""
+    md = _solver(CASES[name], solver)
     n, dt = 4, 5.0
     x, p, occ, C = W.two_orbital_state(md, n, 17, weight=0.6)
     C32 = C.astype(np.complex64)
@@ -217,3 +232,20 @@ def test_profiled_mixed_one_step(P, name):
     assert np.array_equal(st["occ"], ref["occ"])
     assert np.abs(st["x"] - ref["x"]).max() <= 1e-12 * (1 + np.abs(ref["x"]).max())
     assert np.abs(np.transpose(st["C"], (0, 2, 1)) - ref["C"]).max() <= 1e-6
+
+
+@pytest.mark.parametrize("name", ["M20", "M100", "M254"])
+def test_nested_secular_equals_dense_solver(P, name):
+    """The two eigensolvers of the own-profile model give the same ordered
+    eigenvalues (1e-12) and gauge-fixed adsorbate rows (1e-10) on many
+    geometries."""
+    md = CASES[name]
+    n = 24
+    x, p, occ, C = W.two_orbital_state(md, n, 29)
+    a = _ctx(P, md, x, p, occ, C)
+    b = _ctx(P, _solver(md, "dense"), x, p, occ, C)
+    la, Qa, Fa = a.eigen()
+    lb, Qb, Fb = b.eigen()
+    assert np.abs(la - lb).max() <= 1e-12
+    assert np.abs(Qa - Qb).max() <= 1e-10
+    assert np.abs(Fa - Fb).max() <= 1e-9 * max(1.0, np.abs(Fb).max())

@@ -97,7 +97,7 @@ def test_mixed_large_and_ragged_shapes(P, M, Ne, n):
     C = W.mixed_coefficients(occ, N, 23, 0.6)
     B = O.bind(md)
     ctx = P.Context(md, n, precision=P.PREC_MIXED)
-    assert ctx.kernel_shape()[0] == 4
+    assert ctx.kernel_shape()[0] == (32 if N > 224 else 4)
     ctx.set_state(x, p, occ, C.astype(np.complex64))
     g_gj = ctx.hop_probabilities(1.0)
     ctx.set_kernel_shape(0, 0, 512)
@@ -229,3 +229,47 @@ def test_mixed_two_lead_eigenpairs(P):
         lo, Qo = O.eigen(B, x[t])[:2]
         assert np.abs(lam[t] - lo).max() <= 1e-12 * np.abs(lo).max()
         assert np.abs(q0[t] - Qo[0]).max() <= 1e-11
+
+
+@pytest.mark.parametrize("M,Ne,n", [(200, 100, 6), (255, 112, 3), (128, 1, 5), (160, 80, 4), (200, 33, 4)])
+def test_mixed_two_quad_propagator_identical(P, M, Ne, n):
+    """The SIMT propagator with two row quads per thread (shape 32) computes
+    every entry with the same FP32 operations in the same order as the
+    one-quad kernel (shape 4), so one step gives bit-identical states; and
+    both agree with the oracle at the mixed bounds."""
+    md = W.double_well(M, Ne)
+    N = M + 1
+    x, p = W.thermal_harmonic(n, md["mass"], md["par"][0], 0.01, 31)
+    occ = W.random_occupations(n, N, Ne, 32)
+    C = W.mixed_coefficients(occ, N, 33, 0.6).astype(np.complex64)
+    out = {}
+    for ept in (4, 32):
+        ctx = P.Context(md, n, precision=P.PREC_MIXED)
+        ctx.set_state(x, p, occ, C)
+        ctx.set_kernel_shape(ept, 1, 0)
+        ctx.run(1.0, 2, seed=6)
+        out[(ept, 1)] = ctx.get_state()
+        ctx.close()
+    ctx = P.Context(md, n, precision=P.PREC_MIXED)
+    ctx.set_state(x, p, occ, C)
+    ctx.set_kernel_shape(32, 3, 0)
+    ctx.run(1.0, 2, seed=6)
+    out[(32, 3)] = ctx.get_state()
+    ctx.close()
+    a = out[(4, 1)]
+    for key in ((32, 1), (32, 3)):
+        b = out[key]
+        assert np.array_equal(a["C"], b["C"]), key
+        assert np.array_equal(a["occ"], b["occ"]) and np.array_equal(a["x"], b["x"]), key
+    B = O.bind(md)
+    ctx = P.Context(md, n, precision=P.PREC_MIXED)
+    ctx.set_state(x, p, occ, C)
+    ctx.set_kernel_shape(32, 2, 0)
+    ctx.run(1.0, 1, seed=4)
+    st = ctx.get_state()
+    ctx.close()
+    for t in range(n):
+        r = O.step_one(B, x[t], p[t], occ[t].astype(np.int32), C[t].T.astype(np.complex128), 1.0, seed=4,
+                       traj=t, n=0)
+        assert np.array_equal(st["occ"][t], r["occ"])
+        assert np.abs(st["C"][t].T - r["C"]).max() <= 1e-6
