@@ -134,6 +134,43 @@ __device__ __forceinline__ void write_geo2(const DevState &s, int64_t t, const M
     g[5] = kv[1];
 }
 
+// Adsorbate quantities at x formed once per CTA by thread 0 and shared
+// (an FP64 instruction costs a warp its issue slot on the FP64 pipe whatever
+// its active lanes, so every thread evaluating the same exponentials would
+// cost every warp that much).  Block-wide; ends with a barrier; x must be
+// readable by thread 0.
+__device__ __forceinline__ Ads2 ads2_block(const Model2Dev &md, const double *x, Ads2 *sh)
+{
+    if (threadIdx.x == 0) *sh = ads2_eval(md, x);
+    __syncthreads();
+    return *sh;
+}
+
+// Both ends of a step: adsorbate quantities at x_prev and x, and the
+// velocity projections with v_prev and p / mass; formed once per CTA as
+// ads2_block.
+struct Ends2 {
+    Ads2 e0, e1;
+    double hv0[2], kv0[2], hv1[2], kv1[2];
+};
+__device__ __forceinline__ void ends2_block(const DevState &s, const Model2Dev &md, int64_t t, Ends2 *sh)
+{
+    if (threadIdx.x == 0) {
+        double x0[6], v0[6], x1[6], v1[6];
+        for (int y = 0; y < 6; ++y) {
+            x0[y] = s.x_prev[t * 6 + y];
+            v0[y] = s.vprev[t * 6 + y];
+            x1[y] = s.x[t * 6 + y];
+            v1[y] = s.p[t * 6 + y] / md.mass;
+        }
+        sh->e0 = ads2_eval(md, x0);
+        sh->e1 = ads2_eval(md, x1);
+        ads2_project(md, sh->e0, v0, sh->hv0, sh->kv0);
+        ads2_project(md, sh->e1, v1, sh->hv1, sh->kv1);
+    }
+    __syncthreads();
+}
+
 // Force component y on the occupied surface from the occupied sums
 // S_a = sum Q_aj^2 and U_a = sum Q_aj^2 (lam_j - h_a).
 __device__ __forceinline__ double force2(const Model2Dev &md, const Ads2 &ad, const double *x, int y,
@@ -458,17 +495,11 @@ __global__ void __launch_bounds__(256) k2_build_w(DevState s, Model2Dev md, doub
         a1[i] = s.q0[t * N + i];
         b1[i] = s.q2[t * N + i];
     }
-    double x0[6], v0[6], x1[6], v1[6];
-    for (int y = 0; y < 6; ++y) {
-        x0[y] = s.x_prev[t * 6 + y];
-        v0[y] = s.vprev[t * 6 + y];
-        x1[y] = s.x[t * 6 + y];
-        v1[y] = s.p[t * 6 + y] / md.mass;
-    }
-    const Ads2 e0 = ads2_eval(md, x0), e1 = ads2_eval(md, x1);
-    double hv0[2], kv0[2], hv1[2], kv1[2];
-    ads2_project(md, e0, v0, hv0, kv0);
-    ads2_project(md, e1, v1, hv1, kv1);
+    __shared__ Ends2 ends;
+    ends2_block(s, md, t, &ends);
+    const Ads2 e0 = ends.e0, e1 = ends.e1;
+    const double hv0[2] = {ends.hv0[0], ends.hv0[1]}, kv0[2] = {ends.kv0[0], ends.kv0[1]};
+    const double hv1[2] = {ends.hv1[0], ends.hv1[1]}, kv1[2] = {ends.kv1[0], ends.kv1[1]};
     __syncthreads();
     const double hdt = 0.5 * dt;
     double *W = s.scratch + t * s.scratch_stride;
@@ -513,17 +544,11 @@ __global__ void __launch_bounds__(256) k2_build_w_f32(DevState s, Model2Dev md, 
     float2 *l0 = reinterpret_cast<float2 *>(red + 32), *l1 = l0 + N;  // lam as (hi, lo) per end
     float *a0 = reinterpret_cast<float *>(l1 + N), *b0 = a0 + N, *a1 = b0 + N, *b1 = a1 + N;
     float *m00 = b1 + N, *m01 = m00 + N, *m10 = m01 + N, *m11 = m10 + N;  // lam - h_a per end
-    double x0[6], v0[6], x1[6], v1[6];
-    for (int y = 0; y < 6; ++y) {
-        x0[y] = s.x_prev[t * 6 + y];
-        v0[y] = s.vprev[t * 6 + y];
-        x1[y] = s.x[t * 6 + y];
-        v1[y] = s.p[t * 6 + y] / md.mass;
-    }
-    const Ads2 e0 = ads2_eval(md, x0), e1 = ads2_eval(md, x1);
-    double hv0[2], kv0[2], hv1[2], kv1[2];
-    ads2_project(md, e0, v0, hv0, kv0);
-    ads2_project(md, e1, v1, hv1, kv1);
+    __shared__ Ends2 ends;
+    ends2_block(s, md, t, &ends);
+    const Ads2 e0 = ends.e0, e1 = ends.e1;
+    const double hv0[2] = {ends.hv0[0], ends.hv0[1]}, kv0[2] = {ends.kv0[0], ends.kv0[1]};
+    const double hv1[2] = {ends.hv1[0], ends.hv1[1]}, kv1[2] = {ends.kv1[0], ends.kv1[1]};
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         const double la = s.lam_prev[t * N + i], lb = s.lam[t * N + i];
         const float ha = (float)la, hb = (float)lb;
@@ -593,7 +618,8 @@ __global__ void __launch_bounds__(64) k2_accept(DevState s, Model2Dev md)
         ps[tid] = s.p[t * 6 + tid];
     }
     __syncthreads();
-    const Ads2 ad = ads2_eval(md, xs);
+    __shared__ Ads2 ad_sh;
+    const Ads2 ad = ads2_block(md, xs, &ad_sh);
     if (tid == 0) {
         s_hopped = 0;
         const int pair = s.hop_pair[t];
@@ -729,7 +755,8 @@ __global__ void __launch_bounds__(256) k2g_reduce(DevState s, Model2Dev md, doub
     if (t < 0 || (s.status[t] & ST_DONE)) return;
     const int N = s.N, M = s.M, lda = dense_lda(N), tid = threadIdx.x;
     kick_drift2(s, md, t, dt, mode, xs);
-    const Ads2 ad = ads2_eval(md, xs);
+    __shared__ Ads2 ad_sh;
+    const Ads2 ad = ads2_block(md, xs, &ad_sh);
     double *v = g2_sh, *w = v + N, *r1 = w + N, *d = r1 + N, *e = d + N, *tau = e + N, *sh = tau + N;
     double *out = s.scratch + t * s.scratch_stride;  // d, e, Y
     double *A = dense_in_smem(N) ? sh + 8 : out + 4 * N;
@@ -769,7 +796,9 @@ __global__ void __launch_bounds__(128) k2g_ql(DevState s, int L)
     if (valid && !ok) atomicOr(&s.status[t], ST_SECULAR);
 }
 
-__global__ void __launch_bounds__(256) k2g_finish(DevState s, Model2Dev md, double dt, int mode)
+// sorted: the eigenvalues arrive in ascending order (the nested secular
+// path), so the rank sort (N^2 FP64 comparisons) is skipped.
+__global__ void __launch_bounds__(256) k2g_finish(DevState s, Model2Dev md, double dt, int mode, int sorted)
 {
     extern __shared__ __align__(16) double f2_sh[];
     __shared__ double xs[6], ps[6], xp[6], red[32];
@@ -789,11 +818,15 @@ __global__ void __launch_bounds__(256) k2g_finish(DevState s, Model2Dev md, doub
         y1[i] = b[2 * N + 2 * i + 1];
     }
     __syncthreads();
-    const Ads2 ad = ads2_eval(md, xs);
+    __shared__ Ads2 ad_sh;
+    const Ads2 ad = ads2_block(md, xs, &ad_sh);
     for (int i = tid; i < N; i += blockDim.x) {  // ascending, ties by index
         const double li = ev[i];
-        int r = 0;
-        for (int j = 0; j < N; ++j) r += (ev[j] < li) || (ev[j] == li && j < i);
+        int r = i;
+        if (!sorted) {
+            r = 0;
+            for (int j = 0; j < N; ++j) r += (ev[j] < li) || (ev[j] == li && j < i);
+        }
         lam_s[r] = li;
         Q0_s[r] = y0[i];
         Q1_s[r] = y1[i];
@@ -811,7 +844,8 @@ __global__ void __launch_bounds__(256) k2g_finish(DevState s, Model2Dev md, doub
         // overlap with the previous step's eigenvector j (bath rows rebuilt
         // from the adsorbate rows; FP32 sums: only the comparison with -1/2
         // is used)
-        const Ads2 adp = ads2_eval(md, xp);
+        __shared__ Ads2 adp_sh;
+        const Ads2 adp = ads2_block(md, xp, &adp_sh);
         for (int j = tid; j < N; j += blockDim.x) {
             const double q0 = Q0_s[j], q1 = Q1_s[j], lj = lam_s[j];
             const double p0 = s.q0_prev[t * N + j], p1 = s.q2_prev[t * N + j], lp = s.lam_prev[t * N + j];
@@ -892,7 +926,8 @@ __global__ void __maxnreg__(128) k2n_eigen(DevState s, Model2Dev md, double dt, 
     const double g1 = (warm && tid < M1) ? md.mu[t * M1 + tid] : 0.0;
     const double g2 = (warm && tid < N) ? s.lam[t * N + tid] : 0.0;
     kick_drift2(s, md, t, dt, mode, xs);
-    const Ads2 ad = ads2_eval(md, xs);
+    __shared__ Ads2 ad_sh;
+    const Ads2 ad = ads2_block(md, xs, &ad_sh);
     double *eps_s = n2_sh, *z2 = eps_s + M, *mu = z2 + M, *sv = mu + M1, *c2 = sv + M1, *cs = c2 + M1,
            *tau1 = cs + M1;
     int *o1 = reinterpret_cast<int *>(tau1 + M1);
@@ -1121,7 +1156,7 @@ cudaError_t launch_eigen2(iesh2_ctx *ctx, double dt, int mode)
         else k2n_eigen<false><<<(unsigned)d.n, threads, nested_smem(d.M), ctx->stream>>>(d, ctx->md, dt, mode);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        k2g_finish<<<(unsigned)d.n, 256, (size_t)6 * d.N * sizeof(double), ctx->stream>>>(d, ctx->md, dt, mode);
+        k2g_finish<<<(unsigned)d.n, 256, (size_t)6 * d.N * sizeof(double), ctx->stream>>>(d, ctx->md, dt, mode, 1);
         return cudaGetLastError();
     }
     if (ctx->dense) {
@@ -1132,7 +1167,7 @@ cudaError_t launch_eigen2(iesh2_ctx *ctx, double dt, int mode)
         const int64_t warps = (d.n + L - 1) / L;
         k2g_ql<<<(unsigned)((warps + 3) / 4), 128, 0, ctx->stream>>>(d, L);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k2g_finish<<<(unsigned)d.n, 256, (size_t)6 * d.N * sizeof(double), ctx->stream>>>(d, ctx->md, dt, mode);
+        k2g_finish<<<(unsigned)d.n, 256, (size_t)6 * d.N * sizeof(double), ctx->stream>>>(d, ctx->md, dt, mode, 0);
         return cudaGetLastError();
     }
     const int tpb = eigen_tpb(d.N);
