@@ -92,24 +92,59 @@ __device__ __forceinline__ void hop_finish(const DevState &s, int64_t t, double 
             slot_sum[a] = sa;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double cum = 0.0;
-            int a_hit = -1;
-            for (int a = 0; a < Ne; ++a) {
-                if (cum + slot_sum[a] > zeta) {
-                    a_hit = a;
-                    break;
+        // The running sum in that order, by warp 0: each lane sums a run of
+        // consecutive slots (then of candidates), a warp scan gives the sums
+        // before each run, and each lane walks its run; the first lane whose
+        // run crosses zeta holds the hop.  (One thread walking all Ne + nu
+        // terms would issue each FP64 addition alone, and on this GPU an
+        // FP64 instruction costs a warp its slot on the pipe whatever its
+        // active lanes.)  The sums round differently from a single serial
+        // sum only at the last bit.
+        if (threadIdx.x < 32) {
+            constexpr unsigned kFull = 0xffffffffu;
+            const int lane = threadIdx.x;
+            auto scan_excl = [&](double v) {  // sum of v over the lanes below
+                double inc = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const double w = __shfl_up_sync(kFull, inc, o);
+                    if (lane >= o) inc += w;
+                }
+                const double ex = __shfl_up_sync(kFull, inc, 1);
+                return lane == 0 ? 0.0 : ex;
+            };
+            const int pa = (Ne + 31) / 32, a0 = lane * pa, a1 = min(Ne, a0 + pa);
+            double loc = 0.0;
+            for (int a = a0; a < a1; ++a) loc += slot_sum[a];
+            double cum = scan_excl(loc), cum_hit = 0.0;
+            int hit = -1;
+            for (int a = a0; a < a1; ++a) {
+                if (hit < 0 && cum + slot_sum[a] > zeta) {
+                    hit = a;
+                    cum_hit = cum;
                 }
                 cum += slot_sum[a];
             }
-            if (a_hit >= 0) {
-                for (int u = 0; u < nu; ++u) {
-                    cum += G[(int64_t)a_hit * N + unocc[u]];
-                    if (cum > zeta) {
-                        s_hop_a = a_hit;
-                        s_hop_m = unocc[u];
-                        break;
-                    }
+            const unsigned ba = __ballot_sync(kFull, hit >= 0);
+            if (ba) {
+                const int src = __ffs(ba) - 1;
+                const int a_hit = __shfl_sync(kFull, hit, src);
+                const double base = __shfl_sync(kFull, cum_hit, src);
+                const double *Ga = G + (int64_t)a_hit * N;
+                const int pu = (nu + 31) / 32, u0 = lane * pu, u1 = min(nu, u0 + pu);
+                double l2 = 0.0;
+                for (int u = u0; u < u1; ++u) l2 += Ga[unocc[u]];
+                double c2 = base + scan_excl(l2);
+                int m_hit = -1;
+                for (int u = u0; u < u1; ++u) {
+                    c2 += Ga[unocc[u]];
+                    if (m_hit < 0 && c2 > zeta) m_hit = unocc[u];
+                }
+                const unsigned bm = __ballot_sync(kFull, m_hit >= 0);
+                const int m_sel = bm ? __shfl_sync(kFull, m_hit, __ffs(bm) - 1) : -1;
+                if (lane == 0 && m_sel >= 0) {
+                    s_hop_a = a_hit;
+                    s_hop_m = m_sel;
                 }
             }
         }
