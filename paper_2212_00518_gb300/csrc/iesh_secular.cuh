@@ -29,9 +29,11 @@ struct Roundoff<float> {
 // estimate's relative error |e| far below 2^-18 the truncated e^3 term is
 // below 2^-54, so the result is within about an ulp of 1/d.  Three FMAs
 // replace a full division in the secular sums, which are the FP64-bound
-// part of the eigen solve, and in the couplings d_jk.  Inputs are pole
-// distances and eigenvalue gaps, never subnormal (the estimate flushes
-// subnormal inputs to zero).
+// part of the eigen solve, in the couplings d_jk and in the iteration's
+// safeguarded proposals.  Inputs are pole distances, eigenvalue gaps and
+// proposal denominators; a zero or subnormal input (the estimate flushes
+// subnormals to zero) gives a non-finite result, which the callers either
+// cannot produce or reject.
 template <class R>
 __device__ __forceinline__ R pole_recip(R d)
 {
@@ -251,11 +253,14 @@ __device__ __forceinline__ Sec<R> sec_eval(const Poles<R> &P, int o, R tau, R eo
             }
         }
     }
-    const R qo = P.z2[o] / tau;
+    // origin term: one reciprocal of tau (never zero or subnormal: the
+    // iteration keeps it strictly inside its bracket) serves both quotients
+    const R rt = pole_recip<R>(tau);
+    const R qo = P.z2[o] * rt;
     Sec<R> e;
     e.g = (eomh + tau) - s1 - qo;
     e.gp_rest = R(1) + s2;
-    e.gp = e.gp_rest + qo / tau;
+    e.gp = e.gp_rest + qo * rt;
     e.qo = qo;
     e.sabs = sa;
     return e;
@@ -293,7 +298,13 @@ __device__ bool sec_iterate(const Poles<R> &P, R h, int o, int kind, R D, R &lo,
         if (fabs(e.g) <= R(8) * u * e.sabs) return true;
         if (e.g < R(0)) lo = tau;
         else hi = tau;
+        // The quotients below are model-root proposals, safeguarded by the
+        // bracket: reciprocals (pole_recip, within about an ulp) instead of
+        // correctly rounded divisions, which cost several FP64 instructions
+        // each on the iteration's serial path.  A zero or subnormal
+        // denominator gives a non-finite proposal and the bisection step.
         R tn;
+        const R rt = pole_recip<R>(tau);
         if (kind <= 1) {
             // model root of c tau^2 + B tau + s D = 0 in the gap, by the form
             // without cancellation for the sign of B (B < 0 happens when the
@@ -301,17 +312,19 @@ __device__ bool sec_iterate(const Poles<R> &P, R h, int o, int kind, R D, R &lo,
             const R sg = kind == 0 ? R(1) : R(-1);
             const R tp = tau - sg * D;
             const R t = e.gp_rest * tp * tp;
-            const R c = sg * (e.g + s / tau + t / tp);
+            const R c = sg * (e.g + s * rt + t * pole_recip<R>(tp));
             const R B = c * D + s + t;
             const R sq = sqrt(fmax(B * B - R(4) * c * s * D, R(0)));
-            if (B >= R(0) || c == R(0)) tn = sg * R(2) * s * D / (B + sq);
-            else tn = sg * (B - sq) / (R(2) * c);
+            if (B >= R(0) || c == R(0)) tn = sg * R(2) * s * D * pole_recip<R>(B + sq);
+            else tn = sg * (B - sq) * pole_recip<R>(R(2) * c);
         } else {
             const R ee = e.gp_rest;
-            const R c = e.g - ee * tau + s / tau;
+            const R c = e.g - ee * tau + s * rt;
             const R sq = sqrt(fmax(c * c + R(4) * ee * s, R(0)));
-            if (kind == 2) tn = (c >= R(0)) ? (-c - sq) / (R(2) * ee) : -R(2) * s / (sq - c);
-            else tn = (c <= R(0)) ? (sq - c) / (R(2) * ee) : R(2) * s / (c + sq);
+            if (kind == 2)
+                tn = (c >= R(0)) ? (-c - sq) * pole_recip<R>(R(2) * ee) : -R(2) * s * pole_recip<R>(sq - c);
+            else
+                tn = (c <= R(0)) ? (sq - c) * pole_recip<R>(R(2) * ee) : R(2) * s * pole_recip<R>(c + sq);
         }
         if (!(tn > lo && tn < hi)) tn = R(0.5) * (lo + hi);
         const bool tiny = fabs(tn - tau) <= R(2) * u * fabs(tn);
