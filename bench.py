@@ -241,7 +241,8 @@ def run_ours(args):
         ms, _ = agg(ms=ev0.elapsed_time(ev1))
         prof = c.profile_read()
         c.profile(False)
-        out = dict(ms=ms, prof=prof, K=c.propagator_terms(), tc=c.kernel_shape()[0] == 8,
+        shape = c.kernel_shape()[0]
+        out = dict(ms=ms, prof=prof, K=c.propagator_terms(), tc=shape if shape in (8, 16) else 0,
                    status=c.get_state()["status"], clocks=clk.summary() if clk else None, n=n)
         if e2e:
             # end to end through the C-ABI: every step loads the whole state from a
@@ -316,7 +317,17 @@ def run_ours(args):
         w_tc = prop_w + 8.0 * (N - Ne) * Ne * Ne + 8.0 / 3.0 * Ne ** 3
         w_64 = step_w - w_tc
         t_star = w_tc / (ptf * 1e12) + w_64 / (FP64_NOMINAL_TFLOPS * 1e12)
-        if r["tc"]:
+        if r["tc"] == 16:
+            # FP16 operands: the dense FP16 rate equals the bf16 one
+            Kp, NB = (N + 15) // 16 * 16, (2 * Ne + 15) // 16 * 16
+            pbf = measured_peaks().get("bf16_tflops")
+            roof = {"bound": "tensor", "kernel": "k_cheb_tc16 (tcgen05 kind::f16, FP16 split operands, "
+                                                 "two CTAs per SM)",
+                    "peak": pbf if pbf else 1900.0,
+                    "peak_source": ("of measured: MEASURED_PEAKS.json bf16_tflops (FP16 dense = bf16 dense)"
+                                    if pbf else "of fallback: 1.9 PFLOP/s bf16 burst"),
+                    "executed_tensor_tflops": exe * 3 * (128 * Kp * NB) / (N * N * 2 * Ne) if exe else None}
+        elif r["tc"]:
             Kp, NB = (N + 7) // 8 * 8, (2 * Ne + 15) // 16 * 16
             roof = {"bound": "tensor", "kernel": "k_cheb_tc (tcgen05 kind::tf32, 3xTF32)",
                     "peak": ptf, "peak_source": src,
@@ -337,9 +348,10 @@ def run_ours(args):
                                          "divided by the measured time per trajectory-step"})
         return roof
 
-    MIXED_DTYPE = ("f32 coefficients, coupling generator, propagation (3xTF32 tensor cores for "
-                   "N <= 128, FP32 SIMT above), overlap LU or Gauss-Jordan ratios; double-float "
-                   "secular sums; f64 eigen iteration, forces, hop selection and rescale")
+    MIXED_DTYPE = ("f32 coefficients, coupling generator, propagation (tensor cores for N <= 128: "
+                   "FP16 hi + lo split operands, about 22 bits each, FP32 accumulation, where two CTAs "
+                   "fit an SM, else 3xTF32; FP32 SIMT above), overlap LU or Gauss-Jordan ratios; "
+                   "double-float secular sums; f64 eigen iteration, forces, hop selection and rescale")
 
     # ---------------------------------------------- headline: M = args.M
     n = args.n_traj

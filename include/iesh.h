@@ -279,7 +279,10 @@ const char *iesh_ensemble_last_error(const iesh_ensemble *ens);
  * 4; the second term stages W) at most 110 KiB; or cheb_ept 32 (8 orbitals
  * x 4 electrons per thread, one CTA per SM) with cheb_G * ceil(ceil(N/4)/2)
  * <= 256 and the same shared memory at most 220 KiB; or cheb_ept 8 with
- * cheb_G 1, the tensor-core kernel (N <= 128, Ne <= 56).  hop_threads (256 or 512):
+ * cheb_G 1, the tensor-core kernel (N <= 128, Ne <= 56, 3xTF32); or
+ * cheb_ept 16 with cheb_G 1, the tensor-core kernel on FP16 split operands
+ * with two CTAs per SM (N <= 128, Ne <= 56, its shared memory at most 110
+ * KiB).  hop_threads (256 or 512):
  * threads of the LU hop kernel; 0 restores the built-in choice, which for
  * mixed contexts is a Gauss-Jordan elimination of all determinant ratios,
  * in registers for N <= 128 and Ne <= 56 and with the rows past 128 in

@@ -396,6 +396,7 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
     d.traj_base = (uint64_t)opt->traj_base;
     configure_hop_smem();
     configure_cheb_tc();
+    configure_cheb_tc16();
     {
         std::vector<float> ed((size_t)M * M);
         for (int a = 0; a < M; ++a)
@@ -648,7 +649,8 @@ iesh_status iesh_set_kernel_shape(iesh_ctx *ctx, int cheb_ept, int cheb_G, int h
     if (ctx->opt.precision == IESH_PREC_MIXED) {
         const bool simt = (cheb_ept == 4 && cheb32_shape_ok(ctx->N, cheb_G, 1)) ||
                           (cheb_ept == 32 && cheb32_shape_ok(ctx->N, cheb_G, 2));
-        const bool tc = cheb_ept == 8 && cheb_G == 1 && cheb_tc_eligible(ctx->N, ctx->Ne);
+        const bool tc = (cheb_ept == 8 && cheb_G == 1 && cheb_tc_eligible(ctx->N, ctx->Ne)) ||
+                        (cheb_ept == 16 && cheb_G == 1 && cheb_tc16_eligible(ctx->N, ctx->Ne));
         if (!((cheb_ept == 0 && cheb_G == 0) || simt || tc))
             return fail(ctx, IESH_EINVAL,
                         "mixed propagator shape (%d, %d) invalid for N=%d, Ne=%d (need ept 4 with "
@@ -672,7 +674,10 @@ iesh_status iesh_get_kernel_shape(iesh_ctx *ctx, int *cheb_ept, int *cheb_G, int
     if (!ctx) return IESH_EINVAL;
     int e = ctx->ds.cheb_ept, g = ctx->ds.cheb_G;
     if (e == 0) {
-        if (ctx->opt.precision == IESH_PREC_MIXED && cheb_tc_eligible(ctx->N, ctx->Ne)) {
+        if (ctx->opt.precision == IESH_PREC_MIXED && cheb_tc16_eligible(ctx->N, ctx->Ne)) {
+            e = 16;
+            g = 1;
+        } else if (ctx->opt.precision == IESH_PREC_MIXED && cheb_tc_eligible(ctx->N, ctx->Ne)) {
             e = 8;
             g = 1;
         } else if (ctx->opt.precision == IESH_PREC_MIXED) {

@@ -57,6 +57,13 @@ size_t cheb_tc_smem_bytes(int N, int Ne);
 bool cheb_tc_eligible(int N, int Ne);
 void configure_cheb_tc();
 cudaError_t launch_cheb_tc(const DevState &s, double dt, cudaStream_t st);
+// The same on FP16 split operands, two CTAs per SM (shared memory at most
+// kChebTc16MaxSmem each)
+constexpr size_t kChebTc16MaxSmem = 110 * 1024;
+size_t cheb_tc16_smem_bytes(int N, int Ne);
+bool cheb_tc16_eligible(int N, int Ne);
+void configure_cheb_tc16();
+cudaError_t launch_cheb_tc16(const DevState &s, double dt, cudaStream_t st);
 // unitarity check of the coefficient columns (sets ST_NORM), observables
 // out[4][n] = (kinetic energy, potential energy, occupied-surface and
 // wavefunction impurity populations), batch status summary out[9]

@@ -1303,6 +1303,9 @@ cudaError_t launch_cheb(const DevState &s, double dt, bool mixed, cudaStream_t s
     if (mixed) {
         // tensor cores (3xTF32) when the trajectory fits one CTA, unless a
         // SIMT shape was requested
+        // tensor cores: FP16 split operands (two CTAs per SM) where they fit,
+        // else 3xTF32 (one CTA per SM), unless a shape was requested
+        if (s.cheb_ept == 16 || (s.cheb_ept == 0 && cheb_tc16_eligible(s.N, s.Ne))) return launch_cheb_tc16(s, dt, st);
         if (s.cheb_ept == 8 || (s.cheb_ept == 0 && cheb_tc_eligible(s.N, s.Ne))) return launch_cheb_tc(s, dt, st);
         // SIMT: one row quad per thread (cheb_ept 4) or two (cheb_ept 32); by
         // default two past N = 224, where its one CTA per SM measured faster

@@ -1319,6 +1319,7 @@ iesh_status iesh2_create(iesh2_ctx **out, const iesh2_model *model, int precisio
     d.eigen_dfloat = ctx->mixed ? 1 : 0;
     configure_hop_smem();
     configure_cheb_tc();
+    configure_cheb_tc16();
     // the slots of the eigen kernel can pass the 48 KiB default (N near 65)
     CU2(cudaFuncSetAttribute(k2_eigen<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)eigen2_smem(N, M, eigen_tpb(N), false)));

@@ -86,7 +86,7 @@ def autotune(ctx, x, p, occ, C, dt, steps=3, seed=0):
         return prof["propagate"][0], prof["hop"][0]
 
     default = scratch.kernel_shape()[:2]
-    cands = [default] if default[0] == 8 else cheb_candidates(ctx.N, ctx.Ne, precision=ctx.precision)
+    cands = [default] if default[0] in (8, 16) else cheb_candidates(ctx.N, ctx.Ne, precision=ctx.precision)
     for ept, G in cands:
         times_cheb[(ept, G)] = trial(ept, G, 0)[0]
     for hop in (0, 256, 512):

@@ -62,7 +62,7 @@ def test_mixed_one_step(P, name, kernel):
     if kernel == "simt":
         ctx.set_kernel_shape(4, 1, 0)
     else:
-        assert ctx.kernel_shape()[0] == (8 if md["M"] + 1 <= 128 else 4)
+        assert ctx.kernel_shape()[0] in ((8, 16) if md["M"] + 1 <= 128 else (4,))
     ctx.set_state(x, p, occ, C.astype(np.complex64))
     g = ctx.hop_probabilities(dt)
     gref = []
@@ -272,4 +272,42 @@ def test_mixed_two_quad_propagator_identical(P, M, Ne, n):
         r = O.step_one(B, x[t], p[t], occ[t].astype(np.int32), C[t].T.astype(np.complex128), 1.0, seed=4,
                        traj=t, n=0)
         assert np.array_equal(st["occ"][t], r["occ"])
+        assert np.abs(st["C"][t].T - r["C"]).max() <= 1e-6
+
+
+@pytest.mark.parametrize("M,Ne,n", [(100, 50, 6), (20, 10, 8), (110, 50, 4), (64, 1, 4), (9, 4, 3)])
+def test_mixed_fp16_tensor_core_propagator(P, M, Ne, n):
+    """The tensor-core propagator on FP16 split operands (shape 16: scaled
+    hi + lo FP16 pairs, about 22 bits each, the Chebyshev sum in tensor
+    memory): one step against the oracle at the mixed bounds, and against
+    the 3xTF32 kernel where that one fits (both within about 2^-22 of |W||T|
+    per order; at N = 111 only the FP16 kernel's shared memory fits)."""
+    md = W.double_well(M, Ne)
+    N = M + 1
+    x, p = W.thermal_harmonic(n, md["mass"], md["par"][0], 0.01, 41)
+    occ = W.random_occupations(n, N, Ne, 42)
+    C = W.mixed_coefficients(occ, N, 43, 0.6).astype(np.complex64)
+    out = {}
+    for ept in (8, 16):
+        ctx = P.Context(md, n, precision=P.PREC_MIXED)
+        ctx.set_state(x, p, occ, C)
+        try:
+            ctx.set_kernel_shape(ept, 1, 0)
+        except P.IeshError:
+            assert ept == 8 and M == 110
+            ctx.close()
+            continue
+        ctx.run(1.0, 1, seed=4)
+        out[ept] = ctx.get_state()
+        ctx.close()
+    st = out[16]
+    assert np.all(st["status"] == 0)
+    if 8 in out:
+        assert np.abs(st["C"] - out[8]["C"]).max() <= 2e-6
+    B = O.bind(md)
+    for t in range(n):
+        r = O.step_one(B, x[t], p[t], occ[t].astype(np.int32), C[t].T.astype(np.complex128), 1.0, seed=4,
+                       traj=t, n=0)
+        assert np.array_equal(st["occ"][t], r["occ"])
+        assert abs(st["x"][t] - r["x"]) <= 1e-13 * (1 + abs(r["x"]))
         assert np.abs(st["C"][t].T - r["C"]).max() <= 1e-6
