@@ -24,8 +24,8 @@
 // + lo), T_{k-1} is held in registers.
 //
 // One CTA per trajectory, 512 threads: warp w reads TMEM lanes 32 (w % 4) ..
-// +31 (orbital row j = 32 (w % 4) + lane) and owns the column quarter w / 4
-// of the 2Ne real columns.  Each order: one thread issues the 3 x K/16 MMAs
+// +31 (orbital row j = 32 (w % 4) + lane) and owns the electrons e = 4q + w/4
+// (so that each thread's B entries step by one 8-column group per electron).  Each order: one thread issues the 3 x K/16 MMAs
 // and commits them to an mbarrier; every thread waits (bounded), loads its D
 // and Chebyshev-sum entries from tensor memory, forms T_{k+1} for its row
 // and columns, stores the sum back and rewrites its B entries in place.
@@ -43,7 +43,7 @@ namespace {
 
 constexpr int kT16M = 128;          // MMA rows (orbitals, padded)
 constexpr int kT16Threads = 512;    // 4 lane quarters x 4 column groups
-constexpr int kT16MaxChunks = 7;    // 4-column chunks per thread: 2 Ne <= 112
+constexpr int kT16MaxPairs = 14;    // electrons per thread (e = 4 q + column group): Ne <= 56
 constexpr int kT16LboA = 128, kT16LboB = 144;
 constexpr int kT16Cols = 256;       // TMEM columns: D [0, 128), Chebyshev sum [128, 256)
 constexpr int kT16AccCol = 128;
@@ -58,7 +58,7 @@ constexpr float kT16InvST = 1.0f / 16384.0f, kT16InvD = 1.0f / (8192.0f * 16384.
 // of D depends on row j of A alone).  `total` also covers the reads of A_lo
 // past the end of B.
 struct T16Shape {
-    int Kp, NB, cpt, rg, sboA, sboB, usedA, bytesB, total;
+    int Kp, NB, rg, sboA, sboB, usedA, bytesB, total;
 };
 
 __host__ __device__ inline T16Shape t16_shape(int N, int Ne)
@@ -66,7 +66,6 @@ __host__ __device__ inline T16Shape t16_shape(int N, int Ne)
     T16Shape t;
     t.Kp = (N + 15) & ~15;
     t.NB = (2 * Ne + 15) & ~15;
-    t.cpt = t.NB / 4;
     t.rg = (N + 7) / 8;
     t.sboA = (t.Kp / 8) * kT16LboA;
     t.sboB = (t.Kp / 8) * kT16LboB;
@@ -108,10 +107,15 @@ __global__ void __launch_bounds__(kT16Threads, 2) k_cheb_tc16(DevState s, double
     unsigned char *Bhi = t16_smem + 2 * sh.usedA, *Blo = Bhi + sh.bytesB;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int j = 32 * (warp & 3) + lane;  // my orbital row = my TMEM lane
-    const int cg = warp >> 2;              // my column quarter
-    const int c0 = cg * sh.cpt;
-    const int nch = sh.cpt / 4;
+    const int cg = warp >> 2;              // my column group: electrons e = 4 q + cg
+    const int npair = (Ne + 3) / 4;        // my electrons (q < npair; e < Ne checked)
     const bool rowok = j < N;
+    // B entry (column n, row j) of electron e = 4q + cg: n = 2e in the 8-column
+    // group q at 32 cg bytes into it (Re; Im 16 bytes on), so q steps by sboB
+    const int jb = (j >> 3) * kT16LboB + (j & 7) * 2 + 32 * cg;
+    // TMEM: D of electron e at columns 2e, 2e + 1 (8q + 2cg); my Chebyshev
+    // sums at kT16AccCol + 28 cg + 2q (private to my column group)
+    const uint32_t accc = (uint32_t)(kT16AccCol + 2 * kT16MaxPairs * cg);
 
     if (tid == 0) tc::mbar_init(&mbar, 1);
     if (warp == 0) tc::tmem_alloc(&tmem_slot, (uint32_t)kT16Cols);
@@ -123,8 +127,11 @@ __global__ void __launch_bounds__(kT16Threads, 2) k_cheb_tc16(DevState s, double
     const double rho0 = s.cheb[t * kChebStride + 1];
     const float ws = rho0 > 0.0 ? (float)(2.0 / rho0) * kT16SW : 0.0f;
     const int kc8 = sh.Kp / 8;
-    for (int it = tid; it < 8 * sh.rg * kc8; it += kT16Threads) {
-        const int row = it / kc8, kc = it - row * kc8;
+    // consecutive threads take consecutive rows of one K chunk: their 16-byte
+    // stores fill whole core matrices (no bank conflicts)
+    const int nrow = 8 * sh.rg;
+    for (int it = tid; it < nrow * kc8; it += kT16Threads) {
+        const int kc = it / nrow, row = it - kc * nrow;
         __align__(16) __half hi[8], lo[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -163,25 +170,24 @@ __global__ void __launch_bounds__(kT16Threads, 2) k_cheb_tc16(DevState s, double
     const float Lc = rowok ? w2 * (float)(0.5 * dt * (s.lam_prev[t * N + j] + s.lam[t * N + j]) - c) : 0.0f;
     const float J0 = (float)J[0];
 
-    // T_0 = C: my row, my columns (B entry (col, j) at offB(col, j); col and
-    // col + 1, one electron, 16 bytes apart); the Chebyshev sum J_0 C into
-    // tensor memory
-    float prv[4 * kT16MaxChunks];
+    // T_0 = C: my row, my electrons; the Chebyshev sum J_0 C into tensor memory
+    float prv[2 * kT16MaxPairs];
 #pragma unroll
-    for (int ch = 0; ch < kT16MaxChunks; ++ch) {
-        float a[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int q = 0; q < kT16MaxPairs; q += 2) {
+        if (q >= npair) break;  // uniform
+        float a[4];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int col = c0 + 4 * ch + 2 * h, e = col >> 1;
-            const bool mine = ch < nch && rowok && e < Ne;
+            const int e = 4 * (q + h) + cg;
+            const bool mine = q + h < npair && rowok && e < Ne;
             float2 v = make_float2(0.f, 0.f);
             if (mine) v = C[(int64_t)e * N + j];
-            prv[4 * ch + 2 * h] = 0.f;
-            prv[4 * ch + 2 * h + 1] = 0.f;
+            prv[2 * (q + h)] = 0.f;
+            prv[2 * (q + h) + 1] = 0.f;
             a[2 * h] = J0 * v.x;
             a[2 * h + 1] = J0 * v.y;
             if (mine) {
-                const int ob = t16_offB(sh, col, j);
+                const int ob = (q + h) * sh.sboB + jb;
                 __half hr, lr, hi_, li;
                 split16(kT16ST * v.x, hr, lr);
                 split16(kT16ST * v.y, hi_, li);
@@ -191,8 +197,7 @@ __global__ void __launch_bounds__(kT16Threads, 2) k_cheb_tc16(DevState s, double
                 *reinterpret_cast<__half *>(Blo + ob + 16) = li;
             }
         }
-        if (ch < nch)  // warp-uniform
-            tc::tmem_st4(my_lane + (uint32_t)(kT16AccCol + c0 + 4 * ch), a[0], a[1], a[2], a[3]);
+        tc::tmem_st4(my_lane + accc + 2 * q, a[0], a[1], a[2], a[3]);
     }
     tc::tmem_wait_st();
     tc::fence_async_smem();
@@ -229,17 +234,18 @@ __global__ void __launch_bounds__(kT16Threads, 2) k_cheb_tc16(DevState s, double
         const float ca = ph == 0 ? cj : (ph == 2 ? -cj : 0.f), cbf = ph == 1 ? -cj : (ph == 3 ? cj : 0.f);
         const bool first = k == 0;
 #pragma unroll
-        for (int ch = 0; ch < kT16MaxChunks; ++ch) {
-            if (ch >= nch) continue;  // warp-uniform
+        for (int q = 0; q < kT16MaxPairs; q += 2) {
+            if (q >= npair) break;  // uniform
             float d[4], a[4];
-            tc::tmem_ld4(my_lane + (uint32_t)(c0 + 4 * ch), d[0], d[1], d[2], d[3]);
-            tc::tmem_ld4(my_lane + (uint32_t)(kT16AccCol + c0 + 4 * ch), a[0], a[1], a[2], a[3]);
+            tc::tmem_ld2(my_lane + (uint32_t)(8 * q + 2 * cg), d[0], d[1]);
+            tc::tmem_ld2(my_lane + (uint32_t)(8 * (q + 1) + 2 * cg), d[2], d[3]);
+            tc::tmem_ld4(my_lane + accc + 2 * q, a[0], a[1], a[2], a[3]);
             tc::tmem_wait_ld();
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int col = c0 + 4 * ch + 2 * h, e = col >> 1;
-                if (rowok && e < Ne) {
-                    const int ob = t16_offB(sh, col, j);
+                const int e = 4 * (q + h) + cg;
+                if (q + h < npair && rowok && e < Ne) {
+                    const int ob = (q + h) * sh.sboB + jb;
                     // T_k from its own B entries
                     const float own_r = (__half2float(*reinterpret_cast<const __half *>(Bhi + ob)) +
                                          __half2float(*reinterpret_cast<const __half *>(Blo + ob))) * kT16InvST;
@@ -249,7 +255,7 @@ __global__ void __launch_bounds__(kT16Threads, 2) k_cheb_tc16(DevState s, double
                     const float dr = d[2 * h] * kT16InvD, di = d[2 * h + 1] * kT16InvD;
                     const float xr = fmaf(Lc, own_r, di);
                     const float xi = fmaf(Lc, own_i, -dr);
-                    float *pp = prv + 4 * ch + 2 * h;
+                    float *pp = prv + 2 * (q + h);
                     const float nr = first ? 0.5f * xr : xr - pp[0];
                     const float ni = first ? 0.5f * xi : xi - pp[1];
                     pp[0] = own_r;
@@ -266,7 +272,7 @@ __global__ void __launch_bounds__(kT16Threads, 2) k_cheb_tc16(DevState s, double
                     *reinterpret_cast<__half *>(Blo + ob + 16) = li;
                 }
             }
-            tc::tmem_st4(my_lane + (uint32_t)(kT16AccCol + c0 + 4 * ch), a[0], a[1], a[2], a[3]);
+            tc::tmem_st4(my_lane + accc + 2 * q, a[0], a[1], a[2], a[3]);
         }
         tc::tmem_wait_st();
         tc::fence_async_smem();
@@ -283,15 +289,15 @@ __global__ void __launch_bounds__(kT16Threads, 2) k_cheb_tc16(DevState s, double
     } else {
         const float sc = s_sc[1], cc = s_sc[2];
 #pragma unroll
-        for (int ch = 0; ch < kT16MaxChunks; ++ch) {
-            if (ch >= nch) continue;  // warp-uniform
+        for (int q = 0; q < kT16MaxPairs; q += 2) {
+            if (q >= npair) break;  // uniform
             float a[4];
-            tc::tmem_ld4(my_lane + (uint32_t)(kT16AccCol + c0 + 4 * ch), a[0], a[1], a[2], a[3]);
+            tc::tmem_ld4(my_lane + accc + 2 * q, a[0], a[1], a[2], a[3]);
             tc::tmem_wait_ld();
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int e = (c0 + 4 * ch + 2 * h) >> 1;
-                if (rowok && e < Ne) {
+                const int e = 4 * (q + h) + cg;
+                if (q + h < npair && rowok && e < Ne) {
                     const float ar = a[2 * h], ai = a[2 * h + 1];
                     C[(int64_t)e * N + j] = make_float2(fmaf(cc, ar, sc * ai), fmaf(cc, ai, -(sc * ar)));
                 }
@@ -309,7 +315,7 @@ size_t cheb_tc16_smem_bytes(int N, int Ne) { return (size_t)t16_shape(N, Ne).tot
 
 bool cheb_tc16_eligible(int N, int Ne)
 {
-    return N >= 2 && N <= kT16M && Ne >= 1 && 2 * Ne <= 4 * 4 * kT16MaxChunks &&
+    return N >= 2 && N <= kT16M && Ne >= 1 && Ne <= 4 * kT16MaxPairs &&
            cheb_tc16_smem_bytes(N, Ne) <= kChebTc16MaxSmem;
 }
 

@@ -130,6 +130,15 @@ __device__ __forceinline__ void tmem_ld4(uint32_t addr, float &a, float &b, floa
     d = __uint_as_float(r3);
 }
 
+// Two consecutive 32-bit columns of this thread's TMEM lane (32x32b shape).
+__device__ __forceinline__ void tmem_ld2(uint32_t addr, float &a, float &b)
+{
+    uint32_t r0, r1;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr) : "memory");
+    a = __uint_as_float(r0);
+    b = __uint_as_float(r1);
+}
+
 // Four consecutive 32-bit columns of this thread's TMEM lane (32x32b shape).
 __device__ __forceinline__ void tmem_st4(uint32_t addr, float a, float b, float c, float d)
 {
