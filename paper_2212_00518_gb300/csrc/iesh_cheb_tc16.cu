@@ -49,7 +49,8 @@ constexpr int kT16Cols = 256;       // TMEM columns: D [0, 128), Chebyshev sum [
 constexpr int kT16AccCol = 128;
 constexpr int kT16WaitLimit = 1 << 22;
 constexpr float kT16SW = 8192.0f, kT16ST = 16384.0f;  // 2^13, 2^14
-constexpr float kT16InvST = 1.0f / 16384.0f, kT16InvD = 1.0f / (8192.0f * 16384.0f);
+constexpr float kT16InvST = 1.0f / 16384.0f;
+constexpr float kT16DScaled = 1.0f / 8192.0f;  // D' = 2^27 D, read in the 2^14 unit of T
 
 // Shared layout: A_hi and A_lo hold only their rg = ceil(N/8) used row
 // groups, back to back, then B_hi and B_lo.  An MMA still reads 16 row groups
@@ -91,6 +92,13 @@ __device__ __forceinline__ void split16(float x, __half &hi, __half &lo)
 {
     hi = __float2half_rn(x);
     lo = __float2half_rn(x - __half2float(hi));
+}
+// the same for a pair (Re, Im) with paired conversions
+__device__ __forceinline__ void split16x2(float xr, float xi, __half2 &hi, __half2 &lo)
+{
+    hi = __floats2half2_rn(xr, xi);
+    const float2 hf = __half22float2(hi);
+    lo = __floats2half2_rn(xr - hf.x, xi - hf.y);
 }
 
 __global__ void __launch_bounds__(kT16Threads, 2) k_cheb_tc16(DevState s, double dt, int64_t t_base)
@@ -229,7 +237,10 @@ __global__ void __launch_bounds__(kT16Threads, 2) k_cheb_tc16(DevState s, double
             break;
         }
         tc::fence_after_sync();
-        const float cj = s_cj[k + 1];
+        // T_k, T_{k+1} and T_{k-1} (prv) are handled in the scaled unit of
+        // the B operand (2^14 T): D enters as 2^-13 D' and the Chebyshev
+        // coefficients carry the 2^-14 back
+        const float cj = s_cj[k + 1] * kT16InvST;
         const int ph = (k + 1) & 3;  // (-i)^(k+1) = (1, 0), (0, -1), (-1, 0), (0, 1)
         const float ca = ph == 0 ? cj : (ph == 2 ? -cj : 0.f), cbf = ph == 1 ? -cj : (ph == 3 ? cj : 0.f);
         const bool first = k == 0;
@@ -246,15 +257,14 @@ __global__ void __launch_bounds__(kT16Threads, 2) k_cheb_tc16(DevState s, double
                 const int e = 4 * (q + h) + cg;
                 if (q + h < npair && rowok && e < Ne) {
                     const int ob = (q + h) * sh.sboB + jb;
-                    // T_k from its own B entries
-                    const float own_r = (__half2float(*reinterpret_cast<const __half *>(Bhi + ob)) +
-                                         __half2float(*reinterpret_cast<const __half *>(Blo + ob))) * kT16InvST;
-                    const float own_i = (__half2float(*reinterpret_cast<const __half *>(Bhi + ob + 16)) +
-                                         __half2float(*reinterpret_cast<const __half *>(Blo + ob + 16))) * kT16InvST;
+                    // 2^14 T_k from its own B entries
+                    const float own_r = __half2float(*reinterpret_cast<const __half *>(Bhi + ob)) +
+                                        __half2float(*reinterpret_cast<const __half *>(Blo + ob));
+                    const float own_i = __half2float(*reinterpret_cast<const __half *>(Bhi + ob + 16)) +
+                                        __half2float(*reinterpret_cast<const __half *>(Blo + ob + 16));
                     // 2 (X t)_j = 2 ((L_j - c) t_j - i (W t)_j) / rho, D_j = 2 (W t)_j / rho
-                    const float dr = d[2 * h] * kT16InvD, di = d[2 * h + 1] * kT16InvD;
-                    const float xr = fmaf(Lc, own_r, di);
-                    const float xi = fmaf(Lc, own_i, -dr);
+                    const float xr = fmaf(d[2 * h + 1], kT16DScaled, Lc * own_r);
+                    const float xi = fmaf(-d[2 * h], kT16DScaled, Lc * own_i);
                     float *pp = prv + 2 * (q + h);
                     const float nr = first ? 0.5f * xr : xr - pp[0];
                     const float ni = first ? 0.5f * xi : xi - pp[1];
@@ -263,13 +273,12 @@ __global__ void __launch_bounds__(kT16Threads, 2) k_cheb_tc16(DevState s, double
                     // acc += cj (-i)^(k+1) n without a branch: (ca, cbf) = cj (-i)^(k+1)
                     a[2 * h] = fmaf(ca, nr, fmaf(-cbf, ni, a[2 * h]));
                     a[2 * h + 1] = fmaf(ca, ni, fmaf(cbf, nr, a[2 * h + 1]));
-                    __half hr, lr, hi_, li;
-                    split16(kT16ST * nr, hr, lr);
-                    split16(kT16ST * ni, hi_, li);
-                    *reinterpret_cast<__half *>(Bhi + ob) = hr;
-                    *reinterpret_cast<__half *>(Blo + ob) = lr;
-                    *reinterpret_cast<__half *>(Bhi + ob + 16) = hi_;
-                    *reinterpret_cast<__half *>(Blo + ob + 16) = li;
+                    __half2 hi2, lo2;
+                    split16x2(nr, ni, hi2, lo2);
+                    *reinterpret_cast<__half *>(Bhi + ob) = __low2half(hi2);
+                    *reinterpret_cast<__half *>(Blo + ob) = __low2half(lo2);
+                    *reinterpret_cast<__half *>(Bhi + ob + 16) = __high2half(hi2);
+                    *reinterpret_cast<__half *>(Blo + ob + 16) = __high2half(lo2);
                 }
             }
             tc::tmem_st4(my_lane + accc + 2 * q, a[0], a[1], a[2], a[3]);
