@@ -140,6 +140,11 @@ typedef struct {
     double norm_tol;   /* IESH_TRAJ_NORM_DRIFT threshold, checked after every step
                           of iesh_run (0: 1e-8 for FP64, 1e-3 for the mixed path;
                           < 0: no check) */
+    int no_deflation;  /* FP64 averaged propagator: 1 runs the Chebyshev series over
+                          the whole spectrum interval always; 0 (default) takes an
+                          isolated top eigenvalue out of it where that shortens the
+                          series by at least 2 terms, propagating its eigenvector
+                          exactly (same result within the series tolerance) */
 } iesh_options;
 
 /* Create a context for up to max_traj trajectories of `model`.  Discretises

@@ -370,6 +370,8 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
     A(d.status, T) A(d.nstep, T) A(d.hops, T) A(d.frus, T)
     A(d.scratch, T * (size_t)d.scratch_stride)
     A(d.cheb, T * kChebStride)
+    if (!ctx->mixed && opt->propagator == IESH_PROP_AVERAGED && !opt->no_deflation)
+        A(d.defl, T * (2 * (size_t)N + 2))
     A(ctx->live, T)
     A(ctx->n_live, 1)
     A(ctx->obs, 4 * T)
@@ -658,7 +660,7 @@ iesh_status iesh_set_kernel_shape(iesh_ctx *ctx, int cheb_ept, int cheb_G, int h
                         "shared-memory cap, or ept 8, G 1 for the tensor-core kernel: N <= 128, Ne <= 56)",
                         cheb_ept, cheb_G, ctx->N, ctx->Ne);
     } else if (cheb_ept < 0 || cheb_ept > 2 || cheb_G < 0 || (cheb_ept > 0) != (cheb_G > 0) ||
-               cheb_G * ctx->N > 1024) {
+               cheb_threads(ctx->N, cheb_G, ctx->ds.defl != nullptr) > 1024) {
         return fail(ctx, IESH_EINVAL, "propagator shape (%d, %d) invalid for N=%d", cheb_ept, cheb_G, ctx->N);
     }
     if (hop_threads != 0 && hop_threads != 256 && hop_threads != 512)
@@ -685,7 +687,7 @@ iesh_status iesh_get_kernel_shape(iesh_ctx *ctx, int *cheb_ept, int *cheb_G, int
             e = qpt == 2 ? 32 : 4;
             cheb32_shape(ctx->N, ctx->Ne, g, qpt);
         } else {
-            cheb_shape(ctx->N, ctx->Ne, e, g);
+            cheb_shape(ctx->N, ctx->Ne, e, g, ctx->ds.defl != nullptr);
         }
     }
     if (cheb_ept) *cheb_ept = e;

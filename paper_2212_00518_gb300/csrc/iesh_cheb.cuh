@@ -44,13 +44,11 @@ __device__ inline void bessel_j(double rho, int K, double *J)
     for (int k = 0; k <= K; ++k) J[k] *= sc;
 }
 
-// Chebyshev degree and coefficients for a spectrum inside [lo, hi] (in units
-// of dt): the smallest K whose tail bound 2 sum_{k>K} (rho/2)^k / k! is below
-// tol, and J_0..J_K(rho).  Called by one thread per trajectory.
-__device__ inline void cheb_setup(const DevState &s, int64_t t, double lo, double hi, double tol)
+// Number of Chebyshev terms for the half-width rho at tolerance tol: the
+// smallest K whose tail bound 2 sum_{k>K} (rho/2)^k / k! is below tol, at
+// most kChebMax - 2.
+__host__ __device__ inline int cheb_terms(double rho, double tol)
 {
-    double *cb = s.cheb + t * kChebStride;
-    const double c = 0.5 * (lo + hi), rho = 0.5 * (hi - lo);
     int K = 0;
     double term = rho * 0.5;  // (rho/2)^{K+1} / (K+1)!
     while (K < kChebMax - 2) {
@@ -60,6 +58,17 @@ __device__ inline void cheb_setup(const DevState &s, int64_t t, double lo, doubl
         ++K;
         term *= (rho * 0.5) / (K + 1);
     }
+    return K;
+}
+
+// Chebyshev degree and coefficients for a spectrum inside [lo, hi] (in units
+// of dt): K = cheb_terms(rho, tol) and J_0..J_K(rho).  Called by one thread
+// per trajectory.
+__device__ inline void cheb_setup(const DevState &s, int64_t t, double lo, double hi, double tol)
+{
+    double *cb = s.cheb + t * kChebStride;
+    const double c = 0.5 * (lo + hi), rho = 0.5 * (hi - lo);
+    const int K = cheb_terms(rho, tol);
     if (K >= kChebMax - 2) atomicOr(&s.status[t], ST_PROP);
     cb[0] = c;
     cb[1] = rho;

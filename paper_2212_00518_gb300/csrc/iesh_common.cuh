@@ -45,6 +45,10 @@ struct DevState {
     double *scratch;           // [n][scratch_stride] per-trajectory workspace
     int64_t scratch_stride;    // doubles per trajectory
     double *cheb;              // [n][kChebStride]: c, rho, K, J_0..J_K
+    // FP64 one-coordinate contexts: [n][2N + 2] per trajectory: a flag, the
+    // isolated top eigenvalue mu of the generator and its eigenvector u (Re
+    // u[N], Im u[N]) when the propagator deflates it (null: never)
+    double *defl;
     double *rec_sh, *rec_wf;   // [max_records][n]
     int record_every, max_records;
     double z_done;

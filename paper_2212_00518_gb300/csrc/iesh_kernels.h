@@ -38,7 +38,8 @@ cudaError_t launch_hop_gj(const DevState &s, double dt, double mass, uint64_t se
 // Bath of one lead: energies and weights (Gauss-Legendre split at mu, or trapezoid)
 void lead_bath(int disc, int n, double a, double b, double mu, int n_lo, std::vector<double> &eps,
                std::vector<double> &w);
-void cheb_shape(int N, int Ne, int &ept, int &G);
+void cheb_shape(int N, int Ne, int &ept, int &G, bool defl = false);
+int cheb_threads(int N, int G, bool defl);
 // Trajectories per CTA of the eigen kernels (slots of N threads, <= 512 threads)
 int eigen_tpb(int N);
 // FP32 (mixed-precision) propagator: 4 electrons per thread, G column

@@ -200,6 +200,23 @@ __global__ void k_force(DevState s)
 }
 
 // ============================================================ couplings
+// Deflation of an isolated top level (FP64 propagator).  When the top row's
+// Gershgorin disc of H = dt Abar = L - i W lies above every other row's disc
+// (the other rows' radii taken without the top column), exactly one
+// eigenvalue mu lies in it, and by interlacing every other eigenvalue lies
+// in [lo, hb]: lo the full Gershgorin minimum, hb = max_{k != top} (L_k +
+// R_k - |W_top,k|).  The Chebyshev series then only needs to cover [lo, hb]
+// if the component along mu's eigenvector u is propagated exactly, as e^{-i
+// mu} (u^H c) u; the bulk half-width is typically a fraction of the full one
+// when the adsorbate level sits far from the band (K 14 -> 10 at 1e-15 for
+// the double well).  u comes from the power iteration with the shift sigma =
+// centre of [lo, hb], whose convergence factor is the bulk half-width over
+// mu - sigma, to a residual |H u - mu u| <= 1e-14 |mu - sigma|; without
+// convergence within kDeflIter iterations, or when the deflated series is
+// not at least kDeflGain terms shorter, the full interval is used.
+constexpr int kDeflIter = 48;
+constexpr int kDeflGain = 2;
+
 __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double mass, double tol)
 {
     extern __shared__ double sh[];
@@ -207,6 +224,7 @@ __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double m
     if (t < 0 || (s.status[t] & ST_DONE)) return;
     const int N = s.N;
     double *l0 = sh, *q00 = l0 + N, *l1 = q00 + N, *q01 = l1 + N, *red = q01 + N;
+    double *Lk_s = red + 32, *hb_s = Lk_s + N, *ur = hb_s + N, *ui = ur + N;  // deflation
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         l0[i] = s.lam_prev[t * N + i];
         q00[i] = s.q0_prev[t * N + i];
@@ -233,10 +251,78 @@ __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double m
         const double Lk = 0.5 * dt * (lk0 + lk1);
         lo = fmin(lo, Lk - Rk);
         hi = fmax(hi, Lk + Rk);
+        Lk_s[k] = Lk;
+        // upper end of row k's disc without the top column; for the top row
+        // the lower end of its disc
+        hb_s[k] = k == N - 1 ? Lk - Rk : Lk + Rk - fabs(W[(int64_t)(N - 1) * N + k]);
     }
     lo = block_min(lo, red);
     hi = block_max(hi, red);
-    if (threadIdx.x == 0) cheb_setup(s, t, lo, hi, tol);
+    double *df = s.defl ? s.defl + t * (2 * (int64_t)N + 2) : nullptr;
+    bool deflate = false;
+    double hb = hi, mu = 0.0;
+    if (df && N >= 3 && N <= (int)blockDim.x) {
+        const int top = N - 1;  // eigenvalues ascending at both ends: L is ascending
+        double b = -__longlong_as_double(0x7ff0000000000000ll);
+        for (int k = threadIdx.x; k < top; k += blockDim.x) b = fmax(b, hb_s[k]);
+        b = block_max(b, red);
+        const double top_lo = hb_s[top];
+        if (top_lo > b && cheb_terms(0.5 * (b - lo), tol) + kDeflGain <= cheb_terms(0.5 * (hi - lo), tol)) {
+            // power iteration for the top eigenvector, thread j < N owns u_j
+            const double sigma = 0.5 * (lo + b);
+            const int j = threadIdx.x;
+            const bool rj = j < N;
+            const double Lj = rj ? Lk_s[j] - sigma : 0.0;
+            if (rj) {
+                ur[j] = j == top ? 1.0 : 0.0;
+                ui[j] = 0.0;
+            }
+            __syncthreads();
+            for (int it = 0; it < kDeflIter; ++it) {
+                double vr = 0.0, vi = 0.0;
+                if (rj) {
+                    // (W u)_j = -sum_k W[k N + j] u_k (W antisymmetric; column reads coalesce)
+                    double wr = 0.0, wi = 0.0;
+                    for (int k = 0; k < N; ++k) {
+                        const double w = W[(int64_t)k * N + j];
+                        wr = fma(-w, ur[k], wr);
+                        wi = fma(-w, ui[k], wi);
+                    }
+                    // (H - sigma) u = (L - sigma) u - i W u
+                    vr = fma(Lj, ur[j], wi);
+                    vi = fma(Lj, ui[j], -wr);
+                }
+                const double rq = block_sum(rj ? fma(ur[j], vr, ui[j] * vi) : 0.0, red);  // u^H (H - sigma) u
+                const double nv = block_sum(fma(vr, vr, vi * vi), red);
+                const double er = rj ? fma(-rq, ur[j], vr) : 0.0, ei = rj ? fma(-rq, ui[j], vi) : 0.0;
+                const double res = block_sum(fma(er, er, ei * ei), red);
+                if (res <= 1e-28 * rq * rq) {  // uniform: every thread holds the same sums
+                    deflate = rq > 0.0;
+                    mu = sigma + rq;
+                    break;
+                }
+                const double inv = 1.0 / sqrt(nv);
+                if (rj) {
+                    ur[j] = vr * inv;
+                    ui[j] = vi * inv;
+                }
+                __syncthreads();
+            }
+            if (deflate) hb = b;
+        }
+    }
+    if (threadIdx.x == 0) {
+        cheb_setup(s, t, lo, hb, tol);
+        if (df) {
+            df[0] = deflate ? 1.0 : 0.0;
+            df[1] = mu;
+        }
+    }
+    if (deflate)
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            df[2 + j] = ur[j];
+            df[2 + N + j] = ui[j];
+        }
 }
 
 // Mixed precision: W in FP32.  Each eigenvalue is written relative to its
@@ -333,6 +419,23 @@ struct Cplx<float> {
     typedef float2 T;
 };
 
+// Deflation (s.defl, see k_build_w): when the trajectory's flag is set, the
+// series covers only the bulk interval, and the component along the
+// isolated eigenvector u is taken out and propagated exactly:
+//   exp(-iH) c = e^{-i mu} a u + e^{-ic} sum_k ... T_k(X) (c - a u),  a = u^H c.
+// Each column group then has two more threads, j = N and N + 1, that run the
+// rows' loop over i with Re u and Im u in place of a column of W: they form
+// A = sum_i Re u_i t_i and B = sum_i Im u_i t_i with the same instructions as
+// the rows (an FP64 warp instruction costs its pipe slot whatever its active
+// lanes, so a separate loop would cost a whole pass), and u^H t = (Re A +
+// Im B) + i (Im A - Re B).  The projection needs no extra barrier: with s =
+// u^H T_k, T_k' = T_k - s u and, u being an eigenvector of X with X u = mu_x
+// u, X T_k' = X T_k - s mu_x u.  Every order projects T_k (and carries the
+// projected T_k as the next T_{k-1}), so rounding cannot let the u component
+// grow with the series' value at mu (about 13^k for the double well).  The
+// first order's s is a; the rows correct the J_0 term of the sum by -J_0 a
+// u.  Without the flag (or s.defl null: no extra threads) the arithmetic is
+// the plain series.
 template <int EPT, class RT>
 __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int64_t t_base)
 {
@@ -344,20 +447,35 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
     const int64_t t = traj_of(s, t_base + blockIdx.y);
     if (t < 0 || (s.status[t] & ST_DONE)) return;
     const int N = s.N, Ne = s.Ne;
+    const int NG = s.defl ? N + 2 : N;  // threads per column group
     const int NB = G * EPT, W2 = 2 * NB;
-    const int g = threadIdx.x / N;
-    const int j = threadIdx.x - g * N;
-    const bool act = g < G;
+    const int g = threadIdx.x / NG;
+    const int j = threadIdx.x - g * NG;
+    const bool inr = g < G;
+    const bool act = inr && j < N;         // a row thread
     const int e0 = blockIdx.x * NB + g * EPT;  // first electron of this thread
     const double *cb = s.cheb + t * kChebStride;
     const double c = cb[0], rho = cb[1];
     const int K = (int)cb[2];
     const double *J = cb + 3;
+    const double *df = s.defl ? s.defl + t * (2 * (int64_t)N + 2) : nullptr;
+    const bool defl = df && df[0] != 0.0;  // uniform over the CTA
+    const bool dot = defl && inr && j >= N;  // j = N: A, j = N + 1: B
+    RT *sdot = tk + (size_t)N * W2;           // [G][EPT][A, B][re, im] of the order
+    RT *sa = sdot + 2 * W2;                   // the same for T_0 = c
+    RT *su = sa + 2 * W2;                     // [2N + 1] Re u, Im u, mu_x = (mu - c) / rho
     const RT inv_rho = (RT)(rho > 0.0 ? 1.0 / rho : 0.0);
     const RT *__restrict__ W = reinterpret_cast<const RT *>(s.scratch + t * s.scratch_stride);
+    // the coefficients of thread j: column j of W (stride N), or Re u / Im u
+    const RT *wb = act ? W + j : (dot ? reinterpret_cast<const RT *>(df + 2 + (int64_t)(j - N) * N) : W);
+    const int ws = act ? N : 1;
     CT *C = reinterpret_cast<CT *>(s.C) + (int64_t)t * Ne * N;
     const RT Lc = (RT)(act ? 0.5 * dt * (s.lam_prev[t * N + j] + s.lam[t * N + j]) - c : 0.0);
-    RT *myrow = tk + j * W2 + 2 * EPT * g;
+    if (defl) {
+        for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) su[i] = (RT)df[2 + i];
+        if (threadIdx.x == 0) su[2 * N] = (RT)((df[1] - c) * (rho > 0.0 ? 1.0 / rho : 0.0));
+    }
+    RT *myrow = tk + (act ? j : 0) * W2 + 2 * EPT * g;
 
     RT tp[2 * EPT], acc[2 * EPT];
     const RT J0 = (RT)J[0];
@@ -381,14 +499,29 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
         RT y[2 * EPT];
 #pragma unroll
         for (int q = 0; q < 2 * EPT; ++q) y[q] = 0;
-        if (act) {
+        if (act || dot) {
             const RT *col = tk + 2 * EPT * g;
+            const RT *__restrict__ wp = wb;
 #pragma unroll 4
             for (int i = 0; i < N; ++i) {
-                const RT w = W[(int64_t)i * N + j];  // W_ij = -W_ji
+                const RT w = *wp;  // a row: W_ij = -W_ji; else Re u_i or Im u_i
+                wp += ws;
                 const RT *row = col + i * W2;
 #pragma unroll
                 for (int q = 0; q < 2 * EPT; ++q) y[q] = fma(w, row[q], y[q]);
+            }
+        }
+        if (dot) {
+            const int ab = j - N;  // 0: A, 1: B
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                RT *d = sdot + (g * EPT + e) * 4 + 2 * ab;
+                d[0] = y[2 * e];
+                d[1] = y[2 * e + 1];
+                if (k == 0) {
+                    d[2 * W2] = y[2 * e];
+                    d[2 * W2 + 1] = y[2 * e + 1];
+                }
             }
         }
         RT own[2 * EPT];
@@ -402,10 +535,32 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
             const int ph = (k + 1) & 3;  // (-i)^(k+1)
 #pragma unroll
             for (int e = 0; e < EPT; ++e) {
+                RT sr = 0, si = 0, ur_j = 0, ui_j = 0, mux = 0;
+                if (defl) {
+                    // s = u^H T_k = (Re A + Im B) + i (Im A - Re B)
+                    const RT *d = sdot + (g * EPT + e) * 4;
+                    sr = d[0] + d[3];
+                    si = d[1] - d[2];
+                    ur_j = su[j];
+                    ui_j = su[N + j];
+                    mux = su[2 * N];
+                }
                 // (X t)_j = ((L_j - c) t_j - i (W t)_j) / rho and (W t)_j = -y.
                 // Explicit FMAs fix the rounding independently of the CTA shape.
-                const RT xr = fma(Lc, own[2 * e], -y[2 * e + 1]) * inv_rho;
-                const RT xi = fma(Lc, own[2 * e + 1], y[2 * e]) * inv_rho;
+                RT xr = fma(Lc, own[2 * e], -y[2 * e + 1]) * inv_rho;
+                RT xi = fma(Lc, own[2 * e + 1], y[2 * e]) * inv_rho;
+                if (defl) {
+                    // s u_j and the projected T_k and X T_k
+                    const RT pr = fma(sr, ur_j, -(si * ui_j)), pi = fma(sr, ui_j, si * ur_j);
+                    own[2 * e] -= pr;
+                    own[2 * e + 1] -= pi;
+                    xr = fma(-mux, pr, xr);
+                    xi = fma(-mux, pi, xi);
+                    if (k == 0) {  // s = a: the J_0 term becomes J_0 (c - a u)
+                        acc[2 * e] = fma(-J0, pr, acc[2 * e]);
+                        acc[2 * e + 1] = fma(-J0, pi, acc[2 * e + 1]);
+                    }
+                }
                 RT nr, ni;
                 if (k == 0) {
                     nr = xr;
@@ -439,6 +594,9 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
         double scd, ccd;
         sincos(c, &scd, &ccd);
         const RT sc = (RT)scd, cc = (RT)ccd;
+        double smd = 0.0, cmd = 1.0;
+        if (defl) sincos(df[1], &smd, &cmd);
+        const RT sm = (RT)smd, cm = (RT)cmd;
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
             if (e0 + e < Ne) {
@@ -446,6 +604,16 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
                 CT out;
                 out.x = fma(cc, ar, sc * ai);
                 out.y = fma(cc, ai, -(sc * ar));
+                if (defl) {
+                    // + e^{-i mu} a u_j
+                    const RT ur_j = su[j], ui_j = su[N + j];
+                    const RT *d = sa + (g * EPT + e) * 4;
+                    const RT are = d[0] + d[3], aim = d[1] - d[2];
+                    const RT br = fma(are, ur_j, -(aim * ui_j));
+                    const RT bi = fma(are, ui_j, aim * ur_j);
+                    out.x += fma(cm, br, sm * bi);
+                    out.y += fma(cm, bi, -(sm * br));
+                }
                 C[(int64_t)(e0 + e) * N + j] = out;
             }
         }
@@ -1266,26 +1434,35 @@ cudaError_t launch_coupling(const DevState &s, double dt, double mass, double to
         const size_t smem = (size_t)(32 + s.N) * sizeof(double) + (size_t)8 * s.N * sizeof(float);
         k_build_w_f32<<<(unsigned)s.n, threads, smem, st>>>(s, dt, mass, tol);
     } else {
-        k_build_w<<<(unsigned)s.n, threads, (size_t)(4 * s.N + 32) * sizeof(double), st>>>(s, dt, mass, tol);
+        k_build_w<<<(unsigned)s.n, threads, (size_t)(8 * s.N + 32) * sizeof(double), st>>>(s, dt, mass, tol);
     }
     return cudaGetLastError();
 }
 
+// Threads of a k_cheb CTA: G column groups of N rows, plus the two
+// projection threads of each group when the propagator deflates, rounded up
+// to whole warps.
+int cheb_threads(int N, int G, bool defl)
+{
+    return (G * (N + (defl ? 2 : 0)) + 31) & ~31;
+}
+
 // Column-group shape of k_cheb: EPT electrons per thread and G groups per
-// CTA, chosen to fill warps (rows x groups close to a multiple of 32) and to
-// waste no electron slots, within 1024 threads.
-void cheb_shape(int N, int Ne, int &ept, int &G)
+// CTA, chosen to fill warps (row threads close to the CTA's warps x 32, the
+// projection threads counted as overhead) and to waste no electron slots,
+// within 1024 threads.
+void cheb_shape(int N, int Ne, int &ept, int &G, bool defl)
 {
     double best = -1.0;
     ept = 1;
     G = 1;
     for (int e = 2; e >= 1; --e) {
-        for (int g = 1; g * N <= 1024; ++g) {
+        for (int g = 1; cheb_threads(N, g, defl) <= 1024; ++g) {
             const int nb = g * e;
             if (nb > 2 * Ne + 1) break;
-            const int thr = g * N, thr32 = (thr + 31) & ~31;
+            const int thr32 = cheb_threads(N, g, defl);
             const int blocks = (Ne + nb - 1) / nb;
-            const double eff = (double)thr / thr32 * (double)Ne / (blocks * nb);
+            const double eff = (double)(g * N) / thr32 * (double)Ne / (blocks * nb);
             // prefer larger CTAs at equal efficiency (fewer W reloads)
             const double score = eff + 1e-4 * nb;
             if (score > best) {
@@ -1329,14 +1506,15 @@ cudaError_t launch_cheb(const DevState &s, double dt, bool mixed, cudaStream_t s
         return cudaSuccess;
     }
     int ept, G;
-    cheb_shape(s.N, s.Ne, ept, G);
+    cheb_shape(s.N, s.Ne, ept, G, s.defl != nullptr);
     if (s.cheb_ept > 0 && s.cheb_G > 0) {
         ept = s.cheb_ept;
         G = s.cheb_G;
     }
     const int nb = G * ept;
-    const size_t smem = (size_t)s.N * 2 * nb * sizeof(double);
-    const int threads = (G * s.N + 31) & ~31;
+    // T_k [N][2 nb]; when deflating (A, B) of T_k and of c [nb][4] each, u and mu_x
+    const size_t smem = ((size_t)s.N * 2 * nb + (s.defl ? 8 * nb + 2 * s.N + 1 : 0)) * sizeof(double);
+    const int threads = cheb_threads(s.N, G, s.defl != nullptr);
     for (int64_t t0 = 0; t0 < s.n; t0 += 65535) {
         const int64_t cnt = (s.n - t0 < 65535) ? s.n - t0 : 65535;
         dim3 grid((unsigned)((s.Ne + nb - 1) / nb), (unsigned)cnt);

@@ -72,7 +72,8 @@ class _Options(ctypes.Structure):
                 ("record_every", ctypes.c_int), ("max_records", ctypes.c_int),
                 ("z_done", ctypes.c_double), ("compact_every", ctypes.c_int),
                 ("propagator", ctypes.c_int), ("traj_base", ctypes.c_int64),
-                ("prop_tol", ctypes.c_double), ("norm_tol", ctypes.c_double)]
+                ("prop_tol", ctypes.c_double), ("norm_tol", ctypes.c_double),
+                ("no_deflation", ctypes.c_int)]
 
 
 EXPORTS = ["iesh_create", "iesh_destroy", "iesh_bath", "iesh_init_state", "iesh_set_state",
@@ -228,7 +229,7 @@ class Context:
 
     def __init__(self, model, max_traj, precision=PREC_FP64, skip_bound=False, record_every=0,
                  max_records=0, z_done=0.0, compact_every=0, stream=None, propagator=PROP_AVERAGED,
-                 traj_base=0, prop_tol=0.0, norm_tol=0.0):
+                 traj_base=0, prop_tol=0.0, norm_tol=0.0, deflation=True):
         self.L = load()
         self.model = dict(model)
         self.N = int(model["M"]) + 1
@@ -238,9 +239,10 @@ class Context:
         self.n = 0
         self._m = model_struct(model)
         self.propagator = int(propagator)
+        self.deflation = bool(deflation)
         self._o = _Options(precision, int(bool(skip_bound)), int(record_every), int(max_records),
                            float(z_done), int(compact_every), self.propagator, int(traj_base),
-                           float(prop_tol), float(norm_tol))
+                           float(prop_tol), float(norm_tol), int(not deflation))
         self.stream = current_stream_handle() if stream is None else stream
         h = _vp()
         rc = self.L.iesh_create(ctypes.byref(h), ctypes.byref(self._m), ctypes.byref(self._o),

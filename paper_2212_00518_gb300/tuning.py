@@ -20,11 +20,13 @@ from . import iesh as _I
 _CACHE = {}
 
 
-def cheb_candidates(N, Ne, limit=6, precision=0):
+def cheb_candidates(N, Ne, limit=6, precision=0, deflation=True):
     """Propagator shapes ranked by lane and electron-slot efficiency.
 
-    FP64: (ept, G) with ept 1 or 2 electrons per thread and G * N <= 1024
-    threads.  Mixed precision: (4, G), 4 orbitals x 4 electrons per thread
+    FP64: (ept, G) with ept 1 or 2 electrons per thread and G * NG threads,
+    rounded up to whole warps, within 1024; NG = N + 2 with deflation (two
+    threads per column group form the projections on the isolated
+    eigenvector), else N.  Mixed precision: (4, G), 4 orbitals x 4 electrons per thread
     and G * ceil(N / 4) <= 256 threads, two buffers of Np x (8G + 1) floats
     (Np = N rounded up to a multiple of 4) and a ring of 3 x 16 rows of W
     (48 Np floats) in at most 110 KiB; or (32, G), 8 orbitals x 4
@@ -47,15 +49,15 @@ def cheb_candidates(N, Ne, limit=6, precision=0):
                 out.append((eff, nb, ept, G))
         out.sort(key=lambda r: (-r[0], -r[1]))
         return [(ept, G) for _, _, ept, G in out[:limit]]
+    NG = N + 2 if deflation else N
     for ept in (2, 1):
         for G in range(1, 1024 // N + 1):
             nb = G * ept
-            if nb > 2 * Ne + 1:
+            thr32 = (G * NG + 31) // 32 * 32
+            if nb > 2 * Ne + 1 or thr32 > 1024:
                 break
-            thr = G * N
-            thr32 = (thr + 31) // 32 * 32
             blocks = -(-Ne // nb)
-            eff = thr / thr32 * Ne / (blocks * nb)
+            eff = G * N / thr32 * Ne / (blocks * nb)
             out.append((eff, nb, ept, G))
     out.sort(key=lambda r: (-r[0], -r[1]))
     return [(ept, G) for _, _, ept, G in out[:limit]]
@@ -67,12 +69,13 @@ def autotune(ctx, x, p, occ, C, dt, steps=3, seed=0):
     Returns dict(cheb=(ept, G), hop_threads=..., times={...})."""
     import torch
 
-    key = (ctx.N, ctx.Ne, ctx.precision, int(x.shape[0]))
+    key = (ctx.N, ctx.Ne, ctx.precision, int(x.shape[0]), ctx.deflation)
     if key in _CACHE:
         best = _CACHE[key]
         ctx.set_kernel_shape(best["cheb"][0], best["cheb"][1], best["hop_threads"])
         return best
-    scratch = _I.Context(ctx.model, int(x.shape[0]), precision=ctx.precision, stream=ctx.stream)
+    scratch = _I.Context(ctx.model, int(x.shape[0]), precision=ctx.precision, stream=ctx.stream,
+                         deflation=ctx.deflation)
     times_cheb, times_hop = {}, {}
 
     def trial(ept, G, hop):
@@ -86,7 +89,9 @@ def autotune(ctx, x, p, occ, C, dt, steps=3, seed=0):
         return prof["propagate"][0], prof["hop"][0]
 
     default = scratch.kernel_shape()[:2]
-    cands = [default] if default[0] in (8, 16) else cheb_candidates(ctx.N, ctx.Ne, precision=ctx.precision)
+    cands = [default] if default[0] in (8, 16) else cheb_candidates(
+        ctx.N, ctx.Ne, precision=ctx.precision,
+        deflation=ctx.deflation and ctx.precision == _I.PREC_FP64 and ctx.propagator == _I.PROP_AVERAGED)
     for ept, G in cands:
         times_cheb[(ept, G)] = trial(ept, G, 0)[0]
     for hop in (0, 256, 512):

@@ -117,7 +117,8 @@ def test_tuner_shapes_within_documented_limits(N):
     threads and 8 Np (8G + 1) + 192 Np bytes of shared memory (two buffers
     and the ring of W rows) within 110 KiB for G > 1, or (32, G) with
     G * ceil(ceil(N/4)/2) <= 256 and the same bytes within 220 KiB; FP64
-    (ept, G) with ept in {1, 2} and G * N <= 1024."""
+    (ept, G) with ept in {1, 2} and G * (N + 2) <= 1024 (G * N without
+    deflation)."""
     from paper_2212_00518_gb300 import tuning
     from paper_2212_00518_gb300 import iesh as I
     Np = -(-N // 4) * 4
@@ -131,5 +132,8 @@ def test_tuner_shapes_within_documented_limits(N):
             rows, cap = (nq, 110) if ept == 4 else (-(-nq // 2), 220)
             assert G * rows <= 256
             assert G == 1 or 8 * Np * (8 * G + 1) + 192 * Np <= cap * 1024
+        # deflation adds two threads per column group
         fp64 = tuning.cheb_candidates(N, Ne, precision=I.PREC_FP64)
-        assert fp64 and all(ept in (1, 2) and G * N <= 1024 for ept, G in fp64)
+        assert fp64 and all(ept in (1, 2) and G * (N + 2) <= 1024 for ept, G in fp64)
+        plain = tuning.cheb_candidates(N, Ne, precision=I.PREC_FP64, deflation=False)
+        assert plain and all(ept in (1, 2) and G * N <= 1024 for ept, G in plain)
