@@ -370,7 +370,7 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
     A(d.status, T) A(d.nstep, T) A(d.hops, T) A(d.frus, T)
     A(d.scratch, T * (size_t)d.scratch_stride)
     A(d.cheb, T * kChebStride)
-    if (!ctx->mixed && opt->propagator == IESH_PROP_AVERAGED && !opt->no_deflation)
+    if (opt->propagator == IESH_PROP_AVERAGED && !opt->no_deflation)
         A(d.defl, T * (2 * (size_t)N + 2))
     A(ctx->live, T)
     A(ctx->n_live, 1)
@@ -649,8 +649,9 @@ iesh_status iesh_set_kernel_shape(iesh_ctx *ctx, int cheb_ept, int cheb_G, int h
 {
     if (!ctx) return IESH_EINVAL;
     if (ctx->opt.precision == IESH_PREC_MIXED) {
-        const bool simt = (cheb_ept == 4 && cheb32_shape_ok(ctx->N, cheb_G, 1)) ||
-                          (cheb_ept == 32 && cheb32_shape_ok(ctx->N, cheb_G, 2));
+        const bool dfl = ctx->ds.defl != nullptr;  // the SIMT kernel deflates
+        const bool simt = (cheb_ept == 4 && cheb32_shape_ok(ctx->N, cheb_G, 1, dfl)) ||
+                          (cheb_ept == 32 && cheb32_shape_ok(ctx->N, cheb_G, 2, dfl));
         const bool tc = (cheb_ept == 8 && cheb_G == 1 && cheb_tc_eligible(ctx->N, ctx->Ne)) ||
                         (cheb_ept == 16 && cheb_G == 1 && cheb_tc16_eligible(ctx->N, ctx->Ne));
         if (!((cheb_ept == 0 && cheb_G == 0) || simt || tc))
@@ -685,7 +686,7 @@ iesh_status iesh_get_kernel_shape(iesh_ctx *ctx, int *cheb_ept, int *cheb_G, int
         } else if (ctx->opt.precision == IESH_PREC_MIXED) {
             const int qpt = ctx->N > kCheb32WideMinN ? 2 : 1;
             e = qpt == 2 ? 32 : 4;
-            cheb32_shape(ctx->N, ctx->Ne, g, qpt);
+            cheb32_shape(ctx->N, ctx->Ne, g, qpt, ctx->ds.defl != nullptr);
         } else {
             cheb_shape(ctx->N, ctx->Ne, e, g, ctx->ds.defl != nullptr);
         }

@@ -49,9 +49,10 @@ constexpr size_t kCheb32WideMaxSmem = 220 * 1024;
 constexpr int kCheb32WideMinN = 224;  // default to two row quads per thread past this N
 constexpr int kCheb32WRows = 16; // rows of W per chunk staged in shared memory
 constexpr int kCheb32WRing = 3;  // chunks in the ring (filled 2 ahead)
-size_t cheb32_smem_bytes(int N, int G);
-void cheb32_shape(int N, int Ne, int &G, int qpt = 1);
-bool cheb32_shape_ok(int N, int G, int qpt);
+size_t cheb32_smem_bytes(int N, int G, bool defl = false);
+void cheb32_shape(int N, int Ne, int &G, int qpt = 1, bool defl = false);
+bool cheb32_shape_ok(int N, int G, int qpt, bool defl = false);
+bool mixed_deflates(const DevState &s);
 // FP32 propagator on the tensor cores (3xTF32), N <= 128 and Ne <= 56
 constexpr size_t kChebTcMaxSmem = 224 * 1024;
 size_t cheb_tc_smem_bytes(int N, int Ne);

@@ -208,12 +208,19 @@ __global__ void k_force(DevState s)
 // R_k - |W_top,k|).  The Chebyshev series then only needs to cover [lo, hb]
 // if the component along mu's eigenvector u is propagated exactly, as e^{-i
 // mu} (u^H c) u; the bulk half-width is typically a fraction of the full one
-// when the adsorbate level sits far from the band (K 14 -> 10 at 1e-15 for
-// the double well).  u comes from the power iteration with the shift sigma =
-// centre of [lo, hb], whose convergence factor is the bulk half-width over
-// mu - sigma, to a residual |H u - mu u| <= 1e-14 |mu - sigma|; without
-// convergence within kDeflIter iterations, or when the deflated series is
-// not at least kDeflGain terms shorter, the full interval is used.
+// when the adsorbate level sits far from the band (K 14 -> 9 at 1e-15 for
+// the double well).  u comes from a diagonally preconditioned fixed-point
+// iteration (the Jacobi correction of Davidson's method): u_top = 1, mu the
+// Rayleigh quotient, r = H u - mu u, u_k -= r_k / (L_k - mu) for k != top.
+// At the eigenvector it is a fixed point, and it contracts by max_k R'_k /
+// (mu - L_k) < 1, R'_k row k's radius without the top column, which the
+// disc test bounds below 1 (on the double well the band rows barely couple
+// and three iterations reach the tolerance, against about ten for the
+// shifted power iteration, whose factor is the bulk half-width over mu minus
+// the bulk centre).  It stops at a residual |H u - mu u| <= 1e-14 |mu -
+// sigma| |u|, sigma the centre of [lo, hb]; without convergence within
+// kDeflIter iterations, or when the deflated series is not at least
+// kDeflGain terms shorter, the full interval is used.
 constexpr int kDeflIter = 48;
 constexpr int kDeflGain = 2;
 
@@ -266,20 +273,23 @@ __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double m
         double b = -__longlong_as_double(0x7ff0000000000000ll);
         for (int k = threadIdx.x; k < top; k += blockDim.x) b = fmax(b, hb_s[k]);
         b = block_max(b, red);
-        const double top_lo = hb_s[top];
-        if (top_lo > b && cheb_terms(0.5 * (b - lo), tol) + kDeflGain <= cheb_terms(0.5 * (hi - lo), tol)) {
-            // power iteration for the top eigenvector, thread j < N owns u_j
+        // one thread takes the decision (the term counts are FP64 loops)
+        __shared__ int go;
+        if (threadIdx.x == 0)
+            go = hb_s[top] > b && cheb_terms(0.5 * (b - lo), tol) + kDeflGain <= cheb_terms(0.5 * (hi - lo), tol);
+        __syncthreads();
+        if (go) {
             const double sigma = 0.5 * (lo + b);
             const int j = threadIdx.x;
             const bool rj = j < N;
-            const double Lj = rj ? Lk_s[j] - sigma : 0.0;
+            const double Lj = rj ? Lk_s[j] : 0.0;
             if (rj) {
                 ur[j] = j == top ? 1.0 : 0.0;
                 ui[j] = 0.0;
             }
             __syncthreads();
             for (int it = 0; it < kDeflIter; ++it) {
-                double vr = 0.0, vi = 0.0;
+                double hr = 0.0, hv = 0.0;
                 if (rj) {
                     // (W u)_j = -sum_k W[k N + j] u_k (W antisymmetric; column reads coalesce)
                     double wr = 0.0, wi = 0.0;
@@ -288,23 +298,30 @@ __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double m
                         wr = fma(-w, ur[k], wr);
                         wi = fma(-w, ui[k], wi);
                     }
-                    // (H - sigma) u = (L - sigma) u - i W u
-                    vr = fma(Lj, ur[j], wi);
-                    vi = fma(Lj, ui[j], -wr);
+                    // H u = L u - i W u
+                    hr = fma(Lj, ur[j], wi);
+                    hv = fma(Lj, ui[j], -wr);
                 }
-                const double rq = block_sum(rj ? fma(ur[j], vr, ui[j] * vi) : 0.0, red);  // u^H (H - sigma) u
-                const double nv = block_sum(fma(vr, vr, vi * vi), red);
-                const double er = rj ? fma(-rq, ur[j], vr) : 0.0, ei = rj ? fma(-rq, ui[j], vi) : 0.0;
+                const double num = block_sum(rj ? fma(ur[j], hr, ui[j] * hv) : 0.0, red);  // u^H H u
+                const double den = block_sum(rj ? fma(ur[j], ur[j], ui[j] * ui[j]) : 0.0, red);
+                const double m = num / den;
+                const double er = rj ? fma(-m, ur[j], hr) : 0.0, ei = rj ? fma(-m, ui[j], hv) : 0.0;
                 const double res = block_sum(fma(er, er, ei * ei), red);
-                if (res <= 1e-28 * rq * rq) {  // uniform: every thread holds the same sums
-                    deflate = rq > 0.0;
-                    mu = sigma + rq;
+                const double gap = m - sigma;
+                if (res <= 1e-28 * gap * gap * den) {  // uniform: every thread holds the same sums
+                    deflate = gap > 0.0;
+                    mu = m;
+                    if (rj) {
+                        const double inv = 1.0 / sqrt(den);
+                        ur[j] *= inv;
+                        ui[j] *= inv;
+                    }
                     break;
                 }
-                const double inv = 1.0 / sqrt(nv);
-                if (rj) {
-                    ur[j] = vr * inv;
-                    ui[j] = vi * inv;
+                if (rj && j != top) {
+                    const double d = 1.0 / (Lj - m);
+                    ur[j] = fma(-er, d, ur[j]);
+                    ui[j] = fma(-ei, d, ui[j]);
                 }
                 __syncthreads();
             }
@@ -330,7 +347,20 @@ __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double m
 // is then the FP32 pole difference (a table rounded once from FP64) plus the
 // difference of the small offsets, so nearly degenerate pairs keep FP32
 // relative accuracy.  The numerators are formed in FP32.
-__global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, double mass, double tol)
+// dfl (the SIMT propagator k_cheb_f32t deflates): W rows are padded to Np =
+// N + 2 rounded up to 4, and when the top level is isolated (the test of
+// k_build_w) its eigenvector u of the FP32 generator is computed in FP32, to
+// a residual |H u - mu u| <= kDeflRes32
+// |mu - sigma|, about 4 FP32 ulps (the computed residual's own rounding is
+// about one ulp of mu at the top component; one or two iterations on the
+// double well, whose top level couples weakly): the exact term then errs by
+// at most |u^H c| kDeflRes32 |mu - sigma| per step; the iteration is the
+// preconditioned one of k_build_w, in FP32 on H - sigma; Re u and Im u go to the padding columns N and N + 1 of W,
+// where the propagator's row threads of those two rows form u^H T_k in its
+// matvec, and to s.defl as for FP64.
+constexpr float kDeflRes32 = 2.5e-7f;
+
+__global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, double mass, double tol, int dfl)
 {
     extern __shared__ double sh[];
     const int64_t t = traj_of(s, blockIdx.x);
@@ -342,6 +372,8 @@ __global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, doub
     float *lmh = qf + 2 * N;                           // [2][N] lam - h
     float *tau = lmh + 2 * N;                          // [2][N] lam - eps_o
     int *org = reinterpret_cast<int *>(tau + 2 * N);   // [2][N] o
+    double *hb_s = reinterpret_cast<double *>(org + 2 * N);  // [N] deflation: disc ends
+    float *ur = reinterpret_cast<float *>(hb_s + N), *ui = ur + N;  // [N] each
     for (int r = threadIdx.x; r < N; r += blockDim.x) {
         double lsum = 0.0;
         for (int gi = 0; gi < 2; ++gi) {
@@ -365,7 +397,7 @@ __global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, doub
     const float a0 = (float)(0.5 * dt * s.vprev[t]), a1 = (float)(0.5 * dt * (s.p[t] / mass));
     __syncthreads();
     float *W = reinterpret_cast<float *>(s.scratch + t * s.scratch_stride);  // [N][Np]
-    const int Np = (N + 3) & ~3;
+    const int Np = ((dfl ? N + 2 : N) + 3) & ~3;
     const float *__restrict__ E = s.epsdiff;  // [M][M] eps_a - eps_b
     double lo = __longlong_as_double(0x7ff0000000000000ll), hi = -lo;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
@@ -392,10 +424,84 @@ __global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, doub
             for (int j = 0; j < N; ++j) W[(int64_t)j * Np + N + k] = 0.0f;  // row padding
         lo = fmin(lo, Lsum[k] - R);
         hi = fmax(hi, Lsum[k] + R);
+        if (dfl) hb_s[k] = k == N - 1 ? Lsum[k] - R : Lsum[k] + R - fabs((double)W[(int64_t)(N - 1) * Np + k]);
     }
     lo = block_min(lo, red);
     hi = block_max(hi, red);
-    if (threadIdx.x == 0) cheb_setup(s, t, lo, hi, tol);
+    double *df = (dfl && s.defl) ? s.defl + t * (2 * (int64_t)N + 2) : nullptr;
+    bool deflate = false;
+    double hb = hi, mu = 0.0;
+    if (df && N >= 3 && N <= (int)blockDim.x) {
+        const int top = N - 1;
+        double b = -__longlong_as_double(0x7ff0000000000000ll);
+        for (int k = threadIdx.x; k < top; k += blockDim.x) b = fmax(b, hb_s[k]);
+        b = block_max(b, red);  // also orders the W stores before the reads below
+        __shared__ int go;  // one thread takes the decision (the term counts are FP64 loops)
+        if (threadIdx.x == 0)
+            go = hb_s[top] > b && cheb_terms(0.5 * (b - lo), tol) + kDeflGain <= cheb_terms(0.5 * (hi - lo), tol);
+        __syncthreads();
+        if (go) {
+            // the preconditioned iteration of k_build_w, on H - sigma in FP32
+            const double sigma = 0.5 * (lo + b);
+            const int j = threadIdx.x;
+            const bool rj = j < N;
+            const float Lj = rj ? (float)(Lsum[j] - sigma) : 0.f;
+            if (rj) {
+                ur[j] = j == top ? 1.f : 0.f;
+                ui[j] = 0.f;
+            }
+            __syncthreads();
+            for (int it = 0; it < kDeflIter; ++it) {
+                float hr = 0.f, hv = 0.f;
+                if (rj) {
+                    float wr = 0.f, wi = 0.f;  // (W u)_j = -sum_k W[k Np + j] u_k
+                    for (int k = 0; k < N; ++k) {
+                        const float w = W[(int64_t)k * Np + j];
+                        wr = fmaf(-w, ur[k], wr);
+                        wi = fmaf(-w, ui[k], wi);
+                    }
+                    hr = fmaf(Lj, ur[j], wi);  // (H - sigma) u
+                    hv = fmaf(Lj, ui[j], -wr);
+                }
+                const double num = block_sum(rj ? (double)fmaf(ur[j], hr, ui[j] * hv) : 0.0, red);
+                const double den = block_sum(rj ? (double)fmaf(ur[j], ur[j], ui[j] * ui[j]) : 0.0, red);
+                const float m = (float)(num / den);  // Rayleigh quotient of H - sigma
+                const float er = rj ? fmaf(-m, ur[j], hr) : 0.f, ei = rj ? fmaf(-m, ui[j], hv) : 0.f;
+                const double res = block_sum((double)fmaf(er, er, ei * ei), red);
+                if (res <= (double)kDeflRes32 * kDeflRes32 * m * m * den) {  // uniform
+                    deflate = m > 0.f;
+                    mu = sigma + (double)m;
+                    if (rj) {
+                        const float inv = (float)(1.0 / sqrt(den));
+                        ur[j] *= inv;
+                        ui[j] *= inv;
+                    }
+                    break;
+                }
+                if (rj && j != top) {
+                    const float d = 1.f / (Lj - m);
+                    ur[j] = fmaf(-er, d, ur[j]);
+                    ui[j] = fmaf(-ei, d, ui[j]);
+                }
+                __syncthreads();
+            }
+            if (deflate) hb = b;
+        }
+    }
+    if (threadIdx.x == 0) {
+        cheb_setup(s, t, lo, hb, tol);
+        if (df) {
+            df[0] = deflate ? 1.0 : 0.0;
+            df[1] = mu;
+        }
+    }
+    if (deflate)
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            W[(int64_t)i * Np + N] = ur[i];
+            W[(int64_t)i * Np + N + 1] = ui[i];
+            df[2 + i] = ur[i];
+            df[2 + N + i] = ui[i];
+        }
 }
 
 // ============================================================ propagator
@@ -640,17 +746,25 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
 // gap after every row quad puts the row quads of consecutive threads 4
 // banks apart, so the per-thread row accesses of the recurrence are
 // conflict-free float4 accesses.
+// Deflation (dfl, s.defl; see k_build_w and k_cheb): W carries Re u and Im u
+// as rows N and N + 1, so the thread of those rows forms A = sum_i Re u_i
+// t_i and B = sum_i Im u_i t_i in the matvec like any row, and publishes
+// them (one more barrier per order); s_k = u^H T_k = (Re A + Im B) + i (Im
+// A - Re B).  The rows then use X T_k' = X T_k - s_k mu_x u and, for the
+// recurrence, T_{k-1}' = T_{k-1} - s_{k-1} u (the buffer holds T_{k-1} as
+// computed, so s is double-buffered by order).
 __device__ __forceinline__ int cheb32_row(int j, int W2) { return j * W2 + ((j >> 2) << 2); }
 
 template <int CE, int QPT>
-__global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1) k_cheb_f32t(DevState s, double dt, int G, int64_t t_base)
+__global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1)
+    k_cheb_f32t(DevState s, double dt, int G, int64_t t_base, int dfl)
 {
     constexpr int RQ = 4 * QPT, NR = 2 * CE, NV = NR / 4;  // NV float4 per row
     extern __shared__ __align__(16) unsigned char cheb32_smem[];
     const int64_t t = traj_of(s, t_base + blockIdx.y);
     if (t < 0 || (s.status[t] & ST_DONE)) return;
-    const int N = s.N, Ne = s.Ne, Np = (N + 3) & ~3;
-    const int nq = (N + 3) / 4, nqh = (nq + QPT - 1) / QPT;
+    const int N = s.N, Ne = s.Ne, Nr = dfl ? N + 2 : N, Np = (Nr + 3) & ~3;  // Nr: rows of W
+    const int nq = (Nr + 3) / 4, nqh = (nq + QPT - 1) / QPT;
     const int W2 = NR * G;
     float *buf0 = reinterpret_cast<float *>(cheb32_smem);
     float *buf1 = buf0 + cheb32_row(Np, W2);
@@ -672,7 +786,7 @@ __global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1) k_cheb_f32t(DevState s,
     const double *J = cb + 3;
     // per-trajectory scalars in FP32, formed once (FP64 work costs every warp
     // that issues it): 2 J_k, 1 / rho, sin c, cos c
-    __shared__ float s_cj[kChebMax], s_sc[3];
+    __shared__ float s_cj[kChebMax], s_sc[5];
     for (int q = threadIdx.x; q <= K; q += blockDim.x) s_cj[q] = (float)(2.0 * J[q]);
     if (threadIdx.x == 0) {
         double scd, ccd;
@@ -680,6 +794,10 @@ __global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1) k_cheb_f32t(DevState s,
         s_sc[0] = (float)(rho > 0.0 ? 1.0 / rho : 0.0);
         s_sc[1] = (float)scd;
         s_sc[2] = (float)ccd;
+        double smd = 0.0, cmd = 1.0;  // e^{-i mu} of the deflated level
+        if (dfl && s.defl[t * (2 * (int64_t)s.N + 2)] != 0.0) sincos(s.defl[t * (2 * (int64_t)s.N + 2) + 1], &smd, &cmd);
+        s_sc[3] = (float)smd;
+        s_sc[4] = (float)cmd;
     }
     const float *__restrict__ W = reinterpret_cast<const float *>(s.scratch + t * s.scratch_stride);
     float2 *C = reinterpret_cast<float2 *>(s.C) + (int64_t)t * Ne * N;
@@ -722,6 +840,16 @@ __global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1) k_cheb_f32t(DevState s,
         }
         cp_async_commit();
     };
+    // deflation: s_k of the order, double-buffered [2][G][CE][A, B][re, im];
+    // a = s_0 [G][CE][4]; Re u, Im u, mu_x
+    float *sdot = wring + kCheb32WRing * kCheb32WRows * Np;
+    float *sa = sdot + 8 * CE * G, *su = sa + 4 * CE * G;
+    const double *df = dfl ? s.defl + t * (2 * (int64_t)N + 2) : nullptr;
+    const bool defl = df && df[0] != 0.0;  // uniform over the CTA
+    if (defl) {
+        for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) su[i] = (float)df[2 + i];
+        if (threadIdx.x == 0) su[2 * N] = (float)((df[1] - c) * (rho > 0.0 ? 1.0 / rho : 0.0));
+    }
     for (int g = 0; g < kCheb32WRing - 1; ++g) fetch(g);
     __syncthreads();
     const float inv_rho = s_sc[0];
@@ -785,6 +913,30 @@ __global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1) k_cheb_f32t(DevState s,
                 for (int r = 0; u + r < rows; ++r) row(wp + r * Np, tp + r * W2);
             }
         }
+        const float *sk = sdot + (k & 1) * 4 * CE * G, *skm = sdot + ((k + 1) & 1) * 4 * CE * G;
+        if (defl) {
+            if (act) {
+#pragma unroll
+                for (int h = 0; h < QPT; ++h)
+#pragma unroll
+                    for (int r4 = 0; r4 < 4; ++r4) {
+                        const int j = j0(h) + r4;
+                        if (j == N || j == N + 1) {
+#pragma unroll
+                            for (int e = 0; e < CE; ++e) {
+                                float *d = sdot + (k & 1) * 4 * CE * G + (cg * CE + e) * 4 + 2 * (j - N);
+                                d[0] = y[4 * h + r4][2 * e];
+                                d[1] = y[4 * h + r4][2 * e + 1];
+                                if (k == 0) {
+                                    d[4 * CE * G * 2] = y[4 * h + r4][2 * e];  // sa
+                                    d[4 * CE * G * 2 + 1] = y[4 * h + r4][2 * e + 1];
+                                }
+                            }
+                        }
+                    }
+            }
+            __syncthreads();
+        }
         if (act) {
             const float cj = s_cj[k + 1];
             const int ph = (k + 1) & 3;  // (-i)^(k+1) = (1, 0), (0, -1), (-1, 0), (0, 1)
@@ -815,14 +967,32 @@ __global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1) k_cheb_f32t(DevState s,
 #pragma unroll
                         for (int e = 0; e < CE; ++e) {
                             // (X t)_j = ((L_j - c) t_j - i (W t)_j) / rho and (W t)_j = -y
-                            const float xr = fmaf(Lc[r], own[2 * e], -y[r][2 * e + 1]) * inv_rho;
-                            const float xi = fmaf(Lc[r], own[2 * e + 1], y[r][2 * e]) * inv_rho;
+                            float xr = fmaf(Lc[r], own[2 * e], -y[r][2 * e + 1]) * inv_rho;
+                            float xi = fmaf(Lc[r], own[2 * e + 1], y[r][2 * e]) * inv_rho;
+                            float *a = acc[r] + 2 * e;
+                            if (defl) {
+                                const int j = j0(h) + r4;
+                                const float urj = su[j], uij = su[N + j], mux = su[2 * N];
+                                const float *d = sk + (cg * CE + e) * 4;
+                                const float sr = d[0] + d[3], si = d[1] - d[2];
+                                const float pr = fmaf(sr, urj, -(si * uij)), pi = fmaf(sr, uij, si * urj);
+                                xr = fmaf(-mux, pr, xr);
+                                xi = fmaf(-mux, pi, xi);
+                                if (k == 0) {  // s_0 = a: the J_0 term becomes J_0 (c - a u)
+                                    a[0] = fmaf(-J0, pr, a[0]);
+                                    a[1] = fmaf(-J0, pi, a[1]);
+                                } else {
+                                    const float *dm = skm + (cg * CE + e) * 4;
+                                    const float qr = dm[0] + dm[3], qi = dm[1] - dm[2];
+                                    prv[2 * e] -= fmaf(qr, urj, -(qi * uij));
+                                    prv[2 * e + 1] -= fmaf(qr, uij, qi * urj);
+                                }
+                            }
                             float nr = xr, ni = xi;
                             if (k > 0) {
                                 nr = fmaf(2.f, xr, -prv[2 * e]);
                                 ni = fmaf(2.f, xi, -prv[2 * e + 1]);
                             }
-                            float *a = acc[r] + 2 * e;
                             // acc += cj (-i)^(k+1) n without a branch: (ca, cb) = cj (-i)^(k+1)
                             a[0] = fmaf(ca, nr, fmaf(-cb, ni, a[0]));
                             a[1] = fmaf(ca, ni, fmaf(cb, nr, a[1]));
@@ -849,7 +1019,17 @@ __global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1) k_cheb_f32t(DevState s,
                 for (int e = 0; e < CE; ++e)
                     if (j < N && e0 + e < Ne) {
                         const float ar = acc[r][2 * e], ai = acc[r][2 * e + 1];
-                        C[(int64_t)(e0 + e) * N + j] = make_float2(fmaf(cc, ar, sc * ai), fmaf(cc, ai, -(sc * ar)));
+                        float2 out = make_float2(fmaf(cc, ar, sc * ai), fmaf(cc, ai, -(sc * ar)));
+                        if (defl) {
+                            // + e^{-i mu} a u_j
+                            const float urj = su[j], uij = su[N + j];
+                            const float *d = sa + (cg * CE + e) * 4;
+                            const float are = d[0] + d[3], aim = d[1] - d[2];
+                            const float br = fmaf(are, urj, -(aim * uij)), bi = fmaf(are, uij, aim * urj);
+                            out.x += fmaf(s_sc[4], br, s_sc[3] * bi);
+                            out.y += fmaf(s_sc[4], bi, -(s_sc[3] * br));
+                        }
+                        C[(int64_t)(e0 + e) * N + j] = out;
                     }
             }
     }
@@ -858,24 +1038,27 @@ __global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1) k_cheb_f32t(DevState s,
 // Column groups of k_cheb_f32t: fill the CTA (row slots x groups <= 256)
 // and waste few electron slots; with one row quad per thread two CTAs must
 // fit in an SM's shared memory, with two quads one.
-size_t cheb32_smem_bytes(int N, int G)
+// With deflation W has N + 2 rows (Re u, Im u) and the CTA keeps the
+// projections (3 x 16 G floats) and u (2N + 1 floats).
+size_t cheb32_smem_bytes(int N, int G, bool defl)
 {
-    const int Np = (N + 3) & ~3;
+    const int Np = ((defl ? N + 2 : N) + 3) & ~3;
     // two buffers of padded rows and the ring of W chunks
-    return ((size_t)2 * (Np * 8 * G + Np) + (size_t)kCheb32WRing * kCheb32WRows * Np) * sizeof(float);
+    return ((size_t)2 * (Np * 8 * G + Np) + (size_t)kCheb32WRing * kCheb32WRows * Np +
+            (defl ? (size_t)48 * G + 2 * N + 1 : 0)) * sizeof(float);
 }
-bool cheb32_shape_ok(int N, int G, int qpt)
+bool cheb32_shape_ok(int N, int G, int qpt, bool defl)
 {
-    const int nqh = ((N + 3) / 4 + qpt - 1) / qpt;
+    const int nqh = (((defl ? N + 2 : N) + 3) / 4 + qpt - 1) / qpt;
     return (qpt == 1 || qpt == 2) && G >= 1 && G * nqh <= 256 &&
-           cheb32_smem_bytes(N, G) <= (qpt == 1 ? kCheb32MaxSmem : kCheb32WideMaxSmem);
+           cheb32_smem_bytes(N, G, defl) <= (qpt == 1 ? kCheb32MaxSmem : kCheb32WideMaxSmem);
 }
-void cheb32_shape(int N, int Ne, int &G, int qpt)
+void cheb32_shape(int N, int Ne, int &G, int qpt, bool defl)
 {
-    const int nq = ((N + 3) / 4 + qpt - 1) / qpt;
+    const int nq = (((defl ? N + 2 : N) + 3) / 4 + qpt - 1) / qpt;
     double best = -1.0;
     G = 1;
-    for (int g = 1; g == 1 || cheb32_shape_ok(N, g, qpt); ++g) {
+    for (int g = 1; g == 1 || cheb32_shape_ok(N, g, qpt, defl); ++g) {
         if (g * nq > 256) break;
         const int nb = 4 * g, thr = g * nq, thr32 = (thr + 31) & ~31;
         const int blocks = (Ne + nb - 1) / nb;
@@ -1425,14 +1608,28 @@ cudaError_t launch_force(const DevState &s, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// The mixed path's propagator is the SIMT kernel k_cheb_f32t: requested by
+// shape (cheb_ept 4 or 32), or by default where neither tensor-core kernel
+// fits.
+static bool mixed_uses_simt(const DevState &s)
+{
+    if (s.cheb_ept == 16 || s.cheb_ept == 8) return false;
+    if (s.cheb_ept == 4 || s.cheb_ept == 32) return true;
+    return !cheb_tc16_eligible(s.N, s.Ne) && !cheb_tc_eligible(s.N, s.Ne);
+}
+
+bool mixed_deflates(const DevState &s) { return s.defl != nullptr && mixed_uses_simt(s); }
+
 cudaError_t launch_coupling(const DevState &s, double dt, double mass, double tol, bool mixed,
                             cudaStream_t st)
 {
     if (s.n == 0) return cudaSuccess;
     const int threads = round32(s.N < 256 ? s.N : 256);
     if (mixed) {
-        const size_t smem = (size_t)(32 + s.N) * sizeof(double) + (size_t)8 * s.N * sizeof(float);
-        k_build_w_f32<<<(unsigned)s.n, threads, smem, st>>>(s, dt, mass, tol);
+        // the deflation's disc ends and u only when it may run (occupancy)
+        const bool dfl = mixed_deflates(s);
+        const size_t smem = (size_t)(32 + (dfl ? 2 : 1) * s.N) * sizeof(double) + (size_t)(dfl ? 10 : 8) * s.N * sizeof(float);
+        k_build_w_f32<<<(unsigned)s.n, threads, smem, st>>>(s, dt, mass, tol, dfl ? 1 : 0);
     } else {
         k_build_w<<<(unsigned)s.n, threads, (size_t)(8 * s.N + 32) * sizeof(double), st>>>(s, dt, mass, tol);
     }
@@ -1489,17 +1686,18 @@ cudaError_t launch_cheb(const DevState &s, double dt, bool mixed, cudaStream_t s
         // (N = 256: 24.5 against 29.9 ms per step at 4096 trajectories; at
         // N = 201 it measured 29.4 against 26.2 ms)
         const int qpt = s.cheb_ept == 32 || (s.cheb_ept == 0 && s.N > kCheb32WideMinN) ? 2 : 1;
+        const bool dfl = mixed_deflates(s);
         int G;
-        cheb32_shape(s.N, s.Ne, G, qpt);
+        cheb32_shape(s.N, s.Ne, G, qpt, dfl);
         if (s.cheb_G > 0 && (s.cheb_ept == 4 || s.cheb_ept == 32)) G = s.cheb_G;
-        const int nb = 4 * G, nqh = ((s.N + 3) / 4 + qpt - 1) / qpt;
-        const size_t smem = cheb32_smem_bytes(s.N, G);
+        const int nb = 4 * G, nqh = (((dfl ? s.N + 2 : s.N) + 3) / 4 + qpt - 1) / qpt;
+        const size_t smem = cheb32_smem_bytes(s.N, G, dfl);
         const int threads = (G * nqh + 31) & ~31;
         for (int64_t t0 = 0; t0 < s.n; t0 += 65535) {
             const int64_t cnt = (s.n - t0 < 65535) ? s.n - t0 : 65535;
             dim3 grid((unsigned)((s.Ne + nb - 1) / nb), (unsigned)cnt);
-            if (qpt == 2) k_cheb_f32t<4, 2><<<grid, threads, smem, st>>>(s, dt, G, t0);
-            else k_cheb_f32t<4, 1><<<grid, threads, smem, st>>>(s, dt, G, t0);
+            if (qpt == 2) k_cheb_f32t<4, 2><<<grid, threads, smem, st>>>(s, dt, G, t0, dfl ? 1 : 0);
+            else k_cheb_f32t<4, 1><<<grid, threads, smem, st>>>(s, dt, G, t0, dfl ? 1 : 0);
             const cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }

@@ -31,15 +31,17 @@ def cheb_candidates(N, Ne, limit=6, precision=0, deflation=True):
     (Np = N rounded up to a multiple of 4) and a ring of 3 x 16 rows of W
     (48 Np floats) in at most 110 KiB; or (32, G), 8 orbitals x 4
     electrons per thread, G * ceil(ceil(N / 4) / 2) <= 256 threads, the same
-    buffers in at most 220 KiB."""
+    buffers in at most 220 KiB.  With deflation the SIMT kernel's W has N + 2
+    rows (N + 2 in place of N above) and it keeps 48 G + 2 N + 1 more floats."""
     out = []
     if precision == _I.PREC_MIXED:
-        nq = -(-N // 4)
+        nq = -(-(N + 2 if deflation else N) // 4)
         Np = 4 * nq
         # (4, G): one row quad per thread, 110 KiB; (32, G): two, 220 KiB
         for ept, nqh, cap in ((4, nq, 110), (32, -(-nq // 2), 220)):
             for G in range(1, 256 // nqh + 1):
-                if G > 1 and (2 * (Np * 8 * G + Np) + 48 * Np) * 4 > cap * 1024:
+                extra = 48 * G + 2 * N + 1 if deflation else 0
+                if G > 1 and (2 * (Np * 8 * G + Np) + 48 * Np + extra) * 4 > cap * 1024:
                     break
                 nb = 4 * G
                 if nb > 4 * Ne + 3:
@@ -91,7 +93,7 @@ def autotune(ctx, x, p, occ, C, dt, steps=3, seed=0):
     default = scratch.kernel_shape()[:2]
     cands = [default] if default[0] in (8, 16) else cheb_candidates(
         ctx.N, ctx.Ne, precision=ctx.precision,
-        deflation=ctx.deflation and ctx.precision == _I.PREC_FP64 and ctx.propagator == _I.PROP_AVERAGED)
+        deflation=ctx.deflation and ctx.propagator == _I.PROP_AVERAGED)
     for ept, G in cands:
         times_cheb[(ept, G)] = trial(ept, G, 0)[0]
     for hop in (0, 256, 512):

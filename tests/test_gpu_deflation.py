@@ -132,3 +132,56 @@ def test_every_shape_gives_the_same_bits(P):
         if ref is None:
             ref = Cs
         assert np.array_equal(Cs, ref), (ept, G)
+
+
+def _pair_mixed(P, md, n, x, p, occ, C, steps, shape=None, seed=0):
+    out = []
+    for defl in (True, False):
+        ctx = P.Context(md, n, precision=P.PREC_MIXED, deflation=defl)
+        if shape:
+            ctx.set_kernel_shape(*shape, 0)
+        ctx.set_state(x, p, occ, C.astype(np.complex64))
+        ctx.run(1.0, steps, seed=seed)
+        st = ctx.get_state()
+        st["K"] = np.asarray(ctx.propagator_terms()).copy()
+        st["hops"] = ctx.counters()[1]
+        ctx.close()
+        out.append(st)
+    return out
+
+
+@pytest.mark.parametrize("M,shape", [(200, None), (100, (4, 3)), (100, (32, 2))])
+def test_mixed_simt_deflation(P, M, shape):
+    """The SIMT FP32 propagator deflates with its own FP32 eigenvector: the
+    series is at least two terms shorter (or, where the FP32 power iteration
+    does not reach its residual, unchanged), the step agrees with the plain
+    series within the mixed path's one-step bound (C 1e-6) and with the
+    oracle's FP64 step within the same bound."""
+    md = W.double_well(M)
+    n = 128
+    x, p, occ, C = _state(md, n, 29 + M)
+    d, f = _pair_mixed(P, md, n, x, p, occ, C, 1, shape)
+    assert np.all(d["status"] == 0) and np.all(f["status"] == 0)
+    shorter = d["K"] <= f["K"] - 2
+    assert np.all(shorter | (d["K"] == f["K"]))
+    assert shorter.mean() >= 0.95, shorter.mean()
+    assert np.array_equal(d["occ"], f["occ"])
+    assert np.abs(d["C"] - f["C"]).max() <= 1e-6
+    B = O.bind(md)
+    C32 = C.astype(np.complex64).astype(np.complex128)
+    for t in (0, 5, 64, 127):
+        r = O.step_one(B, x[t], p[t], occ[t].astype(np.int32), C32[t].T, 1.0, seed=0, traj=t, n=0)
+        assert np.array_equal(d["occ"][t], r["occ"]), t
+        assert np.abs(d["C"][t].T - r["C"]).max() <= 1e-6, t
+
+
+def test_mixed_deflation_many_steps(P):
+    """30 steps: deflated and plain mixed runs take the same hops and stay
+    within the accumulated bound (30 x 1e-6)."""
+    md = W.double_well(200)
+    n = 256
+    x, p, occ, C = _state(md, n, 71)
+    d, f = _pair_mixed(P, md, n, x, p, occ, C, 30, seed=2)
+    assert np.array_equal(d["occ"], f["occ"]) and np.array_equal(d["hops"], f["hops"])
+    assert np.abs(d["C"] - f["C"]).max() <= 30e-6
+    assert np.abs(d["p"] - f["p"]).max() <= 1e-5 * np.abs(f["p"]).max()

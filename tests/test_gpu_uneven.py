@@ -209,7 +209,9 @@ def test_autotuned_shapes_keep_results(P, precision):
     for k in ("x", "p", "occ", "C"):
         assert np.array_equal(st[k], ref[k]), k
     # every SIMT candidate shape gives the same bits (for the mixed path the
-    # default is the tensor-core kernel, whose arithmetic differs)
+    # default is the tensor-core kernel, whose arithmetic differs: the SIMT
+    # kernel deflates the isolated top level and sums a shorter series, so the
+    # two differ by up to the mixed path's one-step bound, 1e-6 in C, per step)
     first = None
     for ept, G in tuning.cheb_candidates(61, 30, precision=precision):
         other = P.Context(md, n, precision=precision)
@@ -222,7 +224,7 @@ def test_autotuned_shapes_keep_results(P, precision):
             assert np.array_equal(Co, ref["C"]), (ept, G)
         elif first is None:
             first = Co
-            assert np.abs(Co - ref["C"]).max() <= 2e-6
+            assert np.abs(Co - ref["C"]).max() <= 5 * 1e-6
         else:
             assert np.array_equal(Co, first), (ept, G)
 
