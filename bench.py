@@ -41,8 +41,10 @@ TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 tensor rate
 # the named batch size, divided by it: the traffic is per-trajectory streams of C and
 # W, so it scales with the batch.  A shape or kernel not in the table reports null.
 DRAM_BYTES_PER_TRAJ = {
-    # filled from ncu captures of the kernel as it stands (deflated FP64
-    # propagator: none yet)
+    # deflated k_cheb, dram__bytes_read.sum + dram__bytes_write.sum of a
+    # 1024-trajectory capture / 1024
+    ("k_cheb_defl", 101, 50): (170.136832e6 + 50.660352e6) / 1024,
+    ("k_cheb_defl", 201, 100): (674.422784e6 + 295.774976e6) / 1024,
 }
 
 
@@ -311,7 +313,9 @@ def run_ours(args):
         t = pm / pn / 1e3 if pn else None
         prop_w, step_w = useful_flops(N, Ne)
         ach = prop_w * n / t / 1e12 if t else None
-        exe = float(np.sum(r["K"].astype(np.float64))) * 4.0 * N * N * Ne / t / 1e12 if t else None
+        # the SIMT kernel deflates: two more rows (Re u, Im u) in its matvec
+        Nr = N if r["tc"] else N + 2
+        exe = float(np.sum(r["K"].astype(np.float64))) * 4.0 * N * Nr * Ne / t / 1e12 if t else None
         ptf, src = tf32_peak()
         step_s = r["ms"] / args.steps / 1e3
         # time bound of the whole step: FP32/TF32 contractions on the tensor cores,

@@ -360,8 +360,10 @@ __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double m
 // matvec, and to s.defl as for FP64.
 constexpr float kDeflRes32 = 2.5e-7f;
 
-__global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, double mass, double tol, int dfl)
+template <bool DFL>
+__global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, double mass, double tol)
 {
+    constexpr int dfl = DFL;  // a template parameter: the plain kernel keeps its registers
     extern __shared__ double sh[];
     const int64_t t = traj_of(s, blockIdx.x);
     if (t < 0 || (s.status[t] & ST_DONE)) return;
@@ -1629,7 +1631,8 @@ cudaError_t launch_coupling(const DevState &s, double dt, double mass, double to
         // the deflation's disc ends and u only when it may run (occupancy)
         const bool dfl = mixed_deflates(s);
         const size_t smem = (size_t)(32 + (dfl ? 2 : 1) * s.N) * sizeof(double) + (size_t)(dfl ? 10 : 8) * s.N * sizeof(float);
-        k_build_w_f32<<<(unsigned)s.n, threads, smem, st>>>(s, dt, mass, tol, dfl ? 1 : 0);
+        if (dfl) k_build_w_f32<true><<<(unsigned)s.n, threads, smem, st>>>(s, dt, mass, tol);
+        else k_build_w_f32<false><<<(unsigned)s.n, threads, smem, st>>>(s, dt, mass, tol);
     } else {
         k_build_w<<<(unsigned)s.n, threads, (size_t)(8 * s.N + 32) * sizeof(double), st>>>(s, dt, mass, tol);
     }
