@@ -221,7 +221,8 @@ def run_ours(args):
     def measure(md, dt, x, p, occ, C, precision, sample_clocks=False, propagator=0, e2e=True):
         n = x.shape[0]
         c = P.Context(md, n, precision=precision, stream=stream.cuda_stream, propagator=propagator,
-                      skip_bound=args.skip_bound, traj_base=replica_traj_base(rank, n))
+                      skip_bound=args.skip_bound, traj_base=replica_traj_base(rank, n),
+                      deflation=not args.no_deflation)
         c.set_state(x, p, occ, C if precision == P.PREC_FP64 else C.astype(np.complex64))
         for _ in range(args.warmup):
             c.run(dt, 1, seed)
@@ -865,6 +866,9 @@ def main():
                     help="dw: the double-well batch (default, --M/--n-traj); the others print "
                          "secondary measurements")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-deflation", dest="no_deflation", action="store_true",
+                    help="run the Chebyshev series over the whole spectrum interval (no deflation "
+                         "of the isolated top level)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

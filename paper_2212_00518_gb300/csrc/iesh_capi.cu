@@ -371,7 +371,7 @@ iesh_status iesh_create(iesh_ctx **out, const iesh_model *model, const iesh_opti
     A(d.scratch, T * (size_t)d.scratch_stride)
     A(d.cheb, T * kChebStride)
     if (opt->propagator == IESH_PROP_AVERAGED && !opt->no_deflation)
-        A(d.defl, T * (2 * (size_t)N + 2))
+        A(d.defl, T * (size_t)defl_stride(N, Ne))
     A(ctx->live, T)
     A(ctx->n_live, 1)
     A(ctx->obs, 4 * T)
@@ -649,9 +649,8 @@ iesh_status iesh_set_kernel_shape(iesh_ctx *ctx, int cheb_ept, int cheb_G, int h
 {
     if (!ctx) return IESH_EINVAL;
     if (ctx->opt.precision == IESH_PREC_MIXED) {
-        const bool dfl = ctx->ds.defl != nullptr;  // the SIMT kernel deflates
-        const bool simt = (cheb_ept == 4 && cheb32_shape_ok(ctx->N, cheb_G, 1, dfl)) ||
-                          (cheb_ept == 32 && cheb32_shape_ok(ctx->N, cheb_G, 2, dfl));
+        const bool simt = (cheb_ept == 4 && cheb32_shape_ok(ctx->N, cheb_G, 1)) ||
+                          (cheb_ept == 32 && cheb32_shape_ok(ctx->N, cheb_G, 2));
         const bool tc = (cheb_ept == 8 && cheb_G == 1 && cheb_tc_eligible(ctx->N, ctx->Ne)) ||
                         (cheb_ept == 16 && cheb_G == 1 && cheb_tc16_eligible(ctx->N, ctx->Ne));
         if (!((cheb_ept == 0 && cheb_G == 0) || simt || tc))
@@ -661,7 +660,7 @@ iesh_status iesh_set_kernel_shape(iesh_ctx *ctx, int cheb_ept, int cheb_G, int h
                         "shared-memory cap, or ept 8, G 1 for the tensor-core kernel: N <= 128, Ne <= 56)",
                         cheb_ept, cheb_G, ctx->N, ctx->Ne);
     } else if (cheb_ept < 0 || cheb_ept > 2 || cheb_G < 0 || (cheb_ept > 0) != (cheb_G > 0) ||
-               cheb_threads(ctx->N, cheb_G, ctx->ds.defl != nullptr) > 1024) {
+               cheb_G * ctx->N > 1024) {
         return fail(ctx, IESH_EINVAL, "propagator shape (%d, %d) invalid for N=%d", cheb_ept, cheb_G, ctx->N);
     }
     if (hop_threads != 0 && hop_threads != 256 && hop_threads != 512)
@@ -686,9 +685,9 @@ iesh_status iesh_get_kernel_shape(iesh_ctx *ctx, int *cheb_ept, int *cheb_G, int
         } else if (ctx->opt.precision == IESH_PREC_MIXED) {
             const int qpt = ctx->N > kCheb32WideMinN ? 2 : 1;
             e = qpt == 2 ? 32 : 4;
-            cheb32_shape(ctx->N, ctx->Ne, g, qpt, ctx->ds.defl != nullptr);
+            cheb32_shape(ctx->N, ctx->Ne, g, qpt);
         } else {
-            cheb_shape(ctx->N, ctx->Ne, e, g, ctx->ds.defl != nullptr);
+            cheb_shape(ctx->N, ctx->Ne, e, g);
         }
     }
     if (cheb_ept) *cheb_ept = e;

@@ -44,21 +44,54 @@ __device__ inline void bessel_j(double rho, int K, double *J)
     for (int k = 0; k <= K; ++k) J[k] *= sc;
 }
 
+// 1/k for k < kChebMax + 2, so that the term count needs no division (it
+// runs in one thread of a block, where each FP64 instruction costs a whole
+// warp's pipe slot).
+struct RecipTable {
+    double v[kChebMax + 2];
+    constexpr RecipTable() : v()
+    {
+        for (int k = 1; k < kChebMax + 2; ++k) v[k] = 1.0 / k;
+    }
+};
+static __constant__ RecipTable kRecip = RecipTable();
+
 // Number of Chebyshev terms for the half-width rho at tolerance tol: the
 // smallest K whose tail bound 2 sum_{k>K} (rho/2)^k / k! is below tol, at
-// most kChebMax - 2.
-__host__ __device__ inline int cheb_terms(double rho, double tol)
+// most kChebMax - 2.  The tail is bounded by the geometric series of ratio
+// (rho/2)/(K+2): 2 term / (1 - ratio) <= tol, tested as 2 term <= tol (1 -
+// ratio).
+__device__ inline int cheb_terms(double rho, double tol)
 {
     int K = 0;
-    double term = rho * 0.5;  // (rho/2)^{K+1} / (K+1)!
+    const double h = rho * 0.5;
+    double term = h;  // (rho/2)^{K+1} / (K+1)!
     while (K < kChebMax - 2) {
-        const double ratio = (rho * 0.5) / (K + 2);
-        const double tail = (ratio < 1.0) ? 2.0 * term / (1.0 - ratio) : 1e300;
-        if (tail <= tol) break;
+        const double ratio = h * kRecip.v[K + 2];
+        if (ratio < 1.0 && 2.0 * term <= tol * (1.0 - ratio)) break;
         ++K;
-        term *= (rho * 0.5) / (K + 1);
+        term *= h * kRecip.v[K + 1];
     }
     return K;
+}
+
+// Bound on the amplification, by the series over [c - rho, c + rho], of a
+// component along an eigenvector whose eigenvalue mu lies outside it:
+// |J_0| + 2 sum_{k=1..K} |J_k(rho)| |T_k(mu_x)|, mu_x = (mu - c) / rho.
+__device__ inline double cheb_amplification(const double *cb, double mu)
+{
+    const double c = cb[0], rho = cb[1];
+    const int K = (int)cb[2];
+    const double *J = cb + 3;
+    const double x = rho > 0.0 ? (mu - c) / rho : 0.0;
+    double tm = 1.0, tk = x, A = fabs(J[0]);
+    for (int k = 1; k <= K; ++k) {
+        A += 2.0 * fabs(J[k]) * fabs(tk);
+        const double tn = 2.0 * x * tk - tm;
+        tm = tk;
+        tk = tn;
+    }
+    return A;
 }
 
 // Chebyshev degree and coefficients for a spectrum inside [lo, hi] (in units

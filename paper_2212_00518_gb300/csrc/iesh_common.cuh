@@ -30,6 +30,16 @@ struct ModelDev {
 };
 
 // Device pointers of a context's state (structure of arrays).
+// Deflation record per trajectory, defl_stride doubles: [0] flag, [1] mu,
+// [2] cos mu, [3] sin mu; from kDeflHead the eigenvector u (Re u[N], Im
+// u[N]) and a = u^H c (Re a[Ne], Im a[Ne]), as doubles in FP64 contexts and
+// as packed floats in mixed ones.
+constexpr int kDeflHead = 4;
+__host__ __device__ constexpr int64_t defl_stride(int N, int Ne)
+{
+    return kDeflHead + 2 * (int64_t)N + 2 * (int64_t)Ne;
+}
+
 struct DevState {
     int N, M, Ne;
     int64_t n;                 // trajectories in the batch
@@ -45,9 +55,10 @@ struct DevState {
     double *scratch;           // [n][scratch_stride] per-trajectory workspace
     int64_t scratch_stride;    // doubles per trajectory
     double *cheb;              // [n][kChebStride]: c, rho, K, J_0..J_K
-    // FP64 one-coordinate contexts: [n][2N + 2] per trajectory: a flag, the
-    // isolated top eigenvalue mu of the generator and its eigenvector u (Re
-    // u[N], Im u[N]) when the propagator deflates it (null: never)
+    // [n][defl_stride(N, Ne)] per trajectory when the propagator deflates the
+    // isolated top level of the generator (null: never): a flag, its
+    // eigenvalue mu, its eigenvector u (Re u[N], Im u[N]) and the components
+    // a = u^H c of the electrons (Re a[Ne], Im a[Ne])
     double *defl;
     double *rec_sh, *rec_wf;   // [max_records][n]
     int record_every, max_records;
@@ -264,6 +275,30 @@ struct OpMin {
 struct OpMax {
     __device__ double operator()(double a, double b) const { return fmax(a, b); }
 };
+
+// Deflated propagation (the isolated top level of the generator, s.defl laid
+// out as defl_stride): the start value c - a u of row j of electron e and
+// the end term e^{-i mu} a u_j, in the propagator's arithmetic R (explicit
+// FMAs).
+template <class R, class CT>
+__device__ __forceinline__ CT defl_start(const double *df, int N, int Ne, int j, int e, CT v)
+{
+    const R *q = reinterpret_cast<const R *>(df + kDeflHead);
+    const R ur = q[j], ui = q[N + j], ar = q[2 * N + e], ai = q[2 * N + Ne + e];
+    v.x -= fma(ar, ur, -(ai * ui));
+    v.y -= fma(ar, ui, ai * ur);
+    return v;
+}
+template <class R, class CT>
+__device__ __forceinline__ CT defl_end(const double *df, int N, int Ne, int j, int e, R cm, R sm, CT out)
+{
+    const R *q = reinterpret_cast<const R *>(df + kDeflHead);
+    const R ur = q[j], ui = q[N + j], ar = q[2 * N + e], ai = q[2 * N + Ne + e];
+    const R br = fma(ar, ur, -(ai * ui)), bi = fma(ar, ui, ai * ur);  // a u_j
+    out.x += fma(cm, br, sm * bi);                                     // e^{-i mu} a u_j
+    out.y += fma(cm, bi, -(sm * br));
+    return out;
+}
 
 __device__ __forceinline__ double block_sum(double v, double *red)
 {

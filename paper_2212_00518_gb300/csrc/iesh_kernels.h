@@ -38,8 +38,7 @@ cudaError_t launch_hop_gj(const DevState &s, double dt, double mass, uint64_t se
 // Bath of one lead: energies and weights (Gauss-Legendre split at mu, or trapezoid)
 void lead_bath(int disc, int n, double a, double b, double mu, int n_lo, std::vector<double> &eps,
                std::vector<double> &w);
-void cheb_shape(int N, int Ne, int &ept, int &G, bool defl = false);
-int cheb_threads(int N, int G, bool defl);
+void cheb_shape(int N, int Ne, int &ept, int &G);
 // Trajectories per CTA of the eigen kernels (slots of N threads, <= 512 threads)
 int eigen_tpb(int N);
 // FP32 (mixed-precision) propagator: 4 electrons per thread, G column
@@ -49,9 +48,10 @@ constexpr size_t kCheb32WideMaxSmem = 220 * 1024;
 constexpr int kCheb32WideMinN = 224;  // default to two row quads per thread past this N
 constexpr int kCheb32WRows = 16; // rows of W per chunk staged in shared memory
 constexpr int kCheb32WRing = 3;  // chunks in the ring (filled 2 ahead)
-size_t cheb32_smem_bytes(int N, int G, bool defl = false);
-void cheb32_shape(int N, int Ne, int &G, int qpt = 1, bool defl = false);
-bool cheb32_shape_ok(int N, int G, int qpt, bool defl = false);
+size_t cheb32_smem_bytes(int N, int G);
+void cheb32_shape(int N, int Ne, int &G, int qpt = 1);
+bool cheb32_shape_ok(int N, int G, int qpt);
+// the mixed propagators deflate (k_build_w_f32<true> sets the level up)
 bool mixed_deflates(const DevState &s);
 // FP32 propagator on the tensor cores (3xTF32), N <= 128 and Ne <= 56
 constexpr size_t kChebTcMaxSmem = 224 * 1024;

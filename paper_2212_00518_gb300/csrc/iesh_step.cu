@@ -209,7 +209,12 @@ __global__ void k_force(DevState s)
 // if the component along mu's eigenvector u is propagated exactly, as e^{-i
 // mu} (u^H c) u; the bulk half-width is typically a fraction of the full one
 // when the adsorbate level sits far from the band (K 14 -> 9 at 1e-15 for
-// the double well).  u comes from a diagonally preconditioned fixed-point
+// the double well).  The propagators start the series from c - (u^H c) u,
+// which has no u component in exact arithmetic, so no later order needs a
+// projection; the u components that rounding leaves in later orders are
+// carried by the series, whose value at mu is bounded by cheb_amplification
+// (about 7 on the double well): with that bound above kDeflAmp64 (FP64) or
+// kDeflAmp32 (FP32) the full interval is used.  u comes from a diagonally preconditioned fixed-point
 // iteration (the Jacobi correction of Davidson's method): u_top = 1, mu the
 // Rayleigh quotient, r = H u - mu u, u_k -= r_k / (L_k - mu) for k != top.
 // At the eigenvector it is a fixed point, and it contracts by max_k R'_k /
@@ -223,6 +228,27 @@ __global__ void k_force(DevState s)
 // kDeflGain terms shorter, the full interval is used.
 constexpr int kDeflIter = 48;
 constexpr int kDeflGain = 2;
+constexpr double kDeflAmp64 = 1e3, kDeflAmp32 = 16.0;
+
+// Thread 0 has set up the series over the bulk interval; it keeps the
+// deflation if the series amplifies the u direction by at most amp, else it
+// sets the full interval up.  Returns the block-uniform decision.
+__device__ inline bool defl_keep(const DevState &s, int64_t t, bool deflate, double mu, double lo, double hi,
+                                 double tol, double amp, double *df, int *flag)
+{
+    if (threadIdx.x == 0) {
+        bool k = deflate && cheb_amplification(s.cheb + t * kChebStride, mu) <= amp;
+        if (deflate && !k) cheb_setup(s, t, lo, hi, tol);
+        *flag = k;
+        if (df) {
+            df[0] = k ? 1.0 : 0.0;
+            df[1] = mu;
+            if (k) sincos(mu, &df[3], &df[2]);  // once per trajectory
+        }
+    }
+    __syncthreads();
+    return *flag != 0;
+}
 
 __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double mass, double tol)
 {
@@ -265,7 +291,7 @@ __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double m
     }
     lo = block_min(lo, red);
     hi = block_max(hi, red);
-    double *df = s.defl ? s.defl + t * (2 * (int64_t)N + 2) : nullptr;
+    double *df = s.defl ? s.defl + t * defl_stride(N, s.Ne) : nullptr;
     bool deflate = false;
     double hb = hi, mu = 0.0;
     if (df && N >= 3 && N <= (int)blockDim.x) {
@@ -328,18 +354,35 @@ __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double m
             if (deflate) hb = b;
         }
     }
-    if (threadIdx.x == 0) {
-        cheb_setup(s, t, lo, hb, tol);
-        if (df) {
-            df[0] = deflate ? 1.0 : 0.0;
-            df[1] = mu;
+    if (threadIdx.x == 0) cheb_setup(s, t, lo, hb, tol);
+    __shared__ int keep;
+    if (!defl_keep(s, t, deflate, mu, lo, hi, tol, kDeflAmp64, df, &keep)) return;
+    const int Ne = s.Ne;
+    double *q = df + kDeflHead;
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        q[j] = ur[j];
+        q[N + j] = ui[j];
+    }
+    // a_e = u^H c_e, one warp per electron
+    const double2 *C = reinterpret_cast<const double2 *>(s.C) + t * (int64_t)Ne * N;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int e = threadIdx.x >> 5; e < Ne; e += nw) {
+        double ar = 0.0, ai = 0.0;
+        for (int j = lane; j < N; j += 32) {
+            const double2 c = C[(int64_t)e * N + j];
+            ar = fma(ur[j], c.x, fma(ui[j], c.y, ar));
+            ai = fma(ur[j], c.y, fma(-ui[j], c.x, ai));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ar += __shfl_xor_sync(0xffffffffu, ar, o);
+            ai += __shfl_xor_sync(0xffffffffu, ai, o);
+        }
+        if (lane == 0) {
+            q[2 * N + e] = ar;
+            q[2 * N + Ne + e] = ai;
         }
     }
-    if (deflate)
-        for (int j = threadIdx.x; j < N; j += blockDim.x) {
-            df[2 + j] = ur[j];
-            df[2 + N + j] = ui[j];
-        }
 }
 
 // Mixed precision: W in FP32.  Each eigenvalue is written relative to its
@@ -347,18 +390,16 @@ __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double m
 // is then the FP32 pole difference (a table rounded once from FP64) plus the
 // difference of the small offsets, so nearly degenerate pairs keep FP32
 // relative accuracy.  The numerators are formed in FP32.
-// dfl (the SIMT propagator k_cheb_f32t deflates): W rows are padded to Np =
-// N + 2 rounded up to 4, and when the top level is isolated (the test of
-// k_build_w) its eigenvector u of the FP32 generator is computed in FP32, to
-// a residual |H u - mu u| <= kDeflRes32
-// |mu - sigma|, about 4 FP32 ulps (the computed residual's own rounding is
-// about one ulp of mu at the top component; one or two iterations on the
-// double well, whose top level couples weakly): the exact term then errs by
-// at most |u^H c| kDeflRes32 |mu - sigma| per step; the iteration is the
-// preconditioned one of k_build_w, in FP32 on H - sigma; Re u and Im u go to the padding columns N and N + 1 of W,
-// where the propagator's row threads of those two rows form u^H T_k in its
-// matvec, and to s.defl as for FP64.
-constexpr float kDeflRes32 = 2.5e-7f;
+// DFL (the mixed propagator deflates): when the top level is isolated (the
+// test of k_build_w) its eigenvector u of the FP32 generator comes from the
+// preconditioned iteration of k_build_w on H - sigma, in FP32 but for the
+// top row (u_top = 1), whose residual is formed in FP64: in FP32 its
+// rounding, about one ulp of mu, would be the floor of the whole residual.
+// It stops at |H u - mu u| <= kDeflRes32 |mu - sigma| |u| (one or two
+// corrections on the double well, whose top level couples weakly), so the
+// eigenvector's error adds no more than about 1e-8 |u^H c| per step.  u, mu
+// and a = u^H c (FP32 products and sums) go to s.defl as for FP64.
+constexpr float kDeflRes32 = 1e-9f;
 
 template <bool DFL>
 __global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, double mass, double tol)
@@ -399,7 +440,7 @@ __global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, doub
     const float a0 = (float)(0.5 * dt * s.vprev[t]), a1 = (float)(0.5 * dt * (s.p[t] / mass));
     __syncthreads();
     float *W = reinterpret_cast<float *>(s.scratch + t * s.scratch_stride);  // [N][Np]
-    const int Np = ((dfl ? N + 2 : N) + 3) & ~3;
+    const int Np = (N + 3) & ~3;
     const float *__restrict__ E = s.epsdiff;  // [M][M] eps_a - eps_b
     double lo = __longlong_as_double(0x7ff0000000000000ll), hi = -lo;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
@@ -430,7 +471,7 @@ __global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, doub
     }
     lo = block_min(lo, red);
     hi = block_max(hi, red);
-    double *df = (dfl && s.defl) ? s.defl + t * (2 * (int64_t)N + 2) : nullptr;
+    double *df = (dfl && s.defl) ? s.defl + t * defl_stride(N, s.Ne) : nullptr;
     bool deflate = false;
     double hb = hi, mu = 0.0;
     if (df && N >= 3 && N <= (int)blockDim.x) {
@@ -443,45 +484,54 @@ __global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, doub
             go = hb_s[top] > b && cheb_terms(0.5 * (b - lo), tol) + kDeflGain <= cheb_terms(0.5 * (hi - lo), tol);
         __syncthreads();
         if (go) {
-            // the preconditioned iteration of k_build_w, on H - sigma in FP32
+            // the preconditioned iteration with u_top = 1 and mu taken from the
+            // top row, mu = ((H - sigma) u)_top (the top thread, in FP64), so
+            // that r_top vanishes and the other rows' residuals are formed
+            // from small quantities in FP32
             const double sigma = 0.5 * (lo + b);
             const int j = threadIdx.x;
-            const bool rj = j < N;
+            const bool rj = j < N, tj = j == top;
             const float Lj = rj ? (float)(Lsum[j] - sigma) : 0.f;
+            __shared__ double s_m;
             if (rj) {
-                ur[j] = j == top ? 1.f : 0.f;
+                ur[j] = tj ? 1.f : 0.f;
                 ui[j] = 0.f;
             }
             __syncthreads();
             for (int it = 0; it < kDeflIter; ++it) {
-                float hr = 0.f, hv = 0.f;
-                if (rj) {
-                    float wr = 0.f, wi = 0.f;  // (W u)_j = -sum_k W[k Np + j] u_k
+                float wr = 0.f, wi = 0.f;  // (W u)_j = -sum_k W[k Np + j] u_k
+                if (rj)
                     for (int k = 0; k < N; ++k) {
                         const float w = W[(int64_t)k * Np + j];
                         wr = fmaf(-w, ur[k], wr);
                         wi = fmaf(-w, ui[k], wi);
                     }
-                    hr = fmaf(Lj, ur[j], wi);  // (H - sigma) u
-                    hv = fmaf(Lj, ui[j], -wr);
+                // (H - sigma) u = (L - sigma) u - i W u; the top row gives mu
+                if (tj) s_m = fma(Lsum[j] - sigma, (double)ur[j], (double)wi);
+                __syncthreads();
+                const double m = s_m;
+                float er = 0.f, ei = 0.f;
+                if (rj && !tj) {
+                    er = fmaf(Lj - (float)m, ur[j], wi);
+                    ei = fmaf(Lj - (float)m, ui[j], -wr);
+                } else if (tj) {
+                    ei = -wr;  // the imaginary part of the top row's residual
                 }
-                const double num = block_sum(rj ? (double)fmaf(ur[j], hr, ui[j] * hv) : 0.0, red);
-                const double den = block_sum(rj ? (double)fmaf(ur[j], ur[j], ui[j] * ui[j]) : 0.0, red);
-                const float m = (float)(num / den);  // Rayleigh quotient of H - sigma
-                const float er = rj ? fmaf(-m, ur[j], hr) : 0.f, ei = rj ? fmaf(-m, ui[j], hv) : 0.f;
                 const double res = block_sum((double)fmaf(er, er, ei * ei), red);
+                const double den = 1.0;  // |u|^2 >= u_top^2 = 1: the test below is conservative
                 if (res <= (double)kDeflRes32 * kDeflRes32 * m * m * den) {  // uniform
-                    deflate = m > 0.f;
-                    mu = sigma + (double)m;
+                    deflate = m > 0.0;
+                    mu = sigma + m;
+                    const double nrm = block_sum(rj ? (double)fmaf(ur[j], ur[j], ui[j] * ui[j]) : 0.0, red);
                     if (rj) {
-                        const float inv = (float)(1.0 / sqrt(den));
+                        const float inv = (float)(1.0 / sqrt(nrm));
                         ur[j] *= inv;
                         ui[j] *= inv;
                     }
                     break;
                 }
-                if (rj && j != top) {
-                    const float d = 1.f / (Lj - m);
+                if (rj && !tj) {
+                    const float d = 1.f / (Lj - (float)m);
                     ur[j] = fmaf(-er, d, ur[j]);
                     ui[j] = fmaf(-ei, d, ui[j]);
                 }
@@ -490,20 +540,36 @@ __global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, doub
             if (deflate) hb = b;
         }
     }
-    if (threadIdx.x == 0) {
-        cheb_setup(s, t, lo, hb, tol);
-        if (df) {
-            df[0] = deflate ? 1.0 : 0.0;
-            df[1] = mu;
+    if (threadIdx.x == 0) cheb_setup(s, t, lo, hb, tol);
+    if (!dfl) return;
+    __shared__ int keep;
+    if (!defl_keep(s, t, deflate, mu, lo, hi, tol, kDeflAmp32, df, &keep)) return;
+    const int Ne = s.Ne;
+    float *q = reinterpret_cast<float *>(df + kDeflHead);  // packed floats
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        q[j] = ur[j];
+        q[N + j] = ui[j];
+    }
+    // a_e = u^H c_e in FP32, one warp per electron
+    const float2 *C = reinterpret_cast<const float2 *>(s.C) + t * (int64_t)Ne * N;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int e = threadIdx.x >> 5; e < Ne; e += nw) {
+        float ar = 0.f, ai = 0.f;
+        for (int j = lane; j < N; j += 32) {
+            const float2 c = C[(int64_t)e * N + j];
+            ar = fmaf(ur[j], c.x, fmaf(ui[j], c.y, ar));
+            ai = fmaf(ur[j], c.y, fmaf(-ui[j], c.x, ai));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ar += __shfl_xor_sync(0xffffffffu, ar, o);
+            ai += __shfl_xor_sync(0xffffffffu, ai, o);
+        }
+        if (lane == 0) {
+            q[2 * N + e] = ar;
+            q[2 * N + Ne + e] = ai;
         }
     }
-    if (deflate)
-        for (int i = threadIdx.x; i < N; i += blockDim.x) {
-            W[(int64_t)i * Np + N] = ur[i];
-            W[(int64_t)i * Np + N + 1] = ui[i];
-            df[2 + i] = ur[i];
-            df[2 + N + i] = ui[i];
-        }
 }
 
 // ============================================================ propagator
@@ -516,8 +582,12 @@ __global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, doub
 // electrons (columns) of one trajectory; thread (g, j) owns orbital row j of
 // the EPT electrons of column group g, so every warp is (nearly) full on the
 // FP64 pipe, which is the bound of this kernel.
+// Deflation (s.defl, flag set by k_build_w): the interval is the bulk one,
+// the series starts from T_0 = c - a u (a = u^H c), and the isolated level's
+// share e^{-i mu} a u is added at the end; the loop is the plain one.
 template <class RT>
 struct Cplx;
+
 template <>
 struct Cplx<double> {
     typedef double2 T;
@@ -527,23 +597,6 @@ struct Cplx<float> {
     typedef float2 T;
 };
 
-// Deflation (s.defl, see k_build_w): when the trajectory's flag is set, the
-// series covers only the bulk interval, and the component along the
-// isolated eigenvector u is taken out and propagated exactly:
-//   exp(-iH) c = e^{-i mu} a u + e^{-ic} sum_k ... T_k(X) (c - a u),  a = u^H c.
-// Each column group then has two more threads, j = N and N + 1, that run the
-// rows' loop over i with Re u and Im u in place of a column of W: they form
-// A = sum_i Re u_i t_i and B = sum_i Im u_i t_i with the same instructions as
-// the rows (an FP64 warp instruction costs its pipe slot whatever its active
-// lanes, so a separate loop would cost a whole pass), and u^H t = (Re A +
-// Im B) + i (Im A - Re B).  The projection needs no extra barrier: with s =
-// u^H T_k, T_k' = T_k - s u and, u being an eigenvector of X with X u = mu_x
-// u, X T_k' = X T_k - s mu_x u.  Every order projects T_k (and carries the
-// projected T_k as the next T_{k-1}), so rounding cannot let the u component
-// grow with the series' value at mu (about 13^k for the double well).  The
-// first order's s is a; the rows correct the J_0 term of the sum by -J_0 a
-// u.  Without the flag (or s.defl null: no extra threads) the arithmetic is
-// the plain series.
 template <int EPT, class RT>
 __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int64_t t_base)
 {
@@ -555,35 +608,22 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
     const int64_t t = traj_of(s, t_base + blockIdx.y);
     if (t < 0 || (s.status[t] & ST_DONE)) return;
     const int N = s.N, Ne = s.Ne;
-    const int NG = s.defl ? N + 2 : N;  // threads per column group
     const int NB = G * EPT, W2 = 2 * NB;
-    const int g = threadIdx.x / NG;
-    const int j = threadIdx.x - g * NG;
-    const bool inr = g < G;
-    const bool act = inr && j < N;         // a row thread
+    const int g = threadIdx.x / N;
+    const int j = threadIdx.x - g * N;
+    const bool act = g < G;
     const int e0 = blockIdx.x * NB + g * EPT;  // first electron of this thread
     const double *cb = s.cheb + t * kChebStride;
     const double c = cb[0], rho = cb[1];
     const int K = (int)cb[2];
     const double *J = cb + 3;
-    const double *df = s.defl ? s.defl + t * (2 * (int64_t)N + 2) : nullptr;
-    const bool defl = df && df[0] != 0.0;  // uniform over the CTA
-    const bool dot = defl && inr && j >= N;  // j = N: A, j = N + 1: B
-    RT *sdot = tk + (size_t)N * W2;           // [G][EPT][A, B][re, im] of the order
-    RT *sa = sdot + 2 * W2;                   // the same for T_0 = c
-    RT *su = sa + 2 * W2;                     // [2N + 1] Re u, Im u, mu_x = (mu - c) / rho
     const RT inv_rho = (RT)(rho > 0.0 ? 1.0 / rho : 0.0);
     const RT *__restrict__ W = reinterpret_cast<const RT *>(s.scratch + t * s.scratch_stride);
-    // the coefficients of thread j: column j of W (stride N), or Re u / Im u
-    const RT *wb = act ? W + j : (dot ? reinterpret_cast<const RT *>(df + 2 + (int64_t)(j - N) * N) : W);
-    const int ws = act ? N : 1;
     CT *C = reinterpret_cast<CT *>(s.C) + (int64_t)t * Ne * N;
     const RT Lc = (RT)(act ? 0.5 * dt * (s.lam_prev[t * N + j] + s.lam[t * N + j]) - c : 0.0);
-    if (defl) {
-        for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) su[i] = (RT)df[2 + i];
-        if (threadIdx.x == 0) su[2 * N] = (RT)((df[1] - c) * (rho > 0.0 ? 1.0 / rho : 0.0));
-    }
-    RT *myrow = tk + (act ? j : 0) * W2 + 2 * EPT * g;
+    RT *myrow = tk + j * W2 + 2 * EPT * g;
+    // deflation: read again after the loop (nothing of it stays in registers)
+    const bool defl0 = s.defl && s.defl[t * defl_stride(N, Ne)] != 0.0;
 
     RT tp[2 * EPT], acc[2 * EPT];
     const RT J0 = (RT)J[0];
@@ -592,7 +632,10 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
         CT v;
         v.x = 0;
         v.y = 0;
-        if (act && e0 + e < Ne) v = C[(int64_t)(e0 + e) * N + j];
+        if (act && e0 + e < Ne) {
+            v = C[(int64_t)(e0 + e) * N + j];
+            if (defl0) v = defl_start<RT>(s.defl + t * defl_stride(N, Ne), N, Ne, j, e0 + e, v);
+        }
         tp[2 * e] = v.x;
         tp[2 * e + 1] = v.y;
         acc[2 * e] = J0 * v.x;
@@ -607,29 +650,14 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
         RT y[2 * EPT];
 #pragma unroll
         for (int q = 0; q < 2 * EPT; ++q) y[q] = 0;
-        if (act || dot) {
+        if (act) {
             const RT *col = tk + 2 * EPT * g;
-            const RT *__restrict__ wp = wb;
 #pragma unroll 4
             for (int i = 0; i < N; ++i) {
-                const RT w = *wp;  // a row: W_ij = -W_ji; else Re u_i or Im u_i
-                wp += ws;
+                const RT w = W[(int64_t)i * N + j];  // W_ij = -W_ji
                 const RT *row = col + i * W2;
 #pragma unroll
                 for (int q = 0; q < 2 * EPT; ++q) y[q] = fma(w, row[q], y[q]);
-            }
-        }
-        if (dot) {
-            const int ab = j - N;  // 0: A, 1: B
-#pragma unroll
-            for (int e = 0; e < EPT; ++e) {
-                RT *d = sdot + (g * EPT + e) * 4 + 2 * ab;
-                d[0] = y[2 * e];
-                d[1] = y[2 * e + 1];
-                if (k == 0) {
-                    d[2 * W2] = y[2 * e];
-                    d[2 * W2 + 1] = y[2 * e + 1];
-                }
             }
         }
         RT own[2 * EPT];
@@ -643,32 +671,10 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
             const int ph = (k + 1) & 3;  // (-i)^(k+1)
 #pragma unroll
             for (int e = 0; e < EPT; ++e) {
-                RT sr = 0, si = 0, ur_j = 0, ui_j = 0, mux = 0;
-                if (defl) {
-                    // s = u^H T_k = (Re A + Im B) + i (Im A - Re B)
-                    const RT *d = sdot + (g * EPT + e) * 4;
-                    sr = d[0] + d[3];
-                    si = d[1] - d[2];
-                    ur_j = su[j];
-                    ui_j = su[N + j];
-                    mux = su[2 * N];
-                }
                 // (X t)_j = ((L_j - c) t_j - i (W t)_j) / rho and (W t)_j = -y.
                 // Explicit FMAs fix the rounding independently of the CTA shape.
-                RT xr = fma(Lc, own[2 * e], -y[2 * e + 1]) * inv_rho;
-                RT xi = fma(Lc, own[2 * e + 1], y[2 * e]) * inv_rho;
-                if (defl) {
-                    // s u_j and the projected T_k and X T_k
-                    const RT pr = fma(sr, ur_j, -(si * ui_j)), pi = fma(sr, ui_j, si * ur_j);
-                    own[2 * e] -= pr;
-                    own[2 * e + 1] -= pi;
-                    xr = fma(-mux, pr, xr);
-                    xi = fma(-mux, pi, xi);
-                    if (k == 0) {  // s = a: the J_0 term becomes J_0 (c - a u)
-                        acc[2 * e] = fma(-J0, pr, acc[2 * e]);
-                        acc[2 * e + 1] = fma(-J0, pi, acc[2 * e + 1]);
-                    }
-                }
+                const RT xr = fma(Lc, own[2 * e], -y[2 * e + 1]) * inv_rho;
+                const RT xi = fma(Lc, own[2 * e + 1], y[2 * e]) * inv_rho;
                 RT nr, ni;
                 if (k == 0) {
                     nr = xr;
@@ -699,12 +705,15 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
         __syncthreads();
     }
     if (act) {
-        double scd, ccd;
+        const double *df = s.defl ? s.defl + t * defl_stride(N, Ne) : nullptr;
+        const bool defl = df && df[0] != 0.0;
+        double scd, ccd, smd = 0.0, cmd = 1.0;
         sincos(c, &scd, &ccd);
+        if (defl) {
+            cmd = df[2];
+            smd = df[3];
+        }
         const RT sc = (RT)scd, cc = (RT)ccd;
-        double smd = 0.0, cmd = 1.0;
-        if (defl) sincos(df[1], &smd, &cmd);
-        const RT sm = (RT)smd, cm = (RT)cmd;
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
             if (e0 + e < Ne) {
@@ -712,16 +721,7 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
                 CT out;
                 out.x = fma(cc, ar, sc * ai);
                 out.y = fma(cc, ai, -(sc * ar));
-                if (defl) {
-                    // + e^{-i mu} a u_j
-                    const RT ur_j = su[j], ui_j = su[N + j];
-                    const RT *d = sa + (g * EPT + e) * 4;
-                    const RT are = d[0] + d[3], aim = d[1] - d[2];
-                    const RT br = fma(are, ur_j, -(aim * ui_j));
-                    const RT bi = fma(are, ui_j, aim * ur_j);
-                    out.x += fma(cm, br, sm * bi);
-                    out.y += fma(cm, bi, -(sm * br));
-                }
+                if (defl) out = defl_end<RT>(df, N, Ne, j, e0 + e, (RT)cmd, (RT)smd, out);
                 C[(int64_t)(e0 + e) * N + j] = out;
             }
         }
@@ -748,13 +748,6 @@ __global__ void __launch_bounds__(1024) k_cheb(DevState s, double dt, int G, int
 // gap after every row quad puts the row quads of consecutive threads 4
 // banks apart, so the per-thread row accesses of the recurrence are
 // conflict-free float4 accesses.
-// Deflation (dfl, s.defl; see k_build_w and k_cheb): W carries Re u and Im u
-// as rows N and N + 1, so the thread of those rows forms A = sum_i Re u_i
-// t_i and B = sum_i Im u_i t_i in the matvec like any row, and publishes
-// them (one more barrier per order); s_k = u^H T_k = (Re A + Im B) + i (Im
-// A - Re B).  The rows then use X T_k' = X T_k - s_k mu_x u and, for the
-// recurrence, T_{k-1}' = T_{k-1} - s_{k-1} u (the buffer holds T_{k-1} as
-// computed, so s is double-buffered by order).
 __device__ __forceinline__ int cheb32_row(int j, int W2) { return j * W2 + ((j >> 2) << 2); }
 
 template <int CE, int QPT>
@@ -765,8 +758,11 @@ __global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1)
     extern __shared__ __align__(16) unsigned char cheb32_smem[];
     const int64_t t = traj_of(s, t_base + blockIdx.y);
     if (t < 0 || (s.status[t] & ST_DONE)) return;
-    const int N = s.N, Ne = s.Ne, Nr = dfl ? N + 2 : N, Np = (Nr + 3) & ~3;  // Nr: rows of W
-    const int nq = (Nr + 3) / 4, nqh = (nq + QPT - 1) / QPT;
+    const int N = s.N, Ne = s.Ne, Np = (N + 3) & ~3;
+    // deflation (set up by k_build_w_f32<true>): start from c - a u, add
+    // e^{-i mu} a u at the end (the flag is read again there)
+    const bool defl0 = dfl && s.defl[t * defl_stride(N, Ne)] != 0.0;
+    const int nq = (N + 3) / 4, nqh = (nq + QPT - 1) / QPT;
     const int W2 = NR * G;
     float *buf0 = reinterpret_cast<float *>(cheb32_smem);
     float *buf1 = buf0 + cheb32_row(Np, W2);
@@ -796,10 +792,10 @@ __global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1)
         s_sc[0] = (float)(rho > 0.0 ? 1.0 / rho : 0.0);
         s_sc[1] = (float)scd;
         s_sc[2] = (float)ccd;
-        double smd = 0.0, cmd = 1.0;  // e^{-i mu} of the deflated level
-        if (dfl && s.defl[t * (2 * (int64_t)s.N + 2)] != 0.0) sincos(s.defl[t * (2 * (int64_t)s.N + 2) + 1], &smd, &cmd);
-        s_sc[3] = (float)smd;
-        s_sc[4] = (float)cmd;
+        if (defl0) {
+            s_sc[3] = (float)s.defl[t * defl_stride(N, Ne) + 3];  // e^{-i mu}
+            s_sc[4] = (float)s.defl[t * defl_stride(N, Ne) + 2];
+        }
     }
     const float *__restrict__ W = reinterpret_cast<const float *>(s.scratch + t * s.scratch_stride);
     float2 *C = reinterpret_cast<float2 *>(s.C) + (int64_t)t * Ne * N;
@@ -816,7 +812,10 @@ __global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1)
 #pragma unroll
             for (int e = 0; e < CE; ++e) {
                 float2 ce = make_float2(0.f, 0.f);
-                if (ok && e0 + e < Ne) ce = C[(int64_t)(e0 + e) * N + j];
+                if (ok && e0 + e < Ne) {
+                    ce = C[(int64_t)(e0 + e) * N + j];
+                    if (defl0) ce = defl_start<float>(s.defl + t * defl_stride(N, Ne), N, Ne, j, e0 + e, ce);
+                }
                 v[2 * e] = ce.x;
                 v[2 * e + 1] = ce.y;
                 acc[r][2 * e] = J0 * ce.x;
@@ -842,16 +841,6 @@ __global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1)
         }
         cp_async_commit();
     };
-    // deflation: s_k of the order, double-buffered [2][G][CE][A, B][re, im];
-    // a = s_0 [G][CE][4]; Re u, Im u, mu_x
-    float *sdot = wring + kCheb32WRing * kCheb32WRows * Np;
-    float *sa = sdot + 8 * CE * G, *su = sa + 4 * CE * G;
-    const double *df = dfl ? s.defl + t * (2 * (int64_t)N + 2) : nullptr;
-    const bool defl = df && df[0] != 0.0;  // uniform over the CTA
-    if (defl) {
-        for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) su[i] = (float)df[2 + i];
-        if (threadIdx.x == 0) su[2 * N] = (float)((df[1] - c) * (rho > 0.0 ? 1.0 / rho : 0.0));
-    }
     for (int g = 0; g < kCheb32WRing - 1; ++g) fetch(g);
     __syncthreads();
     const float inv_rho = s_sc[0];
@@ -915,30 +904,6 @@ __global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1)
                 for (int r = 0; u + r < rows; ++r) row(wp + r * Np, tp + r * W2);
             }
         }
-        const float *sk = sdot + (k & 1) * 4 * CE * G, *skm = sdot + ((k + 1) & 1) * 4 * CE * G;
-        if (defl) {
-            if (act) {
-#pragma unroll
-                for (int h = 0; h < QPT; ++h)
-#pragma unroll
-                    for (int r4 = 0; r4 < 4; ++r4) {
-                        const int j = j0(h) + r4;
-                        if (j == N || j == N + 1) {
-#pragma unroll
-                            for (int e = 0; e < CE; ++e) {
-                                float *d = sdot + (k & 1) * 4 * CE * G + (cg * CE + e) * 4 + 2 * (j - N);
-                                d[0] = y[4 * h + r4][2 * e];
-                                d[1] = y[4 * h + r4][2 * e + 1];
-                                if (k == 0) {
-                                    d[4 * CE * G * 2] = y[4 * h + r4][2 * e];  // sa
-                                    d[4 * CE * G * 2 + 1] = y[4 * h + r4][2 * e + 1];
-                                }
-                            }
-                        }
-                    }
-            }
-            __syncthreads();
-        }
         if (act) {
             const float cj = s_cj[k + 1];
             const int ph = (k + 1) & 3;  // (-i)^(k+1) = (1, 0), (0, -1), (-1, 0), (0, 1)
@@ -969,32 +934,14 @@ __global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1)
 #pragma unroll
                         for (int e = 0; e < CE; ++e) {
                             // (X t)_j = ((L_j - c) t_j - i (W t)_j) / rho and (W t)_j = -y
-                            float xr = fmaf(Lc[r], own[2 * e], -y[r][2 * e + 1]) * inv_rho;
-                            float xi = fmaf(Lc[r], own[2 * e + 1], y[r][2 * e]) * inv_rho;
-                            float *a = acc[r] + 2 * e;
-                            if (defl) {
-                                const int j = j0(h) + r4;
-                                const float urj = su[j], uij = su[N + j], mux = su[2 * N];
-                                const float *d = sk + (cg * CE + e) * 4;
-                                const float sr = d[0] + d[3], si = d[1] - d[2];
-                                const float pr = fmaf(sr, urj, -(si * uij)), pi = fmaf(sr, uij, si * urj);
-                                xr = fmaf(-mux, pr, xr);
-                                xi = fmaf(-mux, pi, xi);
-                                if (k == 0) {  // s_0 = a: the J_0 term becomes J_0 (c - a u)
-                                    a[0] = fmaf(-J0, pr, a[0]);
-                                    a[1] = fmaf(-J0, pi, a[1]);
-                                } else {
-                                    const float *dm = skm + (cg * CE + e) * 4;
-                                    const float qr = dm[0] + dm[3], qi = dm[1] - dm[2];
-                                    prv[2 * e] -= fmaf(qr, urj, -(qi * uij));
-                                    prv[2 * e + 1] -= fmaf(qr, uij, qi * urj);
-                                }
-                            }
+                            const float xr = fmaf(Lc[r], own[2 * e], -y[r][2 * e + 1]) * inv_rho;
+                            const float xi = fmaf(Lc[r], own[2 * e + 1], y[r][2 * e]) * inv_rho;
                             float nr = xr, ni = xi;
                             if (k > 0) {
                                 nr = fmaf(2.f, xr, -prv[2 * e]);
                                 ni = fmaf(2.f, xi, -prv[2 * e + 1]);
                             }
+                            float *a = acc[r] + 2 * e;
                             // acc += cj (-i)^(k+1) n without a branch: (ca, cb) = cj (-i)^(k+1)
                             a[0] = fmaf(ca, nr, fmaf(-cb, ni, a[0]));
                             a[1] = fmaf(ca, ni, fmaf(cb, nr, a[1]));
@@ -1012,6 +959,8 @@ __global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1)
     cp_async_wait<0>();  // no copy outlives the CTA
     if (act) {
         const float sc = s_sc[1], cc = s_sc[2];
+        const double *df = dfl ? s.defl + t * defl_stride(N, Ne) : nullptr;
+        const bool defl = df && df[0] != 0.0;
 #pragma unroll
         for (int h = 0; h < QPT; ++h)
 #pragma unroll
@@ -1022,15 +971,7 @@ __global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1)
                     if (j < N && e0 + e < Ne) {
                         const float ar = acc[r][2 * e], ai = acc[r][2 * e + 1];
                         float2 out = make_float2(fmaf(cc, ar, sc * ai), fmaf(cc, ai, -(sc * ar)));
-                        if (defl) {
-                            // + e^{-i mu} a u_j
-                            const float urj = su[j], uij = su[N + j];
-                            const float *d = sa + (cg * CE + e) * 4;
-                            const float are = d[0] + d[3], aim = d[1] - d[2];
-                            const float br = fmaf(are, urj, -(aim * uij)), bi = fmaf(are, uij, aim * urj);
-                            out.x += fmaf(s_sc[4], br, s_sc[3] * bi);
-                            out.y += fmaf(s_sc[4], bi, -(s_sc[3] * br));
-                        }
+                        if (defl) out = defl_end<float>(df, N, Ne, j, e0 + e, s_sc[4], s_sc[3], out);
                         C[(int64_t)(e0 + e) * N + j] = out;
                     }
             }
@@ -1040,27 +981,24 @@ __global__ void __launch_bounds__(256, QPT == 1 ? 2 : 1)
 // Column groups of k_cheb_f32t: fill the CTA (row slots x groups <= 256)
 // and waste few electron slots; with one row quad per thread two CTAs must
 // fit in an SM's shared memory, with two quads one.
-// With deflation W has N + 2 rows (Re u, Im u) and the CTA keeps the
-// projections (3 x 16 G floats) and u (2N + 1 floats).
-size_t cheb32_smem_bytes(int N, int G, bool defl)
+size_t cheb32_smem_bytes(int N, int G)
 {
-    const int Np = ((defl ? N + 2 : N) + 3) & ~3;
+    const int Np = (N + 3) & ~3;
     // two buffers of padded rows and the ring of W chunks
-    return ((size_t)2 * (Np * 8 * G + Np) + (size_t)kCheb32WRing * kCheb32WRows * Np +
-            (defl ? (size_t)48 * G + 2 * N + 1 : 0)) * sizeof(float);
+    return ((size_t)2 * (Np * 8 * G + Np) + (size_t)kCheb32WRing * kCheb32WRows * Np) * sizeof(float);
 }
-bool cheb32_shape_ok(int N, int G, int qpt, bool defl)
+bool cheb32_shape_ok(int N, int G, int qpt)
 {
-    const int nqh = (((defl ? N + 2 : N) + 3) / 4 + qpt - 1) / qpt;
+    const int nqh = ((N + 3) / 4 + qpt - 1) / qpt;
     return (qpt == 1 || qpt == 2) && G >= 1 && G * nqh <= 256 &&
-           cheb32_smem_bytes(N, G, defl) <= (qpt == 1 ? kCheb32MaxSmem : kCheb32WideMaxSmem);
+           cheb32_smem_bytes(N, G) <= (qpt == 1 ? kCheb32MaxSmem : kCheb32WideMaxSmem);
 }
-void cheb32_shape(int N, int Ne, int &G, int qpt, bool defl)
+void cheb32_shape(int N, int Ne, int &G, int qpt)
 {
-    const int nq = (((defl ? N + 2 : N) + 3) / 4 + qpt - 1) / qpt;
+    const int nq = ((N + 3) / 4 + qpt - 1) / qpt;
     double best = -1.0;
     G = 1;
-    for (int g = 1; g == 1 || cheb32_shape_ok(N, g, qpt, defl); ++g) {
+    for (int g = 1; g == 1 || cheb32_shape_ok(N, g, qpt); ++g) {
         if (g * nq > 256) break;
         const int nb = 4 * g, thr = g * nq, thr32 = (thr + 31) & ~31;
         const int blocks = (Ne + nb - 1) / nb;
@@ -1610,9 +1548,13 @@ cudaError_t launch_force(const DevState &s, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// The mixed path's propagator is the SIMT kernel k_cheb_f32t: requested by
-// shape (cheb_ept 4 or 32), or by default where neither tensor-core kernel
-// fits.
+// Every mixed propagator can deflate (it only changes its start value and
+// adds the exact term), but only the SIMT kernel k_cheb_f32t does by
+// default: requested by shape (cheb_ept 4 or 32), or where neither
+// tensor-core kernel fits.  The tensor-core kernels' orders are cheap enough
+// that the eigenvector set-up costs more than the orders it saves (measured
+// at N = 101, Ne = 50, 4096 trajectories: coupling +0.19 ms, propagation
+// -0.13 ms per step).
 static bool mixed_uses_simt(const DevState &s)
 {
     if (s.cheb_ept == 16 || s.cheb_ept == 8) return false;
@@ -1639,30 +1581,21 @@ cudaError_t launch_coupling(const DevState &s, double dt, double mass, double to
     return cudaGetLastError();
 }
 
-// Threads of a k_cheb CTA: G column groups of N rows, plus the two
-// projection threads of each group when the propagator deflates, rounded up
-// to whole warps.
-int cheb_threads(int N, int G, bool defl)
-{
-    return (G * (N + (defl ? 2 : 0)) + 31) & ~31;
-}
-
 // Column-group shape of k_cheb: EPT electrons per thread and G groups per
-// CTA, chosen to fill warps (row threads close to the CTA's warps x 32, the
-// projection threads counted as overhead) and to waste no electron slots,
-// within 1024 threads.
-void cheb_shape(int N, int Ne, int &ept, int &G, bool defl)
+// CTA, chosen to fill warps (rows x groups close to a multiple of 32) and to
+// waste no electron slots, within 1024 threads.
+void cheb_shape(int N, int Ne, int &ept, int &G)
 {
     double best = -1.0;
     ept = 1;
     G = 1;
     for (int e = 2; e >= 1; --e) {
-        for (int g = 1; cheb_threads(N, g, defl) <= 1024; ++g) {
+        for (int g = 1; g * N <= 1024; ++g) {
             const int nb = g * e;
             if (nb > 2 * Ne + 1) break;
-            const int thr32 = cheb_threads(N, g, defl);
+            const int thr = g * N, thr32 = (thr + 31) & ~31;
             const int blocks = (Ne + nb - 1) / nb;
-            const double eff = (double)(g * N) / thr32 * (double)Ne / (blocks * nb);
+            const double eff = (double)thr / thr32 * (double)Ne / (blocks * nb);
             // prefer larger CTAs at equal efficiency (fewer W reloads)
             const double score = eff + 1e-4 * nb;
             if (score > best) {
@@ -1689,33 +1622,32 @@ cudaError_t launch_cheb(const DevState &s, double dt, bool mixed, cudaStream_t s
         // (N = 256: 24.5 against 29.9 ms per step at 4096 trajectories; at
         // N = 201 it measured 29.4 against 26.2 ms)
         const int qpt = s.cheb_ept == 32 || (s.cheb_ept == 0 && s.N > kCheb32WideMinN) ? 2 : 1;
-        const bool dfl = mixed_deflates(s);
         int G;
-        cheb32_shape(s.N, s.Ne, G, qpt, dfl);
+        cheb32_shape(s.N, s.Ne, G, qpt);
         if (s.cheb_G > 0 && (s.cheb_ept == 4 || s.cheb_ept == 32)) G = s.cheb_G;
-        const int nb = 4 * G, nqh = (((dfl ? s.N + 2 : s.N) + 3) / 4 + qpt - 1) / qpt;
-        const size_t smem = cheb32_smem_bytes(s.N, G, dfl);
+        const int nb = 4 * G, nqh = ((s.N + 3) / 4 + qpt - 1) / qpt;
+        const size_t smem = cheb32_smem_bytes(s.N, G);
         const int threads = (G * nqh + 31) & ~31;
         for (int64_t t0 = 0; t0 < s.n; t0 += 65535) {
             const int64_t cnt = (s.n - t0 < 65535) ? s.n - t0 : 65535;
             dim3 grid((unsigned)((s.Ne + nb - 1) / nb), (unsigned)cnt);
-            if (qpt == 2) k_cheb_f32t<4, 2><<<grid, threads, smem, st>>>(s, dt, G, t0, dfl ? 1 : 0);
-            else k_cheb_f32t<4, 1><<<grid, threads, smem, st>>>(s, dt, G, t0, dfl ? 1 : 0);
+            const int dfl = mixed_deflates(s) ? 1 : 0;
+            if (qpt == 2) k_cheb_f32t<4, 2><<<grid, threads, smem, st>>>(s, dt, G, t0, dfl);
+            else k_cheb_f32t<4, 1><<<grid, threads, smem, st>>>(s, dt, G, t0, dfl);
             const cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
     }
     int ept, G;
-    cheb_shape(s.N, s.Ne, ept, G, s.defl != nullptr);
+    cheb_shape(s.N, s.Ne, ept, G);
     if (s.cheb_ept > 0 && s.cheb_G > 0) {
         ept = s.cheb_ept;
         G = s.cheb_G;
     }
     const int nb = G * ept;
-    // T_k [N][2 nb]; when deflating (A, B) of T_k and of c [nb][4] each, u and mu_x
-    const size_t smem = ((size_t)s.N * 2 * nb + (s.defl ? 8 * nb + 2 * s.N + 1 : 0)) * sizeof(double);
-    const int threads = cheb_threads(s.N, G, s.defl != nullptr);
+    const size_t smem = (size_t)s.N * 2 * nb * sizeof(double);
+    const int threads = (G * s.N + 31) & ~31;
     for (int64_t t0 = 0; t0 < s.n; t0 += 65535) {
         const int64_t cnt = (s.n - t0 < 65535) ? s.n - t0 : 65535;
         dim3 grid((unsigned)((s.Ne + nb - 1) / nb), (unsigned)cnt);

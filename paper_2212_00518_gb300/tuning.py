@@ -20,28 +20,24 @@ from . import iesh as _I
 _CACHE = {}
 
 
-def cheb_candidates(N, Ne, limit=6, precision=0, deflation=True):
+def cheb_candidates(N, Ne, limit=6, precision=0):
     """Propagator shapes ranked by lane and electron-slot efficiency.
 
-    FP64: (ept, G) with ept 1 or 2 electrons per thread and G * NG threads,
-    rounded up to whole warps, within 1024; NG = N + 2 with deflation (two
-    threads per column group form the projections on the isolated
-    eigenvector), else N.  Mixed precision: (4, G), 4 orbitals x 4 electrons per thread
+    FP64: (ept, G) with ept 1 or 2 electrons per thread and G * N <= 1024
+    threads.  Mixed precision: (4, G), 4 orbitals x 4 electrons per thread
     and G * ceil(N / 4) <= 256 threads, two buffers of Np x (8G + 1) floats
     (Np = N rounded up to a multiple of 4) and a ring of 3 x 16 rows of W
     (48 Np floats) in at most 110 KiB; or (32, G), 8 orbitals x 4
     electrons per thread, G * ceil(ceil(N / 4) / 2) <= 256 threads, the same
-    buffers in at most 220 KiB.  With deflation the SIMT kernel's W has N + 2
-    rows (N + 2 in place of N above) and it keeps 48 G + 2 N + 1 more floats."""
+    buffers in at most 220 KiB."""
     out = []
     if precision == _I.PREC_MIXED:
-        nq = -(-(N + 2 if deflation else N) // 4)
+        nq = -(-N // 4)
         Np = 4 * nq
         # (4, G): one row quad per thread, 110 KiB; (32, G): two, 220 KiB
         for ept, nqh, cap in ((4, nq, 110), (32, -(-nq // 2), 220)):
             for G in range(1, 256 // nqh + 1):
-                extra = 48 * G + 2 * N + 1 if deflation else 0
-                if G > 1 and (2 * (Np * 8 * G + Np) + 48 * Np + extra) * 4 > cap * 1024:
+                if G > 1 and (2 * (Np * 8 * G + Np) + 48 * Np) * 4 > cap * 1024:
                     break
                 nb = 4 * G
                 if nb > 4 * Ne + 3:
@@ -51,15 +47,15 @@ def cheb_candidates(N, Ne, limit=6, precision=0, deflation=True):
                 out.append((eff, nb, ept, G))
         out.sort(key=lambda r: (-r[0], -r[1]))
         return [(ept, G) for _, _, ept, G in out[:limit]]
-    NG = N + 2 if deflation else N
     for ept in (2, 1):
         for G in range(1, 1024 // N + 1):
             nb = G * ept
-            thr32 = (G * NG + 31) // 32 * 32
-            if nb > 2 * Ne + 1 or thr32 > 1024:
+            if nb > 2 * Ne + 1:
                 break
+            thr = G * N
+            thr32 = (thr + 31) // 32 * 32
             blocks = -(-Ne // nb)
-            eff = G * N / thr32 * Ne / (blocks * nb)
+            eff = thr / thr32 * Ne / (blocks * nb)
             out.append((eff, nb, ept, G))
     out.sort(key=lambda r: (-r[0], -r[1]))
     return [(ept, G) for _, _, ept, G in out[:limit]]
@@ -91,9 +87,7 @@ def autotune(ctx, x, p, occ, C, dt, steps=3, seed=0):
         return prof["propagate"][0], prof["hop"][0]
 
     default = scratch.kernel_shape()[:2]
-    cands = [default] if default[0] in (8, 16) else cheb_candidates(
-        ctx.N, ctx.Ne, precision=ctx.precision,
-        deflation=ctx.deflation and ctx.propagator == _I.PROP_AVERAGED)
+    cands = [default] if default[0] in (8, 16) else cheb_candidates(ctx.N, ctx.Ne, precision=ctx.precision)
     for ept, G in cands:
         times_cheb[(ept, G)] = trial(ept, G, 0)[0]
     for hop in (0, 256, 512):

@@ -116,29 +116,20 @@ def test_tuner_shapes_within_documented_limits(N):
     accepts by its documented limits: mixed (4, G) with G * ceil(N/4) <= 256
     threads and 8 Np (8G + 1) + 192 Np bytes of shared memory (two buffers
     and the ring of W rows) within 110 KiB for G > 1, or (32, G) with
-    G * ceil(ceil(N/4)/2) <= 256 and the same bytes within 220 KiB (N + 2 in
-    place of N with deflation, plus its 48 G + 2 N + 1 floats); FP64
-    (ept, G) with ept in {1, 2} and G * (N + 2) <= 1024 (G * N without
-    deflation)."""
+    G * ceil(ceil(N/4)/2) <= 256 and the same bytes within 220 KiB; FP64
+    (ept, G) with ept in {1, 2} and G * N <= 1024."""
     from paper_2212_00518_gb300 import tuning
     from paper_2212_00518_gb300 import iesh as I
+    Np = -(-N // 4) * 4
     for Ne in (1, N // 2, N - 1):
         if Ne < 1:
             continue
-        # with deflation the SIMT kernel's W has N + 2 rows and 48 G + 2 N + 1
-        # more floats of shared memory
-        for defl in (True, False):
-            mixed = tuning.cheb_candidates(N, Ne, precision=I.PREC_MIXED, deflation=defl)
-            assert mixed and all(ept in (4, 32) for ept, _ in mixed)
-            nq = -(-(N + 2 if defl else N) // 4)
-            Np = 4 * nq
-            for ept, G in mixed:
-                rows, cap = (nq, 110) if ept == 4 else (-(-nq // 2), 220)
-                extra = 4 * (48 * G + 2 * N + 1) if defl else 0
-                assert G * rows <= 256
-                assert G == 1 or 8 * Np * (8 * G + 1) + 192 * Np + extra <= cap * 1024
-        # deflation adds two threads per column group
+        mixed = tuning.cheb_candidates(N, Ne, precision=I.PREC_MIXED)
+        assert mixed and all(ept in (4, 32) for ept, _ in mixed)
+        for ept, G in mixed:
+            nq = -(-N // 4)
+            rows, cap = (nq, 110) if ept == 4 else (-(-nq // 2), 220)
+            assert G * rows <= 256
+            assert G == 1 or 8 * Np * (8 * G + 1) + 192 * Np <= cap * 1024
         fp64 = tuning.cheb_candidates(N, Ne, precision=I.PREC_FP64)
-        assert fp64 and all(ept in (1, 2) and G * (N + 2) <= 1024 for ept, G in fp64)
-        plain = tuning.cheb_candidates(N, Ne, precision=I.PREC_FP64, deflation=False)
-        assert plain and all(ept in (1, 2) and G * N <= 1024 for ept, G in plain)
+        assert fp64 and all(ept in (1, 2) and G * N <= 1024 for ept, G in fp64)

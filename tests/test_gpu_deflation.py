@@ -1,11 +1,11 @@
-"""GPU checks of the deflated FP64 propagator.
+"""GPU checks of the deflated propagators.
 
 When the top eigenvalue of the step's generator lies apart from the rest of
 the spectrum (Gershgorin discs and interlacing), the Chebyshev series of
-exp(-i dt Abar) (Sec. II C) runs over the bulk interval only, and the
-component along the isolated eigenvector is propagated exactly.  Both forms
-compute the same exponential to within the series tolerance (1e-15 per step
-in FP64), so:
+exp(-i dt Abar) (Sec. II C) runs over the bulk interval only, from c - a u
+(a = u^H c), and the component along the isolated eigenvector is propagated
+exactly.  Both forms compute the same exponential to within the series
+tolerance (1e-15 per step in FP64), so:
   - a deflating context and one with deflation off agree to 1e-12 in C per
     step and take identical hop decisions;
   - trajectories whose series length did not change took the plain path and
@@ -13,8 +13,9 @@ in FP64), so:
   - on the double well (adsorbate level above the band) the series is at
     least two terms shorter for every trajectory;
   - the deflated path matches the oracle's one-step propagation to 1e-12;
-  - every FP64 propagator shape gives the same bits (the projections are
-    summed in one fixed order per electron).
+  - every FP64 propagator shape gives the same bits (the start value and the
+    end term are formed per entry, in a fixed order).
+The mixed path's kernels are held to its one-step bound (C 1e-6).
 """
 import numpy as np
 import pytest
@@ -151,12 +152,12 @@ def _pair_mixed(P, md, n, x, p, occ, C, steps, shape=None, seed=0):
 
 
 @pytest.mark.parametrize("M,shape", [(200, None), (100, (4, 3)), (100, (32, 2))])
-def test_mixed_simt_deflation(P, M, shape):
-    """The SIMT FP32 propagator deflates with its own FP32 eigenvector: the
-    series is at least two terms shorter (or, where the FP32 power iteration
-    does not reach its residual, unchanged), the step agrees with the plain
-    series within the mixed path's one-step bound (C 1e-6) and with the
-    oracle's FP64 step within the same bound."""
+def test_mixed_deflation(P, M, shape):
+    """The SIMT propagator (the default at M = 200, shapes 4 and 32) deflates
+    with the FP32 eigenvector: the series is at least two terms shorter (or,
+    where the FP32 iteration does not reach its residual, unchanged), the
+    step agrees with the plain series within the mixed path's one-step bound
+    (C 1e-6) and with the oracle's FP64 step within the same bound."""
     md = W.double_well(M)
     n = 128
     x, p, occ, C = _state(md, n, 29 + M)
@@ -185,3 +186,16 @@ def test_mixed_deflation_many_steps(P):
     assert np.array_equal(d["occ"], f["occ"]) and np.array_equal(d["hops"], f["hops"])
     assert np.abs(d["C"] - f["C"]).max() <= 30e-6
     assert np.abs(d["p"] - f["p"]).max() <= 1e-5 * np.abs(f["p"]).max()
+
+
+@pytest.mark.parametrize("shape", [None, (8, 1)])
+def test_tensor_core_paths_do_not_deflate(P, shape):
+    """The tensor-core propagators (FP16 split, the default at M = 100;
+    3xTF32, shape 8) keep the full interval: deflating and plain contexts
+    take the same series and give the same bits."""
+    md = W.double_well(100)
+    n = 64
+    x, p, occ, C = _state(md, n, 83)
+    d, f = _pair_mixed(P, md, n, x, p, occ, C, 2, shape)
+    assert np.array_equal(d["K"], f["K"])
+    assert np.array_equal(d["C"], f["C"])
