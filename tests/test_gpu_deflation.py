@@ -199,3 +199,71 @@ def test_tensor_core_paths_do_not_deflate(P, shape):
     d, f = _pair_mixed(P, md, n, x, p, occ, C, 2, shape)
     assert np.array_equal(d["K"], f["K"])
     assert np.array_equal(d["C"], f["C"])
+
+
+def _dt_pair(P, md, n, x, p, occ, C, dt, precision, shape=None):
+    out = []
+    for defl in (True, False):
+        ctx = P.Context(md, n, precision=precision, deflation=defl)
+        if shape:
+            ctx.set_kernel_shape(*shape, 0)
+        ctx.set_state(x, p, occ, C if precision == P.PREC_FP64 else C.astype(np.complex64))
+        ctx.run(dt, 1, seed=0)
+        st = ctx.get_state()
+        st["K"] = np.asarray(ctx.propagator_terms()).copy()
+        ctx.close()
+        out.append(st)
+    return out
+
+
+def test_amplification_guard(P):
+    """With a long time step the bulk series amplifies the u direction by
+    |J_0| + 2 sum |J_k| |T_k(mu_x)| (about 50 at dt = 3, 3e4 at dt = 8 on the
+    double well): FP64 deflates at dt = 3 (bound 1e3) and keeps the full
+    interval at dt = 8, bit for bit; the FP32 SIMT path keeps it at dt = 3
+    (bound 16)."""
+    md = W.double_well(100)
+    n = 32
+    x, p, occ, C = _state(md, n, 91)
+    d, f = _dt_pair(P, md, n, x, p, occ, C, 3.0, P.PREC_FP64)
+    assert np.all(d["K"] <= f["K"] - 2)
+    assert np.abs(d["C"] - f["C"]).max() <= 1e-12
+    d, f = _dt_pair(P, md, n, x, p, occ, C, 8.0, P.PREC_FP64)
+    assert np.array_equal(d["K"], f["K"]) and np.array_equal(d["C"], f["C"])
+    d, f = _dt_pair(P, md, n, x, p, occ, C, 3.0, P.PREC_MIXED, shape=(4, 3))
+    assert np.array_equal(d["K"], f["K"]) and np.array_equal(d["C"], f["C"])
+
+
+@pytest.mark.parametrize("precision,shape", [(0, None), (1, (4, 3))])
+def test_resume_is_bit_exact_while_deflating(P, precision, shape):
+    """The deflation record is rebuilt every step from the state, so a run
+    split by a checkpoint gives the same bits as the undivided run."""
+    md = W.double_well(100)
+    n = 48
+    x, p, occ, C = _state(md, n, 97)
+    C = C if precision == P.PREC_FP64 else C.astype(np.complex64)
+
+    def ctx():
+        c = P.Context(md, n, precision=precision)
+        if shape:
+            c.set_kernel_shape(*shape, 0)
+        return c
+
+    a = ctx()
+    a.set_state(x, p, occ, C)
+    a.run(1.0, 8, seed=4)
+    ref = a.get_state()
+    assert a.propagator_terms().max() <= (10 if precision == 0 else 6)
+    a.close()
+    b = ctx()
+    b.set_state(x, p, occ, C)
+    b.run(1.0, 4, seed=4)
+    blob = b.checkpoint_save()
+    b.close()
+    c = ctx()
+    c.checkpoint_load(blob)
+    c.run(1.0, 4, seed=4)
+    st = c.get_state()
+    c.close()
+    for k in ("x", "p", "occ", "C", "status"):
+        assert np.array_equal(st[k], ref[k]), k
