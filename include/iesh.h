@@ -209,6 +209,26 @@ iesh_status iesh_checkpoint_bytes(iesh_ctx *ctx, size_t *bytes);
 iesh_status iesh_checkpoint_save(iesh_ctx *ctx, void *buf, size_t bytes);
 iesh_status iesh_checkpoint_load(iesh_ctx *ctx, const void *buf, size_t bytes);
 
+/* Advance a batch held in host memory: the same result, bit for bit, as
+ * iesh_checkpoint_load(in), iesh_run(dt, n_steps, seed) and
+ * iesh_checkpoint_save(out), with the copies overlapped with the steps.
+ * The batch is cut into `chunks` trajectory ranges (<= 0: 4).  Range c is
+ * copied in on a stream of its own, stepped on the context's stream once it
+ * has landed, and copied out on a third stream while range c + 1 steps.
+ * Every step kernel treats trajectories independently, so ranges give the
+ * same bits as the whole batch.
+ * in: a checkpoint of iesh_checkpoint_save (host memory, `bytes` long; page
+ *   locked for the copies to overlap).
+ * out: host buffer of the same size for the checkpoint after the steps.  It
+ *   may be `in`: each range is read before it is written.
+ * The context's device state then holds the advanced batch.  Returns after
+ * the copies out have finished.  IESH_EUNSUPPORTED with population records
+ * or the device work list on (their arrays are not trajectory-major);
+ * IESH_EINVAL for a checkpoint that does not match the context, as
+ * iesh_checkpoint_load. */
+iesh_status iesh_run_host(iesh_ctx *ctx, const void *in, void *out, size_t bytes, double dt, int64_t n_steps,
+                          uint64_t seed, int chunks);
+
 /* Observables of every trajectory at its current state (Sec. III C/D):
  * ke[n] = p^2 / 2m, epot[n] = U0(x) + sum_{i in s} lambda_i (the classical
  * IESH Hamiltonian of Sec. II B without the kinetic term), and the impurity

@@ -35,6 +35,9 @@ struct iesh_ctx {
     KernelTimer timer;  // kernel timing
     double *obs = nullptr;        // [4][max_traj] observables
     uint32_t *summary = nullptr;  // [9] status summary
+    // iesh_run_host: copy streams and per-chunk events, made on first use
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    std::vector<cudaEvent_t> ev;
 };
 
 // Launch `fn` (returning cudaError_t), bracketed by events when profiling.
@@ -290,6 +293,12 @@ iesh_status iesh_destroy(iesh_ctx *ctx)
 {
     if (!ctx) return IESH_OK;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (cudaStream_t s : {ctx->s_in, ctx->s_out})
+        if (s) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     ctx->timer.release();
     for (void *p : ctx->allocs) cudaFree(p);
     delete ctx;
@@ -593,10 +602,11 @@ iesh_status iesh_get_records(iesh_ctx *ctx, double *pop_sh, double *pop_wf, int6
 // Enqueue n_steps steps on stream st (the context's own stream for
 // iesh_run, the ensemble's capture stream for iesh_ensemble_create).  With
 // compact_on_cadence the work list is compacted every compact_every steps.
-static iesh_status enqueue_steps(iesh_ctx *ctx, double dt, int64_t n_steps, uint64_t seed, cudaStream_t st,
-                                 bool compact_on_cadence)
+// The step kernels on the trajectories of d (the context's whole state, or
+// a view of a range of it).
+static iesh_status enqueue_steps_on(iesh_ctx *ctx, const DevState &d, double dt, int64_t n_steps, uint64_t seed,
+                                    cudaStream_t st, bool compact_on_cadence)
 {
-    const DevState &d = ctx->ds;
     const bool mx = ctx->mixed;
     // Chebyshev truncation: FP64 rounding level, or FP32 level for the mixed path
     const double tol = ctx->opt.prop_tol > 0.0 ? ctx->opt.prop_tol : (mx ? 1e-7 : 1e-15);
@@ -621,6 +631,41 @@ static iesh_status enqueue_steps(iesh_ctx *ctx, double dt, int64_t n_steps, uint
             CU(tm(IESH_K_OTHER, [&] { return launch_compact(d, ctx->live, ctx->n_live, st); }));
     }
     return IESH_OK;
+}
+
+static iesh_status enqueue_steps(iesh_ctx *ctx, double dt, int64_t n_steps, uint64_t seed, cudaStream_t st,
+                                 bool compact_on_cadence)
+{
+    return enqueue_steps_on(ctx, ctx->ds, dt, n_steps, seed, st, compact_on_cadence);
+}
+
+// View of trajectories [t0, t0 + cnt) of the context's state: every
+// per-trajectory array offset by t0 rows, the Philox id base by t0.  The step
+// kernels treat trajectories independently, so a range gives the same bits
+// as the whole batch.  Records ([max_records][n]) and the work list are not
+// trajectory-major: callers require both off.
+static DevState state_view(const DevState &d, int64_t t0, int64_t cnt, size_t c_bytes)
+{
+    DevState v = d;
+    const int64_t N = d.N, Ne = d.Ne;
+    auto off = [&](auto *&ptr, int64_t per) {
+        if (ptr) ptr += t0 * per;
+    };
+    off(v.x, 1), off(v.p, 1), off(v.F, 1), off(v.dU0, 1), off(v.vprev, 1);
+    off(v.occ, Ne);
+    if (v.C) v.C = static_cast<char *>(v.C) + t0 * Ne * N * (int64_t)c_bytes;
+    off(v.lam, N), off(v.q0, N), off(v.lam_prev, N), off(v.q0_prev, N);
+    off(v.geo, 4), off(v.geo_prev, 4);
+    off(v.status, 1), off(v.nstep, 1), off(v.hops, 1), off(v.frus, 1);
+    off(v.scratch, d.scratch_stride);
+    off(v.cheb, kChebStride);
+    off(v.defl, defl_stride(d.N, d.Ne));
+    off(v.rt, N), off(v.rt_prev, N), off(v.ro, N), off(v.ro_prev, N);
+    off(v.fx, 1), off(v.fx_prev, 1);
+    off(v.q2, N), off(v.q2_prev, N), off(v.geo2, 8), off(v.x_prev, 6), off(v.hop_pair, 1);
+    v.n = cnt;
+    v.traj_base = d.traj_base + (uint64_t)t0;
+    return v;
 }
 
 iesh_status iesh_run(iesh_ctx *ctx, double dt, int64_t n_steps, uint64_t seed)
@@ -875,6 +920,95 @@ iesh_status iesh_checkpoint_load(iesh_ctx *ctx, const void *buf, size_t bytes)
     CU(launch_live_init(h.n, ctx->live, ctx->n_live, ctx->stream));
     if (ctx->opt.compact_every > 0) CU(launch_compact(d, ctx->live, ctx->n_live, ctx->stream));
     if (is_host_ptr(buf)) CU(cudaStreamSynchronize(ctx->stream));
+    ctx->have_state = true;
+    return IESH_OK;
+}
+
+iesh_status iesh_run_host(iesh_ctx *ctx, const void *in, void *out, size_t bytes, double dt, int64_t n_steps,
+                          uint64_t seed, int chunks)
+{
+    if (!ctx || !in || !out) return IESH_EINVAL;
+    if (!(dt > 0.0) || n_steps < 0) return fail(ctx, IESH_EINVAL, "need dt > 0 and n_steps >= 0");
+    if (ctx->ds.max_records > 0 || ctx->opt.compact_every > 0)
+        return fail(ctx, IESH_EUNSUPPORTED, "run_host needs records and the work list off");
+    if (bytes < kCkptHeader) return fail(ctx, IESH_EINVAL, "checkpoint shorter than its header");
+    CkptHeader h;
+    memcpy(&h, in, sizeof h);  // host memory
+    if (memcmp(h.magic, kCkptMagic, 8) != 0) return fail(ctx, IESH_EINVAL, "not an IESH checkpoint");
+    if (h.N != ctx->N || h.Ne != ctx->Ne || h.mixed != (ctx->mixed ? 1 : 0) ||
+        h.propagator != ctx->opt.propagator || h.max_records != 0 || h.record_every != ctx->ds.record_every)
+        return fail(ctx, IESH_EINVAL, "checkpoint of N=%d, Ne=%d, mixed=%d, propagator=%d does not match this context",
+                    h.N, h.Ne, h.mixed, h.propagator);
+    const int64_t n = h.n;
+    if (n < 0 || n > ctx->max_traj)
+        return fail(ctx, IESH_EINVAL, "checkpoint holds %lld trajectories, context at most %lld", (long long)n,
+                    (long long)ctx->max_traj);
+    if (bytes < ckpt_bytes(ctx, n)) return fail(ctx, IESH_EINVAL, "checkpoint truncated");
+    const int nc = (int)std::max<int64_t>(1, std::min<int64_t>(chunks > 0 ? chunks : 4, std::max<int64_t>(n, 1)));
+    if (!ctx->s_in) CU(cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking));
+    if (!ctx->s_out) CU(cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking));
+    while ((int)ctx->ev.size() < 2 * nc + 2) {
+        cudaEvent_t e;
+        CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->ev.push_back(e);
+    }
+    cudaEvent_t *ev_in = ctx->ev.data(), *ev_run = ev_in + nc, ev_start = ev_in[2 * nc], ev_end = ev_in[2 * nc + 1];
+    DevState &d = ctx->ds;
+    d.n = n;
+    // section layout of the blob; every section is linear in the batch size
+    const std::vector<Section> all = ckpt_sections(ctx, n), per = ckpt_sections(ctx, 1);
+    std::vector<size_t> base(all.size());
+    size_t off = kCkptHeader;
+    for (size_t k = 0; k < all.size(); ++k) {
+        base[k] = off;
+        off += (all[k].bytes + 15) & ~(size_t)15;
+    }
+    const char *src = static_cast<const char *>(in);
+    char *dst = static_cast<char *>(out);
+    // the copies in wait for work already queued on the context's stream
+    CU(cudaEventRecord(ev_start, ctx->stream));
+    CU(cudaStreamWaitEvent(ctx->s_in, ev_start, 0));
+    const size_t cb = ctx->mixed ? 8 : 16;
+    auto range = [&](int c, int64_t &t0, int64_t &t1) {
+        t0 = n * c / nc;
+        t1 = n * (c + 1) / nc;
+    };
+    for (int c = 0; c < nc; ++c) {
+        int64_t t0, t1;
+        range(c, t0, t1);
+        for (size_t k = 0; k < all.size(); ++k) {
+            const size_t b = per[k].bytes, len = b * (size_t)(t1 - t0);
+            if (len)
+                CU(cudaMemcpyAsync(static_cast<char *>(all[k].dev) + b * t0, src + base[k] + b * t0, len,
+                                   cudaMemcpyHostToDevice, ctx->s_in));
+        }
+        CU(cudaEventRecord(ev_in[c], ctx->s_in));
+    }
+    for (int c = 0; c < nc; ++c) {
+        int64_t t0, t1;
+        range(c, t0, t1);
+        CU(cudaStreamWaitEvent(ctx->stream, ev_in[c], 0));
+        if (t1 > t0) {
+            const DevState v = state_view(d, t0, t1 - t0, cb);
+            iesh_status st = enqueue_steps_on(ctx, v, dt, n_steps, seed, ctx->stream, false);
+            if (st != IESH_OK) return st;
+        }
+        CU(cudaEventRecord(ev_run[c], ctx->stream));
+        CU(cudaStreamWaitEvent(ctx->s_out, ev_run[c], 0));
+        for (size_t k = 0; k < all.size(); ++k) {
+            const size_t b = per[k].bytes, len = b * (size_t)(t1 - t0);
+            if (len)
+                CU(cudaMemcpyAsync(dst + base[k] + b * t0, static_cast<char *>(all[k].dev) + b * t0, len,
+                                   cudaMemcpyDeviceToHost, ctx->s_out));
+        }
+    }
+    // later work on the context's stream follows the copies out
+    CU(cudaEventRecord(ev_end, ctx->s_out));
+    CU(cudaStreamWaitEvent(ctx->stream, ev_end, 0));
+    CU(cudaStreamSynchronize(ctx->s_out));
+    ctx->steps_since_init = h.steps_since_init + n_steps;
+    h.steps_since_init = ctx->steps_since_init;
+    memcpy(dst, &h, sizeof h);  // after the copies: out may be in
     ctx->have_state = true;
     return IESH_OK;
 }

@@ -86,7 +86,7 @@ EXPORTS = ["iesh_create", "iesh_destroy", "iesh_bath", "iesh_init_state", "iesh_
            "iesh2_destroy", "iesh2_last_error", "iesh2_set_state", "iesh2_get_state", "iesh2_run",
            "iesh2_get_eigen", "iesh2_hop_probabilities", "iesh2_get_counters", "iesh2_profile",
            "iesh2_profile_read", "iesh_checkpoint_bytes", "iesh_checkpoint_save",
-           "iesh_checkpoint_load", "iesh_observables", "iesh_check", "iesh_syev_work_bytes",
+           "iesh_checkpoint_load", "iesh_run_host", "iesh_observables", "iesh_check", "iesh_syev_work_bytes",
            "iesh_syev_batched", "iesh_ensemble_create", "iesh_ensemble_run",
            "iesh_ensemble_status", "iesh_ensemble_destroy", "iesh_ensemble_last_error",
            "iesh_diag_reciprocal"]
@@ -149,6 +149,8 @@ def load(path=LIB_PATH):
     L.iesh_checkpoint_bytes.argtypes = [_vp, _vp]
     L.iesh_checkpoint_save.argtypes = [_vp, _vp, ctypes.c_size_t]
     L.iesh_checkpoint_load.argtypes = [_vp, _vp, ctypes.c_size_t]
+    L.iesh_run_host.argtypes = [_vp, _vp, _vp, ctypes.c_size_t, ctypes.c_double, ctypes.c_int64,
+                                ctypes.c_uint64, ctypes.c_int]
     L.iesh_observables.argtypes = [_vp, _vp, _vp, _vp, _vp]
     L.iesh_check.argtypes = [_vp, _vp]
     L.iesh_ensemble_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int,
@@ -383,6 +385,16 @@ class Context:
         self._check(self.L.iesh_checkpoint_save(self._h, _ptr(buf), int(size)),
                     "iesh_checkpoint_save")
         return buf
+
+    def run_host(self, src, dst, dt, n_steps, seed=0, chunks=0):
+        """Advance the batch held in the host checkpoint `src` by n_steps and
+        write the result to `dst` (may be `src`), copies overlapped with the
+        steps over `chunks` trajectory ranges (iesh_run_host)."""
+        size = src.nbytes if isinstance(src, np.ndarray) else src.numel() * src.element_size()
+        self._check(self.L.iesh_run_host(self._h, _ptr(src), _ptr(dst), int(size), float(dt), int(n_steps),
+                                         int(seed), int(chunks)), "iesh_run_host")
+        hdr = np.asarray(src[:64].cpu() if hasattr(src, "cpu") else src[:64]).view(np.int64)
+        self.n = int(hdr[3])
 
     def checkpoint_load(self, buf):
         size = buf.nbytes if isinstance(buf, np.ndarray) else buf.numel() * buf.element_size()
