@@ -317,13 +317,18 @@ __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double m
             for (int it = 0; it < kDeflIter; ++it) {
                 double hr = 0.0, hv = 0.0;
                 if (rj) {
-                    // (W u)_j = -sum_k W[k N + j] u_k (W antisymmetric; column reads coalesce)
+                    // (W u)_j = -sum_k W[k N + j] u_k (W antisymmetric; column reads
+                    // coalesce); the start u = e_top needs only row top (the other
+                    // terms are exact zeros)
                     double wr = 0.0, wi = 0.0;
-                    for (int k = 0; k < N; ++k) {
-                        const double w = W[(int64_t)k * N + j];
-                        wr = fma(-w, ur[k], wr);
-                        wi = fma(-w, ui[k], wi);
-                    }
+                    if (it == 0)
+                        wr = -W[(int64_t)top * N + j];
+                    else
+                        for (int k = 0; k < N; ++k) {
+                            const double w = W[(int64_t)k * N + j];
+                            wr = fma(-w, ur[k], wr);
+                            wi = fma(-w, ui[k], wi);
+                        }
                     // H u = L u - i W u
                     hr = fma(Lj, ur[j], wi);
                     hv = fma(Lj, ui[j], -wr);
@@ -500,7 +505,9 @@ __global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, doub
             __syncthreads();
             for (int it = 0; it < kDeflIter; ++it) {
                 float wr = 0.f, wi = 0.f;  // (W u)_j = -sum_k W[k Np + j] u_k
-                if (rj)
+                if (rj && it == 0)
+                    wr = -W[(int64_t)top * Np + j];  // u = e_top: the other terms are exact zeros
+                else if (rj)
                     for (int k = 0; k < N; ++k) {
                         const float w = W[(int64_t)k * Np + j];
                         wr = fmaf(-w, ur[k], wr);
