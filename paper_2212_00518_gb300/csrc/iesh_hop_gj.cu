@@ -61,7 +61,7 @@ __device__ __forceinline__ float2 pick_col(const float2 (&z)[kGjRPT][kGjCPT], in
 static_assert(kGjRPT == 4 && kGjCPT == 7, "pick_col covers 4 x 7 register tiles");
 
 template <bool EXT>
-__global__ void __launch_bounds__(kGjThreads, 2) k_hop_gj(DevState s, double dt, double mass, uint64_t seed,
+__global__ void __launch_bounds__(kGjThreads, 3) k_hop_gj(DevState s, double dt, double mass, uint64_t seed,
                                                           double *g_out)
 {
     const int64_t t = traj_of(s, blockIdx.x);

@@ -53,7 +53,7 @@ __device__ __forceinline__ void slot_tree_sum(double *red, int r, bool inslot, i
 // tpb trajectories per CTA, one thread per root.
 // DF: the secular sums in double-float arithmetic (mixed path).
 template <bool DF>
-__global__ void __launch_bounds__(256, 2) k_eigen(DevState s, ModelDev md, double dt, int mode, int tpb)
+__global__ void __launch_bounds__(256, 3) k_eigen(DevState s, ModelDev md, double dt, int mode, int tpb)
 {
     extern __shared__ double sh[];
     const int N = s.N, M = s.M, Ne = s.Ne;
