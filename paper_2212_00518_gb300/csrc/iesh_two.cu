@@ -218,7 +218,7 @@ struct Eig2Slot {
 // the bath poles in double-float arithmetic (mixed path; the bath
 // differences from the context's table, those to h_- per trajectory).
 template <bool DF>
-__global__ void __launch_bounds__(256, 2) k2_eigen(DevState s, Model2Dev md, double dt, int mode, int tpb)
+__global__ void __launch_bounds__(256, 3) k2_eigen(DevState s, Model2Dev md, double dt, int mode, int tpb)
 {
     extern __shared__ double e2_sh[];
     const int N = s.N, M = s.M, Ne = s.Ne;
