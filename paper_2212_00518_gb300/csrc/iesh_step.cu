@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(256) k_build_w(DevState s, double dt, double m
 constexpr float kDeflRes32 = 1e-9f;
 
 template <bool DFL>
-__global__ void __launch_bounds__(256) k_build_w_f32(DevState s, double dt, double mass, double tol)
+__global__ void __launch_bounds__(256, 5) k_build_w_f32(DevState s, double dt, double mass, double tol)
 {
     constexpr int dfl = DFL;  // a template parameter: the plain kernel keeps its registers
     extern __shared__ double sh[];
