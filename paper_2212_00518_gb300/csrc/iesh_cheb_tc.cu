@@ -74,22 +74,17 @@ __device__ __forceinline__ int offA(const TcShape &sh, int row, int k)
     return (row >> 3) * sh.sboA + (k >> 2) * kTcLboA + (row & 7) * 16 + (k & 3) * 4;
 }
 
-template <bool DFL>
 __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt, int64_t t_base)
 {
-    constexpr int dfl = DFL;  // a template parameter: the plain kernel is unchanged
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
     // per-trajectory scalars in FP32, formed once (FP64 work costs every warp
     // that issues it): 2 J_k, 1 / rho, sin c, cos c
-    __shared__ float s_cj[kChebMax], s_sc[5];
+    __shared__ float s_cj[kChebMax], s_sc[3];
     const int64_t t = traj_of(s, t_base + blockIdx.x);
     if (t < 0 || (s.status[t] & ST_DONE)) return;  // uniform over the CTA
     const int N = s.N, Ne = s.Ne, Np = (N + 3) & ~3;
-    // deflation (set up by k_build_w_f32<true>): start from c - a u, add
-    // e^{-i mu} a u at the end (the flag is read again there)
-    const bool defl0 = dfl && s.defl[t * defl_stride(N, Ne)] != 0.0;
     const TcShape sh = tc_shape(N, Ne);
     unsigned char *Ahi = tc_smem, *Alo = tc_smem + sh.bytesA;
     unsigned char *Bhi = tc_smem + 2 * sh.bytesA, *Blo = Bhi + sh.bytesB;
@@ -157,10 +152,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
         sincos(c, &scd, &ccd);
         s_sc[1] = (float)scd;
         s_sc[2] = (float)ccd;
-        if (defl0) {
-            s_sc[3] = (float)s.defl[t * defl_stride(N, Ne) + 3];  // e^{-i mu}
-            s_sc[4] = (float)s.defl[t * defl_stride(N, Ne) + 2];
-        }
     }
     float2 *C = reinterpret_cast<float2 *>(s.C) + (int64_t)t * Ne * N;
     // 2 (L_j - c) / rho, the diagonal's share of 2 X
@@ -180,10 +171,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
             const int col = c0 + 4 * ch + 2 * h, e = col >> 1;
             const bool mine = ch < nch && rowok && e < Ne;
             float2 v = make_float2(0.f, 0.f);
-            if (mine) {
-                v = C[(int64_t)e * N + j];
-                if (defl0) v = defl_start<float>(s.defl + t * defl_stride(N, Ne), N, Ne, j, e, v);
-            }
+            if (mine) v = C[(int64_t)e * N + j];
             prv[4 * ch + 2 * h] = 0.f;
             prv[4 * ch + 2 * h + 1] = 0.f;
             acc[4 * ch + 2 * h] = J0 * v.x;
@@ -296,15 +284,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_cheb_tc(DevState s, double dt
                     C[(int64_t)e * N + j] = make_float2(fmaf(cc, ar, sc * ai), fmaf(cc, ai, -(sc * ar)));
                 }
             }
-        // deflation: add the exact term in a second pass over this thread's
-        // own entries (the accumulators are dead by then)
-        const double *df = dfl ? s.defl + t * defl_stride(N, Ne) : nullptr;
-        if (df && df[0] != 0.0)
-            for (int ch = 0; ch < nch; ++ch)
-                for (int h = 0; h < 2; ++h) {
-                    const int e = (c0 + 4 * ch + 2 * h) >> 1;
-                    if (e < Ne) C[(int64_t)e * N + j] = defl_end<float>(df, N, Ne, j, e, s_sc[4], s_sc[3], C[(int64_t)e * N + j]);
-                }
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -327,8 +306,7 @@ bool cheb_tc_eligible(int N, int Ne)
 
 void configure_cheb_tc()
 {
-    cudaFuncSetAttribute(k_cheb_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChebTcMaxSmem);
-    cudaFuncSetAttribute(k_cheb_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChebTcMaxSmem);
+    cudaFuncSetAttribute(k_cheb_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChebTcMaxSmem);
     cudaGetLastError();
 }
 
@@ -339,8 +317,7 @@ cudaError_t launch_cheb_tc(const DevState &s, double dt, cudaStream_t st)
     const size_t smem = cheb_tc_smem_bytes(s.N, s.Ne);
     for (int64_t t0 = 0; t0 < s.n; t0 += 2147483647LL) {
         const int64_t cnt = (s.n - t0 < 2147483647LL) ? s.n - t0 : 2147483647LL;
-        if (mixed_deflates(s)) k_cheb_tc<true><<<(unsigned)cnt, kTcThreads, smem, st>>>(s, dt, t0);
-        else k_cheb_tc<false><<<(unsigned)cnt, kTcThreads, smem, st>>>(s, dt, t0);
+        k_cheb_tc<<<(unsigned)cnt, kTcThreads, smem, st>>>(s, dt, t0);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -23,9 +23,6 @@
 // MMAs do.  T_k for the recurrence is read back from its own B entries (hi
 // + lo), T_{k-1} is held in registers.
 //
-// Deflation (dfl; the top level set up by k_build_w_f32<true>): the series
-// starts from c - a u and the write-back adds e^{-i mu} a u.
-//
 // One CTA per trajectory, 512 threads: warp w reads TMEM lanes 32 (w % 4) ..
 // +31 (orbital row j = 32 (w % 4) + lane) and owns the electrons e = 4q + w/4
 // (so that each thread's B entries step by one 8-column group per electron).  Each order: one thread issues the 3 x K/16 MMAs
@@ -104,19 +101,15 @@ __device__ __forceinline__ void split16x2(float xr, float xi, __half2 &hi, __hal
     lo = __floats2half2_rn(xr - hf.x, xi - hf.y);
 }
 
-template <bool DFL>
 __global__ void __launch_bounds__(kT16Threads, 2) k_cheb_tc16(DevState s, double dt, int64_t t_base)
 {
-    constexpr int dfl = DFL;  // a template parameter: the plain kernel is unchanged
     extern __shared__ __align__(1024) unsigned char t16_smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
-    __shared__ float s_cj[kChebMax], s_sc[5];
+    __shared__ float s_cj[kChebMax], s_sc[3];
     const int64_t t = traj_of(s, t_base + blockIdx.x);
     if (t < 0 || (s.status[t] & ST_DONE)) return;  // uniform over the CTA
     const int N = s.N, Ne = s.Ne, Np = (N + 3) & ~3;
-    const double *df = dfl ? s.defl + t * defl_stride(N, Ne) : nullptr;
-    const bool defl = df && df[0] != 0.0;
     const T16Shape sh = t16_shape(N, Ne);
     unsigned char *Ahi = t16_smem, *Alo = t16_smem + sh.usedA;
     unsigned char *Bhi = t16_smem + 2 * sh.usedA, *Blo = Bhi + sh.bytesB;
@@ -174,10 +167,6 @@ __global__ void __launch_bounds__(kT16Threads, 2) k_cheb_tc16(DevState s, double
         sincos(c, &scd, &ccd);
         s_sc[1] = (float)scd;
         s_sc[2] = (float)ccd;
-        if (defl) {
-            s_sc[3] = (float)df[3];  // e^{-i mu}
-            s_sc[4] = (float)df[2];
-        }
     }
     __syncthreads();  // B zeroed before the T_0 entries land; TMEM base published
     tc::fence_after_sync();
@@ -200,10 +189,7 @@ __global__ void __launch_bounds__(kT16Threads, 2) k_cheb_tc16(DevState s, double
             const int e = 4 * (q + h) + cg;
             const bool mine = q + h < npair && rowok && e < Ne;
             float2 v = make_float2(0.f, 0.f);
-            if (mine) {
-                v = C[(int64_t)e * N + j];
-                if (defl) v = defl_start<float>(df, N, Ne, j, e, v);
-            }
+            if (mine) v = C[(int64_t)e * N + j];
             prv[2 * (q + h)] = 0.f;
             prv[2 * (q + h) + 1] = 0.f;
             a[2 * h] = J0 * v.x;
@@ -322,9 +308,7 @@ __global__ void __launch_bounds__(kT16Threads, 2) k_cheb_tc16(DevState s, double
                 const int e = 4 * (q + h) + cg;
                 if (q + h < npair && rowok && e < Ne) {
                     const float ar = a[2 * h], ai = a[2 * h + 1];
-                    float2 out = make_float2(fmaf(cc, ar, sc * ai), fmaf(cc, ai, -(sc * ar)));
-                    if (defl) out = defl_end<float>(df, N, Ne, j, e, s_sc[4], s_sc[3], out);
-                    C[(int64_t)e * N + j] = out;
+                    C[(int64_t)e * N + j] = make_float2(fmaf(cc, ar, sc * ai), fmaf(cc, ai, -(sc * ar)));
                 }
             }
         }
@@ -346,11 +330,9 @@ bool cheb_tc16_eligible(int N, int Ne)
 
 void configure_cheb_tc16()
 {
-    for (auto fn : {k_cheb_tc16<false>, k_cheb_tc16<true>}) {
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChebTc16MaxSmem);
+    cudaFuncSetAttribute(k_cheb_tc16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChebTc16MaxSmem);
     // all of the unified L1 / shared memory as shared, so that two CTAs fit
-        cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    }
+    cudaFuncSetAttribute(k_cheb_tc16, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaGetLastError();
 }
 
@@ -361,8 +343,7 @@ cudaError_t launch_cheb_tc16(const DevState &s, double dt, cudaStream_t st)
     const size_t smem = cheb_tc16_smem_bytes(s.N, s.Ne);
     for (int64_t t0 = 0; t0 < s.n; t0 += 2147483647LL) {
         const int64_t cnt = (s.n - t0 < 2147483647LL) ? s.n - t0 : 2147483647LL;
-        if (mixed_deflates(s)) k_cheb_tc16<true><<<(unsigned)cnt, kT16Threads, smem, st>>>(s, dt, t0);
-        else k_cheb_tc16<false><<<(unsigned)cnt, kT16Threads, smem, st>>>(s, dt, t0);
+        k_cheb_tc16<<<(unsigned)cnt, kT16Threads, smem, st>>>(s, dt, t0);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -51,7 +51,7 @@ constexpr int kCheb32WRing = 3;  // chunks in the ring (filled 2 ahead)
 size_t cheb32_smem_bytes(int N, int G);
 void cheb32_shape(int N, int Ne, int &G, int qpt = 1);
 bool cheb32_shape_ok(int N, int G, int qpt);
-// the mixed propagators deflate (k_build_w_f32<true> sets the level up)
+// the mixed SIMT propagator deflates (k_build_w_f32<true> sets the level up)
 bool mixed_deflates(const DevState &s);
 // FP32 propagator on the tensor cores (3xTF32), N <= 128 and Ne <= 56
 constexpr size_t kChebTcMaxSmem = 224 * 1024;

@@ -1555,13 +1555,12 @@ cudaError_t launch_force(const DevState &s, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// Every mixed propagator can deflate (it only changes its start value and
-// adds the exact term), but only the SIMT kernel k_cheb_f32t does by
-// default: requested by shape (cheb_ept 4 or 32), or where neither
-// tensor-core kernel fits.  The tensor-core kernels' orders are cheap enough
-// that the eigenvector set-up costs more than the orders it saves (measured
-// at N = 101, Ne = 50, 4096 trajectories: coupling +0.19 ms, propagation
-// -0.13 ms per step).
+// The mixed path deflates on the SIMT kernel k_cheb_f32t only: requested by
+// shape (cheb_ept 4 or 32), or where neither tensor-core kernel fits.  The
+// tensor-core kernels' orders are cheap enough that the eigenvector set-up
+// costs more than the orders it saves (measured with a deflating FP16 split
+// kernel at N = 101, Ne = 50, 4096 trajectories: coupling +0.19 ms,
+// propagation -0.13 ms per step), so they keep the full interval.
 static bool mixed_uses_simt(const DevState &s)
 {
     if (s.cheb_ept == 16 || s.cheb_ept == 8) return false;
