@@ -224,8 +224,8 @@ iesh_status iesh_checkpoint_load(iesh_ctx *ctx, const void *buf, size_t bytes);
  * The context's device state then holds the advanced batch.  Returns after
  * the copies out have finished.  IESH_EUNSUPPORTED with population records
  * or the device work list on (their arrays are not trajectory-major);
- * IESH_EINVAL for a checkpoint that does not match the context, as
- * iesh_checkpoint_load. */
+ * IESH_EINVAL for device buffers, or for a checkpoint that does not match
+ * the context, as iesh_checkpoint_load. */
 iesh_status iesh_run_host(iesh_ctx *ctx, const void *in, void *out, size_t bytes, double dt, int64_t n_steps,
                           uint64_t seed, int chunks);
 

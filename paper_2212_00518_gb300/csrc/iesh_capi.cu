@@ -929,6 +929,7 @@ iesh_status iesh_run_host(iesh_ctx *ctx, const void *in, void *out, size_t bytes
 {
     if (!ctx || !in || !out) return IESH_EINVAL;
     if (!(dt > 0.0) || n_steps < 0) return fail(ctx, IESH_EINVAL, "need dt > 0 and n_steps >= 0");
+    if (!is_host_ptr(in) || !is_host_ptr(out)) return fail(ctx, IESH_EINVAL, "run_host needs host buffers");
     if (ctx->ds.max_records > 0 || ctx->opt.compact_every > 0)
         return fail(ctx, IESH_EUNSUPPORTED, "run_host needs records and the work list off");
     if (bytes < kCkptHeader) return fail(ctx, IESH_EINVAL, "checkpoint shorter than its header");

@@ -90,5 +90,10 @@ def test_run_host_refusals(P):
     other = P.Context(W.double_well(30), n)
     with pytest.raises(P.iesh.IeshError):
         other.run_host(blob, blob.copy(), 1.0, 1)
+    # device buffers: the call is for host memory
+    import torch
+    dev = torch.from_numpy(blob).cuda()
+    with pytest.raises(P.iesh.IeshError):
+        a.run_host(dev, dev, 1.0, 1)
     for ctx in (a, r, other):
         ctx.close()
