@@ -213,7 +213,7 @@ __global__ void k_force(DevState s)
 // which has no u component in exact arithmetic, so no later order needs a
 // projection; the u components that rounding leaves in later orders are
 // carried by the series, whose value at mu is bounded by cheb_amplification
-// (about 7 on the double well): with that bound above kDeflAmp64 (FP64) or
+// (4 to 8 on the double well at dt = 1): with that bound above kDeflAmp64 (FP64) or
 // kDeflAmp32 (FP32) the full interval is used.  u comes from a diagonally preconditioned fixed-point
 // iteration (the Jacobi correction of Davidson's method): u_top = 1, mu the
 // Rayleigh quotient, r = H u - mu u, u_k -= r_k / (L_k - mu) for k != top.
